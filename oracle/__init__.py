@@ -1,0 +1,410 @@
+"""CPU oracle of the preconditioned Krylov path — TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, single-threaded FP64 reference implementations of every step of
+the path (SpMV, BLAS-1, ILU(0), block ILU(0), triangular solves, quasi-IMPES
+CPR, GMRES / FGMRES / BiCGSTAB) in plain C (oracle.c), plus the learned
+pressure stage in numpy (convnet.py).  Only the test suite, the smoke check
+and the benchmark's CPU-baseline leg may import this package.  It shares no
+code with the CUDA library; inputs come from the seeded generators in
+``synth``.
+
+Parity status: every function here is pinned by tests/test_oracle_pins.py
+against closed forms, brute force or textbook special cases.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+OK, NOT_CONVERGED, INVALID, ZERO_PIVOT, BREAKDOWN = 0, 1, -1, -3, -4
+PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CALLBACK = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, -ffp-contract=off)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-std=c11", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(_LIB)
+        _declare(_lib)
+    return _lib
+
+
+# ----------------------------------------------------------------------------
+# ctypes structures (mirrors of the structs in oracle.c)
+# ----------------------------------------------------------------------------
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+_f32p = C.POINTER(C.c_float)
+APPLY_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, _f64p, _f64p)
+
+
+class _Mat(C.Structure):
+    _fields_ = [("bs", C.c_int32), ("nrows", C.c_int32), ("ptr", _i32p),
+                ("col", _i32p), ("val", _f64p)]
+
+
+class _PC(C.Structure):
+    _fields_ = [("type", C.c_int32), ("mixed", C.c_int32),
+                ("n", C.c_int32), ("ptr", _i32p), ("col", _i32p),
+                ("lu", _f64p), ("lu32", _f32p),
+                ("nb", C.c_int32), ("bs", C.c_int32), ("bptr", _i32p), ("bcol", _i32p),
+                ("blu", _f64p), ("bdinv", _f64p), ("blu32", _f32p), ("bdinv32", _f32p),
+                ("A", C.POINTER(_Mat)), ("w", _f64p),
+                ("pstage", APPLY_FN), ("pstage_user", C.c_void_p),
+                ("fn", APPLY_FN), ("user", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32),
+                ("pad", C.c_int32), ("true_rel_res", C.c_double),
+                ("implicit_rel_res", C.c_double)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, restarts=self.restarts, status=self.status,
+                    true_rel_res=self.true_rel_res, implicit_rel_res=self.implicit_rel_res)
+
+
+def _declare(L):
+    mp = C.POINTER(_Mat)
+    L.or_spmv.argtypes = [mp, _f64p, _f64p]
+    L.or_amxpby.argtypes = [C.c_double, mp, _f64p, C.c_double, _f64p]
+    L.or_axpby.argtypes = [C.c_int64, C.c_double, _f64p, C.c_double, _f64p]
+    L.or_axpbyz.argtypes = [C.c_int64, C.c_double, _f64p, C.c_double, _f64p, _f64p]
+    L.or_dot.argtypes = [C.c_int64, _f64p, _f64p]
+    L.or_dot.restype = C.c_double
+    L.or_norm2.argtypes = [C.c_int64, _f64p]
+    L.or_norm2.restype = C.c_double
+    L.or_set.argtypes = [C.c_int64, C.c_double, _f64p]
+    L.or_ilu0.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _i32p]
+    L.or_ilu0_solve.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
+    L.or_ilu0_solve_f32.argtypes = [C.c_int32, _i32p, _i32p, _f32p, _f64p, _f64p]
+    L.or_bilu0.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _i32p]
+    L.or_bilu0_solve.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+    L.or_bilu0_solve_f32.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, _f32p, _f32p, _f64p, _f64p]
+    L.or_qimpes_weights.argtypes = [mp, _f64p]
+    L.or_qimpes_app.argtypes = [mp, _f64p, _f64p]
+    L.or_qimpes_restrict.argtypes = [C.c_int32, C.c_int32, _f64p, _f64p, _f64p]
+    L.or_prolong.argtypes = [C.c_int32, C.c_int32, _f64p, _f64p]
+    L.or_pc_apply.argtypes = [C.POINTER(_PC), C.c_int64, _f64p, _f64p]
+    L.or_orthogonalise.argtypes = [C.c_int64, C.c_int32, _f64p, _f64p, _f64p, C.c_int32]
+    L.or_gmres.argtypes = [mp, C.POINTER(_PC), _f64p, _f64p, C.c_int32, C.c_double, C.c_int32,
+                           C.c_int32, C.c_int32, C.c_int32, _f64p, C.c_int32, C.POINTER(Info)]
+    L.or_bicgstab.argtypes = [mp, C.POINTER(_PC), _f64p, _f64p, C.c_double, C.c_int32,
+                              _f64p, C.c_int32, C.POINTER(Info)]
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ----------------------------------------------------------------------------
+# Matrices
+# ----------------------------------------------------------------------------
+class Mat:
+    """CSR (bs=1) or BSR matrix held for the oracle."""
+
+    def __init__(self, ptr, col, val, bs: int = 1):
+        self.bs = int(bs)
+        self.ptr, self.col, self.val = _i32(ptr), _i32(col), _f64(val)
+        self.nrows = self.ptr.shape[0] - 1
+        self.n = self.nrows * self.bs
+        self.s = _Mat(self.bs, self.nrows, _p(self.ptr, C.c_int32), _p(self.col, C.c_int32),
+                      _p(self.val, C.c_double))
+
+    @classmethod
+    def csr(cls, m: dict):
+        return cls(m["rowptr"], m["col"], m["val"], 1)
+
+    @classmethod
+    def bsr(cls, m: dict):
+        return cls(m["browptr"], m["bcol"], m["bval"], m["bs"])
+
+
+def spmv(A: Mat, x):
+    x = _f64(x)
+    y = np.empty(A.n)
+    lib().or_spmv(C.byref(A.s), _p(x, C.c_double), _p(y, C.c_double))
+    return y
+
+
+def amxpby(a, A: Mat, x, b, y):
+    x = _f64(x)
+    y = _f64(y).copy()
+    lib().or_amxpby(a, C.byref(A.s), _p(x, C.c_double), b, _p(y, C.c_double))
+    return y
+
+
+def axpby(a, x, b, y):
+    x, y = _f64(x), _f64(y).copy()
+    lib().or_axpby(x.size, a, _p(x, C.c_double), b, _p(y, C.c_double))
+    return y
+
+
+def axpbyz(a, x, b, y):
+    x, y = _f64(x), _f64(y)
+    z = np.empty_like(x)
+    lib().or_axpbyz(x.size, a, _p(x, C.c_double), b, _p(y, C.c_double), _p(z, C.c_double))
+    return z
+
+
+def dot(x, y):
+    x, y = _f64(x), _f64(y)
+    return lib().or_dot(x.size, _p(x, C.c_double), _p(y, C.c_double))
+
+
+def norm2(x):
+    x = _f64(x)
+    return lib().or_norm2(x.size, _p(x, C.c_double))
+
+
+def set_value(n, v):
+    x = np.empty(n)
+    lib().or_set(n, v, _p(x, C.c_double))
+    return x
+
+
+# ----------------------------------------------------------------------------
+# Factorisations and triangular solves
+# ----------------------------------------------------------------------------
+def ilu0(A: Mat):
+    """ILU(0) factors in A's pattern; returns (status, bad_row, lu)."""
+    assert A.bs == 1
+    lu = np.empty_like(A.val)
+    bad = C.c_int32(-1)
+    st = lib().or_ilu0(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
+                       _p(A.val, C.c_double), _p(lu, C.c_double), C.byref(bad))
+    return st, bad.value, lu
+
+
+def ilu0_solve(A: Mat, lu, r, fp32: bool = False):
+    r = _f64(r)
+    z = np.empty(A.n)
+    if fp32:
+        lu32 = np.ascontiguousarray(lu, dtype=np.float32)
+        lib().or_ilu0_solve_f32(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
+                                _p(lu32, C.c_float), _p(r, C.c_double), _p(z, C.c_double))
+    else:
+        lu = _f64(lu)
+        lib().or_ilu0_solve(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
+                            _p(lu, C.c_double), _p(r, C.c_double), _p(z, C.c_double))
+    return z
+
+
+def bilu0(A: Mat):
+    """Block ILU(0); returns (status, bad_block_row, lu, dinv)."""
+    lu = np.empty_like(A.val)
+    dinv = np.empty(A.nrows * A.bs * A.bs)
+    bad = C.c_int32(-1)
+    st = lib().or_bilu0(A.nrows, A.bs, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
+                        _p(A.val, C.c_double), _p(lu, C.c_double), _p(dinv, C.c_double),
+                        C.byref(bad))
+    return st, bad.value, lu, dinv
+
+
+def bilu0_solve(A: Mat, lu, dinv, r, fp32: bool = False):
+    r = _f64(r)
+    z = np.empty(A.n)
+    if fp32:
+        lu32 = np.ascontiguousarray(lu, dtype=np.float32)
+        d32 = np.ascontiguousarray(dinv, dtype=np.float32)
+        lib().or_bilu0_solve_f32(A.nrows, A.bs, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
+                                 _p(lu32, C.c_float), _p(d32, C.c_float),
+                                 _p(r, C.c_double), _p(z, C.c_double))
+    else:
+        lib().or_bilu0_solve(A.nrows, A.bs, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
+                             _p(_f64(lu), C.c_double), _p(_f64(dinv), C.c_double),
+                             _p(r, C.c_double), _p(z, C.c_double))
+    return z
+
+
+def qimpes_weights(A: Mat):
+    w = np.empty(A.nrows * (A.bs - 1))
+    lib().or_qimpes_weights(C.byref(A.s), _p(w, C.c_double))
+    return w
+
+
+def qimpes_app(A: Mat, w):
+    w = _f64(w)
+    app = np.empty(A.col.shape[0])
+    lib().or_qimpes_app(C.byref(A.s), _p(w, C.c_double), _p(app, C.c_double))
+    return app
+
+
+def qimpes_restrict(nb, bs, w, f):
+    w, f = _f64(w), _f64(f)
+    rp = np.empty(nb)
+    lib().or_qimpes_restrict(nb, bs, _p(w, C.c_double), _p(f, C.c_double), _p(rp, C.c_double))
+    return rp
+
+
+def prolong(nb, bs, p):
+    p = _f64(p)
+    z = np.empty(nb * bs)
+    lib().or_prolong(nb, bs, _p(p, C.c_double), _p(z, C.c_double))
+    return z
+
+
+def orthogonalise(V, w, i, mgs=False):
+    """CGS2 (or MGS) step against columns 0..i of V (shape (k, n), row k = v_k)."""
+    V = _f64(V)
+    w = _f64(w).copy()
+    n = w.size
+    h = np.zeros(i + 2)
+    lib().or_orthogonalise(n, i, _p(V, C.c_double), _p(w, C.c_double), _p(h, C.c_double), int(mgs))
+    return w, h
+
+
+# ----------------------------------------------------------------------------
+# Preconditioners
+# ----------------------------------------------------------------------------
+class PC:
+    """Oracle preconditioner: none / ilu0 / bilu0 / cpr / callback.
+
+    kind='cpr' on a BSR matrix: quasi-IMPES restriction, ILU(0) of App'
+    (or `pstage`, a callable rp -> zp), prolongation, residual, block ILU(0).
+    kind='cpr' on a CSR matrix (bs=1): restriction = identity, App' = A,
+    second stage = ILU(0) of A.
+    """
+
+    def __init__(self, A: Mat, kind: str = "ilu0", mixed: bool = False, pstage=None, fn=None):
+        self.A = A
+        self.kind = kind
+        self._keep = []
+        s = _PC()
+        s.mixed = int(mixed)
+        self.status = OK
+        if kind == "none":
+            s.type = PC_NONE
+        elif kind == "ilu0":
+            st, bad, lu = ilu0(A)
+            self.status, self.bad = st, bad
+            self.lu = lu
+            self._set_ilu(s, A.ptr, A.col, A.nrows, lu)
+            s.type = PC_ILU0
+        elif kind == "bilu0":
+            self._set_bilu(s, A)
+            s.type = PC_BILU0
+        elif kind == "cpr":
+            self._set_bilu(s, A)
+            if A.bs > 1:
+                self.w = qimpes_weights(A)
+                self.app_val = qimpes_app(A, self.w)
+            else:
+                self.w = np.zeros(0)
+                self.app_val = A.val.copy()
+            self.App = Mat(A.ptr, A.col, self.app_val, 1)
+            st, bad, lu = ilu0(self.App)
+            if st != OK:
+                self.status, self.bad = st, bad
+            self.lu = lu
+            self._set_ilu(s, A.ptr, A.col, A.nrows, lu)
+            s.A = C.pointer(A.s)
+            s.w = _p(self.w, C.c_double) if self.w.size else None
+            if pstage is not None:
+                s.pstage = self._wrap(pstage)
+            s.type = PC_CPR
+        elif kind == "callback":
+            s.fn = self._wrap(fn)
+            s.type = PC_CALLBACK
+        else:
+            raise ValueError(kind)
+        self.s = s
+
+    def _wrap(self, f):
+        def cb(user, n, r, z):
+            rv = np.ctypeslib.as_array(r, shape=(n,))
+            zv = np.ctypeslib.as_array(z, shape=(n,))
+            zv[:] = f(rv.copy())
+            return 0
+        cfn = APPLY_FN(cb)
+        self._keep.append(cfn)
+        return cfn
+
+    def _set_ilu(self, s, ptr, col, n, lu):
+        self.lu32 = lu.astype(np.float32)
+        self._keep += [ptr, col, lu, self.lu32]
+        s.n = n
+        s.ptr, s.col = _p(ptr, C.c_int32), _p(col, C.c_int32)
+        s.lu, s.lu32 = _p(lu, C.c_double), _p(self.lu32, C.c_float)
+
+    def _set_bilu(self, s, A):
+        st, bad, blu, dinv = bilu0(A)
+        self.bstatus = st
+        if st != OK:
+            self.status, self.bad = st, bad
+        self.blu, self.bdinv = blu, dinv
+        self.blu32, self.bdinv32 = blu.astype(np.float32), dinv.astype(np.float32)
+        self._keep += [blu, dinv, self.blu32, self.bdinv32]
+        s.nb, s.bs = A.nrows, A.bs
+        s.bptr, s.bcol = _p(A.ptr, C.c_int32), _p(A.col, C.c_int32)
+        s.blu, s.bdinv = _p(blu, C.c_double), _p(dinv, C.c_double)
+        s.blu32, s.bdinv32 = _p(self.blu32, C.c_float), _p(self.bdinv32, C.c_float)
+
+    def apply(self, r):
+        r = _f64(r)
+        z = np.empty_like(r)
+        st = lib().or_pc_apply(C.byref(self.s), r.size, _p(r, C.c_double), _p(z, C.c_double))
+        if st != OK:
+            raise RuntimeError("oracle preconditioner apply failed: %d" % st)
+        return z
+
+
+# ----------------------------------------------------------------------------
+# Solvers
+# ----------------------------------------------------------------------------
+def gmres(A: Mat, M: PC | None, b, x0=None, restart=30, rtol=1e-8, maxit=10000,
+          side="right", flexible=False, mgs=False, hist_len=0):
+    """Restarted GMRES(m) / FGMRES(m); returns (x, info dict, history)."""
+    b = _f64(b)
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    info = Info()
+    hist = np.zeros(max(hist_len, 1))
+    Ms = M.s if M is not None else PC(A, "none").s
+    lib().or_gmres(C.byref(A.s), C.byref(Ms), _p(b, C.c_double), _p(x, C.c_double),
+                   restart, rtol, maxit, 1 if side == "left" else 0, int(flexible), int(mgs),
+                   _p(hist, C.c_double), hist_len, C.byref(info))
+    return x, info.as_dict(), hist[:min(hist_len, info.iters)]
+
+
+def fgmres(A, M, b, x0=None, restart=30, rtol=1e-8, maxit=10000, hist_len=0):
+    return gmres(A, M, b, x0, restart, rtol, maxit, "right", True, False, hist_len)
+
+
+def bicgstab(A: Mat, M: PC | None, b, x0=None, rtol=1e-8, maxit=10000, hist_len=0):
+    b = _f64(b)
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    info = Info()
+    hist = np.zeros(max(hist_len, 1))
+    Ms = M.s if M is not None else PC(A, "none").s
+    lib().or_bicgstab(C.byref(A.s), C.byref(Ms), _p(b, C.c_double), _p(x, C.c_double),
+                      rtol, maxit, _p(hist, C.c_double), hist_len, C.byref(info))
+    return x, info.as_dict(), hist[:min(hist_len, info.iters)]

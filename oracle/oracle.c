@@ -1,0 +1,740 @@
+/*
+ * Plain, slow, single-threaded FP64 CPU oracle of the preconditioned Krylov
+ * path (Liu & Chen, "Scalable linear solvers for sparse linear systems from
+ * large-scale numerical simulations").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; the two meet only through
+ * the arrays produced by the seeded input generators.
+ *
+ * Conventions: every summation runs in ascending column order, one row at a
+ * time; no blocking, reordering or fusion.  Build with -ffp-contract=off so
+ * that no multiply-add is contracted (results are then the same on x86-64
+ * and AArch64).
+ *
+ * Parity status of each function is listed where it is defined; all of them
+ * are pinned by tests/test_oracle_pins.py except the learned stage, which
+ * lives in oracle/convnet.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_NOT_CONVERGED 1
+#define OR_INVALID (-1)
+#define OR_ZERO_PIVOT (-3)
+#define OR_BREAKDOWN (-4)
+
+/* ------------------------------------------------------------------------ */
+/* Matrix: CSR (bs = 1) or BSR with bs x bs row-major blocks.                */
+/* Sec. 2.3, Fig. 15 (MAT: per-row column indices and values).               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t bs;          /* 1 => CSR; > 1 => BSR */
+    int32_t nrows;       /* block rows */
+    const int32_t *ptr;  /* nrows + 1 */
+    const int32_t *col;  /* block column of each stored block */
+    const double *val;   /* bs*bs values per stored block, row-major */
+} or_mat;
+
+/* y = A x.  Sec. 2.3, Fig. 20 (MatVecMXY): y_i = sum_j a_ij x_j. */
+void or_spmv(const or_mat *A, const double *x, double *y)
+{
+    const int32_t bs = A->bs;
+    for (int32_t I = 0; I < A->nrows; ++I) {
+        for (int32_t r = 0; r < bs; ++r) {
+            double acc = 0.0;
+            for (int32_t p = A->ptr[I]; p < A->ptr[I + 1]; ++p) {
+                const double *blk = A->val + (size_t)p * bs * bs + (size_t)r * bs;
+                for (int32_t c = 0; c < bs; ++c)
+                    acc += blk[c] * x[(size_t)A->col[p] * bs + c];
+            }
+            y[(size_t)I * bs + r] = acc;
+        }
+    }
+}
+
+/* y = a*(A x) + b*y.  Sec. 2.3, Fig. 21 (MatVecAMXPBY). */
+void or_amxpby(double a, const or_mat *A, const double *x, double b, double *y)
+{
+    const int32_t bs = A->bs;
+    for (int32_t I = 0; I < A->nrows; ++I) {
+        for (int32_t r = 0; r < bs; ++r) {
+            double acc = 0.0;
+            for (int32_t p = A->ptr[I]; p < A->ptr[I + 1]; ++p) {
+                const double *blk = A->val + (size_t)p * bs * bs + (size_t)r * bs;
+                for (int32_t c = 0; c < bs; ++c)
+                    acc += blk[c] * x[(size_t)A->col[p] * bs + c];
+            }
+            const size_t i = (size_t)I * bs + r;
+            y[i] = a * acc + b * y[i];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* BLAS-1.  Sec. 2.2, Figs. 10-13.                                            */
+/* ------------------------------------------------------------------------ */
+/* y = a x + b y (Fig. 10, VecAXPBY) */
+void or_axpby(int64_t n, double a, const double *x, double b, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) y[i] = a * x[i] + b * y[i];
+}
+
+/* z = a x + b y (Fig. 11, VecAXPBYZ) */
+void or_axpbyz(int64_t n, double a, const double *x, double b, const double *y, double *z)
+{
+    for (int64_t i = 0; i < n; ++i) z[i] = a * x[i] + b * y[i];
+}
+
+/* <x, y> (Fig. 12, VecDot; one process, so no reduction across ranks) */
+double or_dot(int64_t n, const double *x, const double *y)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+    return s;
+}
+
+double or_norm2(int64_t n, const double *x) { return sqrt(or_dot(n, x, x)); }
+
+/* x_i = v (Fig. 13, VecSetValue) */
+void or_set(int64_t n, double v, double *x)
+{
+    for (int64_t i = 0; i < n; ++i) x[i] = v;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ILU(0).  Sec. 4.1, Eq. 3 names the factorisation L U and its two          */
+/* triangular solves; ILU(0) keeps exactly the pattern of A (Saad,           */
+/* "Iterative methods for sparse linear systems", the IKJ variant).          */
+/* Result: lu holds the strictly lower part of L (unit diagonal implied)     */
+/* and the upper part of U including its diagonal, in A's pattern.           */
+/* Requires sorted columns and a stored diagonal in every row.               */
+/* ------------------------------------------------------------------------ */
+static int32_t find_diag(const int32_t *ptr, const int32_t *col, int32_t i)
+{
+    for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p)
+        if (col[p] == i) return p;
+    return -1;
+}
+
+int or_ilu0(int32_t n, const int32_t *ptr, const int32_t *col, const double *a,
+            double *lu, int32_t *bad_row)
+{
+    memcpy(lu, a, sizeof(double) * (size_t)ptr[n]);
+    *bad_row = -1;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t di = find_diag(ptr, col, i);
+        if (di < 0) { *bad_row = i; return OR_INVALID; }
+        for (int32_t p = ptr[i]; p < di; ++p) {
+            const int32_t k = col[p];
+            const int32_t dk = find_diag(ptr, col, k);
+            const double piv = lu[dk];
+            lu[p] = lu[p] / piv;
+            /* a_ij -= a_ik * a_kj for j > k in pat(i) and pat(k) */
+            int32_t q = p + 1;
+            for (int32_t r = dk + 1; r < ptr[k + 1]; ++r) {
+                const int32_t j = col[r];
+                while (q < ptr[i + 1] && col[q] < j) ++q;
+                if (q == ptr[i + 1]) break;
+                if (col[q] == j) lu[q] = lu[q] - lu[p] * lu[r];
+            }
+        }
+        if (!(lu[di] != 0.0) || !isfinite(lu[di])) { *bad_row = i; return OR_ZERO_PIVOT; }
+    }
+    return OR_OK;
+}
+
+/* z = U^{-1} L^{-1} r (Eq. 3: L y = r, then U z = y). */
+void or_ilu0_solve(int32_t n, const int32_t *ptr, const int32_t *col, const double *lu,
+                   const double *r, double *z)
+{
+    double *y = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int32_t i = 0; i < n; ++i) {
+        double acc = r[i];
+        for (int32_t p = ptr[i]; p < ptr[i + 1] && col[p] < i; ++p) acc -= lu[p] * y[col[p]];
+        y[i] = acc;
+    }
+    for (int32_t i = n - 1; i >= 0; --i) {
+        const int32_t di = find_diag(ptr, col, i);
+        double acc = y[i];
+        for (int32_t p = di + 1; p < ptr[i + 1]; ++p) acc -= lu[p] * z[col[p]];
+        z[i] = acc / lu[di];
+    }
+    free(y);
+}
+
+/* Same solve with FP32 factors and FP32 arithmetic (the mixed-precision
+ * preconditioner apply): r is rounded to FP32 on entry, z widened on exit. */
+void or_ilu0_solve_f32(int32_t n, const int32_t *ptr, const int32_t *col, const float *lu,
+                       const double *r, double *z)
+{
+    float *y = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float *w = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    for (int32_t i = 0; i < n; ++i) {
+        float acc = (float)r[i];
+        for (int32_t p = ptr[i]; p < ptr[i + 1] && col[p] < i; ++p) acc -= lu[p] * y[col[p]];
+        y[i] = acc;
+    }
+    for (int32_t i = n - 1; i >= 0; --i) {
+        const int32_t di = find_diag(ptr, col, i);
+        float acc = y[i];
+        for (int32_t p = di + 1; p < ptr[i + 1]; ++p) acc -= lu[p] * w[col[p]];
+        w[i] = acc / lu[di];
+    }
+    for (int32_t i = 0; i < n; ++i) z[i] = (double)w[i];
+    free(y);
+    free(w);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Block ILU(0) with bs x bs blocks (not in the paper, which cites block-    */
+/* wise ILU as related work in Sec. 1): ILU(0) over the block pattern, with  */
+/* L_IK = A_IK inv(U_KK) and A_IJ -= L_IK U_KJ.  dinv holds inv(U_II).        */
+/* ------------------------------------------------------------------------ */
+
+/* inverse of a bs x bs row-major block by Gauss-Jordan elimination with
+ * partial pivoting; returns 0 when a pivot is zero or non-finite. */
+static int block_inverse(int32_t bs, const double *a, double *inv)
+{
+    double m[64], e[64];
+    if (bs > 8) return 0;
+    for (int32_t i = 0; i < bs * bs; ++i) { m[i] = a[i]; e[i] = 0.0; }
+    for (int32_t i = 0; i < bs; ++i) e[i * bs + i] = 1.0;
+    for (int32_t c = 0; c < bs; ++c) {
+        int32_t piv = c;
+        for (int32_t r = c + 1; r < bs; ++r)
+            if (fabs(m[r * bs + c]) > fabs(m[piv * bs + c])) piv = r;
+        if (!(m[piv * bs + c] != 0.0) || !isfinite(m[piv * bs + c])) return 0;
+        if (piv != c) {
+            for (int32_t k = 0; k < bs; ++k) {
+                double t = m[c * bs + k]; m[c * bs + k] = m[piv * bs + k]; m[piv * bs + k] = t;
+                t = e[c * bs + k]; e[c * bs + k] = e[piv * bs + k]; e[piv * bs + k] = t;
+            }
+        }
+        const double d = m[c * bs + c];
+        for (int32_t k = 0; k < bs; ++k) { m[c * bs + k] /= d; e[c * bs + k] /= d; }
+        for (int32_t r = 0; r < bs; ++r) {
+            if (r == c) continue;
+            const double f = m[r * bs + c];
+            for (int32_t k = 0; k < bs; ++k) {
+                m[r * bs + k] -= f * m[c * bs + k];
+                e[r * bs + k] -= f * e[c * bs + k];
+            }
+        }
+    }
+    for (int32_t i = 0; i < bs * bs; ++i) inv[i] = e[i];
+    return 1;
+}
+
+/* c = a b for bs x bs row-major blocks */
+static void block_mul(int32_t bs, const double *a, const double *b, double *c)
+{
+    for (int32_t i = 0; i < bs; ++i)
+        for (int32_t j = 0; j < bs; ++j) {
+            double s = 0.0;
+            for (int32_t k = 0; k < bs; ++k) s += a[i * bs + k] * b[k * bs + j];
+            c[i * bs + j] = s;
+        }
+}
+
+int or_bilu0(int32_t nb, int32_t bs, const int32_t *ptr, const int32_t *col, const double *a,
+             double *lu, double *dinv, int32_t *bad_row)
+{
+    const size_t b2 = (size_t)bs * bs;
+    double t[64], u[64];
+    if (bs < 1 || bs > 8) return OR_INVALID;
+    memcpy(lu, a, sizeof(double) * b2 * (size_t)ptr[nb]);
+    *bad_row = -1;
+    for (int32_t I = 0; I < nb; ++I) {
+        const int32_t dI = find_diag(ptr, col, I);
+        if (dI < 0) { *bad_row = I; return OR_INVALID; }
+        for (int32_t p = ptr[I]; p < dI; ++p) {
+            const int32_t K = col[p];
+            const int32_t dK = find_diag(ptr, col, K);
+            block_mul(bs, lu + p * b2, dinv + (size_t)K * b2, t);
+            memcpy(lu + p * b2, t, sizeof(double) * b2);
+            int32_t q = p + 1;
+            for (int32_t r = dK + 1; r < ptr[K + 1]; ++r) {
+                const int32_t J = col[r];
+                while (q < ptr[I + 1] && col[q] < J) ++q;
+                if (q == ptr[I + 1]) break;
+                if (col[q] == J) {
+                    block_mul(bs, lu + p * b2, lu + r * b2, u);
+                    for (size_t e = 0; e < b2; ++e) lu[q * b2 + e] = lu[q * b2 + e] - u[e];
+                }
+            }
+        }
+        if (!block_inverse(bs, lu + dI * b2, dinv + (size_t)I * b2)) { *bad_row = I; return OR_ZERO_PIVOT; }
+    }
+    return OR_OK;
+}
+
+/* z = U^{-1} L^{-1} r over blocks: y_I = r_I - sum_{J<I} L_IJ y_J;
+ * z_I = inv(U_II) (y_I - sum_{J>I} U_IJ z_J). */
+void or_bilu0_solve(int32_t nb, int32_t bs, const int32_t *ptr, const int32_t *col,
+                    const double *lu, const double *dinv, const double *r, double *z)
+{
+    const size_t b2 = (size_t)bs * bs;
+    double *y = (double *)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1) * bs);
+    double acc[8];
+    for (int32_t I = 0; I < nb; ++I) {
+        for (int32_t k = 0; k < bs; ++k) acc[k] = r[(size_t)I * bs + k];
+        for (int32_t p = ptr[I]; p < ptr[I + 1] && col[p] < I; ++p)
+            for (int32_t k = 0; k < bs; ++k)
+                for (int32_t c = 0; c < bs; ++c)
+                    acc[k] -= lu[p * b2 + k * bs + c] * y[(size_t)col[p] * bs + c];
+        for (int32_t k = 0; k < bs; ++k) y[(size_t)I * bs + k] = acc[k];
+    }
+    for (int32_t I = nb - 1; I >= 0; --I) {
+        const int32_t dI = find_diag(ptr, col, I);
+        for (int32_t k = 0; k < bs; ++k) acc[k] = y[(size_t)I * bs + k];
+        for (int32_t p = dI + 1; p < ptr[I + 1]; ++p)
+            for (int32_t k = 0; k < bs; ++k)
+                for (int32_t c = 0; c < bs; ++c)
+                    acc[k] -= lu[p * b2 + k * bs + c] * z[(size_t)col[p] * bs + c];
+        for (int32_t k = 0; k < bs; ++k) {
+            double s = 0.0;
+            for (int32_t c = 0; c < bs; ++c) s += dinv[(size_t)I * b2 + k * bs + c] * acc[c];
+            z[(size_t)I * bs + k] = s;
+        }
+    }
+    free(y);
+}
+
+/* FP32 factors and arithmetic (mixed-precision apply). */
+void or_bilu0_solve_f32(int32_t nb, int32_t bs, const int32_t *ptr, const int32_t *col,
+                        const float *lu, const float *dinv, const double *r, double *z)
+{
+    const size_t b2 = (size_t)bs * bs;
+    float *y = (float *)malloc(sizeof(float) * (size_t)(nb > 0 ? nb : 1) * bs);
+    float *w = (float *)malloc(sizeof(float) * (size_t)(nb > 0 ? nb : 1) * bs);
+    float acc[8];
+    for (int32_t I = 0; I < nb; ++I) {
+        for (int32_t k = 0; k < bs; ++k) acc[k] = (float)r[(size_t)I * bs + k];
+        for (int32_t p = ptr[I]; p < ptr[I + 1] && col[p] < I; ++p)
+            for (int32_t k = 0; k < bs; ++k)
+                for (int32_t c = 0; c < bs; ++c)
+                    acc[k] -= lu[p * b2 + k * bs + c] * y[(size_t)col[p] * bs + c];
+        for (int32_t k = 0; k < bs; ++k) y[(size_t)I * bs + k] = acc[k];
+    }
+    for (int32_t I = nb - 1; I >= 0; --I) {
+        const int32_t dI = find_diag(ptr, col, I);
+        for (int32_t k = 0; k < bs; ++k) acc[k] = y[(size_t)I * bs + k];
+        for (int32_t p = dI + 1; p < ptr[I + 1]; ++p)
+            for (int32_t k = 0; k < bs; ++k)
+                for (int32_t c = 0; c < bs; ++c)
+                    acc[k] -= lu[p * b2 + k * bs + c] * w[(size_t)col[p] * bs + c];
+        for (int32_t k = 0; k < bs; ++k) {
+            float s = 0.0f;
+            for (int32_t c = 0; c < bs; ++c) s += dinv[(size_t)I * b2 + k * bs + c] * acc[c];
+            w[(size_t)I * bs + k] = s;
+        }
+    }
+    for (size_t i = 0; i < (size_t)nb * bs; ++i) z[i] = (double)w[i];
+    free(y);
+    free(w);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quasi-IMPES decoupling and the CPR restriction / prolongation.            */
+/* Sec. 4.3, Eqs. 5-9: Pi_r picks the pressure unknowns, Pi_p injects a      */
+/* pressure vector with zero saturations.  Quasi-IMPES (named in Example 2)  */
+/* left-scales each cell's equations: weight w_Ik = -D_I[0][k] / D_I[k][k]   */
+/* with D_I the diagonal block, so the decoupled pressure row is             */
+/* row 0 + sum_k w_Ik row k of block row I.                                  */
+/* ------------------------------------------------------------------------ */
+void or_qimpes_weights(const or_mat *A, double *w)
+{
+    const int32_t bs = A->bs;
+    const size_t b2 = (size_t)bs * bs;
+    for (int32_t I = 0; I < A->nrows; ++I) {
+        const int32_t dI = find_diag(A->ptr, A->col, I);
+        const double *D = A->val + (size_t)dI * b2;
+        for (int32_t k = 1; k < bs; ++k)
+            w[(size_t)I * (bs - 1) + (k - 1)] = -D[k] / D[k * bs + k];
+    }
+}
+
+/* App' in the block pattern of A: pressure-column entry of the decoupled
+ * pressure row, A_IJ[0][0] + sum_k w_Ik A_IJ[k][0]. */
+void or_qimpes_app(const or_mat *A, const double *w, double *app)
+{
+    const int32_t bs = A->bs;
+    const size_t b2 = (size_t)bs * bs;
+    for (int32_t I = 0; I < A->nrows; ++I)
+        for (int32_t p = A->ptr[I]; p < A->ptr[I + 1]; ++p) {
+            const double *B = A->val + (size_t)p * b2;
+            double s = B[0];
+            for (int32_t k = 1; k < bs; ++k) s += w[(size_t)I * (bs - 1) + (k - 1)] * B[k * bs];
+            app[p] = s;
+        }
+}
+
+/* rp_I = f_{I,0} + sum_k w_Ik f_{I,k}  (Pi_r after the decoupling) */
+void or_qimpes_restrict(int32_t nb, int32_t bs, const double *w, const double *f, double *rp)
+{
+    for (int32_t I = 0; I < nb; ++I) {
+        double s = f[(size_t)I * bs];
+        for (int32_t k = 1; k < bs; ++k) s += w[(size_t)I * (bs - 1) + (k - 1)] * f[(size_t)I * bs + k];
+        rp[I] = s;
+    }
+}
+
+/* Pi_p (Eq. 8): z_{I,0} = p_I, z_{I,k} = 0 */
+void or_prolong(int32_t nb, int32_t bs, const double *p, double *z)
+{
+    for (int32_t I = 0; I < nb; ++I) {
+        z[(size_t)I * bs] = p[I];
+        for (int32_t k = 1; k < bs; ++k) z[(size_t)I * bs + k] = 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioner object (Sec. 3, Fig. 29: setup / solve / destroy).         */
+/* ------------------------------------------------------------------------ */
+typedef int (*or_apply_fn)(void *user, int64_t n, const double *r, double *z);
+
+enum { OR_PC_NONE = 0, OR_PC_ILU0 = 1, OR_PC_BILU0 = 2, OR_PC_CPR = 3, OR_PC_CALLBACK = 4 };
+
+typedef struct {
+    int32_t type;
+    int32_t mixed;              /* 1: FP32 factors and FP32 applies */
+    /* scalar ILU(0): on A (type ILU0) or on App' (type CPR pressure stage) */
+    int32_t n;
+    const int32_t *ptr, *col;
+    const double *lu;
+    const float *lu32;
+    /* block ILU(0) (type BILU0, and the second stage of CPR) */
+    int32_t nb, bs;
+    const int32_t *bptr, *bcol;
+    const double *blu, *bdinv;
+    const float *blu32, *bdinv32;
+    /* CPR */
+    const or_mat *A;
+    const double *w;            /* nb x (bs-1) quasi-IMPES weights */
+    or_apply_fn pstage;         /* optional pressure-stage override */
+    void *pstage_user;
+    /* plain callback preconditioner */
+    or_apply_fn fn;
+    void *user;
+} or_pc;
+
+static int64_t pc_len(const or_pc *M, int64_t n) { (void)M; return n; }
+
+/* z = M^{-1} r */
+int or_pc_apply(const or_pc *M, int64_t n, const double *r, double *z)
+{
+    (void)pc_len;
+    switch (M ? M->type : OR_PC_NONE) {
+    case OR_PC_NONE:
+        memcpy(z, r, sizeof(double) * (size_t)n);
+        return OR_OK;
+    case OR_PC_ILU0:
+        if (M->mixed) or_ilu0_solve_f32(M->n, M->ptr, M->col, M->lu32, r, z);
+        else or_ilu0_solve(M->n, M->ptr, M->col, M->lu, r, z);
+        return OR_OK;
+    case OR_PC_BILU0:
+        if (M->mixed) or_bilu0_solve_f32(M->nb, M->bs, M->bptr, M->bcol, M->blu32, M->bdinv32, r, z);
+        else or_bilu0_solve(M->nb, M->bs, M->bptr, M->bcol, M->blu, M->bdinv, r, z);
+        return OR_OK;
+    case OR_PC_CALLBACK:
+        return M->fn(M->user, n, r, z);
+    case OR_PC_CPR: {
+        /* Two-stage CPR in the pressure-first order (Alg. 6, read as:
+         * x = Pi_p M_p^{-1} Pi_r f;  r = f - A x;  x = x + R(A)^{-1} r). */
+        const int32_t nb = M->nb, bs = M->bs;
+        double *rp = (double *)malloc(sizeof(double) * (size_t)nb);
+        double *zp = (double *)malloc(sizeof(double) * (size_t)nb);
+        double *res = (double *)malloc(sizeof(double) * (size_t)n);
+        double *z2 = (double *)malloc(sizeof(double) * (size_t)n);
+        int st = OR_OK;
+        or_qimpes_restrict(nb, bs, M->w, r, rp);
+        if (M->pstage) st = M->pstage(M->pstage_user, nb, rp, zp);
+        else if (M->mixed) or_ilu0_solve_f32(M->n, M->ptr, M->col, M->lu32, rp, zp);
+        else or_ilu0_solve(M->n, M->ptr, M->col, M->lu, rp, zp);
+        or_prolong(nb, bs, zp, z);
+        memcpy(res, r, sizeof(double) * (size_t)n);
+        or_amxpby(-1.0, M->A, z, 1.0, res);
+        if (M->mixed) or_bilu0_solve_f32(nb, bs, M->bptr, M->bcol, M->blu32, M->bdinv32, res, z2);
+        else or_bilu0_solve(nb, bs, M->bptr, M->bcol, M->blu, M->bdinv, res, z2);
+        for (int64_t i = 0; i < n; ++i) z[i] = z[i] + z2[i];
+        free(rp); free(zp); free(res); free(z2);
+        return st;
+    }
+    default:
+        return OR_INVALID;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Krylov solvers.                                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t iters;             /* inner iterations (Arnoldi steps / BiCGSTAB loops) */
+    int32_t restarts;          /* completed GMRES cycles */
+    int32_t status;
+    int32_t pad;
+    double true_rel_res;       /* ||b - A x|| / ||b|| at exit, recomputed */
+    double implicit_rel_res;   /* the solver's own residual estimate at exit */
+} or_info;
+
+static int64_t mat_n(const or_mat *A) { return (int64_t)A->nrows * A->bs; }
+
+/* One Arnoldi step with classical Gram-Schmidt and one full
+ * reorthogonalisation pass (CGS2): orthogonalises w against the i+1 columns
+ * of V (ld = n) and returns h[0..i] plus h[i+1] = ||w||.  With mgs = 1 it runs
+ * modified Gram-Schmidt instead (Alg. 1, inner loop over k). */
+void or_orthogonalise(int64_t n, int32_t i, const double *V, double *w, double *h, int32_t mgs)
+{
+    if (mgs) {
+        for (int32_t k = 0; k <= i; ++k) {
+            const double *v = V + (size_t)k * n;
+            h[k] = or_dot(n, w, v);
+            for (int64_t r = 0; r < n; ++r) w[r] = w[r] - h[k] * v[r];
+        }
+    } else {
+        double t[512];
+        for (int32_t k = 0; k <= i; ++k) h[k] = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int32_t k = 0; k <= i; ++k) t[k] = or_dot(n, V + (size_t)k * n, w);
+            for (int64_t r = 0; r < n; ++r) {
+                double s = 0.0;
+                for (int32_t k = 0; k <= i; ++k) s += V[(size_t)k * n + r] * t[k];
+                w[r] = w[r] - s;
+            }
+            for (int32_t k = 0; k <= i; ++k) h[k] += t[k];
+        }
+    }
+    h[i + 1] = or_norm2(n, w);
+}
+
+/* Restarted GMRES(m) (Sec. 3, Alg. 1) and flexible GMRES.
+ *  side = 0: right preconditioning, A M^{-1} u = b, x = M^{-1} u; the
+ *            implicit residual is the true residual norm of the iterate.
+ *  side = 1: left preconditioning exactly as Alg. 1 (M r = b - A x0,
+ *            M w = A v); stopping test on the preconditioned residual.
+ *  flexible = 1 (right side only): keeps z_i = M^{-1} v_i and forms
+ *            x += Z y (Saad's FGMRES), so M may change between steps.
+ * Orthogonalisation: CGS2 (mgs = 0) or MGS as printed in Alg. 1 (mgs = 1).
+ * Givens rotations reduce the Hessenberg matrix; the least-squares problem
+ * min ||s - H y|| of Alg. 1 is then a triangular back-substitution.
+ * Convergence: ||b - A x|| <= rtol ||b|| checked with the true residual at
+ * the end of every cycle; inside a cycle the rotated residual |g_{i+1}|
+ * ends the cycle early.  maxit counts inner iterations. */
+int or_gmres(const or_mat *A, const or_pc *M, const double *b, double *x,
+             int32_t m, double rtol, int32_t maxit, int32_t side, int32_t flexible,
+             int32_t mgs, double *hist, int32_t hist_len, or_info *info)
+{
+    const int64_t n = mat_n(A);
+    memset(info, 0, sizeof(*info));
+    if (m < 1 || m > 500 || n < 1) { info->status = OR_INVALID; return OR_INVALID; }
+    double *V = (double *)malloc(sizeof(double) * (size_t)n * (m + 1));
+    double *Z = flexible ? (double *)malloc(sizeof(double) * (size_t)n * m) : NULL;
+    double *H = (double *)calloc((size_t)(m + 1) * m, sizeof(double)); /* column-major, ld m+1 */
+    double *cs = (double *)malloc(sizeof(double) * m);
+    double *sn = (double *)malloc(sizeof(double) * m);
+    double *g = (double *)malloc(sizeof(double) * (m + 1));
+    double *y = (double *)malloc(sizeof(double) * (m + 1));
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *t = (double *)malloc(sizeof(double) * (size_t)n);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+
+    const double bnorm = or_norm2(n, b);
+    int status = OR_NOT_CONVERGED;
+    int32_t iters = 0, cycles = 0;
+    double implicit = 0.0;
+    if (bnorm == 0.0) {
+        or_set(n, 0.0, x);
+        status = OR_OK;
+        goto done;
+    }
+    double tol;
+    /* reference norm for the stopping test */
+    if (side == 1) {
+        or_pc_apply(M, n, b, t);
+        tol = rtol * or_norm2(n, t);
+    } else {
+        tol = rtol * bnorm;
+    }
+    for (;;) {
+        /* r = b - A x (Fig. 21 with a = -1, b = 1) */
+        memcpy(r, b, sizeof(double) * (size_t)n);
+        or_amxpby(-1.0, A, x, 1.0, r);
+        if (side == 1) { or_pc_apply(M, n, r, t); memcpy(r, t, sizeof(double) * (size_t)n); }
+        const double beta = or_norm2(n, r);
+        implicit = beta;
+        if (beta <= tol) { status = OR_OK; break; }
+        if (iters >= maxit) break;
+        for (int64_t k = 0; k < n; ++k) V[k] = r[k] / beta;
+        g[0] = beta;
+        for (int32_t k = 1; k <= m; ++k) g[k] = 0.0;
+        int32_t kdim = 0;
+        for (int32_t i = 0; i < m; ++i) {
+            double *vi = V + (size_t)i * n;
+            double *zi = flexible ? Z + (size_t)i * n : t;
+            if (side == 1) {
+                or_spmv(A, vi, t);
+                or_pc_apply(M, n, t, w);
+            } else {
+                or_pc_apply(M, n, vi, zi);
+                or_spmv(A, zi, w);
+            }
+            const double w0 = or_norm2(n, w);
+            double *h = H + (size_t)i * (m + 1);
+            or_orthogonalise(n, i, V, w, h, mgs);
+            /* apply the previous rotations to column i */
+            for (int32_t k = 0; k < i; ++k) {
+                const double a = h[k], c = h[k + 1];
+                h[k] = cs[k] * a + sn[k] * c;
+                h[k + 1] = -sn[k] * a + cs[k] * c;
+            }
+            const double hnext = h[i + 1];
+            const double rho = hypot(h[i], hnext);
+            cs[i] = h[i] / rho;
+            sn[i] = hnext / rho;
+            h[i] = rho;
+            h[i + 1] = 0.0;
+            g[i + 1] = -sn[i] * g[i];
+            g[i] = cs[i] * g[i];
+            ++iters;
+            kdim = i + 1;
+            implicit = fabs(g[i + 1]);
+            if (hist && iters - 1 < hist_len) hist[iters - 1] = implicit / (side == 1 ? tol / rtol : bnorm);
+            const int happy = hnext <= 1e-14 * w0;
+            if (implicit <= tol || iters >= maxit || happy || i == m - 1) break;
+            double *vn = V + (size_t)(i + 1) * n;
+            for (int64_t k = 0; k < n; ++k) vn[k] = w[k] / hnext;
+        }
+        /* back-substitution H(0:k,0:k) y = g(0:k) */
+        for (int32_t k = kdim - 1; k >= 0; --k) {
+            double s = g[k];
+            for (int32_t j = k + 1; j < kdim; ++j) s -= H[(size_t)j * (m + 1) + k] * y[j];
+            y[k] = s / H[(size_t)k * (m + 1) + k];
+        }
+        if (flexible) {
+            for (int64_t r2 = 0; r2 < n; ++r2) {
+                double s = 0.0;
+                for (int32_t j = 0; j < kdim; ++j) s += Z[(size_t)j * n + r2] * y[j];
+                x[r2] = x[r2] + s;
+            }
+        } else {
+            for (int64_t r2 = 0; r2 < n; ++r2) {
+                double s = 0.0;
+                for (int32_t j = 0; j < kdim; ++j) s += V[(size_t)j * n + r2] * y[j];
+                w[r2] = s;
+            }
+            if (side == 1) {
+                for (int64_t r2 = 0; r2 < n; ++r2) x[r2] = x[r2] + w[r2];
+            } else {
+                or_pc_apply(M, n, w, t);
+                for (int64_t r2 = 0; r2 < n; ++r2) x[r2] = x[r2] + t[r2];
+            }
+        }
+        ++cycles;
+    }
+done:
+    memcpy(r, b, sizeof(double) * (size_t)n);
+    or_amxpby(-1.0, A, x, 1.0, r);
+    info->true_rel_res = bnorm > 0.0 ? or_norm2(n, r) / bnorm : 0.0;
+    info->implicit_rel_res = bnorm > 0.0 ? implicit / (side == 1 ? tol / rtol : bnorm) : 0.0;
+    if (side == 0 && status == OR_OK && info->true_rel_res > rtol) status = OR_NOT_CONVERGED;
+    info->iters = iters;
+    info->restarts = cycles;
+    info->status = status;
+    free(V); free(Z); free(H); free(cs); free(sn); free(g); free(y); free(r); free(t); free(w);
+    return status;
+}
+
+/* Right-preconditioned BiCGSTAB (named in Sec. 3 and used in Examples 2, 4
+ * and 5; the paper does not print it, so this is van der Vorst's 1992
+ * algorithm as given in Saad's book, with z = M^{-1} applied to p and s).
+ * All scalars FP64.  One iteration = one full loop; a half-step exit on
+ * ||s|| counts as one iteration.  On an implicit convergence the true
+ * residual is recomputed; if it has drifted above the tolerance the method
+ * restarts from the true residual. */
+int or_bicgstab(const or_mat *A, const or_pc *M, const double *b, double *x,
+                double rtol, int32_t maxit, double *hist, int32_t hist_len, or_info *info)
+{
+    const int64_t n = mat_n(A);
+    memset(info, 0, sizeof(*info));
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *rh = (double *)malloc(sizeof(double) * (size_t)n);
+    double *p = (double *)malloc(sizeof(double) * (size_t)n);
+    double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    double *s = (double *)malloc(sizeof(double) * (size_t)n);
+    double *t = (double *)malloc(sizeof(double) * (size_t)n);
+    double *ph = (double *)malloc(sizeof(double) * (size_t)n);
+    double *sh = (double *)malloc(sizeof(double) * (size_t)n);
+    const double bnorm = or_norm2(n, b);
+    int status = OR_NOT_CONVERGED;
+    int32_t it = 0;
+    double implicit = 0.0;
+    if (bnorm == 0.0) { or_set(n, 0.0, x); status = OR_OK; goto done; }
+    const double tol = rtol * bnorm;
+    int fresh = 1;
+    double rho0 = 1.0, alpha = 1.0, omega = 1.0;
+    while (it < maxit) {
+        if (fresh) {
+            memcpy(r, b, sizeof(double) * (size_t)n);
+            or_amxpby(-1.0, A, x, 1.0, r);
+            implicit = or_norm2(n, r);
+            if (implicit <= tol) { status = OR_OK; break; }
+            memcpy(rh, r, sizeof(double) * (size_t)n);
+            or_set(n, 0.0, p);
+            or_set(n, 0.0, v);
+            rho0 = alpha = omega = 1.0;
+            fresh = 0;
+        }
+        const double rho = or_dot(n, rh, r);
+        if (!(fabs(rho) > 0.0) || !isfinite(rho)) { status = OR_BREAKDOWN; break; }
+        const double beta = (rho / rho0) * (alpha / omega);
+        /* p = r + beta (p - omega v) */
+        for (int64_t k = 0; k < n; ++k) p[k] = r[k] + beta * (p[k] - omega * v[k]);
+        or_pc_apply(M, n, p, ph);
+        or_spmv(A, ph, v);
+        const double rv = or_dot(n, rh, v);
+        if (!(fabs(rv) > 0.0) || !isfinite(rv)) { status = OR_BREAKDOWN; break; }
+        alpha = rho / rv;
+        for (int64_t k = 0; k < n; ++k) s[k] = r[k] - alpha * v[k];
+        ++it;
+        const double snorm = or_norm2(n, s);
+        if (snorm <= tol) {
+            for (int64_t k = 0; k < n; ++k) x[k] = x[k] + alpha * ph[k];
+            implicit = snorm;
+            if (hist && it - 1 < hist_len) hist[it - 1] = snorm / bnorm;
+            fresh = 1;            /* confirm with the true residual */
+            continue;
+        }
+        or_pc_apply(M, n, s, sh);
+        or_spmv(A, sh, t);
+        const double tt = or_dot(n, t, t);
+        const double ts = or_dot(n, t, s);
+        omega = tt > 0.0 ? ts / tt : 0.0;
+        for (int64_t k = 0; k < n; ++k) x[k] = x[k] + alpha * ph[k] + omega * sh[k];
+        for (int64_t k = 0; k < n; ++k) r[k] = s[k] - omega * t[k];
+        rho0 = rho;
+        implicit = or_norm2(n, r);
+        if (hist && it - 1 < hist_len) hist[it - 1] = implicit / bnorm;
+        if (implicit <= tol) { fresh = 1; continue; }
+        if (!(omega != 0.0) || !isfinite(omega)) { status = OR_BREAKDOWN; break; }
+    }
+    if (status == OR_NOT_CONVERGED && fresh && it >= maxit) {
+        /* the last loop ended on an implicit convergence: confirm it */
+        memcpy(r, b, sizeof(double) * (size_t)n);
+        or_amxpby(-1.0, A, x, 1.0, r);
+        if (or_norm2(n, r) <= tol) status = OR_OK;
+    }
+done:
+    memcpy(r, b, sizeof(double) * (size_t)n);
+    or_amxpby(-1.0, A, x, 1.0, r);
+    info->true_rel_res = bnorm > 0.0 ? or_norm2(n, r) / bnorm : 0.0;
+    info->implicit_rel_res = bnorm > 0.0 ? implicit / bnorm : 0.0;
+    info->iters = it;
+    info->status = status;
+    free(r); free(rh); free(p); free(v); free(s); free(t); free(ph); free(sh);
+    return status;
+}

@@ -1,0 +1,573 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each test checks one oracle function against a closed form, brute force on a
+tiny input, a textbook special case or an algebraic invariant, chosen so that
+a dropped term, a wrong sign, a wrong index or a transposed operand fails.
+CPU only.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------
+# helpers building small test matrices (inputs only)
+# ----------------------------------------------------------------------------
+def csr_dict(A):
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    return dict(n=A.shape[0], rowptr=A.indptr.astype(np.int32), col=A.indices.astype(np.int32),
+                val=A.data.astype(np.float64))
+
+
+def dense_pattern_csr(D):
+    """Every entry of a dense matrix stored explicitly (a full pattern)."""
+    n = D.shape[0]
+    return dict(n=n, rowptr=(np.arange(n + 1) * n).astype(np.int32),
+                col=np.tile(np.arange(n), n).astype(np.int32), val=D.reshape(-1).copy())
+
+
+def poisson1d(n):
+    return sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1], format="csr")
+
+
+def poisson3d_dirichlet(nx, ny, nz):
+    Ix, Iy, Iz = sp.eye(nx), sp.eye(ny), sp.eye(nz)
+    return (sp.kron(Iz, sp.kron(Iy, poisson1d(nx))) + sp.kron(Iz, sp.kron(poisson1d(ny), Ix))
+            + sp.kron(poisson1d(nz), sp.kron(Iy, Ix))).tocsr()
+
+
+def eig1d(n, k):
+    j = np.arange(1, n + 1)
+    return np.sin(k * np.pi * j / (n + 1)), 2.0 - 2.0 * np.cos(k * np.pi / (n + 1))
+
+
+def lu_dense_from_ilu(d, lu):
+    """Dense L (unit lower) and U from factors stored in d's pattern."""
+    n = d["n"]
+    L, U = np.eye(n), np.zeros((n, n))
+    for i in range(n):
+        for p in range(d["rowptr"][i], d["rowptr"][i + 1]):
+            j = d["col"][p]
+            if j < i:
+                L[i, j] = lu[p]
+            else:
+                U[i, j] = lu[p]
+    return L, U
+
+
+# ----------------------------------------------------------------------------
+# generator (inputs)
+# ----------------------------------------------------------------------------
+def test_generator_pressure_matrix_properties():
+    g = synth.Grid(6, 5, 4)
+    m = synth.pressure_7pt(g, 7, kz_scale=0.1)
+    A = sp.csr_matrix((m["val"], m["col"], m["rowptr"]), shape=(g.n, g.n)).toarray()
+    assert np.allclose(A, A.T, rtol=0, atol=0)
+    assert np.allclose(A.sum(axis=1), 1e-3, rtol=0, atol=1e-12)
+    off = A - np.diag(np.diag(A))
+    assert (off <= 0).all() and (np.diag(A) > 0).all()
+    nnz = 7 * g.n - 2 * (g.nx * g.ny + g.ny * g.nz + g.nx * g.nz)
+    assert m["col"].size == nnz
+    for i in range(g.n):
+        c = m["col"][m["rowptr"][i]:m["rowptr"][i + 1]]
+        assert (np.diff(c) > 0).all() and i in c
+    m2 = synth.pressure_7pt(g, 7, kz_scale=0.1)
+    m3 = synth.pressure_7pt(g, 8, kz_scale=0.1)
+    assert np.array_equal(m["val"], m2["val"]) and not np.array_equal(m["val"], m3["val"])
+
+
+def test_generator_bsr_properties():
+    g = synth.Grid(4, 3, 3)
+    m = synth.black_oil_bsr3(g, 3)
+    c = synth.csr_from_bsr(m)
+    A = sp.csr_matrix((c["val"], c["col"], c["rowptr"]), shape=(c["n"], c["n"])).toarray()
+    p = synth.pressure_7pt(g, 3)
+    App = sp.csr_matrix((p["val"], p["col"], p["rowptr"]), shape=(g.n, g.n)).toarray()
+    assert np.array_equal(A[0::3, 0::3], App)
+    for s in (1, 2):
+        rows = A[s::3]
+        d = np.abs(rows[np.arange(g.n), np.arange(g.n) * 3 + s])
+        others = np.abs(rows).sum(axis=1) - d
+        assert (d > others).all()                       # diagonally dominant saturation rows
+        assert np.allclose(A[s::3, 0::3].sum(axis=1), 0, atol=1e-12)  # zero-sum pressure part
+
+
+# ----------------------------------------------------------------------------
+# SpMV and BLAS-1 (Sec. 2.2-2.3, Figs. 10-13, 20-21)
+# ----------------------------------------------------------------------------
+def test_spmv_integer_exact(orc):
+    rng = np.random.default_rng(0)
+    n = 57
+    D = rng.integers(-5, 6, size=(n, n)).astype(float)
+    D[rng.random((n, n)) < 0.8] = 0.0
+    D[3, :] = 0.0                                       # an empty row
+    d = csr_dict(D)
+    x = rng.integers(-9, 10, size=n).astype(float)
+    A = orc.Mat.csr(d)
+    assert np.array_equal(orc.spmv(A, x), D @ x)
+    y = rng.integers(-9, 10, size=n).astype(float)
+    assert np.array_equal(orc.amxpby(2.0, A, x, -3.0, y), 2.0 * (D @ x) - 3.0 * y)
+
+
+def test_bsr_spmv_integer_exact(orc):
+    rng = np.random.default_rng(1)
+    nb, bs = 11, 3
+    mask = rng.random((nb, nb)) < 0.35
+    np.fill_diagonal(mask, True)
+    ptr = np.concatenate([[0], np.cumsum(mask.sum(axis=1))]).astype(np.int32)
+    col = np.nonzero(mask)[1].astype(np.int32)
+    blocks = rng.integers(-4, 5, size=(col.size, bs, bs)).astype(float)
+    D = np.zeros((nb * bs, nb * bs))
+    k = 0
+    for I in range(nb):
+        for J in np.nonzero(mask[I])[0]:
+            D[I * bs:(I + 1) * bs, J * bs:(J + 1) * bs] = blocks[k]
+            k += 1
+    A = orc.Mat(ptr, col, blocks.reshape(-1), bs)
+    x = rng.integers(-9, 10, size=nb * bs).astype(float)
+    assert np.array_equal(orc.spmv(A, x), D @ x)
+    y = np.arange(nb * bs, dtype=float)
+    assert np.array_equal(orc.amxpby(-1.0, A, x, 1.0, y), y - D @ x)
+
+
+def test_blas1_closed_forms(orc):
+    n = 1000
+    x = np.arange(1, n + 1, dtype=float)
+    assert orc.dot(x, x) == n * (n + 1) * (2 * n + 1) / 6
+    assert orc.norm2(np.ones(n)) == np.sqrt(n)
+    y = x[::-1].copy()                                   # n+1-i
+    assert np.array_equal(orc.axpby(2.0, x, 3.0, y), 2 * x + 3 * (n + 1 - x))
+    assert np.array_equal(orc.axpbyz(-1.0, x, 1.0, y, ), (n + 1) - 2 * x)
+    assert np.array_equal(orc.set_value(5, 2.5), np.full(5, 2.5))
+    assert orc.dot(x, -x) == -orc.dot(x, x)
+
+
+# ----------------------------------------------------------------------------
+# ILU(0) and triangular solves (Sec. 4.1, Eq. 3)
+# ----------------------------------------------------------------------------
+def test_ilu0_tridiagonal_is_exact_lu(orc):
+    rng = np.random.default_rng(2)
+    n = 40
+    D = np.diag(3 + rng.random(n)) + np.diag(-rng.random(n - 1), 1) + np.diag(-rng.random(n - 1), -1)
+    d = csr_dict(D)
+    st, bad, lu = orc.ilu0(orc.Mat.csr(d))
+    assert st == 0
+    L, U = lu_dense_from_ilu(d, lu)
+    P, Lr, Ur = sla.lu(D)
+    assert np.array_equal(P, np.eye(n))                 # no pivoting needed: plain LU
+    assert np.allclose(L, Lr, rtol=0, atol=1e-14) and np.allclose(U, Ur, rtol=1e-14, atol=1e-14)
+
+
+def test_ilu0_dense_pattern_is_lu(orc):
+    rng = np.random.default_rng(3)
+    n = 12
+    D = rng.standard_normal((n, n)) + n * np.eye(n)
+    d = dense_pattern_csr(D)
+    st, _, lu = orc.ilu0(orc.Mat.csr(d))
+    assert st == 0
+    L, U = lu_dense_from_ilu(d, lu)
+    P, Lr, Ur = sla.lu(D)
+    if np.array_equal(P, np.eye(n)):
+        assert np.allclose(L, Lr, atol=1e-13) and np.allclose(U, Ur, atol=1e-12)
+    assert np.allclose(L @ U, D, atol=1e-12)
+
+
+def test_ilu0_pattern_invariant_7pt(orc):
+    g = synth.Grid(5, 4, 3)
+    d = synth.pressure_7pt(g, 11)
+    st, _, lu = orc.ilu0(orc.Mat.csr(d))
+    assert st == 0
+    L, U = lu_dense_from_ilu(d, lu)
+    A = sp.csr_matrix((d["val"], d["col"], d["rowptr"]), shape=(g.n, g.n)).toarray()
+    P = A != 0
+    LU = L @ U
+    assert np.allclose(LU[P], A[P], rtol=1e-13, atol=1e-13)     # (LU)_ij = a_ij on pat(A)
+    assert np.abs(LU[~P]).max() > 1e-6                           # fill was dropped (not exact LU)
+    assert (np.tril(L, -1)[~P] == 0).all() and (U[~P] == 0).all()
+
+
+def test_ilu0_zero_pivot_reported(orc):
+    D = np.array([[1.0, 2.0, 0.0], [0.5, 1.0, 1.0], [0.0, 1.0, 3.0]])   # u_11 = 1 - 0.5*2 = 0
+    st, bad, _ = orc.ilu0(orc.Mat.csr(csr_dict(D)))
+    assert st == orc.ZERO_PIVOT and bad == 1
+
+
+def test_ilu0_solve_tridiagonal_is_thomas(orc):
+    rng = np.random.default_rng(4)
+    n = 64
+    lo, dg, up = -rng.random(n - 1), 3 + rng.random(n), -rng.random(n - 1)
+    D = np.diag(dg) + np.diag(up, 1) + np.diag(lo, -1)
+    d = csr_dict(D)
+    A = orc.Mat.csr(d)
+    _, _, lu = orc.ilu0(A)
+    r = rng.standard_normal(n)
+    ab = np.zeros((3, n))
+    ab[0, 1:], ab[1], ab[2, :-1] = up, dg, lo
+    z_ref = sla.solve_banded((1, 1), ab, r)
+    assert np.allclose(orc.ilu0_solve(A, lu, r), z_ref, rtol=1e-13, atol=1e-13)
+
+
+def test_ilu0_solve_inverts_lu(orc):
+    g = synth.Grid(6, 5, 4)
+    d = synth.pressure_7pt(g, 5, kz_scale=0.1)
+    A = orc.Mat.csr(d)
+    _, _, lu = orc.ilu0(A)
+    L, U = lu_dense_from_ilu(d, lu)
+    r = np.random.default_rng(5).standard_normal(g.n)
+    z = orc.ilu0_solve(A, lu, r)
+    assert np.linalg.norm(L @ (U @ z) - r) <= 1e-13 * np.linalg.norm(r)
+    z32 = orc.ilu0_solve(A, lu, r, fp32=True)
+    assert np.linalg.norm(z32 - z) <= 1e-5 * np.linalg.norm(z)
+    assert np.linalg.norm(z32 - z) > 0
+
+
+# ----------------------------------------------------------------------------
+# Block ILU(0)
+# ----------------------------------------------------------------------------
+def _block_dense(m):
+    c = synth.csr_from_bsr(m)
+    return sp.csr_matrix((c["val"], c["col"], c["rowptr"]), shape=(c["n"], c["n"])).toarray()
+
+
+def _block_lu_dense(m, lu, dinv):
+    nb, bs = m["nb"], m["bs"]
+    L, U = np.eye(nb * bs), np.zeros((nb * bs, nb * bs))
+    blk = lu.reshape(-1, bs, bs)
+    for I in range(nb):
+        for p in range(m["browptr"][I], m["browptr"][I + 1]):
+            J = m["bcol"][p]
+            tgt = L if J < I else U
+            tgt[I * bs:(I + 1) * bs, J * bs:(J + 1) * bs] = blk[p]
+    return L, U
+
+
+def test_bilu0_bs1_equals_ilu0(orc):
+    d = synth.pressure_7pt(synth.Grid(5, 4, 3), 12)
+    A = orc.Mat.csr(d)
+    _, _, lu = orc.ilu0(A)
+    st, _, blu, dinv = orc.bilu0(A)
+    assert st == 0
+    assert np.allclose(blu, lu, rtol=1e-14, atol=1e-15)
+    diag = lu[[np.nonzero(d["col"][d["rowptr"][i]:d["rowptr"][i + 1]] == i)[0][0] + d["rowptr"][i]
+               for i in range(d["n"])]]
+    assert np.allclose(dinv, 1.0 / diag, rtol=1e-15)
+
+
+def test_bilu0_block_tridiagonal_is_exact_block_lu(orc):
+    m = synth.black_oil_bsr3(synth.Grid(9, 1, 1), 4)     # a 1-D chain: block tridiagonal
+    A = orc.Mat.bsr(m)
+    st, _, lu, dinv = orc.bilu0(A)
+    assert st == 0
+    L, U = _block_lu_dense(m, lu, dinv)
+    D = _block_dense(m)
+    assert np.allclose(L @ U, D, rtol=1e-13, atol=1e-13)
+    for I in range(m["nb"]):
+        UII = U[3 * I:3 * I + 3, 3 * I:3 * I + 3]
+        assert np.allclose(dinv.reshape(-1, 3, 3)[I] @ UII, np.eye(3), atol=1e-13)
+
+
+def test_bilu0_decoupled_equals_scalar_ilu0(orc):
+    """Diagonal blocks only (no coupling between components): block ILU(0)
+    splits into three independent scalar ILU(0) factorisations."""
+    g = synth.Grid(4, 4, 3)
+    ds = [synth.pressure_7pt(g, 20 + s) for s in range(3)]
+    ptr, col = ds[0]["rowptr"], ds[0]["col"]
+    blocks = np.zeros((col.size, 3, 3))
+    for s in range(3):
+        blocks[:, s, s] = ds[s]["val"]
+    A = orc.Mat(ptr, col, blocks.reshape(-1), 3)
+    st, _, lu, dinv = orc.bilu0(A)
+    assert st == 0
+    lu = lu.reshape(-1, 3, 3)
+    for s in range(3):
+        _, _, lus = orc.ilu0(orc.Mat.csr(ds[s]))
+        assert np.allclose(lu[:, s, s], lus, rtol=1e-14, atol=1e-15)
+    off = lu.copy()
+    for s in range(3):
+        off[:, s, s] = 0
+    assert (off == 0).all()
+
+
+def test_bilu0_solve_inverts_block_lu(orc):
+    m = synth.black_oil_bsr3(synth.Grid(4, 3, 3), 6)
+    A = orc.Mat.bsr(m)
+    st, _, lu, dinv = orc.bilu0(A)
+    assert st == 0
+    L, U = _block_lu_dense(m, lu, dinv)
+    r = np.random.default_rng(6).standard_normal(A.n)
+    z = orc.bilu0_solve(A, lu, dinv, r)
+    assert np.linalg.norm(L @ (U @ z) - r) <= 1e-12 * np.linalg.norm(r)
+    z32 = orc.bilu0_solve(A, lu, dinv, r, fp32=True)
+    assert np.linalg.norm(z32 - z) <= 1e-5 * np.linalg.norm(z)
+
+
+# ----------------------------------------------------------------------------
+# Quasi-IMPES CPR (Sec. 4.3, Eqs. 5-9, Alg. 6)
+# ----------------------------------------------------------------------------
+def _read_golden_qimpes():
+    rows = {}
+    W = []
+    for line in open(os.path.join(GOLDEN, "qimpes_two_cell.txt")):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        if line[0] == "W":
+            W.append([float(v) for v in line[2:]])
+        else:
+            rows[line[0]] = np.array([float(v) for v in line[1:]])
+    return rows, np.array(W)
+
+
+def test_qimpes_two_cell_golden(orc):
+    g, W = _read_golden_qimpes()
+    ptr = np.array([0, 2, 4], np.int32)
+    col = np.array([0, 1, 0, 1], np.int32)
+    val = np.concatenate([g["A00"], g["A01"], g["A10"], g["A11"]])
+    A = orc.Mat(ptr, col, val, 3)
+    w = orc.qimpes_weights(A)
+    assert np.allclose(w.reshape(2, 2), W, rtol=0, atol=1e-15)
+    assert np.allclose(orc.qimpes_app(A, w), g["APP"], rtol=0, atol=1e-14)
+    assert np.allclose(orc.qimpes_restrict(2, 3, w, g["F"]), g["RP"], rtol=0, atol=1e-14)
+
+
+def test_restrict_prolong_identity_and_scaling_invariance(orc):
+    m = synth.black_oil_bsr3(synth.Grid(4, 3, 2), 9)
+    A = orc.Mat.bsr(m)
+    w = orc.qimpes_weights(A)
+    p = np.random.default_rng(7).standard_normal(m["nb"])
+    assert np.array_equal(orc.qimpes_restrict(m["nb"], 3, w, orc.prolong(m["nb"], 3, p)), p)
+    # scaling the saturation equations of each cell leaves App' and Pi_r f unchanged
+    s = 0.5 + np.random.default_rng(8).random((m["nb"], 2))
+    bv = m["bval"].reshape(-1, 3, 3).copy()
+    row_of = np.repeat(np.arange(m["nb"]), np.diff(m["browptr"]))
+    bv[:, 1, :] *= s[row_of, 0:1]
+    bv[:, 2, :] *= s[row_of, 1:2]
+    A2 = orc.Mat(m["browptr"], m["bcol"], bv.reshape(-1), 3)
+    w2 = orc.qimpes_weights(A2)
+    assert np.allclose(orc.qimpes_app(A2, w2), orc.qimpes_app(A, w), rtol=1e-14, atol=1e-14)
+    f = np.random.default_rng(9).standard_normal(A.n)
+    f2 = f.reshape(-1, 3).copy()
+    f2[:, 1:] *= s
+    assert np.allclose(orc.qimpes_restrict(m["nb"], 3, w2, f2.reshape(-1)),
+                       orc.qimpes_restrict(m["nb"], 3, w, f), rtol=1e-13, atol=1e-13)
+
+
+def test_cpr_exact_pressure_stage_without_coupling(orc):
+    """No pressure-saturation coupling and an exact pressure solve: the CPR
+    apply returns the exact pressure solution (the second stage sees a zero
+    pressure residual)."""
+    g = synth.Grid(4, 3, 3)
+    m = synth.black_oil_bsr3(g, 10)
+    bv = m["bval"].reshape(-1, 3, 3).copy()
+    bv[:, 0, 1:] = 0.0
+    bv[:, 1:, 0] = 0.0
+    A = orc.Mat(m["browptr"], m["bcol"], bv.reshape(-1), 3)
+    p = synth.pressure_7pt(g, 10)
+    App = sp.csr_matrix((p["val"], p["col"], p["rowptr"]), shape=(g.n, g.n)).tocsc()
+    lu = spla.splu(App)
+    M = orc.PC(A, "cpr", pstage=lambda rp: lu.solve(rp))
+    f = np.random.default_rng(11).standard_normal(A.n)
+    z = M.apply(f)
+    assert np.allclose(z[0::3], lu.solve(f[0::3]), rtol=1e-12, atol=1e-12)
+    # with the pressure stage dropped, CPR is block ILU(0) alone
+    M0 = orc.PC(A, "cpr", pstage=lambda rp: np.zeros_like(rp))
+    Mb = orc.PC(A, "bilu0")
+    assert np.allclose(M0.apply(f), Mb.apply(f), rtol=1e-14, atol=1e-14)
+
+
+def test_cpr_scalar_exact_stage_is_exact(orc):
+    d = synth.pressure_7pt(synth.Grid(5, 4, 3), 13)
+    A = orc.Mat.csr(d)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"])).tocsc()
+    lu = spla.splu(S)
+    M = orc.PC(A, "cpr", pstage=lambda r: lu.solve(r))
+    f = np.random.default_rng(12).standard_normal(A.n)
+    assert np.allclose(M.apply(f), lu.solve(f), rtol=1e-10, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# GMRES / FGMRES (Sec. 3, Alg. 1)
+# ----------------------------------------------------------------------------
+def test_gmres_full_space_converges_within_n(orc):
+    rng = np.random.default_rng(13)
+    n = 40
+    D = rng.standard_normal((n, n)) + 4 * np.eye(n)
+    A = orc.Mat.csr(dense_pattern_csr(D))
+    b = rng.standard_normal(n)
+    x, info, _ = orc.gmres(A, None, b, restart=n, rtol=1e-12, maxit=n)
+    assert info["status"] == 0 and info["iters"] <= n
+    assert np.allclose(x, np.linalg.solve(D, b), rtol=1e-9, atol=1e-10)
+
+
+def test_gmres_poisson1d_eigenvector_one_step(orc):
+    n = 50
+    A = orc.Mat.csr(csr_dict(poisson1d(n)))
+    v, lam = eig1d(n, 3)
+    x, info, _ = orc.gmres(A, None, v, restart=30, rtol=1e-12)
+    assert info["iters"] == 1 and info["status"] == 0
+    assert np.allclose(x, v / lam, rtol=1e-12, atol=1e-12)
+
+
+def test_gmres_q_eigenvectors_q_steps(orc):
+    n = 50
+    A = orc.Mat.csr(csr_dict(poisson1d(n)))
+    b = sum(eig1d(n, k)[0] * c for k, c in zip((1, 4, 9, 20), (1.0, -2.0, 0.5, 3.0)))
+    x, info, hist = orc.gmres(A, None, b, restart=30, rtol=1e-8, hist_len=4)
+    assert info["iters"] == 4 and hist[2] > 0.1      # far from converged one step earlier
+    xr = sum(eig1d(n, k)[0] * c / eig1d(n, k)[1] for k, c in zip((1, 4, 9, 20), (1.0, -2.0, 0.5, 3.0)))
+    assert np.allclose(x, xr, rtol=1e-6, atol=1e-6 * np.abs(xr).max())
+
+
+def test_gmres_poisson3d_dirichlet_eigenvector(orc):
+    nx, ny, nz = 6, 5, 4
+    A = orc.Mat.csr(csr_dict(poisson3d_dirichlet(nx, ny, nz)))
+    vx, lx = eig1d(nx, 2)
+    vy, ly = eig1d(ny, 1)
+    vz, lz = eig1d(nz, 3)
+    v = np.einsum("k,j,i->kji", vz, vy, vx).reshape(-1)
+    for solver in ("gmres", "bicgstab"):
+        if solver == "gmres":
+            x, info, _ = orc.gmres(A, None, v, rtol=1e-12)
+        else:
+            x, info, _ = orc.bicgstab(A, None, v, rtol=1e-12)
+        assert info["iters"] == 1, solver
+        assert np.allclose(x, v / (lx + ly + lz), rtol=1e-12, atol=1e-13)
+
+
+def test_cgs2_arnoldi_relation(orc):
+    """A M^{-1} V_m = V_{m+1} Hbar and V^T V = I for the CGS2 step."""
+    d = synth.pressure_7pt(synth.Grid(6, 6, 5), 14)
+    A = orc.Mat.csr(d)
+    M = orc.PC(A, "ilu0")
+    n, m = d["n"], 12
+    V = np.zeros((m + 1, n))
+    H = np.zeros((m + 1, m))
+    r = np.random.default_rng(15).standard_normal(n)
+    V[0] = r / np.linalg.norm(r)
+    for i in range(m):
+        w = orc.spmv(A, M.apply(V[i]))
+        w, h = orc.orthogonalise(V[:i + 1], w, i)
+        H[:i + 2, i] = h
+        V[i + 1] = w / h[i + 1]
+    AMV = np.stack([orc.spmv(A, M.apply(V[i])) for i in range(m)])
+    assert np.abs(AMV.T - V.T @ H).max() <= 1e-12 * np.abs(AMV).max()
+    assert np.abs(V @ V.T - np.eye(m + 1)).max() <= 1e-12
+    # the MGS variant builds the same Hessenberg matrix (up to rounding)
+    w0 = orc.spmv(A, M.apply(V[m - 1]))
+    _, h_c = orc.orthogonalise(V[:m], w0, m - 1)
+    _, h_m = orc.orthogonalise(V[:m], w0, m - 1, mgs=True)
+    assert np.allclose(h_c, h_m, rtol=1e-10, atol=1e-12)
+
+
+def test_gmres_ilu0_matches_direct_solution(orc):
+    d = synth.pressure_7pt(synth.Grid(8, 8, 8), 16)
+    A = orc.Mat.csr(d)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"]))
+    xt = synth.x_true(d["n"], 16)
+    b = S @ xt
+    M = orc.PC(A, "ilu0")
+    for kw in (dict(), dict(mgs=True), dict(flexible=True)):
+        x, info, _ = orc.gmres(A, M, b, restart=30, rtol=1e-12, **kw)
+        assert info["status"] == 0
+        assert np.linalg.norm(b - S @ x) <= 1e-12 * np.linalg.norm(b) * 1.0001
+        assert np.linalg.norm(x - spla.spsolve(S.tocsc(), b)) <= 1e-6 * np.linalg.norm(xt)
+    x, info, _ = orc.gmres(A, M, b, restart=30, rtol=1e-12, side="left")
+    assert info["status"] == 0
+    assert np.linalg.norm(x - spla.spsolve(S.tocsc(), b)) <= 1e-6 * np.linalg.norm(xt)
+
+
+def test_gmres_mgs_and_cgs2_iteration_counts_agree(orc):
+    d = synth.pressure_7pt(synth.Grid(16, 16, 16), 17)
+    A = orc.Mat.csr(d)
+    b = orc.spmv(A, synth.x_true(d["n"], 17))
+    M = orc.PC(A, "ilu0")
+    _, i1, _ = orc.gmres(A, M, b)
+    _, i2, _ = orc.gmres(A, M, b, mgs=True)
+    assert abs(i1["iters"] - i2["iters"]) <= 2
+
+
+def test_gmres_exact_preconditioner_one_step(orc):
+    d = synth.pressure_7pt(synth.Grid(5, 5, 4), 18)
+    A = orc.Mat.csr(d)
+    lu = spla.splu(sp.csr_matrix((d["val"], d["col"], d["rowptr"])).tocsc())
+    M = orc.PC(A, "callback", fn=lambda r: lu.solve(r))
+    b = np.random.default_rng(19).standard_normal(d["n"])
+    for flexible in (False, True):
+        x, info, _ = orc.gmres(A, M, b, rtol=1e-10, flexible=flexible)
+        assert info["iters"] == 1
+    x, info, _ = orc.gmres(A, M, b, rtol=1e-10, side="left")
+    assert info["iters"] == 1
+    x, info, _ = orc.bicgstab(A, M, b, rtol=1e-10)
+    assert info["iters"] == 1
+
+
+def test_fgmres_equals_gmres_for_fixed_preconditioner(orc):
+    d = synth.pressure_7pt(synth.Grid(10, 9, 8), 20)
+    A = orc.Mat.csr(d)
+    b = orc.spmv(A, synth.x_true(d["n"], 20))
+    M = orc.PC(A, "ilu0")
+    for maxit in (7, 30, 47):
+        x1, i1, h1 = orc.gmres(A, M, b, restart=20, rtol=1e-14, maxit=maxit, hist_len=maxit)
+        x2, i2, h2 = orc.fgmres(A, M, b, restart=20, rtol=1e-14, maxit=maxit, hist_len=maxit)
+        assert i1["iters"] == i2["iters"] == maxit
+        assert np.allclose(x1, x2, rtol=1e-12, atol=1e-12 * np.abs(x1).max())
+        assert np.allclose(h1, h2, rtol=1e-10)
+
+
+def test_gmres_edge_cases(orc):
+    d = synth.pressure_7pt(synth.Grid(4, 4, 4), 21)
+    A = orc.Mat.csr(d)
+    x, info, _ = orc.gmres(A, None, np.zeros(d["n"]), x0=np.ones(d["n"]))
+    assert info["status"] == 0 and info["iters"] == 0 and (x == 0).all()
+    xt = synth.x_true(d["n"], 21)
+    b = orc.spmv(A, xt)
+    x, info, _ = orc.gmres(A, None, b, maxit=5)
+    assert info["status"] == orc.NOT_CONVERGED and info["iters"] == 5
+    x, info, _ = orc.gmres(A, None, b, x0=xt)
+    assert info["status"] == 0 and info["iters"] == 0
+
+
+# ----------------------------------------------------------------------------
+# BiCGSTAB
+# ----------------------------------------------------------------------------
+def test_bicgstab_matches_direct_and_breakdown(orc):
+    d = synth.pressure_7pt(synth.Grid(8, 7, 6), 22, kz_scale=0.1)
+    A = orc.Mat.csr(d)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"]))
+    b = S @ synth.x_true(d["n"], 22)
+    for M in (None, orc.PC(A, "ilu0")):
+        x, info, _ = orc.bicgstab(A, M, b, rtol=1e-12)
+        assert info["status"] == 0
+        assert np.linalg.norm(b - S @ x) <= 1e-12 * np.linalg.norm(b) * 1.0001
+        assert np.allclose(x, spla.spsolve(S.tocsc(), b), rtol=1e-8, atol=1e-8)
+    # (rhat, A p) = 0 on the first step: A = [[0,1],[1,0]], b = e1
+    B = orc.Mat.csr(csr_dict(np.array([[0.0, 1.0], [1.0, 0.0]])))
+    _, info, _ = orc.bicgstab(B, None, np.array([1.0, 0.0]))
+    assert info["status"] == orc.BREAKDOWN
+
+
+def test_bicgstab_single_eigvec_and_spd_count(orc):
+    n = 60
+    A = orc.Mat.csr(csr_dict(poisson1d(n)))
+    v, lam = eig1d(n, 5)
+    x, info, _ = orc.bicgstab(A, None, v, rtol=1e-12)
+    assert info["iters"] == 1 and np.allclose(x, v / lam, rtol=1e-12, atol=1e-13)
+
+
+def test_mixed_precision_preconditioners_converge(orc):
+    d = synth.pressure_7pt(synth.Grid(12, 12, 8), 23, kz_scale=0.1)
+    A = orc.Mat.csr(d)
+    b = orc.spmv(A, synth.x_true(d["n"], 23))
+    x64, i64, _ = orc.gmres(A, orc.PC(A, "ilu0"), b)
+    x32, i32, _ = orc.gmres(A, orc.PC(A, "ilu0", mixed=True), b)
+    assert i32["status"] == 0 and i32["true_rel_res"] <= 1e-8
+    assert abs(i32["iters"] - i64["iters"]) <= 3
