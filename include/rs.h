@@ -1,0 +1,191 @@
+/*
+ * rs.h — C ABI of the GB300 preconditioned Krylov library.
+ *
+ * The calls follow the paper's statement of the problem (Liu & Chen,
+ * "Scalable linear solvers for sparse linear systems from large-scale
+ * numerical simulations"): vectors (Sec. 2.2, Figs. 6-13), matrices and
+ * matrix-vector products (Sec. 2.3, Figs. 15-21), preconditioners with
+ * setup / apply / destroy (Sec. 3, Fig. 29; Sec. 4), and solvers returning
+ * an iteration count and a residual (Sec. 3, Fig. 22, Alg. 1).
+ *
+ * General rules
+ *  - Every call returns an rs_status (0 = success); nothing asserts or exits.
+ *  - All work is ordered on the stream given to rs_init.  Calls that return
+ *    a host scalar (rs_vec_dot, rs_vec_norm2), copy to host (rs_vec_get with
+ *    RS_MEM_HOST) or solve (rs_solve_*) synchronise that stream before they
+ *    return; all other calls only enqueue work.
+ *  - Handles are created by *_create / *_setup, owned by the caller and
+ *    released with the matching *_destroy(&h), which sets *h to NULL.
+ *    A matrix or vector must outlive every preconditioner built from it.
+ *  - Creation calls copy the caller's arrays (host or device, per `mem`);
+ *    the caller keeps ownership of what it passed in.
+ *  - Indices are int32, 0-based.  CSR/BSR rows must list their columns in
+ *    strictly ascending order and hold the diagonal; violations return
+ *    RS_ERR_BAD_PATTERN.
+ *  - Every device-side wait is bounded; a wait that runs out makes the call
+ *    return RS_ERR_DEVICE_TIMEOUT and leaves the context usable.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rs_ctx rs_ctx;
+typedef struct rs_mat rs_mat;
+typedef struct rs_vec rs_vec;
+typedef struct rs_pc rs_pc;
+typedef struct rs_net rs_net;
+
+typedef enum {
+    RS_OK = 0,
+    RS_NOT_CONVERGED = 1,        /* maxit reached; x holds the last iterate   */
+    RS_ERR_INVALID_ARG = -1,
+    RS_ERR_BAD_PATTERN = -2,     /* unsorted / missing diagonal / out of range */
+    RS_ERR_ZERO_PIVOT = -3,      /* zero or non-finite pivot (row in info)    */
+    RS_ERR_BREAKDOWN = -4,       /* BiCGSTAB rho or (rhat, v) vanished        */
+    RS_ERR_DEVICE_TIMEOUT = -5,  /* a bounded device-side wait expired        */
+    RS_ERR_CUDA = -6,
+    RS_ERR_OOM = -7,
+    RS_ERR_SIZE_MISMATCH = -8
+} rs_status;
+
+typedef enum { RS_MEM_HOST = 0, RS_MEM_DEVICE = 1 } rs_mem;
+
+typedef enum {
+    RS_PC_NONE = 0,
+    RS_PC_ILU0 = 1,       /* ILU(0) of a CSR matrix (Sec. 4.1, Eq. 3)        */
+    RS_PC_BILU0 = 2,      /* block ILU(0) of a BSR matrix                     */
+    RS_PC_CPR = 3,        /* two-stage CPR, pressure stage ILU(0) (Alg. 6)    */
+    RS_PC_CPR_LEARNED = 4 /* two-stage CPR, pressure stage = learned network  */
+} rs_pc_type;
+
+typedef enum {
+    RS_FP64 = 0,          /* factors and applies in FP64                      */
+    RS_MIXED = 1          /* FP32 factors and applies, FP64 Krylov outer loop */
+} rs_prec;
+
+typedef struct {
+    int32_t prec;         /* rs_prec                                          */
+    int32_t nx, ny, nz;   /* grid of the pressure unknowns (learned stage)    */
+    const rs_net *net;    /* trained network (RS_PC_CPR_LEARNED)              */
+    const double *log_perm; /* device pointer, nx*ny*nz log-permeabilities    */
+} rs_pc_opts;
+
+typedef struct {
+    int32_t iters;            /* inner iterations (Arnoldi steps / BiCGSTAB loops) */
+    int32_t restarts;         /* completed GMRES cycles                       */
+    int32_t status;           /* rs_status of the solve                       */
+    int32_t bad_row;          /* row of a zero pivot, else -1                 */
+    double true_rel_res;      /* ||b - A x||_2 / ||b||_2, recomputed in FP64  */
+    double implicit_rel_res;  /* the solver's own residual estimate / ||b||   */
+    double solve_s;           /* wall time of the solve call                  */
+} rs_solve_info;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Binds the library to CUDA device `device` and the caller's stream
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream). */
+int rs_init(rs_ctx **ctx, int device, void *cuda_stream);
+int rs_finalize(rs_ctx **ctx);
+/* Waits for all work enqueued on the context's stream. */
+int rs_sync(rs_ctx *ctx);
+const char *rs_status_str(int status);
+/* Number of kernels this library has launched on the context so far. */
+int64_t rs_launch_count(const rs_ctx *ctx);
+
+/* ---- vectors (Sec. 2.2) ----------------------------------------------- */
+
+/* VecCreate (Fig. 7): an owned FP64 device vector of n entries, zeroed. */
+int rs_vec_create(rs_ctx *ctx, int32_t n, rs_vec **v);
+/* A non-owning view of n FP64 values at device address `dev` (e.g. memory
+ * allocated by PyTorch).  The memory must stay valid while the view lives. */
+int rs_vec_wrap(rs_ctx *ctx, int32_t n, double *dev, rs_vec **v);
+int rs_vec_destroy(rs_vec **v);
+int32_t rs_vec_size(const rs_vec *v);
+double *rs_vec_data(rs_vec *v);
+/* Copy n values in from / out to host or device memory. */
+int rs_vec_set(rs_vec *v, const double *src, int mem);
+int rs_vec_get(const rs_vec *v, double *dst, int mem);
+/* VecSetValue (Fig. 13): x_i = a. */
+int rs_vec_set_value(rs_vec *x, double a);
+/* VecAXPBY (Fig. 10): y = a x + b y. */
+int rs_vec_axpby(double a, const rs_vec *x, double b, rs_vec *y);
+/* VecAXPBYZ (Fig. 11): z = a x + b y. */
+int rs_vec_axpbyz(double a, const rs_vec *x, double b, const rs_vec *y, rs_vec *z);
+/* VecDot (Fig. 12): *out = <x, y> (deterministic tree reduction). */
+int rs_vec_dot(const rs_vec *x, const rs_vec *y, double *out);
+/* *out = ||x||_2. */
+int rs_vec_norm2(const rs_vec *x, double *out);
+
+/* ---- matrices (Sec. 2.3) ---------------------------------------------- */
+
+/* MatCreate/MatAssemble (Figs. 16-19) for an n x n CSR matrix:
+ * rowptr[n+1], col[nnz], val[nnz] (FP64), host or device per `mem`. */
+int rs_mat_create_csr(rs_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t *col,
+                      const double *val, int mem, rs_mat **A);
+/* A block matrix of nb x nb blocks of size bs x bs (bs = 3 for the
+ * black-oil systems of Eq. 9, one block per cell): browptr[nb+1],
+ * bcol[nnzb], bval[nnzb*bs*bs] with each block row-major. */
+int rs_mat_create_bsr(rs_ctx *ctx, int32_t nb, int32_t bs, const int32_t *browptr,
+                      const int32_t *bcol, const double *bval, int mem, rs_mat **A);
+int rs_mat_destroy(rs_mat **A);
+/* Scalar dimension (n for CSR, nb*bs for BSR). */
+int32_t rs_mat_size(const rs_mat *A);
+/* MatVecMXY (Fig. 20): y = A x. */
+int rs_mat_spmv(const rs_mat *A, const rs_vec *x, rs_vec *y);
+/* MatVecAMXPBY (Fig. 21): y = a A x + b y (b = 0 ignores y's contents). */
+int rs_mat_amxpby(double a, const rs_mat *A, const rs_vec *x, double b, rs_vec *y);
+
+/* ---- preconditioners (Sec. 3 Fig. 29, Sec. 4) -------------------------- */
+
+/* Builds M for A.  RS_PC_ILU0 needs a CSR matrix; RS_PC_BILU0 a BSR matrix;
+ * RS_PC_CPR a BSR matrix (quasi-IMPES pressure restriction, ILU(0) of the
+ * decoupled pressure matrix, then block ILU(0)) or a CSR matrix (pressure
+ * stage on A itself, second stage ILU(0)).  opts may be NULL (FP64).
+ * Returns RS_ERR_ZERO_PIVOT when a factorisation meets a zero pivot. */
+int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs_pc_opts *opts,
+                     rs_pc **M);
+/* z = M^{-1} r. */
+int rs_precond_apply(rs_pc *M, const rs_vec *r, rs_vec *z);
+/* Copies the ILU(0) factor values (FP64, in the pattern of the factored
+ * matrix: strict lower part of L, then U with its diagonal) to host memory.
+ * For RS_PC_CPR the factored matrix is the decoupled pressure matrix. */
+int rs_precond_get_ilu(const rs_pc *M, double *lu_host, int32_t nnz);
+/* Block ILU(0) factors: lu_host[nnzb*bs*bs] and the inverted diagonal
+ * blocks dinv_host[nb*bs*bs]. */
+int rs_precond_get_bilu(const rs_pc *M, double *lu_host, double *dinv_host);
+/* CPR on a block matrix: quasi-IMPES weights w_host[nb*(bs-1)] and the
+ * decoupled pressure matrix values app_host[nnzb] (block pattern of A).
+ * Either pointer may be NULL. */
+int rs_precond_get_cpr(const rs_pc *M, double *w_host, double *app_host);
+/* Row of the last zero pivot met by setup, or -1. */
+int32_t rs_precond_bad_row(const rs_pc *M);
+int rs_precond_destroy(rs_pc **M);
+
+/* ---- Krylov solvers (Sec. 3, Alg. 1) ----------------------------------- */
+/* x holds the initial guess on entry and the solution on exit.  Converged
+ * means ||b - A x||_2 <= rtol ||b||_2 for the recomputed FP64 residual.
+ * maxit counts inner iterations.  M may be NULL (no preconditioner).
+ * Right preconditioning throughout; orthogonalisation by classical
+ * Gram-Schmidt with one reorthogonalisation pass (CGS2).  1 <= restart <= 64.
+ * Returns RS_OK, RS_NOT_CONVERGED (info filled, x = last iterate) or an
+ * error; info->status repeats the return value. */
+int rs_solve_gmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_t restart,
+                   double rtol, int32_t maxit, rs_solve_info *info);
+/* Flexible GMRES: keeps z_i = M^{-1} v_i, so M may change between steps
+ * (the learned pressure stage). */
+int rs_solve_fgmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_t restart,
+                    double rtol, int32_t maxit, rs_solve_info *info);
+/* BiCGSTAB (named in Sec. 3; used in Examples 2, 4, 5). */
+int rs_solve_bicgstab(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, double rtol,
+                      int32_t maxit, rs_solve_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_H */

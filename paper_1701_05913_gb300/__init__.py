@@ -1,0 +1,342 @@
+"""Python binding of the GB300 preconditioned Krylov library (librs.so).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels
+of librs.so, reached through the C ABI declared in include/rs.h.  PyTorch
+supplies device memory (tensors) and the CUDA stream.  There is no CPU
+fallback: if the library is missing or no GPU is present, calls raise.
+
+Raw entry points keep their C names (``rs_init``, ``rs_mat_create_csr``,
+``rs_solve_gmres`` ...) on the loaded library object returned by ``lib()``;
+the classes below wrap the handles.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "librs.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_BAD_PATTERN, ERR_ZERO_PIVOT, ERR_BREAKDOWN = -1, -2, -3, -4
+ERR_DEVICE_TIMEOUT, ERR_CUDA, ERR_OOM, ERR_SIZE_MISMATCH = -5, -6, -7, -8
+MEM_HOST, MEM_DEVICE = 0, 1
+PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CPR_LEARNED = 0, 1, 2, 3, 4
+FP64, MIXED = 0, 1
+
+_PC_KIND = {"none": PC_NONE, "ilu0": PC_ILU0, "bilu0": PC_BILU0, "cpr": PC_CPR,
+            "cpr_learned": PC_CPR_LEARNED}
+
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+_f32p = C.POINTER(C.c_float)
+_vp = C.c_void_p
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32),
+                ("bad_row", C.c_int32), ("true_rel_res", C.c_double),
+                ("implicit_rel_res", C.c_double), ("solve_s", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PcOpts(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("net", _vp), ("log_perm", _vp)]
+
+
+# (name, restype, argtypes) for every exported symbol of include/rs.h
+SIGNATURES = [
+    ("rs_init", C.c_int, [C.POINTER(_vp), C.c_int, _vp]),
+    ("rs_finalize", C.c_int, [C.POINTER(_vp)]),
+    ("rs_sync", C.c_int, [_vp]),
+    ("rs_status_str", C.c_char_p, [C.c_int]),
+    ("rs_launch_count", C.c_int64, [_vp]),
+    ("rs_vec_create", C.c_int, [_vp, C.c_int32, C.POINTER(_vp)]),
+    ("rs_vec_wrap", C.c_int, [_vp, C.c_int32, _vp, C.POINTER(_vp)]),
+    ("rs_vec_destroy", C.c_int, [C.POINTER(_vp)]),
+    ("rs_vec_size", C.c_int32, [_vp]),
+    ("rs_vec_data", _vp, [_vp]),
+    ("rs_vec_set", C.c_int, [_vp, _vp, C.c_int]),
+    ("rs_vec_get", C.c_int, [_vp, _vp, C.c_int]),
+    ("rs_vec_set_value", C.c_int, [_vp, C.c_double]),
+    ("rs_vec_axpby", C.c_int, [C.c_double, _vp, C.c_double, _vp]),
+    ("rs_vec_axpbyz", C.c_int, [C.c_double, _vp, C.c_double, _vp, _vp]),
+    ("rs_vec_dot", C.c_int, [_vp, _vp, _f64p]),
+    ("rs_vec_norm2", C.c_int, [_vp, _f64p]),
+    ("rs_mat_create_csr", C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, C.c_int, C.POINTER(_vp)]),
+    ("rs_mat_create_bsr", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_int,
+                                    C.POINTER(_vp)]),
+    ("rs_mat_destroy", C.c_int, [C.POINTER(_vp)]),
+    ("rs_mat_size", C.c_int32, [_vp]),
+    ("rs_mat_spmv", C.c_int, [_vp, _vp, _vp]),
+    ("rs_mat_amxpby", C.c_int, [C.c_double, _vp, _vp, C.c_double, _vp]),
+    ("rs_precond_setup", C.c_int, [_vp, _vp, C.c_int, C.POINTER(PcOpts), C.POINTER(_vp)]),
+    ("rs_precond_apply", C.c_int, [_vp, _vp, _vp]),
+    ("rs_precond_get_ilu", C.c_int, [_vp, _f64p, C.c_int32]),
+    ("rs_precond_get_bilu", C.c_int, [_vp, _f64p, _f64p]),
+    ("rs_precond_get_cpr", C.c_int, [_vp, _f64p, _f64p]),
+    ("rs_precond_bad_row", C.c_int32, [_vp]),
+    ("rs_precond_destroy", C.c_int, [C.POINTER(_vp)]),
+    ("rs_solve_gmres", C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_double, C.c_int32,
+                                 C.POINTER(SolveInfo)]),
+    ("rs_solve_fgmres", C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_double, C.c_int32,
+                                  C.POINTER(SolveInfo)]),
+    ("rs_solve_bicgstab", C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int32,
+                                    C.POINTER(SolveInfo)]),
+]
+
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force, verbose=verbose)
+
+
+def lib():
+    """Loads librs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("librs.so not built: run __graft_entry__.build() "
+                              "(or python -m paper_1701_05913_gb300._build)")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class RsError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = lib().rs_status_str(status).decode()
+        super().__init__("%s failed: %s (%d)" % (what, msg, status))
+
+
+def _check(status, what):
+    if status != OK:
+        raise RsError(status, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_f64(t):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t, dtype=np.float64))
+    t = t.to(device="cuda", dtype=torch.float64).contiguous()
+    return t
+
+
+def _dev_i32(t):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t, dtype=np.int32))
+    return t.to(device="cuda", dtype=torch.int32).contiguous()
+
+
+class Context:
+    """rs_init on a CUDA device and a stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the CUDA library needs a GPU; none is visible")
+        torch.cuda.set_device(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.h = _vp()
+        _check(lib().rs_init(C.byref(self.h), device, _vp(stream.cuda_stream)), "rs_init")
+
+    def sync(self):
+        _check(lib().rs_sync(self.h), "rs_sync")
+
+    def launches(self) -> int:
+        return lib().rs_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            lib().rs_finalize(C.byref(self.h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Vec:
+    """An FP64 device vector viewing a torch tensor (rs_vec_wrap)."""
+
+    def __init__(self, ctx: Context, t):
+        self.ctx = ctx
+        self.t = _dev_f64(t)
+        self.n = self.t.numel()
+        self.h = _vp()
+        _check(lib().rs_vec_wrap(ctx.h, self.n, _vp(self.t.data_ptr()), C.byref(self.h)), "rs_vec_wrap")
+
+    @classmethod
+    def zeros(cls, ctx, n):
+        return cls(ctx, _torch().zeros(n, dtype=_torch().float64, device="cuda"))
+
+    def numpy(self):
+        self.ctx.sync()
+        return self.t.cpu().numpy()
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().rs_vec_destroy(C.byref(self.h))
+        except Exception:
+            pass
+
+
+class Mat:
+    """CSR or BSR matrix handle (the library keeps its own device copy)."""
+
+    def __init__(self, ctx: Context, ptr, col, val, bs: int = 1):
+        self.ctx = ctx
+        self.bs = int(bs)
+        p, c, v = _dev_i32(ptr), _dev_i32(col), _dev_f64(val)
+        self.nrows = p.numel() - 1
+        self.n = self.nrows * self.bs
+        self.h = _vp()
+        if self.bs == 1:
+            st = lib().rs_mat_create_csr(ctx.h, self.nrows, _vp(p.data_ptr()), _vp(c.data_ptr()),
+                                         _vp(v.data_ptr()), MEM_DEVICE, C.byref(self.h))
+        else:
+            st = lib().rs_mat_create_bsr(ctx.h, self.nrows, self.bs, _vp(p.data_ptr()),
+                                         _vp(c.data_ptr()), _vp(v.data_ptr()), MEM_DEVICE,
+                                         C.byref(self.h))
+        _check(st, "rs_mat_create")
+        self.nnz = c.numel()
+
+    @classmethod
+    def csr(cls, ctx, m: dict):
+        return cls(ctx, m["rowptr"], m["col"], m["val"], 1)
+
+    @classmethod
+    def bsr(cls, ctx, m: dict):
+        return cls(ctx, m["browptr"], m["bcol"], m["bval"], m["bs"])
+
+    def spmv(self, x: Vec, y: Vec):
+        _check(lib().rs_mat_spmv(self.h, x.h, y.h), "rs_mat_spmv")
+
+    def amxpby(self, a, x: Vec, b, y: Vec):
+        _check(lib().rs_mat_amxpby(a, self.h, x.h, b, y.h), "rs_mat_amxpby")
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().rs_mat_destroy(C.byref(self.h))
+        except Exception:
+            pass
+
+
+class Precond:
+    """rs_precond_setup / apply / destroy."""
+
+    def __init__(self, ctx: Context, A: Mat, kind: str = "ilu0", prec: str = "fp64",
+                 net=None, log_perm=None, grid=None):
+        self.ctx, self.A, self.kind = ctx, A, kind
+        opts = PcOpts()
+        opts.prec = MIXED if prec == "mixed" else FP64
+        self._keep = []
+        if net is not None:
+            opts.net = net.h
+            lp = _dev_f64(log_perm)
+            self._keep += [net, lp]
+            opts.log_perm = lp.data_ptr()
+            opts.nx, opts.ny, opts.nz = grid
+        self.h = _vp()
+        self.status = lib().rs_precond_setup(ctx.h, A.h, _PC_KIND[kind], C.byref(opts), C.byref(self.h))
+        self.bad_row = lib().rs_precond_bad_row(self.h) if self.h else -1
+        if self.status != ERR_ZERO_PIVOT:
+            _check(self.status, "rs_precond_setup")
+
+    def apply(self, r: Vec, z: Vec):
+        _check(lib().rs_precond_apply(self.h, r.h, z.h), "rs_precond_apply")
+
+    def ilu_factors(self, nnz):
+        out = np.empty(nnz)
+        _check(lib().rs_precond_get_ilu(self.h, out.ctypes.data_as(_f64p), nnz), "rs_precond_get_ilu")
+        return out
+
+    def bilu_factors(self):
+        bs = self.A.bs
+        lu = np.empty(self.A.nnz * bs * bs)
+        dinv = np.empty(self.A.nrows * bs * bs)
+        _check(lib().rs_precond_get_bilu(self.h, lu.ctypes.data_as(_f64p), dinv.ctypes.data_as(_f64p)),
+               "rs_precond_get_bilu")
+        return lu, dinv
+
+    def cpr_data(self):
+        bs = self.A.bs
+        w = np.empty(self.A.nrows * (bs - 1))
+        app = np.empty(self.A.nnz)
+        _check(lib().rs_precond_get_cpr(self.h, w.ctypes.data_as(_f64p), app.ctypes.data_as(_f64p)),
+               "rs_precond_get_cpr")
+        return w, app
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().rs_precond_destroy(C.byref(self.h))
+        except Exception:
+            pass
+
+
+def _solve(fn, A, M, b, x, *args):
+    info = SolveInfo()
+    st = fn(A.h, M.h if M is not None else None, b.h, x.h, *args, C.byref(info))
+    if st not in (OK, NOT_CONVERGED, ERR_BREAKDOWN):
+        raise RsError(st, fn.__name__)
+    return info.as_dict()
+
+
+def solve_gmres(A: Mat, M, b: Vec, x: Vec, restart=30, rtol=1e-8, maxit=10000):
+    return _solve(lib().rs_solve_gmres, A, M, b, x, restart, rtol, maxit)
+
+
+def solve_fgmres(A: Mat, M, b: Vec, x: Vec, restart=30, rtol=1e-8, maxit=10000):
+    return _solve(lib().rs_solve_fgmres, A, M, b, x, restart, rtol, maxit)
+
+
+def solve_bicgstab(A: Mat, M, b: Vec, x: Vec, rtol=1e-8, maxit=10000):
+    return _solve(lib().rs_solve_bicgstab, A, M, b, x, rtol, maxit)
+
+
+def vec_dot(x: Vec, y: Vec) -> float:
+    out = C.c_double()
+    _check(lib().rs_vec_dot(x.h, y.h, C.byref(out)), "rs_vec_dot")
+    return out.value
+
+
+def vec_norm2(x: Vec) -> float:
+    out = C.c_double()
+    _check(lib().rs_vec_norm2(x.h, C.byref(out)), "rs_vec_norm2")
+    return out.value
+
+
+def vec_axpby(a, x: Vec, b, y: Vec):
+    _check(lib().rs_vec_axpby(a, x.h, b, y.h), "rs_vec_axpby")
+
+
+def vec_axpbyz(a, x: Vec, b, y: Vec, z: Vec):
+    _check(lib().rs_vec_axpbyz(a, x.h, b, y.h, z.h), "rs_vec_axpbyz")
+
+
+def vec_set_value(x: Vec, a):
+    _check(lib().rs_vec_set_value(x.h, a), "rs_vec_set_value")

@@ -1,0 +1,580 @@
+// Context, vectors, matrices, BLAS-1 and SpMV kernels.
+//
+// Vectors: Sec. 2.2 (VEC, Figs. 6-13).  Matrices and products: Sec. 2.3
+// (MAT, Figs. 15-21).  One process owns the whole matrix, so the halo
+// exchange of MatVecMXY and the all-reduce of VecDot have no counterpart:
+// dot products are deterministic two-level tree reductions on the device.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rs_internal.cuh"
+
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+void rs_set_last_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
+
+int rs_count_launch(rs_ctx *ctx)
+{
+    ctx->launches++;
+    return RS_OK;
+}
+
+int rs_check_launch(rs_ctx *ctx)
+{
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        rs_set_last_cuda_error(e);
+        return RS_ERR_CUDA;
+    }
+    return RS_OK;
+}
+
+int rs_alloc(rs_ctx *ctx, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+        rs_set_last_cuda_error(e);
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? RS_ERR_OOM : RS_ERR_CUDA;
+    }
+    return RS_OK;
+}
+
+void rs_free(rs_ctx *ctx, void *p)
+{
+    if (p) cudaFreeAsync(p, ctx->stream);
+}
+
+extern "C" const char *rs_status_str(int s)
+{
+    switch (s) {
+    case RS_OK: return "ok";
+    case RS_NOT_CONVERGED: return "not converged within maxit";
+    case RS_ERR_INVALID_ARG: return "invalid argument";
+    case RS_ERR_BAD_PATTERN: return "bad sparsity pattern (unsorted, missing diagonal or out of range)";
+    case RS_ERR_ZERO_PIVOT: return "zero or non-finite pivot";
+    case RS_ERR_BREAKDOWN: return "Krylov breakdown";
+    case RS_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case RS_ERR_CUDA: return cudaGetErrorString(g_last_cuda_error);
+    case RS_ERR_OOM: return "out of device memory";
+    case RS_ERR_SIZE_MISMATCH: return "size mismatch";
+    default: return "unknown status";
+    }
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" int rs_init(rs_ctx **out, int device, void *stream)
+{
+    if (!out) return RS_ERR_INVALID_ARG;
+    *out = nullptr;
+    RS_CUDA_TRY(cudaSetDevice(device));
+    rs_ctx *c = new rs_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    c->red_blocks = 2 * c->num_sms;
+    c->launches = 0;
+    int clock_khz = 2000000;
+    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, device);
+    c->spin_limit = (long long)clock_khz * 1000LL * 2;   // about two seconds
+    // the stream-ordered pool keeps freed blocks for reuse
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    int st = RS_OK;
+    st = st ? st : rs_alloc(c, (void **)&c->red_partials,
+                            sizeof(double) * (size_t)c->red_blocks * (RS_MAX_RESTART + 8));
+    st = st ? st : rs_alloc(c, (void **)&c->red_ticket, sizeof(unsigned) * 8);
+    st = st ? st : rs_alloc(c, (void **)&c->d_scalars, sizeof(double) * 64);
+    st = st ? st : rs_alloc(c, (void **)&c->d_err, sizeof(int) * 2);
+    if (st) { delete c; return st; }
+    c->d_bad_row = c->d_err + 1;
+    cudaMemsetAsync(c->red_ticket, 0, sizeof(unsigned) * 8, c->stream);
+    cudaMemsetAsync(c->d_scalars, 0, sizeof(double) * 64, c->stream);
+    int init[2] = {0, 0x7fffffff};
+    cudaMemcpyAsync(c->d_err, init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
+    if (cudaMallocHost((void **)&c->h_pinned, sizeof(double) * 64) != cudaSuccess) {
+        delete c;
+        return RS_ERR_OOM;
+    }
+    RS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *out = c;
+    return RS_OK;
+}
+
+extern "C" int rs_finalize(rs_ctx **pc)
+{
+    if (!pc || !*pc) return RS_OK;
+    rs_ctx *c = *pc;
+    cudaStreamSynchronize(c->stream);
+    rs_free(c, c->red_partials);
+    rs_free(c, c->red_ticket);
+    rs_free(c, c->d_scalars);
+    rs_free(c, c->d_err);
+    cudaStreamSynchronize(c->stream);
+    cudaFreeHost(c->h_pinned);
+    delete c;
+    *pc = nullptr;
+    return RS_OK;
+}
+
+extern "C" int rs_sync(rs_ctx *ctx)
+{
+    if (!ctx) return RS_ERR_INVALID_ARG;
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return RS_OK;
+}
+
+extern "C" int64_t rs_launch_count(const rs_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int rs_collect_device_error(rs_ctx *ctx, int *bad_row)
+{
+    int h[2];
+    RS_CUDA_TRY(cudaMemcpyAsync(h, ctx->d_err, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (h[0] == 0) return RS_OK;
+    int init[2] = {0, 0x7fffffff};
+    RS_CUDA_TRY(cudaMemcpyAsync(ctx->d_err, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (bad_row) *bad_row = h[1] == 0x7fffffff ? -1 : h[1];
+    if (h[0] & RS_DEVERR_TIMEOUT) return RS_ERR_DEVICE_TIMEOUT;
+    if (h[0] & RS_DEVERR_PIVOT) return RS_ERR_ZERO_PIVOT;
+    return RS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// BLAS-1 kernels (Figs. 10-13)
+// ---------------------------------------------------------------------------
+static int blas_grid(rs_ctx *ctx, int n)
+{
+    int g = (n + 255) / 256;
+    int cap = ctx->num_sms * 8;
+    return std::max(1, std::min(g, cap));
+}
+
+__global__ void k_set(int n, double a, double *x)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = a;
+}
+
+__global__ void k_axpby(int n, double a, const double *__restrict__ x, double b, double *y)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = b == 0.0 ? a * x[i] : a * x[i] + b * y[i];
+}
+
+__global__ void k_axpbyz(int n, double a, const double *__restrict__ x, double b,
+                         const double *__restrict__ y, double *__restrict__ z)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        z[i] = a * x[i] + b * y[i];
+}
+
+// Two-level deterministic dot product: fixed grid, per-block partial sums,
+// the last block to finish adds the partials in block order.
+__global__ void __launch_bounds__(RS_RED_THREADS)
+k_dot(int n, const double *__restrict__ x, const double *__restrict__ y, double *partials,
+      unsigned *ticket, double *out, int sqrt_out)
+{
+    __shared__ double sm[RS_RED_THREADS / 32];
+    __shared__ bool last;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const int stride = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        a0 += x[i] * y[i];
+        a1 += x[i + stride] * y[i + stride];
+        a2 += x[i + 2 * stride] * y[i + 2 * stride];
+        a3 += x[i + 3 * stride] * y[i + 3 * stride];
+    }
+    for (; i < n; i += stride) a0 += x[i] * y[i];
+    double a = warp_sum((a0 + a1) + (a2 + a3));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < RS_RED_THREADS / 32; ++w) s += sm[w];
+        partials[blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 32) {
+        double s = 0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(partials + b);
+        s = warp_sum(s);
+        if (threadIdx.x == 0) {
+            *out = sqrt_out ? sqrt(s) : s;
+            *ticket = 0;
+        }
+    }
+}
+
+int rs_axpby_launch(rs_ctx *ctx, int n, double a, const double *x, double b, double *y)
+{
+    if (n <= 0) return RS_OK;
+    k_axpby<<<blas_grid(ctx, n), 256, 0, ctx->stream>>>(n, a, x, b, y);
+    return rs_check_launch(ctx);
+}
+
+int rs_dot_launch(rs_ctx *ctx, int n, const double *x, const double *y, double *out_dev)
+{
+    if (n <= 0) {
+        RS_CUDA_TRY(cudaMemsetAsync(out_dev, 0, sizeof(double), ctx->stream));
+        return RS_OK;
+    }
+    k_dot<<<ctx->red_blocks, RS_RED_THREADS, 0, ctx->stream>>>(n, x, y, ctx->red_partials,
+                                                               ctx->red_ticket, out_dev, 0);
+    return rs_check_launch(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// vectors
+// ---------------------------------------------------------------------------
+extern "C" int rs_vec_create(rs_ctx *ctx, int32_t n, rs_vec **v)
+{
+    if (!ctx || !v || n < 0) return RS_ERR_INVALID_ARG;
+    rs_vec *x = new rs_vec();
+    x->ctx = ctx;
+    x->n = n;
+    x->owns = 1;
+    int st = rs_alloc(ctx, (void **)&x->d, sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (st) { delete x; return st; }
+    cudaMemsetAsync(x->d, 0, sizeof(double) * (size_t)n, ctx->stream);
+    *v = x;
+    return RS_OK;
+}
+
+extern "C" int rs_vec_wrap(rs_ctx *ctx, int32_t n, double *dev, rs_vec **v)
+{
+    if (!ctx || !v || n < 0 || (!dev && n > 0)) return RS_ERR_INVALID_ARG;
+    rs_vec *x = new rs_vec();
+    x->ctx = ctx;
+    x->n = n;
+    x->d = dev;
+    x->owns = 0;
+    *v = x;
+    return RS_OK;
+}
+
+extern "C" int rs_vec_destroy(rs_vec **v)
+{
+    if (!v || !*v) return RS_OK;
+    if ((*v)->owns) rs_free((*v)->ctx, (*v)->d);
+    delete *v;
+    *v = nullptr;
+    return RS_OK;
+}
+
+extern "C" int32_t rs_vec_size(const rs_vec *v) { return v ? v->n : -1; }
+extern "C" double *rs_vec_data(rs_vec *v) { return v ? v->d : nullptr; }
+
+extern "C" int rs_vec_set(rs_vec *v, const double *src, int mem)
+{
+    if (!v || (!src && v->n > 0)) return RS_ERR_INVALID_ARG;
+    if (v->n == 0) return RS_OK;
+    RS_CUDA_TRY(cudaMemcpyAsync(v->d, src, sizeof(double) * (size_t)v->n,
+                                mem == RS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                v->ctx->stream));
+    if (mem == RS_MEM_HOST) RS_CUDA_TRY(cudaStreamSynchronize(v->ctx->stream));
+    return RS_OK;
+}
+
+extern "C" int rs_vec_get(const rs_vec *v, double *dst, int mem)
+{
+    if (!v || (!dst && v->n > 0)) return RS_ERR_INVALID_ARG;
+    if (v->n == 0) return RS_OK;
+    RS_CUDA_TRY(cudaMemcpyAsync(dst, v->d, sizeof(double) * (size_t)v->n,
+                                mem == RS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                v->ctx->stream));
+    if (mem == RS_MEM_HOST) RS_CUDA_TRY(cudaStreamSynchronize(v->ctx->stream));
+    return RS_OK;
+}
+
+extern "C" int rs_vec_set_value(rs_vec *x, double a)
+{
+    if (!x) return RS_ERR_INVALID_ARG;
+    if (x->n == 0) return RS_OK;
+    k_set<<<blas_grid(x->ctx, x->n), 256, 0, x->ctx->stream>>>(x->n, a, x->d);
+    return rs_check_launch(x->ctx);
+}
+
+extern "C" int rs_vec_axpby(double a, const rs_vec *x, double b, rs_vec *y)
+{
+    if (!x || !y) return RS_ERR_INVALID_ARG;
+    if (x->n != y->n) return RS_ERR_SIZE_MISMATCH;
+    return rs_axpby_launch(y->ctx, y->n, a, x->d, b, y->d);
+}
+
+extern "C" int rs_vec_axpbyz(double a, const rs_vec *x, double b, const rs_vec *y, rs_vec *z)
+{
+    if (!x || !y || !z) return RS_ERR_INVALID_ARG;
+    if (x->n != y->n || x->n != z->n) return RS_ERR_SIZE_MISMATCH;
+    if (z->n == 0) return RS_OK;
+    k_axpbyz<<<blas_grid(z->ctx, z->n), 256, 0, z->ctx->stream>>>(z->n, a, x->d, b, y->d, z->d);
+    return rs_check_launch(z->ctx);
+}
+
+static int dot_to_host(rs_ctx *ctx, int n, const double *x, const double *y, int sq, double *out)
+{
+    if (n == 0) { *out = 0.0; return RS_OK; }
+    k_dot<<<ctx->red_blocks, RS_RED_THREADS, 0, ctx->stream>>>(n, x, y, ctx->red_partials,
+                                                               ctx->red_ticket, ctx->d_scalars, sq);
+    RS_TRY(rs_check_launch(ctx));
+    RS_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scalars, sizeof(double),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    *out = ctx->h_pinned[0];
+    return RS_OK;
+}
+
+extern "C" int rs_vec_dot(const rs_vec *x, const rs_vec *y, double *out)
+{
+    if (!x || !y || !out) return RS_ERR_INVALID_ARG;
+    if (x->n != y->n) return RS_ERR_SIZE_MISMATCH;
+    return dot_to_host(x->ctx, x->n, x->d, y->d, 0, out);
+}
+
+extern "C" int rs_vec_norm2(const rs_vec *x, double *out)
+{
+    if (!x || !out) return RS_ERR_INVALID_ARG;
+    return dot_to_host(x->ctx, x->n, x->d, x->d, 1, out);
+}
+
+// ---------------------------------------------------------------------------
+// SpMV kernels (Figs. 20-21)
+// ---------------------------------------------------------------------------
+// CSR: L lanes per row; each lane strides over the row's nonzeros, the group
+// adds its lanes with shuffles.  mode 0: y = alpha*Ax + beta*y;
+// mode 1: y = b - Ax (residual, b passed in `bvec`).
+template <int L>
+__global__ void __launch_bounds__(256)
+k_spmv_csr(int n, const int *__restrict__ ptr, const int *__restrict__ col,
+           const double *__restrict__ val, const double *__restrict__ x, double alpha, double beta,
+           const double *__restrict__ bvec, double *__restrict__ y, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = gid / L;
+    const int lane = gid % L;
+    const bool active = row < n;
+    double acc = 0.0;
+    if (active) {
+        const int s = ptr[row], e = ptr[row + 1];
+        for (int p = s + lane; p < e; p += L) acc += val[p] * __ldg(x + col[p]);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
+    if (active && lane == 0) {
+        if (bvec) y[row] = bvec[row] - acc;
+        else if (beta == 0.0) y[row] = alpha * acc;
+        else y[row] = alpha * acc + beta * y[row];
+    }
+}
+
+// BSR: one thread per scalar row (block row I, component r).
+template <int BS>
+__global__ void __launch_bounds__(256)
+k_spmv_bsr(int nb, int bsr, const int *__restrict__ ptr, const int *__restrict__ col,
+           const double *__restrict__ val, const double *__restrict__ x, double alpha, double beta,
+           const double *__restrict__ bvec, double *__restrict__ y, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    const int bs = BS > 0 ? BS : bsr;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nb * bs) return;
+    const int I = (int)(t / bs), r = (int)(t % bs);
+    double acc = 0.0;
+    for (int p = ptr[I]; p < ptr[I + 1]; ++p) {
+        const double *blk = val + (size_t)p * bs * bs + (size_t)r * bs;
+        const double *xs = x + (size_t)col[p] * bs;
+        if (BS > 0) {
+#pragma unroll
+            for (int c = 0; c < (BS > 0 ? BS : 1); ++c) acc += blk[c] * __ldg(xs + c);
+        } else {
+            for (int c = 0; c < bs; ++c) acc += blk[c] * __ldg(xs + c);
+        }
+    }
+    if (bvec) y[t] = bvec[t] - acc;
+    else if (beta == 0.0) y[t] = alpha * acc;
+    else y[t] = alpha * acc + beta * y[t];
+}
+
+static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double beta,
+                         const double *bvec, double *y, const int *skip)
+{
+    rs_ctx *ctx = A->ctx;
+    if (A->n == 0) return RS_OK;
+    if (A->bs == 1) {
+        const int L = A->lanes;
+        const int64_t threads = (int64_t)A->n * L;
+        const int grid = (int)((threads + 255) / 256);
+        switch (L) {
+#define RS_SPMV_CASE(LL)                                                                    \
+    case LL:                                                                                \
+        k_spmv_csr<LL><<<grid, 256, 0, ctx->stream>>>(A->n, A->ptr, A->col, A->val, x, alpha, \
+                                                      beta, bvec, y, skip);                 \
+        break;
+            RS_SPMV_CASE(1)
+            RS_SPMV_CASE(2)
+            RS_SPMV_CASE(4)
+            RS_SPMV_CASE(8)
+            RS_SPMV_CASE(16)
+            RS_SPMV_CASE(32)
+#undef RS_SPMV_CASE
+        default: return RS_ERR_INVALID_ARG;
+        }
+    } else {
+        const int64_t threads = (int64_t)A->nrows * A->bs;
+        const int grid = (int)((threads + 255) / 256);
+        if (A->bs == 3)
+            k_spmv_bsr<3><<<grid, 256, 0, ctx->stream>>>(A->nrows, 3, A->ptr, A->col, A->val, x,
+                                                         alpha, beta, bvec, y, skip);
+        else if (A->bs == 2)
+            k_spmv_bsr<2><<<grid, 256, 0, ctx->stream>>>(A->nrows, 2, A->ptr, A->col, A->val, x,
+                                                         alpha, beta, bvec, y, skip);
+        else
+            k_spmv_bsr<0><<<grid, 256, 0, ctx->stream>>>(A->nrows, A->bs, A->ptr, A->col, A->val,
+                                                         x, alpha, beta, bvec, y, skip);
+    }
+    return rs_check_launch(ctx);
+}
+
+int rs_spmv_launch(const rs_mat *A, const double *x, double alpha, double beta, double *y,
+                   const int *skip)
+{
+    return spmv_dispatch(A, x, alpha, beta, nullptr, y, skip);
+}
+
+int rs_residual_launch(const rs_mat *A, const double *b, const double *x, double *r,
+                       double *norm2_out, const int *skip)
+{
+    RS_TRY(spmv_dispatch(A, x, -1.0, 0.0, b, r, skip));
+    if (norm2_out) RS_TRY(rs_dot_launch(A->ctx, A->n, r, r, norm2_out));
+    return RS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// matrices
+// ---------------------------------------------------------------------------
+static int validate_pattern(int nrows, int ncols, const std::vector<int> &ptr,
+                            const std::vector<int> &col)
+{
+    if ((int)ptr.size() != nrows + 1 || ptr[0] != 0) return RS_ERR_BAD_PATTERN;
+    for (int i = 0; i < nrows; ++i) {
+        if (ptr[i + 1] < ptr[i]) return RS_ERR_BAD_PATTERN;
+        bool diag = false;
+        for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+            const int c = col[p];
+            if (c < 0 || c >= ncols) return RS_ERR_BAD_PATTERN;
+            if (p > ptr[i] && col[p - 1] >= c) return RS_ERR_BAD_PATTERN;
+            if (c == i) diag = true;
+        }
+        if (!diag) return RS_ERR_BAD_PATTERN;
+    }
+    if ((size_t)ptr[nrows] != col.size()) return RS_ERR_BAD_PATTERN;
+    return RS_OK;
+}
+
+static int mat_create(rs_ctx *ctx, int nrows, int bs, const int32_t *ptr, const int32_t *col,
+                      const double *val, int mem, rs_mat **out)
+{
+    if (!ctx || !out || nrows < 0 || bs < 1 || bs > 8 || !ptr) return RS_ERR_INVALID_ARG;
+    if ((int64_t)nrows * bs > 0x7fffffffLL) return RS_ERR_INVALID_ARG;
+    *out = nullptr;
+    const cudaMemcpyKind h2d = mem == RS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind d2h = mem == RS_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+    rs_mat *A = new rs_mat();
+    A->ctx = ctx;
+    A->bs = bs;
+    A->nrows = nrows;
+    A->n = nrows * bs;
+    A->h_ptr.resize(nrows + 1);
+    RS_CUDA_TRY(cudaMemcpyAsync(A->h_ptr.data(), ptr, sizeof(int) * (nrows + 1), d2h, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    const int64_t nnzb = A->h_ptr[nrows];
+    if (nnzb < 0 || (!col && nnzb > 0) || (!val && nnzb > 0) ||
+        nnzb * bs * bs > 0x7fffffffLL) {
+        delete A;
+        return RS_ERR_INVALID_ARG;
+    }
+    A->nnzb = nnzb;
+    A->h_col.resize(nnzb);
+    if (nnzb) {
+        RS_CUDA_TRY(cudaMemcpyAsync(A->h_col.data(), col, sizeof(int) * nnzb, d2h, ctx->stream));
+        RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    int st = validate_pattern(nrows, nrows, A->h_ptr, A->h_col);
+    if (st) { delete A; return st; }
+    st = rs_alloc(ctx, (void **)&A->ptr, sizeof(int) * (nrows + 1));
+    st = st ? st : rs_alloc(ctx, (void **)&A->col, sizeof(int) * nnzb);
+    st = st ? st : rs_alloc(ctx, (void **)&A->val, sizeof(double) * nnzb * bs * bs);
+    if (st) { rs_free(ctx, A->ptr); rs_free(ctx, A->col); delete A; return st; }
+    RS_CUDA_TRY(cudaMemcpyAsync(A->ptr, ptr, sizeof(int) * (nrows + 1), h2d, ctx->stream));
+    if (nnzb) {
+        RS_CUDA_TRY(cudaMemcpyAsync(A->col, col, sizeof(int) * nnzb, h2d, ctx->stream));
+        RS_CUDA_TRY(cudaMemcpyAsync(A->val, val, sizeof(double) * nnzb * bs * bs, h2d, ctx->stream));
+    }
+    if (mem == RS_MEM_HOST) RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    // lanes per row of the CSR kernel: the power of two nearest the mean row length
+    const double mean = nrows ? (double)nnzb / nrows : 1.0;
+    int L = 1;
+    while (L < 32 && L * 1.5 < mean) L <<= 1;
+    A->lanes = L;
+    *out = A;
+    return RS_OK;
+}
+
+extern "C" int rs_mat_create_csr(rs_ctx *ctx, int32_t n, const int32_t *rowptr,
+                                 const int32_t *col, const double *val, int mem, rs_mat **A)
+{
+    return mat_create(ctx, n, 1, rowptr, col, val, mem, A);
+}
+
+extern "C" int rs_mat_create_bsr(rs_ctx *ctx, int32_t nb, int32_t bs, const int32_t *browptr,
+                                 const int32_t *bcol, const double *bval, int mem, rs_mat **A)
+{
+    return mat_create(ctx, nb, bs, browptr, bcol, bval, mem, A);
+}
+
+extern "C" int rs_mat_destroy(rs_mat **pA)
+{
+    if (!pA || !*pA) return RS_OK;
+    rs_mat *A = *pA;
+    rs_free(A->ctx, A->ptr);
+    rs_free(A->ctx, A->col);
+    rs_free(A->ctx, A->val);
+    delete A;
+    *pA = nullptr;
+    return RS_OK;
+}
+
+extern "C" int32_t rs_mat_size(const rs_mat *A) { return A ? A->n : -1; }
+
+extern "C" int rs_mat_spmv(const rs_mat *A, const rs_vec *x, rs_vec *y)
+{
+    if (!A || !x || !y) return RS_ERR_INVALID_ARG;
+    if (x->n != A->n || y->n != A->n) return RS_ERR_SIZE_MISMATCH;
+    if (x->d == y->d && A->n > 0) return RS_ERR_INVALID_ARG;
+    return rs_spmv_launch(A, x->d, 1.0, 0.0, y->d, nullptr);
+}
+
+extern "C" int rs_mat_amxpby(double a, const rs_mat *A, const rs_vec *x, double b, rs_vec *y)
+{
+    if (!A || !x || !y) return RS_ERR_INVALID_ARG;
+    if (x->n != A->n || y->n != A->n) return RS_ERR_SIZE_MISMATCH;
+    if (x->d == y->d && A->n > 0) return RS_ERR_INVALID_ARG;
+    return rs_spmv_launch(A, x->d, a, b, y->d, nullptr);
+}

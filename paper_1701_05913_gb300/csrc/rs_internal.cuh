@@ -1,0 +1,212 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "rs.h"
+
+#define RS_MAX_RESTART 64
+#define RS_RED_THREADS 256
+#define RS_SLICE 32            // rows per slice of the sliced-ELL factor layout
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+#define RS_CUDA_TRY(expr)                                                     \
+    do {                                                                      \
+        cudaError_t _e = (expr);                                              \
+        if (_e != cudaSuccess) {                                              \
+            rs_set_last_cuda_error(_e);                                       \
+            return _e == cudaErrorMemoryAllocation ? RS_ERR_OOM : RS_ERR_CUDA; \
+        }                                                                     \
+    } while (0)
+
+#define RS_TRY(expr)                    \
+    do {                                \
+        int _s = (expr);                \
+        if (_s != RS_OK) return _s;     \
+    } while (0)
+
+void rs_set_last_cuda_error(cudaError_t e);
+
+// device error word bits
+#define RS_DEVERR_TIMEOUT 1
+#define RS_DEVERR_PIVOT 2
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct rs_ctx {
+    int device;
+    cudaStream_t stream;
+    int num_sms;
+    int red_blocks;          // fixed grid of the reduction kernels
+    double *red_partials;    // red_blocks * (RS_MAX_RESTART + 8) doubles
+    unsigned *red_ticket;    // last-block ticket of the reduction kernels
+    double *d_scalars;       // small device scalar area (64 doubles)
+    int *d_err;              // device error word
+    int *d_bad_row;          // smallest row with a bad pivot
+    double *h_pinned;        // pinned host staging (64 doubles)
+    long long launches;
+    long long spin_limit;    // clock cycles a device-side wait may take
+};
+
+struct rs_mat {
+    rs_ctx *ctx;
+    int bs;                  // 1 = CSR
+    int nrows;               // block rows
+    int n;                   // scalar rows
+    int64_t nnzb;            // stored blocks (scalars for CSR)
+    int *ptr, *col;
+    double *val;
+    std::vector<int> h_ptr, h_col;   // host copy of the pattern (analysis)
+    int lanes;               // SpMV lanes per row (CSR)
+};
+
+struct rs_vec {
+    rs_ctx *ctx;
+    int n;
+    double *d;
+    int owns;
+};
+
+// state of one sync-free sweep: work ticket, finished-block count, epoch
+struct SweepState {
+    unsigned ticket;
+    unsigned done;
+    int epoch;
+    int pad;
+};
+
+// Level-scheduled, sliced-ELL layout of one triangular factor.
+struct TriLayout {
+    int npad = 0;            // positions (levels padded to multiples of 32)
+    int nslices = 0;
+    int nlevels = 0;
+    int64_t nent = 0;        // sliced-ELL entries (incl. padding)
+    int *pos = nullptr;      // [npad] row at each position or -1
+    int *slice_ptr = nullptr;// [nslices+1] first entry of each slice
+    int *col = nullptr;      // [nent] column (block column) or -1
+    int *src = nullptr;      // [nent] index of the entry in the CSR/BSR value array or -1
+    int *dsrc = nullptr;     // [npad] index of the diagonal entry (U only) or -1
+    void *val = nullptr;     // [nent * bs*bs] factor values (float or double)
+    void *diag = nullptr;    // [npad * bs*bs] U: diagonal (bs=1) or its inverse (bs>1)
+};
+
+// ILU(0) / block ILU(0) of one matrix pattern.
+struct IluFactor {
+    rs_ctx *ctx = nullptr;
+    int bs = 1;
+    int nrows = 0;
+    int64_t nnzb = 0;
+    int fp32 = 0;            // apply precision
+    const int *ptr = nullptr, *col = nullptr;  // pattern (device, borrowed)
+    int *diagpos = nullptr;  // [nrows]
+    double *lu = nullptr;    // [nnzb*bs*bs] FP64 factors in the matrix pattern
+    double *dinv = nullptr;  // [nrows*bs*bs] inverted diagonal blocks (bs > 1)
+    TriLayout L, U;
+    int *flags = nullptr;    // [nrows] sweep flags
+    SweepState *state = nullptr;
+    void *ywork = nullptr;   // [nrows*bs] intermediate of the L sweep
+    void *zwork = nullptr;   // [nrows*bs] FP32 output of the U sweep (fp32)
+    int host_epoch = 0;
+};
+
+struct rs_pc {
+    rs_ctx *ctx;
+    int type;
+    int prec;
+    const rs_mat *A;
+    IluFactor *ilu;          // ILU0, or pressure stage of CPR
+    IluFactor *bilu;         // BILU0, or second stage of CPR
+    // CPR
+    int *app_ptr_unused;
+    double *app_val;         // decoupled pressure matrix values (block pattern)
+    double *w;               // quasi-IMPES weights [nb*(bs-1)]
+    double *rp, *zp;         // pressure-stage vectors [nb]
+    double *t1, *t2;         // full-size work vectors [n]
+    // learned pressure stage
+    const rs_net *net;
+    const double *log_perm;
+    int nx, ny, nz;
+    int bad_row;
+};
+
+// ---------------------------------------------------------------------------
+// internal entry points shared across translation units
+// ---------------------------------------------------------------------------
+int rs_count_launch(rs_ctx *ctx);
+int rs_check_launch(rs_ctx *ctx);
+int rs_alloc(rs_ctx *ctx, void **p, size_t bytes);
+void rs_free(rs_ctx *ctx, void *p);
+
+// y = alpha * A x + beta * y (beta == 0: y not read).  Kernels given a
+// non-null `skip` return at once when *skip != 0 (a device flag).
+int rs_spmv_launch(const rs_mat *A, const double *x, double alpha, double beta, double *y,
+                   const int *skip);
+// r = b - A x and, if norm2_out != nullptr, *norm2_out (device) = ||r||^2
+int rs_residual_launch(const rs_mat *A, const double *b, const double *x, double *r,
+                       double *norm2_out, const int *skip);
+// device-scalar BLAS-1
+int rs_axpby_launch(rs_ctx *ctx, int n, double a, const double *x, double b, double *y);
+int rs_dot_launch(rs_ctx *ctx, int n, const double *x, const double *y, double *out_dev);
+
+// ILU
+int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr,
+                  const int *d_col, const std::vector<int> &h_ptr,
+                  const std::vector<int> &h_col, int fp32, IluFactor **out, int *bad_row);
+int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row);
+int rs_ilu_apply(IluFactor *f, const double *r, double *z, const double *scale_dev,
+                 const int *skip);
+void rs_ilu_destroy(IluFactor *f);
+
+// CPR / learned pressure stage
+int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip);
+int rs_net_apply_pressure(rs_pc *M, const double *rp, double *zp, const int *skip);
+
+// reads back and clears the device error word; maps it to a status
+int rs_collect_device_error(rs_ctx *ctx, int *bad_row);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Waits until flag >= epoch (wrap-safe) or the clock budget runs out.
+// Returns false on timeout.
+__device__ __forceinline__ bool wait_epoch(const int *flag, int epoch, long long limit)
+{
+    int v = ld_acquire(flag);
+    if (v - epoch >= 0) return true;
+    const long long t0 = clock64();
+    unsigned ns = 8;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        v = ld_acquire(flag);
+        if (v - epoch >= 0) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+#endif

@@ -1,0 +1,664 @@
+// Krylov solvers: restarted GMRES(m) (Sec. 3, Alg. 1), flexible GMRES and
+// BiCGSTAB (named in Sec. 3), right-preconditioned, FP64.
+//
+// Device-resident design: the Hessenberg matrix, the Givens rotations, the
+// rotated residual and every BiCGSTAB scalar live in device memory and are
+// updated by the last block of the reduction that produces them, so a whole
+// GMRES cycle (or a batch of BiCGSTAB iterations) is enqueued without waiting
+// for the host.  Once a cycle has converged, a device flag makes every later
+// kernel of the cycle return at once.  The host reads the state back twice
+// per GMRES cycle and once per batch of BiCGSTAB iterations.
+//
+// Orthogonalisation is classical Gram-Schmidt with one full
+// reorthogonalisation pass (CGS2) instead of the modified Gram-Schmidt loop
+// printed in Alg. 1: the 2(i+1) dot products of step i become three fused
+// passes over the basis V (dots; update + dots; update + norm), each a
+// tall-skinny product computed row-wise with per-block partial sums.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "rs_internal.cuh"
+
+#define RS_PSTRIDE (RS_MAX_RESTART + 8)   // partials per block in ctx->red_partials
+
+struct GmresDev {
+    double H[(RS_MAX_RESTART + 1) * RS_MAX_RESTART];   // column-major, ld = m+1
+    double cs[RS_MAX_RESTART], sn[RS_MAX_RESTART];
+    double g[RS_MAX_RESTART + 1], y[RS_MAX_RESTART + 1];
+    double h1[RS_MAX_RESTART + 2], h2[RS_MAX_RESTART + 2];
+    double bnorm, tol, beta, inv_h, w0sq, implicit, r2;
+    int iters, k, cycle_done, converged, maxit, m, noupd, status;
+};
+
+// ---------------------------------------------------------------------------
+// block reduction of up to NC+1 per-thread sums with a last-block finish
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ bool reduce_partials(double (&acc)[NV], int nv, double *partials,
+                                                unsigned *ticket, double *out)
+{
+    __shared__ double sm[RS_RED_THREADS / 32][NV];
+    __shared__ bool last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (k < nv) {
+            const double v = warp_sum(acc[k]);
+            if (lane == 0) sm[warp][k] = v;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < RS_RED_THREADS / 32; ++w) s += sm[w][k];
+        partials[(size_t)blockIdx.x * RS_PSTRIDE + k] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int k = warp; k < nv; k += RS_RED_THREADS / 32) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partials + (size_t)b * RS_PSTRIDE + k);
+        s = warp_sum(s);
+        if (lane == 0) out[k] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0;
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// CGS2 kernels for Arnoldi step i (nc = i+1 basis vectors, w in V[:, i+1])
+// ---------------------------------------------------------------------------
+// pass 1: h1 = V^T w, plus ||w||^2 for the breakdown test
+template <int NC>
+__global__ void __launch_bounds__(RS_RED_THREADS)
+k_cgs_dots(int n, int ld, int nc, const double *__restrict__ V, const double *__restrict__ w,
+           double *partials, unsigned *ticket, GmresDev *d)
+{
+    if (*(volatile int *)&d->cycle_done) return;
+    double acc[NC + 1];
+#pragma unroll
+    for (int k = 0; k <= NC; ++k) acc[k] = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const double wr = w[r];
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            if (k < nc) acc[k] += V[(size_t)k * ld + r] * wr;
+        acc[NC] += wr * wr;
+    }
+    // move the norm into slot nc so the reduction covers slots 0..nc
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+        if (k == nc) acc[k] = acc[NC];
+    double *out = d->h1;
+    if (reduce_partials<NC + 1>(acc, nc + 1, partials, ticket, out)) {
+        if (threadIdx.x == 0) d->w0sq = out[nc];
+    }
+}
+
+// pass 2: w -= V h1; h2 = V^T w; H[:, i] = h1 + h2
+template <int NC>
+__global__ void __launch_bounds__(RS_RED_THREADS)
+k_cgs_update_dots(int n, int ld, int nc, const double *__restrict__ V, double *__restrict__ w,
+                  double *partials, unsigned *ticket, GmresDev *d)
+{
+    if (*(volatile int *)&d->cycle_done) return;
+    __shared__ double hs[NC];
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) hs[k] = d->h1[k];
+    __syncthreads();
+    double acc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        double v[NC];
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if (k < nc) {
+                v[k] = V[(size_t)k * ld + r];
+                s += v[k] * hs[k];
+            }
+        }
+        const double w1 = w[r] - s;
+        w[r] = w1;
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            if (k < nc) acc[k] += v[k] * w1;
+    }
+    if (reduce_partials<NC>(acc, nc, partials, ticket, d->h2)) {
+        const int i = nc - 1, m1 = d->m + 1;
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) d->H[(size_t)i * m1 + k] = hs[k] + d->h2[k];
+    }
+}
+
+// pass 3: w -= V h2; h_{i+1,i} = ||w||; Givens update; convergence test
+template <int NC>
+__global__ void __launch_bounds__(RS_RED_THREADS)
+k_cgs_update_norm(int n, int ld, int nc, const double *__restrict__ V, double *__restrict__ w,
+                  double *partials, unsigned *ticket, GmresDev *d)
+{
+    if (*(volatile int *)&d->cycle_done) return;
+    __shared__ double hs[NC];
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) hs[k] = d->h2[k];
+    __syncthreads();
+    double acc[1] = {0.0};
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            if (k < nc) s += V[(size_t)k * ld + r] * hs[k];
+        const double w2 = w[r] - s;
+        w[r] = w2;
+        acc[0] += w2 * w2;
+    }
+    if (reduce_partials<1>(acc, 1, partials, ticket, &d->r2)) {
+        if (threadIdx.x == 0) {
+            const int i = nc - 1, m1 = d->m + 1;
+            double *h = d->H + (size_t)i * m1;
+            const double hnext = sqrt(d->r2);
+            for (int k = 0; k < i; ++k) {
+                const double a = h[k], b = h[k + 1];
+                h[k] = d->cs[k] * a + d->sn[k] * b;
+                h[k + 1] = -d->sn[k] * a + d->cs[k] * b;
+            }
+            const double rho = hypot(h[i], hnext);
+            d->cs[i] = h[i] / rho;
+            d->sn[i] = hnext / rho;
+            h[i] = rho;
+            h[i + 1] = 0.0;
+            d->g[i + 1] = -d->sn[i] * d->g[i];
+            d->g[i] = d->cs[i] * d->g[i];
+            d->iters += 1;
+            d->k = i + 1;
+            d->implicit = fabs(d->g[i + 1]);
+            const bool happy = hnext <= 1e-14 * sqrt(d->w0sq);
+            if (d->implicit <= d->tol || d->iters >= d->maxit || happy || i == d->m - 1)
+                d->cycle_done = 1;
+            d->inv_h = 1.0 / hnext;
+        }
+    }
+}
+
+// x[r] (or u[r]) = sum_j B[j][r] y[j] for j < k; add = 1 accumulates into x
+__global__ void k_basis_combine(int n, int ld, const double *__restrict__ B, const GmresDev *d,
+                                double *__restrict__ x, int add)
+{
+    if (*(volatile const int *)&d->noupd) return;
+    __shared__ double ys[RS_MAX_RESTART];
+    const int k = d->k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = d->y[j];
+    __syncthreads();
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < k; ++j) s += B[(size_t)j * ld + r] * ys[j];
+        x[r] = add ? x[r] + s : s;
+    }
+}
+
+// v = s * r with s a device scalar
+__global__ void k_scale_dev(int n, const double *__restrict__ r, const double *__restrict__ s,
+                            double *__restrict__ v, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    const double a = *s;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = a * r[i];
+}
+
+__global__ void k_axpy_skip(int n, const double *__restrict__ x, double *__restrict__ y, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] += x[i];
+}
+
+// cycle start: beta = ||r||, convergence test on the true residual
+__global__ void k_gmres_start(GmresDev *d, const double *r2, double rtol, int first)
+{
+    if (threadIdx.x != 0) return;
+    const double beta = sqrt(*r2);
+    if (first) {
+        d->tol = rtol * d->bnorm;
+    }
+    d->beta = beta;
+    d->implicit = beta;
+    d->converged = beta <= d->tol;
+    d->cycle_done = d->converged || d->iters >= d->maxit;
+    d->g[0] = beta;
+    for (int j = 1; j <= d->m; ++j) d->g[j] = 0.0;
+    d->k = 0;
+    d->noupd = 1;
+    d->inv_h = 1.0 / beta;
+}
+
+// y = H(0:k,0:k)^{-1} g(0:k) by back-substitution
+__global__ void k_gmres_backsolve(GmresDev *d)
+{
+    if (threadIdx.x != 0) return;
+    const int k = d->k, m1 = d->m + 1;
+    for (int j = k - 1; j >= 0; --j) {
+        double s = d->g[j];
+        for (int l = j + 1; l < k; ++l) s -= d->H[(size_t)l * m1 + j] * d->y[l];
+        d->y[j] = s / d->H[(size_t)j * m1 + j];
+    }
+    d->noupd = k == 0;
+}
+
+static int red_grid(rs_ctx *ctx) { return ctx->red_blocks; }
+
+static int blas_grid(rs_ctx *ctx, int n)
+{
+    return std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8));
+}
+
+template <int NC>
+static void launch_cgs(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
+{
+    double *w = V + (size_t)nc * ld;
+    const int g = red_grid(ctx);
+    k_cgs_dots<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
+    k_cgs_update_dots<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
+    k_cgs_update_norm<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
+}
+
+static int cgs_step(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
+{
+    if (nc <= 8) launch_cgs<8>(ctx, n, ld, nc, V, d);
+    else if (nc <= 16) launch_cgs<16>(ctx, n, ld, nc, V, d);
+    else if (nc <= 32) launch_cgs<32>(ctx, n, ld, nc, V, d);
+    else launch_cgs<64>(ctx, n, ld, nc, V, d);
+    ctx->launches += 2;
+    return rs_check_launch(ctx);
+}
+
+static int finish_info(rs_ctx *ctx, const rs_mat *A, const double *b, const double *x, double *r,
+                       double bnorm, rs_solve_info *info)
+{
+    RS_TRY(rs_residual_launch(A, b, x, r, ctx->d_scalars + 1, nullptr));
+    RS_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_scalars + 1, sizeof(double),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    info->true_rel_res = bnorm > 0 ? sqrt(ctx->h_pinned[1]) / bnorm : 0.0;
+    return RS_OK;
+}
+
+static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, int m, double rtol,
+                      int maxit, int flexible, rs_solve_info *info)
+{
+    if (!A || !bv || !xv || !info) return RS_ERR_INVALID_ARG;
+    if (m < 1 || m > RS_MAX_RESTART || maxit < 0 || !(rtol >= 0)) return RS_ERR_INVALID_ARG;
+    if (bv->n != A->n || xv->n != A->n) return RS_ERR_SIZE_MISMATCH;
+    if (M && M->A->n != A->n) return RS_ERR_SIZE_MISMATCH;
+    memset(info, 0, sizeof(*info));
+    info->bad_row = -1;
+    rs_ctx *ctx = A->ctx;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int n = A->n;
+    const int ld = (n + 31) / 32 * 32;
+    double *V = nullptr, *Z = nullptr, *r = nullptr, *t = nullptr;
+    GmresDev *d = nullptr;
+    int st = rs_alloc(ctx, (void **)&V, sizeof(double) * (size_t)ld * (m + 1));
+    if (!st && flexible) st = rs_alloc(ctx, (void **)&Z, sizeof(double) * (size_t)ld * m);
+    if (!st) st = rs_alloc(ctx, (void **)&r, sizeof(double) * ld);
+    if (!st) st = rs_alloc(ctx, (void **)&t, sizeof(double) * ld);
+    if (!st) st = rs_alloc(ctx, (void **)&d, sizeof(GmresDev));
+    int status = RS_NOT_CONVERGED;
+    double bnorm = 0.0;
+    const double *b = bv->d;
+    double *x = xv->d;
+    if (st) goto out;
+    {
+        GmresDev h0;
+        memset(&h0, 0, sizeof(h0));
+        h0.m = m;
+        h0.maxit = maxit;
+        h0.noupd = 1;
+        // ||b||
+        st = rs_dot_launch(ctx, n, b, b, ctx->d_scalars);
+        if (st) goto out;
+        if (cudaMemcpyAsync(ctx->h_pinned, ctx->d_scalars, sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            st = RS_ERR_CUDA;
+            goto out;
+        }
+        bnorm = sqrt(ctx->h_pinned[0]);
+        if (bnorm == 0.0) {
+            cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream);
+            status = RS_OK;
+            goto done;
+        }
+        h0.bnorm = bnorm;
+        cudaMemcpyAsync(d, &h0, sizeof(h0), cudaMemcpyHostToDevice, ctx->stream);
+        const int gb = blas_grid(ctx, n);
+        int *cycle_done = &d->cycle_done;
+        int *noupd = &d->noupd;
+        int first = 1;
+        for (;;) {
+            // true residual and cycle start
+            st = rs_residual_launch(A, b, x, r, &d->r2, nullptr);
+            if (st) goto out;
+            k_gmres_start<<<1, 32, 0, ctx->stream>>>(d, &d->r2, rtol, first);
+            first = 0;
+            ctx->launches++;
+            int hs[4];
+            if (cudaMemcpyAsync(hs, &d->iters, sizeof(int) * 4, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+                cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+                st = RS_ERR_CUDA;
+                goto out;
+            }
+            // hs: iters, k, cycle_done, converged
+            info->iters = hs[0];
+            if (hs[3]) { status = RS_OK; break; }
+            if (hs[2]) { status = RS_NOT_CONVERGED; break; }
+            k_scale_dev<<<gb, 256, 0, ctx->stream>>>(n, r, &d->inv_h, V, nullptr);
+            ctx->launches++;
+            for (int i = 0; i < m; ++i) {
+                double *vi = V + (size_t)i * ld;
+                double *zi = flexible ? Z + (size_t)i * ld : t;
+                double *w = V + (size_t)(i + 1) * ld;
+                if (M) st = rs_pc_apply_dev(M, vi, zi, cycle_done);
+                else zi = vi;
+                if (!st) st = rs_spmv_launch(A, zi, 1.0, 0.0, w, cycle_done);
+                if (!st) st = cgs_step(ctx, n, ld, i + 1, V, d);
+                if (st) goto out;
+                if (i + 1 < m) {
+                    k_scale_dev<<<gb, 256, 0, ctx->stream>>>(n, w, &d->inv_h, w, cycle_done);
+                    ctx->launches++;
+                }
+            }
+            k_gmres_backsolve<<<1, 32, 0, ctx->stream>>>(d);
+            ctx->launches++;
+            if (flexible) {
+                k_basis_combine<<<gb, 256, 0, ctx->stream>>>(n, ld, Z, d, x, 1);
+                ctx->launches++;
+            } else {
+                k_basis_combine<<<gb, 256, 0, ctx->stream>>>(n, ld, V, d, r, 0);
+                ctx->launches++;
+                if (M) {
+                    st = rs_pc_apply_dev(M, r, t, noupd);
+                    if (st) goto out;
+                    k_axpy_skip<<<gb, 256, 0, ctx->stream>>>(n, t, x, noupd);
+                } else {
+                    k_axpy_skip<<<gb, 256, 0, ctx->stream>>>(n, r, x, noupd);
+                }
+                ctx->launches++;
+            }
+            info->restarts++;
+            if (cudaGetLastError() != cudaSuccess) { st = RS_ERR_CUDA; goto out; }
+        }
+        GmresDev hf;
+        cudaMemcpyAsync(&hf, d, sizeof(hf), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        info->iters = hf.iters;
+        info->implicit_rel_res = hf.implicit / bnorm;
+    }
+done:
+    st = rs_collect_device_error(ctx, &info->bad_row);
+    if (st) goto out;
+    st = finish_info(ctx, A, b, x, r ? r : t, bnorm, info);
+    if (st) goto out;
+    if (status == RS_OK && info->true_rel_res > rtol && bnorm > 0) status = RS_NOT_CONVERGED;
+out:
+    rs_free(ctx, V);
+    rs_free(ctx, Z);
+    rs_free(ctx, r);
+    rs_free(ctx, t);
+    rs_free(ctx, d);
+    info->status = st ? st : status;
+    info->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return info->status;
+}
+
+extern "C" int rs_solve_gmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_t restart,
+                              double rtol, int32_t maxit, rs_solve_info *info)
+{
+    return gmres_impl(A, M, b, x, restart, rtol, maxit, 0, info);
+}
+
+extern "C" int rs_solve_fgmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_t restart,
+                               double rtol, int32_t maxit, rs_solve_info *info)
+{
+    return gmres_impl(A, M, b, x, restart, rtol, maxit, 1, info);
+}
+
+// ---------------------------------------------------------------------------
+// BiCGSTAB
+// ---------------------------------------------------------------------------
+struct BicgDev {
+    double red[8];          // reduction outputs
+    double rho, rho0, alpha, omega, beta, tol, bnorm, implicit;
+    int iters, done, half, fresh, breakdown, maxit, status, pad;
+};
+
+// generic fused row kernel with up to 3 dot products and a scalar epilogue
+//  op 0: p = r + beta (p - omega v)                             (no dots)
+//  op 1: s = r - alpha v;  red = {||s||^2}                       -> half-step test
+//  op 2: x += alpha ph + omega sh; r = s - omega t; red = {(rh,r), ||r||^2}
+//  op 3: red = {(rh, v)}                                        -> alpha
+//  op 4: red = {(t, s), (t, t)}                                 -> omega
+//  op 5: x += alpha ph (half-step exit)
+__global__ void __launch_bounds__(RS_RED_THREADS)
+k_bicg(int op, int n, double *p, double *r, const double *__restrict__ v, double *s,
+       const double *__restrict__ t, double *x, const double *__restrict__ ph,
+       const double *__restrict__ sh, const double *__restrict__ rh, double *partials,
+       unsigned *ticket, BicgDev *d)
+{
+    if (op != 5 && (*(volatile int *)&d->done || *(volatile int *)&d->half)) return;
+    if (op == 5 && !*(volatile int *)&d->half) return;
+    const double alpha = d->alpha, omega = d->omega, beta = d->beta;
+    double acc[2] = {0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        switch (op) {
+        case 0: p[i] = r[i] + beta * (p[i] - omega * v[i]); break;
+        case 1: { const double si = r[i] - alpha * v[i]; s[i] = si; acc[0] += si * si; break; }
+        case 2: {
+            x[i] = x[i] + alpha * ph[i] + omega * sh[i];
+            const double ri = s[i] - omega * t[i];
+            r[i] = ri;
+            acc[0] += rh[i] * ri;
+            acc[1] += ri * ri;
+            break;
+        }
+        case 3: acc[0] += rh[i] * v[i]; break;
+        case 4: acc[0] += t[i] * s[i]; acc[1] += t[i] * t[i]; break;
+        case 5: x[i] = x[i] + alpha * ph[i]; break;
+        }
+    }
+    if (op == 0) return;
+    if (op == 5) {
+        // the half-step update runs once: the last block to finish clears the flag
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
+                d->half = 0;
+                *ticket = 0;
+                __threadfence();
+            }
+        }
+        return;
+    }
+    const int nv = (op == 2 || op == 4) ? 2 : 1;
+    if (!reduce_partials<2>(acc, nv, partials, ticket, d->red)) return;
+    if (threadIdx.x != 0) return;
+    switch (op) {
+    case 1: {
+        d->iters += 1;
+        const double sn = sqrt(d->red[0]);
+        if (sn <= d->tol) { d->half = 1; d->implicit = sn; d->done = 1; d->fresh = 1; }
+        break;
+    }
+    case 2: {
+        const double rho = d->red[0];
+        const double rn = sqrt(d->red[1]);
+        d->implicit = rn;
+        d->rho0 = d->rho;
+        if (rn <= d->tol) { d->done = 1; d->fresh = 1; break; }
+        if (!(d->omega != 0.0) || !isfinite(d->omega)) { d->breakdown = 1; d->done = 1; break; }
+        if (!(fabs(rho) > 0.0) || !isfinite(rho)) { d->breakdown = 1; d->done = 1; break; }
+        d->beta = (rho / d->rho0) * (d->alpha / d->omega);
+        d->rho = rho;
+        if (d->iters >= d->maxit) d->done = 1;
+        break;
+    }
+    case 3: {
+        const double rv = d->red[0];
+        if (!(fabs(rv) > 0.0) || !isfinite(rv)) { d->breakdown = 1; d->done = 1; break; }
+        d->alpha = d->rho / rv;
+        break;
+    }
+    case 4: {
+        const double ts = d->red[0], tt = d->red[1];
+        d->omega = tt > 0.0 ? ts / tt : 0.0;
+        break;
+    }
+    }
+}
+
+// restart from the true residual r = b - A x (already in r, ||r||^2 in red[1])
+__global__ void k_bicg_restart(int n, const double *__restrict__ r, double *rh, double *p, double *v,
+                               BicgDev *d)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        rh[i] = r[i];
+        p[i] = 0.0;
+        v[i] = 0.0;
+    }
+}
+
+__global__ void k_bicg_restart_scalars(BicgDev *d, const double *r2)
+{
+    if (threadIdx.x) return;
+    const double rn = sqrt(*r2);
+    d->implicit = rn;
+    d->fresh = 0;
+    d->half = 0;
+    d->done = 0;
+    if (rn <= d->tol) { d->done = 1; d->status = 1; return; }   // status 1: converged
+    if (d->iters >= d->maxit) { d->done = 1; return; }
+    // rho = (rh, r) = ||r||^2 with rh = r; beta multiplies p = 0, so its value is irrelevant
+    d->rho0 = 1.0;
+    d->alpha = 1.0;
+    d->omega = 1.0;
+    d->rho = *r2;
+    d->beta = 0.0;
+    if (!(d->rho > 0.0) || !isfinite(d->rho)) { d->breakdown = 1; d->done = 1; }
+}
+
+extern "C" int rs_solve_bicgstab(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, double rtol,
+                                 int32_t maxit, rs_solve_info *info)
+{
+    if (!A || !bv || !xv || !info) return RS_ERR_INVALID_ARG;
+    if (maxit < 0 || !(rtol >= 0)) return RS_ERR_INVALID_ARG;
+    if (bv->n != A->n || xv->n != A->n) return RS_ERR_SIZE_MISMATCH;
+    memset(info, 0, sizeof(*info));
+    info->bad_row = -1;
+    rs_ctx *ctx = A->ctx;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int n = A->n;
+    const int ld = (n + 31) / 32 * 32;
+    double *buf = nullptr;
+    BicgDev *d = nullptr;
+    int st = rs_alloc(ctx, (void **)&buf, sizeof(double) * (size_t)ld * 8);
+    if (!st) st = rs_alloc(ctx, (void **)&d, sizeof(BicgDev));
+    int status = RS_NOT_CONVERGED;
+    double bnorm = 0.0;
+    const double *b = bv->d;
+    double *x = xv->d;
+    double *r = buf, *rh = buf + ld, *p = buf + 2 * (size_t)ld, *v = buf + 3 * (size_t)ld;
+    double *s = buf + 4 * (size_t)ld, *t = buf + 5 * (size_t)ld, *ph = buf + 6 * (size_t)ld;
+    double *sh = buf + 7 * (size_t)ld;
+    if (!M) {            // no preconditioner: M^{-1} p = p, M^{-1} s = s
+        ph = p;
+        sh = s;
+    }
+    if (st) goto out;
+    {
+        st = rs_dot_launch(ctx, n, b, b, ctx->d_scalars);
+        if (st) goto out;
+        cudaMemcpyAsync(ctx->h_pinned, ctx->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { st = RS_ERR_CUDA; goto out; }
+        bnorm = sqrt(ctx->h_pinned[0]);
+        if (bnorm == 0.0) {
+            cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream);
+            status = RS_OK;
+            goto done;
+        }
+        BicgDev h0;
+        memset(&h0, 0, sizeof(h0));
+        h0.tol = rtol * bnorm;
+        h0.bnorm = bnorm;
+        h0.maxit = maxit;
+        cudaMemcpyAsync(d, &h0, sizeof(h0), cudaMemcpyHostToDevice, ctx->stream);
+        const int gr = red_grid(ctx), gb = blas_grid(ctx, n);
+        int *halt = &d->done;
+        const int batch = 8;
+        for (;;) {
+            // (re)start from the true residual
+            st = rs_residual_launch(A, b, x, r, &d->red[1], nullptr);
+            if (st) goto out;
+            k_bicg_restart<<<gb, 256, 0, ctx->stream>>>(n, r, rh, p, v, d);
+            k_bicg_restart_scalars<<<1, 32, 0, ctx->stream>>>(d, &d->red[1]);
+            ctx->launches += 2;
+            bool restart = false;
+            while (!restart) {
+                for (int it = 0; it < batch; ++it) {
+                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(0, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                   ctx->red_partials, ctx->red_ticket, d);
+                    ctx->launches++;
+                    if (M) st = rs_pc_apply_dev(M, p, ph, halt);
+                    if (st) goto out;
+                    st = rs_spmv_launch(A, ph, 1.0, 0.0, v, halt);
+                    if (st) goto out;
+                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(3, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                   ctx->red_partials, ctx->red_ticket, d);
+                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(1, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                   ctx->red_partials, ctx->red_ticket, d);
+                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(5, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                   ctx->red_partials, ctx->red_ticket, d);
+                    ctx->launches += 3;
+                    if (M) st = rs_pc_apply_dev(M, s, sh, halt);
+                    if (st) goto out;
+                    st = rs_spmv_launch(A, sh, 1.0, 0.0, t, halt);
+                    if (st) goto out;
+                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(4, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                   ctx->red_partials, ctx->red_ticket, d);
+                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(2, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                   ctx->red_partials, ctx->red_ticket, d);
+                    ctx->launches += 2;
+                }
+                BicgDev hd;
+                if (cudaMemcpyAsync(&hd, d, sizeof(hd), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+                    cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+                    st = RS_ERR_CUDA;
+                    goto out;
+                }
+                info->iters = hd.iters;
+                info->implicit_rel_res = hd.implicit / bnorm;
+                if (hd.status == 1) { status = RS_OK; goto done; }
+                if (hd.breakdown) { status = RS_ERR_BREAKDOWN; goto done; }
+                if (hd.fresh) { restart = true; break; }       // confirm with the true residual
+                if (hd.done || hd.iters >= maxit) { status = RS_NOT_CONVERGED; goto done; }
+            }
+        }
+    }
+done:
+    st = rs_collect_device_error(ctx, &info->bad_row);
+    if (st) goto out;
+    st = finish_info(ctx, A, b, x, r, bnorm, info);
+    if (st) goto out;
+    if (status == RS_OK && info->true_rel_res > rtol && bnorm > 0) status = RS_NOT_CONVERGED;
+    if (status == RS_NOT_CONVERGED && info->true_rel_res <= rtol && bnorm > 0) status = RS_OK;
+out:
+    rs_free(ctx, buf);
+    rs_free(ctx, d);
+    info->status = st ? st : status;
+    info->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return info->status;
+}

@@ -1,0 +1,266 @@
+// Preconditioner objects: setup / apply / destroy (Sec. 3, Fig. 29) for
+// ILU(0), block ILU(0) and the two-stage CPR preconditioner (Sec. 4.3).
+//
+// CPR, pressure stage first (Alg. 6, read as the standard two-stage form:
+//   z1 = Pi_p M_p^{-1} Pi_r f;   t = f - A z1;   z = z1 + R(A)^{-1} t),
+// where Pi_r is the quasi-IMPES-weighted restriction to the pressure
+// unknowns (Eqs. 5-7), Pi_p injects pressures with zero saturations (Eq. 8),
+// M_p is ILU(0) of the decoupled pressure matrix App' (or the learned
+// network) and R is block ILU(0) of the full matrix.  On a CSR matrix the
+// restriction is the identity and App' = A.
+#include <algorithm>
+
+#include "rs_internal.cuh"
+
+// quasi-IMPES weights w_Ik = -D_I[0][k] / D_I[k][k] (D_I the diagonal block)
+__global__ void k_qimpes_weights(int nb, int bs, const int *__restrict__ diagpos,
+                                 const double *__restrict__ val, double *__restrict__ w)
+{
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nb; I += gridDim.x * blockDim.x) {
+        const double *D = val + (size_t)diagpos[I] * bs * bs;
+        for (int k = 1; k < bs; ++k) w[(size_t)I * (bs - 1) + k - 1] = -D[k] / D[k * bs + k];
+    }
+}
+
+// App'_IJ = A_IJ[0][0] + sum_k w_Ik A_IJ[k][0]
+__global__ void k_qimpes_app(int nb, int bs, const int *__restrict__ ptr, const double *__restrict__ val,
+                             const double *__restrict__ w, double *__restrict__ app)
+{
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nb; I += gridDim.x * blockDim.x) {
+        for (int p = ptr[I]; p < ptr[I + 1]; ++p) {
+            const double *B = val + (size_t)p * bs * bs;
+            double s = B[0];
+            for (int k = 1; k < bs; ++k) s += w[(size_t)I * (bs - 1) + k - 1] * B[k * bs];
+            app[p] = s;
+        }
+    }
+}
+
+// rp_I = f_I0 + sum_k w_Ik f_Ik
+__global__ void k_qimpes_restrict(int nb, int bs, const double *__restrict__ w,
+                                  const double *__restrict__ f, double *__restrict__ rp,
+                                  const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nb; I += gridDim.x * blockDim.x) {
+        double s = f[(size_t)I * bs];
+        for (int k = 1; k < bs; ++k) s += w[(size_t)I * (bs - 1) + k - 1] * f[(size_t)I * bs + k];
+        rp[I] = s;
+    }
+}
+
+// z_I0 = p_I, z_Ik = 0 (Eq. 8)
+__global__ void k_prolong(int nb, int bs, const double *__restrict__ p, double *__restrict__ z,
+                          const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nb * bs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(t / bs), k = (int)(t % bs);
+        z[t] = k == 0 ? p[I] : 0.0;
+    }
+}
+
+__global__ void k_copy_add(int64_t n, const double *__restrict__ a, double *__restrict__ z,
+                           int add, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = add ? z[i] + a[i] : a[i];
+}
+
+static int grid_for(rs_ctx *ctx, int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8));
+}
+
+int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip)
+{
+    rs_ctx *ctx = M->ctx;
+    const rs_mat *A = M->A;
+    switch (M->type) {
+    case RS_PC_NONE:
+        k_copy_add<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(A->n, r, z, 0, skip);
+        return rs_check_launch(ctx);
+    case RS_PC_ILU0:
+        return rs_ilu_apply(M->ilu, r, z, nullptr, skip);
+    case RS_PC_BILU0:
+        return rs_ilu_apply(M->bilu, r, z, nullptr, skip);
+    case RS_PC_CPR:
+    case RS_PC_CPR_LEARNED: {
+        const int nb = A->nrows, bs = A->bs;
+        const double *rp = r;
+        if (bs > 1) {
+            k_qimpes_restrict<<<grid_for(ctx, nb), 256, 0, ctx->stream>>>(nb, bs, M->w, r, M->rp, skip);
+            RS_TRY(rs_check_launch(ctx));
+            rp = M->rp;
+        }
+        double *zp = bs > 1 ? M->zp : M->t2;
+        if (M->type == RS_PC_CPR_LEARNED) RS_TRY(rs_net_apply_pressure(M, rp, zp, skip));
+        else RS_TRY(rs_ilu_apply(M->ilu, rp, zp, nullptr, skip));
+        if (bs > 1) {
+            k_prolong<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(nb, bs, M->zp, M->t2, skip);
+            RS_TRY(rs_check_launch(ctx));
+        }
+        // t1 = f - A z1
+        RS_TRY(rs_residual_launch(A, r, M->t2, M->t1, nullptr, skip));
+        // z = z1 + R^{-1} t1
+        RS_TRY(rs_ilu_apply(M->bilu, M->t1, z, nullptr, skip));
+        k_copy_add<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(A->n, M->t2, z, 1, skip);
+        return rs_check_launch(ctx);
+    }
+    default:
+        return RS_ERR_INVALID_ARG;
+    }
+}
+
+static void pc_free(rs_pc *M)
+{
+    if (!M) return;
+    rs_ctx *ctx = M->ctx;
+    if (M->ilu && M->ilu != M->bilu) rs_ilu_destroy(M->ilu);
+    if (M->bilu) rs_ilu_destroy(M->bilu);
+    rs_free(ctx, M->app_val);
+    rs_free(ctx, M->w);
+    rs_free(ctx, M->rp);
+    rs_free(ctx, M->zp);
+    rs_free(ctx, M->t1);
+    rs_free(ctx, M->t2);
+    delete M;
+}
+
+extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs_pc_opts *opts,
+                                rs_pc **out)
+{
+    if (!ctx || !A || !out) return RS_ERR_INVALID_ARG;
+    *out = nullptr;
+    rs_pc *M = new rs_pc();
+    M->ctx = ctx;
+    M->type = type;
+    M->prec = opts ? opts->prec : RS_FP64;
+    M->A = A;
+    M->bad_row = -1;
+    const int fp32 = M->prec == RS_MIXED;
+    int st = RS_OK;
+    int bad = -1;
+    switch (type) {
+    case RS_PC_NONE:
+        break;
+    case RS_PC_ILU0:
+        if (A->bs != 1) { st = RS_ERR_INVALID_ARG; break; }
+        st = rs_ilu_create(ctx, 1, A->nrows, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
+        if (!st) st = rs_ilu_factor(M->ilu, A->val, &bad);
+        break;
+    case RS_PC_BILU0:
+        st = rs_ilu_create(ctx, A->bs, A->nrows, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
+        if (!st) st = rs_ilu_factor(M->bilu, A->val, &bad);
+        break;
+    case RS_PC_CPR:
+    case RS_PC_CPR_LEARNED: {
+        const int nb = A->nrows, bs = A->bs;
+        if (type == RS_PC_CPR_LEARNED) {
+            if (!opts || !opts->net || !opts->log_perm || (int64_t)opts->nx * opts->ny * opts->nz != nb) {
+                st = RS_ERR_INVALID_ARG;
+                break;
+            }
+            M->net = opts->net;
+            M->log_perm = opts->log_perm;
+            M->nx = opts->nx;
+            M->ny = opts->ny;
+            M->nz = opts->nz;
+        }
+        st = rs_ilu_create(ctx, bs, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
+        if (!st) st = rs_ilu_factor(M->bilu, A->val, &bad);
+        if (st) break;
+        st = rs_alloc(ctx, (void **)&M->t1, sizeof(double) * (A->n > 0 ? A->n : 1));
+        if (!st) st = rs_alloc(ctx, (void **)&M->t2, sizeof(double) * (A->n > 0 ? A->n : 1));
+        if (st) break;
+        if (bs == 1) {
+            M->ilu = M->bilu;     // pressure stage = ILU(0) of A itself
+            break;
+        }
+        st = rs_alloc(ctx, (void **)&M->w, sizeof(double) * (size_t)nb * (bs - 1));
+        if (!st) st = rs_alloc(ctx, (void **)&M->app_val, sizeof(double) * (A->nnzb > 0 ? A->nnzb : 1));
+        if (!st) st = rs_alloc(ctx, (void **)&M->rp, sizeof(double) * (nb > 0 ? nb : 1));
+        if (!st) st = rs_alloc(ctx, (void **)&M->zp, sizeof(double) * (nb > 0 ? nb : 1));
+        if (st) break;
+        if (nb > 0) {
+            k_qimpes_weights<<<grid_for(ctx, nb), 256, 0, ctx->stream>>>(nb, bs, M->bilu->diagpos, A->val, M->w);
+            k_qimpes_app<<<grid_for(ctx, nb), 256, 0, ctx->stream>>>(nb, bs, A->ptr, A->val, M->w, M->app_val);
+            st = rs_check_launch(ctx);
+            ctx->launches++;
+        }
+        if (!st) st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
+        if (!st) st = rs_ilu_factor(M->ilu, M->app_val, &bad);
+        break;
+    }
+    default:
+        st = RS_ERR_INVALID_ARG;
+    }
+    M->bad_row = bad;
+    if (st == RS_ERR_ZERO_PIVOT) {
+        *out = M;          // keep the handle so the caller can query the row
+        return st;
+    }
+    if (st) {
+        pc_free(M);
+        return st;
+    }
+    *out = M;
+    return RS_OK;
+}
+
+extern "C" int rs_precond_apply(rs_pc *M, const rs_vec *r, rs_vec *z)
+{
+    if (!M || !r || !z) return RS_ERR_INVALID_ARG;
+    if (r->n != M->A->n || z->n != M->A->n) return RS_ERR_SIZE_MISMATCH;
+    RS_TRY(rs_pc_apply_dev(M, r->d, z->d, nullptr));
+    return RS_OK;
+}
+
+extern "C" int rs_precond_get_ilu(const rs_pc *M, double *lu_host, int32_t nnz)
+{
+    if (!M || !M->ilu || !lu_host) return RS_ERR_INVALID_ARG;
+    if (nnz != M->ilu->nnzb) return RS_ERR_SIZE_MISMATCH;
+    RS_CUDA_TRY(cudaMemcpyAsync(lu_host, M->ilu->lu, sizeof(double) * nnz, cudaMemcpyDeviceToHost,
+                                M->ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(M->ctx->stream));
+    return RS_OK;
+}
+
+extern "C" int rs_precond_get_bilu(const rs_pc *M, double *lu_host, double *dinv_host)
+{
+    if (!M || !M->bilu || !lu_host || !dinv_host) return RS_ERR_INVALID_ARG;
+    const size_t b2 = (size_t)M->bilu->bs * M->bilu->bs;
+    RS_CUDA_TRY(cudaMemcpyAsync(lu_host, M->bilu->lu, sizeof(double) * b2 * M->bilu->nnzb,
+                                cudaMemcpyDeviceToHost, M->ctx->stream));
+    RS_CUDA_TRY(cudaMemcpyAsync(dinv_host, M->bilu->dinv, sizeof(double) * b2 * M->bilu->nrows,
+                                cudaMemcpyDeviceToHost, M->ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(M->ctx->stream));
+    return RS_OK;
+}
+
+extern "C" int rs_precond_get_cpr(const rs_pc *M, double *w_host, double *app_host)
+{
+    if (!M || !M->w || !M->app_val) return RS_ERR_INVALID_ARG;
+    const rs_mat *A = M->A;
+    if (w_host)
+        RS_CUDA_TRY(cudaMemcpyAsync(w_host, M->w, sizeof(double) * (size_t)A->nrows * (A->bs - 1),
+                                    cudaMemcpyDeviceToHost, M->ctx->stream));
+    if (app_host)
+        RS_CUDA_TRY(cudaMemcpyAsync(app_host, M->app_val, sizeof(double) * A->nnzb,
+                                    cudaMemcpyDeviceToHost, M->ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(M->ctx->stream));
+    return RS_OK;
+}
+
+extern "C" int32_t rs_precond_bad_row(const rs_pc *M) { return M ? M->bad_row : -1; }
+
+extern "C" int rs_precond_destroy(rs_pc **M)
+{
+    if (!M || !*M) return RS_OK;
+    pc_free(*M);
+    *M = nullptr;
+    return RS_OK;
+}

@@ -1,0 +1,342 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (floating point): SpMV <= 1e-12 relative, ILU(0) factors <= 1e-10
+relative, final true relative residual <= 1e-8, solution <= 1e-6 relative to
+the oracle's, FP64 iteration counts within +-2.  Integer-valued SpMV must
+match bit for bit.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(rs):
+    return rs.Context(0)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def vec(rs, ctx, x):
+    return rs.Vec(ctx, x)
+
+
+def csr_random_int(n, rng, density=0.2):
+    import scipy.sparse as sp
+    D = rng.integers(-5, 6, size=(n, n)).astype(float)
+    D[rng.random((n, n)) > density] = 0.0
+    np.fill_diagonal(D, rng.integers(10, 20, size=n))
+    A = sp.csr_matrix(D)
+    A.sort_indices()
+    return dict(n=n, rowptr=A.indptr.astype(np.int32), col=A.indices.astype(np.int32),
+                val=A.data.astype(np.float64))
+
+
+# ----------------------------------------------------------------------------
+# SpMV and BLAS-1
+# ----------------------------------------------------------------------------
+def test_spmv_integer_bit_exact(rs, ctx, orc):
+    rng = np.random.default_rng(0)
+    for n in (1, 37, 300):
+        d = csr_random_int(n, rng, density=0.1 if n > 50 else 0.5)
+        A = rs.Mat.csr(ctx, d)
+        x = rng.integers(-9, 10, size=n).astype(float)
+        y = rs.Vec.zeros(ctx, n)
+        A.spmv(vec(rs, ctx, x), y)
+        assert np.array_equal(y.numpy(), orc.spmv(orc.Mat.csr(d), x))
+        y0 = rng.integers(-9, 10, size=n).astype(float)
+        yv = vec(rs, ctx, y0)
+        A.amxpby(-2.0, vec(rs, ctx, x), 3.0, yv)
+        assert np.array_equal(yv.numpy(), orc.amxpby(-2.0, orc.Mat.csr(d), x, 3.0, y0))
+
+
+def test_bsr_spmv_integer_bit_exact(rs, ctx, orc):
+    g = synth.Grid(7, 5, 3)
+    m = synth.black_oil_bsr3(g, 2)
+    rng = np.random.default_rng(1)
+    m["bval"] = rng.integers(-5, 6, size=m["bval"].size).astype(float)
+    A = rs.Mat.bsr(ctx, m)
+    x = rng.integers(-9, 10, size=g.n * 3).astype(float)
+    y = rs.Vec.zeros(ctx, g.n * 3)
+    A.spmv(vec(rs, ctx, x), y)
+    assert np.array_equal(y.numpy(), orc.spmv(orc.Mat.bsr(m), x))
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 17), (32, 32, 32)])
+def test_spmv_fp64_7pt(rs, ctx, orc, shape):
+    g = synth.Grid(*shape)
+    d = synth.pressure_7pt(g, 3, kz_scale=0.1)
+    A = rs.Mat.csr(ctx, d)
+    x = synth.x_true(g.n, 3)
+    y = rs.Vec.zeros(ctx, g.n)
+    A.spmv(vec(rs, ctx, x), y)
+    ref = orc.spmv(orc.Mat.csr(d), x)
+    assert np.max(np.abs(y.numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_blas1(rs, ctx, orc):
+    rng = np.random.default_rng(4)
+    for n in (0, 1, 33, 100003):
+        x, y = rng.standard_normal(n), rng.standard_normal(n)
+        xv, yv, zv = vec(rs, ctx, x), vec(rs, ctx, y), rs.Vec.zeros(ctx, n)
+        assert abs(rs.vec_dot(xv, yv) - orc.dot(x, y)) <= 1e-12 * max(1.0, abs(orc.dot(np.abs(x), np.abs(y))))
+        assert abs(rs.vec_norm2(xv) - orc.norm2(x)) <= 1e-13 * max(orc.norm2(x), 1e-300)
+        rs.vec_axpbyz(0.5, xv, -2.0, yv, zv)
+        assert np.allclose(zv.numpy(), orc.axpbyz(0.5, x, -2.0, y), rtol=1e-15, atol=0)
+        rs.vec_axpby(1.5, xv, 0.25, yv)
+        assert np.allclose(yv.numpy(), orc.axpby(1.5, x, 0.25, y), rtol=1e-15, atol=0)
+        rs.vec_set_value(xv, 2.5)
+        assert np.array_equal(xv.numpy(), orc.set_value(n, 2.5))
+    # dot of 1..n is exact in FP64 for this n: closed form
+    n = 1000
+    v = vec(rs, ctx, np.arange(1, n + 1, dtype=float))
+    assert rs.vec_dot(v, v) == n * (n + 1) * (2 * n + 1) / 6
+
+
+# ----------------------------------------------------------------------------
+# ILU(0) / block ILU(0) / CPR
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(5, 4, 3), (24, 20, 17), (32, 32, 32)])
+def test_ilu0_factors_and_apply(rs, ctx, orc, shape):
+    g = synth.Grid(*shape)
+    d = synth.pressure_7pt(g, 5, kz_scale=0.1)
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "ilu0")
+    lu = M.ilu_factors(d["col"].size)
+    Ao = orc.Mat.csr(d)
+    st, _, lu_ref = orc.ilu0(Ao)
+    assert st == 0
+    assert np.max(np.abs(lu - lu_ref) / np.maximum(np.abs(lu_ref), 1e-300)) <= 1e-10
+    r = np.random.default_rng(6).standard_normal(g.n)
+    z = rs.Vec.zeros(ctx, g.n)
+    M.apply(vec(rs, ctx, r), z)
+    assert rel(z.numpy(), orc.ilu0_solve(Ao, lu_ref, r)) <= 1e-12
+    # repeated applies reuse the self-cleaning sweep state
+    z2 = rs.Vec.zeros(ctx, g.n)
+    for _ in range(3):
+        M.apply(vec(rs, ctx, r), z2)
+    assert np.array_equal(z.numpy(), z2.numpy())
+    Mm = rs.Precond(ctx, A, "ilu0", prec="mixed")
+    M.apply(vec(rs, ctx, r), z)
+    Mm.apply(vec(rs, ctx, r), z2)
+    zr32 = orc.ilu0_solve(Ao, lu_ref, r, fp32=True)
+    assert rel(z2.numpy(), zr32) <= 1e-5
+    assert rel(z2.numpy(), z.numpy()) <= 1e-5
+
+
+def test_ilu0_zero_pivot(rs, ctx):
+    d = dict(n=3, rowptr=np.array([0, 2, 5, 7], np.int32), col=np.array([0, 1, 0, 1, 2, 1, 2], np.int32),
+             val=np.array([1.0, 2.0, 0.5, 1.0, 1.0, 1.0, 3.0]))
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "ilu0")
+    assert M.status == rs.ERR_ZERO_PIVOT and M.bad_row == 1
+
+
+def test_bad_pattern_rejected(rs, ctx):
+    d = dict(n=2, rowptr=np.array([0, 2, 3], np.int32), col=np.array([1, 0, 1], np.int32),
+             val=np.ones(3))
+    with pytest.raises(rs.RsError) as e:
+        rs.Mat.csr(ctx, d)
+    assert e.value.status == rs.ERR_BAD_PATTERN
+    d = dict(n=2, rowptr=np.array([0, 1, 2], np.int32), col=np.array([1, 1], np.int32), val=np.ones(2))
+    with pytest.raises(rs.RsError):
+        rs.Mat.csr(ctx, d)
+
+
+@pytest.mark.parametrize("shape", [(4, 3, 3), (13, 11, 7)])
+def test_bilu0_factors_and_apply(rs, ctx, orc, shape):
+    g = synth.Grid(*shape)
+    m = synth.black_oil_bsr3(g, 8)
+    A = rs.Mat.bsr(ctx, m)
+    Ao = orc.Mat.bsr(m)
+    st, _, lu_ref, dinv_ref = orc.bilu0(Ao)
+    assert st == 0
+    for prec in ("fp64", "mixed"):
+        M = rs.Precond(ctx, A, "bilu0", prec=prec)
+        lu, dinv = M.bilu_factors()
+        assert rel(lu, lu_ref) <= 1e-12 and rel(dinv, dinv_ref) <= 1e-12
+        r = np.random.default_rng(9).standard_normal(A.n)
+        z = rs.Vec.zeros(ctx, A.n)
+        M.apply(vec(rs, ctx, r), z)
+        ref = orc.bilu0_solve(Ao, lu_ref, dinv_ref, r, fp32=(prec == "mixed"))
+        assert rel(z.numpy(), ref) <= (1e-12 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cpr_apply(rs, ctx, orc, prec):
+    g = synth.Grid(10, 9, 6)
+    m = synth.black_oil_bsr3(g, 12)
+    A = rs.Mat.bsr(ctx, m)
+    Ao = orc.Mat.bsr(m)
+    M = rs.Precond(ctx, A, "cpr", prec=prec)
+    Mo = orc.PC(Ao, "cpr", mixed=(prec == "mixed"))
+    w, app = M.cpr_data()
+    assert rel(w, Mo.w) <= 1e-14 and rel(app, Mo.app_val) <= 1e-14
+    f = np.random.default_rng(13).standard_normal(A.n)
+    z = rs.Vec.zeros(ctx, A.n)
+    M.apply(vec(rs, ctx, f), z)
+    assert rel(z.numpy(), Mo.apply(f)) <= (1e-12 if prec == "fp64" else 1e-5)
+
+
+def test_cpr_scalar_matrix(rs, ctx, orc):
+    d = synth.pressure_7pt(synth.Grid(12, 10, 9), 14)
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "cpr")
+    Mo = orc.PC(orc.Mat.csr(d), "cpr")
+    f = np.random.default_rng(15).standard_normal(d["n"])
+    z = rs.Vec.zeros(ctx, d["n"])
+    M.apply(vec(rs, ctx, f), z)
+    assert rel(z.numpy(), Mo.apply(f)) <= 1e-12
+
+
+# ----------------------------------------------------------------------------
+# Krylov solvers
+# ----------------------------------------------------------------------------
+def _problem(shape, seed, kz=1.0):
+    g = synth.Grid(*shape)
+    d = synth.pressure_7pt(g, seed, kz_scale=kz)
+    return g, d
+
+
+@pytest.mark.parametrize("solver", ["gmres", "fgmres", "bicgstab"])
+@pytest.mark.parametrize("shape,kz", [((32, 32, 32), 1.0), ((20, 17, 9), 0.1)])
+def test_krylov_ilu0_fp64_parity(rs, ctx, orc, solver, shape, kz):
+    g, d = _problem(shape, 1, kz)
+    Ao = orc.Mat.csr(d)
+    xt = synth.x_true(g.n, 1)
+    b = orc.spmv(Ao, xt)
+    Mo = orc.PC(Ao, "ilu0")
+    if solver == "bicgstab":
+        xo, io, _ = orc.bicgstab(Ao, Mo, b, rtol=1e-8)
+    else:
+        xo, io, _ = orc.gmres(Ao, Mo, b, restart=30, rtol=1e-8, flexible=(solver == "fgmres"))
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "ilu0")
+    x = rs.Vec.zeros(ctx, g.n)
+    fn = dict(gmres=rs.solve_gmres, fgmres=rs.solve_fgmres, bicgstab=rs.solve_bicgstab)[solver]
+    kw = dict(rtol=1e-8, maxit=10000) if solver == "bicgstab" else dict(restart=30, rtol=1e-8, maxit=10000)
+    info = fn(A, M, vec(rs, ctx, b), x, **kw)
+    xs = x.numpy()
+    true = orc.norm2(b - orc.spmv(Ao, xs)) / orc.norm2(b)
+    assert info["status"] == 0 and io["status"] == 0
+    assert true <= 1e-8 and abs(info["true_rel_res"] - true) <= 1e-12
+    assert abs(info["iters"] - io["iters"]) <= 2, (info, io)
+    assert rel(xs, xo) <= 1e-6
+
+
+def test_gmres_mixed_precision_error_vs_oracle(rs, ctx, orc):
+    g, d = _problem((24, 24, 16), 2, 0.1)
+    Ao = orc.Mat.csr(d)
+    b = orc.spmv(Ao, synth.x_true(g.n, 2))
+    xo, io, _ = orc.gmres(Ao, orc.PC(Ao, "ilu0"), b)
+    A = rs.Mat.csr(ctx, d)
+    for solver in (rs.solve_gmres, rs.solve_bicgstab):
+        x = rs.Vec.zeros(ctx, g.n)
+        info = solver(A, rs.Precond(ctx, A, "ilu0", prec="mixed"), vec(rs, ctx, b), x)
+        xs = x.numpy()
+        assert info["status"] == 0
+        assert orc.norm2(b - orc.spmv(Ao, xs)) / orc.norm2(b) <= 1e-8
+        assert rel(xs, xo) <= 1e-5
+
+
+def test_unpreconditioned_and_edge_cases(rs, ctx, orc):
+    g, d = _problem((8, 7, 6), 3)
+    Ao = orc.Mat.csr(d)
+    b = orc.spmv(Ao, synth.x_true(g.n, 3))
+    A = rs.Mat.csr(ctx, d)
+    xo, io, _ = orc.gmres(Ao, None, b, restart=20, rtol=1e-10)
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_gmres(A, None, vec(rs, ctx, b), x, restart=20, rtol=1e-10)
+    assert info["status"] == 0 and abs(info["iters"] - io["iters"]) <= 2
+    xo, io, _ = orc.bicgstab(Ao, None, b, rtol=1e-10)
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_bicgstab(A, None, vec(rs, ctx, b), x, rtol=1e-10)
+    assert info["status"] == 0 and abs(info["iters"] - io["iters"]) <= 2
+    # b = 0 gives x = 0 at once
+    x = vec(rs, ctx, np.ones(g.n))
+    info = rs.solve_gmres(A, None, vec(rs, ctx, np.zeros(g.n)), x)
+    assert info["status"] == 0 and info["iters"] == 0 and (x.numpy() == 0).all()
+    # maxit reached
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_gmres(A, None, vec(rs, ctx, b), x, maxit=5)
+    assert info["status"] == rs.NOT_CONVERGED and info["iters"] == 5
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_bicgstab(A, None, vec(rs, ctx, b), x, maxit=3)
+    assert info["status"] == rs.NOT_CONVERGED and info["iters"] == 3
+    # exact initial guess
+    x = vec(rs, ctx, synth.x_true(g.n, 3))
+    info = rs.solve_gmres(A, None, vec(rs, ctx, b), x)
+    assert info["status"] == 0 and info["iters"] == 0
+
+
+def test_poisson_eigenvector_one_step(rs, ctx):
+    import scipy.sparse as sp
+    n = 50
+    P = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1], format="csr")
+    P.sort_indices()
+    d = dict(n=n, rowptr=P.indptr.astype(np.int32), col=P.indices.astype(np.int32), val=P.data)
+    A = rs.Mat.csr(ctx, d)
+    j = np.arange(1, n + 1)
+    v = np.sin(3 * np.pi * j / (n + 1))
+    lam = 2 - 2 * np.cos(3 * np.pi / (n + 1))
+    for fn in (rs.solve_gmres, rs.solve_bicgstab):
+        x = rs.Vec.zeros(ctx, n)
+        info = fn(A, None, vec(rs, ctx, v), x, rtol=1e-12)
+        assert info["iters"] == 1
+        assert np.allclose(x.numpy(), v / lam, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fgmres_cpr_bsr(rs, ctx, orc, prec):
+    g = synth.Grid(16, 12, 8)
+    m = synth.black_oil_bsr3(g, 21)
+    Ao = orc.Mat.bsr(m)
+    b = orc.spmv(Ao, synth.x_true(Ao.n, 21))
+    xo, io, _ = orc.fgmres(Ao, orc.PC(Ao, "cpr", mixed=(prec == "mixed")), b, restart=30, rtol=1e-8)
+    A = rs.Mat.bsr(ctx, m)
+    M = rs.Precond(ctx, A, "cpr", prec=prec)
+    x = rs.Vec.zeros(ctx, A.n)
+    info = rs.solve_fgmres(A, M, vec(rs, ctx, b), x, restart=30, rtol=1e-8)
+    xs = x.numpy()
+    assert info["status"] == 0 and io["status"] == 0
+    assert orc.norm2(b - orc.spmv(Ao, xs)) / orc.norm2(b) <= 1e-8
+    assert abs(info["iters"] - io["iters"]) <= 2
+    assert rel(xs, xo) <= 1e-6
+
+
+# ----------------------------------------------------------------------------
+# full size (128 x 128 x 64, the benchmarked configuration): sampled rows and
+# properties that hold at any size
+# ----------------------------------------------------------------------------
+@pytest.mark.slow
+def test_full_size_spmv_sampled_and_solve(rs, ctx, orc):
+    g = synth.Grid(128, 128, 64)
+    d = synth.pressure_7pt(g, 1, kz_scale=0.1)
+    Ao = orc.Mat.csr(d)
+    xt = synth.x_true(g.n, 1)
+    b = orc.spmv(Ao, xt)
+    A = rs.Mat.csr(ctx, d)
+    y = rs.Vec.zeros(ctx, g.n)
+    A.spmv(vec(rs, ctx, xt), y)
+    ys = y.numpy()
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([[0, g.n - 1], rng.integers(0, g.n, 4000)])
+    for i in rows:
+        s, e = d["rowptr"][i], d["rowptr"][i + 1]
+        ref = sum(d["val"][p] * xt[d["col"][p]] for p in range(s, e))
+        assert abs(ys[i] - ref) <= 1e-12 * max(abs(ref), np.abs(d["val"][s:e]).sum())
+    for prec in ("fp64", "mixed"):
+        M = rs.Precond(ctx, A, "ilu0", prec=prec)
+        for fn in (rs.solve_gmres, rs.solve_bicgstab):
+            x = rs.Vec.zeros(ctx, g.n)
+            info = fn(A, M, vec(rs, ctx, b), x)
+            xs = x.numpy()
+            true = orc.norm2(b - orc.spmv(Ao, xs)) / orc.norm2(b)
+            assert info["status"] == 0 and true <= 1e-8, (prec, fn.__name__, info)
+            assert rel(xs, xt) <= 1e-3
