@@ -6,6 +6,7 @@
 // dot products are deterministic two-level tree reductions on the device.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -85,6 +86,11 @@ extern "C" int rs_init(rs_ctx **out, int device, void *stream)
     int clock_khz = 2000000;
     cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, device);
     c->spin_limit = (long long)clock_khz * 1000LL * 2;   // about two seconds
+    c->sweep_blocks = 4 * c->num_sms;
+    if (const char *e = getenv("RS_SWEEP_BLOCKS_PER_SM")) {
+        const int v = atoi(e);
+        if (v >= 1 && v <= 16) c->sweep_blocks = v * c->num_sms;
+    }
     // the stream-ordered pool keeps freed blocks for reuse
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -170,14 +176,14 @@ __global__ void k_set(int n, double a, double *x)
 __global__ void k_axpby(int n, double a, const double *__restrict__ x, double b, double *y)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        y[i] = b == 0.0 ? a * x[i] : a * x[i] + b * y[i];
+        y[i] = b == 0.0 ? __dmul_rn(a, x[i]) : __dadd_rn(__dmul_rn(a, x[i]), __dmul_rn(b, y[i]));
 }
 
 __global__ void k_axpbyz(int n, double a, const double *__restrict__ x, double b,
                          const double *__restrict__ y, double *__restrict__ z)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        z[i] = a * x[i] + b * y[i];
+        z[i] = __dadd_rn(__dmul_rn(a, x[i]), __dmul_rn(b, y[i]));
 }
 
 // Two-level deterministic dot product: fixed grid, per-block partial sums,
@@ -373,14 +379,58 @@ k_spmv_csr(int n, const int *__restrict__ ptr, const int *__restrict__ col,
     double acc = 0.0;
     if (active) {
         const int s = ptr[row], e = ptr[row + 1];
-        for (int p = s + lane; p < e; p += L) acc += val[p] * __ldg(x + col[p]);
+        for (int p = s + lane; p < e; p += L) acc = __dadd_rn(acc, __dmul_rn(val[p], __ldg(x + col[p])));
     }
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
     if (active && lane == 0) {
-        if (bvec) y[row] = bvec[row] - acc;
-        else if (beta == 0.0) y[row] = alpha * acc;
-        else y[row] = alpha * acc + beta * y[row];
+        if (bvec) y[row] = __dsub_rn(bvec[row], acc);
+        else if (beta == 0.0) y[row] = __dmul_rn(alpha, acc);
+        else y[row] = __dadd_rn(__dmul_rn(alpha, acc), __dmul_rn(beta, y[row]));
+    }
+}
+
+// CSR, short rows: each block stages the values and column indices of its
+// 256 consecutive rows in shared memory with coalesced loads (one 8-byte
+// and one 4-byte stream), then each thread forms one row from shared memory.
+// Blocks whose rows hold more than RS_SPMV_STAGE nonzeros read their rows
+// straight from global memory.
+#define RS_SPMV_ROWS 256
+#define RS_SPMV_STAGE 2560
+__global__ void __launch_bounds__(RS_SPMV_ROWS)
+k_spmv_csr_stream(int n, const int *__restrict__ ptr, const int *__restrict__ col,
+                  const double *__restrict__ val, const double *__restrict__ x, double alpha,
+                  double beta, const double *__restrict__ bvec, double *__restrict__ y,
+                  const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    __shared__ double sval[RS_SPMV_STAGE];
+    __shared__ int scol[RS_SPMV_STAGE];
+    const int row0 = blockIdx.x * RS_SPMV_ROWS;
+    const int nrow = min(RS_SPMV_ROWS, n - row0);
+    const int s = ptr[row0], e = ptr[row0 + nrow];
+    const int cnt = e - s;
+    const int r = row0 + threadIdx.x;
+    const bool active = threadIdx.x < nrow;
+    int a = 0, b = 0;
+    if (active) { a = ptr[r]; b = ptr[r + 1]; }
+    double acc = 0.0;
+    if (cnt <= RS_SPMV_STAGE) {
+#pragma unroll 4
+        for (int k = threadIdx.x; k < cnt; k += RS_SPMV_ROWS) {
+            sval[k] = val[s + k];
+            scol[k] = col[s + k];
+        }
+        __syncthreads();
+        if (active)
+            for (int p = a - s; p < b - s; ++p) acc = __dadd_rn(acc, __dmul_rn(sval[p], __ldg(x + scol[p])));
+    } else if (active) {
+        for (int p = a; p < b; ++p) acc = __dadd_rn(acc, __dmul_rn(val[p], __ldg(x + col[p])));
+    }
+    if (active) {
+        if (bvec) y[r] = __dsub_rn(bvec[r], acc);
+        else if (beta == 0.0) y[r] = __dmul_rn(alpha, acc);
+        else y[r] = __dadd_rn(__dmul_rn(alpha, acc), __dmul_rn(beta, y[r]));
     }
 }
 
@@ -402,14 +452,14 @@ k_spmv_bsr(int nb, int bsr, const int *__restrict__ ptr, const int *__restrict__
         const double *xs = x + (size_t)col[p] * bs;
         if (BS > 0) {
 #pragma unroll
-            for (int c = 0; c < (BS > 0 ? BS : 1); ++c) acc += blk[c] * __ldg(xs + c);
+            for (int c = 0; c < (BS > 0 ? BS : 1); ++c) acc = __dadd_rn(acc, __dmul_rn(blk[c], __ldg(xs + c)));
         } else {
-            for (int c = 0; c < bs; ++c) acc += blk[c] * __ldg(xs + c);
+            for (int c = 0; c < bs; ++c) acc = __dadd_rn(acc, __dmul_rn(blk[c], __ldg(xs + c)));
         }
     }
-    if (bvec) y[t] = bvec[t] - acc;
-    else if (beta == 0.0) y[t] = alpha * acc;
-    else y[t] = alpha * acc + beta * y[t];
+    if (bvec) y[t] = __dsub_rn(bvec[t], acc);
+    else if (beta == 0.0) y[t] = __dmul_rn(alpha, acc);
+    else y[t] = __dadd_rn(__dmul_rn(alpha, acc), __dmul_rn(beta, y[t]));
 }
 
 static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double beta,
@@ -417,7 +467,11 @@ static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double 
 {
     rs_ctx *ctx = A->ctx;
     if (A->n == 0) return RS_OK;
-    if (A->bs == 1) {
+    if (A->bs == 1 && A->lanes <= 8) {
+        const int grid = (A->n + RS_SPMV_ROWS - 1) / RS_SPMV_ROWS;
+        k_spmv_csr_stream<<<grid, RS_SPMV_ROWS, 0, ctx->stream>>>(A->n, A->ptr, A->col, A->val, x, alpha,
+                                                                   beta, bvec, y, skip);
+    } else if (A->bs == 1) {
         const int L = A->lanes;
         const int64_t threads = (int64_t)A->n * L;
         const int grid = (int)((threads + 255) / 256);

@@ -102,12 +102,22 @@ static int build_layout(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     T.nslices = nslices;
     T.nlevels = nlev;
     T.nent = nent;
+    T.nwarps = nslices;
+    std::vector<int> wlev(nslices), lnw(nlev > 0 ? nlev : 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+        lnw[l] = (int)((start[l + 1] - start[l]) / 32);
+        for (int64_t wi = start[l] / 32; wi < start[l + 1] / 32; ++wi) wlev[wi] = l;
+    }
     int st = RS_OK;
     st = st ? st : rs_alloc(ctx, (void **)&T.pos, sizeof(int) * npad);
     st = st ? st : rs_alloc(ctx, (void **)&T.slice_ptr, sizeof(int) * (nslices + 1));
     st = st ? st : rs_alloc(ctx, (void **)&T.col, sizeof(int) * nent);
     st = st ? st : rs_alloc(ctx, (void **)&T.src, sizeof(int) * nent);
     st = st ? st : rs_alloc(ctx, (void **)&T.dsrc, sizeof(int) * npad);
+    st = st ? st : rs_alloc(ctx, (void **)&T.warp_level, sizeof(int) * (nslices > 0 ? nslices : 1));
+    st = st ? st : rs_alloc(ctx, (void **)&T.level_nwarps, sizeof(int) * lnw.size());
+    st = st ? st : rs_alloc(ctx, (void **)&T.level_count, sizeof(int) * lnw.size());
+    st = st ? st : rs_alloc(ctx, (void **)&T.level_done, sizeof(int) * lnw.size());
     if (st) return st;
     cudaStream_t s = ctx->stream;
     RS_CUDA_TRY(cudaMemcpyAsync(T.pos, pos.data(), sizeof(int) * npad, cudaMemcpyHostToDevice, s));
@@ -118,6 +128,11 @@ static int build_layout(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
         RS_CUDA_TRY(cudaMemcpyAsync(T.src, esrc.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, s));
     }
     RS_CUDA_TRY(cudaMemcpyAsync(T.dsrc, dsrc.data(), sizeof(int) * npad, cudaMemcpyHostToDevice, s));
+    if (nslices)
+        RS_CUDA_TRY(cudaMemcpyAsync(T.warp_level, wlev.data(), sizeof(int) * nslices, cudaMemcpyHostToDevice, s));
+    RS_CUDA_TRY(cudaMemcpyAsync(T.level_nwarps, lnw.data(), sizeof(int) * lnw.size(), cudaMemcpyHostToDevice, s));
+    RS_CUDA_TRY(cudaMemsetAsync(T.level_count, 0, sizeof(int) * lnw.size(), s));
+    RS_CUDA_TRY(cudaMemsetAsync(T.level_done, 0, sizeof(int) * lnw.size(), s));
     RS_CUDA_TRY(cudaStreamSynchronize(s));   // host vectors go out of scope
     return RS_OK;
 }
@@ -131,64 +146,115 @@ static void free_layout(rs_ctx *ctx, TriLayout &T)
     rs_free(ctx, T.dsrc);
     rs_free(ctx, T.val);
     rs_free(ctx, T.diag);
+    rs_free(ctx, T.warp_level);
+    rs_free(ctx, T.level_nwarps);
+    rs_free(ctx, T.level_count);
+    rs_free(ctx, T.level_done);
     T = TriLayout();
 }
 
 // ---------------------------------------------------------------------------
-// sweep bookkeeping shared by all sync-free kernels
+// persistent level-chained sweep
 // ---------------------------------------------------------------------------
-struct SweepTicket {
-    int base;
-    int epoch;
+// Positions are processed one warp (32 positions of one level) at a time.
+// Blocks stay resident and take tickets of blockDim positions in order.
+// A warp of level l waits until level l-1 is complete (then every level
+// below it is complete too: each warp of level l-1 itself waited for l-2),
+// which one lane polls.  After its rows are written the warp counts itself
+// into its level; the last warp of the level resets the counter and
+// publishes the level with a release store of the sweep's epoch.
+struct SweepArgs {
+    int npad;
+    int64_t nent;
+    const int *pos, *sptr, *ecol;
+    const int *wlev, *lnw;
+    int *lcount, *ldone;
+    SweepState *st;
+    int *err;
+    long long limit;
+    const int *skip;
 };
 
-__device__ __forceinline__ void sweep_begin(SweepState *st, int *s_base, int *s_epoch)
+static SweepArgs sweep_args(rs_ctx *ctx, const TriLayout &T, SweepState *st, const int *skip)
 {
-    if (threadIdx.x == 0) {
-        *s_base = (int)atomicAdd(&st->ticket, 1u) * blockDim.x;
-        *s_epoch = *(volatile int *)&st->epoch;
-    }
-    __syncthreads();
+    SweepArgs a;
+    a.npad = T.npad;
+    a.nent = T.nent;
+    a.pos = T.pos;
+    a.sptr = T.slice_ptr;
+    a.ecol = T.col;
+    a.wlev = T.warp_level;
+    a.lnw = T.level_nwarps;
+    a.lcount = T.level_count;
+    a.ldone = T.level_done;
+    a.st = st;
+    a.err = ctx->d_err;
+    a.limit = ctx->spin_limit;
+    a.skip = skip;
+    return a;
 }
 
-__device__ __forceinline__ void sweep_end(SweepState *st, int epoch)
+__device__ __forceinline__ void report_timeout(int *err) { atomicOr(err, RS_DEVERR_TIMEOUT); }
+
+template <class Body>
+__device__ __forceinline__ void run_sweep(const SweepArgs &a, Body body)
 {
-    __syncthreads();
+    if (a.skip && *(volatile const int *)a.skip) return;   // uniform over the grid
+    __shared__ int s_base, s_epoch;
+    if (threadIdx.x == 0) s_epoch = *(volatile int *)&a.st->epoch;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) s_base = (int)atomicAdd(&a.st->ticket, 1u) * (int)blockDim.x;
+        __syncthreads();
+        const int base = s_base, epoch = s_epoch;
+        __syncthreads();
+        if (base >= a.npad) break;
+        const int w0 = base + warp * 32;
+        if (w0 < a.npad) {
+            const int lev = a.wlev[w0 >> 5];
+            if (lev > 0) {
+                if (lane == 0 && !wait_epoch(a.ldone + lev - 1, epoch, a.limit)) report_timeout(a.err);
+                __syncwarp();
+            }
+            body(w0 + lane);
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                const int old = atomicAdd(a.lcount + lev, 1);
+                if (old == a.lnw[lev] - 1) {
+                    a.lcount[lev] = 0;
+                    st_release(a.ldone + lev, epoch);
+                }
+            }
+        }
+    }
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned d = atomicAdd(&st->done, 1u);
-        if (d == gridDim.x - 1) {
-            st->ticket = 0;
-            st->done = 0;
-            st->epoch = epoch + 1;
+        if (atomicAdd(&a.st->done, 1u) == gridDim.x - 1) {
+            a.st->ticket = 0;
+            a.st->done = 0;
+            a.st->epoch = s_epoch + 1;
             __threadfence();
         }
     }
 }
 
-__device__ __forceinline__ void report_timeout(int *err) { atomicOr(err, RS_DEVERR_TIMEOUT); }
-
 // ---------------------------------------------------------------------------
-// numeric factorisation
+// numeric factorisation (schedule of the L sweep)
 // ---------------------------------------------------------------------------
 // Scalar ILU(0), IKJ form: for each k < i in row i (ascending): l_ik = a_ik / u_kk,
 // then a_ij -= l_ik u_kj for every j > k present in both rows.
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
-k_ilu0_factor(int npad, const int *__restrict__ pos, const int *__restrict__ ptr,
-              const int *__restrict__ col, const int *__restrict__ diagpos, double *lu,
-              int *flags, SweepState *st, int *err, int *bad_row, long long limit)
+k_ilu0_factor(SweepArgs a, const int *__restrict__ ptr, const int *__restrict__ col,
+              const int *__restrict__ diagpos, double *lu, int *bad_row)
 {
-    __shared__ int s_base, s_epoch;
-    sweep_begin(st, &s_base, &s_epoch);
-    const int epoch = s_epoch;
-    const int p = s_base + threadIdx.x;
-    const int row = p < npad ? pos[p] : -1;
-    if (row >= 0) {
+    run_sweep(a, [&](int p) {
+        const int row = a.pos[p];
+        if (row < 0) return;
         const int e_i = ptr[row + 1];
         const int d_i = diagpos[row];
         for (int q = ptr[row]; q < d_i; ++q) {
             const int k = col[q];
-            if (!wait_epoch(flags + k, epoch, limit)) report_timeout(err);
             const int d_k = diagpos[k];
             const double lik = lu[q] / __ldcg(lu + d_k);
             lu[q] = lik;
@@ -203,17 +269,15 @@ k_ilu0_factor(int npad, const int *__restrict__ pos, const int *__restrict__ ptr
         }
         const double d = lu[d_i];
         if (!(d != 0.0) || !isfinite(d)) {
-            atomicOr(err, RS_DEVERR_PIVOT);
+            atomicOr(a.err, RS_DEVERR_PIVOT);
             atomicMin(bad_row, row);
         }
-        st_release(flags + row, epoch);
-    }
-    sweep_end(st, epoch);
+    });
 }
 
 // bs x bs block helpers (row-major, registers)
 template <int BS>
-__device__ __forceinline__ void blk_mul(const double *a, const double *b, double *c)
+__device__ __forceinline__ void blk_mul(const double *x, const double *y, double *c)
 {
 #pragma unroll
     for (int i = 0; i < BS; ++i)
@@ -221,7 +285,7 @@ __device__ __forceinline__ void blk_mul(const double *a, const double *b, double
         for (int j = 0; j < BS; ++j) {
             double s = 0.0;
 #pragma unroll
-            for (int k = 0; k < BS; ++k) s = __dadd_rn(s, __dmul_rn(a[i * BS + k], b[k * BS + j]));
+            for (int k = 0; k < BS; ++k) s = __dadd_rn(s, __dmul_rn(x[i * BS + k], y[k * BS + j]));
             c[i * BS + j] = s;
         }
 }
@@ -241,7 +305,6 @@ __device__ bool blk_inverse(const double *a, double *inv)
 #pragma unroll
         for (int r = c + 1; r < BS; ++r)
             if (fabs(m[r * BS + c]) > fabs(m[piv * BS + c])) piv = r;
-        // swap rows c and piv (done with selects to keep arrays in registers)
 #pragma unroll
         for (int r = c + 1; r < BS; ++r) {
             if (r == piv) {
@@ -275,28 +338,23 @@ __device__ bool blk_inverse(const double *a, double *inv)
 // Block ILU(0): L_IK = A_IK inv(U_KK); A_IJ -= L_IK U_KJ; dinv_I = inv(U_II).
 template <int BS>
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
-k_bilu0_factor(int npad, const int *__restrict__ pos, const int *__restrict__ ptr,
-               const int *__restrict__ col, const int *__restrict__ diagpos, double *lu,
-               double *dinv, int *flags, SweepState *st, int *err, int *bad_row, long long limit)
+k_bilu0_factor(SweepArgs a, const int *__restrict__ ptr, const int *__restrict__ col,
+               const int *__restrict__ diagpos, double *lu, double *dinv, int *bad_row)
 {
     constexpr int B2 = BS * BS;
-    __shared__ int s_base, s_epoch;
-    sweep_begin(st, &s_base, &s_epoch);
-    const int epoch = s_epoch;
-    const int p = s_base + threadIdx.x;
-    const int row = p < npad ? pos[p] : -1;
-    if (row >= 0) {
+    run_sweep(a, [&](int p) {
+        const int row = a.pos[p];
+        if (row < 0) return;
         const int e_i = ptr[row + 1];
         const int d_i = diagpos[row];
-        double a[B2], t[B2], u[B2], c[B2];
+        double x[B2], t[B2], u[B2], c[B2];
         for (int q = ptr[row]; q < d_i; ++q) {
             const int k = col[q];
-            if (!wait_epoch(flags + k, epoch, limit)) report_timeout(err);
 #pragma unroll
-            for (int x = 0; x < B2; ++x) { a[x] = lu[(size_t)q * B2 + x]; t[x] = __ldcg(dinv + (size_t)k * B2 + x); }
-            blk_mul<BS>(a, t, c);                      // L_IK
+            for (int v = 0; v < B2; ++v) { x[v] = lu[(size_t)q * B2 + v]; t[v] = __ldcg(dinv + (size_t)k * B2 + v); }
+            blk_mul<BS>(x, t, c);                      // L_IK
 #pragma unroll
-            for (int x = 0; x < B2; ++x) lu[(size_t)q * B2 + x] = c[x];
+            for (int v = 0; v < B2; ++v) lu[(size_t)q * B2 + v] = c[v];
             int qq = q + 1;
             const int e_k = ptr[k + 1];
             for (int r = diagpos[k] + 1; r < e_k; ++r) {
@@ -305,27 +363,25 @@ k_bilu0_factor(int npad, const int *__restrict__ pos, const int *__restrict__ pt
                 if (qq == e_i) break;
                 if (col[qq] == j) {
 #pragma unroll
-                    for (int x = 0; x < B2; ++x) t[x] = __ldcg(lu + (size_t)r * B2 + x);
+                    for (int v = 0; v < B2; ++v) t[v] = __ldcg(lu + (size_t)r * B2 + v);
                     blk_mul<BS>(c, t, u);
 #pragma unroll
-                    for (int x = 0; x < B2; ++x)
-                        lu[(size_t)qq * B2 + x] = __dsub_rn(lu[(size_t)qq * B2 + x], u[x]);
+                    for (int v = 0; v < B2; ++v)
+                        lu[(size_t)qq * B2 + v] = __dsub_rn(lu[(size_t)qq * B2 + v], u[v]);
                 }
             }
         }
 #pragma unroll
-        for (int x = 0; x < B2; ++x) a[x] = lu[(size_t)d_i * B2 + x];
-        if (!blk_inverse<BS>(a, t)) {
-            atomicOr(err, RS_DEVERR_PIVOT);
+        for (int v = 0; v < B2; ++v) x[v] = lu[(size_t)d_i * B2 + v];
+        if (!blk_inverse<BS>(x, t)) {
+            atomicOr(a.err, RS_DEVERR_PIVOT);
             atomicMin(bad_row, row);
 #pragma unroll
-            for (int x = 0; x < B2; ++x) t[x] = 0.0;
+            for (int v = 0; v < B2; ++v) t[v] = 0.0;
         }
 #pragma unroll
-        for (int x = 0; x < B2; ++x) dinv[(size_t)row * B2 + x] = t[x];
-        st_release(flags + row, epoch);
-    }
-    sweep_end(st, epoch);
+        for (int v = 0; v < B2; ++v) dinv[(size_t)row * B2 + v] = t[v];
+    });
 }
 
 // Gather the factor values of one triangle into its sliced-ELL arrays
@@ -360,105 +416,242 @@ __global__ void k_gather_diag(int npad, int b2, const int *__restrict__ pos, con
 // ---------------------------------------------------------------------------
 // triangular sweeps
 // ---------------------------------------------------------------------------
+// The value of a row is its own ready flag: before a sweep every entry of its
+// work vector holds a signalling-NaN bit pattern that arithmetic never
+// produces; a thread polls the entries it depends on until they change, and
+// publishes its row with one plain 8-byte (or 4-byte) store, which is
+// single-copy atomic.  The L sweep resets the U sweep's work vector to the
+// sentinel (row by row) and the U sweep resets the L sweep's, so no clearing
+// pass is needed.  Every index and factor value a row needs is loaded before
+// its first wait; only the dependency values are read after it.
+template <typename T> struct Sentinel;
+template <> struct Sentinel<double> {
+    typedef unsigned long long bits_t;
+    static constexpr bits_t bits = 0xFFF5A5A5A5A5A5A5ull;
+};
+template <> struct Sentinel<float> {
+    typedef unsigned int bits_t;
+    static constexpr bits_t bits = 0xFFB5A5A5u;
+};
+
+__device__ __forceinline__ unsigned long long ld_relaxed_bits(const double *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_relaxed_bits(const float *p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(double *p, double v)
+{
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(float *p, float v)
+{
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ double bits_to(double, unsigned long long b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ float bits_to(float, unsigned int b) { return __uint_as_float(b); }
+
+// Returns the value at p once it is no longer the sentinel (bounded wait).
+template <typename T>
+__device__ __forceinline__ T wait_value(const T *p, long long limit, int *err)
+{
+    typedef typename Sentinel<T>::bits_t B;
+    B v = ld_relaxed_bits(p);
+    if (v != Sentinel<T>::bits) return bits_to(T(), v);
+    const long long t0 = clock64();
+    unsigned ns = 16;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 128) ns <<= 1;
+        v = ld_relaxed_bits(p);
+        if (v != Sentinel<T>::bits) return bits_to(T(), v);
+        if (clock64() - t0 > limit) {
+            atomicOr(err, RS_DEVERR_TIMEOUT);
+            return bits_to(T(), v);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_fill_sentinel(int64_t n, T *v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = bits_to(T(), Sentinel<T>::bits);
+}
+
+// persistent ticketed loop over positions (no level synchronisation)
+template <class Body>
+__device__ __forceinline__ void run_rows(const SweepArgs &a, Body body)
+{
+    if (a.skip && *(volatile const int *)a.skip) return;   // uniform over the grid
+    __shared__ int s_base;
+    for (;;) {
+        if (threadIdx.x == 0) s_base = (int)atomicAdd(&a.st->ticket, 1u) * (int)blockDim.x;
+        __syncthreads();
+        const int base = s_base;
+        __syncthreads();
+        if (base >= a.npad) break;
+        const int p = base + threadIdx.x;
+        if (p < a.npad) body(p);
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.st->done, 1u) == gridDim.x - 1) {
+            a.st->ticket = 0;
+            a.st->done = 0;
+            __threadfence();
+        }
+    }
+}
+
+#define RS_PREFETCH 4   // sliced-ELL entries loaded ahead of the waits
+
+// Separately rounded multiply and subtract (no contraction into a fused
+// multiply-add), so the sweeps round exactly like a sequential row-by-row
+// solve that evaluates acc - l*y in ascending column order.
+__device__ __forceinline__ double msub(double acc, double a, double b) { return __dsub_rn(acc, __dmul_rn(a, b)); }
+__device__ __forceinline__ float msub(float acc, float a, float b) { return __fsub_rn(acc, __fmul_rn(a, b)); }
+__device__ __forceinline__ double madd(double acc, double a, double b) { return __dadd_rn(acc, __dmul_rn(a, b)); }
+__device__ __forceinline__ float madd(float acc, float a, float b) { return __fadd_rn(acc, __fmul_rn(a, b)); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// Loads the BS values of every prefetched dependency at once, then polls
+// again only those still holding the sentinel.
+template <int BS, typename T>
+__device__ __forceinline__ void gather_ready(const T *vec, const int (&c)[RS_PREFETCH],
+                                             T (&out)[RS_PREFETCH][BS], long long limit, int *err)
+{
+    typedef typename Sentinel<T>::bits_t B;
+    B b[RS_PREFETCH][BS];
+#pragma unroll
+    for (int j = 0; j < RS_PREFETCH; ++j)
+#pragma unroll
+        for (int k = 0; k < BS; ++k) b[j][k] = c[j] >= 0 ? ld_relaxed_bits(vec + (size_t)c[j] * BS + k) : (B)0;
+#pragma unroll
+    for (int j = 0; j < RS_PREFETCH; ++j)
+#pragma unroll
+        for (int k = 0; k < BS; ++k) {
+            if (c[j] >= 0 && b[j][k] == Sentinel<T>::bits)
+                out[j][k] = wait_value(vec + (size_t)c[j] * BS + k, limit, err);
+            else
+                out[j][k] = bits_to(T(), b[j][k]);
+        }
+}
+
 // L y = r (unit lower).  TI: type of r; T: working type.  scale (device,
-// optional) multiplies r on load.
+// optional) multiplies r on load.  zreset: the U sweep's work vector.
 template <int BS, typename T, typename TI>
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
-k_lsolve(int npad, int64_t nent, const int *__restrict__ pos, const int *__restrict__ sptr,
-         const int *__restrict__ ecol, const T *__restrict__ val, const TI *__restrict__ r,
-         const double *__restrict__ scale, T *y, int *flags, SweepState *st, int *err,
-         long long limit, const int *skip)
+k_lsolve(SweepArgs a, const T *__restrict__ val, const TI *__restrict__ r,
+         const double *__restrict__ scale, T *y, T *zreset)
 {
-    if (skip && *(volatile const int *)skip) return;   // uniform over the grid
-    __shared__ int s_base, s_epoch;
-    sweep_begin(st, &s_base, &s_epoch);
-    const int epoch = s_epoch;
-    const int p = s_base + threadIdx.x;
-    const int row = p < npad ? pos[p] : -1;
-    if (row >= 0) {
+    run_rows(a, [&](int p) {
+        const int row = a.pos[p];
+        if (row < 0) return;
+        const int s = p >> 5, lane = p & 31;
+        const int off = a.sptr[s];
+        const int w = (a.sptr[s + 1] - off) >> 5;
         const double sc = scale ? *scale : 1.0;
         T acc[BS];
 #pragma unroll
-        for (int k = 0; k < BS; ++k) acc[k] = (T)(sc == 1.0 ? (double)r[(size_t)row * BS + k]
-                                                            : (double)r[(size_t)row * BS + k] * sc);
-        const int s = p >> 5, lane = p & 31;
-        const int off = sptr[s];
-        const int w = (sptr[s + 1] - off) >> 5;
-        for (int e = 0; e < w; ++e) {
-            const int idx = off + e * 32 + lane;
-            const int c = ecol[idx];
-            if (c < 0) continue;
-            if (!wait_epoch(flags + c, epoch, limit)) report_timeout(err);
-            T yc[BS];
+        for (int k = 0; k < BS; ++k) {
+            acc[k] = (T)(sc == 1.0 ? (double)r[(size_t)row * BS + k] : __dmul_rn((double)r[(size_t)row * BS + k], sc));
+            zreset[(size_t)row * BS + k] = bits_to(T(), Sentinel<T>::bits);
+        }
+        for (int e0 = 0; e0 < w; e0 += RS_PREFETCH) {
+            int c[RS_PREFETCH];
+            T v[RS_PREFETCH][BS * BS];
 #pragma unroll
-            for (int k = 0; k < BS; ++k) yc[k] = __ldcg(y + (size_t)c * BS + k);
+            for (int j = 0; j < RS_PREFETCH; ++j) {
+                const int idx = off + (e0 + j) * 32 + lane;
+                c[j] = e0 + j < w ? a.ecol[idx] : -1;
 #pragma unroll
-            for (int i = 0; i < BS; ++i)
+                for (int q = 0; q < BS * BS; ++q) v[j][q] = c[j] >= 0 ? val[(size_t)q * a.nent + idx] : T(0);
+            }
+            T yc[RS_PREFETCH][BS];
+            gather_ready<BS, T>(y, c, yc, a.limit, a.err);
 #pragma unroll
-                for (int k = 0; k < BS; ++k) acc[i] -= val[(size_t)(i * BS + k) * nent + idx] * yc[k];
+            for (int j = 0; j < RS_PREFETCH; ++j) {
+                if (c[j] < 0) continue;
+#pragma unroll
+                for (int i = 0; i < BS; ++i)
+#pragma unroll
+                    for (int k = 0; k < BS; ++k) acc[i] = msub(acc[i], v[j][i * BS + k], yc[j][k]);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < BS; ++k) y[(size_t)row * BS + k] = acc[k];
-        st_release(flags + row, epoch);
-    }
-    sweep_end(st, epoch);
+        for (int k = 0; k < BS; ++k) st_relaxed(y + (size_t)row * BS + k, acc[k]);
+    });
 }
 
-// U z = y.  z (type T) carries values between rows; out (FP64, optional)
-// receives a widened copy.
+// U z = y.  z (type T) carries values between rows (and is reset to the
+// sentinel by the next L sweep); out (FP64) receives the result; y is reset
+// to the sentinel for the next L sweep.
 template <int BS, typename T>
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
-k_usolve(int npad, int64_t nent, const int *__restrict__ pos, const int *__restrict__ sptr,
-         const int *__restrict__ ecol, const T *__restrict__ val, const T *__restrict__ diag,
-         const T *__restrict__ y, T *z, double *__restrict__ out, int *flags, SweepState *st,
-         int *err, long long limit, const int *skip)
+k_usolve(SweepArgs a, const T *__restrict__ val, const T *__restrict__ diag, T *y, T *z,
+         double *__restrict__ out)
 {
-    if (skip && *(volatile const int *)skip) return;   // uniform over the grid
-    __shared__ int s_base, s_epoch;
-    sweep_begin(st, &s_base, &s_epoch);
-    const int epoch = s_epoch;
-    const int p = s_base + threadIdx.x;
-    const int row = p < npad ? pos[p] : -1;
-    if (row >= 0) {
-        T acc[BS];
-#pragma unroll
-        for (int k = 0; k < BS; ++k) acc[k] = y[(size_t)row * BS + k];
+    run_rows(a, [&](int p) {
+        const int row = a.pos[p];
+        if (row < 0) return;
         const int s = p >> 5, lane = p & 31;
-        const int off = sptr[s];
-        const int w = (sptr[s + 1] - off) >> 5;
-        for (int e = 0; e < w; ++e) {
-            const int idx = off + e * 32 + lane;
-            const int c = ecol[idx];
-            if (c < 0) continue;
-            if (!wait_epoch(flags + c, epoch, limit)) report_timeout(err);
-            T zc[BS];
+        const int off = a.sptr[s];
+        const int w = (a.sptr[s + 1] - off) >> 5;
+        T acc[BS], dg[BS * BS];
 #pragma unroll
-            for (int k = 0; k < BS; ++k) zc[k] = __ldcg(z + (size_t)c * BS + k);
+        for (int k = 0; k < BS; ++k) {
+            acc[k] = y[(size_t)row * BS + k];
+            y[(size_t)row * BS + k] = bits_to(T(), Sentinel<T>::bits);
+        }
 #pragma unroll
-            for (int i = 0; i < BS; ++i)
+        for (int q = 0; q < BS * BS; ++q) dg[q] = diag[(size_t)q * a.npad + p];
+        for (int e0 = 0; e0 < w; e0 += RS_PREFETCH) {
+            int c[RS_PREFETCH];
+            T v[RS_PREFETCH][BS * BS];
 #pragma unroll
-                for (int k = 0; k < BS; ++k) acc[i] -= val[(size_t)(i * BS + k) * nent + idx] * zc[k];
+            for (int j = 0; j < RS_PREFETCH; ++j) {
+                const int idx = off + (e0 + j) * 32 + lane;
+                c[j] = e0 + j < w ? a.ecol[idx] : -1;
+#pragma unroll
+                for (int q = 0; q < BS * BS; ++q) v[j][q] = c[j] >= 0 ? val[(size_t)q * a.nent + idx] : T(0);
+            }
+            T zc[RS_PREFETCH][BS];
+            gather_ready<BS, T>(z, c, zc, a.limit, a.err);
+#pragma unroll
+            for (int j = 0; j < RS_PREFETCH; ++j) {
+                if (c[j] < 0) continue;
+#pragma unroll
+                for (int i = 0; i < BS; ++i)
+#pragma unroll
+                    for (int k = 0; k < BS; ++k) acc[i] = msub(acc[i], v[j][i * BS + k], zc[j][k]);
+            }
         }
         T res[BS];
         if (BS == 1) {
-            res[0] = acc[0] / diag[p];
+            res[0] = rdiv(acc[0], dg[0]);
         } else {
 #pragma unroll
             for (int i = 0; i < BS; ++i) {
                 T sum = 0;
 #pragma unroll
-                for (int k = 0; k < BS; ++k) sum += diag[(size_t)(i * BS + k) * npad + p] * acc[k];
+                for (int k = 0; k < BS; ++k) sum = madd(sum, dg[i * BS + k], acc[k]);
                 res[i] = sum;
             }
         }
 #pragma unroll
         for (int k = 0; k < BS; ++k) {
-            z[(size_t)row * BS + k] = res[k];
-            if (out) out[(size_t)row * BS + k] = (double)res[k];
+            st_relaxed(z + (size_t)row * BS + k, res[k]);
+            out[(size_t)row * BS + k] = (double)res[k];
         }
-        st_release(flags + row, epoch);
-    }
-    sweep_end(st, epoch);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -495,8 +688,21 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
     st = st ? st : rs_alloc(ctx, (void **)&f->flags, sizeof(int) * (nrows > 0 ? nrows : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->state, sizeof(SweepState));
     st = st ? st : rs_alloc(ctx, &f->ywork, esz * bs * (nrows > 0 ? nrows : 1));
-    if (!st && fp32) st = rs_alloc(ctx, &f->zwork, esz * bs * (nrows > 0 ? nrows : 1));
+    st = st ? st : rs_alloc(ctx, &f->zwork, esz * bs * (nrows > 0 ? nrows : 1));
     if (st) { rs_ilu_destroy(f); return st; }
+    {
+        const int64_t nv = (int64_t)bs * (nrows > 0 ? nrows : 1);
+        const int g = (int)std::min<int64_t>((nv + 255) / 256, 4096);
+        if (fp32) {
+            k_fill_sentinel<float><<<g, 256, 0, ctx->stream>>>(nv, (float *)f->ywork);
+            k_fill_sentinel<float><<<g, 256, 0, ctx->stream>>>(nv, (float *)f->zwork);
+        } else {
+            k_fill_sentinel<double><<<g, 256, 0, ctx->stream>>>(nv, (double *)f->ywork);
+            k_fill_sentinel<double><<<g, 256, 0, ctx->stream>>>(nv, (double *)f->zwork);
+        }
+        RS_TRY(rs_check_launch(ctx));
+        ctx->launches++;
+    }
     SweepState s0 = {0u, 0u, 1, 0};
     RS_CUDA_TRY(cudaMemsetAsync(f->flags, 0, sizeof(int) * (nrows > 0 ? nrows : 1), ctx->stream));
     RS_CUDA_TRY(cudaMemcpyAsync(f->state, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->stream));
@@ -523,7 +729,11 @@ void rs_ilu_destroy(IluFactor *f)
     delete f;
 }
 
-static int sweep_grid(int npad) { return (npad + RS_SWEEP_THREADS - 1) / RS_SWEEP_THREADS; }
+static int sweep_grid(rs_ctx *ctx, int npad)
+{
+    const int need = (npad + RS_SWEEP_THREADS - 1) / RS_SWEEP_THREADS;
+    return std::max(1, std::min(need, ctx->sweep_blocks));
+}
 
 int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row)
 {
@@ -533,18 +743,18 @@ int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row)
     if (f->nrows == 0) return RS_OK;
     RS_CUDA_TRY(cudaMemcpyAsync(f->lu, d_val, sizeof(double) * b2 * f->nnzb, cudaMemcpyDeviceToDevice,
                                 ctx->stream));
-    const int g = sweep_grid(f->L.npad);
+    const int g = sweep_grid(ctx, f->L.npad);
+    const SweepArgs a = sweep_args(ctx, f->L, f->state, nullptr);
     switch (f->bs) {
     case 1:
-        k_ilu0_factor<<<g, RS_SWEEP_THREADS, 0, ctx->stream>>>(f->L.npad, f->L.pos, f->ptr, f->col,
-                                                              f->diagpos, f->lu, f->flags, f->state,
-                                                              ctx->d_err, ctx->d_bad_row, ctx->spin_limit);
+        k_ilu0_factor<<<g, RS_SWEEP_THREADS, 0, ctx->stream>>>(a, f->ptr, f->col, f->diagpos, f->lu,
+                                                              ctx->d_bad_row);
         break;
-#define RS_BF(BB)                                                                              \
-    case BB:                                                                                   \
-        k_bilu0_factor<BB><<<g, RS_SWEEP_THREADS, 0, ctx->stream>>>(                           \
-            f->L.npad, f->L.pos, f->ptr, f->col, f->diagpos, f->lu, f->dinv, f->flags, f->state, \
-            ctx->d_err, ctx->d_bad_row, ctx->spin_limit);                                      \
+#define RS_BF(BB)                                                                          \
+    case BB:                                                                               \
+        k_bilu0_factor<BB><<<g, RS_SWEEP_THREADS, 0, ctx->stream>>>(a, f->ptr, f->col,     \
+                                                                    f->diagpos, f->lu,    \
+                                                                    f->dinv, ctx->d_bad_row); \
         break;
         RS_BF(2)
         RS_BF(3)
@@ -577,15 +787,12 @@ static int apply_typed(IluFactor *f, const double *r, double *z, const double *s
 {
     rs_ctx *ctx = f->ctx;
     T *y = (T *)f->ywork;
-    k_lsolve<BS, T, double><<<sweep_grid(f->L.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
-        f->L.npad, f->L.nent, f->L.pos, f->L.slice_ptr, f->L.col, (const T *)f->L.val, r, scale, y,
-        f->flags, f->state, ctx->d_err, ctx->spin_limit, skip);
+    T *zt = (T *)f->zwork;
+    k_lsolve<BS, T, double><<<sweep_grid(ctx, f->L.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
+        sweep_args(ctx, f->L, f->state, skip), (const T *)f->L.val, r, scale, y, zt);
     RS_TRY(rs_check_launch(ctx));
-    T *zt = sizeof(T) == sizeof(double) ? (T *)z : (T *)f->zwork;
-    double *out = sizeof(T) == sizeof(double) ? nullptr : z;
-    k_usolve<BS, T><<<sweep_grid(f->U.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
-        f->U.npad, f->U.nent, f->U.pos, f->U.slice_ptr, f->U.col, (const T *)f->U.val,
-        (const T *)f->U.diag, y, zt, out, f->flags, f->state, ctx->d_err, ctx->spin_limit, skip);
+    k_usolve<BS, T><<<sweep_grid(ctx, f->U.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
+        sweep_args(ctx, f->U, f->state, skip), (const T *)f->U.val, (const T *)f->U.diag, y, zt, z);
     return rs_check_launch(ctx);
 }
 

@@ -52,6 +52,7 @@ struct rs_ctx {
     double *h_pinned;        // pinned host staging (64 doubles)
     long long launches;
     long long spin_limit;    // clock cycles a device-side wait may take
+    int sweep_blocks;        // resident blocks of the persistent triangular sweeps
 };
 
 struct rs_mat {
@@ -94,6 +95,13 @@ struct TriLayout {
     int *dsrc = nullptr;     // [npad] index of the diagonal entry (U only) or -1
     void *val = nullptr;     // [nent * bs*bs] factor values (float or double)
     void *diag = nullptr;    // [npad * bs*bs] U: diagonal (bs=1) or its inverse (bs>1)
+    // level schedule: level of every warp of positions, warps per level, and
+    // per-level arrival counters / completion epochs used by the sweeps
+    int nwarps = 0;
+    int *warp_level = nullptr;   // [nwarps]
+    int *level_nwarps = nullptr; // [nlevels]
+    int *level_count = nullptr;  // [nlevels] (self-resetting)
+    int *level_done = nullptr;   // [nlevels] epoch of the sweep that last completed the level
 };
 
 // ILU(0) / block ILU(0) of one matrix pattern.

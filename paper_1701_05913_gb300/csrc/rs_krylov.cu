@@ -29,7 +29,7 @@ struct GmresDev {
     double cs[RS_MAX_RESTART], sn[RS_MAX_RESTART];
     double g[RS_MAX_RESTART + 1], y[RS_MAX_RESTART + 1];
     double h1[RS_MAX_RESTART + 2], h2[RS_MAX_RESTART + 2];
-    double bnorm, tol, beta, inv_h, w0sq, implicit, r2;
+    double bnorm, tol, beta, hdiv, w0sq, implicit, r2;
     int iters, k, cycle_done, converged, maxit, m, noupd, status;
 };
 
@@ -90,8 +90,8 @@ k_cgs_dots(int n, int ld, int nc, const double *__restrict__ V, const double *__
         const double wr = w[r];
 #pragma unroll
         for (int k = 0; k < NC; ++k)
-            if (k < nc) acc[k] += V[(size_t)k * ld + r] * wr;
-        acc[NC] += wr * wr;
+            if (k < nc) acc[k] = __dadd_rn(acc[k], __dmul_rn(V[(size_t)k * ld + r], wr));
+        acc[NC] = __dadd_rn(acc[NC], __dmul_rn(wr, wr));
     }
     // move the norm into slot nc so the reduction covers slots 0..nc
 #pragma unroll
@@ -123,14 +123,14 @@ k_cgs_update_dots(int n, int ld, int nc, const double *__restrict__ V, double *_
         for (int k = 0; k < NC; ++k) {
             if (k < nc) {
                 v[k] = V[(size_t)k * ld + r];
-                s += v[k] * hs[k];
+                s = __dadd_rn(s, __dmul_rn(v[k], hs[k]));
             }
         }
-        const double w1 = w[r] - s;
+        const double w1 = __dsub_rn(w[r], s);
         w[r] = w1;
 #pragma unroll
         for (int k = 0; k < NC; ++k)
-            if (k < nc) acc[k] += v[k] * w1;
+            if (k < nc) acc[k] = __dadd_rn(acc[k], __dmul_rn(v[k], w1));
     }
     if (reduce_partials<NC>(acc, nc, partials, ticket, d->h2)) {
         const int i = nc - 1, m1 = d->m + 1;
@@ -153,10 +153,10 @@ k_cgs_update_norm(int n, int ld, int nc, const double *__restrict__ V, double *_
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < NC; ++k)
-            if (k < nc) s += V[(size_t)k * ld + r] * hs[k];
-        const double w2 = w[r] - s;
+            if (k < nc) s = __dadd_rn(s, __dmul_rn(V[(size_t)k * ld + r], hs[k]));
+        const double w2 = __dsub_rn(w[r], s);
         w[r] = w2;
-        acc[0] += w2 * w2;
+        acc[0] = __dadd_rn(acc[0], __dmul_rn(w2, w2));
     }
     if (reduce_partials<1>(acc, 1, partials, ticket, &d->r2)) {
         if (threadIdx.x == 0) {
@@ -165,23 +165,23 @@ k_cgs_update_norm(int n, int ld, int nc, const double *__restrict__ V, double *_
             const double hnext = sqrt(d->r2);
             for (int k = 0; k < i; ++k) {
                 const double a = h[k], b = h[k + 1];
-                h[k] = d->cs[k] * a + d->sn[k] * b;
-                h[k + 1] = -d->sn[k] * a + d->cs[k] * b;
+                h[k] = __dadd_rn(__dmul_rn(d->cs[k], a), __dmul_rn(d->sn[k], b));
+                h[k + 1] = __dadd_rn(__dmul_rn(-d->sn[k], a), __dmul_rn(d->cs[k], b));
             }
             const double rho = hypot(h[i], hnext);
-            d->cs[i] = h[i] / rho;
-            d->sn[i] = hnext / rho;
+            d->cs[i] = __ddiv_rn(h[i], rho);
+            d->sn[i] = __ddiv_rn(hnext, rho);
             h[i] = rho;
             h[i + 1] = 0.0;
-            d->g[i + 1] = -d->sn[i] * d->g[i];
-            d->g[i] = d->cs[i] * d->g[i];
+            d->g[i + 1] = __dmul_rn(-d->sn[i], d->g[i]);
+            d->g[i] = __dmul_rn(d->cs[i], d->g[i]);
             d->iters += 1;
             d->k = i + 1;
             d->implicit = fabs(d->g[i + 1]);
             const bool happy = hnext <= 1e-14 * sqrt(d->w0sq);
             if (d->implicit <= d->tol || d->iters >= d->maxit || happy || i == d->m - 1)
                 d->cycle_done = 1;
-            d->inv_h = 1.0 / hnext;
+            d->hdiv = hnext;     // v_{i+1} = w / h_{i+1,i}
         }
     }
 }
@@ -197,18 +197,18 @@ __global__ void k_basis_combine(int n, int ld, const double *__restrict__ B, con
     __syncthreads();
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int j = 0; j < k; ++j) s += B[(size_t)j * ld + r] * ys[j];
-        x[r] = add ? x[r] + s : s;
+        for (int j = 0; j < k; ++j) s = __dadd_rn(s, __dmul_rn(B[(size_t)j * ld + r], ys[j]));
+        x[r] = add ? __dadd_rn(x[r], s) : s;
     }
 }
 
-// v = s * r with s a device scalar
+// v = r / s with s a device scalar (a division, as the normalisation is written)
 __global__ void k_scale_dev(int n, const double *__restrict__ r, const double *__restrict__ s,
                             double *__restrict__ v, const int *skip)
 {
     if (skip && *(volatile const int *)skip) return;
     const double a = *s;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = a * r[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = __ddiv_rn(r[i], a);
 }
 
 __global__ void k_axpy_skip(int n, const double *__restrict__ x, double *__restrict__ y, const int *skip)
@@ -233,7 +233,7 @@ __global__ void k_gmres_start(GmresDev *d, const double *r2, double rtol, int fi
     for (int j = 1; j <= d->m; ++j) d->g[j] = 0.0;
     d->k = 0;
     d->noupd = 1;
-    d->inv_h = 1.0 / beta;
+    d->hdiv = beta;      // v_1 = r / beta
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k) by back-substitution
@@ -243,8 +243,8 @@ __global__ void k_gmres_backsolve(GmresDev *d)
     const int k = d->k, m1 = d->m + 1;
     for (int j = k - 1; j >= 0; --j) {
         double s = d->g[j];
-        for (int l = j + 1; l < k; ++l) s -= d->H[(size_t)l * m1 + j] * d->y[l];
-        d->y[j] = s / d->H[(size_t)j * m1 + j];
+        for (int l = j + 1; l < k; ++l) s = __dsub_rn(s, __dmul_rn(d->H[(size_t)l * m1 + j], d->y[l]));
+        d->y[j] = __ddiv_rn(s, d->H[(size_t)j * m1 + j]);
     }
     d->noupd = k == 0;
 }
@@ -356,7 +356,7 @@ static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, i
             info->iters = hs[0];
             if (hs[3]) { status = RS_OK; break; }
             if (hs[2]) { status = RS_NOT_CONVERGED; break; }
-            k_scale_dev<<<gb, 256, 0, ctx->stream>>>(n, r, &d->inv_h, V, nullptr);
+            k_scale_dev<<<gb, 256, 0, ctx->stream>>>(n, r, &d->hdiv, V, nullptr);
             ctx->launches++;
             for (int i = 0; i < m; ++i) {
                 double *vi = V + (size_t)i * ld;
@@ -368,7 +368,7 @@ static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, i
                 if (!st) st = cgs_step(ctx, n, ld, i + 1, V, d);
                 if (st) goto out;
                 if (i + 1 < m) {
-                    k_scale_dev<<<gb, 256, 0, ctx->stream>>>(n, w, &d->inv_h, w, cycle_done);
+                    k_scale_dev<<<gb, 256, 0, ctx->stream>>>(n, w, &d->hdiv, w, cycle_done);
                     ctx->launches++;
                 }
             }
@@ -455,19 +455,27 @@ k_bicg(int op, int n, double *p, double *r, const double *__restrict__ v, double
     double acc[2] = {0.0, 0.0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         switch (op) {
-        case 0: p[i] = r[i] + beta * (p[i] - omega * v[i]); break;
-        case 1: { const double si = r[i] - alpha * v[i]; s[i] = si; acc[0] += si * si; break; }
-        case 2: {
-            x[i] = x[i] + alpha * ph[i] + omega * sh[i];
-            const double ri = s[i] - omega * t[i];
-            r[i] = ri;
-            acc[0] += rh[i] * ri;
-            acc[1] += ri * ri;
+        case 0: p[i] = __dadd_rn(r[i], __dmul_rn(beta, __dsub_rn(p[i], __dmul_rn(omega, v[i])))); break;
+        case 1: {
+            const double si = __dsub_rn(r[i], __dmul_rn(alpha, v[i]));
+            s[i] = si;
+            acc[0] = __dadd_rn(acc[0], __dmul_rn(si, si));
             break;
         }
-        case 3: acc[0] += rh[i] * v[i]; break;
-        case 4: acc[0] += t[i] * s[i]; acc[1] += t[i] * t[i]; break;
-        case 5: x[i] = x[i] + alpha * ph[i]; break;
+        case 2: {
+            x[i] = __dadd_rn(__dadd_rn(x[i], __dmul_rn(alpha, ph[i])), __dmul_rn(omega, sh[i]));
+            const double ri = __dsub_rn(s[i], __dmul_rn(omega, t[i]));
+            r[i] = ri;
+            acc[0] = __dadd_rn(acc[0], __dmul_rn(rh[i], ri));
+            acc[1] = __dadd_rn(acc[1], __dmul_rn(ri, ri));
+            break;
+        }
+        case 3: acc[0] = __dadd_rn(acc[0], __dmul_rn(rh[i], v[i])); break;
+        case 4:
+            acc[0] = __dadd_rn(acc[0], __dmul_rn(t[i], s[i]));
+            acc[1] = __dadd_rn(acc[1], __dmul_rn(t[i], t[i]));
+            break;
+        case 5: x[i] = __dadd_rn(x[i], __dmul_rn(alpha, ph[i])); break;
         }
     }
     if (op == 0) return;

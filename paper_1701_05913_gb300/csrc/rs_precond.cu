@@ -30,7 +30,7 @@ __global__ void k_qimpes_app(int nb, int bs, const int *__restrict__ ptr, const 
         for (int p = ptr[I]; p < ptr[I + 1]; ++p) {
             const double *B = val + (size_t)p * bs * bs;
             double s = B[0];
-            for (int k = 1; k < bs; ++k) s += w[(size_t)I * (bs - 1) + k - 1] * B[k * bs];
+            for (int k = 1; k < bs; ++k) s = __dadd_rn(s, __dmul_rn(w[(size_t)I * (bs - 1) + k - 1], B[k * bs]));
             app[p] = s;
         }
     }
@@ -44,7 +44,7 @@ __global__ void k_qimpes_restrict(int nb, int bs, const double *__restrict__ w,
     if (skip && *(volatile const int *)skip) return;
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nb; I += gridDim.x * blockDim.x) {
         double s = f[(size_t)I * bs];
-        for (int k = 1; k < bs; ++k) s += w[(size_t)I * (bs - 1) + k - 1] * f[(size_t)I * bs + k];
+        for (int k = 1; k < bs; ++k) s = __dadd_rn(s, __dmul_rn(w[(size_t)I * (bs - 1) + k - 1], f[(size_t)I * bs + k]));
         rp[I] = s;
     }
 }
@@ -67,7 +67,7 @@ __global__ void k_copy_add(int64_t n, const double *__restrict__ a, double *__re
     if (skip && *(volatile const int *)skip) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        z[i] = add ? z[i] + a[i] : a[i];
+        z[i] = add ? __dadd_rn(z[i], a[i]) : a[i];
 }
 
 static int grid_for(rs_ctx *ctx, int64_t n)
