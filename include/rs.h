@@ -97,6 +97,16 @@ const char *rs_status_str(int status);
 /* Number of kernels this library has launched on the context so far. */
 int64_t rs_launch_count(const rs_ctx *ctx);
 
+/* Optional profiler: when enabled, every kernel the library launches is
+ * bracketed by CUDA events on the context's stream and its device time is
+ * added to its class.  Classes, in order: SpMV, L sweep, U sweep, CGS dots,
+ * CGS update+dots, CGS update+norm, BLAS-1, other preconditioner kernels,
+ * factorisation, solver scalar kernels, network.  nkinds >= 11. */
+int rs_prof_enable(rs_ctx *ctx, int on);
+/* Reads (and with reset != 0 clears) the accumulated milliseconds and launch
+ * counts per class; synchronises the stream. */
+int rs_prof_read(rs_ctx *ctx, double *ms, int64_t *launches, int32_t nkinds, int reset);
+
 /* ---- vectors (Sec. 2.2) ----------------------------------------------- */
 
 /* VecCreate (Fig. 7): an owned FP64 device vector of n entries, zeroed. */

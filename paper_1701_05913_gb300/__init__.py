@@ -56,6 +56,8 @@ SIGNATURES = [
     ("rs_sync", C.c_int, [_vp]),
     ("rs_status_str", C.c_char_p, [C.c_int]),
     ("rs_launch_count", C.c_int64, [_vp]),
+    ("rs_prof_enable", C.c_int, [_vp, C.c_int]),
+    ("rs_prof_read", C.c_int, [_vp, _f64p, C.POINTER(C.c_int64), C.c_int32, C.c_int]),
     ("rs_vec_create", C.c_int, [_vp, C.c_int32, C.POINTER(_vp)]),
     ("rs_vec_wrap", C.c_int, [_vp, C.c_int32, _vp, C.POINTER(_vp)]),
     ("rs_vec_destroy", C.c_int, [C.POINTER(_vp)]),
@@ -165,6 +167,19 @@ class Context:
 
     def launches(self) -> int:
         return lib().rs_launch_count(self.h)
+
+    PROF_KINDS = ("spmv", "l_sweep", "u_sweep", "cgs_dots", "cgs_update_dots", "cgs_update_norm",
+                  "blas1", "precond_other", "factor", "solver_scalar", "net")
+
+    def prof_enable(self, on=True):
+        _check(lib().rs_prof_enable(self.h, int(on)), "rs_prof_enable")
+
+    def prof_read(self, reset=True):
+        k = len(self.PROF_KINDS)
+        ms = (C.c_double * k)()
+        cnt = (C.c_int64 * k)()
+        _check(lib().rs_prof_read(self.h, ms, cnt, k, int(reset)), "rs_prof_read")
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(self.PROF_KINDS)}
 
     def close(self):
         if self.h:

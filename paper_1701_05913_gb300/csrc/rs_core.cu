@@ -83,6 +83,8 @@ extern "C" int rs_init(rs_ctx **out, int device, void *stream)
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     c->red_blocks = 2 * c->num_sms;
     c->launches = 0;
+    c->prof_on = 0;
+    for (int k = 0; k < RS_PROF_NKINDS; ++k) { c->prof_ms[k] = 0.0; c->prof_count[k] = 0; }
     int clock_khz = 2000000;
     cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, device);
     c->spin_limit = (long long)clock_khz * 1000LL * 2;   // about two seconds
@@ -129,6 +131,8 @@ extern "C" int rs_finalize(rs_ctx **pc)
     rs_free(c, c->d_err);
     cudaStreamSynchronize(c->stream);
     cudaFreeHost(c->h_pinned);
+    for (const RsProfRec &r : c->prof_pending) { cudaEventDestroy(r.ev0); cudaEventDestroy(r.ev1); }
+    for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
     delete c;
     *pc = nullptr;
     return RS_OK;
@@ -142,6 +146,77 @@ extern "C" int rs_sync(rs_ctx *ctx)
 }
 
 extern "C" int64_t rs_launch_count(const rs_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+// ---------------------------------------------------------------------------
+// event profiler
+// ---------------------------------------------------------------------------
+static cudaEvent_t prof_event(rs_ctx *c)
+{
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+RsProfScope::RsProfScope(rs_ctx *c, int k) : ctx(c), kind(k), ev1(nullptr)
+{
+    if (!ctx || !ctx->prof_on) return;
+    RsProfRec r;
+    r.kind = kind;
+    r.ev0 = prof_event(ctx);
+    r.ev1 = prof_event(ctx);
+    cudaEventRecord(r.ev0, ctx->stream);
+    ev1 = r.ev1;
+    ctx->prof_pending.push_back(r);
+}
+
+RsProfScope::~RsProfScope()
+{
+    if (ev1) cudaEventRecord(ev1, ctx->stream);
+}
+
+static void prof_resolve(rs_ctx *c)
+{
+    if (c->prof_pending.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (const RsProfRec &r : c->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.ev0, r.ev1) == cudaSuccess) {
+            c->prof_ms[r.kind] += ms;
+            c->prof_count[r.kind] += 1;
+        }
+        c->prof_pool.push_back(r.ev0);
+        c->prof_pool.push_back(r.ev1);
+    }
+    c->prof_pending.clear();
+}
+
+extern "C" int rs_prof_enable(rs_ctx *ctx, int on)
+{
+    if (!ctx) return RS_ERR_INVALID_ARG;
+    prof_resolve(ctx);
+    ctx->prof_on = on ? 1 : 0;
+    return RS_OK;
+}
+
+extern "C" int rs_prof_read(rs_ctx *ctx, double *ms, int64_t *launches, int32_t nkinds, int reset)
+{
+    if (!ctx || !ms || !launches || nkinds < RS_PROF_NKINDS) return RS_ERR_INVALID_ARG;
+    prof_resolve(ctx);
+    for (int k = 0; k < RS_PROF_NKINDS; ++k) {
+        ms[k] = ctx->prof_ms[k];
+        launches[k] = ctx->prof_count[k];
+        if (reset) {
+            ctx->prof_ms[k] = 0.0;
+            ctx->prof_count[k] = 0;
+        }
+    }
+    return RS_OK;
+}
 
 int rs_collect_device_error(rs_ctx *ctx, int *bad_row)
 {
@@ -176,14 +251,14 @@ __global__ void k_set(int n, double a, double *x)
 __global__ void k_axpby(int n, double a, const double *__restrict__ x, double b, double *y)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        y[i] = b == 0.0 ? __dmul_rn(a, x[i]) : __dadd_rn(__dmul_rn(a, x[i]), __dmul_rn(b, y[i]));
+        y[i] = b == 0.0 ? a * x[i] : fma(a, x[i], b * y[i]);
 }
 
 __global__ void k_axpbyz(int n, double a, const double *__restrict__ x, double b,
                          const double *__restrict__ y, double *__restrict__ z)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        z[i] = __dadd_rn(__dmul_rn(a, x[i]), __dmul_rn(b, y[i]));
+        z[i] = fma(a, x[i], b * y[i]);
 }
 
 // Two-level deterministic dot product: fixed grid, per-block partial sums,
@@ -231,6 +306,7 @@ k_dot(int n, const double *__restrict__ x, const double *__restrict__ y, double 
 int rs_axpby_launch(rs_ctx *ctx, int n, double a, const double *x, double b, double *y)
 {
     if (n <= 0) return RS_OK;
+    RsProfScope prof(ctx, RS_PROF_BLAS1);
     k_axpby<<<blas_grid(ctx, n), 256, 0, ctx->stream>>>(n, a, x, b, y);
     return rs_check_launch(ctx);
 }
@@ -241,6 +317,7 @@ int rs_dot_launch(rs_ctx *ctx, int n, const double *x, const double *y, double *
         RS_CUDA_TRY(cudaMemsetAsync(out_dev, 0, sizeof(double), ctx->stream));
         return RS_OK;
     }
+    RsProfScope prof(ctx, RS_PROF_BLAS1);
     k_dot<<<ctx->red_blocks, RS_RED_THREADS, 0, ctx->stream>>>(n, x, y, ctx->red_partials,
                                                                ctx->red_ticket, out_dev, 0);
     return rs_check_launch(ctx);
@@ -379,14 +456,14 @@ k_spmv_csr(int n, const int *__restrict__ ptr, const int *__restrict__ col,
     double acc = 0.0;
     if (active) {
         const int s = ptr[row], e = ptr[row + 1];
-        for (int p = s + lane; p < e; p += L) acc = __dadd_rn(acc, __dmul_rn(val[p], __ldg(x + col[p])));
+        for (int p = s + lane; p < e; p += L) acc = fma(val[p], __ldg(x + col[p]), acc);
     }
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
     if (active && lane == 0) {
         if (bvec) y[row] = __dsub_rn(bvec[row], acc);
         else if (beta == 0.0) y[row] = __dmul_rn(alpha, acc);
-        else y[row] = __dadd_rn(__dmul_rn(alpha, acc), __dmul_rn(beta, y[row]));
+        else y[row] = fma(alpha, acc, beta * y[row]);
     }
 }
 
@@ -423,14 +500,14 @@ k_spmv_csr_stream(int n, const int *__restrict__ ptr, const int *__restrict__ co
         }
         __syncthreads();
         if (active)
-            for (int p = a - s; p < b - s; ++p) acc = __dadd_rn(acc, __dmul_rn(sval[p], __ldg(x + scol[p])));
+            for (int p = a - s; p < b - s; ++p) acc = fma(sval[p], __ldg(x + scol[p]), acc);
     } else if (active) {
-        for (int p = a; p < b; ++p) acc = __dadd_rn(acc, __dmul_rn(val[p], __ldg(x + col[p])));
+        for (int p = a; p < b; ++p) acc = fma(val[p], __ldg(x + col[p]), acc);
     }
     if (active) {
         if (bvec) y[r] = __dsub_rn(bvec[r], acc);
         else if (beta == 0.0) y[r] = __dmul_rn(alpha, acc);
-        else y[r] = __dadd_rn(__dmul_rn(alpha, acc), __dmul_rn(beta, y[r]));
+        else y[r] = fma(alpha, acc, beta * y[r]);
     }
 }
 
@@ -452,14 +529,14 @@ k_spmv_bsr(int nb, int bsr, const int *__restrict__ ptr, const int *__restrict__
         const double *xs = x + (size_t)col[p] * bs;
         if (BS > 0) {
 #pragma unroll
-            for (int c = 0; c < (BS > 0 ? BS : 1); ++c) acc = __dadd_rn(acc, __dmul_rn(blk[c], __ldg(xs + c)));
+            for (int c = 0; c < (BS > 0 ? BS : 1); ++c) acc = fma(blk[c], __ldg(xs + c), acc);
         } else {
-            for (int c = 0; c < bs; ++c) acc = __dadd_rn(acc, __dmul_rn(blk[c], __ldg(xs + c)));
+            for (int c = 0; c < bs; ++c) acc = fma(blk[c], __ldg(xs + c), acc);
         }
     }
     if (bvec) y[t] = __dsub_rn(bvec[t], acc);
     else if (beta == 0.0) y[t] = __dmul_rn(alpha, acc);
-    else y[t] = __dadd_rn(__dmul_rn(alpha, acc), __dmul_rn(beta, y[t]));
+    else y[t] = fma(alpha, acc, beta * y[t]);
 }
 
 static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double beta,
@@ -467,6 +544,7 @@ static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double 
 {
     rs_ctx *ctx = A->ctx;
     if (A->n == 0) return RS_OK;
+    RsProfScope prof(ctx, RS_PROF_SPMV);
     if (A->bs == 1 && A->lanes <= 8) {
         const int grid = (A->n + RS_SPMV_ROWS - 1) / RS_SPMV_ROWS;
         k_spmv_csr_stream<<<grid, RS_SPMV_ROWS, 0, ctx->stream>>>(A->n, A->ptr, A->col, A->val, x, alpha,

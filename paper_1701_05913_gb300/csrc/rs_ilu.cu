@@ -137,6 +137,98 @@ static int build_layout(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     return RS_OK;
 }
 
+// Segment layout (scalar factors): segment s holds rows [32 s, 32 s + 32).
+// Its level is one more than the highest level of the segments holding the
+// columns it reads outside itself (lower columns for L, higher for U).
+static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
+                          const std::vector<int> &col, const std::vector<int> &diag, bool lower,
+                          SegLayout &S)
+{
+    const int nseg = (nrows + 31) / 32;
+    std::vector<int> lev(nseg, 0), width(nseg, 0);
+    std::vector<unsigned char> kind(nseg, 1);
+    int nlev = 0;
+    for (int t = 0; t < nseg; ++t) {
+        const int sg = lower ? t : nseg - 1 - t;
+        const int r0 = sg * 32, r1 = std::min(r0 + 32, nrows);
+        int l = 0, w = 0;
+        for (int i = r0; i < r1; ++i) {
+            const int q0 = lower ? ptr[i] : diag[i] + 1;
+            const int q1 = lower ? diag[i] : ptr[i + 1];
+            w = std::max(w, q1 - q0);
+            for (int q = q0; q < q1; ++q) {
+                const int c = col[q];
+                if (c >= r0 && c < r1) {
+                    if (c != (lower ? i - 1 : i + 1)) kind[sg] = 0;
+                } else {
+                    l = std::max(l, lev[c / 32] + 1);
+                }
+            }
+        }
+        lev[sg] = l;
+        width[sg] = w;
+        nlev = std::max(nlev, l + 1);
+    }
+    std::vector<int> order(nseg);
+    for (int t = 0; t < nseg; ++t) order[t] = lower ? t : nseg - 1 - t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lev[a] < lev[b]; });
+    std::vector<int> sptr(nseg + 1, 0);
+    int64_t nent = 0;
+    for (int sg = 0; sg < nseg; ++sg) {
+        sptr[sg] = (int)nent;
+        nent += (int64_t)width[sg] * 32;
+        if (nent > 0x7fffffffLL) return RS_ERR_INVALID_ARG;
+    }
+    sptr[nseg] = (int)nent;
+    std::vector<int> ecol(nent, -1), esrc(nent, -1);
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int r0 = sg * 32, r1 = std::min(r0 + 32, nrows);
+        for (int i = r0; i < r1; ++i) {
+            const int q0 = lower ? ptr[i] : diag[i] + 1;
+            const int q1 = lower ? diag[i] : ptr[i + 1];
+            for (int q = q0; q < q1; ++q) {
+                const int64_t e = sptr[sg] + (int64_t)(q - q0) * 32 + (i - r0);
+                ecol[e] = col[q];
+                esrc[e] = q;
+            }
+        }
+    }
+    S.nseg = nseg;
+    S.nlevels = nlev;
+    S.nent = nent;
+    int st = RS_OK;
+    st = st ? st : rs_alloc(ctx, (void **)&S.order, sizeof(int) * (nseg > 0 ? nseg : 1));
+    st = st ? st : rs_alloc(ctx, (void **)&S.sptr, sizeof(int) * (nseg + 1));
+    st = st ? st : rs_alloc(ctx, (void **)&S.col, sizeof(int) * (nent > 0 ? nent : 1));
+    st = st ? st : rs_alloc(ctx, (void **)&S.src, sizeof(int) * (nent > 0 ? nent : 1));
+    st = st ? st : rs_alloc(ctx, (void **)&S.kind, nseg > 0 ? nseg : 1);
+    if (st) return st;
+    cudaStream_t sm = ctx->stream;
+    if (nseg) {
+        RS_CUDA_TRY(cudaMemcpyAsync(S.order, order.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, sm));
+        RS_CUDA_TRY(cudaMemcpyAsync(S.kind, kind.data(), nseg, cudaMemcpyHostToDevice, sm));
+    }
+    RS_CUDA_TRY(cudaMemcpyAsync(S.sptr, sptr.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, sm));
+    if (nent) {
+        RS_CUDA_TRY(cudaMemcpyAsync(S.col, ecol.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, sm));
+        RS_CUDA_TRY(cudaMemcpyAsync(S.src, esrc.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, sm));
+    }
+    RS_CUDA_TRY(cudaStreamSynchronize(sm));
+    return RS_OK;
+}
+
+static void free_segments(rs_ctx *ctx, SegLayout &S)
+{
+    rs_free(ctx, S.order);
+    rs_free(ctx, S.sptr);
+    rs_free(ctx, S.col);
+    rs_free(ctx, S.src);
+    rs_free(ctx, S.kind);
+    rs_free(ctx, S.val);
+    rs_free(ctx, S.rdiag);
+    S = SegLayout();
+}
+
 static void free_layout(rs_ctx *ctx, TriLayout &T)
 {
     rs_free(ctx, T.pos);
@@ -397,7 +489,8 @@ __global__ void k_gather_tri(int64_t nent, int b2, const int *__restrict__ src,
     }
 }
 
-// diagonal of U per position: u_ii (scalar) or inv(U_II) (blocks)
+// diagonal of U per position: u_ii (FP32) or 1/u_ii (FP64) for scalars,
+// inv(U_II) for blocks
 template <typename T>
 __global__ void k_gather_diag(int npad, int b2, const int *__restrict__ pos, const int *__restrict__ dsrc,
                               const double *__restrict__ lu, const double *__restrict__ dinv,
@@ -407,7 +500,10 @@ __global__ void k_gather_diag(int npad, int b2, const int *__restrict__ pos, con
         const int row = pos[p];
         for (int x = 0; x < b2; ++x) {
             double v = 1.0;
-            if (row >= 0) v = b2 == 1 ? lu[dsrc[p]] : dinv[(size_t)row * b2 + x];
+            if (row >= 0) {
+                if (b2 > 1) v = dinv[(size_t)row * b2 + x];
+                else v = sizeof(T) == sizeof(double) ? 1.0 / lu[dsrc[p]] : lu[dsrc[p]];
+            }
             diag[(size_t)x * npad + p] = (T)v;
         }
     }
@@ -464,11 +560,15 @@ __device__ __forceinline__ T wait_value(const T *p, long long limit, int *err)
     typedef typename Sentinel<T>::bits_t B;
     B v = ld_relaxed_bits(p);
     if (v != Sentinel<T>::bits) return bits_to(T(), v);
+    for (int spin = 0; spin < 4; ++spin) {
+        v = ld_relaxed_bits(p);
+        if (v != Sentinel<T>::bits) return bits_to(T(), v);
+    }
     const long long t0 = clock64();
-    unsigned ns = 16;
+    unsigned ns = 32;
     for (;;) {
         __nanosleep(ns);
-        if (ns < 128) ns <<= 1;
+        if (ns < 256) ns <<= 1;
         v = ld_relaxed_bits(p);
         if (v != Sentinel<T>::bits) return bits_to(T(), v);
         if (clock64() - t0 > limit) {
@@ -512,15 +612,18 @@ __device__ __forceinline__ void run_rows(const SweepArgs &a, Body body)
 
 #define RS_PREFETCH 4   // sliced-ELL entries loaded ahead of the waits
 
-// Separately rounded multiply and subtract (no contraction into a fused
-// multiply-add), so the sweeps round exactly like a sequential row-by-row
-// solve that evaluates acc - l*y in ascending column order.
-__device__ __forceinline__ double msub(double acc, double a, double b) { return __dsub_rn(acc, __dmul_rn(a, b)); }
+// Arithmetic of the sweeps.  FP32 (the mixed-precision apply): separately
+// rounded multiply and subtract and a true division, in ascending column
+// order — the rounding of a sequential row-by-row solve.  FP64: fused
+// multiply-adds and a multiply by the stored reciprocal of u_ii, because
+// FP64 instructions are scarce on this GPU and sit on the sweep's critical
+// path (one row per level step).
+__device__ __forceinline__ double msub(double acc, double a, double b) { return fma(-a, b, acc); }
 __device__ __forceinline__ float msub(float acc, float a, float b) { return __fsub_rn(acc, __fmul_rn(a, b)); }
-__device__ __forceinline__ double madd(double acc, double a, double b) { return __dadd_rn(acc, __dmul_rn(a, b)); }
+__device__ __forceinline__ double madd(double acc, double a, double b) { return fma(a, b, acc); }
 __device__ __forceinline__ float madd(float acc, float a, float b) { return __fadd_rn(acc, __fmul_rn(a, b)); }
-__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
-__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double udiv(double a, double rdiag) { return a * rdiag; }
+__device__ __forceinline__ float udiv(float a, float diag) { return __fdiv_rn(a, diag); }
 
 // Loads the BS values of every prefetched dependency at once, then polls
 // again only those still holding the sentinel.
@@ -636,7 +739,7 @@ k_usolve(SweepArgs a, const T *__restrict__ val, const T *__restrict__ diag, T *
         }
         T res[BS];
         if (BS == 1) {
-            res[0] = rdiv(acc[0], dg[0]);
+            res[0] = udiv(acc[0], dg[0]);
         } else {
 #pragma unroll
             for (int i = 0; i < BS; ++i) {
@@ -652,6 +755,213 @@ k_usolve(SweepArgs a, const T *__restrict__ val, const T *__restrict__ diag, T *
             out[(size_t)row * BS + k] = (double)res[k];
         }
     });
+}
+
+// ---------------------------------------------------------------------------
+// segment sweeps (scalar factors)
+// ---------------------------------------------------------------------------
+// One warp per segment of 32 consecutive rows, segments taken in level
+// order from a warp-granular ticket.  Each lane subtracts the contributions
+// of its row's columns outside the segment (loaded together, polled on the
+// sentinel).  What remains inside the segment is, for the usual stencils in
+// natural order, a first-order recurrence y_t = c_t + a_t y_{t-1} (L) or
+// z_t = c_t + a_t z_{t+1} (U), solved with a 5-step warp scan of affine
+// maps; any other in-segment pattern is resolved lane by lane with
+// broadcasts.
+struct SegArgs {
+    int nrows, nseg;
+    const int *order, *sptr, *ecol;
+    const unsigned char *kind;
+    SweepState *st;
+    int *err;
+    long long limit;
+    const int *skip;
+};
+
+static SegArgs seg_args(rs_ctx *ctx, const SegLayout &S, int nrows, SweepState *st, const int *skip)
+{
+    SegArgs a;
+    a.nrows = nrows;
+    a.nseg = S.nseg;
+    a.order = S.order;
+    a.sptr = S.sptr;
+    a.ecol = S.col;
+    a.kind = S.kind;
+    a.st = st;
+    a.err = ctx->d_err;
+    a.limit = ctx->spin_limit;
+    a.skip = skip;
+    return a;
+}
+
+#define RS_SEG_CHUNK 8
+
+template <typename T>
+__device__ __forceinline__ T fmadd(T a, T b, T c) { return fma(a, b, c); }
+
+// acc -= sum of v * x[c] over this lane's entries with columns outside
+// [lo, hi); records the coefficient of column `adj` (the adjacent row) in a.
+template <typename T>
+__device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restrict__ val, const T *x,
+                                             int off, int w, int lane, int lo, int hi, int adj,
+                                             T &acc, T &a)
+{
+    typedef typename Sentinel<T>::bits_t B;
+    for (int e0 = 0; e0 < w; e0 += RS_SEG_CHUNK) {
+        int c[RS_SEG_CHUNK];
+        T v[RS_SEG_CHUNK];
+        B b[RS_SEG_CHUNK];
+#pragma unroll
+        for (int j = 0; j < RS_SEG_CHUNK; ++j) {
+            const int idx = off + (e0 + j) * 32 + lane;
+            c[j] = e0 + j < w ? g.ecol[idx] : -1;
+            v[j] = c[j] >= 0 ? val[idx] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < RS_SEG_CHUNK; ++j)
+            b[j] = (c[j] >= 0 && (c[j] < lo || c[j] >= hi)) ? ld_relaxed_bits(x + c[j]) : (B)0;
+#pragma unroll
+        for (int j = 0; j < RS_SEG_CHUNK; ++j) {
+            if (c[j] < 0) continue;
+            if (c[j] < lo || c[j] >= hi) {
+                const T xv = b[j] == Sentinel<T>::bits ? wait_value(x + c[j], g.limit, g.err) : bits_to(T(), b[j]);
+                acc = msub(acc, v[j], xv);
+            } else if (c[j] == adj) {
+                a = -v[j];
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RS_SWEEP_THREADS)
+k_lsolve_seg(SegArgs g, const T *__restrict__ val, const double *__restrict__ r,
+             const double *__restrict__ scale, T *y, T *zreset)
+{
+    if (g.skip && *(volatile const int *)g.skip) return;
+    const int lane = threadIdx.x & 31;
+    const double sc = scale ? *scale : 1.0;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&g.st->ticket, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= g.nseg) break;
+        const int seg = g.order[t];
+        const int row0 = seg * 32, row = row0 + lane;
+        const bool active = row < g.nrows;
+        const int off = g.sptr[seg];
+        const int w = (g.sptr[seg + 1] - off) >> 5;
+        T acc = active ? (T)(sc == 1.0 ? r[row] : r[row] * sc) : T(0);
+        if (active) zreset[row] = bits_to(T(), Sentinel<T>::bits);
+        T a = T(0);
+        seg_external<T>(g, val, y, off, w, lane, row0, row0 + 32, row - 1, acc, a);
+        if (g.kind[seg]) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T ap = __shfl_up_sync(0xffffffffu, a, o);
+                const T bp = __shfl_up_sync(0xffffffffu, acc, o);
+                if (lane >= o) {
+                    acc = fmadd(a, bp, acc);
+                    a = a * ap;
+                }
+            }
+        } else {
+            // lane k is final once lanes 0..k-1 have been applied
+            for (int k = 0; k < 31; ++k) {
+                const T yk = __shfl_sync(0xffffffffu, acc, k);
+                if (lane > k) {
+                    for (int e = 0; e < w; ++e) {
+                        const int idx = off + e * 32 + lane;
+                        if (g.ecol[idx] == row0 + k) acc = msub(acc, val[idx], yk);
+                    }
+                }
+            }
+        }
+        if (active) st_relaxed(y + row, acc);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&g.st->done, 1u) == gridDim.x - 1) {
+            g.st->ticket = 0;
+            g.st->done = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RS_SWEEP_THREADS)
+k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ rdiag, T *y, T *z,
+             double *__restrict__ out)
+{
+    if (g.skip && *(volatile const int *)g.skip) return;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&g.st->ticket, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= g.nseg) break;
+        const int seg = g.order[t];
+        const int row0 = seg * 32, row = row0 + lane;
+        const bool active = row < g.nrows;
+        const int off = g.sptr[seg];
+        const int w = (g.sptr[seg + 1] - off) >> 5;
+        const T rd = active ? rdiag[row] : T(0);
+        T acc = T(0);
+        if (active) {
+            acc = y[row];
+            y[row] = bits_to(T(), Sentinel<T>::bits);
+        }
+        T a = T(0);
+        seg_external<T>(g, val, z, off, w, lane, row0, row0 + 32, row + 1, acc, a);
+        if (g.kind[seg]) {
+            acc = acc * rd;
+            a = a * rd;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T ap = __shfl_down_sync(0xffffffffu, a, o);
+                const T bp = __shfl_down_sync(0xffffffffu, acc, o);
+                if (lane + o < 32) {
+                    acc = fmadd(a, bp, acc);
+                    a = a * ap;
+                }
+            }
+        } else {
+            // lane k is final once lanes k+1..31 have been applied
+            for (int k = 31; k > 0; --k) {
+                const T zk = __shfl_sync(0xffffffffu, acc * rd, k);
+                if (lane < k) {
+                    for (int e = 0; e < w; ++e) {
+                        const int idx = off + e * 32 + lane;
+                        if (g.ecol[idx] == row0 + k) acc = msub(acc, val[idx], zk);
+                    }
+                }
+            }
+            acc = acc * rd;
+        }
+        if (active) {
+            st_relaxed(z + row, acc);
+            out[row] = (double)acc;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&g.st->done, 1u) == gridDim.x - 1) {
+            g.st->ticket = 0;
+            g.st->done = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_gather_rdiag(int nrows, int npad, const int *__restrict__ diagpos,
+                               const double *__restrict__ lu, T *__restrict__ rdiag)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x)
+        rdiag[i] = i < nrows ? (T)(1.0 / lu[diagpos[i]]) : T(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -679,6 +989,13 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
     const size_t esz = fp32 ? sizeof(float) : sizeof(double);
     int st = build_layout(ctx, nrows, h_ptr, h_col, diag, true, f->L);
     st = st ? st : build_layout(ctx, nrows, h_ptr, h_col, diag, false, f->U);
+    if (bs == 1) {
+        st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, f->SL);
+        st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, f->SU);
+        st = st ? st : rs_alloc(ctx, &f->SL.val, esz * (f->SL.nent > 0 ? f->SL.nent : 1));
+        st = st ? st : rs_alloc(ctx, &f->SU.val, esz * (f->SU.nent > 0 ? f->SU.nent : 1));
+        st = st ? st : rs_alloc(ctx, &f->SU.rdiag, esz * ((size_t)f->SU.nseg * 32 > 0 ? (size_t)f->SU.nseg * 32 : 1));
+    }
     st = st ? st : rs_alloc(ctx, (void **)&f->diagpos, sizeof(int) * (nrows > 0 ? nrows : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->lu, sizeof(double) * b2 * (nnzb > 0 ? nnzb : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->dinv, sizeof(double) * b2 * (nrows > 0 ? nrows : 1));
@@ -719,6 +1036,8 @@ void rs_ilu_destroy(IluFactor *f)
     rs_ctx *ctx = f->ctx;
     free_layout(ctx, f->L);
     free_layout(ctx, f->U);
+    free_segments(ctx, f->SL);
+    free_segments(ctx, f->SU);
     rs_free(ctx, f->diagpos);
     rs_free(ctx, f->lu);
     rs_free(ctx, f->dinv);
@@ -745,6 +1064,7 @@ int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row)
                                 ctx->stream));
     const int g = sweep_grid(ctx, f->L.npad);
     const SweepArgs a = sweep_args(ctx, f->L, f->state, nullptr);
+    RsProfScope prof(ctx, RS_PROF_FACTOR);
     switch (f->bs) {
     case 1:
         k_ilu0_factor<<<g, RS_SWEEP_THREADS, 0, ctx->stream>>>(a, f->ptr, f->col, f->diagpos, f->lu,
@@ -779,7 +1099,45 @@ int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row)
     }
     RS_TRY(rs_check_launch(ctx));
     ctx->launches += 2;
+    if (f->bs == 1) {
+        const int gl = (int)std::min<int64_t>(std::max<int64_t>((f->SL.nent + 255) / 256, 1), 4096);
+        const int gu2 = (int)std::min<int64_t>(std::max<int64_t>((f->SU.nent + 255) / 256, 1), 4096);
+        const int np = f->SU.nseg * 32;
+        const int gr = std::max(1, std::min((np + 255) / 256, 4096));
+        if (f->fp32) {
+            k_gather_tri<float><<<gl, 256, 0, ctx->stream>>>(f->SL.nent, 1, f->SL.src, f->lu, (float *)f->SL.val);
+            k_gather_tri<float><<<gu2, 256, 0, ctx->stream>>>(f->SU.nent, 1, f->SU.src, f->lu, (float *)f->SU.val);
+            k_gather_rdiag<float><<<gr, 256, 0, ctx->stream>>>(f->nrows, np, f->diagpos, f->lu, (float *)f->SU.rdiag);
+        } else {
+            k_gather_tri<double><<<gl, 256, 0, ctx->stream>>>(f->SL.nent, 1, f->SL.src, f->lu, (double *)f->SL.val);
+            k_gather_tri<double><<<gu2, 256, 0, ctx->stream>>>(f->SU.nent, 1, f->SU.src, f->lu, (double *)f->SU.val);
+            k_gather_rdiag<double><<<gr, 256, 0, ctx->stream>>>(f->nrows, np, f->diagpos, f->lu, (double *)f->SU.rdiag);
+        }
+        RS_TRY(rs_check_launch(ctx));
+        ctx->launches += 2;
+    }
     return rs_collect_device_error(ctx, bad_row);
+}
+
+template <typename T>
+static int apply_seg(IluFactor *f, const double *r, double *z, const double *scale, const int *skip)
+{
+    rs_ctx *ctx = f->ctx;
+    T *y = (T *)f->ywork, *zt = (T *)f->zwork;
+    const int wpb = RS_SWEEP_THREADS / 32;
+    const int gl = std::max(1, std::min((f->SL.nseg + wpb - 1) / wpb, ctx->sweep_blocks));
+    const int gu = std::max(1, std::min((f->SU.nseg + wpb - 1) / wpb, ctx->sweep_blocks));
+    {
+        RsProfScope prof(ctx, RS_PROF_LSWEEP);
+        k_lsolve_seg<T><<<gl, RS_SWEEP_THREADS, 0, ctx->stream>>>(seg_args(ctx, f->SL, f->nrows, f->state, skip),
+                                                                  (const T *)f->SL.val, r, scale, y, zt);
+    }
+    RS_TRY(rs_check_launch(ctx));
+    RsProfScope prof(ctx, RS_PROF_USWEEP);
+    k_usolve_seg<T><<<gu, RS_SWEEP_THREADS, 0, ctx->stream>>>(seg_args(ctx, f->SU, f->nrows, f->state, skip),
+                                                              (const T *)f->SU.val, (const T *)f->SU.rdiag,
+                                                              y, zt, z);
+    return rs_check_launch(ctx);
 }
 
 template <int BS, typename T>
@@ -788,6 +1146,7 @@ static int apply_typed(IluFactor *f, const double *r, double *z, const double *s
     rs_ctx *ctx = f->ctx;
     T *y = (T *)f->ywork;
     T *zt = (T *)f->zwork;
+    RsProfScope prof(ctx, RS_PROF_LSWEEP);
     k_lsolve<BS, T, double><<<sweep_grid(ctx, f->L.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
         sweep_args(ctx, f->L, f->state, skip), (const T *)f->L.val, r, scale, y, zt);
     RS_TRY(rs_check_launch(ctx));
@@ -800,7 +1159,7 @@ int rs_ilu_apply(IluFactor *f, const double *r, double *z, const double *scale, 
 {
     if (f->nrows == 0) return RS_OK;
     switch (f->bs) {
-    case 1: return f->fp32 ? apply_typed<1, float>(f, r, z, scale, skip) : apply_typed<1, double>(f, r, z, scale, skip);
+    case 1: return f->fp32 ? apply_seg<float>(f, r, z, scale, skip) : apply_seg<double>(f, r, z, scale, skip);
     case 2: return f->fp32 ? apply_typed<2, float>(f, r, z, scale, skip) : apply_typed<2, double>(f, r, z, scale, skip);
     case 3: return f->fp32 ? apply_typed<3, float>(f, r, z, scale, skip) : apply_typed<3, double>(f, r, z, scale, skip);
     case 4: return f->fp32 ? apply_typed<4, float>(f, r, z, scale, skip) : apply_typed<4, double>(f, r, z, scale, skip);

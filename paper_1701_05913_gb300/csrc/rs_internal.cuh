@@ -39,6 +39,27 @@ void rs_set_last_cuda_error(cudaError_t e);
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------
+// kernel classes timed by the optional event profiler
+enum RsProfKind {
+    RS_PROF_SPMV = 0,
+    RS_PROF_LSWEEP,
+    RS_PROF_USWEEP,
+    RS_PROF_CGS_DOTS,
+    RS_PROF_CGS_UPDATE_DOTS,
+    RS_PROF_CGS_UPDATE_NORM,
+    RS_PROF_BLAS1,
+    RS_PROF_PRECOND_OTHER,
+    RS_PROF_FACTOR,
+    RS_PROF_SOLVER_SCALAR,
+    RS_PROF_NET,
+    RS_PROF_NKINDS
+};
+
+struct RsProfRec {
+    int kind;
+    cudaEvent_t ev0, ev1;
+};
+
 struct rs_ctx {
     int device;
     cudaStream_t stream;
@@ -53,6 +74,21 @@ struct rs_ctx {
     long long launches;
     long long spin_limit;    // clock cycles a device-side wait may take
     int sweep_blocks;        // resident blocks of the persistent triangular sweeps
+    // event profiler (off unless rs_prof_enable)
+    int prof_on;
+    std::vector<RsProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[RS_PROF_NKINDS];
+    long long prof_count[RS_PROF_NKINDS];
+};
+
+// Records an event pair around the launches in its scope when profiling is on.
+struct RsProfScope {
+    rs_ctx *ctx;
+    int kind;
+    cudaEvent_t ev1;
+    RsProfScope(rs_ctx *c, int k);
+    ~RsProfScope();
 };
 
 struct rs_mat {
@@ -104,6 +140,22 @@ struct TriLayout {
     int *level_done = nullptr;   // [nlevels] epoch of the sweep that last completed the level
 };
 
+// Segment layout of one scalar triangular factor: segments of 32
+// consecutive rows (one warp each), ordered by their level in the segment
+// dependency graph, entries stored as sliced ELL per segment.
+struct SegLayout {
+    int nseg = 0;
+    int nlevels = 0;
+    int64_t nent = 0;
+    int *order = nullptr;          // [nseg] segment ids in processing order
+    int *sptr = nullptr;           // [nseg+1] first entry of each segment (by id)
+    int *col = nullptr;            // [nent] column or -1
+    int *src = nullptr;            // [nent] index of the entry in the CSR value array or -1
+    unsigned char *kind = nullptr; // [nseg] 1: the only in-segment dependency is the adjacent row
+    void *val = nullptr;           // [nent] factor values (float or double)
+    void *rdiag = nullptr;         // [nseg*32] U: 1 / u_ii by row
+};
+
 // ILU(0) / block ILU(0) of one matrix pattern.
 struct IluFactor {
     rs_ctx *ctx = nullptr;
@@ -115,7 +167,8 @@ struct IluFactor {
     int *diagpos = nullptr;  // [nrows]
     double *lu = nullptr;    // [nnzb*bs*bs] FP64 factors in the matrix pattern
     double *dinv = nullptr;  // [nrows*bs*bs] inverted diagonal blocks (bs > 1)
-    TriLayout L, U;
+    TriLayout L, U;          // row-level schedules (factorisation; block sweeps)
+    SegLayout SL, SU;        // segment layouts of the scalar sweeps
     int *flags = nullptr;    // [nrows] sweep flags
     SweepState *state = nullptr;
     void *ywork = nullptr;   // [nrows*bs] intermediate of the L sweep

@@ -90,8 +90,8 @@ k_cgs_dots(int n, int ld, int nc, const double *__restrict__ V, const double *__
         const double wr = w[r];
 #pragma unroll
         for (int k = 0; k < NC; ++k)
-            if (k < nc) acc[k] = __dadd_rn(acc[k], __dmul_rn(V[(size_t)k * ld + r], wr));
-        acc[NC] = __dadd_rn(acc[NC], __dmul_rn(wr, wr));
+            if (k < nc) acc[k] = fma(V[(size_t)k * ld + r], wr, acc[k]);
+        acc[NC] = fma(wr, wr, acc[NC]);
     }
     // move the norm into slot nc so the reduction covers slots 0..nc
 #pragma unroll
@@ -123,14 +123,14 @@ k_cgs_update_dots(int n, int ld, int nc, const double *__restrict__ V, double *_
         for (int k = 0; k < NC; ++k) {
             if (k < nc) {
                 v[k] = V[(size_t)k * ld + r];
-                s = __dadd_rn(s, __dmul_rn(v[k], hs[k]));
+                s = fma(v[k], hs[k], s);
             }
         }
-        const double w1 = __dsub_rn(w[r], s);
+        const double w1 = w[r] - s;
         w[r] = w1;
 #pragma unroll
         for (int k = 0; k < NC; ++k)
-            if (k < nc) acc[k] = __dadd_rn(acc[k], __dmul_rn(v[k], w1));
+            if (k < nc) acc[k] = fma(v[k], w1, acc[k]);
     }
     if (reduce_partials<NC>(acc, nc, partials, ticket, d->h2)) {
         const int i = nc - 1, m1 = d->m + 1;
@@ -153,10 +153,10 @@ k_cgs_update_norm(int n, int ld, int nc, const double *__restrict__ V, double *_
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < NC; ++k)
-            if (k < nc) s = __dadd_rn(s, __dmul_rn(V[(size_t)k * ld + r], hs[k]));
-        const double w2 = __dsub_rn(w[r], s);
+            if (k < nc) s = fma(V[(size_t)k * ld + r], hs[k], s);
+        const double w2 = w[r] - s;
         w[r] = w2;
-        acc[0] = __dadd_rn(acc[0], __dmul_rn(w2, w2));
+        acc[0] = fma(w2, w2, acc[0]);
     }
     if (reduce_partials<1>(acc, 1, partials, ticket, &d->r2)) {
         if (threadIdx.x == 0) {
@@ -181,7 +181,7 @@ k_cgs_update_norm(int n, int ld, int nc, const double *__restrict__ V, double *_
             const bool happy = hnext <= 1e-14 * sqrt(d->w0sq);
             if (d->implicit <= d->tol || d->iters >= d->maxit || happy || i == d->m - 1)
                 d->cycle_done = 1;
-            d->hdiv = hnext;     // v_{i+1} = w / h_{i+1,i}
+            d->hdiv = 1.0 / hnext;     // v_{i+1} = w / h_{i+1,i}
         }
     }
 }
@@ -197,18 +197,18 @@ __global__ void k_basis_combine(int n, int ld, const double *__restrict__ B, con
     __syncthreads();
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int j = 0; j < k; ++j) s = __dadd_rn(s, __dmul_rn(B[(size_t)j * ld + r], ys[j]));
+        for (int j = 0; j < k; ++j) s = fma(B[(size_t)j * ld + r], ys[j], s);
         x[r] = add ? __dadd_rn(x[r], s) : s;
     }
 }
 
-// v = r / s with s a device scalar (a division, as the normalisation is written)
+// v = s * r with s a device scalar (the reciprocal of the normalising norm)
 __global__ void k_scale_dev(int n, const double *__restrict__ r, const double *__restrict__ s,
                             double *__restrict__ v, const int *skip)
 {
     if (skip && *(volatile const int *)skip) return;
     const double a = *s;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = __ddiv_rn(r[i], a);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = r[i] * a;
 }
 
 __global__ void k_axpy_skip(int n, const double *__restrict__ x, double *__restrict__ y, const int *skip)
@@ -233,7 +233,7 @@ __global__ void k_gmres_start(GmresDev *d, const double *r2, double rtol, int fi
     for (int j = 1; j <= d->m; ++j) d->g[j] = 0.0;
     d->k = 0;
     d->noupd = 1;
-    d->hdiv = beta;      // v_1 = r / beta
+    d->hdiv = 1.0 / beta;      // v_1 = r / beta
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k) by back-substitution
@@ -243,7 +243,7 @@ __global__ void k_gmres_backsolve(GmresDev *d)
     const int k = d->k, m1 = d->m + 1;
     for (int j = k - 1; j >= 0; --j) {
         double s = d->g[j];
-        for (int l = j + 1; l < k; ++l) s = __dsub_rn(s, __dmul_rn(d->H[(size_t)l * m1 + j], d->y[l]));
+        for (int l = j + 1; l < k; ++l) s = fma(-d->H[(size_t)l * m1 + j], d->y[l], s);
         d->y[j] = __ddiv_rn(s, d->H[(size_t)j * m1 + j]);
     }
     d->noupd = k == 0;
@@ -261,8 +261,15 @@ static void launch_cgs(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *
 {
     double *w = V + (size_t)nc * ld;
     const int g = red_grid(ctx);
-    k_cgs_dots<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
-    k_cgs_update_dots<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
+    {
+        RsProfScope prof(ctx, RS_PROF_CGS_DOTS);
+        k_cgs_dots<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
+    }
+    {
+        RsProfScope prof(ctx, RS_PROF_CGS_UPDATE_DOTS);
+        k_cgs_update_dots<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
+    }
+    RsProfScope prof(ctx, RS_PROF_CGS_UPDATE_NORM);
     k_cgs_update_norm<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
 }
 
@@ -455,27 +462,27 @@ k_bicg(int op, int n, double *p, double *r, const double *__restrict__ v, double
     double acc[2] = {0.0, 0.0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         switch (op) {
-        case 0: p[i] = __dadd_rn(r[i], __dmul_rn(beta, __dsub_rn(p[i], __dmul_rn(omega, v[i])))); break;
+        case 0: p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]); break;
         case 1: {
-            const double si = __dsub_rn(r[i], __dmul_rn(alpha, v[i]));
+            const double si = fma(-alpha, v[i], r[i]);
             s[i] = si;
-            acc[0] = __dadd_rn(acc[0], __dmul_rn(si, si));
+            acc[0] = fma(si, si, acc[0]);
             break;
         }
         case 2: {
-            x[i] = __dadd_rn(__dadd_rn(x[i], __dmul_rn(alpha, ph[i])), __dmul_rn(omega, sh[i]));
-            const double ri = __dsub_rn(s[i], __dmul_rn(omega, t[i]));
+            x[i] = fma(omega, sh[i], fma(alpha, ph[i], x[i]));
+            const double ri = fma(-omega, t[i], s[i]);
             r[i] = ri;
-            acc[0] = __dadd_rn(acc[0], __dmul_rn(rh[i], ri));
-            acc[1] = __dadd_rn(acc[1], __dmul_rn(ri, ri));
+            acc[0] = fma(rh[i], ri, acc[0]);
+            acc[1] = fma(ri, ri, acc[1]);
             break;
         }
-        case 3: acc[0] = __dadd_rn(acc[0], __dmul_rn(rh[i], v[i])); break;
+        case 3: acc[0] = fma(rh[i], v[i], acc[0]); break;
         case 4:
-            acc[0] = __dadd_rn(acc[0], __dmul_rn(t[i], s[i]));
-            acc[1] = __dadd_rn(acc[1], __dmul_rn(t[i], t[i]));
+            acc[0] = fma(t[i], s[i], acc[0]);
+            acc[1] = fma(t[i], t[i], acc[1]);
             break;
-        case 5: x[i] = __dadd_rn(x[i], __dmul_rn(alpha, ph[i])); break;
+        case 5: x[i] = fma(alpha, ph[i], x[i]); break;
         }
     }
     if (op == 0) return;
