@@ -89,6 +89,11 @@ extern "C" int rs_init(rs_ctx **out, int device, void *stream)
     cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, device);
     c->spin_limit = (long long)clock_khz * 1000LL * 2;   // about two seconds
     c->sweep_blocks = 4 * c->num_sms;
+    c->sleep_cap_ns = 256;
+    if (const char *e = getenv("RS_SWEEP_SLEEP_CAP_NS")) {
+        const int v = atoi(e);
+        if (v >= 16 && v <= 100000) c->sleep_cap_ns = (unsigned)v;
+    }
     if (const char *e = getenv("RS_SWEEP_BLOCKS_PER_SM")) {
         const int v = atoi(e);
         if (v >= 1 && v <= 16) c->sweep_blocks = v * c->num_sms;

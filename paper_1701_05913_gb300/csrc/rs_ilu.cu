@@ -770,6 +770,7 @@ k_usolve(SweepArgs a, const T *__restrict__ val, const T *__restrict__ diag, T *
 // broadcasts.
 struct SegArgs {
     int nrows, nseg;
+    unsigned sleep_cap;
     const int *order, *sptr, *ecol;
     const unsigned char *kind;
     SweepState *st;
@@ -783,6 +784,7 @@ static SegArgs seg_args(rs_ctx *ctx, const SegLayout &S, int nrows, SweepState *
     SegArgs a;
     a.nrows = nrows;
     a.nseg = S.nseg;
+    a.sleep_cap = ctx->sleep_cap_ns;
     a.order = S.order;
     a.sptr = S.sptr;
     a.ecol = S.col;
@@ -801,6 +803,9 @@ __device__ __forceinline__ T fmadd(T a, T b, T c) { return fma(a, b, c); }
 
 // acc -= sum of v * x[c] over this lane's entries with columns outside
 // [lo, hi); records the coefficient of column `adj` (the adjacent row) in a.
+// All lanes load their outside values at once; while any lane still sees a
+// sentinel the whole warp sleeps once and reloads only the pending values,
+// so the warp stays converged and polls with coalesced loads.
 template <typename T>
 __device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restrict__ val, const T *x,
                                              int off, int w, int lane, int lo, int hi, int adj,
@@ -811,6 +816,7 @@ __device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restri
         int c[RS_SEG_CHUNK];
         T v[RS_SEG_CHUNK];
         B b[RS_SEG_CHUNK];
+        bool ext[RS_SEG_CHUNK];
 #pragma unroll
         for (int j = 0; j < RS_SEG_CHUNK; ++j) {
             const int idx = off + (e0 + j) * 32 + lane;
@@ -818,17 +824,36 @@ __device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restri
             v[j] = c[j] >= 0 ? val[idx] : T(0);
         }
 #pragma unroll
-        for (int j = 0; j < RS_SEG_CHUNK; ++j)
-            b[j] = (c[j] >= 0 && (c[j] < lo || c[j] >= hi)) ? ld_relaxed_bits(x + c[j]) : (B)0;
+        for (int j = 0; j < RS_SEG_CHUNK; ++j) {
+            ext[j] = c[j] >= 0 && (c[j] < lo || c[j] >= hi);
+            b[j] = ext[j] ? ld_relaxed_bits(x + c[j]) : (B)0;
+        }
+        unsigned ns = 0;
+        long long t0 = 0;
+        for (;;) {
+            bool pend = false;
+#pragma unroll
+            for (int j = 0; j < RS_SEG_CHUNK; ++j) pend |= ext[j] && b[j] == Sentinel<T>::bits;
+            if (!__any_sync(0xffffffffu, pend)) break;
+            if (ns == 0) {
+                t0 = clock64();
+            } else {
+                if (clock64() - t0 > g.limit) {
+                    if (pend) atomicOr(g.err, RS_DEVERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(ns);
+            }
+            ns = ns == 0 ? 16 : min(ns * 2, g.sleep_cap);
+#pragma unroll
+            for (int j = 0; j < RS_SEG_CHUNK; ++j)
+                if (ext[j] && b[j] == Sentinel<T>::bits) b[j] = ld_relaxed_bits(x + c[j]);
+        }
 #pragma unroll
         for (int j = 0; j < RS_SEG_CHUNK; ++j) {
             if (c[j] < 0) continue;
-            if (c[j] < lo || c[j] >= hi) {
-                const T xv = b[j] == Sentinel<T>::bits ? wait_value(x + c[j], g.limit, g.err) : bits_to(T(), b[j]);
-                acc = msub(acc, v[j], xv);
-            } else if (c[j] == adj) {
-                a = -v[j];
-            }
+            if (ext[j]) acc = msub(acc, v[j], bits_to(T(), b[j]));
+            else if (c[j] == adj) a = -v[j];
         }
     }
 }

@@ -74,6 +74,7 @@ struct rs_ctx {
     long long launches;
     long long spin_limit;    // clock cycles a device-side wait may take
     int sweep_blocks;        // resident blocks of the persistent triangular sweeps
+    unsigned sleep_cap_ns;   // longest back-off of a polling warp
     // event profiler (off unless rs_prof_enable)
     int prof_on;
     std::vector<RsProfRec> prof_pending;
