@@ -131,6 +131,21 @@ int rs_vec_dot(const rs_vec *x, const rs_vec *y, double *out);
 /* *out = ||x||_2. */
 int rs_vec_norm2(const rs_vec *x, double *out);
 
+/* h[j] = <V_j, w> for the k columns V_j (column j at V + j*ld, n entries
+ * each), like the first pass of the CGS2 step, but without allocating any
+ * device memory: for callers that cannot call cudaMalloc (work recorded
+ * while a stream is captured into a graph, hosts that own all device
+ * memory).  The paper has no counterpart; this is a service of the library.
+ * All pointers are device pointers; the call is ordered on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream) and does not synchronise.
+ * Its scratch is a fixed static device array (512 KB per GPU that loads the
+ * library, held until exit), shared by every call: calls that overlap on the
+ * GPU race.  1 <= k <= 64 (larger k returns RS_ERR_INVALID_ARG); ld >= n.
+ * The first call on a device looks up the array's device address; make it
+ * before any stream capture. */
+int rs_vec_mdot_noalloc(const double *V, int32_t ld, int32_t n, int32_t k, const double *w,
+                        double *h, void *cuda_stream);
+
 /* ---- matrices (Sec. 2.3) ---------------------------------------------- */
 
 /* MatCreate/MatAssemble (Figs. 16-19) for an n x n CSR matrix:

@@ -70,6 +70,7 @@ SIGNATURES = [
     ("rs_vec_axpbyz", C.c_int, [C.c_double, _vp, C.c_double, _vp, _vp]),
     ("rs_vec_dot", C.c_int, [_vp, _vp, _f64p]),
     ("rs_vec_norm2", C.c_int, [_vp, _f64p]),
+    ("rs_vec_mdot_noalloc", C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     ("rs_mat_create_csr", C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, C.c_int, C.POINTER(_vp)]),
     ("rs_mat_create_bsr", C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_int,
                                     C.POINTER(_vp)]),
