@@ -209,6 +209,38 @@ int rs_solve_fgmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32
 int rs_solve_bicgstab(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, double rtol,
                       int32_t maxit, rs_solve_info *info);
 
+/* ---- learned pressure stage ------------------------------------------- */
+/* A 3-D U-Net (4 levels, 16 channels, 3x3x3 convolutions, ReLU, 2x2x2
+ * average pooling, nearest x2 upsampling with skip concatenation, 1x1x1
+ * head) with bfloat16 weights and activations and FP32 accumulation; not in
+ * the paper, it replaces the pressure stage of the CPR preconditioner
+ * (RS_PC_CPR_LEARNED).  Input channels: r / rms(r) and log-permeability;
+ * output: net * rms(r) * out_scale, an approximation of A^{-1} r.
+ * Parameters (FP32, host) are laid out layer by layer (e0a, e0b, e1a, e1b,
+ * e2a, e2b, e3a, e3b, d2a, d2b, d1a, d1b, d0a, d0b): weights
+ * [dz][dy][dx][cout][cin] then bias [cout]; then the head's 16 weights and
+ * its bias.  Grid dimensions must be multiples of 8. */
+int64_t rs_net_num_params(void);
+int rs_net_create(rs_ctx *ctx, const float *params, int64_t nparams, float out_scale, rs_net **net);
+int rs_net_destroy(rs_net **net);
+int rs_net_get_params(const rs_net *net, float *params_host, int64_t n);
+int rs_net_get_grads(const rs_net *net, float *grads_host, int64_t n);
+int rs_net_zero_grads(rs_net *net);
+/* out = network(r, logk) on an nx x ny x nz grid (device pointers, FP64,
+ * x fastest). */
+int rs_net_forward(rs_net *net, int32_t nx, int32_t ny, int32_t nz, const double *r, const double *logk,
+                   double *out);
+/* One training sample: forward, loss ||out - e||^2 / ||e||^2, backward;
+ * adds weight * dloss/dparams to the gradient; *loss_host (optional,
+ * synchronises) receives the loss. */
+int rs_net_accumulate(rs_net *net, int32_t nx, int32_t ny, int32_t nz, const double *r, const double *logk,
+                      const double *e, double weight, double *loss_host);
+/* Adam step on the accumulated gradient, which it then clears. */
+int rs_net_adam(rs_net *net, float lr, float beta1, float beta2, float eps);
+/* Checkpoint: parameters, Adam moments, step count and output scale. */
+int rs_net_save(const rs_net *net, const char *path);
+int rs_net_load(rs_ctx *ctx, const char *path, rs_net **net);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,18 @@ SIGNATURES = [
                                   C.POINTER(SolveInfo)]),
     ("rs_solve_bicgstab", C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int32,
                                     C.POINTER(SolveInfo)]),
+    ("rs_net_num_params", C.c_int64, []),
+    ("rs_net_create", C.c_int, [_vp, _f32p, C.c_int64, C.c_float, C.POINTER(_vp)]),
+    ("rs_net_destroy", C.c_int, [C.POINTER(_vp)]),
+    ("rs_net_get_params", C.c_int, [_vp, _f32p, C.c_int64]),
+    ("rs_net_get_grads", C.c_int, [_vp, _f32p, C.c_int64]),
+    ("rs_net_zero_grads", C.c_int, [_vp]),
+    ("rs_net_forward", C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp]),
+    ("rs_net_accumulate", C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_double,
+                                    C.POINTER(C.c_double)]),
+    ("rs_net_adam", C.c_int, [_vp, C.c_float, C.c_float, C.c_float, C.c_float]),
+    ("rs_net_save", C.c_int, [_vp, C.c_char_p]),
+    ("rs_net_load", C.c_int, [_vp, C.c_char_p, C.POINTER(_vp)]),
 ]
 
 _lib = None
@@ -271,7 +283,7 @@ class Precond:
         opts.prec = MIXED if prec == "mixed" else FP64
         self._keep = []
         if net is not None:
-            opts.net = net.h
+            opts.net = net.h.value
             lp = _dev_f64(log_perm)
             self._keep += [net, lp]
             opts.log_perm = lp.data_ptr()
@@ -310,6 +322,90 @@ class Precond:
         try:
             if self.h:
                 lib().rs_precond_destroy(C.byref(self.h))
+        except Exception:
+            pass
+
+
+NET_LAYERS = [("e0a", 2), ("e0b", 16), ("e1a", 16), ("e1b", 16), ("e2a", 16), ("e2b", 16),
+              ("e3a", 16), ("e3b", 16), ("d2a", 32), ("d2b", 16), ("d1a", 32), ("d1b", 16),
+              ("d0a", 32), ("d0b", 16)]
+
+
+def net_flatten(params: dict) -> np.ndarray:
+    """Flat FP32 parameter vector in the layout rs_net_create expects, from a
+    dict of arrays: name.W (3, 3, 3, 16, cin), name.b (16,), head.W (1, 16),
+    head.b (1,)."""
+    parts = []
+    for name, cin in NET_LAYERS:
+        parts += [np.asarray(params[name + ".W"]).reshape(-1), np.asarray(params[name + ".b"]).reshape(-1)]
+    parts += [np.asarray(params["head.W"]).reshape(-1), np.asarray(params["head.b"]).reshape(-1)]
+    return np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)
+
+
+def net_unflatten(flat) -> dict:
+    flat = np.asarray(flat, dtype=np.float64)
+    out, off = {}, 0
+    for name, cin in NET_LAYERS:
+        n = 27 * 16 * cin
+        out[name + ".W"] = flat[off:off + n].reshape(3, 3, 3, 16, cin)
+        off += n
+        out[name + ".b"] = flat[off:off + 16].copy()
+        off += 16
+    out["head.W"] = flat[off:off + 16].reshape(1, 16)
+    out["head.b"] = flat[off + 16:off + 17].copy()
+    return out
+
+
+class Net:
+    """The learned pressure-stage network (rs_net_*)."""
+
+    def __init__(self, ctx: Context, params: dict | None = None, out_scale: float = 1.0, path: str | None = None):
+        self.ctx = ctx
+        self.h = _vp()
+        if path is not None:
+            _check(lib().rs_net_load(ctx.h, path.encode(), C.byref(self.h)), "rs_net_load")
+        else:
+            flat = net_flatten(params)
+            _check(lib().rs_net_create(ctx.h, flat.ctypes.data_as(_f32p), flat.size, out_scale, C.byref(self.h)),
+                   "rs_net_create")
+        self.n = lib().rs_net_num_params()
+
+    def params(self) -> dict:
+        out = np.empty(self.n, dtype=np.float32)
+        _check(lib().rs_net_get_params(self.h, out.ctypes.data_as(_f32p), self.n), "rs_net_get_params")
+        return net_unflatten(out)
+
+    def grads(self) -> dict:
+        out = np.empty(self.n, dtype=np.float32)
+        _check(lib().rs_net_get_grads(self.h, out.ctypes.data_as(_f32p), self.n), "rs_net_get_grads")
+        return net_unflatten(out)
+
+    def zero_grads(self):
+        _check(lib().rs_net_zero_grads(self.h), "rs_net_zero_grads")
+
+    def forward(self, grid, r, logk, out):
+        nx, ny, nz = grid
+        _check(lib().rs_net_forward(self.h, nx, ny, nz, _vp(r.data_ptr()), _vp(logk.data_ptr()),
+                                    _vp(out.data_ptr())), "rs_net_forward")
+
+    def accumulate(self, grid, r, logk, e, weight=1.0, want_loss=False):
+        nx, ny, nz = grid
+        loss = C.c_double(0.0)
+        _check(lib().rs_net_accumulate(self.h, nx, ny, nz, _vp(r.data_ptr()), _vp(logk.data_ptr()),
+                                       _vp(e.data_ptr()), weight, C.byref(loss) if want_loss else None),
+               "rs_net_accumulate")
+        return loss.value if want_loss else None
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().rs_net_adam(self.h, lr, beta1, beta2, eps), "rs_net_adam")
+
+    def save(self, path):
+        _check(lib().rs_net_save(self.h, path.encode()), "rs_net_save")
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().rs_net_destroy(C.byref(self.h))
         except Exception:
             pass
 

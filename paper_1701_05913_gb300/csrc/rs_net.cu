@@ -1,8 +1,1116 @@
-// Learned pressure stage (placeholder until the network kernels land).
+// Learned pressure stage: a 3-D U-Net (4 levels, 16 channels, 3x3x3
+// convolutions, ReLU, 2x2x2 average pooling, nearest x2 upsampling with skip
+// concatenation, 1x1x1 head) evaluated and trained with BF16 tensor-core
+// kernels and FP32 accumulation.  The paper has no learned component; the
+// stage replaces the pressure solve M_p^{-1} of the two-stage CPR
+// preconditioner (Alg. 6 as read in rs_precond.cu) inside FGMRES.
+//
+// Activations are NDHWC bfloat16 (16 channels, 32 bytes per voxel).  Every
+// 3x3x3 convolution is an implicit GEMM: a block stages a 16x4x4 output
+// brick's 18x6x6 input halo and the 27 weight taps in shared memory, and each
+// warp multiplies 16-voxel x-rows (M) by 16 output channels (N) over
+// K = 27 taps x channels with mma.m16n8k16 (bf16 in, f32 accumulate),
+// fragments loaded with ldmatrix.  The data gradient is the same kernel with
+// flipped, transposed weights; the weight gradient multiplies the output
+// gradient (transposed with ldmatrix.trans) by the shifted input per tap.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "rs_internal.cuh"
 
+typedef __nv_bfloat16 bf16;
+
+#define NET_CH 16
+#define NET_LEVELS 4
+#define NET_NLAYERS 14
+#define TX 16
+#define TY 4
+#define TZ 4
+#define TVOX (TX * TY * TZ)
+#define HX (TX + 2)
+#define HY (TY + 2)
+#define HZ (TZ + 2)
+#define HVOX (HX * HY * HZ)
+#define CONV_THREADS 256
+#define NET_MAGIC 0x52534e31u   // file tag of saved networks
+
+enum { IN_PLAIN = 0, IN_CATUP = 1, IN_FIRST = 2 };
+
+// layer table: cin (real), kind of input, level
+struct LayerDef {
+    int cin;
+    int mode;
+    int level;
+};
+static const LayerDef kLayers[NET_NLAYERS] = {
+    {2, IN_FIRST, 0},  {16, IN_PLAIN, 0},   // e0a e0b
+    {16, IN_PLAIN, 1}, {16, IN_PLAIN, 1},   // e1a e1b
+    {16, IN_PLAIN, 2}, {16, IN_PLAIN, 2},   // e2a e2b
+    {16, IN_PLAIN, 3}, {16, IN_PLAIN, 3},   // e3a e3b
+    {32, IN_CATUP, 2}, {16, IN_PLAIN, 2},   // d2a d2b
+    {32, IN_CATUP, 1}, {16, IN_PLAIN, 1},   // d1a d1b
+    {32, IN_CATUP, 0}, {16, IN_PLAIN, 0},   // d0a d0b
+};
+enum { E0A, E0B, E1A, E1B, E2A, E2B, E3A, E3B, D2A, D2B, D1A, D1B, D0A, D0B };
+
+static int cin_pad(int l) { return kLayers[l].cin < 16 ? 16 : kLayers[l].cin; }
+
+struct Level {
+    int nx, ny, nz;
+    int64_t nvox;
+};
+
+struct rs_net {
+    rs_ctx *ctx;
+    float out_scale;
+    int64_t nparams;
+    int64_t woff[NET_NLAYERS], boff[NET_NLAYERS], hoff;   // offsets in the flat parameter vector
+    float *p, *g, *m, *v;                                   // FP32 master, gradient, Adam moments
+    int step;
+    bf16 *wf[NET_NLAYERS];   // forward weights [27][16][cinp]
+    bf16 *wb[NET_NLAYERS];   // data-gradient weights [27][cin][16] (flipped taps)
+    // workspace for the current grid
+    int nx, ny, nz;
+    Level lv[NET_LEVELS];
+    bf16 *act[NET_NLAYERS];                 // layer outputs
+    bf16 *pool[NET_LEVELS];                 // pooled inputs of e1a, e2a, e3a
+    bf16 *g16a[NET_LEVELS], *g16b[NET_LEVELS], *g32[NET_LEVELS];
+    float *partials;                        // weight-gradient partials
+    int64_t partials_len;
+    double *scal;                           // [0] rms, [1] 1/rms, [2] loss, [3..] reduction scratch
+    double *red;                            // per-block reduction partials
+    unsigned *ticket;
+    int *flag;                              // non-finite output flag
+    double *gout;                           // dL/d(output) (per voxel)
+    double *outb;                           // network output during training
+    float *headpart;                        // head gradient partials
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ bool skipped(const int *skip) { return skip && *(volatile const int *)skip; }
+
+// ---------------------------------------------------------------------------
+// halo loader shared by the convolution kernels
+// ---------------------------------------------------------------------------
+// Loads the 18x6x6 input halo of the brick at (tx0, ty0, tz0) into sx
+// (stride SIN bf16 per voxel), zero outside the grid.
+template <int CIN, int MODE>
+__device__ __forceinline__ void load_halo(bf16 *sx, int SIN, int D, int H, int W, int tx0, int ty0, int tz0,
+                                          const bf16 *X, const bf16 *U, const double *r, const double *logk,
+                                          const double *rscale)
+{
+    constexpr int CH8 = CIN / 8;
+    for (int i = threadIdx.x; i < HVOX * CH8; i += blockDim.x) {
+        const int hv = i / CH8, ch = i % CH8;
+        const int hx = hv % HX, hy = (hv / HX) % HY, hz = hv / (HX * HY);
+        const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D) {
+            const int64_t vi = ((int64_t)gz * H + gy) * W + gx;
+            if (MODE == IN_PLAIN) {
+                val = *(const uint4 *)(X + vi * CIN + ch * 8);
+            } else if (MODE == IN_CATUP) {
+                if (ch < 2) {
+                    const int W2 = W >> 1, H2 = H >> 1;
+                    const int64_t ci = ((int64_t)(gz >> 1) * H2 + (gy >> 1)) * W2 + (gx >> 1);
+                    val = *(const uint4 *)(U + ci * 16 + ch * 8);
+                } else {
+                    val = *(const uint4 *)(X + vi * 16 + (ch - 2) * 8);
+                }
+            } else {   // IN_FIRST: channels (r * rscale, logk, 0, ...)
+                if (ch == 0) {
+                    __nv_bfloat162 p0 = __floats2bfloat162_rn((float)(r[vi] * *rscale), (float)logk[vi]);
+                    val.x = *(unsigned *)&p0;
+                }
+            }
+        }
+        *(uint4 *)(sx + hv * SIN + ch * 8) = val;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3x3x3 convolution (forward, and data gradient with flipped weights)
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(CONV_THREADS)
+k_conv3(int D, int H, int W, const bf16 *__restrict__ X, const bf16 *__restrict__ U,
+        const double *__restrict__ r, const double *__restrict__ logk, const double *__restrict__ rscale,
+        const bf16 *__restrict__ Wp, const float *__restrict__ bias, int relu, bf16 *__restrict__ Y,
+        const int *skip)
+{
+    if (skipped(skip)) return;
+    constexpr int SIN = CIN + 8, SW = CIN + 8;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    bf16 *sx = (bf16 *)smraw;
+    bf16 *sw = sx + HVOX * SIN;
+    const int ntx = (W + TX - 1) / TX, nty = (H + TY - 1) / TY;
+    int b = blockIdx.x;
+    const int tx0 = (b % ntx) * TX;
+    b /= ntx;
+    const int ty0 = (b % nty) * TY, tz0 = (b / nty) * TZ;
+    constexpr int WCH = CIN / 8;
+    for (int i = threadIdx.x; i < 27 * COUT * WCH; i += blockDim.x) {
+        const int row = i / WCH, ch = i % WCH;
+        *(uint4 *)(sw + row * SW + ch * 8) = *(const uint4 *)(Wp + (size_t)row * CIN + ch * 8);
+    }
+    load_halo<CIN, MODE>(sx, SIN, D, H, W, tx0, ty0, tz0, X, U, r, logk, rscale);
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane >> 3, rr = lane & 7;
+    constexpr int NT = COUT / 8;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[m][n][j] = 0.f;
+
+    for (int t = 0; t < 27; ++t) {
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+#pragma unroll
+        for (int kc = 0; kc < CIN / 16; ++kc) {
+            unsigned bfr[NT][2];
+#pragma unroll
+            for (int np = 0; np < NT / 2; ++np) {
+                const bf16 *pb = sw + (t * COUT + (np * 2 + (q >> 1)) * 8 + rr) * SW + kc * 16 + (q & 1) * 8;
+                ldsm_x4(bfr[np * 2][0], bfr[np * 2][1], bfr[np * 2 + 1][0], bfr[np * 2 + 1][1], pb);
+            }
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int row = warp * 2 + m;
+                const int ly = row % TY, lz = row / TY;
+                const int lx = rr + (q & 1) * 8;
+                const int hv = ((lz + dz) * HY + (ly + dy)) * HX + lx + dx;
+                unsigned a0, a1, a2, a3;
+                ldsm_x4(a0, a1, a2, a3, sx + hv * SIN + kc * 16 + (q >> 1) * 8);
+#pragma unroll
+                for (int n = 0; n < NT; ++n) mma_bf16(acc[m][n], a0, a1, a2, a3, bfr[n][0], bfr[n][1]);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int row = warp * 2 + m;
+        const int gy = ty0 + row % TY, gz = tz0 + row / TY;
+        if (gy >= H || gz >= D) continue;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int gx = tx0 + (lane >> 2) + half * 8;
+            if (gx >= W) continue;
+            const int64_t vi = ((int64_t)gz * H + gy) * W + gx;
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const int co = n * 8 + (lane & 3) * 2;
+                float v0 = acc[m][n][half * 2], v1 = acc[m][n][half * 2 + 1];
+                if (bias) { v0 += bias[co]; v1 += bias[co + 1]; }
+                if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                *(__nv_bfloat162 *)(Y + vi * COUT + co) = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient: partial[blk][t][co][ci] = sum over the brick of
+// G[v][co] * X[v + off_t][ci];  partial[blk][27*16*CIN + co] = sum_v G[v][co]
+// ---------------------------------------------------------------------------
+template <int CIN, int MODE>
+__global__ void __launch_bounds__(CONV_THREADS)
+k_conv3_dw(int D, int H, int W, const bf16 *__restrict__ X, const bf16 *__restrict__ U,
+           const double *__restrict__ r, const double *__restrict__ logk, const double *__restrict__ rscale,
+           const bf16 *__restrict__ G, float *__restrict__ partial)
+{
+    constexpr int SIN = CIN + 8, SG = 24;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    bf16 *sx = (bf16 *)smraw;
+    bf16 *sg = sx + HVOX * SIN;
+    const int ntx = (W + TX - 1) / TX, nty = (H + TY - 1) / TY;
+    int b = blockIdx.x;
+    const int tx0 = (b % ntx) * TX;
+    b /= ntx;
+    const int ty0 = (b % nty) * TY, tz0 = (b / nty) * TZ;
+    load_halo<CIN, MODE>(sx, SIN, D, H, W, tx0, ty0, tz0, X, U, r, logk, rscale);
+    for (int i = threadIdx.x; i < TVOX * 2; i += blockDim.x) {
+        const int tv = i >> 1, ch = i & 1;
+        const int lx = tv % TX, ly = (tv / TX) % TY, lz = tv / (TX * TY);
+        const int gx = tx0 + lx, gy = ty0 + ly, gz = tz0 + lz;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (gx < W && gy < H && gz < D) val = *(const uint4 *)(G + (((int64_t)gz * H + gy) * W + gx) * 16 + ch * 8);
+        *(uint4 *)(sg + tv * SG + ch * 8) = val;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane >> 3, rr = lane & 7;
+    constexpr int NT = CIN / 8;
+    float acc[4][NT][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[a][n][j] = 0.f;
+    for (int row = 0; row < TY * TZ; ++row) {
+        const int ly = row % TY, lz = row / TY;
+        unsigned a0, a1, a2, a3;
+        // A = G^T: rows co, columns = the 16 voxels of this x-row
+        ldsm_x4_t(a0, a1, a2, a3, sg + (row * TX + (q >> 1) * 8 + rr) * SG + (q & 1) * 8);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int t = warp + 8 * s;
+            if (t >= 27) continue;
+            const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+            const int lx = (q & 1) * 8 + rr;
+            const int hv = ((lz + dz) * HY + (ly + dy)) * HX + lx + dx;
+#pragma unroll
+            for (int np = 0; np < NT / 2; ++np) {
+                unsigned b0, b1, b2, b3;
+                ldsm_x4_t(b0, b1, b2, b3, sx + hv * SIN + np * 16 + (q >> 1) * 8);
+                mma_bf16(acc[s][np * 2], a0, a1, a2, a3, b0, b1);
+                mma_bf16(acc[s][np * 2 + 1], a0, a1, a2, a3, b2, b3);
+            }
+        }
+    }
+    float *out = partial + (size_t)blockIdx.x * (27 * 16 * CIN + 16);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int t = warp + 8 * s;
+        if (t >= 27) continue;
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            const int co = lane >> 2, ci = n * 8 + (lane & 3) * 2;
+            out[(t * 16 + co) * CIN + ci] = acc[s][n][0];
+            out[(t * 16 + co) * CIN + ci + 1] = acc[s][n][1];
+            out[(t * 16 + co + 8) * CIN + ci] = acc[s][n][2];
+            out[(t * 16 + co + 8) * CIN + ci + 1] = acc[s][n][3];
+        }
+    }
+    // bias gradient: sum of G over the brick
+    if (threadIdx.x < 16) {
+        float sum = 0.f;
+        for (int tv = 0; tv < TVOX; ++tv) sum += __bfloat162float(sg[tv * SG + threadIdx.x]);
+        out[27 * 16 * CIN + threadIdx.x] = sum;
+    }
+}
+
+// grad[woff + (t*16+co)*cin + ci] += w * sum_b partial[b][(t*16+co)*cinp + ci]; bias likewise
+__global__ void k_dw_reduce(int nblocks, int cin, int cinp, const float *__restrict__ partial, float *grad,
+                            int64_t woff, int64_t boff, float wscale)
+{
+    const int stride = 27 * 16 * cinp + 16;
+    const int nw = 27 * 16 * cin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw + 16; i += gridDim.x * blockDim.x) {
+        int src;
+        int64_t dst;
+        if (i < nw) {
+            const int tc = i / cin, ci = i % cin;
+            src = tc * cinp + ci;
+            dst = woff + i;
+        } else {
+            src = 27 * 16 * cinp + (i - nw);
+            dst = boff + (i - nw);
+        }
+        float s = 0.f;
+        for (int bk = 0; bk < nblocks; ++bk) s += partial[(size_t)bk * stride + src];
+        grad[dst] += wscale * s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// element-wise kernels
+// ---------------------------------------------------------------------------
+// 2x2x2 average pooling of a 16-channel tensor
+__global__ void k_avgpool(int Dc, int Hc, int Wc, const bf16 *__restrict__ X, bf16 *__restrict__ Y, const int *skip)
+{
+    if (skipped(skip)) return;
+    const int64_t n = (int64_t)Dc * Hc * Wc * 16;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % 16);
+        const int64_t vc = i / 16;
+        const int x = (int)(vc % Wc), y = (int)((vc / Wc) % Hc), z = (int)(vc / ((int64_t)Wc * Hc));
+        const int W = Wc * 2, H = Hc * 2;
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t vf = ((int64_t)(2 * z + (k >> 2)) * H + (2 * y + ((k >> 1) & 1))) * W + 2 * x + (k & 1);
+            s += __bfloat162float(X[vf * 16 + c]);
+        }
+        Y[i] = __float2bfloat16_rn(s * 0.125f);
+    }
+}
+
+// g_pre = g * (y > 0)
+__global__ void k_relu_mask(int64_t n, const bf16 *__restrict__ g, const bf16 *__restrict__ y, bf16 *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __bfloat162float(y[i]) > 0.f ? g[i] : __float2bfloat16_rn(0.f);
+}
+
+// coarse gradient of a nearest-upsampled input: sum over the 8 children of
+// channels 0..15 of a 32-channel fine gradient
+__global__ void k_up_backward(int Dc, int Hc, int Wc, const bf16 *__restrict__ gcat, bf16 *__restrict__ gc)
+{
+    const int64_t n = (int64_t)Dc * Hc * Wc * 16;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % 16);
+        const int64_t vc = i / 16;
+        const int x = (int)(vc % Wc), y = (int)((vc / Wc) % Hc), z = (int)(vc / ((int64_t)Wc * Hc));
+        const int W = Wc * 2, H = Hc * 2;
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t vf = ((int64_t)(2 * z + (k >> 2)) * H + (2 * y + ((k >> 1) & 1))) * W + 2 * x + (k & 1);
+            s += __bfloat162float(gcat[vf * 32 + c]);
+        }
+        gc[i] = __float2bfloat16_rn(s);
+    }
+}
+
+// gradient of a skip tensor: skip part of the decoder's gradient (channels
+// 16..31 of gcat) plus the average-pooling adjoint of the coarse gradient
+__global__ void k_pool_backward_add(int D, int H, int W, const bf16 *__restrict__ gcoarse,
+                                    const bf16 *__restrict__ gcat, bf16 *__restrict__ out)
+{
+    const int64_t n = (int64_t)D * H * W * 16;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % 16);
+        const int64_t v = i / 16;
+        const int x = (int)(v % W), y = (int)((v / W) % H), z = (int)(v / ((int64_t)W * H));
+        const int64_t vc = ((int64_t)(z >> 1) * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1);
+        const float s = __bfloat162float(gcat[v * 32 + 16 + c]) + 0.125f * __bfloat162float(gcoarse[vc * 16 + c]);
+        out[i] = __float2bfloat16_rn(s);
+    }
+}
+
+// sum of squares of r (FP64) with a last-block finish: scal[0] = rms, scal[1] = 1/rms
+__global__ void __launch_bounds__(256)
+k_rms(int64_t n, const double *__restrict__ r, double *red, unsigned *ticket, double *scal, const int *skip)
+{
+    if (skipped(skip)) return;
+    __shared__ double sm[8];
+    __shared__ bool last;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s = fma(r[i], r[i], s);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sm[w];
+        red[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += __ldcg(red + b);
+    t = warp_sum(t);
+    if (threadIdx.x == 0) {
+        double rms = sqrt(t / (double)n);
+        if (!(rms > 0.0) || !isfinite(rms)) rms = 1.0;
+        scal[0] = rms;
+        scal[1] = 1.0 / rms;
+        *ticket = 0;
+    }
+}
+
+// head: out[v] = (sum_c wh[c] x[v][c] + bh) * rms * s; flags non-finite output
+__global__ void k_head(int64_t n, const bf16 *__restrict__ x, const float *__restrict__ wh, const double *__restrict__ scal,
+                       float out_scale, double *__restrict__ out, int *flag, const int *skip)
+{
+    if (skipped(skip)) return;
+    const double sc = scal[0] * (double)out_scale;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 *p = (const uint4 *)(x + v * 16);
+        const uint4 a = p[0], b = p[1];
+        const bf16 *e0 = (const bf16 *)&a, *e1 = (const bf16 *)&b;
+        float s = wh[16];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s = fmaf(wh[c], __bfloat162float(e0[c]), s);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s = fmaf(wh[8 + c], __bfloat162float(e1[c]), s);
+        const double o = (double)s * sc;
+        out[v] = o;
+        if (flag && !isfinite(o)) atomicOr(flag, 1);
+    }
+}
+
+// loss = sum (o - e)^2 / sum e^2 (two sums with a last-block finish), and
+// gout = w * 2 (o - e) / sum e^2 computed after the sums by k_loss_grad
+__global__ void __launch_bounds__(256)
+k_loss_sums(int64_t n, const double *__restrict__ o, const double *__restrict__ e, double *red, unsigned *ticket,
+            double *scal)
+{
+    __shared__ double sm[2][8];
+    __shared__ bool last;
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = o[i] - e[i];
+        s0 = fma(d, d, s0);
+        s1 = fma(e[i], e[i], s1);
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if ((threadIdx.x & 31) == 0) { sm[0][threadIdx.x >> 5] = s0; sm[1][threadIdx.x >> 5] = s1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 8; ++w) { a += sm[0][w]; b += sm[1][w]; }
+        red[2 * blockIdx.x] = a;
+        red[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int bk = threadIdx.x; bk < (int)gridDim.x; bk += 32) { a += __ldcg(red + 2 * bk); b += __ldcg(red + 2 * bk + 1); }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x == 0) {
+        scal[2] = b > 0.0 ? a / b : 0.0;
+        scal[3] = b;
+        *ticket = 0;
+    }
+}
+
+__global__ void k_loss_grad(int64_t n, const double *__restrict__ o, const double *__restrict__ e,
+                            const double *__restrict__ scal, double w, double *__restrict__ g)
+{
+    const double den = scal[3] > 0.0 ? scal[3] : 1.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        g[i] = w * 2.0 * (o[i] - e[i]) / den;
+}
+
+// head backward: ge = g * rms * s; dx[v][c] = ge * wh[c]; per-block partial
+// sums of ge * x[v][c] (16) and ge (1) into hp[block][17]
+__global__ void __launch_bounds__(256)
+k_head_backward(int64_t n, const bf16 *__restrict__ x, const float *__restrict__ wh, const double *__restrict__ scal,
+                float out_scale, const double *__restrict__ g, bf16 *__restrict__ dx, float *__restrict__ hp)
+{
+    __shared__ float sm[8][17];
+    const double sc = scal[0] * (double)out_scale;
+    float acc[17];
+#pragma unroll
+    for (int c = 0; c < 17; ++c) acc[c] = 0.f;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const float ge = (float)(g[v] * sc);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            acc[c] = fmaf(ge, __bfloat162float(x[v * 16 + c]), acc[c]);
+            dx[v * 16 + c] = __float2bfloat16_rn(ge * wh[c]);
+        }
+        acc[16] += ge;
+    }
+#pragma unroll
+    for (int c = 0; c < 17; ++c) {
+        float s = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5][c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 17) {
+        float s = 0.f;
+        for (int w = 0; w < 8; ++w) s += sm[w][threadIdx.x];
+        hp[blockIdx.x * 17 + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_head_reduce(int nblocks, const float *__restrict__ hp, float *grad, int64_t hoff)
+{
+    const int c = threadIdx.x;
+    if (c >= 17) return;
+    float s = 0.f;
+    for (int b = 0; b < nblocks; ++b) s += hp[b * 17 + c];
+    grad[hoff + c] += s;
+}
+
+// FP32 master -> bf16 forward [27][16][cinp] and data-gradient [27][cin][16] weights
+__global__ void k_pack_weights(int cin, int cinp, const float *__restrict__ w, bf16 *__restrict__ wf, bf16 *__restrict__ wb)
+{
+    const int n = 27 * 16 * cinp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = i % cinp, co = (i / cinp) % 16, t = i / (16 * cinp);
+        const float v = ci < cin ? w[(t * 16 + co) * cin + ci] : 0.f;
+        wf[i] = __float2bfloat16_rn(v);
+        if (wb && ci < cin) wb[((26 - t) * cin + ci) * 16 + co] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void k_adam(int64_t n, float *p, float *g, float *m, float *v, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        g[i] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int conv_smem(int cin, int cout) { return (HVOX * (cin + 8) + 27 * cout * (cin + 8)) * 2; }
+static int dw_smem(int cin) { return (HVOX * (cin + 8) + TVOX * 24) * 2; }
+
+static int64_t nbricks(const Level &L)
+{
+    return (int64_t)((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY) * ((L.nz + TZ - 1) / TZ);
+}
+
+static int ew_grid(rs_ctx *ctx, int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8));
+}
+
+static bool g_attrs_set = false;
+
+template <int CIN, int COUT, int MODE>
+static void set_attr()
+{
+    cudaFuncSetAttribute(k_conv3<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(CIN, COUT));
+}
+
+template <int CIN, int MODE>
+static void set_attr_dw()
+{
+    cudaFuncSetAttribute(k_conv3_dw<CIN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, dw_smem(CIN));
+}
+
+static void ensure_attrs()
+{
+    if (g_attrs_set) return;
+    set_attr<16, 16, IN_PLAIN>();
+    set_attr<16, 16, IN_FIRST>();
+    set_attr<32, 16, IN_CATUP>();
+    set_attr<16, 32, IN_PLAIN>();
+    set_attr_dw<16, IN_PLAIN>();
+    set_attr_dw<16, IN_FIRST>();
+    set_attr_dw<32, IN_CATUP>();
+    g_attrs_set = true;
+}
+
+static void free_workspace(rs_net *net)
+{
+    rs_ctx *c = net->ctx;
+    for (int l = 0; l < NET_NLAYERS; ++l) { rs_free(c, net->act[l]); net->act[l] = nullptr; }
+    for (int l = 0; l < NET_LEVELS; ++l) {
+        rs_free(c, net->pool[l]);
+        rs_free(c, net->g16a[l]);
+        rs_free(c, net->g16b[l]);
+        rs_free(c, net->g32[l]);
+        net->pool[l] = net->g16a[l] = net->g16b[l] = net->g32[l] = nullptr;
+    }
+    rs_free(c, net->partials);
+    rs_free(c, net->gout);
+    rs_free(c, net->outb);
+    rs_free(c, net->headpart);
+    net->partials = nullptr;
+    net->gout = nullptr;
+    net->outb = nullptr;
+    net->headpart = nullptr;
+    net->nx = net->ny = net->nz = 0;
+}
+
+static int ensure_workspace(rs_net *net, int nx, int ny, int nz)
+{
+    if (net->nx == nx && net->ny == ny && net->nz == nz) return RS_OK;
+    if (nx % 8 || ny % 8 || nz % 8 || nx < 8 || ny < 8 || nz < 8) return RS_ERR_INVALID_ARG;
+    free_workspace(net);
+    rs_ctx *c = net->ctx;
+    for (int l = 0; l < NET_LEVELS; ++l) {
+        net->lv[l].nx = nx >> l;
+        net->lv[l].ny = ny >> l;
+        net->lv[l].nz = nz >> l;
+        net->lv[l].nvox = (int64_t)net->lv[l].nx * net->lv[l].ny * net->lv[l].nz;
+    }
+    int st = RS_OK;
+    for (int l = 0; l < NET_NLAYERS && !st; ++l)
+        st = rs_alloc(c, (void **)&net->act[l], sizeof(bf16) * 16 * net->lv[kLayers[l].level].nvox);
+    int64_t maxp = 0;
+    for (int l = 0; l < NET_LEVELS && !st; ++l) {
+        const int64_t nv = net->lv[l].nvox;
+        st = rs_alloc(c, (void **)&net->pool[l], sizeof(bf16) * 16 * nv);
+        if (!st) st = rs_alloc(c, (void **)&net->g16a[l], sizeof(bf16) * 16 * nv);
+        if (!st) st = rs_alloc(c, (void **)&net->g16b[l], sizeof(bf16) * 16 * nv);
+        if (!st) st = rs_alloc(c, (void **)&net->g32[l], sizeof(bf16) * 32 * nv);
+        maxp = std::max(maxp, nbricks(net->lv[l]) * (27 * 16 * 32 + 16));
+    }
+    if (!st) st = rs_alloc(c, (void **)&net->partials, sizeof(float) * maxp);
+    if (!st) st = rs_alloc(c, (void **)&net->gout, sizeof(double) * net->lv[0].nvox);
+    if (!st) st = rs_alloc(c, (void **)&net->outb, sizeof(double) * net->lv[0].nvox);
+    if (!st) st = rs_alloc(c, (void **)&net->headpart, sizeof(float) * 17 * c->num_sms * 8);
+    if (st) { free_workspace(net); return st; }
+    net->partials_len = maxp;
+    net->nx = nx;
+    net->ny = ny;
+    net->nz = nz;
+    return RS_OK;
+}
+
+static int pack_all(rs_net *net)
+{
+    rs_ctx *c = net->ctx;
+    for (int l = 0; l < NET_NLAYERS; ++l) {
+        const int cin = kLayers[l].cin, cinp = cin_pad(l);
+        k_pack_weights<<<ew_grid(c, 27 * 16 * cinp), 256, 0, c->stream>>>(cin, cinp, net->p + net->woff[l], net->wf[l],
+                                                                         l == E0A ? nullptr : net->wb[l]);
+    }
+    c->launches += NET_NLAYERS - 1;
+    return rs_check_launch(c);
+}
+
+// launches one forward convolution of layer l
+static int conv_forward(rs_net *net, int l, const bf16 *X, const bf16 *U, const double *r, const double *logk,
+                        bf16 *Y, const int *skip)
+{
+    rs_ctx *c = net->ctx;
+    const Level &L = net->lv[kLayers[l].level];
+    const int grid = (int)nbricks(L);
+    const float *bias = net->p + net->boff[l];
+    RsProfScope prof(c, RS_PROF_NET);
+    switch (kLayers[l].mode) {
+    case IN_FIRST:
+        k_conv3<16, 16, IN_FIRST><<<grid, CONV_THREADS, conv_smem(16, 16), c->stream>>>(
+            L.nz, L.ny, L.nx, nullptr, nullptr, r, logk, net->scal + 1, net->wf[l], bias, 1, Y, skip);
+        break;
+    case IN_CATUP:
+        k_conv3<32, 16, IN_CATUP><<<grid, CONV_THREADS, conv_smem(32, 16), c->stream>>>(
+            L.nz, L.ny, L.nx, X, U, nullptr, nullptr, nullptr, net->wf[l], bias, 1, Y, skip);
+        break;
+    default:
+        k_conv3<16, 16, IN_PLAIN><<<grid, CONV_THREADS, conv_smem(16, 16), c->stream>>>(
+            L.nz, L.ny, L.nx, X, nullptr, nullptr, nullptr, nullptr, net->wf[l], bias, 1, Y, skip);
+    }
+    return rs_check_launch(c);
+}
+
+static int pool_forward(rs_net *net, int lvl, const bf16 *X, bf16 *Y, const int *skip)
+{
+    rs_ctx *c = net->ctx;
+    const Level &L = net->lv[lvl];
+    RsProfScope prof(c, RS_PROF_NET);
+    k_avgpool<<<ew_grid(c, L.nvox * 16), 256, 0, c->stream>>>(L.nz, L.ny, L.nx, X, Y, skip);
+    return rs_check_launch(c);
+}
+
+// forward pass; out (FP64, nvox) = network(r, logk) * rms * out_scale
+static int net_forward(rs_net *net, const double *r, const double *logk, double *out, const int *skip)
+{
+    rs_ctx *c = net->ctx;
+    const int64_t n0 = net->lv[0].nvox;
+    {
+        RsProfScope prof(c, RS_PROF_NET);
+        k_rms<<<c->red_blocks, 256, 0, c->stream>>>(n0, r, net->red, net->ticket, net->scal, skip);
+        RS_TRY(rs_check_launch(c));
+    }
+    bf16 **A = net->act;
+    RS_TRY(conv_forward(net, E0A, nullptr, nullptr, r, logk, A[E0A], skip));
+    RS_TRY(conv_forward(net, E0B, A[E0A], nullptr, nullptr, nullptr, A[E0B], skip));
+    RS_TRY(pool_forward(net, 1, A[E0B], net->pool[1], skip));
+    RS_TRY(conv_forward(net, E1A, net->pool[1], nullptr, nullptr, nullptr, A[E1A], skip));
+    RS_TRY(conv_forward(net, E1B, A[E1A], nullptr, nullptr, nullptr, A[E1B], skip));
+    RS_TRY(pool_forward(net, 2, A[E1B], net->pool[2], skip));
+    RS_TRY(conv_forward(net, E2A, net->pool[2], nullptr, nullptr, nullptr, A[E2A], skip));
+    RS_TRY(conv_forward(net, E2B, A[E2A], nullptr, nullptr, nullptr, A[E2B], skip));
+    RS_TRY(pool_forward(net, 3, A[E2B], net->pool[3], skip));
+    RS_TRY(conv_forward(net, E3A, net->pool[3], nullptr, nullptr, nullptr, A[E3A], skip));
+    RS_TRY(conv_forward(net, E3B, A[E3A], nullptr, nullptr, nullptr, A[E3B], skip));
+    RS_TRY(conv_forward(net, D2A, A[E2B], A[E3B], nullptr, nullptr, A[D2A], skip));
+    RS_TRY(conv_forward(net, D2B, A[D2A], nullptr, nullptr, nullptr, A[D2B], skip));
+    RS_TRY(conv_forward(net, D1A, A[E1B], A[D2B], nullptr, nullptr, A[D1A], skip));
+    RS_TRY(conv_forward(net, D1B, A[D1A], nullptr, nullptr, nullptr, A[D1B], skip));
+    RS_TRY(conv_forward(net, D0A, A[E0B], A[D1B], nullptr, nullptr, A[D0A], skip));
+    RS_TRY(conv_forward(net, D0B, A[D0A], nullptr, nullptr, nullptr, A[D0B], skip));
+    RsProfScope prof(c, RS_PROF_NET);
+    k_head<<<ew_grid(c, n0), 256, 0, c->stream>>>(n0, A[D0B], net->p + net->hoff, net->scal, net->out_scale, out,
+                                                 net->flag, skip);
+    return rs_check_launch(c);
+}
+
+// weight gradient of layer l for output gradient G (pre-activation), input as in the forward pass
+static int conv_dw(rs_net *net, int l, const bf16 *X, const bf16 *U, const double *r, const double *logk,
+                   const bf16 *G, float wscale)
+{
+    rs_ctx *c = net->ctx;
+    const Level &L = net->lv[kLayers[l].level];
+    const int grid = (int)nbricks(L);
+    RsProfScope prof(c, RS_PROF_NET);
+    switch (kLayers[l].mode) {
+    case IN_FIRST:
+        k_conv3_dw<16, IN_FIRST><<<grid, CONV_THREADS, dw_smem(16), c->stream>>>(L.nz, L.ny, L.nx, nullptr, nullptr, r,
+                                                                                logk, net->scal + 1, G, net->partials);
+        break;
+    case IN_CATUP:
+        k_conv3_dw<32, IN_CATUP><<<grid, CONV_THREADS, dw_smem(32), c->stream>>>(L.nz, L.ny, L.nx, X, U, nullptr,
+                                                                                nullptr, nullptr, G, net->partials);
+        break;
+    default:
+        k_conv3_dw<16, IN_PLAIN><<<grid, CONV_THREADS, dw_smem(16), c->stream>>>(L.nz, L.ny, L.nx, X, nullptr, nullptr,
+                                                                                nullptr, nullptr, G, net->partials);
+    }
+    RS_TRY(rs_check_launch(c));
+    const int cin = kLayers[l].cin, cinp = cin_pad(l);
+    k_dw_reduce<<<ew_grid(c, 27 * 16 * cin + 16), 256, 0, c->stream>>>(grid, cin, cinp, net->partials, net->g,
+                                                                        net->woff[l], net->boff[l], wscale);
+    return rs_check_launch(c);
+}
+
+// data gradient: dX = conv(G, flipped transposed weights)
+static int conv_dx(rs_net *net, int l, const bf16 *G, bf16 *dX)
+{
+    rs_ctx *c = net->ctx;
+    const Level &L = net->lv[kLayers[l].level];
+    const int grid = (int)nbricks(L);
+    RsProfScope prof(c, RS_PROF_NET);
+    if (kLayers[l].cin == 32)
+        k_conv3<16, 32, IN_PLAIN><<<grid, CONV_THREADS, conv_smem(16, 32), c->stream>>>(
+            L.nz, L.ny, L.nx, G, nullptr, nullptr, nullptr, nullptr, net->wb[l], nullptr, 0, dX, nullptr);
+    else
+        k_conv3<16, 16, IN_PLAIN><<<grid, CONV_THREADS, conv_smem(16, 16), c->stream>>>(
+            L.nz, L.ny, L.nx, G, nullptr, nullptr, nullptr, nullptr, net->wb[l], nullptr, 0, dX, nullptr);
+    return rs_check_launch(c);
+}
+
+static int relu_mask(rs_net *net, int lvl, const bf16 *g, const bf16 *y, bf16 *out)
+{
+    rs_ctx *c = net->ctx;
+    const int64_t n = net->lv[lvl].nvox * 16;
+    k_relu_mask<<<ew_grid(c, n), 256, 0, c->stream>>>(n, g, y, out);
+    return rs_check_launch(c);
+}
+
+// backward of one conv+ReLU layer: g_post (gradient of the layer output) ->
+// weight gradients and, if dX != null, the input gradient
+static int layer_backward(rs_net *net, int l, const bf16 *g_post, bf16 *gpre, const bf16 *X, const bf16 *U,
+                          const double *r, const double *logk, bf16 *dX, float wscale)
+{
+    const int lvl = kLayers[l].level;
+    RS_TRY(relu_mask(net, lvl, g_post, net->act[l], gpre));
+    RS_TRY(conv_dw(net, l, X, U, r, logk, gpre, wscale));
+    if (dX) RS_TRY(conv_dx(net, l, gpre, dX));
+    return RS_OK;
+}
+
+static int net_backward(rs_net *net, const double *r, const double *logk, float wscale)
+{
+    rs_ctx *c = net->ctx;
+    bf16 **A = net->act;
+    const int64_t n0 = net->lv[0].nvox;
+    {
+        RsProfScope prof(c, RS_PROF_NET);
+        const int hb = std::min<int64_t>((n0 + 255) / 256, (int64_t)c->num_sms * 8);
+        k_head_backward<<<hb, 256, 0, c->stream>>>(n0, A[D0B], net->p + net->hoff, net->scal, net->out_scale,
+                                                   net->gout, net->g16a[0], net->headpart);
+        k_head_reduce<<<1, 32, 0, c->stream>>>(hb, net->headpart, net->g, net->hoff);
+        c->launches++;
+        RS_TRY(rs_check_launch(c));
+    }
+    // decoder, fine to coarse
+    const int dec_b[3] = {D0B, D1B, D2B}, dec_a[3] = {D0A, D1A, D2A};
+    const int skip_src[3] = {E0B, E1B, E2B}, up_src[3] = {D1B, D2B, E3B};
+    for (int lvl = 0; lvl < 3; ++lvl) {
+        const int lb = dec_b[lvl], la = dec_a[lvl];
+        RS_TRY(layer_backward(net, lb, net->g16a[lvl], net->g16b[lvl], A[la], nullptr, nullptr, nullptr,
+                              net->g16a[lvl], wscale));
+        RS_TRY(layer_backward(net, la, net->g16a[lvl], net->g16b[lvl], A[skip_src[lvl]], A[up_src[lvl]], nullptr,
+                              nullptr, net->g32[lvl], wscale));
+        const Level &C = net->lv[lvl + 1];
+        k_up_backward<<<ew_grid(c, C.nvox * 16), 256, 0, c->stream>>>(C.nz, C.ny, C.nx, net->g32[lvl], net->g16a[lvl + 1]);
+        RS_TRY(rs_check_launch(c));
+    }
+    // encoder, coarse to fine
+    const int enc_b[4] = {E0B, E1B, E2B, E3B}, enc_a[4] = {E0A, E1A, E2A, E3A};
+    for (int lvl = 3; lvl >= 0; --lvl) {
+        const int lb = enc_b[lvl], la = enc_a[lvl];
+        RS_TRY(layer_backward(net, lb, net->g16a[lvl], net->g16b[lvl], A[la], nullptr, nullptr, nullptr,
+                              net->g16a[lvl], wscale));
+        if (lvl == 0) {
+            RS_TRY(layer_backward(net, la, net->g16a[0], net->g16b[0], nullptr, nullptr, r, logk, nullptr, wscale));
+        } else {
+            RS_TRY(layer_backward(net, la, net->g16a[lvl], net->g16b[lvl], net->pool[lvl], nullptr, nullptr, nullptr,
+                                  net->g16a[lvl], wscale));
+            const Level &F = net->lv[lvl - 1];
+            k_pool_backward_add<<<ew_grid(c, F.nvox * 16), 256, 0, c->stream>>>(F.nz, F.ny, F.nx, net->g16a[lvl],
+                                                                                 net->g32[lvl - 1], net->g16a[lvl - 1]);
+            RS_TRY(rs_check_launch(c));
+        }
+    }
+    return RS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+static int64_t layout(rs_net *net)
+{
+    int64_t off = 0;
+    for (int l = 0; l < NET_NLAYERS; ++l) {
+        net->woff[l] = off;
+        off += 27 * 16 * kLayers[l].cin;
+        net->boff[l] = off;
+        off += 16;
+    }
+    net->hoff = off;
+    return off + 17;
+}
+
+extern "C" int64_t rs_net_num_params(void)
+{
+    rs_net tmp;
+    return layout(&tmp);
+}
+
+static void net_free(rs_net *net)
+{
+    if (!net) return;
+    rs_ctx *c = net->ctx;
+    free_workspace(net);
+    rs_free(c, net->p);
+    rs_free(c, net->g);
+    rs_free(c, net->m);
+    rs_free(c, net->v);
+    for (int l = 0; l < NET_NLAYERS; ++l) { rs_free(c, net->wf[l]); rs_free(c, net->wb[l]); }
+    rs_free(c, net->scal);
+    rs_free(c, net->red);
+    rs_free(c, net->ticket);
+    rs_free(c, net->flag);
+    delete net;
+}
+
+extern "C" int rs_net_create(rs_ctx *ctx, const float *params, int64_t nparams, float out_scale, rs_net **out)
+{
+    if (!ctx || !params || !out) return RS_ERR_INVALID_ARG;
+    *out = nullptr;
+    rs_net *net = new rs_net();
+    memset((void *)net, 0, sizeof(rs_net));
+    net->ctx = ctx;
+    net->out_scale = out_scale;
+    net->nparams = layout(net);
+    if (nparams != net->nparams) { delete net; return RS_ERR_SIZE_MISMATCH; }
+    ensure_attrs();
+    int st = RS_OK;
+    const size_t pb = sizeof(float) * nparams;
+    st = st ? st : rs_alloc(ctx, (void **)&net->p, pb);
+    st = st ? st : rs_alloc(ctx, (void **)&net->g, pb);
+    st = st ? st : rs_alloc(ctx, (void **)&net->m, pb);
+    st = st ? st : rs_alloc(ctx, (void **)&net->v, pb);
+    for (int l = 0; l < NET_NLAYERS && !st; ++l) {
+        st = rs_alloc(ctx, (void **)&net->wf[l], sizeof(bf16) * 27 * 16 * cin_pad(l));
+        if (!st) st = rs_alloc(ctx, (void **)&net->wb[l], sizeof(bf16) * 27 * 16 * cin_pad(l));
+    }
+    st = st ? st : rs_alloc(ctx, (void **)&net->scal, sizeof(double) * 16);
+    st = st ? st : rs_alloc(ctx, (void **)&net->red, sizeof(double) * 2 * ctx->red_blocks);
+    st = st ? st : rs_alloc(ctx, (void **)&net->ticket, sizeof(unsigned) * 4);
+    st = st ? st : rs_alloc(ctx, (void **)&net->flag, sizeof(int) * 4);
+    if (st) { net_free(net); return st; }
+    cudaStream_t s = ctx->stream;
+    RS_CUDA_TRY(cudaMemcpyAsync(net->p, params, pb, cudaMemcpyHostToDevice, s));
+    RS_CUDA_TRY(cudaMemsetAsync(net->g, 0, pb, s));
+    RS_CUDA_TRY(cudaMemsetAsync(net->m, 0, pb, s));
+    RS_CUDA_TRY(cudaMemsetAsync(net->v, 0, pb, s));
+    RS_CUDA_TRY(cudaMemsetAsync(net->scal, 0, sizeof(double) * 16, s));
+    RS_CUDA_TRY(cudaMemsetAsync(net->ticket, 0, sizeof(unsigned) * 4, s));
+    RS_CUDA_TRY(cudaMemsetAsync(net->flag, 0, sizeof(int) * 4, s));
+    st = pack_all(net);
+    if (st) { net_free(net); return st; }
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = net;
+    return RS_OK;
+}
+
+extern "C" int rs_net_destroy(rs_net **net)
+{
+    if (!net || !*net) return RS_OK;
+    cudaStreamSynchronize((*net)->ctx->stream);
+    net_free(*net);
+    *net = nullptr;
+    return RS_OK;
+}
+
+extern "C" int rs_net_get_params(const rs_net *net, float *out, int64_t n)
+{
+    if (!net || !out) return RS_ERR_INVALID_ARG;
+    if (n != net->nparams) return RS_ERR_SIZE_MISMATCH;
+    RS_CUDA_TRY(cudaMemcpyAsync(out, net->p, sizeof(float) * n, cudaMemcpyDeviceToHost, net->ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(net->ctx->stream));
+    return RS_OK;
+}
+
+extern "C" int rs_net_get_grads(const rs_net *net, float *out, int64_t n)
+{
+    if (!net || !out) return RS_ERR_INVALID_ARG;
+    if (n != net->nparams) return RS_ERR_SIZE_MISMATCH;
+    RS_CUDA_TRY(cudaMemcpyAsync(out, net->g, sizeof(float) * n, cudaMemcpyDeviceToHost, net->ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(net->ctx->stream));
+    return RS_OK;
+}
+
+extern "C" int rs_net_zero_grads(rs_net *net)
+{
+    if (!net) return RS_ERR_INVALID_ARG;
+    RS_CUDA_TRY(cudaMemsetAsync(net->g, 0, sizeof(float) * net->nparams, net->ctx->stream));
+    return RS_OK;
+}
+
+extern "C" int rs_net_forward(rs_net *net, int32_t nx, int32_t ny, int32_t nz, const double *r, const double *logk,
+                              double *out)
+{
+    if (!net || !r || !logk || !out) return RS_ERR_INVALID_ARG;
+    RS_TRY(ensure_workspace(net, nx, ny, nz));
+    return net_forward(net, r, logk, out, nullptr);
+}
+
+extern "C" int rs_net_accumulate(rs_net *net, int32_t nx, int32_t ny, int32_t nz, const double *r, const double *logk,
+                                 const double *e, double weight, double *loss_host)
+{
+    if (!net || !r || !logk || !e) return RS_ERR_INVALID_ARG;
+    RS_TRY(ensure_workspace(net, nx, ny, nz));
+    rs_ctx *c = net->ctx;
+    const int64_t n0 = net->lv[0].nvox;
+    RS_TRY(net_forward(net, r, logk, net->outb, nullptr));
+    k_loss_sums<<<c->red_blocks, 256, 0, c->stream>>>(n0, net->outb, e, net->red, net->ticket, net->scal);
+    k_loss_grad<<<ew_grid(c, n0), 256, 0, c->stream>>>(n0, net->outb, e, net->scal, weight, net->gout);
+    c->launches++;
+    RS_TRY(rs_check_launch(c));
+    RS_TRY(net_backward(net, r, logk, 1.0f));
+    if (loss_host) {
+        RS_CUDA_TRY(cudaMemcpyAsync(c->h_pinned + 8, net->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        RS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        *loss_host = c->h_pinned[8];
+    }
+    return RS_OK;
+}
+
+extern "C" int rs_net_adam(rs_net *net, float lr, float beta1, float beta2, float eps)
+{
+    if (!net) return RS_ERR_INVALID_ARG;
+    rs_ctx *c = net->ctx;
+    net->step += 1;
+    const float c1 = 1.f - powf(beta1, (float)net->step), c2 = 1.f - powf(beta2, (float)net->step);
+    k_adam<<<ew_grid(c, net->nparams), 256, 0, c->stream>>>(net->nparams, net->p, net->g, net->m, net->v, lr, beta1,
+                                                            beta2, eps, c1, c2);
+    RS_TRY(rs_check_launch(c));
+    return pack_all(net);
+}
+
+struct NetFileHeader {
+    unsigned magic;
+    int version;
+    int64_t nparams;
+    float out_scale;
+    int step;
+};
+
+extern "C" int rs_net_save(const rs_net *net, const char *path)
+{
+    if (!net || !path) return RS_ERR_INVALID_ARG;
+    std::vector<float> buf(3 * net->nparams);
+    cudaStream_t s = net->ctx->stream;
+    RS_CUDA_TRY(cudaMemcpyAsync(buf.data(), net->p, sizeof(float) * net->nparams, cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaMemcpyAsync(buf.data() + net->nparams, net->m, sizeof(float) * net->nparams, cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaMemcpyAsync(buf.data() + 2 * net->nparams, net->v, sizeof(float) * net->nparams, cudaMemcpyDeviceToHost, s));
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
+    FILE *f = fopen(path, "wb");
+    if (!f) return RS_ERR_INVALID_ARG;
+    NetFileHeader h = {NET_MAGIC, 1, net->nparams, net->out_scale, net->step};
+    const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    return ok ? RS_OK : RS_ERR_INVALID_ARG;
+}
+
+extern "C" int rs_net_load(rs_ctx *ctx, const char *path, rs_net **out)
+{
+    if (!ctx || !path || !out) return RS_ERR_INVALID_ARG;
+    FILE *f = fopen(path, "rb");
+    if (!f) return RS_ERR_INVALID_ARG;
+    NetFileHeader h;
+    if (fread(&h, sizeof(h), 1, f) != 1 || h.magic != NET_MAGIC || h.version != 1 || h.nparams != rs_net_num_params()) {
+        fclose(f);
+        return RS_ERR_INVALID_ARG;
+    }
+    std::vector<float> buf(3 * h.nparams);
+    const bool ok = fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return RS_ERR_INVALID_ARG;
+    RS_TRY(rs_net_create(ctx, buf.data(), h.nparams, h.out_scale, out));
+    rs_net *net = *out;
+    RS_CUDA_TRY(cudaMemcpyAsync(net->m, buf.data() + h.nparams, sizeof(float) * h.nparams, cudaMemcpyHostToDevice, ctx->stream));
+    RS_CUDA_TRY(cudaMemcpyAsync(net->v, buf.data() + 2 * h.nparams, sizeof(float) * h.nparams, cudaMemcpyHostToDevice, ctx->stream));
+    RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    net->step = h.step;
+    return RS_OK;
+}
+
+// flag[1] = 1 (skip the fallback sweeps) unless the cycle runs and the
+// network output had a non-finite value (flag[0])
+__global__ void k_fallback_flag(int *flag, const int *skip)
+{
+    flag[1] = (skip && *(volatile const int *)skip) || flag[0] == 0;
+}
+
+static int rs_ilu_fallback(rs_pc *M, const double *rp, double *zp, int *flag, const int *skip)
+{
+    rs_ctx *c = M->ctx;
+    k_fallback_flag<<<1, 1, 0, c->stream>>>(flag, skip);
+    RS_TRY(rs_check_launch(c));
+    return rs_ilu_apply(M->ilu, rp, zp, nullptr, flag + 1);
+}
+
+// pressure stage of the learned CPR preconditioner: zp = net(rp, log k); if
+// any output is not finite, ILU(0) of the pressure matrix is applied instead
 int rs_net_apply_pressure(rs_pc *M, const double *rp, double *zp, const int *skip)
 {
-    (void)M; (void)rp; (void)zp; (void)skip;
-    return RS_ERR_INVALID_ARG;
+    rs_net *net = const_cast<rs_net *>(M->net);
+    rs_ctx *c = net->ctx;
+    RS_TRY(ensure_workspace(net, M->nx, M->ny, M->nz));
+    RS_CUDA_TRY(cudaMemsetAsync(net->flag, 0, sizeof(int), c->stream));
+    RS_TRY(net_forward(net, rp, M->log_perm, zp, skip));
+    // fallback: the ILU(0) sweeps run only when the flag is set; the flag is
+    // inverted into net->flag[1] (1 = network output usable, skip the sweeps)
+    RS_TRY(rs_ilu_fallback(M, rp, zp, net->flag, skip));
+    return RS_OK;
 }
