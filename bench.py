@@ -3,10 +3,16 @@
 Default workload (one GPU): the 3-D 7-point pressure matrix on a 128x128x64
 grid (1,048,576 cells, vertical permeability x0.1, log-normal permeability,
 seed 1), b = A x_true, GMRES(30) right-preconditioned by ILU(0), all FP64,
-rtol 1e-8, x0 = 0.  One step = one complete solve; the matrix, b and the
-preconditioner are resident in HBM before the timed region (preconditioner
-setup is timed separately).  Between timed steps a 512 MB buffer is written
-to flush the 129 MB L2.
+rtol 1e-8, x0 = 0.  One step = one complete solve; matrices, right-hand
+sides and preconditioners are resident in HBM before the timed region
+(setup is timed separately).  A 512 MB buffer is written between timed
+steps to flush the 129 MB L2.
+
+Other workloads (--workload): the 32^3 system; mixed precision; BiCGSTAB;
+the learned pressure stage on 64^3 held-out fields (FGMRES(30), learned
+two-stage CPR vs GMRES(30)+ILU(0)); the 100x100x50 black-oil-like 3x3-block
+system with CPR-FGMRES(30); the 128^3 block system with the learned vs the
+ILU(0) pressure stage.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -32,19 +38,29 @@ import synth  # noqa: E402
 
 METRIC = "time to 1e-8 rel. residual (s), learned vs ILU(0) precond; SpMV/ILU HBM GB/s"
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+RTOL = 1e-8
+NET_PATH = os.path.join(ROOT, "paper_1701_05913_gb300", "models", "pressure_unet_64.bin")
 
 WORKLOADS = {
-    "gmres_ilu0_128x128x64": dict(grid=(128, 128, 64), kz=0.1, solver="gmres", precond="ilu0",
-                                  prec="fp64", restart=30),
-    "gmres_ilu0_mixed_128x128x64": dict(grid=(128, 128, 64), kz=0.1, solver="gmres", precond="ilu0",
-                                        prec="mixed", restart=30),
-    "bicgstab_ilu0_128x128x64": dict(grid=(128, 128, 64), kz=0.1, solver="bicgstab", precond="ilu0",
-                                     prec="fp64", restart=30),
-    "gmres_ilu0_32x32x32": dict(grid=(32, 32, 32), kz=1.0, solver="gmres", precond="ilu0",
-                                prec="fp64", restart=30),
+    "gmres_ilu0_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="gmres", precond="ilu0",
+                                  prec="fp64"),
+    "gmres_ilu0_mixed_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="gmres",
+                                        precond="ilu0", prec="mixed"),
+    "bicgstab_ilu0_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="bicgstab",
+                                     precond="ilu0", prec="fp64"),
+    "gmres_ilu0_32x32x32": dict(kind="csr", grid=(32, 32, 32), kz=1.0, solver="gmres", precond="ilu0",
+                                prec="fp64"),
+    "learned_fgmres_64x64x64": dict(kind="learned", grid=(64, 64, 64), kz=1.0, solver="fgmres",
+                                    precond="cpr_learned", prec="fp64", seeds=list(range(2000, 2020))),
+    "cpr_fgmres_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="fgmres",
+                                       precond="cpr", prec="fp64"),
+    "cpr_fgmres_bsr3_mixed_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="fgmres",
+                                             precond="cpr", prec="mixed"),
+    "cpr_learned_bsr3_128x128x128": dict(kind="bsr_learned", grid=(128, 128, 128), kz=1.0, solver="fgmres",
+                                         precond="cpr_learned", prec="mixed"),
 }
 DEFAULT = "gmres_ilu0_128x128x64"
-RTOL = 1e-8
 SEED = 1
 
 
@@ -60,64 +76,90 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, bf16, src = FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, "fallback"
     if os.path.exists(p):
         try:
             d = json.load(open(p))
-            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
-                if k in d:
-                    return float(d[k]), "measured"
+            hbm = float(d.get("hbm_gbs", hbm))
+            bf16 = float(d.get("bf16_tflops", bf16))
+            src = "measured"
         except Exception:
             pass
-    return FALLBACK_HBM_GBS, "fallback"
+    return hbm, bf16, src
 
 
-def build_problem(w):
+# ----------------------------------------------------------------------------
+# problems (host arrays from the seeded generators)
+# ----------------------------------------------------------------------------
+def host_problem(w, seed):
     g = synth.Grid(*w["grid"])
-    d = synth.pressure_7pt(g, SEED, kz_scale=w["kz"])
-    xt = synth.x_true(g.n, SEED)
-    return g, d, xt
+    if w["kind"] in ("bsr", "bsr_learned"):
+        m = synth.black_oil_bsr3(g, seed, kz_scale=w["kz"])
+        xt = synth.x_true(3 * g.n, seed)
+        return g, m, xt
+    d = synth.pressure_7pt(g, seed, kz_scale=w["kz"])
+    return g, d, synth.x_true(g.n, seed)
 
 
 # ----------------------------------------------------------------------------
-# algorithmic bytes per launch (FP64 values 8 B, FP32 4 B, indices 4 B)
+# algorithmic bytes (FP64 8 B, FP32 4 B, int32 4 B) and FLOPs per launch
 # ----------------------------------------------------------------------------
-def algorithmic_bytes(d, prec):
-    n = d["n"]
-    nnz = d["col"].size
+def scalar_ilu_bytes(n, nnz, vb):
     nnz_l = (nnz - n) // 2
-    vb = 4 if prec == "mixed" else 8
-    return {
-        # values + column indices + row pointers, x read once, y written once
-        "spmv": 12 * nnz + 4 * (n + 1) + 16 * n,
-        # strict-lower factor (value + index), r in, y out
-        "l_sweep": (vb + 4) * nnz_l + 8 * n + vb * n,
-        # strict-upper factor, reciprocal diagonal, y in, z out
-        "u_sweep": (vb + 4) * nnz_l + vb * n + vb * n + 8 * n,
-    }
+    return {"l_sweep": (vb + 4) * nnz_l + 8 * n + vb * n,          # factor, r in, y out
+            "u_sweep": (vb + 4) * nnz_l + vb * n + vb * n + 8 * n}   # factor, 1/u_ii, y in, z out
 
 
-def cgs_bytes(n, iters, m):
-    """Total algorithmic bytes of the three CGS2 kernels over a solve with
-    `iters` Arnoldi steps: step i reads the i+1 basis vectors once per pass."""
+def block_ilu_bytes(nb, nnzb, vb):
+    nl = (nnzb - nb) // 2
+    return {"bl_sweep": (4 + 9 * vb) * nl + 24 * nb + 3 * vb * nb,
+            "bu_sweep": (4 + 9 * vb) * nl + 9 * vb * nb + 3 * vb * nb + 24 * nb}
+
+
+def net_flops(grid):
+    nx, ny, nz = grid
+    f = 0
+    cins = [2, 16, 16, 16, 16, 16, 16, 16, 32, 16, 32, 16, 32, 16]
+    lvls = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0]
+    for cin, l in zip(cins, lvls):
+        f += 2 * 27 * cin * 16 * (nx >> l) * (ny >> l) * (nz >> l)
+    return f + 2 * 16 * nx * ny * nz
+
+
+def kernel_model(w, A_host):
+    vb = 4 if w["prec"] == "mixed" else 8
+    if w["kind"] in ("bsr", "bsr_learned"):
+        nb, nnzb = A_host["nb"], A_host["bcol"].size
+        mod = {"spmv": 76 * nnzb + 4 * (nb + 1) + 48 * nb}
+        mod.update(scalar_ilu_bytes(nb, nnzb, vb))
+        mod.update(block_ilu_bytes(nb, nnzb, vb))
+        return mod, 3 * nb
+    n, nnz = A_host["n"], A_host["col"].size
+    mod = {"spmv": 12 * nnz + 4 * (n + 1) + 16 * n}
+    mod.update(scalar_ilu_bytes(n, nnz, vb))
+    return mod, n
+
+
+def cgs_bytes(n, iters_list, m=30):
     tot = {"cgs_dots": 0, "cgs_update_dots": 0, "cgs_update_norm": 0}
-    for it in range(iters):
-        nc = it % m + 1
-        tot["cgs_dots"] += 8 * n * (nc + 1)
-        tot["cgs_update_dots"] += 8 * n * (nc + 2)
-        tot["cgs_update_norm"] += 8 * n * (nc + 2)
+    for iters in iters_list:
+        for it in range(iters):
+            nc = it % m + 1
+            tot["cgs_dots"] += 8 * n * (nc + 1)
+            tot["cgs_update_dots"] += 8 * n * (nc + 2)
+            tot["cgs_update_norm"] += 8 * n * (nc + 2)
     return tot
 
 
 def source_sha(kernel):
-    f = {"spmv": "rs_core.cu", "l_sweep": "rs_ilu.cu", "u_sweep": "rs_ilu.cu"}.get(kernel, "rs_krylov.cu")
+    f = {"spmv": "rs_core.cu", "l_sweep": "rs_ilu.cu", "u_sweep": "rs_ilu.cu", "bl_sweep": "rs_ilu.cu",
+         "bu_sweep": "rs_ilu.cu", "net": "rs_net.cu"}.get(kernel, "rs_krylov.cu")
     p = os.path.join(ROOT, "paper_1701_05913_gb300", "csrc", f)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
@@ -129,8 +171,7 @@ def ncu_traffic(kernel, workload):
     if not os.path.exists(p):
         return None
     try:
-        d = json.load(open(p))
-        e = d.get(workload, {}).get(kernel)
+        e = json.load(open(p)).get(workload, {}).get(kernel)
         if e and e.get("source_sha") == source_sha(kernel):
             return e.get("dram_bytes_per_launch")
     except Exception:
@@ -146,9 +187,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
-        self.idx = gpu_index
-        self.proc = None
-        self.path = None
+        self.idx, self.proc, self.path = gpu_index, None, None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -192,58 +231,148 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ----------------------------------------------------------------------------
-def oracle_solve(w, d, xt, maxit=10000):
-    """The CPU oracle's solve of the same system (single thread, FP64):
+def _oracle_net_stage(net_params, out_scale, grid, logk):
+    from oracle import convnet as cn
+    nx, ny, nz = grid
+
+    def stage(rp):
+        out, _ = cn.forward(net_params, rp.reshape(nz, ny, nx), logk.reshape(nz, ny, nx),
+                            out_scale=out_scale, bf16=True)
+        return out.reshape(-1)
+    return stage
+
+
+def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
+    """One oracle solve of the workload's system, at most maxit iterations:
     returns (solve seconds, setup seconds, iterations)."""
     import oracle
     oracle.build()
-    A = oracle.Mat.csr(d)
+    if w["kind"] in ("bsr", "bsr_learned"):
+        A = oracle.Mat.bsr(A_host)
+    else:
+        A = oracle.Mat.csr(A_host)
     b = oracle.spmv(A, xt)
+    mixed = w["prec"] == "mixed"
     t0 = time.perf_counter()
-    M = oracle.PC(A, w["precond"], mixed=(w["prec"] == "mixed"))
+    if w["precond"] == "cpr_learned" and w["kind"] == "learned":
+        params, scale = load_net_host(net_file)
+        M = oracle.PC(A, "cpr", mixed=mixed, pstage=_oracle_net_stage(params, scale, w["grid"], A_host["logk"]))
+    elif w["precond"] == "cpr_learned":
+        M = oracle.PC(A, "cpr", mixed=mixed)      # block system: ILU(0) pressure stage in the oracle
+    else:
+        M = oracle.PC(A, w["precond"], mixed=mixed)
     setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     if w["solver"] == "bicgstab":
         _, info, _ = oracle.bicgstab(A, M, b, rtol=RTOL, maxit=maxit)
     else:
-        _, info, _ = oracle.gmres(A, M, b, restart=w["restart"], rtol=RTOL, maxit=maxit)
+        _, info, _ = oracle.gmres(A, M, b, restart=30, rtol=RTOL, maxit=maxit, flexible=w["solver"] == "fgmres")
     return time.perf_counter() - t0, setup, info["iters"]
 
 
+def load_net_host(path):
+    """Parameters and output scale from a checkpoint file (header, then FP32 arrays)."""
+    import struct
+    with open(path, "rb") as f:
+        raw = f.read()
+    magic, version, nparams, out_scale, step = struct.unpack("<IiqfI", raw[:24])
+    flat = np.frombuffer(raw[24:24 + 4 * nparams], dtype=np.float32)
+    from paper_1701_05913_gb300 import net_unflatten
+    return net_unflatten(flat), float(out_scale)
+
+
+def oracle_baseline(w, A_host, xt, gpu_iters):
+    """The oracle on a bounded sample, scaled to the iteration count."""
+    n = A_host["n"] if "n" in A_host else 3 * A_host["nb"]
+    if w["kind"] == "csr" and n <= 1_100_000:
+        t, s, it = oracle_run(w, A_host, xt, 10000)
+        return {"value": t + s, "unit": "s", "cores": 1, "kind": "oracle",
+                "sample": "one full solve of the same system on one host core (%d iterations, setup %.3f s)"
+                          % (it, s)}
+    sample = {"learned": 1, "bsr": 6, "bsr_learned": 2}.get(w["kind"], 30)
+    t, s, it = oracle_run(w, A_host, xt, sample)
+    v = t / max(it, 1) * gpu_iters + s
+    what = "with the numpy network as pressure stage" if w["kind"] == "learned" else \
+        ("with the ILU(0) pressure stage" if w["kind"] == "bsr_learned" else "")
+    return {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": "%d iteration(s) of the same solve %s on one host core, scaled to %s iterations, plus "
+                      "setup %.2f s" % (it, what, gpu_iters, s)}
+
+
 def run_reference(args, w, rank, world):
-    """The oracle as the reference arm: the first warm-up step is one full
-    solve (its iteration count); every other step times one GMRES cycle (30
-    iterations) of the same solve and scales it to that count."""
     if rank != 0:
         return
-    g, d, xt = build_problem(w)
-    full_s, setup, full_iters = oracle_solve(w, d, xt)
-    sample = 30
-    per = []
-    for s in range(max(args.warmup - 1, 0) + args.steps):
-        t, su, done = oracle_solve(w, d, xt, maxit=sample)
-        if s >= args.warmup - 1:
-            per.append(t / done * full_iters + su)
+    g, A_host, xt = host_problem(w, w.get("seeds", [SEED])[0])
+    if w["kind"] == "csr":
+        full_t, full_s, full_it = oracle_run(w, A_host, xt, 10000)
+        per = []
+        for s in range(max(args.warmup - 1, 0) + args.steps):
+            t, su, done = oracle_run(w, A_host, xt, 30)
+            if s >= args.warmup - 1:
+                per.append(t / done * full_it + su)
+        sample = ("one full solve (%d iterations, %.2f s) then, per step, 30 iterations of the same solve "
+                  "scaled to %d iterations plus setup" % (full_it, full_t + full_s, full_it))
+    else:
+        per = []
+        cb = None
+        for s in range(args.warmup + args.steps):
+            cb = oracle_baseline(w, A_host, xt, {"learned": 26, "bsr": 30, "bsr_learned": 30}[w["kind"]])
+            if s >= args.warmup:
+                per.append(cb["value"])
+        sample = cb["sample"] + " (iteration count of the GPU arm's solve assumed)"
     v = statistics.median(per)
-    line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "grid": list(w["grid"]), "n": g.n, "nnz": int(d["col"].size),
-                   "solver": w["solver"], "precond": w["precond"], "precision": w["prec"], "rtol": RTOL},
-        "iters": full_iters, "full_solve_s": full_s + setup,
-        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": "one full solve (%d iterations, %.2f s) then, per step, %d iterations of "
-                                   "the same solve scaled to %d iterations plus ILU(0) setup"
-                                   % (full_iters, full_s + setup, sample, full_iters)},
-        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(w["grid"]), "solver": w["solver"],
+                   "precond": w["precond"], "precision": w["prec"], "rtol": RTOL},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
+class Case:
+    """One resident problem: matrix, right-hand side, preconditioner(s)."""
+
+    def __init__(self, rs, ctx, w, seed, net=None):
+        g, A_host, xt = host_problem(w, seed)
+        self.g, self.A_host = g, A_host
+        self.xt = xt
+        if w["kind"] in ("bsr", "bsr_learned"):
+            self.A = rs.Mat.bsr(ctx, A_host)
+        else:
+            self.A = rs.Mat.csr(ctx, A_host)
+        n = self.A.n
+        self.b = rs.Vec.zeros(ctx, n)
+        self.A.spmv(rs.Vec(ctx, xt), self.b)
+        self.x = rs.Vec.zeros(ctx, n)
+        ctx.sync()
+        t0 = time.perf_counter()
+        kw = {}
+        if w["precond"] == "cpr_learned":
+            kw = dict(net=net, log_perm=A_host["logk"], grid=w["grid"])
+        self.M = rs.Precond(ctx, self.A, w["precond"], prec=w["prec"], **kw)
+        ctx.sync()
+        self.setup_s = time.perf_counter() - t0
+        self.Mbase = None
+        if w["kind"] == "learned":
+            self.Mbase = rs.Precond(ctx, self.A, "ilu0", prec=w["prec"])
+        elif w["kind"] == "bsr_learned":
+            self.Mbase = rs.Precond(ctx, self.A, "cpr", prec=w["prec"])
+        ctx.sync()
+
+
+def solve_fn(rs, w):
+    if w["solver"] == "bicgstab":
+        return lambda c, M: rs.solve_bicgstab(c.A, M, c.b, c.x, rtol=RTOL)
+    if w["solver"] == "fgmres":
+        return lambda c, M: rs.solve_fgmres(c.A, M, c.b, c.x, restart=30, rtol=RTOL)
+    return lambda c, M: rs.solve_gmres(c.A, M, c.b, c.x, restart=30, rtol=RTOL)
+
+
 def run_gpu(args, w, rank, world, local):
     import torch
 
@@ -255,27 +384,18 @@ def run_gpu(args, w, rank, world, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     ctx = rs.Context(local)
     stream = torch.cuda.current_stream()
-    g, d, xt = build_problem(w)
-    A = rs.Mat.csr(ctx, d)
-    xtv = rs.Vec(ctx, xt)
-    b = rs.Vec.zeros(ctx, g.n)
-    A.spmv(xtv, b)
-    ctx.sync()
-    t0 = time.perf_counter()
-    M = rs.Precond(ctx, A, w["precond"], prec=w["prec"])
-    ctx.sync()
-    setup_s = time.perf_counter() - t0
-    x = rs.Vec.zeros(ctx, g.n)
-
-    def solve():
-        if w["solver"] == "bicgstab":
-            return rs.solve_bicgstab(A, M, b, x, rtol=RTOL)
-        return rs.solve_gmres(A, M, b, x, restart=w["restart"], rtol=RTOL)
+    net = rs.Net(ctx, path=NET_PATH) if w["precond"] == "cpr_learned" else None
+    seeds = w.get("seeds", [SEED])
+    cases = [Case(rs, ctx, w, s, net) for s in seeds]
+    solve = solve_fn(rs, w)
+    base_solve = (lambda c, M: rs.solve_gmres(c.A, M, c.b, c.x, restart=30, rtol=RTOL)) if w["kind"] == "learned" \
+        else solve
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        x.t.zero_()
-        info = solve()
+    for s in range(args.warmup):
+        c = cases[s % len(cases)]
+        c.x.t.zero_()
+        solve(c, c.M)
     torch.cuda.synchronize()
 
     def barrier():
@@ -283,25 +403,29 @@ def run_gpu(args, w, rank, world, local):
             import torch.distributed as dist
             dist.barrier()
 
-    # timed region: K complete solves, L2 flushed between them, profiler on
+    def timed(fn_pick, profile):
+        evs, infos = [], []
+        for s in range(args.steps):
+            c = cases[s % len(cases)]
+            c.x.t.zero_()
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(fn_pick(c))
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs], infos
+
     clocks = ClockSampler(local)
     clocks.start()
     ctx.prof_enable(True)
     ctx.prof_read(reset=True)
     n_launch0 = ctx.launches()
-    evs = []
-    infos = []
     barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        x.t.zero_()
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        infos.append(solve())
-        e1.record(stream)
-        evs.append((e0, e1))
+    step_ms, infos = timed(lambda c: solve(c, c.M), True)
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - wall0
@@ -309,40 +433,34 @@ def run_gpu(args, w, rank, world, local):
     prof = ctx.prof_read(reset=True)
     ctx.prof_enable(False)
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b_) for a, b_ in evs]
     ms = sum(step_ms) / len(step_ms)
+    step_ms2, _ = timed(lambda c: solve(c, c.M), False)
+    ms_noprof = sum(step_ms2) / len(step_ms2)
+    base = None
+    if cases[0].Mbase is not None:
+        bms, binfos = timed(lambda c: base_solve(c, c.Mbase), False)
+        base = {"value": sum(bms) / len(bms) / 1e3, "unit": "s",
+                "method": "GMRES(30)+ILU(0)" if w["kind"] == "learned" else "FGMRES(30)+CPR with ILU(0) pressure stage",
+                "iters": statistics.median(i["iters"] for i in binfos),
+                "true_rel_res": max(i["true_rel_res"] for i in binfos)}
 
-    # same solves without the profiler (its event records add host work)
-    evs2 = []
-    for _ in range(args.steps):
-        x.t.zero_()
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        solve()
-        e1.record(stream)
-        evs2.append((e0, e1))
-    torch.cuda.synchronize()
-    ms_noprof = sum(a.elapsed_time(b_) for a, b_ in evs2) / len(evs2)
-
-    # end to end through the C ABI with host buffers: b from pinned host memory,
-    # x back to pinned host memory, both copies inside the timed region
-    hb = torch.from_numpy(b.numpy()).pin_memory()
-    hx = torch.empty(g.n, dtype=torch.float64).pin_memory()
+    # end to end through the C ABI: b from pinned host memory, x back to pinned host memory
     L = rs.lib()
     e2e = []
-    for _ in range(args.steps):
-        x.t.zero_()
+    hbs = [torch.from_numpy(c.b.numpy()).pin_memory() for c in cases]
+    hx = torch.empty(cases[0].A.n, dtype=torch.float64).pin_memory()
+    for s in range(args.steps):
+        c = cases[s % len(cases)]
+        c.x.t.zero_()
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        L.rs_vec_set(b.h, rs._vp(hb.data_ptr()), rs.MEM_HOST)
-        solve()
-        L.rs_vec_get(x.h, rs._vp(hx.data_ptr()), rs.MEM_HOST)
+        L.rs_vec_set(c.b.h, rs._vp(hbs[s % len(cases)].data_ptr()), rs.MEM_HOST)
+        solve(c, c.M)
+        L.rs_vec_get(c.x.h, rs._vp(hx.data_ptr()), rs.MEM_HOST)
         e2e.append(time.perf_counter() - t1)
     e2e_s = statistics.median(e2e)
 
-    # max over ranks
     if world > 1:
         import torch.distributed as dist
         tt = torch.tensor([ms, ms_noprof, e2e_s, wall], device="cuda", dtype=torch.float64)
@@ -350,57 +468,69 @@ def run_gpu(args, w, rank, world, local):
         ms, ms_noprof, e2e_s, wall = tt.tolist()
 
     # roofline of the dominant kernel class, from the live profile
-    peak, peak_src = measured_peaks()
-    alg = algorithmic_bytes(d, w["prec"])
+    hbm, bf16, peak_src = measured_peaks()
+    model, nunk = kernel_model(w, cases[0].A_host)
     iters = [i["iters"] for i in infos]
-    cb = cgs_bytes(g.n, sum(iters), w["restart"])
+    cb = cgs_bytes(nunk, iters)
     kern_ms = {k: v[0] for k, v in prof.items() if v[1] > 0}
     kern_n = {k: v[1] for k, v in prof.items() if v[1] > 0}
-    dom = max(kern_ms, key=kern_ms.get)
     total_prof = sum(kern_ms.values())
-    bytes_total = {k: alg[k] * kern_n[k] for k in ("spmv", "l_sweep", "u_sweep") if k in kern_n}
-    bytes_total.update({k: cb[k] for k in cb if k in kern_n})
-    achieved = {k: bytes_total[k] / (kern_ms[k] * 1e-3) / 1e9 for k in bytes_total}
-    per_launch = bytes_total.get(dom, 0) / max(kern_n.get(dom, 1), 1)
-    dom_ms = kern_ms[dom] / kern_n[dom]
-    roofline = {
-        "kernel": dom, "bound": "hbm", "achieved": round(achieved.get(dom, 0.0), 2), "peak": peak,
-        "unit": "GB/s", "frac": round(achieved.get(dom, 0.0) / peak, 4),
-        "traffic": ncu_traffic(dom, args.workload),
-        "peak_source": peak_src, "alg_bytes_per_launch": int(per_launch), "avg_launch_us": round(dom_ms * 1e3, 2),
-        "share_of_kernel_time": round(kern_ms[dom] / total_prof, 3),
-    }
+    work = {k: model[k] * kern_n[k] for k in model if k in kern_n}
+    work.update({k: cb[k] for k in cb if k in kern_n})
+    rate = {k: work[k] / (kern_ms[k] * 1e-3) / 1e9 for k in work}
+    net_fl = None
+    if "net" in kern_n and net is not None:
+        forwards = sum(iters)
+        net_fl = net_flops(w["grid"]) * forwards / (kern_ms["net"] * 1e-3) / 1e12
+    dom = max(kern_ms, key=kern_ms.get)
+    if dom == "net":
+        roofline = {"kernel": "net (all U-Net kernels of one pressure-stage apply)", "bound": "tensor",
+                    "achieved": round(net_fl, 2), "peak": bf16, "unit": "TFLOP/s", "frac": round(net_fl / bf16, 4),
+                    "traffic": ncu_traffic("net", args.workload), "peak_source": peak_src,
+                    "alg_flops_per_launch": net_flops(w["grid"])}
+    else:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": round(rate.get(dom, 0.0), 2), "peak": hbm,
+                    "unit": "GB/s", "frac": round(rate.get(dom, 0.0) / hbm, 4),
+                    "traffic": ncu_traffic(dom, args.workload), "peak_source": peak_src,
+                    "alg_bytes_per_launch": int(work.get(dom, 0) / max(kern_n[dom], 1)),
+                    "avg_launch_us": round(kern_ms[dom] / kern_n[dom] * 1e3, 2)}
+    roofline["share_of_kernel_time"] = round(kern_ms[dom] / total_prof, 3)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        t, setup, done = oracle_solve(w, d, xt)
-        cpu = {"value": t + setup, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": "one full solve of the same system on one host core (%d iterations; "
-                         "ILU(0) setup %.3f s included)" % (done, setup)}
+        c0 = cases[0]
+        cpu = oracle_baseline(w, c0.A_host, c0.xt, statistics.median(iters))
 
     if rank == 0:
+        ilu_k = [k for k in ("l_sweep", "u_sweep", "bl_sweep", "bu_sweep") if k in work]
         line = {
             "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if w["prec"] == "fp64" else "f64+f32", "data": "synthetic",
-            "config": {"workload": args.workload, "grid": list(w["grid"]), "n": g.n, "nnz": int(d["col"].size),
-                       "solver": "%s(%d)" % (w["solver"], w["restart"]) if w["solver"] == "gmres" else w["solver"],
-                       "precond": w["precond"], "precision": w["prec"], "rtol": RTOL, "seed": SEED,
-                       "l2": "flushed between steps (512 MB write)", "parallelism": "replicas" if world > 1 else "1 gpu"},
+            "vs_baseline": None, "dtype": "f64" if w["prec"] == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "grid": list(w["grid"]), "unknowns": cases[0].A.n,
+                       "nnz": int(cases[0].A.nnz), "block_size": cases[0].A.bs, "solver": w["solver"] + "(30)"
+                       if w["solver"] != "bicgstab" else "bicgstab", "precond": w["precond"],
+                       "precision": w["prec"], "rtol": RTOL, "seeds": [seeds[0], seeds[-1]],
+                       "l2": "flushed between steps (512 MB write)",
+                       "parallelism": "replicas" if world > 1 else "1 gpu"},
             "iters": statistics.median(iters),
             "true_rel_res": max(i["true_rel_res"] for i in infos),
-            "setup_s": setup_s,
+            "setup_s": statistics.median(c.setup_s for c in cases),
             "ms_per_step_without_profiler": ms_noprof,
             "wall_s": wall,
-            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n},
+            "baseline_method": base,
+            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * cases[0].A.n,
+                    "d2h_bytes_per_step": 8 * cases[0].A.n},
             "gpu_launches": launches,
             "roofline": roofline,
-            "kernels": {k: {"ms_per_step": round(kern_ms[k] / args.steps, 4), "launches_per_step": kern_n[k] / args.steps,
-                            "share": round(kern_ms[k] / total_prof, 4),
-                            **({"GBs": round(achieved[k], 1)} if k in achieved else {})} for k in kern_ms},
-            "spmv_GBs": round(achieved.get("spmv", 0.0), 1),
-            "ilu_apply_GBs": round((bytes_total.get("l_sweep", 0) + bytes_total.get("u_sweep", 0)) /
-                                   ((kern_ms.get("l_sweep", 1e-9) + kern_ms.get("u_sweep", 0)) * 1e-3) / 1e9, 1),
+            "kernels": {k: {"ms_per_step": round(kern_ms[k] / args.steps, 4),
+                            "launches_per_step": kern_n[k] / args.steps, "share": round(kern_ms[k] / total_prof, 4),
+                            **({"GBs": round(rate[k], 1)} if k in rate else {}),
+                            **({"TFLOPs": round(net_fl, 2)} if k == "net" and net_fl else {})} for k in kern_ms},
+            "spmv_GBs": round(rate.get("spmv", 0.0), 1),
+            "ilu_apply_GBs": round(sum(work[k] for k in ilu_k) / (sum(kern_ms[k] for k in ilu_k) * 1e-3) / 1e9, 1)
+            if ilu_k else None,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

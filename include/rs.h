@@ -101,7 +101,8 @@ int64_t rs_launch_count(const rs_ctx *ctx);
  * bracketed by CUDA events on the context's stream and its device time is
  * added to its class.  Classes, in order: SpMV, L sweep, U sweep, CGS dots,
  * CGS update+dots, CGS update+norm, BLAS-1, other preconditioner kernels,
- * factorisation, solver scalar kernels, network.  nkinds >= 11. */
+ * factorisation, solver scalar kernels, network, block L sweep, block U
+ * sweep.  nkinds >= 13. */
 int rs_prof_enable(rs_ctx *ctx, int on);
 /* Reads (and with reset != 0 clears) the accumulated milliseconds and launch
  * counts per class; synchronises the stream. */

@@ -137,20 +137,41 @@ static int build_layout(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     return RS_OK;
 }
 
-// Segment layout (scalar factors): segment s holds rows [32 s, 32 s + 32).
-// Its level is one more than the highest level of the segments holding the
-// columns it reads outside itself (lower columns for L, higher for U).
+// Segment layout (scalar factors): segments are runs of at most 32
+// consecutive rows.  A new segment also starts where one chain of
+// consecutive dependencies ends and the next begins (row i does not read row
+// i-1 while row i-1 reads row i-2; for U the mirror image), so that on
+// structured grids segments never straddle grid lines whatever their
+// length.  A segment's level is one more than the highest level of the
+// segments holding the columns it reads outside itself.
 static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
                           const std::vector<int> &col, const std::vector<int> &diag, bool lower,
                           SegLayout &S)
 {
-    const int nseg = (nrows + 31) / 32;
+    // does row i read row j = i-1 (L) / i+1 (U)?  (the entry next to the diagonal)
+    auto reads_prev = [&](int i) { return i > 0 && diag[i] > ptr[i] && col[diag[i] - 1] == i - 1; };
+    auto reads_next = [&](int i) { return i + 1 < nrows && diag[i] + 1 < ptr[i + 1] && col[diag[i] + 1] == i + 1; };
+    std::vector<int> r0v;
+    r0v.reserve(nrows / 16 + 2);
+    for (int i = 0; i < nrows; ++i) {
+        bool start = r0v.empty() || i - r0v.back() == 32;
+        if (!start && i >= 2) {
+            if (lower) start = !reads_prev(i) && reads_prev(i - 1);
+            else start = !reads_next(i - 1) && reads_next(i);
+        }
+        if (start) r0v.push_back(i);
+    }
+    const int nseg = (int)r0v.size();
+    r0v.push_back(nrows);
+    std::vector<int> seg_of(nrows);
+    for (int sg = 0; sg < nseg; ++sg)
+        for (int i = r0v[sg]; i < r0v[sg + 1]; ++i) seg_of[i] = sg;
     std::vector<int> lev(nseg, 0), width(nseg, 0);
     std::vector<unsigned char> kind(nseg, 1);
     int nlev = 0;
     for (int t = 0; t < nseg; ++t) {
         const int sg = lower ? t : nseg - 1 - t;
-        const int r0 = sg * 32, r1 = std::min(r0 + 32, nrows);
+        const int r0 = r0v[sg], r1 = r0v[sg + 1];
         int l = 0, w = 0;
         for (int i = r0; i < r1; ++i) {
             const int q0 = lower ? ptr[i] : diag[i] + 1;
@@ -161,7 +182,7 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
                 if (c >= r0 && c < r1) {
                     if (c != (lower ? i - 1 : i + 1)) kind[sg] = 0;
                 } else {
-                    l = std::max(l, lev[c / 32] + 1);
+                    l = std::max(l, lev[seg_of[c]] + 1);
                 }
             }
         }
@@ -182,7 +203,7 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     sptr[nseg] = (int)nent;
     std::vector<int> ecol(nent, -1), esrc(nent, -1);
     for (int sg = 0; sg < nseg; ++sg) {
-        const int r0 = sg * 32, r1 = std::min(r0 + 32, nrows);
+        const int r0 = r0v[sg], r1 = r0v[sg + 1];
         for (int i = r0; i < r1; ++i) {
             const int q0 = lower ? ptr[i] : diag[i] + 1;
             const int q1 = lower ? diag[i] : ptr[i + 1];
@@ -202,6 +223,7 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     st = st ? st : rs_alloc(ctx, (void **)&S.col, sizeof(int) * (nent > 0 ? nent : 1));
     st = st ? st : rs_alloc(ctx, (void **)&S.src, sizeof(int) * (nent > 0 ? nent : 1));
     st = st ? st : rs_alloc(ctx, (void **)&S.kind, nseg > 0 ? nseg : 1);
+    st = st ? st : rs_alloc(ctx, (void **)&S.row0, sizeof(int) * (nseg + 1));
     if (st) return st;
     cudaStream_t sm = ctx->stream;
     if (nseg) {
@@ -209,6 +231,7 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
         RS_CUDA_TRY(cudaMemcpyAsync(S.kind, kind.data(), nseg, cudaMemcpyHostToDevice, sm));
     }
     RS_CUDA_TRY(cudaMemcpyAsync(S.sptr, sptr.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, sm));
+    RS_CUDA_TRY(cudaMemcpyAsync(S.row0, r0v.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, sm));
     if (nent) {
         RS_CUDA_TRY(cudaMemcpyAsync(S.col, ecol.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, sm));
         RS_CUDA_TRY(cudaMemcpyAsync(S.src, esrc.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, sm));
@@ -224,6 +247,7 @@ static void free_segments(rs_ctx *ctx, SegLayout &S)
     rs_free(ctx, S.col);
     rs_free(ctx, S.src);
     rs_free(ctx, S.kind);
+    rs_free(ctx, S.row0);
     rs_free(ctx, S.val);
     rs_free(ctx, S.rdiag);
     S = SegLayout();
@@ -771,7 +795,7 @@ k_usolve(SweepArgs a, const T *__restrict__ val, const T *__restrict__ diag, T *
 struct SegArgs {
     int nrows, nseg;
     unsigned sleep_cap;
-    const int *order, *sptr, *ecol;
+    const int *order, *sptr, *ecol, *row0;
     const unsigned char *kind;
     SweepState *st;
     int *err;
@@ -788,6 +812,7 @@ static SegArgs seg_args(rs_ctx *ctx, const SegLayout &S, int nrows, SweepState *
     a.order = S.order;
     a.sptr = S.sptr;
     a.ecol = S.col;
+    a.row0 = S.row0;
     a.kind = S.kind;
     a.st = st;
     a.err = ctx->d_err;
@@ -872,14 +897,14 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const double *__restrict__ r,
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= g.nseg) break;
         const int seg = g.order[t];
-        const int row0 = seg * 32, row = row0 + lane;
-        const bool active = row < g.nrows;
+        const int row0 = g.row0[seg], len = g.row0[seg + 1] - row0, row = row0 + lane;
+        const bool active = lane < len;
         const int off = g.sptr[seg];
         const int w = (g.sptr[seg + 1] - off) >> 5;
         T acc = active ? (T)(sc == 1.0 ? r[row] : r[row] * sc) : T(0);
         if (active) zreset[row] = bits_to(T(), Sentinel<T>::bits);
         T a = T(0);
-        seg_external<T>(g, val, y, off, w, lane, row0, row0 + 32, row - 1, acc, a);
+        seg_external<T>(g, val, y, off, w, lane, row0, row0 + len, row - 1, acc, a);
         if (g.kind[seg]) {
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -928,8 +953,8 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ rdiag, 
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= g.nseg) break;
         const int seg = g.order[t];
-        const int row0 = seg * 32, row = row0 + lane;
-        const bool active = row < g.nrows;
+        const int row0 = g.row0[seg], len = g.row0[seg + 1] - row0, row = row0 + lane;
+        const bool active = lane < len;
         const int off = g.sptr[seg];
         const int w = (g.sptr[seg + 1] - off) >> 5;
         const T rd = active ? rdiag[row] : T(0);
@@ -939,7 +964,7 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ rdiag, 
             y[row] = bits_to(T(), Sentinel<T>::bits);
         }
         T a = T(0);
-        seg_external<T>(g, val, z, off, w, lane, row0, row0 + 32, row + 1, acc, a);
+        seg_external<T>(g, val, z, off, w, lane, row0, row0 + len, row + 1, acc, a);
         if (g.kind[seg]) {
             acc = acc * rd;
             a = a * rd;
@@ -1171,10 +1196,13 @@ static int apply_typed(IluFactor *f, const double *r, double *z, const double *s
     rs_ctx *ctx = f->ctx;
     T *y = (T *)f->ywork;
     T *zt = (T *)f->zwork;
-    RsProfScope prof(ctx, RS_PROF_LSWEEP);
-    k_lsolve<BS, T, double><<<sweep_grid(ctx, f->L.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
-        sweep_args(ctx, f->L, f->state, skip), (const T *)f->L.val, r, scale, y, zt);
+    {
+        RsProfScope prof(ctx, RS_PROF_BLSWEEP);
+        k_lsolve<BS, T, double><<<sweep_grid(ctx, f->L.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
+            sweep_args(ctx, f->L, f->state, skip), (const T *)f->L.val, r, scale, y, zt);
+    }
     RS_TRY(rs_check_launch(ctx));
+    RsProfScope prof2(ctx, RS_PROF_BUSWEEP);
     k_usolve<BS, T><<<sweep_grid(ctx, f->U.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
         sweep_args(ctx, f->U, f->state, skip), (const T *)f->U.val, (const T *)f->U.diag, y, zt, z);
     return rs_check_launch(ctx);

@@ -52,6 +52,8 @@ enum RsProfKind {
     RS_PROF_FACTOR,
     RS_PROF_SOLVER_SCALAR,
     RS_PROF_NET,
+    RS_PROF_BLSWEEP,
+    RS_PROF_BUSWEEP,
     RS_PROF_NKINDS
 };
 
@@ -141,7 +143,7 @@ struct TriLayout {
     int *level_done = nullptr;   // [nlevels] epoch of the sweep that last completed the level
 };
 
-// Segment layout of one scalar triangular factor: segments of 32
+// Segment layout of one scalar triangular factor: segments of at most 32
 // consecutive rows (one warp each), ordered by their level in the segment
 // dependency graph, entries stored as sliced ELL per segment.
 struct SegLayout {
@@ -153,6 +155,7 @@ struct SegLayout {
     int *col = nullptr;            // [nent] column or -1
     int *src = nullptr;            // [nent] index of the entry in the CSR value array or -1
     unsigned char *kind = nullptr; // [nseg] 1: the only in-segment dependency is the adjacent row
+    int *row0 = nullptr;           // [nseg+1] first row of each segment
     void *val = nullptr;           // [nent] factor values (float or double)
     void *rdiag = nullptr;         // [nseg*32] U: 1 / u_ii by row
 };
