@@ -146,6 +146,40 @@ def kernel_model(w, A_host):
     return mod, n
 
 
+def executed_launches(w, infos):
+    """Launches that did work (the rest returned at once on the device's
+    cycle-done flag), per kernel class, from each solve's iteration and
+    cycle counts.  GMRES: one SpMV and one preconditioner apply per Arnoldi
+    step, one true-residual SpMV per cycle plus the final check, and (right
+    preconditioning) one more apply per cycle for the update.  BiCGSTAB: two
+    SpMVs and two applies per iteration."""
+    cpr = w["precond"] in ("cpr", "cpr_learned")
+    block = w["kind"] in ("bsr", "bsr_learned")
+    cnt = {k: 0 for k in ("spmv", "l_sweep", "u_sweep", "bl_sweep", "bu_sweep", "net")}
+    for info in infos:
+        I, C = info["iters"], info["restarts"]
+        if w["solver"] == "bicgstab":
+            applies, spmv = 2 * I, 2 * I + 1
+        else:
+            applies = I + (0 if w["solver"] == "fgmres" else C)
+            spmv = I + C + 1
+        if cpr:
+            spmv += applies                      # residual of the two-stage apply
+        cnt["spmv"] += spmv
+        if w["precond"] == "cpr_learned":
+            cnt["net"] += applies
+        if block:
+            cnt["bl_sweep"] += applies
+            cnt["bu_sweep"] += applies
+            if w["precond"] == "cpr":
+                cnt["l_sweep"] += applies        # ILU(0) of the decoupled pressure matrix
+                cnt["u_sweep"] += applies
+        else:
+            cnt["l_sweep"] += applies            # ILU(0) (or the CPR second stage on A)
+            cnt["u_sweep"] += applies
+    return cnt
+
+
 def cgs_bytes(n, iters_list, m=30):
     tot = {"cgs_dots": 0, "cgs_update_dots": 0, "cgs_update_norm": 0}
     for iters in iters_list:
@@ -331,6 +365,18 @@ def run_reference(args, w, rank, world):
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks of the default
+    process group (a no-op without one); used for the slowest-rank timing."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -462,10 +508,7 @@ def run_gpu(args, w, rank, world, local):
     e2e_s = statistics.median(e2e)
 
     if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms, ms_noprof, e2e_s, wall], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, ms_noprof, e2e_s, wall = tt.tolist()
+        ms, ms_noprof, e2e_s, wall = max_over_ranks([ms, ms_noprof, e2e_s, wall], device="cuda")
 
     # roofline of the dominant kernel class, from the live profile
     hbm, bf16, peak_src = measured_peaks()
@@ -475,13 +518,13 @@ def run_gpu(args, w, rank, world, local):
     kern_ms = {k: v[0] for k, v in prof.items() if v[1] > 0}
     kern_n = {k: v[1] for k, v in prof.items() if v[1] > 0}
     total_prof = sum(kern_ms.values())
-    work = {k: model[k] * kern_n[k] for k in model if k in kern_n}
+    done = executed_launches(w, infos)
+    work = {k: model[k] * done[k] for k in model if k in kern_n and done.get(k)}
     work.update({k: cb[k] for k in cb if k in kern_n})
     rate = {k: work[k] / (kern_ms[k] * 1e-3) / 1e9 for k in work}
     net_fl = None
     if "net" in kern_n and net is not None:
-        forwards = sum(iters)
-        net_fl = net_flops(w["grid"]) * forwards / (kern_ms["net"] * 1e-3) / 1e12
+        net_fl = net_flops(w["grid"]) * done["net"] / (kern_ms["net"] * 1e-3) / 1e12
     dom = max(kern_ms, key=kern_ms.get)
     if dom == "net":
         roofline = {"kernel": "net (all U-Net kernels of one pressure-stage apply)", "bound": "tensor",
@@ -492,8 +535,9 @@ def run_gpu(args, w, rank, world, local):
         roofline = {"kernel": dom, "bound": "hbm", "achieved": round(rate.get(dom, 0.0), 2), "peak": hbm,
                     "unit": "GB/s", "frac": round(rate.get(dom, 0.0) / hbm, 4),
                     "traffic": ncu_traffic(dom, args.workload), "peak_source": peak_src,
-                    "alg_bytes_per_launch": int(work.get(dom, 0) / max(kern_n[dom], 1)),
-                    "avg_launch_us": round(kern_ms[dom] / kern_n[dom] * 1e3, 2)}
+                    "alg_bytes_per_launch": int(work.get(dom, 0) / max(done.get(dom, kern_n[dom]), 1)),
+                    "avg_launch_us": round(kern_ms[dom] / max(done.get(dom, kern_n[dom]), 1) * 1e3, 2),
+                    "launches_with_work": done.get(dom, kern_n[dom]), "launches_total": kern_n[dom]}
     roofline["share_of_kernel_time"] = round(kern_ms[dom] / total_prof, 3)
 
     cpu = None
@@ -525,7 +569,9 @@ def run_gpu(args, w, rank, world, local):
             "gpu_launches": launches,
             "roofline": roofline,
             "kernels": {k: {"ms_per_step": round(kern_ms[k] / args.steps, 4),
-                            "launches_per_step": kern_n[k] / args.steps, "share": round(kern_ms[k] / total_prof, 4),
+                            "launches_per_step": kern_n[k] / args.steps,
+                            **({"launches_with_work_per_step": done[k] / args.steps} if k in done else {}),
+                            "share": round(kern_ms[k] / total_prof, 4),
                             **({"GBs": round(rate[k], 1)} if k in rate else {}),
                             **({"TFLOPs": round(net_fl, 2)} if k == "net" and net_fl else {})} for k in kern_ms},
             "spmv_GBs": round(rate.get("spmv", 0.0), 1),

@@ -2,25 +2,21 @@
 //
 // The factorisation L U ~ A and the two solves L y = r, U z = y are Eq. 3
 // (Sec. 4.1); the paper notes these solves run row by row and scale poorly.
-// Here each row is one GPU thread and rows run as soon as the rows they depend
-// on are final ("sync-free" sweeps):
-//  * the host computes, once per pattern, the level of every row in the
-//    dependency graph of L (and of U) and orders the rows level by level,
-//    each level padded to a multiple of 32 so a warp never holds two levels;
-//  * the factors are stored in that order in a sliced-ELL layout (slices of
-//    32 rows, entry e of the 32 rows of a slice contiguous) so every load of
-//    factor data is coalesced;
-//  * blocks take consecutive work tickets from an atomic counter, so every
-//    row a thread waits for belongs to a block that is already running —
-//    the sweep cannot deadlock; each wait is also bounded in time and
-//    reports RS_ERR_DEVICE_TIMEOUT instead of hanging;
-//  * a row publishes its value with a release store of the sweep's epoch
-//    into its flag, so flags never need clearing; the last block of a sweep
-//    advances the epoch and resets the ticket (the sweep is self-cleaning).
-// The factorisation itself uses the same schedule (the rows that row i reads
-// are exactly its L-dependencies), runs the IKJ update in ascending column
-// order without contracted multiply-adds, and therefore produces the same
-// FP64 factors as a sequential row-by-row ILU(0).
+// Here rows run as soon as the rows they depend on are final ("sync-free"):
+//  * Factorisation: the host levels the rows of the dependency graph of L
+//    (each level padded to a multiple of 32 rows); persistent blocks take the
+//    rows in level order from a ticket counter, one row per thread; a warp
+//    waits until the previous level is complete (a per-level arrival count
+//    and a completion epoch), then runs the IKJ update in ascending column
+//    order without contracted multiply-adds, so the FP64 factors equal those
+//    of a sequential row-by-row ILU(0).
+//  * Sweeps: rows are grouped into segments of up to 32 consecutive (block)
+//    rows, one warp each, taken in segment-level order; a row's value is its
+//    own ready flag (a sentinel NaN pattern until written); the in-segment
+//    recurrence is solved with a warp scan (details at the kernels).
+//  * Every wait is bounded in time and reports RS_ERR_DEVICE_TIMEOUT instead
+//    of hanging; every schedule is deadlock-free because a warp only waits for
+//    rows held by warps that took earlier tickets and are already running.
 #include <math.h>
 
 #include <algorithm>
@@ -34,25 +30,16 @@
 // host analysis
 // ---------------------------------------------------------------------------
 static int build_layout(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
-                        const std::vector<int> &col, const std::vector<int> &diag, bool lower,
-                        TriLayout &T)
+                        const std::vector<int> &col, const std::vector<int> &diag, TriLayout &T)
 {
+    // level of each row in the dependency graph of L
     std::vector<int> lev(nrows, 0);
     int nlev = 0;
-    if (lower) {
-        for (int i = 0; i < nrows; ++i) {
-            int l = 0;
-            for (int q = ptr[i]; q < diag[i]; ++q) l = std::max(l, lev[col[q]] + 1);
-            lev[i] = l;
-            nlev = std::max(nlev, l + 1);
-        }
-    } else {
-        for (int i = nrows - 1; i >= 0; --i) {
-            int l = 0;
-            for (int q = diag[i] + 1; q < ptr[i + 1]; ++q) l = std::max(l, lev[col[q]] + 1);
-            lev[i] = l;
-            nlev = std::max(nlev, l + 1);
-        }
+    for (int i = 0; i < nrows; ++i) {
+        int l = 0;
+        for (int q = ptr[i]; q < diag[i]; ++q) l = std::max(l, lev[col[q]] + 1);
+        lev[i] = l;
+        nlev = std::max(nlev, l + 1);
     }
     std::vector<int> cnt(nlev + 1, 0);
     for (int i = 0; i < nrows; ++i) cnt[lev[i]]++;
@@ -62,74 +49,26 @@ static int build_layout(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     if (npad > 0x7fffffffLL) return RS_ERR_INVALID_ARG;
     std::vector<int> pos(npad, -1);
     std::vector<int64_t> fill(start.begin(), start.end());
-    if (lower) {
-        for (int i = 0; i < nrows; ++i) pos[fill[lev[i]]++] = i;
-    } else {
-        for (int i = nrows - 1; i >= 0; --i) pos[fill[lev[i]]++] = i;
-    }
-    const int nslices = (int)(npad / 32);
-    std::vector<int> sptr(nslices + 1, 0);
-    int64_t nent = 0;
-    for (int s = 0; s < nslices; ++s) {
-        int w = 0;
-        for (int l = 0; l < 32; ++l) {
-            const int row = pos[s * 32 + l];
-            if (row < 0) continue;
-            const int c = lower ? diag[row] - ptr[row] : ptr[row + 1] - diag[row] - 1;
-            w = std::max(w, c);
-        }
-        sptr[s] = (int)nent;
-        nent += (int64_t)w * 32;
-        if (nent > 0x7fffffffLL) return RS_ERR_INVALID_ARG;
-    }
-    sptr[nslices] = (int)nent;
-    std::vector<int> ecol(nent, -1), esrc(nent, -1), dsrc(npad, -1);
-    for (int s = 0; s < nslices; ++s) {
-        for (int l = 0; l < 32; ++l) {
-            const int row = pos[s * 32 + l];
-            if (row < 0) continue;
-            const int q0 = lower ? ptr[row] : diag[row] + 1;
-            const int q1 = lower ? diag[row] : ptr[row + 1];
-            for (int q = q0; q < q1; ++q) {
-                const int64_t e = sptr[s] + (int64_t)(q - q0) * 32 + l;
-                ecol[e] = col[q];
-                esrc[e] = q;
-            }
-            dsrc[s * 32 + l] = diag[row];
-        }
-    }
-    T.npad = (int)npad;
-    T.nslices = nslices;
-    T.nlevels = nlev;
-    T.nent = nent;
-    T.nwarps = nslices;
-    std::vector<int> wlev(nslices), lnw(nlev > 0 ? nlev : 1, 0);
+    for (int i = 0; i < nrows; ++i) pos[fill[lev[i]]++] = i;
+    const int nwarps = (int)(npad / 32);
+    std::vector<int> wlev(nwarps > 0 ? nwarps : 1), lnw(nlev > 0 ? nlev : 1, 0);
     for (int l = 0; l < nlev; ++l) {
         lnw[l] = (int)((start[l + 1] - start[l]) / 32);
         for (int64_t wi = start[l] / 32; wi < start[l + 1] / 32; ++wi) wlev[wi] = l;
     }
+    T.npad = (int)npad;
+    T.nlevels = nlev;
+    T.nwarps = nwarps;
     int st = RS_OK;
-    st = st ? st : rs_alloc(ctx, (void **)&T.pos, sizeof(int) * npad);
-    st = st ? st : rs_alloc(ctx, (void **)&T.slice_ptr, sizeof(int) * (nslices + 1));
-    st = st ? st : rs_alloc(ctx, (void **)&T.col, sizeof(int) * nent);
-    st = st ? st : rs_alloc(ctx, (void **)&T.src, sizeof(int) * nent);
-    st = st ? st : rs_alloc(ctx, (void **)&T.dsrc, sizeof(int) * npad);
-    st = st ? st : rs_alloc(ctx, (void **)&T.warp_level, sizeof(int) * (nslices > 0 ? nslices : 1));
+    st = st ? st : rs_alloc(ctx, (void **)&T.pos, sizeof(int) * (npad > 0 ? npad : 1));
+    st = st ? st : rs_alloc(ctx, (void **)&T.warp_level, sizeof(int) * wlev.size());
     st = st ? st : rs_alloc(ctx, (void **)&T.level_nwarps, sizeof(int) * lnw.size());
     st = st ? st : rs_alloc(ctx, (void **)&T.level_count, sizeof(int) * lnw.size());
     st = st ? st : rs_alloc(ctx, (void **)&T.level_done, sizeof(int) * lnw.size());
     if (st) return st;
     cudaStream_t s = ctx->stream;
-    RS_CUDA_TRY(cudaMemcpyAsync(T.pos, pos.data(), sizeof(int) * npad, cudaMemcpyHostToDevice, s));
-    RS_CUDA_TRY(cudaMemcpyAsync(T.slice_ptr, sptr.data(), sizeof(int) * (nslices + 1),
-                                cudaMemcpyHostToDevice, s));
-    if (nent) {
-        RS_CUDA_TRY(cudaMemcpyAsync(T.col, ecol.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, s));
-        RS_CUDA_TRY(cudaMemcpyAsync(T.src, esrc.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, s));
-    }
-    RS_CUDA_TRY(cudaMemcpyAsync(T.dsrc, dsrc.data(), sizeof(int) * npad, cudaMemcpyHostToDevice, s));
-    if (nslices)
-        RS_CUDA_TRY(cudaMemcpyAsync(T.warp_level, wlev.data(), sizeof(int) * nslices, cudaMemcpyHostToDevice, s));
+    if (npad) RS_CUDA_TRY(cudaMemcpyAsync(T.pos, pos.data(), sizeof(int) * npad, cudaMemcpyHostToDevice, s));
+    RS_CUDA_TRY(cudaMemcpyAsync(T.warp_level, wlev.data(), sizeof(int) * wlev.size(), cudaMemcpyHostToDevice, s));
     RS_CUDA_TRY(cudaMemcpyAsync(T.level_nwarps, lnw.data(), sizeof(int) * lnw.size(), cudaMemcpyHostToDevice, s));
     RS_CUDA_TRY(cudaMemsetAsync(T.level_count, 0, sizeof(int) * lnw.size(), s));
     RS_CUDA_TRY(cudaMemsetAsync(T.level_done, 0, sizeof(int) * lnw.size(), s));
@@ -256,12 +195,6 @@ static void free_segments(rs_ctx *ctx, SegLayout &S)
 static void free_layout(rs_ctx *ctx, TriLayout &T)
 {
     rs_free(ctx, T.pos);
-    rs_free(ctx, T.slice_ptr);
-    rs_free(ctx, T.col);
-    rs_free(ctx, T.src);
-    rs_free(ctx, T.dsrc);
-    rs_free(ctx, T.val);
-    rs_free(ctx, T.diag);
     rs_free(ctx, T.warp_level);
     rs_free(ctx, T.level_nwarps);
     rs_free(ctx, T.level_count);
@@ -281,8 +214,7 @@ static void free_layout(rs_ctx *ctx, TriLayout &T)
 // publishes the level with a release store of the sweep's epoch.
 struct SweepArgs {
     int npad;
-    int64_t nent;
-    const int *pos, *sptr, *ecol;
+    const int *pos;
     const int *wlev, *lnw;
     int *lcount, *ldone;
     SweepState *st;
@@ -295,10 +227,7 @@ static SweepArgs sweep_args(rs_ctx *ctx, const TriLayout &T, SweepState *st, con
 {
     SweepArgs a;
     a.npad = T.npad;
-    a.nent = T.nent;
     a.pos = T.pos;
-    a.sptr = T.slice_ptr;
-    a.ecol = T.col;
     a.wlev = T.warp_level;
     a.lnw = T.level_nwarps;
     a.lcount = T.level_count;
@@ -513,37 +442,15 @@ __global__ void k_gather_tri(int64_t nent, int b2, const int *__restrict__ src,
     }
 }
 
-// diagonal of U per position: u_ii (FP32) or 1/u_ii (FP64) for scalars,
-// inv(U_II) for blocks
-template <typename T>
-__global__ void k_gather_diag(int npad, int b2, const int *__restrict__ pos, const int *__restrict__ dsrc,
-                              const double *__restrict__ lu, const double *__restrict__ dinv,
-                              T *__restrict__ diag)
-{
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npad; p += gridDim.x * blockDim.x) {
-        const int row = pos[p];
-        for (int x = 0; x < b2; ++x) {
-            double v = 1.0;
-            if (row >= 0) {
-                if (b2 > 1) v = dinv[(size_t)row * b2 + x];
-                else v = sizeof(T) == sizeof(double) ? 1.0 / lu[dsrc[p]] : lu[dsrc[p]];
-            }
-            diag[(size_t)x * npad + p] = (T)v;
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
-// triangular sweeps
+// triangular sweeps: the value is its own ready flag
 // ---------------------------------------------------------------------------
-// The value of a row is its own ready flag: before a sweep every entry of its
-// work vector holds a signalling-NaN bit pattern that arithmetic never
-// produces; a thread polls the entries it depends on until they change, and
-// publishes its row with one plain 8-byte (or 4-byte) store, which is
-// single-copy atomic.  The L sweep resets the U sweep's work vector to the
-// sentinel (row by row) and the U sweep resets the L sweep's, so no clearing
-// pass is needed.  Every index and factor value a row needs is loaded before
-// its first wait; only the dependency values are read after it.
+// Before a sweep every entry of its work vector holds a signalling-NaN bit
+// pattern that arithmetic never produces; a warp polls the entries it depends
+// on until they change, and publishes each value with one plain 8-byte (or
+// 4-byte) store, which is single-copy atomic.  The L sweep resets the U
+// sweep's work vector to the sentinel (row by row) and the U sweep resets the
+// L sweep's, so no clearing pass is needed.
 template <typename T> struct Sentinel;
 template <> struct Sentinel<double> {
     typedef unsigned long long bits_t;
@@ -577,31 +484,6 @@ __device__ __forceinline__ void st_relaxed(float *p, float v)
 __device__ __forceinline__ double bits_to(double, unsigned long long b) { return __longlong_as_double((long long)b); }
 __device__ __forceinline__ float bits_to(float, unsigned int b) { return __uint_as_float(b); }
 
-// Returns the value at p once it is no longer the sentinel (bounded wait).
-template <typename T>
-__device__ __forceinline__ T wait_value(const T *p, long long limit, int *err)
-{
-    typedef typename Sentinel<T>::bits_t B;
-    B v = ld_relaxed_bits(p);
-    if (v != Sentinel<T>::bits) return bits_to(T(), v);
-    for (int spin = 0; spin < 4; ++spin) {
-        v = ld_relaxed_bits(p);
-        if (v != Sentinel<T>::bits) return bits_to(T(), v);
-    }
-    const long long t0 = clock64();
-    unsigned ns = 32;
-    for (;;) {
-        __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
-        v = ld_relaxed_bits(p);
-        if (v != Sentinel<T>::bits) return bits_to(T(), v);
-        if (clock64() - t0 > limit) {
-            atomicOr(err, RS_DEVERR_TIMEOUT);
-            return bits_to(T(), v);
-        }
-    }
-}
-
 template <typename T>
 __global__ void k_fill_sentinel(int64_t n, T *v)
 {
@@ -609,194 +491,34 @@ __global__ void k_fill_sentinel(int64_t n, T *v)
         v[i] = bits_to(T(), Sentinel<T>::bits);
 }
 
-// persistent ticketed loop over positions (no level synchronisation)
-template <class Body>
-__device__ __forceinline__ void run_rows(const SweepArgs &a, Body body)
-{
-    if (a.skip && *(volatile const int *)a.skip) return;   // uniform over the grid
-    __shared__ int s_base;
-    for (;;) {
-        if (threadIdx.x == 0) s_base = (int)atomicAdd(&a.st->ticket, 1u) * (int)blockDim.x;
-        __syncthreads();
-        const int base = s_base;
-        __syncthreads();
-        if (base >= a.npad) break;
-        const int p = base + threadIdx.x;
-        if (p < a.npad) body(p);
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&a.st->done, 1u) == gridDim.x - 1) {
-            a.st->ticket = 0;
-            a.st->done = 0;
-            __threadfence();
-        }
-    }
-}
-
-#define RS_PREFETCH 4   // sliced-ELL entries loaded ahead of the waits
-
-// Arithmetic of the sweeps.  FP32 (the mixed-precision apply): separately
-// rounded multiply and subtract and a true division, in ascending column
-// order — the rounding of a sequential row-by-row solve.  FP64: fused
-// multiply-adds and a multiply by the stored reciprocal of u_ii, because
-// FP64 instructions are scarce on this GPU and sit on the sweep's critical
-// path (one row per level step).
+// Arithmetic of the sweeps.  FP64 uses fused multiply-adds (FP64
+// instructions are scarce on this GPU and sit on the critical path); FP32
+// (the mixed-precision apply) rounds the product and the difference
+// separately, in ascending column order.
 __device__ __forceinline__ double msub(double acc, double a, double b) { return fma(-a, b, acc); }
 __device__ __forceinline__ float msub(float acc, float a, float b) { return __fsub_rn(acc, __fmul_rn(a, b)); }
-__device__ __forceinline__ double madd(double acc, double a, double b) { return fma(a, b, acc); }
-__device__ __forceinline__ float madd(float acc, float a, float b) { return __fadd_rn(acc, __fmul_rn(a, b)); }
-__device__ __forceinline__ double udiv(double a, double rdiag) { return a * rdiag; }
-__device__ __forceinline__ float udiv(float a, float diag) { return __fdiv_rn(a, diag); }
-
-// Loads the BS values of every prefetched dependency at once, then polls
-// again only those still holding the sentinel.
-template <int BS, typename T>
-__device__ __forceinline__ void gather_ready(const T *vec, const int (&c)[RS_PREFETCH],
-                                             T (&out)[RS_PREFETCH][BS], long long limit, int *err)
-{
-    typedef typename Sentinel<T>::bits_t B;
-    B b[RS_PREFETCH][BS];
-#pragma unroll
-    for (int j = 0; j < RS_PREFETCH; ++j)
-#pragma unroll
-        for (int k = 0; k < BS; ++k) b[j][k] = c[j] >= 0 ? ld_relaxed_bits(vec + (size_t)c[j] * BS + k) : (B)0;
-#pragma unroll
-    for (int j = 0; j < RS_PREFETCH; ++j)
-#pragma unroll
-        for (int k = 0; k < BS; ++k) {
-            if (c[j] >= 0 && b[j][k] == Sentinel<T>::bits)
-                out[j][k] = wait_value(vec + (size_t)c[j] * BS + k, limit, err);
-            else
-                out[j][k] = bits_to(T(), b[j][k]);
-        }
-}
-
-// L y = r (unit lower).  TI: type of r; T: working type.  scale (device,
-// optional) multiplies r on load.  zreset: the U sweep's work vector.
-template <int BS, typename T, typename TI>
-__global__ void __launch_bounds__(RS_SWEEP_THREADS)
-k_lsolve(SweepArgs a, const T *__restrict__ val, const TI *__restrict__ r,
-         const double *__restrict__ scale, T *y, T *zreset)
-{
-    run_rows(a, [&](int p) {
-        const int row = a.pos[p];
-        if (row < 0) return;
-        const int s = p >> 5, lane = p & 31;
-        const int off = a.sptr[s];
-        const int w = (a.sptr[s + 1] - off) >> 5;
-        const double sc = scale ? *scale : 1.0;
-        T acc[BS];
-#pragma unroll
-        for (int k = 0; k < BS; ++k) {
-            acc[k] = (T)(sc == 1.0 ? (double)r[(size_t)row * BS + k] : __dmul_rn((double)r[(size_t)row * BS + k], sc));
-            zreset[(size_t)row * BS + k] = bits_to(T(), Sentinel<T>::bits);
-        }
-        for (int e0 = 0; e0 < w; e0 += RS_PREFETCH) {
-            int c[RS_PREFETCH];
-            T v[RS_PREFETCH][BS * BS];
-#pragma unroll
-            for (int j = 0; j < RS_PREFETCH; ++j) {
-                const int idx = off + (e0 + j) * 32 + lane;
-                c[j] = e0 + j < w ? a.ecol[idx] : -1;
-#pragma unroll
-                for (int q = 0; q < BS * BS; ++q) v[j][q] = c[j] >= 0 ? val[(size_t)q * a.nent + idx] : T(0);
-            }
-            T yc[RS_PREFETCH][BS];
-            gather_ready<BS, T>(y, c, yc, a.limit, a.err);
-#pragma unroll
-            for (int j = 0; j < RS_PREFETCH; ++j) {
-                if (c[j] < 0) continue;
-#pragma unroll
-                for (int i = 0; i < BS; ++i)
-#pragma unroll
-                    for (int k = 0; k < BS; ++k) acc[i] = msub(acc[i], v[j][i * BS + k], yc[j][k]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < BS; ++k) st_relaxed(y + (size_t)row * BS + k, acc[k]);
-    });
-}
-
-// U z = y.  z (type T) carries values between rows (and is reset to the
-// sentinel by the next L sweep); out (FP64) receives the result; y is reset
-// to the sentinel for the next L sweep.
-template <int BS, typename T>
-__global__ void __launch_bounds__(RS_SWEEP_THREADS)
-k_usolve(SweepArgs a, const T *__restrict__ val, const T *__restrict__ diag, T *y, T *z,
-         double *__restrict__ out)
-{
-    run_rows(a, [&](int p) {
-        const int row = a.pos[p];
-        if (row < 0) return;
-        const int s = p >> 5, lane = p & 31;
-        const int off = a.sptr[s];
-        const int w = (a.sptr[s + 1] - off) >> 5;
-        T acc[BS], dg[BS * BS];
-#pragma unroll
-        for (int k = 0; k < BS; ++k) {
-            acc[k] = y[(size_t)row * BS + k];
-            y[(size_t)row * BS + k] = bits_to(T(), Sentinel<T>::bits);
-        }
-#pragma unroll
-        for (int q = 0; q < BS * BS; ++q) dg[q] = diag[(size_t)q * a.npad + p];
-        for (int e0 = 0; e0 < w; e0 += RS_PREFETCH) {
-            int c[RS_PREFETCH];
-            T v[RS_PREFETCH][BS * BS];
-#pragma unroll
-            for (int j = 0; j < RS_PREFETCH; ++j) {
-                const int idx = off + (e0 + j) * 32 + lane;
-                c[j] = e0 + j < w ? a.ecol[idx] : -1;
-#pragma unroll
-                for (int q = 0; q < BS * BS; ++q) v[j][q] = c[j] >= 0 ? val[(size_t)q * a.nent + idx] : T(0);
-            }
-            T zc[RS_PREFETCH][BS];
-            gather_ready<BS, T>(z, c, zc, a.limit, a.err);
-#pragma unroll
-            for (int j = 0; j < RS_PREFETCH; ++j) {
-                if (c[j] < 0) continue;
-#pragma unroll
-                for (int i = 0; i < BS; ++i)
-#pragma unroll
-                    for (int k = 0; k < BS; ++k) acc[i] = msub(acc[i], v[j][i * BS + k], zc[j][k]);
-            }
-        }
-        T res[BS];
-        if (BS == 1) {
-            res[0] = udiv(acc[0], dg[0]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < BS; ++i) {
-                T sum = 0;
-#pragma unroll
-                for (int k = 0; k < BS; ++k) sum = madd(sum, dg[i * BS + k], acc[k]);
-                res[i] = sum;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < BS; ++k) {
-            st_relaxed(z + (size_t)row * BS + k, res[k]);
-            out[(size_t)row * BS + k] = (double)res[k];
-        }
-    });
-}
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
 
 // ---------------------------------------------------------------------------
-// segment sweeps (scalar factors)
+// segment sweeps
 // ---------------------------------------------------------------------------
-// One warp per segment of 32 consecutive rows, segments taken in level
-// order from a warp-granular ticket.  Each lane subtracts the contributions
-// of its row's columns outside the segment (loaded together, polled on the
-// sentinel).  What remains inside the segment is, for the usual stencils in
-// natural order, a first-order recurrence y_t = c_t + a_t y_{t-1} (L) or
-// z_t = c_t + a_t z_{t+1} (U), solved with a 5-step warp scan of affine
-// maps; any other in-segment pattern is resolved lane by lane with
-// broadcasts.
+// One warp per segment (up to 32 consecutive rows or block rows), segments
+// taken in level order from a warp-granular ticket, so every awaited segment
+// is held by a warp that is already running.  Each lane subtracts the
+// contributions of its row's columns outside the segment (loaded together,
+// polled on the sentinel).  What remains inside the segment is, for the usual
+// stencils in natural order, a first-order recurrence y_t = c_t + A_t y_{t-1}
+// (L) or z_t = c_t + A_t z_{t+1} (U) with A_t a bs x bs block, solved by a
+// 5-step warp scan of affine maps; any other in-segment pattern is resolved
+// lane by lane with broadcasts.
 struct SegArgs {
     int nrows, nseg;
     unsigned sleep_cap;
     const int *order, *sptr, *ecol, *row0;
     const unsigned char *kind;
+    int64_t nent;
+    int npr;                 // padded row count of the diagonal arrays
     SweepState *st;
     int *err;
     long long limit;
@@ -814,6 +536,8 @@ static SegArgs seg_args(rs_ctx *ctx, const SegLayout &S, int nrows, SweepState *
     a.ecol = S.col;
     a.row0 = S.row0;
     a.kind = S.kind;
+    a.nent = S.nent;
+    a.npr = S.nseg * 32;
     a.st = st;
     a.err = ctx->d_err;
     a.limit = ctx->spin_limit;
@@ -821,44 +545,43 @@ static SegArgs seg_args(rs_ctx *ctx, const SegLayout &S, int nrows, SweepState *
     return a;
 }
 
-#define RS_SEG_CHUNK 8
-
-template <typename T>
-__device__ __forceinline__ T fmadd(T a, T b, T c) { return fma(a, b, c); }
-
-// acc -= sum of v * x[c] over this lane's entries with columns outside
-// [lo, hi); records the coefficient of column `adj` (the adjacent row) in a.
+// acc -= sum of V_e x[c_e] over this lane's entries whose block column lies
+// outside [lo, hi); the entry of block column `adj` is returned negated in a.
 // All lanes load their outside values at once; while any lane still sees a
-// sentinel the whole warp sleeps once and reloads only the pending values,
-// so the warp stays converged and polls with coalesced loads.
-template <typename T>
-__device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restrict__ val, const T *x,
-                                             int off, int w, int lane, int lo, int hi, int adj,
-                                             T &acc, T &a)
+// sentinel the whole warp sleeps once and reloads only the pending values.
+template <int BS, typename T>
+__device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restrict__ val, const T *x, int off,
+                                             int w, int lane, int lo, int hi, int adj, T (&acc)[BS],
+                                             T (&a)[BS * BS])
 {
     typedef typename Sentinel<T>::bits_t B;
-    for (int e0 = 0; e0 < w; e0 += RS_SEG_CHUNK) {
-        int c[RS_SEG_CHUNK];
-        T v[RS_SEG_CHUNK];
-        B b[RS_SEG_CHUNK];
-        bool ext[RS_SEG_CHUNK];
+    constexpr int CH = BS == 1 ? 8 : 4;
+    for (int e0 = 0; e0 < w; e0 += CH) {
+        int c[CH];
+        T v[CH][BS * BS];
+        B b[CH][BS];
+        bool ext[CH];
 #pragma unroll
-        for (int j = 0; j < RS_SEG_CHUNK; ++j) {
-            const int idx = off + (e0 + j) * 32 + lane;
+        for (int j = 0; j < CH; ++j) {
+            const int64_t idx = off + (int64_t)(e0 + j) * 32 + lane;
             c[j] = e0 + j < w ? g.ecol[idx] : -1;
-            v[j] = c[j] >= 0 ? val[idx] : T(0);
+#pragma unroll
+            for (int q = 0; q < BS * BS; ++q) v[j][q] = c[j] >= 0 ? val[q * g.nent + idx] : T(0);
         }
 #pragma unroll
-        for (int j = 0; j < RS_SEG_CHUNK; ++j) {
+        for (int j = 0; j < CH; ++j) {
             ext[j] = c[j] >= 0 && (c[j] < lo || c[j] >= hi);
-            b[j] = ext[j] ? ld_relaxed_bits(x + c[j]) : (B)0;
+#pragma unroll
+            for (int k = 0; k < BS; ++k) b[j][k] = ext[j] ? ld_relaxed_bits(x + (size_t)c[j] * BS + k) : (B)0;
         }
         unsigned ns = 0;
         long long t0 = 0;
         for (;;) {
             bool pend = false;
 #pragma unroll
-            for (int j = 0; j < RS_SEG_CHUNK; ++j) pend |= ext[j] && b[j] == Sentinel<T>::bits;
+            for (int j = 0; j < CH; ++j)
+#pragma unroll
+                for (int k = 0; k < BS; ++k) pend |= ext[j] && b[j][k] == Sentinel<T>::bits;
             if (!__any_sync(0xffffffffu, pend)) break;
             if (ns == 0) {
                 t0 = clock64();
@@ -871,19 +594,72 @@ __device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restri
             }
             ns = ns == 0 ? 16 : min(ns * 2, g.sleep_cap);
 #pragma unroll
-            for (int j = 0; j < RS_SEG_CHUNK; ++j)
-                if (ext[j] && b[j] == Sentinel<T>::bits) b[j] = ld_relaxed_bits(x + c[j]);
+            for (int j = 0; j < CH; ++j)
+#pragma unroll
+                for (int k = 0; k < BS; ++k)
+                    if (ext[j] && b[j][k] == Sentinel<T>::bits) b[j][k] = ld_relaxed_bits(x + (size_t)c[j] * BS + k);
         }
 #pragma unroll
-        for (int j = 0; j < RS_SEG_CHUNK; ++j) {
+        for (int j = 0; j < CH; ++j) {
             if (c[j] < 0) continue;
-            if (ext[j]) acc = msub(acc, v[j], bits_to(T(), b[j]));
-            else if (c[j] == adj) a = -v[j];
+            if (ext[j]) {
+#pragma unroll
+                for (int i = 0; i < BS; ++i)
+#pragma unroll
+                    for (int k = 0; k < BS; ++k) acc[i] = msub(acc[i], v[j][i * BS + k], bits_to(T(), b[j][k]));
+            } else if (c[j] == adj) {
+#pragma unroll
+                for (int q = 0; q < BS * BS; ++q) a[q] = -v[j][q];
+            }
         }
     }
 }
 
-template <typename T>
+// affine-map scan step: (a, acc) <- (a, acc) composed with the map of lane
+// `lane - o` (up = true) or `lane + o` (up = false)
+template <int BS, typename T>
+__device__ __forceinline__ void scan_step(T (&a)[BS * BS], T (&acc)[BS], int o, bool up, bool take)
+{
+    T ap[BS * BS], bp[BS];
+#pragma unroll
+    for (int q = 0; q < BS * BS; ++q) ap[q] = up ? __shfl_up_sync(0xffffffffu, a[q], o) : __shfl_down_sync(0xffffffffu, a[q], o);
+#pragma unroll
+    for (int k = 0; k < BS; ++k) bp[k] = up ? __shfl_up_sync(0xffffffffu, acc[k], o) : __shfl_down_sync(0xffffffffu, acc[k], o);
+    if (!take) return;
+    T na[BS * BS];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+#pragma unroll
+        for (int k = 0; k < BS; ++k) acc[i] = mad(a[i * BS + k], bp[k], acc[i]);
+#pragma unroll
+        for (int j = 0; j < BS; ++j) {
+            T sum = T(0);
+#pragma unroll
+            for (int k = 0; k < BS; ++k) sum = mad(a[i * BS + k], ap[k * BS + j], sum);
+            na[i * BS + j] = sum;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < BS * BS; ++q) a[q] = na[q];
+}
+
+template <int BS, typename T>
+__device__ __forceinline__ void seg_end(const SegArgs &g)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&g.st->done, 1u) == gridDim.x - 1) {
+            g.st->ticket = 0;
+            g.st->done = 0;
+            __threadfence();
+        }
+    }
+}
+
+// L y = r (unit lower).  scale (device, optional) multiplies r on load;
+// zreset is the U sweep's work vector.
+template <int BS, typename T>
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
 k_lsolve_seg(SegArgs g, const T *__restrict__ val, const double *__restrict__ r,
              const double *__restrict__ scale, T *y, T *zreset)
@@ -901,48 +677,54 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const double *__restrict__ r,
         const bool active = lane < len;
         const int off = g.sptr[seg];
         const int w = (g.sptr[seg + 1] - off) >> 5;
-        T acc = active ? (T)(sc == 1.0 ? r[row] : r[row] * sc) : T(0);
-        if (active) zreset[row] = bits_to(T(), Sentinel<T>::bits);
-        T a = T(0);
-        seg_external<T>(g, val, y, off, w, lane, row0, row0 + len, row - 1, acc, a);
+        T acc[BS], a[BS * BS];
+#pragma unroll
+        for (int k = 0; k < BS; ++k) {
+            acc[k] = T(0);
+            if (active) {
+                acc[k] = (T)(sc == 1.0 ? r[(size_t)row * BS + k] : r[(size_t)row * BS + k] * sc);
+                zreset[(size_t)row * BS + k] = bits_to(T(), Sentinel<T>::bits);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < BS * BS; ++q) a[q] = T(0);
+        seg_external<BS, T>(g, val, y, off, w, lane, row0, row0 + len, row - 1, acc, a);
         if (g.kind[seg]) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const T ap = __shfl_up_sync(0xffffffffu, a, o);
-                const T bp = __shfl_up_sync(0xffffffffu, acc, o);
-                if (lane >= o) {
-                    acc = fmadd(a, bp, acc);
-                    a = a * ap;
-                }
-            }
+            for (int o = 1; o < 32; o <<= 1) scan_step<BS, T>(a, acc, o, true, lane >= o);
         } else {
             // lane k is final once lanes 0..k-1 have been applied
             for (int k = 0; k < 31; ++k) {
-                const T yk = __shfl_sync(0xffffffffu, acc, k);
+                T yk[BS];
+#pragma unroll
+                for (int i = 0; i < BS; ++i) yk[i] = __shfl_sync(0xffffffffu, acc[i], k);
                 if (lane > k) {
                     for (int e = 0; e < w; ++e) {
-                        const int idx = off + e * 32 + lane;
-                        if (g.ecol[idx] == row0 + k) acc = msub(acc, val[idx], yk);
+                        const int64_t idx = off + (int64_t)e * 32 + lane;
+                        if (g.ecol[idx] != row0 + k) continue;
+#pragma unroll
+                        for (int i = 0; i < BS; ++i)
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], val[(i * BS + j) * g.nent + idx], yk[j]);
                     }
                 }
             }
         }
-        if (active) st_relaxed(y + row, acc);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&g.st->done, 1u) == gridDim.x - 1) {
-            g.st->ticket = 0;
-            g.st->done = 0;
-            __threadfence();
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < BS; ++k) st_relaxed(y + (size_t)row * BS + k, acc[k]);
         }
     }
+    seg_end<BS, T>(g);
 }
 
-template <typename T>
+// U z = y.  dinv holds, per row, 1/u_ii (scalars) or inv(U_II) (blocks),
+// plane-major; z carries values between rows and is reset to the sentinel by
+// the next L sweep; out (FP64) receives the result; y is reset for the next
+// L sweep.
+template <int BS, typename T>
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
-k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ rdiag, T *y, T *z,
+k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ dinv, T *y, T *z,
              double *__restrict__ out)
 {
     if (g.skip && *(volatile const int *)g.skip) return;
@@ -957,61 +739,95 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ rdiag, 
         const bool active = lane < len;
         const int off = g.sptr[seg];
         const int w = (g.sptr[seg + 1] - off) >> 5;
-        const T rd = active ? rdiag[row] : T(0);
-        T acc = T(0);
-        if (active) {
-            acc = y[row];
-            y[row] = bits_to(T(), Sentinel<T>::bits);
-        }
-        T a = T(0);
-        seg_external<T>(g, val, z, off, w, lane, row0, row0 + len, row + 1, acc, a);
-        if (g.kind[seg]) {
-            acc = acc * rd;
-            a = a * rd;
+        T acc[BS], a[BS * BS], dg[BS * BS];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const T ap = __shfl_down_sync(0xffffffffu, a, o);
-                const T bp = __shfl_down_sync(0xffffffffu, acc, o);
-                if (lane + o < 32) {
-                    acc = fmadd(a, bp, acc);
-                    a = a * ap;
+        for (int k = 0; k < BS; ++k) {
+            acc[k] = T(0);
+            if (active) {
+                acc[k] = y[(size_t)row * BS + k];
+                y[(size_t)row * BS + k] = bits_to(T(), Sentinel<T>::bits);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < BS * BS; ++q) {
+            a[q] = T(0);
+            dg[q] = active ? dinv[(size_t)q * g.npr + row] : T(0);
+        }
+        seg_external<BS, T>(g, val, z, off, w, lane, row0, row0 + len, row + 1, acc, a);
+        T res[BS];
+        if (g.kind[seg]) {
+            // z_t = dinv_t (acc_t - U_t z_{t+1}) = B_t + A_t z_{t+1}
+            T A2[BS * BS];
+#pragma unroll
+            for (int i = 0; i < BS; ++i) {
+                T sum = T(0);
+#pragma unroll
+                for (int k = 0; k < BS; ++k) sum = mad(dg[i * BS + k], acc[k], sum);
+                res[i] = sum;
+#pragma unroll
+                for (int j = 0; j < BS; ++j) {
+                    T s2 = T(0);
+#pragma unroll
+                    for (int k = 0; k < BS; ++k) s2 = mad(dg[i * BS + k], a[k * BS + j], s2);
+                    A2[i * BS + j] = s2;
                 }
             }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) scan_step<BS, T>(A2, res, o, false, lane + o < 32);
         } else {
             // lane k is final once lanes k+1..31 have been applied
             for (int k = 31; k > 0; --k) {
-                const T zk = __shfl_sync(0xffffffffu, acc * rd, k);
+                T mine[BS], zk[BS];
+#pragma unroll
+                for (int i = 0; i < BS; ++i) {
+                    T sum = T(0);
+#pragma unroll
+                    for (int j = 0; j < BS; ++j) sum = mad(dg[i * BS + j], acc[j], sum);
+                    mine[i] = sum;
+                }
+#pragma unroll
+                for (int i = 0; i < BS; ++i) zk[i] = __shfl_sync(0xffffffffu, mine[i], k);
                 if (lane < k) {
                     for (int e = 0; e < w; ++e) {
-                        const int idx = off + e * 32 + lane;
-                        if (g.ecol[idx] == row0 + k) acc = msub(acc, val[idx], zk);
+                        const int64_t idx = off + (int64_t)e * 32 + lane;
+                        if (g.ecol[idx] != row0 + k) continue;
+#pragma unroll
+                        for (int i = 0; i < BS; ++i)
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], val[(i * BS + j) * g.nent + idx], zk[j]);
                     }
                 }
             }
-            acc = acc * rd;
+#pragma unroll
+            for (int i = 0; i < BS; ++i) {
+                T sum = T(0);
+#pragma unroll
+                for (int j = 0; j < BS; ++j) sum = mad(dg[i * BS + j], acc[j], sum);
+                res[i] = sum;
+            }
         }
         if (active) {
-            st_relaxed(z + row, acc);
-            out[row] = (double)acc;
+#pragma unroll
+            for (int k = 0; k < BS; ++k) {
+                st_relaxed(z + (size_t)row * BS + k, res[k]);
+                out[(size_t)row * BS + k] = (double)res[k];
+            }
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&g.st->done, 1u) == gridDim.x - 1) {
-            g.st->ticket = 0;
-            g.st->done = 0;
-            __threadfence();
-        }
-    }
+    seg_end<BS, T>(g);
 }
 
+// diagonal inverses per row (plane-major): 1/u_ii for scalars, inv(U_II) for blocks
 template <typename T>
-__global__ void k_gather_rdiag(int nrows, int npad, const int *__restrict__ diagpos,
-                               const double *__restrict__ lu, T *__restrict__ rdiag)
+__global__ void k_gather_dinv(int nrows, int npr, int b2, const int *__restrict__ diagpos,
+                              const double *__restrict__ lu, const double *__restrict__ dinv, T *__restrict__ out)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x)
-        rdiag[i] = i < nrows ? (T)(1.0 / lu[diagpos[i]]) : T(1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npr; i += gridDim.x * blockDim.x)
+        for (int q = 0; q < b2; ++q) {
+            double v = 0.0;
+            if (i < nrows) v = b2 == 1 ? 1.0 / lu[diagpos[i]] : dinv[(size_t)i * b2 + q];
+            out[(size_t)q * npr + i] = (T)v;
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -1037,22 +853,16 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
             if (h_col[q] == i) diag[i] = q;
     const size_t b2 = (size_t)bs * bs;
     const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-    int st = build_layout(ctx, nrows, h_ptr, h_col, diag, true, f->L);
-    st = st ? st : build_layout(ctx, nrows, h_ptr, h_col, diag, false, f->U);
-    if (bs == 1) {
-        st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, f->SL);
-        st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, f->SU);
-        st = st ? st : rs_alloc(ctx, &f->SL.val, esz * (f->SL.nent > 0 ? f->SL.nent : 1));
-        st = st ? st : rs_alloc(ctx, &f->SU.val, esz * (f->SU.nent > 0 ? f->SU.nent : 1));
-        st = st ? st : rs_alloc(ctx, &f->SU.rdiag, esz * ((size_t)f->SU.nseg * 32 > 0 ? (size_t)f->SU.nseg * 32 : 1));
-    }
+    // row-level schedule of the factorisation; segment layouts of the sweeps
+    int st = build_layout(ctx, nrows, h_ptr, h_col, diag, f->L);
+    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, f->SL);
+    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, f->SU);
+    st = st ? st : rs_alloc(ctx, &f->SL.val, esz * b2 * (f->SL.nent > 0 ? f->SL.nent : 1));
+    st = st ? st : rs_alloc(ctx, &f->SU.val, esz * b2 * (f->SU.nent > 0 ? f->SU.nent : 1));
+    st = st ? st : rs_alloc(ctx, &f->SU.rdiag, esz * b2 * ((size_t)f->SU.nseg * 32 > 0 ? (size_t)f->SU.nseg * 32 : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->diagpos, sizeof(int) * (nrows > 0 ? nrows : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->lu, sizeof(double) * b2 * (nnzb > 0 ? nnzb : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->dinv, sizeof(double) * b2 * (nrows > 0 ? nrows : 1));
-    st = st ? st : rs_alloc(ctx, &f->L.val, esz * b2 * (f->L.nent > 0 ? f->L.nent : 1));
-    st = st ? st : rs_alloc(ctx, &f->U.val, esz * b2 * (f->U.nent > 0 ? f->U.nent : 1));
-    st = st ? st : rs_alloc(ctx, &f->U.diag, esz * b2 * (f->U.npad > 0 ? f->U.npad : 1));
-    st = st ? st : rs_alloc(ctx, (void **)&f->flags, sizeof(int) * (nrows > 0 ? nrows : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->state, sizeof(SweepState));
     st = st ? st : rs_alloc(ctx, &f->ywork, esz * bs * (nrows > 0 ? nrows : 1));
     st = st ? st : rs_alloc(ctx, &f->zwork, esz * bs * (nrows > 0 ? nrows : 1));
@@ -1071,7 +881,6 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
         ctx->launches++;
     }
     SweepState s0 = {0u, 0u, 1, 0};
-    RS_CUDA_TRY(cudaMemsetAsync(f->flags, 0, sizeof(int) * (nrows > 0 ? nrows : 1), ctx->stream));
     RS_CUDA_TRY(cudaMemcpyAsync(f->state, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->stream));
     RS_CUDA_TRY(cudaMemcpyAsync(f->diagpos, diag.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice,
                                 ctx->stream));
@@ -1085,13 +894,11 @@ void rs_ilu_destroy(IluFactor *f)
     if (!f) return;
     rs_ctx *ctx = f->ctx;
     free_layout(ctx, f->L);
-    free_layout(ctx, f->U);
     free_segments(ctx, f->SL);
     free_segments(ctx, f->SU);
     rs_free(ctx, f->diagpos);
     rs_free(ctx, f->lu);
     rs_free(ctx, f->dinv);
-    rs_free(ctx, f->flags);
     rs_free(ctx, f->state);
     rs_free(ctx, f->ywork);
     rs_free(ctx, f->zwork);
@@ -1133,43 +940,27 @@ int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row)
     default: return RS_ERR_INVALID_ARG;
     }
     RS_TRY(rs_check_launch(ctx));
-    const int ge = (int)std::min<int64_t>(std::max<int64_t>((f->L.nent + 255) / 256, 1), 4096);
-    const int gu = (int)std::min<int64_t>(std::max<int64_t>((f->U.nent + 255) / 256, 1), 4096);
-    const int gd = std::max(1, std::min((f->U.npad + 255) / 256, 4096));
+    const int gl = (int)std::min<int64_t>(std::max<int64_t>((f->SL.nent + 255) / 256, 1), 4096);
+    const int gu = (int)std::min<int64_t>(std::max<int64_t>((f->SU.nent + 255) / 256, 1), 4096);
+    const int np = f->SU.nseg * 32;
+    const int gr = std::max(1, std::min((np + 255) / 256, 4096));
     if (f->fp32) {
-        k_gather_tri<float><<<ge, 256, 0, ctx->stream>>>(f->L.nent, (int)b2, f->L.src, f->lu, (float *)f->L.val);
-        k_gather_tri<float><<<gu, 256, 0, ctx->stream>>>(f->U.nent, (int)b2, f->U.src, f->lu, (float *)f->U.val);
-        k_gather_diag<float><<<gd, 256, 0, ctx->stream>>>(f->U.npad, (int)b2, f->U.pos, f->U.dsrc, f->lu,
-                                                          f->dinv, (float *)f->U.diag);
+        k_gather_tri<float><<<gl, 256, 0, ctx->stream>>>(f->SL.nent, (int)b2, f->SL.src, f->lu, (float *)f->SL.val);
+        k_gather_tri<float><<<gu, 256, 0, ctx->stream>>>(f->SU.nent, (int)b2, f->SU.src, f->lu, (float *)f->SU.val);
+        k_gather_dinv<float><<<gr, 256, 0, ctx->stream>>>(f->nrows, np, (int)b2, f->diagpos, f->lu, f->dinv,
+                                                          (float *)f->SU.rdiag);
     } else {
-        k_gather_tri<double><<<ge, 256, 0, ctx->stream>>>(f->L.nent, (int)b2, f->L.src, f->lu, (double *)f->L.val);
-        k_gather_tri<double><<<gu, 256, 0, ctx->stream>>>(f->U.nent, (int)b2, f->U.src, f->lu, (double *)f->U.val);
-        k_gather_diag<double><<<gd, 256, 0, ctx->stream>>>(f->U.npad, (int)b2, f->U.pos, f->U.dsrc, f->lu,
-                                                           f->dinv, (double *)f->U.diag);
+        k_gather_tri<double><<<gl, 256, 0, ctx->stream>>>(f->SL.nent, (int)b2, f->SL.src, f->lu, (double *)f->SL.val);
+        k_gather_tri<double><<<gu, 256, 0, ctx->stream>>>(f->SU.nent, (int)b2, f->SU.src, f->lu, (double *)f->SU.val);
+        k_gather_dinv<double><<<gr, 256, 0, ctx->stream>>>(f->nrows, np, (int)b2, f->diagpos, f->lu, f->dinv,
+                                                           (double *)f->SU.rdiag);
     }
     RS_TRY(rs_check_launch(ctx));
     ctx->launches += 2;
-    if (f->bs == 1) {
-        const int gl = (int)std::min<int64_t>(std::max<int64_t>((f->SL.nent + 255) / 256, 1), 4096);
-        const int gu2 = (int)std::min<int64_t>(std::max<int64_t>((f->SU.nent + 255) / 256, 1), 4096);
-        const int np = f->SU.nseg * 32;
-        const int gr = std::max(1, std::min((np + 255) / 256, 4096));
-        if (f->fp32) {
-            k_gather_tri<float><<<gl, 256, 0, ctx->stream>>>(f->SL.nent, 1, f->SL.src, f->lu, (float *)f->SL.val);
-            k_gather_tri<float><<<gu2, 256, 0, ctx->stream>>>(f->SU.nent, 1, f->SU.src, f->lu, (float *)f->SU.val);
-            k_gather_rdiag<float><<<gr, 256, 0, ctx->stream>>>(f->nrows, np, f->diagpos, f->lu, (float *)f->SU.rdiag);
-        } else {
-            k_gather_tri<double><<<gl, 256, 0, ctx->stream>>>(f->SL.nent, 1, f->SL.src, f->lu, (double *)f->SL.val);
-            k_gather_tri<double><<<gu2, 256, 0, ctx->stream>>>(f->SU.nent, 1, f->SU.src, f->lu, (double *)f->SU.val);
-            k_gather_rdiag<double><<<gr, 256, 0, ctx->stream>>>(f->nrows, np, f->diagpos, f->lu, (double *)f->SU.rdiag);
-        }
-        RS_TRY(rs_check_launch(ctx));
-        ctx->launches += 2;
-    }
     return rs_collect_device_error(ctx, bad_row);
 }
 
-template <typename T>
+template <int BS, typename T>
 static int apply_seg(IluFactor *f, const double *r, double *z, const double *scale, const int *skip)
 {
     rs_ctx *ctx = f->ctx;
@@ -1178,33 +969,14 @@ static int apply_seg(IluFactor *f, const double *r, double *z, const double *sca
     const int gl = std::max(1, std::min((f->SL.nseg + wpb - 1) / wpb, ctx->sweep_blocks));
     const int gu = std::max(1, std::min((f->SU.nseg + wpb - 1) / wpb, ctx->sweep_blocks));
     {
-        RsProfScope prof(ctx, RS_PROF_LSWEEP);
-        k_lsolve_seg<T><<<gl, RS_SWEEP_THREADS, 0, ctx->stream>>>(seg_args(ctx, f->SL, f->nrows, f->state, skip),
-                                                                  (const T *)f->SL.val, r, scale, y, zt);
+        RsProfScope prof(ctx, BS == 1 ? RS_PROF_LSWEEP : RS_PROF_BLSWEEP);
+        k_lsolve_seg<BS, T><<<gl, RS_SWEEP_THREADS, 0, ctx->stream>>>(
+            seg_args(ctx, f->SL, f->nrows, f->state, skip), (const T *)f->SL.val, r, scale, y, zt);
     }
     RS_TRY(rs_check_launch(ctx));
-    RsProfScope prof(ctx, RS_PROF_USWEEP);
-    k_usolve_seg<T><<<gu, RS_SWEEP_THREADS, 0, ctx->stream>>>(seg_args(ctx, f->SU, f->nrows, f->state, skip),
-                                                              (const T *)f->SU.val, (const T *)f->SU.rdiag,
-                                                              y, zt, z);
-    return rs_check_launch(ctx);
-}
-
-template <int BS, typename T>
-static int apply_typed(IluFactor *f, const double *r, double *z, const double *scale, const int *skip)
-{
-    rs_ctx *ctx = f->ctx;
-    T *y = (T *)f->ywork;
-    T *zt = (T *)f->zwork;
-    {
-        RsProfScope prof(ctx, RS_PROF_BLSWEEP);
-        k_lsolve<BS, T, double><<<sweep_grid(ctx, f->L.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
-            sweep_args(ctx, f->L, f->state, skip), (const T *)f->L.val, r, scale, y, zt);
-    }
-    RS_TRY(rs_check_launch(ctx));
-    RsProfScope prof2(ctx, RS_PROF_BUSWEEP);
-    k_usolve<BS, T><<<sweep_grid(ctx, f->U.npad), RS_SWEEP_THREADS, 0, ctx->stream>>>(
-        sweep_args(ctx, f->U, f->state, skip), (const T *)f->U.val, (const T *)f->U.diag, y, zt, z);
+    RsProfScope prof(ctx, BS == 1 ? RS_PROF_USWEEP : RS_PROF_BUSWEEP);
+    k_usolve_seg<BS, T><<<gu, RS_SWEEP_THREADS, 0, ctx->stream>>>(
+        seg_args(ctx, f->SU, f->nrows, f->state, skip), (const T *)f->SU.val, (const T *)f->SU.rdiag, y, zt, z);
     return rs_check_launch(ctx);
 }
 
@@ -1212,10 +984,10 @@ int rs_ilu_apply(IluFactor *f, const double *r, double *z, const double *scale, 
 {
     if (f->nrows == 0) return RS_OK;
     switch (f->bs) {
-    case 1: return f->fp32 ? apply_seg<float>(f, r, z, scale, skip) : apply_seg<double>(f, r, z, scale, skip);
-    case 2: return f->fp32 ? apply_typed<2, float>(f, r, z, scale, skip) : apply_typed<2, double>(f, r, z, scale, skip);
-    case 3: return f->fp32 ? apply_typed<3, float>(f, r, z, scale, skip) : apply_typed<3, double>(f, r, z, scale, skip);
-    case 4: return f->fp32 ? apply_typed<4, float>(f, r, z, scale, skip) : apply_typed<4, double>(f, r, z, scale, skip);
+    case 1: return f->fp32 ? apply_seg<1, float>(f, r, z, scale, skip) : apply_seg<1, double>(f, r, z, scale, skip);
+    case 2: return f->fp32 ? apply_seg<2, float>(f, r, z, scale, skip) : apply_seg<2, double>(f, r, z, scale, skip);
+    case 3: return f->fp32 ? apply_seg<3, float>(f, r, z, scale, skip) : apply_seg<3, double>(f, r, z, scale, skip);
+    case 4: return f->fp32 ? apply_seg<4, float>(f, r, z, scale, skip) : apply_seg<4, double>(f, r, z, scale, skip);
     default: return RS_ERR_INVALID_ARG;
     }
 }

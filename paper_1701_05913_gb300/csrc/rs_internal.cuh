@@ -10,7 +10,6 @@
 
 #define RS_MAX_RESTART 64
 #define RS_RED_THREADS 256
-#define RS_SLICE 32            // rows per slice of the sliced-ELL factor layout
 
 // ---------------------------------------------------------------------------
 // error handling
@@ -121,29 +120,20 @@ struct SweepState {
     int pad;
 };
 
-// Level-scheduled, sliced-ELL layout of one triangular factor.
+// Row-level schedule of the ILU(0) factorisation: rows in level order of the
+// dependency graph of L, each level padded to a multiple of 32 positions.
 struct TriLayout {
-    int npad = 0;            // positions (levels padded to multiples of 32)
-    int nslices = 0;
+    int npad = 0;                // positions
     int nlevels = 0;
-    int64_t nent = 0;        // sliced-ELL entries (incl. padding)
-    int *pos = nullptr;      // [npad] row at each position or -1
-    int *slice_ptr = nullptr;// [nslices+1] first entry of each slice
-    int *col = nullptr;      // [nent] column (block column) or -1
-    int *src = nullptr;      // [nent] index of the entry in the CSR/BSR value array or -1
-    int *dsrc = nullptr;     // [npad] index of the diagonal entry (U only) or -1
-    void *val = nullptr;     // [nent * bs*bs] factor values (float or double)
-    void *diag = nullptr;    // [npad * bs*bs] U: diagonal (bs=1) or its inverse (bs>1)
-    // level schedule: level of every warp of positions, warps per level, and
-    // per-level arrival counters / completion epochs used by the sweeps
     int nwarps = 0;
-    int *warp_level = nullptr;   // [nwarps]
-    int *level_nwarps = nullptr; // [nlevels]
-    int *level_count = nullptr;  // [nlevels] (self-resetting)
+    int *pos = nullptr;          // [npad] row at each position or -1
+    int *warp_level = nullptr;   // [nwarps] level of each warp of positions
+    int *level_nwarps = nullptr; // [nlevels] warps per level
+    int *level_count = nullptr;  // [nlevels] arrival counters (self-resetting)
     int *level_done = nullptr;   // [nlevels] epoch of the sweep that last completed the level
 };
 
-// Segment layout of one scalar triangular factor: segments of at most 32
+// Segment layout of one triangular factor: segments of at most 32
 // consecutive rows (one warp each), ordered by their level in the segment
 // dependency graph, entries stored as sliced ELL per segment.
 struct SegLayout {
@@ -157,7 +147,7 @@ struct SegLayout {
     unsigned char *kind = nullptr; // [nseg] 1: the only in-segment dependency is the adjacent row
     int *row0 = nullptr;           // [nseg+1] first row of each segment
     void *val = nullptr;           // [nent] factor values (float or double)
-    void *rdiag = nullptr;         // [nseg*32] U: 1 / u_ii by row
+    void *rdiag = nullptr;         // [bs*bs][nseg*32] U: 1 / u_ii or inv(U_II) by row
 };
 
 // ILU(0) / block ILU(0) of one matrix pattern.
@@ -171,13 +161,11 @@ struct IluFactor {
     int *diagpos = nullptr;  // [nrows]
     double *lu = nullptr;    // [nnzb*bs*bs] FP64 factors in the matrix pattern
     double *dinv = nullptr;  // [nrows*bs*bs] inverted diagonal blocks (bs > 1)
-    TriLayout L, U;          // row-level schedules (factorisation; block sweeps)
+    TriLayout L;             // row-level schedule of the factorisation
     SegLayout SL, SU;        // segment layouts of the scalar sweeps
-    int *flags = nullptr;    // [nrows] sweep flags
     SweepState *state = nullptr;
     void *ywork = nullptr;   // [nrows*bs] intermediate of the L sweep
-    void *zwork = nullptr;   // [nrows*bs] FP32 output of the U sweep (fp32)
-    int host_epoch = 0;
+    void *zwork = nullptr;   // [nrows*bs] values of the U sweep
 };
 
 struct rs_pc {
