@@ -73,6 +73,81 @@ __device__ __forceinline__ bool reduce_partials(double (&acc)[NV], int nv, doubl
     return true;
 }
 
+// Warp reduce-scatter of NC per-lane values (NC a power of two): after
+// log2(NC) exchange-and-add steps lane l holds complete sums of columns
+// [l*NC/32, (l+1)*NC/32) (NC >= 32) or of column l/(32/NC) (NC < 32), for
+// about NC FP64 additions per lane instead of 5 per column.
+template <int NC>
+__device__ __forceinline__ void warp_reduce_scatter(double (&v)[NC], int lane)
+{
+    int width = NC;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        if (NC >= 32 || m >= 32 / NC) {
+            // split: keep one half of the live values, send the other to lane ^ m
+            const bool up = lane & m;
+            const int h = width / 2;
+#pragma unroll
+            for (int j = 0; j < NC / 2; ++j) {
+                if (j < h) {
+                    const double send = up ? v[j] : v[j + h];
+                    const double keep = up ? v[j + h] : v[j];
+                    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+                }
+            }
+            width = h > 0 ? h : 1;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
+        }
+    }
+}
+
+// Block reduction of NC per-thread column sums (and one extra scalar) with a
+// last-block finish: out[k] for k < nc, out[nc] = the extra scalar's sum.
+template <int NC>
+__device__ __forceinline__ bool reduce_columns(double (&acc)[NC], double extra, bool has_extra, int nc,
+                                               double *partials, unsigned *ticket, double *out)
+{
+    __shared__ double sm[RS_RED_THREADS / 32][NC + 1];
+    __shared__ bool last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    warp_reduce_scatter<NC>(acc, lane);
+    if (NC >= 32) {
+#pragma unroll
+        for (int j = 0; j < NC / 32; ++j) sm[warp][lane * (NC / 32) + j] = acc[j];
+    } else {
+        constexpr int G = NC < 32 ? 32 / NC : 1;   // lanes sharing one column
+        if (lane % G == 0) sm[warp][lane / G] = acc[0];
+    }
+    if (has_extra) {
+        const double e = warp_sum(extra);
+        if (lane == 0) sm[warp][NC] = e;
+    }
+    __syncthreads();
+    const int nv = nc + (has_extra ? 1 : 0);
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int src = k < nc ? k : NC;
+        double t = 0.0;
+        for (int w = 0; w < RS_RED_THREADS / 32; ++w) t += sm[w][src];
+        partials[(size_t)blockIdx.x * RS_PSTRIDE + k] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int k = warp; k < nv; k += RS_RED_THREADS / 32) {
+        double t = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partials + (size_t)b * RS_PSTRIDE + k);
+        t = warp_sum(t);
+        if (lane == 0) out[k] = t;
+    }
+    if (threadIdx.x == 0) *ticket = 0;
+    __syncthreads();
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // CGS2 kernels for Arnoldi step i (nc = i+1 basis vectors, w in V[:, i+1])
 // ---------------------------------------------------------------------------
@@ -83,22 +158,19 @@ k_cgs_dots(int n, int ld, int nc, const double *__restrict__ V, const double *__
            double *partials, unsigned *ticket, GmresDev *d)
 {
     if (*(volatile int *)&d->cycle_done) return;
-    double acc[NC + 1];
+    double acc[NC];
+    double ww = 0.0;
 #pragma unroll
-    for (int k = 0; k <= NC; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NC; ++k) acc[k] = 0.0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const double wr = w[r];
 #pragma unroll
         for (int k = 0; k < NC; ++k)
             if (k < nc) acc[k] = fma(V[(size_t)k * ld + r], wr, acc[k]);
-        acc[NC] = fma(wr, wr, acc[NC]);
+        ww = fma(wr, wr, ww);
     }
-    // move the norm into slot nc so the reduction covers slots 0..nc
-#pragma unroll
-    for (int k = 0; k < NC; ++k)
-        if (k == nc) acc[k] = acc[NC];
     double *out = d->h1;
-    if (reduce_partials<NC + 1>(acc, nc + 1, partials, ticket, out)) {
+    if (reduce_columns<NC>(acc, ww, true, nc, partials, ticket, out)) {
         if (threadIdx.x == 0) d->w0sq = out[nc];
     }
 }
@@ -118,21 +190,24 @@ k_cgs_update_dots(int n, int ld, int nc, const double *__restrict__ V, double *_
     for (int k = 0; k < NC; ++k) acc[k] = 0.0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         double v[NC];
-        double s = 0.0;
+        double s0 = 0.0, s1 = 0.0;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             if (k < nc) {
                 v[k] = V[(size_t)k * ld + r];
-                s = fma(v[k], hs[k], s);
+                if (k & 1) s1 = fma(v[k], hs[k], s1);
+                else s0 = fma(v[k], hs[k], s0);
+            } else {
+                v[k] = 0.0;
             }
         }
-        const double w1 = w[r] - s;
+        const double w1 = w[r] - (s0 + s1);
         w[r] = w1;
 #pragma unroll
         for (int k = 0; k < NC; ++k)
             if (k < nc) acc[k] = fma(v[k], w1, acc[k]);
     }
-    if (reduce_partials<NC>(acc, nc, partials, ticket, d->h2)) {
+    if (reduce_columns<NC>(acc, 0.0, false, nc, partials, ticket, d->h2)) {
         const int i = nc - 1, m1 = d->m + 1;
         for (int k = threadIdx.x; k < nc; k += blockDim.x) d->H[(size_t)i * m1 + k] = hs[k] + d->h2[k];
     }
@@ -150,11 +225,15 @@ k_cgs_update_norm(int n, int ld, int nc, const double *__restrict__ V, double *_
     __syncthreads();
     double acc[1] = {0.0};
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        double s = 0.0;
+        double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-        for (int k = 0; k < NC; ++k)
-            if (k < nc) s = fma(V[(size_t)k * ld + r], hs[k], s);
-        const double w2 = w[r] - s;
+        for (int k = 0; k < NC; ++k) {
+            if (k < nc) {
+                if (k & 1) s1 = fma(V[(size_t)k * ld + r], hs[k], s1);
+                else s0 = fma(V[(size_t)k * ld + r], hs[k], s0);
+            }
+        }
+        const double w2 = w[r] - (s0 + s1);
         w[r] = w2;
         acc[0] = fma(w2, w2, acc[0]);
     }
