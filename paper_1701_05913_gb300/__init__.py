@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import sys
 
 import numpy as np
 
@@ -113,6 +114,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return _build.build(force=force, verbose=verbose)
 
 
+def _finalizing() -> bool:
+    """True once the interpreter is shutting down: finalizers then leave the
+    handles to process exit (the driver reclaims the memory), because ctypes,
+    torch and the CUDA runtime may already be half torn down."""
+    return sys.is_finalizing()
+
+
 def lib():
     """Loads librs.so (raises if it has not been built)."""
     global _lib
@@ -200,7 +208,8 @@ class Context:
 
     def __del__(self):
         try:
-            self.close()
+            if not _finalizing():
+                self.close()
         except Exception:
             pass
 
@@ -225,7 +234,7 @@ class Vec:
 
     def __del__(self):
         try:
-            if self.h:
+            if self.h and not _finalizing():
                 lib().rs_vec_destroy(C.byref(self.h))
         except Exception:
             pass
@@ -267,7 +276,7 @@ class Mat:
 
     def __del__(self):
         try:
-            if self.h:
+            if self.h and not _finalizing():
                 lib().rs_mat_destroy(C.byref(self.h))
         except Exception:
             pass
@@ -320,7 +329,7 @@ class Precond:
 
     def __del__(self):
         try:
-            if self.h:
+            if self.h and not _finalizing():
                 lib().rs_precond_destroy(C.byref(self.h))
         except Exception:
             pass
@@ -404,7 +413,7 @@ class Net:
 
     def __del__(self):
         try:
-            if self.h:
+            if self.h and not _finalizing():
                 lib().rs_net_destroy(C.byref(self.h))
         except Exception:
             pass

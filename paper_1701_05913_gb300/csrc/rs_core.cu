@@ -89,10 +89,10 @@ extern "C" int rs_init(rs_ctx **out, int device, void *stream)
     cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, device);
     c->spin_limit = (long long)clock_khz * 1000LL * 2;   // about two seconds
     c->sweep_blocks = 4 * c->num_sms;
-    c->sleep_cap_ns = 128;
+    c->sleep_cap_ns = 0;   // spin: a polling warp reissues its loads as soon as they return
     if (const char *e = getenv("RS_SWEEP_SLEEP_CAP_NS")) {
         const int v = atoi(e);
-        if (v >= 16 && v <= 100000) c->sleep_cap_ns = (unsigned)v;
+        if (v >= 0 && v <= 100000) c->sleep_cap_ns = (unsigned)v;
     }
     if (const char *e = getenv("RS_SWEEP_BLOCKS_PER_SM")) {
         const int v = atoi(e);

@@ -140,6 +140,15 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
         if (nent > 0x7fffffffLL) return RS_ERR_INVALID_ARG;
     }
     sptr[nseg] = (int)nent;
+    // the entry a row of a chain segment reads from its neighbour inside the segment
+    std::vector<int> adjsrc(nrows, -1);
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int r0 = r0v[sg], r1 = r0v[sg + 1];
+        for (int i = r0; i < r1; ++i) {
+            if (lower && i > r0 && reads_prev(i)) adjsrc[i] = diag[i] - 1;
+            if (!lower && i + 1 < r1 && reads_next(i)) adjsrc[i] = diag[i] + 1;
+        }
+    }
     std::vector<int> ecol(nent, -1), esrc(nent, -1);
     for (int sg = 0; sg < nseg; ++sg) {
         const int r0 = r0v[sg], r1 = r0v[sg + 1];
@@ -163,6 +172,7 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     st = st ? st : rs_alloc(ctx, (void **)&S.src, sizeof(int) * (nent > 0 ? nent : 1));
     st = st ? st : rs_alloc(ctx, (void **)&S.kind, nseg > 0 ? nseg : 1);
     st = st ? st : rs_alloc(ctx, (void **)&S.row0, sizeof(int) * (nseg + 1));
+    st = st ? st : rs_alloc(ctx, (void **)&S.adjsrc, sizeof(int) * (nrows > 0 ? nrows : 1));
     if (st) return st;
     cudaStream_t sm = ctx->stream;
     if (nseg) {
@@ -171,6 +181,8 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     }
     RS_CUDA_TRY(cudaMemcpyAsync(S.sptr, sptr.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, sm));
     RS_CUDA_TRY(cudaMemcpyAsync(S.row0, r0v.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, sm));
+    if (nrows)
+        RS_CUDA_TRY(cudaMemcpyAsync(S.adjsrc, adjsrc.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice, sm));
     if (nent) {
         RS_CUDA_TRY(cudaMemcpyAsync(S.col, ecol.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, sm));
         RS_CUDA_TRY(cudaMemcpyAsync(S.src, esrc.data(), sizeof(int) * nent, cudaMemcpyHostToDevice, sm));
@@ -189,6 +201,8 @@ static void free_segments(rs_ctx *ctx, SegLayout &S)
     rs_free(ctx, S.row0);
     rs_free(ctx, S.val);
     rs_free(ctx, S.rdiag);
+    rs_free(ctx, S.adjsrc);
+    rs_free(ctx, S.mul);
     S = SegLayout();
 }
 
@@ -442,6 +456,119 @@ __global__ void k_gather_tri(int64_t nent, int b2, const int *__restrict__ src,
     }
 }
 
+// D_i (the inverse of row i's diagonal block: 1 / u_ii for scalars) of a row
+template <int BS>
+__device__ __forceinline__ void diag_inverse(int row, const int *__restrict__ diagpos, const double *__restrict__ lu,
+                                             const double *__restrict__ dinv, double (&D)[BS * BS])
+{
+    if (BS == 1) {
+        D[0] = 1.0 / lu[diagpos[row]];
+    } else {
+#pragma unroll
+        for (int v = 0; v < BS * BS; ++v) D[v] = dinv[(size_t)row * BS * BS + v];
+    }
+}
+
+// The U triangle premultiplied by the inverted diagonal: entry e of row i
+// holds D_i U_ij, so that the U sweep reads z_i = D_i y_i - sum_j (D_i U_ij) z_j
+// directly.  One warp per segment; products in FP64, rounded once to T.
+template <int BS, typename T>
+__global__ void k_gather_useg(int nseg, int64_t nent, const int *__restrict__ sptr, const int *__restrict__ row0,
+                              const int *__restrict__ src, const int *__restrict__ diagpos,
+                              const double *__restrict__ lu, const double *__restrict__ dinv, T *__restrict__ val)
+{
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int seg = blockIdx.x * wpb + (threadIdx.x >> 5); seg < nseg; seg += gridDim.x * wpb) {
+        const int row = row0[seg] + lane;
+        const bool active = row < row0[seg + 1];
+        double D[BS * BS];
+#pragma unroll
+        for (int v = 0; v < BS * BS; ++v) D[v] = 0.0;
+        if (active) diag_inverse<BS>(row, diagpos, lu, dinv, D);
+        for (int64_t e = sptr[seg] + lane; e < sptr[seg + 1]; e += 32) {
+            const int q = src[e];
+#pragma unroll
+            for (int i = 0; i < BS; ++i)
+#pragma unroll
+                for (int j = 0; j < BS; ++j) {
+                    double t = 0.0;
+                    if (q >= 0)
+#pragma unroll
+                        for (int k = 0; k < BS; ++k) t = fma(D[i * BS + k], lu[(size_t)q * BS * BS + k * BS + j], t);
+                    val[(size_t)(i * BS + j) * nent + e] = (T)t;
+                }
+        }
+    }
+}
+
+// Multipliers of the five steps of the segment scan.  Lane t of a chain
+// segment maps its neighbour's value to its own by the affine map
+// x_t = c_t + A_t x_{t-1} (L: A_t = -L_{t,t-1}) or x_t = c_t + A_t x_{t+1}
+// (U: A_t = -D_t U_{t,t+1}), A_t = 0 where the neighbour lies outside the
+// segment.  Step k (offset o = 2^k) composes each lane's map with the map of
+// lane t -/+ o; the c parts depend on the right-hand side, the A parts do not,
+// so the products A_t^{(k)} are formed here once per factorisation:
+// A^{(0)} = A, A^{(k+1)}_t = A^{(k)}_t A^{(k)}_{t-/+o} (for lanes that take).
+// Stored per segment as [5][bs*bs][32] in T, computed in FP64.
+template <int BS, typename T, bool LOWER>
+__global__ void k_scan_mul(int nseg, const int *__restrict__ row0, const int *__restrict__ adjsrc,
+                           const int *__restrict__ diagpos, const double *__restrict__ lu,
+                           const double *__restrict__ dinv, T *__restrict__ mul)
+{
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int seg = blockIdx.x * wpb + (threadIdx.x >> 5); seg < nseg; seg += gridDim.x * wpb) {
+        const int row = row0[seg] + lane;
+        const int q = row < row0[seg + 1] ? adjsrc[row] : -1;
+        double a[BS * BS];
+#pragma unroll
+        for (int v = 0; v < BS * BS; ++v) a[v] = 0.0;
+        if (q >= 0) {
+            if (LOWER) {
+#pragma unroll
+                for (int v = 0; v < BS * BS; ++v) a[v] = -lu[(size_t)q * BS * BS + v];
+            } else {
+                double D[BS * BS];
+                diag_inverse<BS>(row, diagpos, lu, dinv, D);
+#pragma unroll
+                for (int i = 0; i < BS; ++i)
+#pragma unroll
+                    for (int j = 0; j < BS; ++j) {
+                        double t = 0.0;
+#pragma unroll
+                        for (int k = 0; k < BS; ++k) t = fma(D[i * BS + k], lu[(size_t)q * BS * BS + k * BS + j], t);
+                        a[i * BS + j] = -t;
+                    }
+            }
+        }
+        T *out = mul + (size_t)seg * 5 * BS * BS * 32;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+#pragma unroll
+            for (int v = 0; v < BS * BS; ++v) out[(k * BS * BS + v) * 32 + lane] = (T)a[v];
+            if (k == 4) break;
+            const int o = 1 << k;
+            double ap[BS * BS], na[BS * BS];
+#pragma unroll
+            for (int v = 0; v < BS * BS; ++v)
+                ap[v] = LOWER ? __shfl_up_sync(0xffffffffu, a[v], o) : __shfl_down_sync(0xffffffffu, a[v], o);
+            const bool take = LOWER ? lane >= o : lane + o < 32;
+#pragma unroll
+            for (int i = 0; i < BS; ++i)
+#pragma unroll
+                for (int j = 0; j < BS; ++j) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int m = 0; m < BS; ++m) t = fma(a[i * BS + m], ap[m * BS + j], t);
+                    na[i * BS + j] = t;
+                }
+            if (take) {
+#pragma unroll
+                for (int v = 0; v < BS * BS; ++v) a[v] = na[v];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // triangular sweeps: the value is its own ready flag
 // ---------------------------------------------------------------------------
@@ -510,8 +637,11 @@ __device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a,
 // polled on the sentinel).  What remains inside the segment is, for the usual
 // stencils in natural order, a first-order recurrence y_t = c_t + A_t y_{t-1}
 // (L) or z_t = c_t + A_t z_{t+1} (U) with A_t a bs x bs block, solved by a
-// 5-step warp scan of affine maps; any other in-segment pattern is resolved
-// lane by lane with broadcasts.
+// 5-step warp scan of affine maps whose matrix parts (products of the A_t)
+// are formed once per factorisation and staged into shared memory while the
+// warp waits, so that after the last awaited value arrives a lane does only
+// its subtractions and five multiply-adds of bs-vectors; any other
+// in-segment pattern is resolved lane by lane with broadcasts.
 struct SegArgs {
     int nrows, nseg;
     unsigned sleep_cap;
@@ -546,13 +676,12 @@ static SegArgs seg_args(rs_ctx *ctx, const SegLayout &S, int nrows, SweepState *
 }
 
 // acc -= sum of V_e x[c_e] over this lane's entries whose block column lies
-// outside [lo, hi); the entry of block column `adj` is returned negated in a.
-// All lanes load their outside values at once; while any lane still sees a
-// sentinel the whole warp sleeps once and reloads only the pending values.
+// outside [lo, hi).  All lanes load their outside values at once; while any
+// lane still sees a sentinel the whole warp sleeps once and reloads only the
+// pending values.
 template <int BS, typename T>
 __device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restrict__ val, const T *x, int off,
-                                             int w, int lane, int lo, int hi, int adj, T (&acc)[BS],
-                                             T (&a)[BS * BS])
+                                             int w, int lane, int lo, int hi, T (&acc)[BS])
 {
     typedef typename Sentinel<T>::bits_t B;
     constexpr int CH = BS == 1 ? 8 : 4;
@@ -574,25 +703,27 @@ __device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restri
 #pragma unroll
             for (int k = 0; k < BS; ++k) b[j][k] = ext[j] ? ld_relaxed_bits(x + (size_t)c[j] * BS + k) : (B)0;
         }
+        // back-off: none after the first look, then 16 ns doubling up to
+        // sleep_cap (0: no sleep); the time limit runs from the first look
         unsigned ns = 0;
         long long t0 = 0;
-        for (;;) {
+        for (bool first = true;; first = false) {
             bool pend = false;
 #pragma unroll
             for (int j = 0; j < CH; ++j)
 #pragma unroll
                 for (int k = 0; k < BS; ++k) pend |= ext[j] && b[j][k] == Sentinel<T>::bits;
             if (!__any_sync(0xffffffffu, pend)) break;
-            if (ns == 0) {
+            if (first) {
                 t0 = clock64();
             } else {
                 if (clock64() - t0 > g.limit) {
                     if (pend) atomicOr(g.err, RS_DEVERR_TIMEOUT);
                     break;
                 }
-                __nanosleep(ns);
+                if (ns) __nanosleep(ns);
             }
-            ns = ns == 0 ? 16 : min(ns * 2, g.sleep_cap);
+            ns = first ? min(16u, g.sleep_cap) : min(ns * 2, g.sleep_cap);
 #pragma unroll
             for (int j = 0; j < CH; ++j)
 #pragma unroll
@@ -601,46 +732,63 @@ __device__ __forceinline__ void seg_external(const SegArgs &g, const T *__restri
         }
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
-            if (c[j] < 0) continue;
-            if (ext[j]) {
+            if (!ext[j]) continue;
 #pragma unroll
-                for (int i = 0; i < BS; ++i)
+            for (int i = 0; i < BS; ++i)
 #pragma unroll
-                    for (int k = 0; k < BS; ++k) acc[i] = msub(acc[i], v[j][i * BS + k], bits_to(T(), b[j][k]));
-            } else if (c[j] == adj) {
-#pragma unroll
-                for (int q = 0; q < BS * BS; ++q) a[q] = -v[j][q];
-            }
+                for (int k = 0; k < BS; ++k) acc[i] = msub(acc[i], v[j][i * BS + k], bits_to(T(), b[j][k]));
         }
     }
 }
 
-// affine-map scan step: (a, acc) <- (a, acc) composed with the map of lane
-// `lane - o` (up = true) or `lane + o` (up = false)
-template <int BS, typename T>
-__device__ __forceinline__ void scan_step(T (&a)[BS * BS], T (&acc)[BS], int o, bool up, bool take)
+// The scan multipliers of a chain segment (5 * bs*bs * 32 values, a multiple
+// of 16 bytes) are copied into the warp's slot of shared memory with cp.async
+// before the warp polls, and waited for after: they never sit on the path
+// from the last awaited value to the stores.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
-    T ap[BS * BS], bp[BS];
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int BS, typename T>
+struct ScanStage {
+    static constexpr int N = 5 * BS * BS * 32;                  // elements per segment
+    static constexpr int PIECES = N * (int)sizeof(T) / 16;      // 16-byte pieces
+    static_assert(N * sizeof(T) % 16 == 0, "stage is a multiple of 16 bytes");
+};
+
+template <int BS, typename T>
+__device__ __forceinline__ void stage_mul(const T *__restrict__ mul, int seg, T *stage, int lane)
+{
+    const char *src = (const char *)(mul + (size_t)seg * ScanStage<BS, T>::N);
+    char *dst = (char *)stage;
+    __syncwarp();   // every lane is done reading the previous segment's multipliers
+    for (int c = lane; c < ScanStage<BS, T>::PIECES; c += 32) cp_async16(dst + 16 * c, src + 16 * c);
+}
+
+// x_t = c_t + A_t x_{t-/+1} over the warp: five steps of
+// acc_t += A^{(k)}_t acc_{t-/+o} with the staged multipliers A^{(k)}.
+template <int BS, typename T, bool LOWER>
+__device__ __forceinline__ void scan_staged(const T *stage, T (&acc)[BS], int lane)
+{
+    cp_async_wait_all();
+    __syncwarp();
 #pragma unroll
-    for (int q = 0; q < BS * BS; ++q) ap[q] = up ? __shfl_up_sync(0xffffffffu, a[q], o) : __shfl_down_sync(0xffffffffu, a[q], o);
+    for (int k = 0; k < 5; ++k) {
+        const int o = 1 << k;
+        T bp[BS];
 #pragma unroll
-    for (int k = 0; k < BS; ++k) bp[k] = up ? __shfl_up_sync(0xffffffffu, acc[k], o) : __shfl_down_sync(0xffffffffu, acc[k], o);
-    if (!take) return;
-    T na[BS * BS];
+        for (int i = 0; i < BS; ++i)
+            bp[i] = LOWER ? __shfl_up_sync(0xffffffffu, acc[i], o) : __shfl_down_sync(0xffffffffu, acc[i], o);
+        if (LOWER ? lane >= o : lane + o < 32) {
 #pragma unroll
-    for (int i = 0; i < BS; ++i) {
+            for (int i = 0; i < BS; ++i)
 #pragma unroll
-        for (int k = 0; k < BS; ++k) acc[i] = mad(a[i * BS + k], bp[k], acc[i]);
-#pragma unroll
-        for (int j = 0; j < BS; ++j) {
-            T sum = T(0);
-#pragma unroll
-            for (int k = 0; k < BS; ++k) sum = mad(a[i * BS + k], ap[k * BS + j], sum);
-            na[i * BS + j] = sum;
+                for (int j = 0; j < BS; ++j) acc[i] = mad(stage[((k * BS + i) * BS + j) * 32 + lane], bp[j], acc[i]);
         }
     }
-#pragma unroll
-    for (int q = 0; q < BS * BS; ++q) a[q] = na[q];
 }
 
 template <int BS, typename T>
@@ -661,11 +809,13 @@ __device__ __forceinline__ void seg_end(const SegArgs &g)
 // zreset is the U sweep's work vector.
 template <int BS, typename T>
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
-k_lsolve_seg(SegArgs g, const T *__restrict__ val, const double *__restrict__ r,
+k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, const double *__restrict__ r,
              const double *__restrict__ scale, T *y, T *zreset)
 {
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
     if (g.skip && *(volatile const int *)g.skip) return;
     const int lane = threadIdx.x & 31;
+    T *stage = (T *)sweep_smem + (threadIdx.x >> 5) * ScanStage<BS, T>::N;
     const double sc = scale ? *scale : 1.0;
     for (;;) {
         int t = 0;
@@ -677,7 +827,9 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const double *__restrict__ r,
         const bool active = lane < len;
         const int off = g.sptr[seg];
         const int w = (g.sptr[seg + 1] - off) >> 5;
-        T acc[BS], a[BS * BS];
+        const bool chain = g.kind[seg];   // read before the polls, which order later loads
+        if (chain) stage_mul<BS, T>(mul, seg, stage, lane);
+        T acc[BS];
 #pragma unroll
         for (int k = 0; k < BS; ++k) {
             acc[k] = T(0);
@@ -686,12 +838,9 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const double *__restrict__ r,
                 zreset[(size_t)row * BS + k] = bits_to(T(), Sentinel<T>::bits);
             }
         }
-#pragma unroll
-        for (int q = 0; q < BS * BS; ++q) a[q] = T(0);
-        seg_external<BS, T>(g, val, y, off, w, lane, row0, row0 + len, row - 1, acc, a);
-        if (g.kind[seg]) {
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) scan_step<BS, T>(a, acc, o, true, lane >= o);
+        seg_external<BS, T>(g, val, y, off, w, lane, row0, row0 + len, acc);
+        if (chain) {
+            scan_staged<BS, T, true>(stage, acc, lane);
         } else {
             // lane k is final once lanes 0..k-1 have been applied
             for (int k = 0; k < 31; ++k) {
@@ -718,17 +867,19 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const double *__restrict__ r,
     seg_end<BS, T>(g);
 }
 
-// U z = y.  dinv holds, per row, 1/u_ii (scalars) or inv(U_II) (blocks),
-// plane-major; z carries values between rows and is reset to the sentinel by
-// the next L sweep; out (FP64) receives the result; y is reset for the next
-// L sweep.
+// U z = y.  val holds D_i U_ij (D_i = 1/u_ii or inv(U_II)) and dinv holds
+// D_i per row, plane-major, so z_i = D_i y_i - sum_j (D_i U_ij) z_j; z carries
+// values between rows and is reset to the sentinel by the next L sweep; out
+// (FP64) receives the result; y is reset for the next L sweep.
 template <int BS, typename T>
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
-k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ dinv, T *y, T *z,
-             double *__restrict__ out)
+k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, const T *__restrict__ dinv, T *y,
+             T *z, double *__restrict__ out)
 {
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
     if (g.skip && *(volatile const int *)g.skip) return;
     const int lane = threadIdx.x & 31;
+    T *stage = (T *)sweep_smem + (threadIdx.x >> 5) * ScanStage<BS, T>::N;
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(&g.st->ticket, 1u);
@@ -739,54 +890,33 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ dinv, T
         const bool active = lane < len;
         const int off = g.sptr[seg];
         const int w = (g.sptr[seg + 1] - off) >> 5;
-        T acc[BS], a[BS * BS], dg[BS * BS];
+        const bool chain = g.kind[seg];   // read before the polls, which order later loads
+        if (chain) stage_mul<BS, T>(mul, seg, stage, lane);
+        T yv[BS], acc[BS];
 #pragma unroll
         for (int k = 0; k < BS; ++k) {
-            acc[k] = T(0);
+            yv[k] = T(0);
             if (active) {
-                acc[k] = y[(size_t)row * BS + k];
+                yv[k] = y[(size_t)row * BS + k];
                 y[(size_t)row * BS + k] = bits_to(T(), Sentinel<T>::bits);
             }
         }
 #pragma unroll
-        for (int q = 0; q < BS * BS; ++q) {
-            a[q] = T(0);
-            dg[q] = active ? dinv[(size_t)q * g.npr + row] : T(0);
+        for (int i = 0; i < BS; ++i) {
+            T sum = T(0);
+#pragma unroll
+            for (int k = 0; k < BS; ++k) sum = mad(active ? dinv[(size_t)(i * BS + k) * g.npr + row] : T(0), yv[k], sum);
+            acc[i] = sum;
         }
-        seg_external<BS, T>(g, val, z, off, w, lane, row0, row0 + len, row + 1, acc, a);
-        T res[BS];
-        if (g.kind[seg]) {
-            // z_t = dinv_t (acc_t - U_t z_{t+1}) = B_t + A_t z_{t+1}
-            T A2[BS * BS];
-#pragma unroll
-            for (int i = 0; i < BS; ++i) {
-                T sum = T(0);
-#pragma unroll
-                for (int k = 0; k < BS; ++k) sum = mad(dg[i * BS + k], acc[k], sum);
-                res[i] = sum;
-#pragma unroll
-                for (int j = 0; j < BS; ++j) {
-                    T s2 = T(0);
-#pragma unroll
-                    for (int k = 0; k < BS; ++k) s2 = mad(dg[i * BS + k], a[k * BS + j], s2);
-                    A2[i * BS + j] = s2;
-                }
-            }
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) scan_step<BS, T>(A2, res, o, false, lane + o < 32);
+        seg_external<BS, T>(g, val, z, off, w, lane, row0, row0 + len, acc);
+        if (chain) {
+            scan_staged<BS, T, false>(stage, acc, lane);
         } else {
             // lane k is final once lanes k+1..31 have been applied
             for (int k = 31; k > 0; --k) {
-                T mine[BS], zk[BS];
+                T zk[BS];
 #pragma unroll
-                for (int i = 0; i < BS; ++i) {
-                    T sum = T(0);
-#pragma unroll
-                    for (int j = 0; j < BS; ++j) sum = mad(dg[i * BS + j], acc[j], sum);
-                    mine[i] = sum;
-                }
-#pragma unroll
-                for (int i = 0; i < BS; ++i) zk[i] = __shfl_sync(0xffffffffu, mine[i], k);
+                for (int i = 0; i < BS; ++i) zk[i] = __shfl_sync(0xffffffffu, acc[i], k);
                 if (lane < k) {
                     for (int e = 0; e < w; ++e) {
                         const int64_t idx = off + (int64_t)e * 32 + lane;
@@ -798,19 +928,12 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ dinv, T
                     }
                 }
             }
-#pragma unroll
-            for (int i = 0; i < BS; ++i) {
-                T sum = T(0);
-#pragma unroll
-                for (int j = 0; j < BS; ++j) sum = mad(dg[i * BS + j], acc[j], sum);
-                res[i] = sum;
-            }
         }
         if (active) {
 #pragma unroll
             for (int k = 0; k < BS; ++k) {
-                st_relaxed(z + (size_t)row * BS + k, res[k]);
-                out[(size_t)row * BS + k] = (double)res[k];
+                st_relaxed(z + (size_t)row * BS + k, acc[k]);
+                out[(size_t)row * BS + k] = (double)acc[k];
             }
         }
     }
@@ -860,6 +983,8 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
     st = st ? st : rs_alloc(ctx, &f->SL.val, esz * b2 * (f->SL.nent > 0 ? f->SL.nent : 1));
     st = st ? st : rs_alloc(ctx, &f->SU.val, esz * b2 * (f->SU.nent > 0 ? f->SU.nent : 1));
     st = st ? st : rs_alloc(ctx, &f->SU.rdiag, esz * b2 * ((size_t)f->SU.nseg * 32 > 0 ? (size_t)f->SU.nseg * 32 : 1));
+    st = st ? st : rs_alloc(ctx, &f->SL.mul, esz * b2 * 5 * 32 * (f->SL.nseg > 0 ? (size_t)f->SL.nseg : 1));
+    st = st ? st : rs_alloc(ctx, &f->SU.mul, esz * b2 * 5 * 32 * (f->SU.nseg > 0 ? (size_t)f->SU.nseg : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->diagpos, sizeof(int) * (nrows > 0 ? nrows : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->lu, sizeof(double) * b2 * (nnzb > 0 ? nnzb : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->dinv, sizeof(double) * b2 * (nrows > 0 ? nrows : 1));
@@ -911,6 +1036,32 @@ static int sweep_grid(rs_ctx *ctx, int npad)
     return std::max(1, std::min(need, ctx->sweep_blocks));
 }
 
+// After the numeric factorisation: the sweeps' copies of the factors (L
+// entries; U entries premultiplied by D_i), the diagonal inverses by row and
+// the scan multipliers of both triangles, in the apply precision T.
+template <int BS, typename T>
+static int gather_sweep_data(IluFactor *f, int *bad_row)
+{
+    rs_ctx *ctx = f->ctx;
+    const int b2 = BS * BS;
+    const int gl = (int)std::min<int64_t>(std::max<int64_t>((f->SL.nent + 255) / 256, 1), 4096);
+    const int np = f->SU.nseg * 32;
+    const int gr = std::max(1, std::min((np + 255) / 256, 4096));
+    const int gsl = std::max(1, std::min((f->SL.nseg + 7) / 8, 4096));
+    const int gsu = std::max(1, std::min((f->SU.nseg + 7) / 8, 4096));
+    k_gather_tri<T><<<gl, 256, 0, ctx->stream>>>(f->SL.nent, b2, f->SL.src, f->lu, (T *)f->SL.val);
+    k_gather_useg<BS, T><<<gsu, 256, 0, ctx->stream>>>(f->SU.nseg, f->SU.nent, f->SU.sptr, f->SU.row0, f->SU.src,
+                                                         f->diagpos, f->lu, f->dinv, (T *)f->SU.val);
+    k_gather_dinv<T><<<gr, 256, 0, ctx->stream>>>(f->nrows, np, b2, f->diagpos, f->lu, f->dinv, (T *)f->SU.rdiag);
+    k_scan_mul<BS, T, true><<<gsl, 256, 0, ctx->stream>>>(f->SL.nseg, f->SL.row0, f->SL.adjsrc, f->diagpos, f->lu,
+                                                            f->dinv, (T *)f->SL.mul);
+    k_scan_mul<BS, T, false><<<gsu, 256, 0, ctx->stream>>>(f->SU.nseg, f->SU.row0, f->SU.adjsrc, f->diagpos, f->lu,
+                                                             f->dinv, (T *)f->SU.mul);
+    RS_TRY(rs_check_launch(ctx));
+    ctx->launches += 5;
+    return rs_collect_device_error(ctx, bad_row);
+}
+
 int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row)
 {
     rs_ctx *ctx = f->ctx;
@@ -940,24 +1091,28 @@ int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row)
     default: return RS_ERR_INVALID_ARG;
     }
     RS_TRY(rs_check_launch(ctx));
-    const int gl = (int)std::min<int64_t>(std::max<int64_t>((f->SL.nent + 255) / 256, 1), 4096);
-    const int gu = (int)std::min<int64_t>(std::max<int64_t>((f->SU.nent + 255) / 256, 1), 4096);
-    const int np = f->SU.nseg * 32;
-    const int gr = std::max(1, std::min((np + 255) / 256, 4096));
-    if (f->fp32) {
-        k_gather_tri<float><<<gl, 256, 0, ctx->stream>>>(f->SL.nent, (int)b2, f->SL.src, f->lu, (float *)f->SL.val);
-        k_gather_tri<float><<<gu, 256, 0, ctx->stream>>>(f->SU.nent, (int)b2, f->SU.src, f->lu, (float *)f->SU.val);
-        k_gather_dinv<float><<<gr, 256, 0, ctx->stream>>>(f->nrows, np, (int)b2, f->diagpos, f->lu, f->dinv,
-                                                          (float *)f->SU.rdiag);
-    } else {
-        k_gather_tri<double><<<gl, 256, 0, ctx->stream>>>(f->SL.nent, (int)b2, f->SL.src, f->lu, (double *)f->SL.val);
-        k_gather_tri<double><<<gu, 256, 0, ctx->stream>>>(f->SU.nent, (int)b2, f->SU.src, f->lu, (double *)f->SU.val);
-        k_gather_dinv<double><<<gr, 256, 0, ctx->stream>>>(f->nrows, np, (int)b2, f->diagpos, f->lu, f->dinv,
-                                                           (double *)f->SU.rdiag);
+    switch (f->bs) {
+    case 1: return f->fp32 ? gather_sweep_data<1, float>(f, bad_row) : gather_sweep_data<1, double>(f, bad_row);
+    case 2: return f->fp32 ? gather_sweep_data<2, float>(f, bad_row) : gather_sweep_data<2, double>(f, bad_row);
+    case 3: return f->fp32 ? gather_sweep_data<3, float>(f, bad_row) : gather_sweep_data<3, double>(f, bad_row);
+    default: return f->fp32 ? gather_sweep_data<4, float>(f, bad_row) : gather_sweep_data<4, double>(f, bad_row);
     }
-    RS_TRY(rs_check_launch(ctx));
-    ctx->launches += 2;
-    return rs_collect_device_error(ctx, bad_row);
+}
+
+// Dynamic shared memory of a sweep block: one scan stage per warp.  Above the
+// default 48 KB the kernel's limit is raised once per device.
+template <int BS, typename T, class K>
+static int sweep_smem(rs_ctx *ctx, K kernel, size_t *bytes)
+{
+    static unsigned long long raised = 0;
+    *bytes = (size_t)(RS_SWEEP_THREADS / 32) * ScanStage<BS, T>::N * sizeof(T);
+    if (*bytes <= 48 * 1024) return RS_OK;
+    const unsigned long long bit = 1ull << (ctx->device & 63);
+    if (!(raised & bit)) {
+        RS_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes));
+        raised |= bit;
+    }
+    return RS_OK;
 }
 
 template <int BS, typename T>
@@ -968,15 +1123,23 @@ static int apply_seg(IluFactor *f, const double *r, double *z, const double *sca
     const int wpb = RS_SWEEP_THREADS / 32;
     const int gl = std::max(1, std::min((f->SL.nseg + wpb - 1) / wpb, ctx->sweep_blocks));
     const int gu = std::max(1, std::min((f->SU.nseg + wpb - 1) / wpb, ctx->sweep_blocks));
+    size_t sl = 0, su = 0;
+    {
+        const int e1 = sweep_smem<BS, T>(ctx, k_lsolve_seg<BS, T>, &sl);
+        const int e2 = e1 ? e1 : sweep_smem<BS, T>(ctx, k_usolve_seg<BS, T>, &su);
+        if (e2) return e2;
+    }
     {
         RsProfScope prof(ctx, BS == 1 ? RS_PROF_LSWEEP : RS_PROF_BLSWEEP);
-        k_lsolve_seg<BS, T><<<gl, RS_SWEEP_THREADS, 0, ctx->stream>>>(
-            seg_args(ctx, f->SL, f->nrows, f->state, skip), (const T *)f->SL.val, r, scale, y, zt);
+        k_lsolve_seg<BS, T><<<gl, RS_SWEEP_THREADS, sl, ctx->stream>>>(
+            seg_args(ctx, f->SL, f->nrows, f->state, skip), (const T *)f->SL.val, (const T *)f->SL.mul, r, scale, y,
+            zt);
     }
     RS_TRY(rs_check_launch(ctx));
     RsProfScope prof(ctx, BS == 1 ? RS_PROF_USWEEP : RS_PROF_BUSWEEP);
-    k_usolve_seg<BS, T><<<gu, RS_SWEEP_THREADS, 0, ctx->stream>>>(
-        seg_args(ctx, f->SU, f->nrows, f->state, skip), (const T *)f->SU.val, (const T *)f->SU.rdiag, y, zt, z);
+    k_usolve_seg<BS, T><<<gu, RS_SWEEP_THREADS, su, ctx->stream>>>(
+        seg_args(ctx, f->SU, f->nrows, f->state, skip), (const T *)f->SU.val, (const T *)f->SU.mul,
+        (const T *)f->SU.rdiag, y, zt, z);
     return rs_check_launch(ctx);
 }
 

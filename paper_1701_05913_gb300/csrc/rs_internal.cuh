@@ -75,7 +75,7 @@ struct rs_ctx {
     long long launches;
     long long spin_limit;    // clock cycles a device-side wait may take
     int sweep_blocks;        // resident blocks of the persistent triangular sweeps
-    unsigned sleep_cap_ns;   // longest back-off of a polling warp
+    unsigned sleep_cap_ns;   // longest back-off of a polling warp (0: none)
     // event profiler (off unless rs_prof_enable)
     int prof_on;
     std::vector<RsProfRec> prof_pending;
@@ -146,8 +146,10 @@ struct SegLayout {
     int *src = nullptr;            // [nent] index of the entry in the CSR value array or -1
     unsigned char *kind = nullptr; // [nseg] 1: the only in-segment dependency is the adjacent row
     int *row0 = nullptr;           // [nseg+1] first row of each segment
-    void *val = nullptr;           // [nent] factor values (float or double)
+    void *val = nullptr;           // [bs*bs][nent] factor values (float or double); U: D_i U_ij
     void *rdiag = nullptr;         // [bs*bs][nseg*32] U: 1 / u_ii or inv(U_II) by row
+    int *adjsrc = nullptr;         // [nrows] index of the in-segment adjacent entry or -1
+    void *mul = nullptr;           // [nseg][5][bs*bs][32] multipliers of the scan steps
 };
 
 // ILU(0) / block ILU(0) of one matrix pattern.
