@@ -504,10 +504,28 @@ k_spmv_csr_stream(int n, const int *__restrict__ ptr, const int *__restrict__ co
             scol[k] = col[s + k];
         }
         __syncthreads();
-        if (active)
-            for (int p = a - s; p < b - s; ++p) acc = fma(sval[p], __ldg(x + scol[p]), acc);
+        if (active) {
+            // the gathers of x are issued in groups of 8 (one L2 round trip
+            // per group, not per entry); the sum runs in column order
+            const int pe = b - s;
+            for (int p = a - s; p < pe; p += 8) {
+                double xv[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) xv[q] = p + q < pe ? __ldg(x + scol[p + q]) : 0.0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (p + q < pe) acc = fma(sval[p + q], xv[q], acc);
+            }
+        }
     } else if (active) {
-        for (int p = a; p < b; ++p) acc = fma(val[p], __ldg(x + col[p]), acc);
+        for (int p = a; p < b; p += 8) {
+            double xv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xv[q] = p + q < b ? __ldg(x + col[p + q]) : 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (p + q < b) acc = fma(val[p + q], xv[q], acc);
+        }
     }
     if (active) {
         if (bvec) y[r] = __dsub_rn(bvec[r], acc);

@@ -36,11 +36,11 @@ struct GmresDev {
 // ---------------------------------------------------------------------------
 // block reduction of up to NC+1 per-thread sums with a last-block finish
 // ---------------------------------------------------------------------------
-template <int NV>
+template <int NV, int NW = RS_RED_THREADS / 32>
 __device__ __forceinline__ bool reduce_partials(double (&acc)[NV], int nv, double *partials,
                                                 unsigned *ticket, double *out)
 {
-    __shared__ double sm[RS_RED_THREADS / 32][NV];
+    __shared__ double sm[NW][NV];
     __shared__ bool last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -53,7 +53,7 @@ __device__ __forceinline__ bool reduce_partials(double (&acc)[NV], int nv, doubl
     __syncthreads();
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         double s = 0.0;
-        for (int w = 0; w < RS_RED_THREADS / 32; ++w) s += sm[w][k];
+        for (int w = 0; w < NW; ++w) s += sm[w][k];
         partials[(size_t)blockIdx.x * RS_PSTRIDE + k] = s;
     }
     __threadfence();
@@ -62,7 +62,7 @@ __device__ __forceinline__ bool reduce_partials(double (&acc)[NV], int nv, doubl
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    for (int k = warp; k < nv; k += RS_RED_THREADS / 32) {
+    for (int k = warp; k < nv; k += NW) {
         double s = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partials + (size_t)b * RS_PSTRIDE + k);
         s = warp_sum(s);
@@ -104,11 +104,11 @@ __device__ __forceinline__ void warp_reduce_scatter(double (&v)[NC], int lane)
 
 // Block reduction of NC per-thread column sums (and one extra scalar) with a
 // last-block finish: out[k] for k < nc, out[nc] = the extra scalar's sum.
-template <int NC>
+template <int NC, int NW = RS_RED_THREADS / 32>
 __device__ __forceinline__ bool reduce_columns(double (&acc)[NC], double extra, bool has_extra, int nc,
                                                double *partials, unsigned *ticket, double *out)
 {
-    __shared__ double sm[RS_RED_THREADS / 32][NC + 1];
+    __shared__ double sm[NW][NC + 1];
     __shared__ bool last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     warp_reduce_scatter<NC>(acc, lane);
@@ -128,7 +128,7 @@ __device__ __forceinline__ bool reduce_columns(double (&acc)[NC], double extra, 
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         const int src = k < nc ? k : NC;
         double t = 0.0;
-        for (int w = 0; w < RS_RED_THREADS / 32; ++w) t += sm[w][src];
+        for (int w = 0; w < NW; ++w) t += sm[w][src];
         partials[(size_t)blockIdx.x * RS_PSTRIDE + k] = t;
     }
     __threadfence();
@@ -137,7 +137,7 @@ __device__ __forceinline__ bool reduce_columns(double (&acc)[NC], double extra, 
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    for (int k = warp; k < nv; k += RS_RED_THREADS / 32) {
+    for (int k = warp; k < nv; k += NW) {
         double t = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partials + (size_t)b * RS_PSTRIDE + k);
         t = warp_sum(t);
@@ -149,118 +149,199 @@ __device__ __forceinline__ bool reduce_columns(double (&acc)[NC], double extra, 
 }
 
 // ---------------------------------------------------------------------------
-// CGS2 kernels for Arnoldi step i (nc = i+1 basis vectors, w in V[:, i+1])
+// CGS2 passes for Arnoldi step i (nc = i+1 basis vectors, w in V[:, i+1])
 // ---------------------------------------------------------------------------
-// pass 1: h1 = V^T w, plus ||w||^2 for the breakdown test
+// The passes are FP64-bound (one to two multiply-adds per 8 bytes read, on a
+// GPU with about two FP64 lanes per clock per SM), so the loads are taken off
+// the FP64 warps: one producer thread streams tiles of TILE rows of the nc
+// basis vectors and of w into a shared-memory ring of 3 to 8 stages with bulk copies
+// (completion counted by an mbarrier per stage), and the consumer warps,
+// one row per thread, run only shared-memory loads and multiply-adds.
+//   pass 1 (CGS_DOTS):        h1 = V^T w, and ||w||^2 for the breakdown test
+//   pass 2 (CGS_UPDATE_DOTS): w -= V h1; h2 = V^T w; H[:, i] = h1 + h2
+//   pass 3 (CGS_UPDATE_NORM): w -= V h2; h_{i+1,i} = ||w||; Givens update
+// A block's consumer thread adds its rows in tile order and the block sums go
+// through the fixed last-block reduction, so the results are deterministic.
+enum { CGS_DOTS = 0, CGS_UPDATE_DOTS = 1, CGS_UPDATE_NORM = 2 };
+
 template <int NC>
-__global__ void __launch_bounds__(RS_RED_THREADS)
-k_cgs_dots(int n, int ld, int nc, const double *__restrict__ V, const double *__restrict__ w,
-           double *partials, unsigned *ticket, GmresDev *d)
+struct CgsCfg {
+    static constexpr int CW = NC <= 32 ? 4 : 2;        // consumer warps
+    static constexpr int NW = CW + 1;                   // + the producer warp
+    static constexpr int THREADS = 32 * NW;
+    static constexpr int TILE = 32 * CW;                // rows per tile, one per consumer thread
+    static constexpr int STAGE = (NC + 1) * TILE;       // doubles per stage: NC columns, then w
+    // stages: about 100 KB of ring per block (two blocks per SM), so that a
+    // narrow basis still keeps enough bytes in flight to feed the FP64 pipe
+    static constexpr int S = 100 * 1024 / (STAGE * 8) < 3 ? 3 : (100 * 1024 / (STAGE * 8) > 8 ? 8 : 100 * 1024 / (STAGE * 8));
+    static constexpr size_t SMEM = (size_t)S * STAGE * sizeof(double) + 2 * S * sizeof(unsigned long long);
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
 {
-    if (*(volatile int *)&d->cycle_done) return;
-    double acc[NC];
-    double ww = 0.0;
-#pragma unroll
-    for (int k = 0; k < NC; ++k) acc[k] = 0.0;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        const double wr = w[r];
-#pragma unroll
-        for (int k = 0; k < NC; ++k)
-            if (k < nc) acc[k] = fma(V[(size_t)k * ld + r], wr, acc[k]);
-        ww = fma(wr, wr, ww);
-    }
-    double *out = d->h1;
-    if (reduce_columns<NC>(acc, ww, true, nc, partials, ticket, out)) {
-        if (threadIdx.x == 0) d->w0sq = out[nc];
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Waits for the phase of the given parity to complete; gives up after `limit`
+// clock cycles, setting the timeout bit of the device error word.
+__device__ __forceinline__ void mbar_wait(unsigned long long *b, unsigned parity, long long limit, int *err)
+{
+    if (mbar_try_wait(b, parity)) return;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(b, parity)) {
+        if (clock64() - t0 > limit) {
+            atomicOr(err, RS_DEVERR_TIMEOUT);
+            return;
+        }
     }
 }
-
-// pass 2: w -= V h1; h2 = V^T w; H[:, i] = h1 + h2
-template <int NC>
-__global__ void __launch_bounds__(RS_RED_THREADS)
-k_cgs_update_dots(int n, int ld, int nc, const double *__restrict__ V, double *__restrict__ w,
-                  double *partials, unsigned *ticket, GmresDev *d)
+// bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
 {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+template <int NC, int MODE>
+__global__ void __launch_bounds__(CgsCfg<NC>::THREADS)
+k_cgs_pass(int n, int ld, int nc, const double *__restrict__ V, double *w, double *partials, unsigned *ticket,
+           GmresDev *d, int *err, long long limit)
+{
+    typedef CgsCfg<NC> C;
     if (*(volatile int *)&d->cycle_done) return;
+    extern __shared__ __align__(128) unsigned char cgs_smem[];
+    double *ring = (double *)cgs_smem;
+    unsigned long long *full = (unsigned long long *)(ring + C::S * C::STAGE);
+    unsigned long long *empty = full + C::S;
     __shared__ double hs[NC];
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) hs[k] = d->h1[k];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (MODE != CGS_DOTS)
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) hs[k] = MODE == CGS_UPDATE_DOTS ? d->h1[k] : d->h2[k];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], C::CW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
+    const int ntiles = (n + C::TILE - 1) / C::TILE;
     double acc[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) acc[k] = 0.0;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        double v[NC];
-        double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            if (k < nc) {
-                v[k] = V[(size_t)k * ld + r];
-                if (k & 1) s1 = fma(v[k], hs[k], s1);
-                else s0 = fma(v[k], hs[k], s0);
-            } else {
-                v[k] = 0.0;
+    double extra = 0.0;
+    if (warp == C::CW) {
+        if (lane == 0) {
+            // producer: whole tiles, the last one rounded up to an even row
+            // count (inside the column padding: ld is a multiple of 32)
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                const int s = it % C::S;
+                if (it >= C::S) mbar_wait(&empty[s], (unsigned)((it / C::S - 1) & 1), limit, err);
+                const int r0 = tile * C::TILE;
+                const int rows = min(C::TILE, n - r0);
+                const unsigned bytes = (unsigned)((rows + 1) & ~1) * 8u;
+                double *st = ring + s * C::STAGE;
+                mbar_arrive_expect_tx(&full[s], bytes * (unsigned)(nc + 1));
+                for (int k = 0; k < nc; ++k) bulk_g2s(st + k * C::TILE, V + (size_t)k * ld + r0, bytes, &full[s]);
+                bulk_g2s(st + NC * C::TILE, w + r0, bytes, &full[s]);
             }
         }
-        const double w1 = w[r] - (s0 + s1);
-        w[r] = w1;
+    } else {
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it % C::S;
+            mbar_wait(&full[s], (unsigned)((it / C::S) & 1), limit, err);
+            const double *st = ring + s * C::STAGE + threadIdx.x;
+            const int r = tile * C::TILE + threadIdx.x;
+            if (r < n) {
+                const double wr = st[NC * C::TILE];
+                if (MODE == CGS_DOTS) {
 #pragma unroll
-        for (int k = 0; k < NC; ++k)
-            if (k < nc) acc[k] = fma(v[k], w1, acc[k]);
-    }
-    if (reduce_columns<NC>(acc, 0.0, false, nc, partials, ticket, d->h2)) {
-        const int i = nc - 1, m1 = d->m + 1;
-        for (int k = threadIdx.x; k < nc; k += blockDim.x) d->H[(size_t)i * m1 + k] = hs[k] + d->h2[k];
-    }
-}
-
-// pass 3: w -= V h2; h_{i+1,i} = ||w||; Givens update; convergence test
-template <int NC>
-__global__ void __launch_bounds__(RS_RED_THREADS)
-k_cgs_update_norm(int n, int ld, int nc, const double *__restrict__ V, double *__restrict__ w,
-                  double *partials, unsigned *ticket, GmresDev *d)
-{
-    if (*(volatile int *)&d->cycle_done) return;
-    __shared__ double hs[NC];
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) hs[k] = d->h2[k];
-    __syncthreads();
-    double acc[1] = {0.0};
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        double s0 = 0.0, s1 = 0.0;
+                    for (int k = 0; k < NC; ++k)
+                        if (k < nc) acc[k] = fma(st[k * C::TILE], wr, acc[k]);
+                    extra = fma(wr, wr, extra);
+                } else {
+                    double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            if (k < nc) {
-                if (k & 1) s1 = fma(V[(size_t)k * ld + r], hs[k], s1);
-                else s0 = fma(V[(size_t)k * ld + r], hs[k], s0);
+                    for (int k = 0; k < NC; ++k) {
+                        if (k < nc) {
+                            if (k & 1) s1 = fma(st[k * C::TILE], hs[k], s1);
+                            else s0 = fma(st[k * C::TILE], hs[k], s0);
+                        }
+                    }
+                    const double w1 = wr - (s0 + s1);
+                    w[r] = w1;
+                    if (MODE == CGS_UPDATE_DOTS) {
+#pragma unroll
+                        for (int k = 0; k < NC; ++k)
+                            if (k < nc) acc[k] = fma(st[k * C::TILE], w1, acc[k]);
+                    } else {
+                        extra = fma(w1, w1, extra);
+                    }
+                }
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
         }
-        const double w2 = w[r] - (s0 + s1);
-        w[r] = w2;
-        acc[0] = fma(w2, w2, acc[0]);
     }
-    if (reduce_partials<1>(acc, 1, partials, ticket, &d->r2)) {
-        if (threadIdx.x == 0) {
+    if (MODE == CGS_DOTS) {
+        if (reduce_columns<NC, C::NW>(acc, extra, true, nc, partials, ticket, d->h1)) {
+            if (threadIdx.x == 0) d->w0sq = d->h1[nc];
+        }
+    } else if (MODE == CGS_UPDATE_DOTS) {
+        if (reduce_columns<NC, C::NW>(acc, 0.0, false, nc, partials, ticket, d->h2)) {
             const int i = nc - 1, m1 = d->m + 1;
-            double *h = d->H + (size_t)i * m1;
-            const double hnext = sqrt(d->r2);
-            for (int k = 0; k < i; ++k) {
-                const double a = h[k], b = h[k + 1];
-                h[k] = __dadd_rn(__dmul_rn(d->cs[k], a), __dmul_rn(d->sn[k], b));
-                h[k + 1] = __dadd_rn(__dmul_rn(-d->sn[k], a), __dmul_rn(d->cs[k], b));
+            for (int k = threadIdx.x; k < nc; k += blockDim.x) d->H[(size_t)i * m1 + k] = hs[k] + d->h2[k];
+        }
+    } else {
+        double a1[1] = {extra};
+        if (reduce_partials<1, C::NW>(a1, 1, partials, ticket, &d->r2)) {
+            if (threadIdx.x == 0) {
+                const int i = nc - 1, m1 = d->m + 1;
+                double *h = d->H + (size_t)i * m1;
+                const double hnext = sqrt(d->r2);
+                for (int k = 0; k < i; ++k) {
+                    const double a = h[k], b = h[k + 1];
+                    h[k] = __dadd_rn(__dmul_rn(d->cs[k], a), __dmul_rn(d->sn[k], b));
+                    h[k + 1] = __dadd_rn(__dmul_rn(-d->sn[k], a), __dmul_rn(d->cs[k], b));
+                }
+                const double rho = hypot(h[i], hnext);
+                d->cs[i] = __ddiv_rn(h[i], rho);
+                d->sn[i] = __ddiv_rn(hnext, rho);
+                h[i] = rho;
+                h[i + 1] = 0.0;
+                d->g[i + 1] = __dmul_rn(-d->sn[i], d->g[i]);
+                d->g[i] = __dmul_rn(d->cs[i], d->g[i]);
+                d->iters += 1;
+                d->k = i + 1;
+                d->implicit = fabs(d->g[i + 1]);
+                const bool happy = hnext <= 1e-14 * sqrt(d->w0sq);
+                if (d->implicit <= d->tol || d->iters >= d->maxit || happy || i == d->m - 1)
+                    d->cycle_done = 1;
+                d->hdiv = 1.0 / hnext;     // v_{i+1} = w / h_{i+1,i}
             }
-            const double rho = hypot(h[i], hnext);
-            d->cs[i] = __ddiv_rn(h[i], rho);
-            d->sn[i] = __ddiv_rn(hnext, rho);
-            h[i] = rho;
-            h[i + 1] = 0.0;
-            d->g[i + 1] = __dmul_rn(-d->sn[i], d->g[i]);
-            d->g[i] = __dmul_rn(d->cs[i], d->g[i]);
-            d->iters += 1;
-            d->k = i + 1;
-            d->implicit = fabs(d->g[i + 1]);
-            const bool happy = hnext <= 1e-14 * sqrt(d->w0sq);
-            if (d->implicit <= d->tol || d->iters >= d->maxit || happy || i == d->m - 1)
-                d->cycle_done = 1;
-            d->hdiv = 1.0 / hnext;     // v_{i+1} = w / h_{i+1,i}
         }
     }
 }
@@ -335,31 +416,40 @@ static int blas_grid(rs_ctx *ctx, int n)
     return std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8));
 }
 
-template <int NC>
-static void launch_cgs(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
+template <int NC, int MODE>
+static int launch_cgs_pass(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
 {
-    double *w = V + (size_t)nc * ld;
-    const int g = red_grid(ctx);
-    {
-        RsProfScope prof(ctx, RS_PROF_CGS_DOTS);
-        k_cgs_dots<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
+    typedef CgsCfg<NC> C;
+    static unsigned long long raised = 0;   // devices whose shared-memory limit was raised
+    const unsigned long long bit = 1ull << (ctx->device & 63);
+    if (C::SMEM > 48 * 1024 && !(raised & bit)) {
+        RS_CUDA_TRY(cudaFuncSetAttribute(k_cgs_pass<NC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM));
+        raised |= bit;
     }
-    {
-        RsProfScope prof(ctx, RS_PROF_CGS_UPDATE_DOTS);
-        k_cgs_update_dots<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
-    }
-    RsProfScope prof(ctx, RS_PROF_CGS_UPDATE_NORM);
-    k_cgs_update_norm<NC><<<g, RS_RED_THREADS, 0, ctx->stream>>>(n, ld, nc, V, w, ctx->red_partials, ctx->red_ticket, d);
+    RsProfScope prof(ctx, MODE == CGS_DOTS ? RS_PROF_CGS_DOTS
+                          : MODE == CGS_UPDATE_DOTS ? RS_PROF_CGS_UPDATE_DOTS : RS_PROF_CGS_UPDATE_NORM);
+    k_cgs_pass<NC, MODE><<<red_grid(ctx), C::THREADS, C::SMEM, ctx->stream>>>(
+        n, ld, nc, V, V + (size_t)nc * ld, ctx->red_partials, ctx->red_ticket, d, ctx->d_err, ctx->spin_limit);
+    ctx->launches++;
+    return rs_check_launch(ctx);
+}
+
+template <int NC>
+static int launch_cgs(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
+{
+    int st = launch_cgs_pass<NC, CGS_DOTS>(ctx, n, ld, nc, V, d);
+    if (!st) st = launch_cgs_pass<NC, CGS_UPDATE_DOTS>(ctx, n, ld, nc, V, d);
+    if (!st) st = launch_cgs_pass<NC, CGS_UPDATE_NORM>(ctx, n, ld, nc, V, d);
+    return st;
 }
 
 static int cgs_step(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
 {
-    if (nc <= 8) launch_cgs<8>(ctx, n, ld, nc, V, d);
-    else if (nc <= 16) launch_cgs<16>(ctx, n, ld, nc, V, d);
-    else if (nc <= 32) launch_cgs<32>(ctx, n, ld, nc, V, d);
-    else launch_cgs<64>(ctx, n, ld, nc, V, d);
-    ctx->launches += 2;
-    return rs_check_launch(ctx);
+    if (nc <= 8) return launch_cgs<8>(ctx, n, ld, nc, V, d);
+    if (nc <= 16) return launch_cgs<16>(ctx, n, ld, nc, V, d);
+    if (nc <= 32) return launch_cgs<32>(ctx, n, ld, nc, V, d);
+    return launch_cgs<64>(ctx, n, ld, nc, V, d);
 }
 
 static int finish_info(rs_ctx *ctx, const rs_mat *A, const double *b, const double *x, double *r,
