@@ -467,70 +467,133 @@ k_spmv_csr(int n, const int *__restrict__ ptr, const int *__restrict__ col,
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
     if (active && lane == 0) {
         if (bvec) y[row] = __dsub_rn(bvec[row], acc);
-        else if (beta == 0.0) y[row] = __dmul_rn(alpha, acc);
+        else if (beta == 0.0) y[row] = alpha == 1.0 ? acc : __dmul_rn(alpha, acc);
         else y[row] = fma(alpha, acc, beta * y[row]);
     }
 }
 
-// CSR, short rows: each block stages the values and column indices of its
-// 256 consecutive rows in shared memory with coalesced loads (one 8-byte
-// and one 4-byte stream), then each thread forms one row from shared memory.
-// Blocks whose rows hold more than RS_SPMV_STAGE nonzeros read their rows
-// straight from global memory.
-#define RS_SPMV_ROWS 256
-#define RS_SPMV_STAGE 2560
-__global__ void __launch_bounds__(RS_SPMV_ROWS)
-k_spmv_csr_stream(int n, const int *__restrict__ ptr, const int *__restrict__ col,
-                  const double *__restrict__ val, const double *__restrict__ x, double alpha,
-                  double beta, const double *__restrict__ bvec, double *__restrict__ y,
-                  const int *skip)
+// CSR, short rows: persistent and pipelined.  A block owns every G-th tile
+// of RS_SPMV_TILE consecutive rows.  One producer thread copies a tile's row
+// pointers, values and column indices into a ring of RS_SPMV_S shared-memory
+// stages with bulk copies (ranges widened to 16-byte boundaries; the
+// library's copies of the arrays carry a few padding elements so the widened
+// ranges stay inside them), RS_SPMV_S - 1 tiles ahead of the consumers; each
+// consumer thread forms one row of a tile: gathers of x (the first 8 entries
+// at once), sum in column order, epilogue y = alpha A x (+ beta y) or
+// y = b - A x.  Three blocks fit on an SM.  A tile holding more than
+// RS_SPMV_TNNZ nonzeros is read straight from global memory.
+#define RS_MAT_PAD 8
+#define RS_SPMV_TILE 256
+#define RS_SPMV_TNNZ 1984
+#define RS_SPMV_S 3
+#define RS_SPMV_THREADS (RS_SPMV_TILE + 32)
+struct SpmvStage {
+    double val[RS_SPMV_TNNZ + 8];   // first: 16-byte aligned
+    int col[RS_SPMV_TNNZ + 8];
+    int ptr[RS_SPMV_TILE + 8];
+};
+static_assert(sizeof(SpmvStage) % 16 == 0, "stages stay 16-byte aligned");
+#define RS_SPMV_SMEM (RS_SPMV_S * sizeof(SpmvStage))
+
+__global__ void __launch_bounds__(RS_SPMV_THREADS)
+k_spmv_csr_pipe(int n, const int *__restrict__ ptr, const int *__restrict__ col, const double *__restrict__ val,
+                const double *__restrict__ x, double alpha, double beta, const double *__restrict__ bvec,
+                double *__restrict__ y, const int *skip, int *err, long long limit)
 {
     if (skip && *(volatile const int *)skip) return;
-    __shared__ double sval[RS_SPMV_STAGE];
-    __shared__ int scol[RS_SPMV_STAGE];
-    const int row0 = blockIdx.x * RS_SPMV_ROWS;
-    const int nrow = min(RS_SPMV_ROWS, n - row0);
-    const int s = ptr[row0], e = ptr[row0 + nrow];
-    const int cnt = e - s;
-    const int r = row0 + threadIdx.x;
-    const bool active = threadIdx.x < nrow;
-    int a = 0, b = 0;
-    if (active) { a = ptr[r]; b = ptr[r + 1]; }
-    double acc = 0.0;
-    if (cnt <= RS_SPMV_STAGE) {
-#pragma unroll 4
-        for (int k = threadIdx.x; k < cnt; k += RS_SPMV_ROWS) {
-            sval[k] = val[s + k];
-            scol[k] = col[s + k];
+    extern __shared__ __align__(128) unsigned char spmv_smem[];
+    SpmvStage *stg = (SpmvStage *)spmv_smem;
+    __shared__ unsigned long long full[RS_SPMV_S], empty[RS_SPMV_S];
+    __shared__ int meta[RS_SPMV_S][4];   // first copied index of ptr, val, col; direct flag
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RS_SPMV_S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], RS_SPMV_TILE / 32);
         }
-        __syncthreads();
-        if (active) {
-            // the gathers of x are issued in groups of 8 (one L2 round trip
-            // per group, not per entry); the sum runs in column order
-            const int pe = b - s;
-            for (int p = a - s; p < pe; p += 8) {
-                double xv[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) xv[q] = p + q < pe ? __ldg(x + scol[p + q]) : 0.0;
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (p + q < pe) acc = fma(sval[p + q], xv[q], acc);
-            }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int ntiles = (n + RS_SPMV_TILE - 1) / RS_SPMV_TILE;
+    if (warp == RS_SPMV_TILE / 32) {
+        if (lane != 0) return;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it % RS_SPMV_S;
+            if (it >= RS_SPMV_S) mbar_wait(&empty[s], (unsigned)((it / RS_SPMV_S - 1) & 1), limit, err);
+            const int r0 = tile * RS_SPMV_TILE, r1 = min(r0 + RS_SPMV_TILE, n);
+            const int p0 = ptr[r0], p1 = ptr[r1];
+            const int pa = r0 & ~3, pcnt = (r1 + 1 - pa + 3) & ~3;
+            const int direct = p1 - p0 > RS_SPMV_TNNZ;
+            const int va = p0 & ~1, vcnt = (p1 - va + 1) & ~1;
+            const int ca = p0 & ~3, ccnt = (p1 - ca + 3) & ~3;
+            meta[s][0] = pa;
+            meta[s][1] = va;
+            meta[s][2] = ca;
+            meta[s][3] = direct;
+            const unsigned bytes = (unsigned)pcnt * 4u + (direct ? 0u : (unsigned)vcnt * 8u + (unsigned)ccnt * 4u);
+            mbar_arrive_expect_tx(&full[s], bytes);
+            bulk_g2s(stg[s].ptr, ptr + pa, (unsigned)pcnt * 4u, &full[s]);
+            if (!direct && vcnt > 0) bulk_g2s(stg[s].val, val + va, (unsigned)vcnt * 8u, &full[s]);
+            if (!direct && ccnt > 0) bulk_g2s(stg[s].col, col + ca, (unsigned)ccnt * 4u, &full[s]);
         }
-    } else if (active) {
-        for (int p = a; p < b; p += 8) {
-            double xv[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) xv[q] = p + q < b ? __ldg(x + col[p + q]) : 0.0;
+        return;
+    }
+    // consumers: the gathers of x for tile k+1 are issued before the sums of
+    // tile k, so each warp keeps two tiles of gathers in flight
+    struct Row {
+        int a, b;          // entry range of the row (global indices)
+        double xv[8];      // x at its first 8 entries
+    };
+    auto gather = [&](int it, int tile, Row &R) {
+        const int s = it % RS_SPMV_S;
+        mbar_wait(&full[s], (unsigned)((it / RS_SPMV_S) & 1), limit, err);
+        const SpmvStage &st = stg[s];
+        const int r = tile * RS_SPMV_TILE + threadIdx.x;
+        R.a = R.b = 0;
+        if (r < n) {
+            const int pa = meta[s][0], ca = meta[s][2], direct = meta[s][3];
+            R.a = st.ptr[r - pa];
+            R.b = st.ptr[r + 1 - pa];
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                if (p + q < b) acc = fma(val[p + q], xv[q], acc);
+                R.xv[q] = R.a + q < R.b ? __ldg(x + (direct ? col[R.a + q] : st.col[R.a + q - ca])) : 0.0;
         }
-    }
-    if (active) {
-        if (bvec) y[r] = __dsub_rn(bvec[r], acc);
-        else if (beta == 0.0) y[r] = __dmul_rn(alpha, acc);
-        else y[r] = fma(alpha, acc, beta * y[r]);
+    };
+    auto finish = [&](int it, int tile, const Row &R) {
+        const int s = it % RS_SPMV_S;
+        const SpmvStage &st = stg[s];
+        const int r = tile * RS_SPMV_TILE + threadIdx.x;
+        if (r < n) {
+            const int va = meta[s][1], ca = meta[s][2], direct = meta[s][3];
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (R.a + q < R.b) acc = fma(direct ? val[R.a + q] : st.val[R.a + q - va], R.xv[q], acc);
+            for (int p = R.a + 8; p < R.b; ++p)   // rows longer than 8
+                acc = fma(direct ? val[p] : st.val[p - va], __ldg(x + (direct ? col[p] : st.col[p - ca])), acc);
+            if (bvec) y[r] = __dsub_rn(bvec[r], acc);
+            else if (beta == 0.0) y[r] = alpha == 1.0 ? acc : __dmul_rn(alpha, acc);
+            else y[r] = fma(alpha, acc, beta * y[r]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    };
+    Row R0, R1;
+    int it = 0, tile = blockIdx.x;
+    if (tile < ntiles) gather(0, tile, R0);
+    while (tile < ntiles) {
+        const int t1 = tile + gridDim.x;
+        if (t1 < ntiles) gather(it + 1, t1, R1);
+        finish(it, tile, R0);
+        tile = t1;
+        ++it;
+        if (tile >= ntiles) break;
+        const int t2 = tile + gridDim.x;
+        if (t2 < ntiles) gather(it + 1, t2, R0);
+        finish(it, tile, R1);
+        tile = t2;
+        ++it;
     }
 }
 
@@ -558,7 +621,7 @@ k_spmv_bsr(int nb, int bsr, const int *__restrict__ ptr, const int *__restrict__
         }
     }
     if (bvec) y[t] = __dsub_rn(bvec[t], acc);
-    else if (beta == 0.0) y[t] = __dmul_rn(alpha, acc);
+    else if (beta == 0.0) y[t] = alpha == 1.0 ? acc : __dmul_rn(alpha, acc);
     else y[t] = fma(alpha, acc, beta * y[t]);
 }
 
@@ -569,9 +632,17 @@ static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double 
     if (A->n == 0) return RS_OK;
     RsProfScope prof(ctx, RS_PROF_SPMV);
     if (A->bs == 1 && A->lanes <= 8) {
-        const int grid = (A->n + RS_SPMV_ROWS - 1) / RS_SPMV_ROWS;
-        k_spmv_csr_stream<<<grid, RS_SPMV_ROWS, 0, ctx->stream>>>(A->n, A->ptr, A->col, A->val, x, alpha,
-                                                                   beta, bvec, y, skip);
+        static unsigned long long raised = 0;   // devices whose shared-memory limit was raised
+        const unsigned long long bit = 1ull << (ctx->device & 63);
+        if (!(raised & bit)) {
+            RS_CUDA_TRY(cudaFuncSetAttribute(k_spmv_csr_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)RS_SPMV_SMEM));
+            raised |= bit;
+        }
+        const int tiles = (A->n + RS_SPMV_TILE - 1) / RS_SPMV_TILE;
+        const int grid = std::max(1, std::min(tiles, 3 * ctx->num_sms));
+        k_spmv_csr_pipe<<<grid, RS_SPMV_THREADS, RS_SPMV_SMEM, ctx->stream>>>(
+            A->n, A->ptr, A->col, A->val, x, alpha, beta, bvec, y, skip, ctx->d_err, ctx->spin_limit);
     } else if (A->bs == 1) {
         const int L = A->lanes;
         const int64_t threads = (int64_t)A->n * L;
@@ -673,10 +744,15 @@ static int mat_create(rs_ctx *ctx, int nrows, int bs, const int32_t *ptr, const 
     }
     int st = validate_pattern(nrows, nrows, A->h_ptr, A->h_col);
     if (st) { delete A; return st; }
-    st = rs_alloc(ctx, (void **)&A->ptr, sizeof(int) * (nrows + 1));
-    st = st ? st : rs_alloc(ctx, (void **)&A->col, sizeof(int) * nnzb);
-    st = st ? st : rs_alloc(ctx, (void **)&A->val, sizeof(double) * nnzb * bs * bs);
+    // RS_MAT_PAD zeroed elements after each array: the SpMV's bulk copies
+    // widen their ranges to 16-byte boundaries
+    st = rs_alloc(ctx, (void **)&A->ptr, sizeof(int) * (nrows + 1 + RS_MAT_PAD));
+    st = st ? st : rs_alloc(ctx, (void **)&A->col, sizeof(int) * (nnzb + RS_MAT_PAD));
+    st = st ? st : rs_alloc(ctx, (void **)&A->val, sizeof(double) * (nnzb * bs * bs + RS_MAT_PAD));
     if (st) { rs_free(ctx, A->ptr); rs_free(ctx, A->col); delete A; return st; }
+    RS_CUDA_TRY(cudaMemsetAsync(A->ptr + nrows + 1, 0, sizeof(int) * RS_MAT_PAD, ctx->stream));
+    RS_CUDA_TRY(cudaMemsetAsync(A->col + nnzb, 0, sizeof(int) * RS_MAT_PAD, ctx->stream));
+    RS_CUDA_TRY(cudaMemsetAsync(A->val + nnzb * bs * bs, 0, sizeof(double) * RS_MAT_PAD, ctx->stream));
     RS_CUDA_TRY(cudaMemcpyAsync(A->ptr, ptr, sizeof(int) * (nrows + 1), h2d, ctx->stream));
     if (nnzb) {
         RS_CUDA_TRY(cudaMemcpyAsync(A->col, col, sizeof(int) * nnzb, h2d, ctx->stream));
