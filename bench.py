@@ -539,6 +539,13 @@ def run_gpu(args, w, rank, world, local):
                     "avg_launch_us": round(kern_ms[dom] / max(done.get(dom, kern_n[dom]), 1) * 1e3, 2),
                     "launches_with_work": done.get(dom, kern_n[dom]), "launches_total": kern_n[dom]}
     roofline["share_of_kernel_time"] = round(kern_ms[dom] / total_prof, 3)
+    if dom in ("l_sweep", "u_sweep", "bl_sweep", "bu_sweep") and \
+            dom.startswith("b") == (w["kind"] in ("bsr", "bsr_learned")):
+        # the sweeps are bound by their dependency chain, not by bytes: the
+        # number of segment levels and the time per level
+        lv = cases[0].M.sweep_levels()[0 if dom in ("l_sweep", "bl_sweep") else 1]
+        roofline["critical_path"] = {"segment_levels": lv,
+                                     "us_per_level": round(roofline["avg_launch_us"] / lv, 3)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:

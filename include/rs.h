@@ -190,6 +190,14 @@ int rs_precond_get_bilu(const rs_pc *M, double *lu_host, double *dinv_host);
 int rs_precond_get_cpr(const rs_pc *M, double *w_host, double *app_host);
 /* Row of the last zero pivot met by setup, or -1. */
 int32_t rs_precond_bad_row(const rs_pc *M);
+/* Critical-path length of the triangular sweeps of the full-system factor
+ * (ILU(0), block ILU(0), or the second stage of CPR): the number of segment
+ * levels of the L and of the U sweep, where a segment is a run of at most 32
+ * consecutive (block) rows solved by one warp and a segment's level is one
+ * more than the highest level of the segments it reads (Eq. 3 solved row by
+ * row in dependency order).  RS_ERR_INVALID_ARG for RS_PC_NONE or NULL
+ * arguments. */
+int rs_precond_sweep_levels(const rs_pc *M, int32_t *levels_l, int32_t *levels_u);
 int rs_precond_destroy(rs_pc **M);
 
 /* ---- Krylov solvers (Sec. 3, Alg. 1) ----------------------------------- */

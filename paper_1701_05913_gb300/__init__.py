@@ -85,6 +85,7 @@ SIGNATURES = [
     ("rs_precond_get_bilu", C.c_int, [_vp, _f64p, _f64p]),
     ("rs_precond_get_cpr", C.c_int, [_vp, _f64p, _f64p]),
     ("rs_precond_bad_row", C.c_int32, [_vp]),
+    ("rs_precond_sweep_levels", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("rs_precond_destroy", C.c_int, [C.POINTER(_vp)]),
     ("rs_solve_gmres", C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_double, C.c_int32,
                                  C.POINTER(SolveInfo)]),
@@ -326,6 +327,12 @@ class Precond:
         _check(lib().rs_precond_get_cpr(self.h, w.ctypes.data_as(_f64p), app.ctypes.data_as(_f64p)),
                "rs_precond_get_cpr")
         return w, app
+
+    def sweep_levels(self):
+        """(L levels, U levels) of the full-system factor's triangular sweeps."""
+        a, b = C.c_int32(), C.c_int32()
+        _check(lib().rs_precond_sweep_levels(self.h, C.byref(a), C.byref(b)), "rs_precond_sweep_levels")
+        return a.value, b.value
 
     def __del__(self):
         try:

@@ -257,6 +257,17 @@ extern "C" int rs_precond_get_cpr(const rs_pc *M, double *w_host, double *app_ho
 
 extern "C" int32_t rs_precond_bad_row(const rs_pc *M) { return M ? M->bad_row : -1; }
 
+extern "C" int rs_precond_sweep_levels(const rs_pc *M, int32_t *levels_l, int32_t *levels_u)
+{
+    if (!M || !levels_l || !levels_u) return RS_ERR_INVALID_ARG;
+    // the full-system factor: ILU(0) alone, or the second stage of CPR
+    const IluFactor *f = M->bilu ? M->bilu : M->ilu;
+    if (!f) return RS_ERR_INVALID_ARG;
+    *levels_l = f->SL.nlevels;
+    *levels_u = f->SU.nlevels;
+    return RS_OK;
+}
+
 extern "C" int rs_precond_destroy(rs_pc **M)
 {
     if (!M || !*M) return RS_OK;

@@ -161,6 +161,20 @@ def test_ilu0_factors_and_apply(rs, ctx, orc, shape):
     assert rel(z2.numpy(), z.numpy()) <= 1e-5
 
 
+@pytest.mark.parametrize("shape", [(64, 16, 8), (40, 12, 6), (128, 128, 64), (7, 5, 3)])
+def test_sweep_levels_structured(rs, ctx, shape):
+    """Segments never straddle grid lines, so on an nx x ny x nz 7-point grid
+    both sweeps have ceil(nx/32) + ny + nz - 2 segment levels (the depth of
+    the segment dependency graph: x-segments, then y and z neighbours)."""
+    nx, ny, nz = shape
+    d = synth.pressure_7pt(synth.Grid(nx, ny, nz), 3)
+    A = rs.Mat.csr(ctx, d)
+    expect = -(-nx // 32) + ny + nz - 2
+    for prec in ("fp64", "mixed"):
+        M = rs.Precond(ctx, A, "ilu0", prec=prec)
+        assert M.sweep_levels() == (expect, expect)
+
+
 def test_ilu0_general_pattern(rs, ctx, orc):
     """A random nonsymmetric pattern: in-segment dependencies other than the
     adjacent row take the lane-by-lane path of the sweeps."""
