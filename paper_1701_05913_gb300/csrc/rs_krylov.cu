@@ -177,7 +177,10 @@ struct CgsCfg {
     static constexpr size_t SMEM = (size_t)S * STAGE * sizeof(double) + 2 * S * sizeof(unsigned long long);
 };
 
-template <int NC, int MODE>
+// NC: columns of the ring and of the reduction (a power of two); NCC: the
+// unrolled bound of the multiply-add loops (nc rounded up to 4), so that a
+// row issues at most 3 multiply-adds that are predicated off.
+template <int NC, int NCC, int MODE>
 __global__ void __launch_bounds__(CgsCfg<NC>::THREADS)
 k_cgs_pass(int n, int ld, int nc, const double *__restrict__ V, double *w, double *partials, unsigned *ticket,
            GmresDev *d, int *err, long long limit)
@@ -233,13 +236,13 @@ k_cgs_pass(int n, int ld, int nc, const double *__restrict__ V, double *w, doubl
                 const double wr = st[NC * C::TILE];
                 if (MODE == CGS_DOTS) {
 #pragma unroll
-                    for (int k = 0; k < NC; ++k)
+                    for (int k = 0; k < NCC; ++k)
                         if (k < nc) acc[k] = fma(st[k * C::TILE], wr, acc[k]);
                     extra = fma(wr, wr, extra);
                 } else {
                     double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-                    for (int k = 0; k < NC; ++k) {
+                    for (int k = 0; k < NCC; ++k) {
                         if (k < nc) {
                             if (k & 1) s1 = fma(st[k * C::TILE], hs[k], s1);
                             else s0 = fma(st[k * C::TILE], hs[k], s0);
@@ -249,7 +252,7 @@ k_cgs_pass(int n, int ld, int nc, const double *__restrict__ V, double *w, doubl
                     w[r] = w1;
                     if (MODE == CGS_UPDATE_DOTS) {
 #pragma unroll
-                        for (int k = 0; k < NC; ++k)
+                        for (int k = 0; k < NCC; ++k)
                             if (k < nc) acc[k] = fma(st[k * C::TILE], w1, acc[k]);
                     } else {
                         extra = fma(w1, w1, extra);
@@ -370,40 +373,51 @@ static int blas_grid(rs_ctx *ctx, int n)
     return std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8));
 }
 
-template <int NC, int MODE>
+template <int NC, int NCC, int MODE>
 static int launch_cgs_pass(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
 {
     typedef CgsCfg<NC> C;
     static unsigned long long raised = 0;   // devices whose shared-memory limit was raised
     const unsigned long long bit = 1ull << (ctx->device & 63);
     if (C::SMEM > 48 * 1024 && !(raised & bit)) {
-        RS_CUDA_TRY(cudaFuncSetAttribute(k_cgs_pass<NC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        RS_CUDA_TRY(cudaFuncSetAttribute(k_cgs_pass<NC, NCC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM));
         raised |= bit;
     }
     RsProfScope prof(ctx, MODE == CGS_DOTS ? RS_PROF_CGS_DOTS
                           : MODE == CGS_UPDATE_DOTS ? RS_PROF_CGS_UPDATE_DOTS : RS_PROF_CGS_UPDATE_NORM);
-    k_cgs_pass<NC, MODE><<<red_grid(ctx), C::THREADS, C::SMEM, ctx->stream>>>(
+    k_cgs_pass<NC, NCC, MODE><<<red_grid(ctx), C::THREADS, C::SMEM, ctx->stream>>>(
         n, ld, nc, V, V + (size_t)nc * ld, ctx->red_partials, ctx->red_ticket, d, ctx->d_err, ctx->spin_limit);
     ctx->launches++;
     return rs_check_launch(ctx);
 }
 
-template <int NC>
+template <int NCC>
 static int launch_cgs(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
 {
-    int st = launch_cgs_pass<NC, CGS_DOTS>(ctx, n, ld, nc, V, d);
-    if (!st) st = launch_cgs_pass<NC, CGS_UPDATE_DOTS>(ctx, n, ld, nc, V, d);
-    if (!st) st = launch_cgs_pass<NC, CGS_UPDATE_NORM>(ctx, n, ld, nc, V, d);
+    constexpr int NC = NCC <= 8 ? 8 : NCC <= 16 ? 16 : NCC <= 32 ? 32 : 64;
+    int st = launch_cgs_pass<NC, NCC, CGS_DOTS>(ctx, n, ld, nc, V, d);
+    if (!st) st = launch_cgs_pass<NC, NCC, CGS_UPDATE_DOTS>(ctx, n, ld, nc, V, d);
+    if (!st) st = launch_cgs_pass<NC, NCC, CGS_UPDATE_NORM>(ctx, n, ld, nc, V, d);
     return st;
 }
 
 static int cgs_step(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
 {
-    if (nc <= 8) return launch_cgs<8>(ctx, n, ld, nc, V, d);
-    if (nc <= 16) return launch_cgs<16>(ctx, n, ld, nc, V, d);
-    if (nc <= 32) return launch_cgs<32>(ctx, n, ld, nc, V, d);
-    return launch_cgs<64>(ctx, n, ld, nc, V, d);
+    switch ((nc + 3) / 4) {
+    case 1: return launch_cgs<4>(ctx, n, ld, nc, V, d);
+    case 2: return launch_cgs<8>(ctx, n, ld, nc, V, d);
+    case 3: return launch_cgs<12>(ctx, n, ld, nc, V, d);
+    case 4: return launch_cgs<16>(ctx, n, ld, nc, V, d);
+    case 5: return launch_cgs<20>(ctx, n, ld, nc, V, d);
+    case 6: return launch_cgs<24>(ctx, n, ld, nc, V, d);
+    case 7: return launch_cgs<28>(ctx, n, ld, nc, V, d);
+    case 8: return launch_cgs<32>(ctx, n, ld, nc, V, d);
+    case 9: case 10: return launch_cgs<40>(ctx, n, ld, nc, V, d);
+    case 11: case 12: return launch_cgs<48>(ctx, n, ld, nc, V, d);
+    case 13: case 14: return launch_cgs<56>(ctx, n, ld, nc, V, d);
+    default: return launch_cgs<64>(ctx, n, ld, nc, V, d);
+    }
 }
 
 static int finish_info(rs_ctx *ctx, const rs_mat *A, const double *b, const double *x, double *r,
