@@ -59,6 +59,9 @@ WORKLOADS = {
                                              precond="cpr", prec="mixed"),
     "cpr_learned_bsr3_128x128x128": dict(kind="bsr_learned", grid=(128, 128, 128), kz=1.0, solver="fgmres",
                                          precond="cpr_learned", prec="mixed"),
+    # the paper's production pairing (Examples 2 and 4): BiCGSTAB + CPR-FPF (Alg. 7)
+    "cpr_fpf_bicgstab_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="bicgstab",
+                                             precond="cpr", prec="mixed", form="fpf"),
 }
 DEFAULT = "gmres_ilu0_128x128x64"
 SEED = 1
@@ -163,20 +166,24 @@ def executed_launches(w, infos):
         else:
             applies = I + (0 if w["solver"] == "fgmres" else C)
             spmv = I + C + 1
+        # CPR forms (Algs. 5-8): one residual between consecutive stages,
+        # nF block-ILU(0) stages and nP pressure stages per apply
+        form = w.get("form", "pf").upper() if cpr else "F"
+        nF, nP = form.count("F"), form.count("P")
         if cpr:
-            spmv += applies                      # residual of the two-stage apply
+            spmv += applies * (len(form) - 1)
         cnt["spmv"] += spmv
         if w["precond"] == "cpr_learned":
-            cnt["net"] += applies
+            cnt["net"] += applies * nP
         if block:
-            cnt["bl_sweep"] += applies
-            cnt["bu_sweep"] += applies
+            cnt["bl_sweep"] += applies * nF
+            cnt["bu_sweep"] += applies * nF
             if w["precond"] == "cpr":
-                cnt["l_sweep"] += applies        # ILU(0) of the decoupled pressure matrix
-                cnt["u_sweep"] += applies
+                cnt["l_sweep"] += applies * nP   # ILU(0) of the decoupled pressure matrix
+                cnt["u_sweep"] += applies * nP
         else:
-            cnt["l_sweep"] += applies            # ILU(0) (or the CPR second stage on A)
-            cnt["u_sweep"] += applies
+            cnt["l_sweep"] += applies * nF       # ILU(0) (or the CPR second stage on A)
+            cnt["u_sweep"] += applies * nF
     return cnt
 
 
@@ -294,7 +301,7 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
     elif w["precond"] == "cpr_learned":
         M = oracle.PC(A, "cpr", mixed=mixed)      # block system: ILU(0) pressure stage in the oracle
     else:
-        M = oracle.PC(A, w["precond"], mixed=mixed)
+        M = oracle.PC(A, w["precond"], mixed=mixed, form=w.get("form", "pf"))
     setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     if w["solver"] == "bicgstab":
@@ -397,9 +404,9 @@ class Case:
         self.x = rs.Vec.zeros(ctx, n)
         ctx.sync()
         t0 = time.perf_counter()
-        kw = {}
+        kw = dict(form=w["form"]) if "form" in w else {}
         if w["precond"] == "cpr_learned":
-            kw = dict(net=net, log_perm=A_host["logk"], grid=w["grid"])
+            kw.update(net=net, log_perm=A_host["logk"], grid=w["grid"])
         self.M = rs.Precond(ctx, self.A, w["precond"], prec=w["prec"], **kw)
         ctx.sync()
         self.setup_s = time.perf_counter() - t0
@@ -561,7 +568,8 @@ def run_gpu(args, w, rank, world, local):
             "data": "synthetic",
             "config": {"workload": args.workload, "grid": list(w["grid"]), "unknowns": cases[0].A.n,
                        "nnz": int(cases[0].A.nnz), "block_size": cases[0].A.bs, "solver": w["solver"] + "(30)"
-                       if w["solver"] != "bicgstab" else "bicgstab", "precond": w["precond"],
+                       if w["solver"] != "bicgstab" else "bicgstab",
+                       "precond": w["precond"] + ("-" + w["form"] if "form" in w else ""),
                        "precision": w["prec"], "rtol": RTOL, "seeds": [seeds[0], seeds[-1]],
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": "replicas" if world > 1 else "1 gpu"},

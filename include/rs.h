@@ -68,11 +68,23 @@ typedef enum {
     RS_MIXED = 1          /* FP32 factors and applies, FP64 Krylov outer loop */
 } rs_prec;
 
+/* Order of the stages of a CPR-like preconditioner (Sec. 4.3): F = the block
+ * ILU(0) of the full system, R(A)^{-1}; P = the pressure correction
+ * Pi_p M_p^{-1} Pi_r.  The first stage maps f to x; each later stage forms
+ * r = f - A x and adds its correction to x. */
+typedef enum {
+    RS_CPR_PF = 0,        /* Alg. 6, read as x = P f; r = f - A x; x += F r   */
+    RS_CPR_FP = 1,        /* Alg. 5                                           */
+    RS_CPR_FPF = 2,       /* Alg. 7                                           */
+    RS_CPR_FFPF = 3       /* Alg. 8                                           */
+} rs_cpr_form;
+
 typedef struct {
     int32_t prec;         /* rs_prec                                          */
     int32_t nx, ny, nz;   /* grid of the pressure unknowns (learned stage)    */
     const rs_net *net;    /* trained network (RS_PC_CPR_LEARNED)              */
     const double *log_perm; /* device pointer, nx*ny*nz log-permeabilities    */
+    int32_t cpr_form;     /* rs_cpr_form (RS_PC_CPR, RS_PC_CPR_LEARNED); 0 = PF */
 } rs_pc_opts;
 
 typedef struct {
@@ -170,9 +182,11 @@ int rs_mat_amxpby(double a, const rs_mat *A, const rs_vec *x, double b, rs_vec *
 
 /* Builds M for A.  RS_PC_ILU0 needs a CSR matrix; RS_PC_BILU0 a BSR matrix;
  * RS_PC_CPR a BSR matrix (quasi-IMPES pressure restriction, ILU(0) of the
- * decoupled pressure matrix, then block ILU(0)) or a CSR matrix (pressure
- * stage on A itself, second stage ILU(0)).  opts may be NULL (FP64).
- * Returns RS_ERR_ZERO_PIVOT when a factorisation meets a zero pivot. */
+ * decoupled pressure matrix, block ILU(0) of A) or a CSR matrix (pressure
+ * stage on A itself, second stage ILU(0)); opts->cpr_form picks the order
+ * of the stages (Algs. 5-8).  opts may be NULL (FP64, CPR-PF).
+ * Returns RS_ERR_ZERO_PIVOT when a factorisation meets a zero pivot and
+ * RS_ERR_INVALID_ARG for an unknown cpr_form. */
 int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs_pc_opts *opts,
                      rs_pc **M);
 /* z = M^{-1} r. */

@@ -71,7 +71,7 @@ class _PC(C.Structure):
                 ("blu", _f64p), ("bdinv", _f64p), ("blu32", _f32p), ("bdinv32", _f32p),
                 ("A", C.POINTER(_Mat)), ("w", _f64p),
                 ("pstage", APPLY_FN), ("pstage_user", C.c_void_p),
-                ("fn", APPLY_FN), ("user", C.c_void_p)]
+                ("fn", APPLY_FN), ("user", C.c_void_p), ("form", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -293,14 +293,20 @@ class PC:
     (or `pstage`, a callable rp -> zp), prolongation, residual, block ILU(0).
     kind='cpr' on a CSR matrix (bs=1): restriction = identity, App' = A,
     second stage = ILU(0) of A.
+    form: the order of the stages (F = block ILU(0) of A, P = pressure
+    stage): 'pf' (Alg. 6 as read), 'fp' (Alg. 5), 'fpf' (Alg. 7), 'ffpf'
+    (Alg. 8).
     """
 
-    def __init__(self, A: Mat, kind: str = "ilu0", mixed: bool = False, pstage=None, fn=None):
+    FORMS = ("pf", "fp", "fpf", "ffpf")   # Algs. 6, 5, 7, 8
+
+    def __init__(self, A: Mat, kind: str = "ilu0", mixed: bool = False, pstage=None, fn=None, form: str = "pf"):
         self.A = A
         self.kind = kind
         self._keep = []
         s = _PC()
         s.mixed = int(mixed)
+        s.form = self.FORMS.index(form)
         self.status = OK
         if kind == "none":
             s.type = PC_NONE

@@ -421,7 +421,36 @@ typedef struct {
     /* plain callback preconditioner */
     or_apply_fn fn;
     void *user;
+    /* CPR form: 0 PF (Alg. 6, read as below), 1 FP (Alg. 5), 2 FPF (Alg. 7),
+     * 3 FFPF (Alg. 8) */
+    int32_t form;
 } or_pc;
+
+/* One stage of a CPR-like preconditioner on a right-hand side v:
+ * 'F' = R(A)^{-1} v (block ILU(0) of the full system),
+ * 'P' = Pi_p M_p^{-1} (Pi_r v) (quasi-IMPES restriction, pressure solve by
+ * ILU(0) of App' or the pstage callback, prolongation). */
+static int cpr_stage(const or_pc *M, char kind, int64_t n, const double *v, double *out)
+{
+    const int32_t nb = M->nb, bs = M->bs;
+    if (kind == 'F') {
+        if (M->mixed) or_bilu0_solve_f32(nb, bs, M->bptr, M->bcol, M->blu32, M->bdinv32, v, out);
+        else or_bilu0_solve(nb, bs, M->bptr, M->bcol, M->blu, M->bdinv, v, out);
+        return OR_OK;
+    }
+    double *rp = (double *)malloc(sizeof(double) * (size_t)nb);
+    double *zp = (double *)malloc(sizeof(double) * (size_t)nb);
+    int st = OR_OK;
+    or_qimpes_restrict(nb, bs, M->w, v, rp);
+    if (M->pstage) st = M->pstage(M->pstage_user, nb, rp, zp);
+    else if (M->mixed) or_ilu0_solve_f32(M->n, M->ptr, M->col, M->lu32, rp, zp);
+    else or_ilu0_solve(M->n, M->ptr, M->col, M->lu, rp, zp);
+    or_prolong(nb, bs, zp, out);
+    (void)n;
+    free(rp);
+    free(zp);
+    return st;
+}
 
 static int64_t pc_len(const or_pc *M, int64_t n) { (void)M; return n; }
 
@@ -444,25 +473,24 @@ int or_pc_apply(const or_pc *M, int64_t n, const double *r, double *z)
     case OR_PC_CALLBACK:
         return M->fn(M->user, n, r, z);
     case OR_PC_CPR: {
-        /* Two-stage CPR in the pressure-first order (Alg. 6, read as:
-         * x = Pi_p M_p^{-1} Pi_r f;  r = f - A x;  x = x + R(A)^{-1} r). */
-        const int32_t nb = M->nb, bs = M->bs;
-        double *rp = (double *)malloc(sizeof(double) * (size_t)nb);
-        double *zp = (double *)malloc(sizeof(double) * (size_t)nb);
+        /* CPR-like preconditioners, Algs. 5-8, each step in the printed
+         * order: the first stage maps f to x; every later stage forms
+         * r = f - A x and adds its correction, x = x + stage(r).  Alg. 6 is
+         * garbled as printed (its second step discards the first, its last
+         * uses f) and is read as  x = P f;  r = f - A x;  x = x + F r. */
+        static const char *forms[4] = {"PF", "FP", "FPF", "FFPF"};
+        const char *seq = forms[(M->form >= 0 && M->form < 4) ? M->form : 0];
         double *res = (double *)malloc(sizeof(double) * (size_t)n);
-        double *z2 = (double *)malloc(sizeof(double) * (size_t)n);
-        int st = OR_OK;
-        or_qimpes_restrict(nb, bs, M->w, r, rp);
-        if (M->pstage) st = M->pstage(M->pstage_user, nb, rp, zp);
-        else if (M->mixed) or_ilu0_solve_f32(M->n, M->ptr, M->col, M->lu32, rp, zp);
-        else or_ilu0_solve(M->n, M->ptr, M->col, M->lu, rp, zp);
-        or_prolong(nb, bs, zp, z);
-        memcpy(res, r, sizeof(double) * (size_t)n);
-        or_amxpby(-1.0, M->A, z, 1.0, res);
-        if (M->mixed) or_bilu0_solve_f32(nb, bs, M->bptr, M->bcol, M->blu32, M->bdinv32, res, z2);
-        else or_bilu0_solve(nb, bs, M->bptr, M->bcol, M->blu, M->bdinv, res, z2);
-        for (int64_t i = 0; i < n; ++i) z[i] = z[i] + z2[i];
-        free(rp); free(zp); free(res); free(z2);
+        double *dz = (double *)malloc(sizeof(double) * (size_t)n);
+        int st = cpr_stage(M, seq[0], n, r, z);
+        for (int k = 1; seq[k] && st == OR_OK; ++k) {
+            memcpy(res, r, sizeof(double) * (size_t)n);
+            or_amxpby(-1.0, M->A, z, 1.0, res);
+            st = cpr_stage(M, seq[k], n, res, dz);
+            for (int64_t i = 0; i < n; ++i) z[i] = z[i] + dz[i];
+        }
+        free(res);
+        free(dz);
         return st;
     }
     default:

@@ -47,7 +47,10 @@ class SolveInfo(C.Structure):
 
 class PcOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("net", _vp), ("log_perm", _vp)]
+                ("net", _vp), ("log_perm", _vp), ("cpr_form", C.c_int32)]
+
+
+CPR_FORMS = ("pf", "fp", "fpf", "ffpf")   # rs_cpr_form: Algs. 6, 5, 7, 8
 
 
 # (name, restype, argtypes) for every exported symbol of include/rs.h
@@ -287,10 +290,11 @@ class Precond:
     """rs_precond_setup / apply / destroy."""
 
     def __init__(self, ctx: Context, A: Mat, kind: str = "ilu0", prec: str = "fp64",
-                 net=None, log_perm=None, grid=None):
+                 net=None, log_perm=None, grid=None, form: str = "pf"):
         self.ctx, self.A, self.kind = ctx, A, kind
         opts = PcOpts()
         opts.prec = MIXED if prec == "mixed" else FP64
+        opts.cpr_form = CPR_FORMS.index(form)
         self._keep = []
         if net is not None:
             opts.net = net.h.value

@@ -188,6 +188,7 @@ struct rs_pc {
     const double *log_perm;
     int nx, ny, nz;
     int bad_row;
+    int form;                // rs_cpr_form: order of the CPR stages
 };
 
 // ---------------------------------------------------------------------------

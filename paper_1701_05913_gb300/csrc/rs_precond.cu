@@ -75,6 +75,32 @@ static int grid_for(rs_ctx *ctx, int64_t n)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8));
 }
 
+// One stage of a CPR-like preconditioner on v: 'F' = R(A)^{-1} v, the
+// block ILU(0) of the full system; 'P' = Pi_p M_p^{-1} (Pi_r v), quasi-IMPES
+// restriction (the identity on a scalar matrix), the pressure solve (ILU(0)
+// of the decoupled matrix, or the network) and prolongation.
+static int cpr_stage(rs_pc *M, char kind, const double *v, double *out, const int *skip)
+{
+    rs_ctx *ctx = M->ctx;
+    const rs_mat *A = M->A;
+    if (kind == 'F') return rs_ilu_apply(M->bilu, v, out, nullptr, skip);
+    const int nb = A->nrows, bs = A->bs;
+    const double *rp = v;
+    if (bs > 1) {
+        k_qimpes_restrict<<<grid_for(ctx, nb), 256, 0, ctx->stream>>>(nb, bs, M->w, v, M->rp, skip);
+        RS_TRY(rs_check_launch(ctx));
+        rp = M->rp;
+    }
+    double *zp = bs > 1 ? M->zp : out;
+    if (M->type == RS_PC_CPR_LEARNED) RS_TRY(rs_net_apply_pressure(M, rp, zp, skip));
+    else RS_TRY(rs_ilu_apply(M->ilu, rp, zp, nullptr, skip));
+    if (bs > 1) {
+        k_prolong<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(nb, bs, M->zp, out, skip);
+        RS_TRY(rs_check_launch(ctx));
+    }
+    return RS_OK;
+}
+
 int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip)
 {
     rs_ctx *ctx = M->ctx;
@@ -89,26 +115,18 @@ int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip)
         return rs_ilu_apply(M->bilu, r, z, nullptr, skip);
     case RS_PC_CPR:
     case RS_PC_CPR_LEARNED: {
-        const int nb = A->nrows, bs = A->bs;
-        const double *rp = r;
-        if (bs > 1) {
-            k_qimpes_restrict<<<grid_for(ctx, nb), 256, 0, ctx->stream>>>(nb, bs, M->w, r, M->rp, skip);
-            RS_TRY(rs_check_launch(ctx));
-            rp = M->rp;
-        }
-        double *zp = bs > 1 ? M->zp : M->t2;
-        if (M->type == RS_PC_CPR_LEARNED) RS_TRY(rs_net_apply_pressure(M, rp, zp, skip));
-        else RS_TRY(rs_ilu_apply(M->ilu, rp, zp, nullptr, skip));
-        if (bs > 1) {
-            k_prolong<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(nb, bs, M->zp, M->t2, skip);
+        // Algs. 5-8: the first stage maps f to z; every later stage forms
+        // t1 = f - A z and adds its correction t2 = stage(t1) to z
+        static const char *forms[4] = {"PF", "FP", "FPF", "FFPF"};
+        const char *seq = forms[M->form];
+        RS_TRY(cpr_stage(M, seq[0], r, z, skip));
+        for (int k = 1; seq[k]; ++k) {
+            RS_TRY(rs_residual_launch(A, r, z, M->t1, nullptr, skip));
+            RS_TRY(cpr_stage(M, seq[k], M->t1, M->t2, skip));
+            k_copy_add<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(A->n, M->t2, z, 1, skip);
             RS_TRY(rs_check_launch(ctx));
         }
-        // t1 = f - A z1
-        RS_TRY(rs_residual_launch(A, r, M->t2, M->t1, nullptr, skip));
-        // z = z1 + R^{-1} t1
-        RS_TRY(rs_ilu_apply(M->bilu, M->t1, z, nullptr, skip));
-        k_copy_add<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(A->n, M->t2, z, 1, skip);
-        return rs_check_launch(ctx);
+        return RS_OK;
     }
     default:
         return RS_ERR_INVALID_ARG;
@@ -139,6 +157,11 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
     M->ctx = ctx;
     M->type = type;
     M->prec = opts ? opts->prec : RS_FP64;
+    M->form = opts ? opts->cpr_form : RS_CPR_PF;
+    if (M->form < RS_CPR_PF || M->form > RS_CPR_FFPF) {
+        delete M;
+        return RS_ERR_INVALID_ARG;
+    }
     M->A = A;
     M->bad_row = -1;
     const int fp32 = M->prec == RS_MIXED;

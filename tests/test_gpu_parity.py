@@ -389,6 +389,55 @@ def test_fgmres_cpr_bsr(rs, ctx, orc, prec):
     assert rel(xs, xo) <= 1e-6
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("form", ["fp", "fpf", "ffpf"])
+def test_cpr_forms_apply(rs, ctx, orc, form, prec):
+    """CPR-FP / FPF / FFPF (Algs. 5, 7, 8) against the oracle's forms."""
+    m = synth.black_oil_bsr3(synth.Grid(11, 7, 5), 14)
+    A = rs.Mat.bsr(ctx, m)
+    Ao = orc.Mat.bsr(m)
+    f = np.random.default_rng(15).standard_normal(A.n)
+    z = rs.Vec.zeros(ctx, A.n)
+    rs.Precond(ctx, A, "cpr", prec=prec, form=form).apply(vec(rs, ctx, f), z)
+    ref = orc.PC(Ao, "cpr", mixed=(prec == "mixed"), form=form).apply(f)
+    assert rel(z.numpy(), ref) <= (1e-12 if prec == "fp64" else 1e-5)
+
+
+def test_cpr_form_rejected(rs, ctx):
+    m = synth.black_oil_bsr3(synth.Grid(4, 3, 2), 1)
+    A = rs.Mat.bsr(ctx, m)
+    opts = rs.PcOpts()
+    opts.cpr_form = 7
+    h = rs._vp()
+    assert rs.lib().rs_precond_setup(ctx.h, A.h, rs._PC_KIND["cpr"], rs.C.byref(opts), rs.C.byref(h)) \
+        == rs.ERR_INVALID_ARG
+
+
+def test_cpr_fpf_solvers(rs, ctx, orc):
+    """The paper's production pairings: BiCGSTAB + CPR-FPF (Examples 2, 4)
+    and GMRES(30) + CPR-FPF (Example 3), on a black-oil-like block system."""
+    g = synth.Grid(14, 10, 6)
+    m = synth.black_oil_bsr3(g, 23)
+    Ao = orc.Mat.bsr(m)
+    b = orc.spmv(Ao, synth.x_true(Ao.n, 23))
+    Mo = orc.PC(Ao, "cpr", form="fpf")
+    A = rs.Mat.bsr(ctx, m)
+    M = rs.Precond(ctx, A, "cpr", form="fpf")
+    xo, io, _ = orc.fgmres(Ao, Mo, b, restart=30, rtol=1e-8)
+    x = rs.Vec.zeros(ctx, A.n)
+    info = rs.solve_fgmres(A, M, vec(rs, ctx, b), x, restart=30, rtol=1e-8)
+    assert info["status"] == 0 and io["status"] == 0
+    assert abs(info["iters"] - io["iters"]) <= 2
+    assert orc.norm2(b - orc.spmv(Ao, x.numpy())) / orc.norm2(b) <= 1e-8
+    assert rel(x.numpy(), xo) <= 1e-6
+    _, io2, _ = orc.bicgstab(Ao, Mo, b, rtol=1e-8)
+    x = rs.Vec.zeros(ctx, A.n)
+    info = rs.solve_bicgstab(A, M, vec(rs, ctx, b), x, rtol=1e-8)
+    assert info["status"] == 0 and io2["status"] == 0
+    assert orc.norm2(b - orc.spmv(Ao, x.numpy())) / orc.norm2(b) <= 1e-8
+    assert bicg_iters_ok(orc, Ao, Mo, b, 1e-8, info["iters"], io2["iters"])
+
+
 # ----------------------------------------------------------------------------
 # full size (128 x 128 x 64, the benchmarked configuration): sampled rows and
 # properties that hold at any size

@@ -394,6 +394,52 @@ def test_cpr_scalar_exact_stage_is_exact(orc):
     assert np.allclose(M.apply(f), lu.solve(f), rtol=1e-10, atol=1e-12)
 
 
+def _dense_operator(M, n):
+    """The preconditioner as a dense matrix B (z = B f), column by column."""
+    return np.stack([M.apply(e) for e in np.eye(n)], axis=1)
+
+
+def test_cpr_forms_are_the_printed_compositions(orc):
+    """Algs. 5-8 chain a pressure stage P and the block ILU(0) F through
+    residual corrections, so each form's error propagator I - B A is the
+    product of the stages' propagators in the printed order:
+      PF: E_F E_P,  FP: E_P E_F,  FPF: E_F E_P E_F,  FFPF: E_F E_P E_F E_F.
+    The stages' dense operators come from the separately pinned pieces:
+    B_F from block ILU(0), B_P = Pi_p ILU0(App')^{-1} Pi_r."""
+    m = synth.black_oil_bsr3(synth.Grid(3, 2, 2), 21)
+    A = orc.Mat.bsr(m)
+    D = _block_dense(m)
+    n, nb = D.shape[0], m["nb"]
+    I = np.eye(n)
+    BF = _dense_operator(orc.PC(A, "bilu0"), n)
+    w = orc.qimpes_weights(A)
+    App = orc.Mat(m["browptr"], m["bcol"], orc.qimpes_app(A, w), 1)
+    _, _, lu = orc.ilu0(App)
+
+    def pstage(v):
+        z = np.zeros(n)
+        z[0::3] = orc.ilu0_solve(App, lu, orc.qimpes_restrict(nb, 3, w, v))
+        return z
+    BP = np.stack([pstage(e) for e in np.eye(n)], axis=1)
+    EF, EP = I - BF @ D, I - BP @ D
+    pred = {"pf": EF @ EP, "fp": EP @ EF, "fpf": EF @ EP @ EF, "ffpf": EF @ EP @ EF @ EF}
+    for form in orc.PC.FORMS:
+        E = I - _dense_operator(orc.PC(A, "cpr", form=form), n) @ D
+        assert np.allclose(E, pred[form], rtol=1e-10, atol=1e-12), form
+
+
+def test_cpr_forms_exact_when_block_ilu_is_exact(orc):
+    """On a 1-D chain block ILU(0) is the exact block LU, so every form that
+    ends with (or begins with) an F stage returns A^{-1} f."""
+    m = synth.black_oil_bsr3(synth.Grid(9, 1, 1), 4)
+    A = orc.Mat.bsr(m)
+    D = _block_dense(m)
+    f = np.random.default_rng(22).standard_normal(D.shape[0])
+    x = np.linalg.solve(D, f)
+    for form in orc.PC.FORMS:
+        assert np.allclose(orc.PC(A, "cpr", form=form).apply(f), x, rtol=1e-10, atol=1e-11), form
+
+
 # ----------------------------------------------------------------------------
 # GMRES / FGMRES (Sec. 3, Alg. 1)
 # ----------------------------------------------------------------------------
