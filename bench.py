@@ -59,6 +59,8 @@ WORKLOADS = {
                                              precond="cpr", prec="mixed"),
     "cpr_learned_bsr3_128x128x128": dict(kind="bsr_learned", grid=(128, 128, 128), kz=1.0, solver="fgmres",
                                          precond="cpr_learned", prec="mixed"),
+    "cg_ilu0_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="cg", precond="ilu0",
+                               prec="fp64"),
     # the paper's production pairing (Examples 2 and 4): BiCGSTAB + CPR-FPF (Alg. 7)
     "cpr_fpf_bicgstab_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="bicgstab",
                                              precond="cpr", prec="mixed", form="fpf"),
@@ -163,6 +165,8 @@ def executed_launches(w, infos):
         I, C = info["iters"], info["restarts"]
         if w["solver"] == "bicgstab":
             applies, spmv = 2 * I, 2 * I + 1
+        elif w["solver"] == "cg":
+            applies, spmv = I, I + C + 1
         else:
             applies = I + (0 if w["solver"] == "fgmres" else C)
             spmv = I + C + 1
@@ -306,6 +310,8 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
     t0 = time.perf_counter()
     if w["solver"] == "bicgstab":
         _, info, _ = oracle.bicgstab(A, M, b, rtol=RTOL, maxit=maxit)
+    elif w["solver"] == "cg":
+        _, info, _ = oracle.cg(A, M, b, rtol=RTOL, maxit=maxit)
     else:
         _, info, _ = oracle.gmres(A, M, b, restart=30, rtol=RTOL, maxit=maxit, flexible=w["solver"] == "fgmres")
     return time.perf_counter() - t0, setup, info["iters"]
@@ -421,6 +427,8 @@ class Case:
 def solve_fn(rs, w):
     if w["solver"] == "bicgstab":
         return lambda c, M: rs.solve_bicgstab(c.A, M, c.b, c.x, rtol=RTOL)
+    if w["solver"] == "cg":
+        return lambda c, M: rs.solve_cg(c.A, M, c.b, c.x, rtol=RTOL)
     if w["solver"] == "fgmres":
         return lambda c, M: rs.solve_fgmres(c.A, M, c.b, c.x, restart=30, rtol=RTOL)
     return lambda c, M: rs.solve_gmres(c.A, M, c.b, c.x, restart=30, rtol=RTOL)
@@ -567,8 +575,8 @@ def run_gpu(args, w, rank, world, local):
             "vs_baseline": None, "dtype": "f64" if w["prec"] == "fp64" else "f64+f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "grid": list(w["grid"]), "unknowns": cases[0].A.n,
-                       "nnz": int(cases[0].A.nnz), "block_size": cases[0].A.bs, "solver": w["solver"] + "(30)"
-                       if w["solver"] != "bicgstab" else "bicgstab",
+                       "nnz": int(cases[0].A.nnz), "block_size": cases[0].A.bs,
+                       "solver": w["solver"] + "(30)" if "gmres" in w["solver"] else w["solver"],
                        "precond": w["precond"] + ("-" + w["form"] if "form" in w else ""),
                        "precision": w["prec"], "rtol": RTOL, "seeds": [seeds[0], seeds[-1]],
                        "l2": "flushed between steps (512 MB write)",

@@ -231,6 +231,14 @@ int rs_solve_fgmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32
 /* BiCGSTAB (named in Sec. 3; used in Examples 2, 4, 5). */
 int rs_solve_bicgstab(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, double rtol,
                       int32_t maxit, rs_solve_info *info);
+/* Preconditioned conjugate gradient (Alg. 2) for symmetric positive
+ * definite A and M (e.g. the pressure matrix with ILU(0), whose factors are
+ * then L D L^T).  One iteration is one pass of Alg. 2's loop; the stopping
+ * test on the recursive residual is confirmed on the true residual, from
+ * which the method restarts if it has drifted.  (p, A p) <= 0 or (r, z) = 0
+ * returns RS_ERR_BREAKDOWN. */
+int rs_solve_cg(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, double rtol, int32_t maxit,
+                rs_solve_info *info);
 
 /* ---- learned pressure stage ------------------------------------------- */
 /* A 3-D U-Net (4 levels, 16 channels, 3x3x3 convolutions, ReLU, 2x2x2

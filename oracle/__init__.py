@@ -111,6 +111,8 @@ def _declare(L):
                            C.c_int32, C.c_int32, C.c_int32, _f64p, C.c_int32, C.POINTER(Info)]
     L.or_bicgstab.argtypes = [mp, C.POINTER(_PC), _f64p, _f64p, C.c_double, C.c_int32,
                               _f64p, C.c_int32, C.POINTER(Info)]
+    L.or_cg.argtypes = [mp, C.POINTER(_PC), _f64p, _f64p, C.c_double, C.c_int32,
+                        _f64p, C.c_int32, C.POINTER(Info)]
 
 
 def _p(a, ct):
@@ -403,6 +405,18 @@ def gmres(A: Mat, M: PC | None, b, x0=None, restart=30, rtol=1e-8, maxit=10000,
 
 def fgmres(A, M, b, x0=None, restart=30, rtol=1e-8, maxit=10000, hist_len=0):
     return gmres(A, M, b, x0, restart, rtol, maxit, "right", True, False, hist_len)
+
+
+def cg(A: Mat, M: PC | None, b, x0=None, rtol=1e-8, maxit=10000, hist_len=0):
+    """Preconditioned conjugate gradient (Alg. 2) for SPD A and M."""
+    b = _f64(b)
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    info = Info()
+    hist = np.zeros(max(hist_len, 1))
+    Ms = M.s if M is not None else PC(A, "none").s
+    lib().or_cg(C.byref(A.s), C.byref(Ms), _p(b, C.c_double), _p(x, C.c_double),
+                rtol, maxit, _p(hist, C.c_double), hist_len, C.byref(info))
+    return x, info.as_dict(), hist[:min(hist_len, info.iters)]
 
 
 def bicgstab(A: Mat, M: PC | None, b, x0=None, rtol=1e-8, maxit=10000, hist_len=0):

@@ -766,3 +766,82 @@ done:
     free(r); free(rh); free(p); free(v); free(s); free(t); free(ph); free(sh);
     return status;
 }
+
+/* Preconditioned conjugate gradient, Alg. 2, for symmetric positive definite
+ * A and M.  One iteration is one pass of the printed loop: z = M^{-1} r;
+ * rho = (r, z); p = z (first pass) or p = z + (rho / rho_prev) p; q = A p;
+ * alpha = rho / (p, q); x += alpha p; r -= alpha q; stop on ||r||.  The
+ * stopping norm is the recursive residual; when it passes the tolerance the
+ * true residual b - A x is recomputed, and the loop restarts from it (p
+ * discarded) if it has drifted above.  (p, q) <= 0 or a non-finite rho is a
+ * breakdown (A or M not positive definite). */
+int or_cg(const or_mat *A, const or_pc *M, const double *b, double *x,
+          double rtol, int32_t maxit, double *hist, int32_t hist_len, or_info *info)
+{
+    const int64_t n = mat_n(A);
+    memset(info, 0, sizeof(*info));
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *z = (double *)malloc(sizeof(double) * (size_t)n);
+    double *p = (double *)malloc(sizeof(double) * (size_t)n);
+    double *q = (double *)malloc(sizeof(double) * (size_t)n);
+    const double bnorm = or_norm2(n, b);
+    int status = OR_NOT_CONVERGED;
+    int32_t it = 0;
+    double rn = 0.0;
+    if (bnorm == 0.0) {
+        or_set(n, 0.0, x);
+        status = OR_OK;
+        goto done;
+    }
+    const double tol = rtol * bnorm;
+    for (;;) {
+        /* r = b - A x (line 1) */
+        memcpy(r, b, sizeof(double) * (size_t)n);
+        or_amxpby(-1.0, A, x, 1.0, r);
+        rn = or_norm2(n, r);
+        if (rn <= tol) { status = OR_OK; break; }
+        if (it >= maxit) break;
+        double rho_prev = 0.0;
+        int first = 1, converged = 0;
+        while (it < maxit) {
+            or_pc_apply(M, n, r, z);                               /* line 4 */
+            const double rho = or_dot(n, r, z);                    /* line 5 */
+            if (!isfinite(rho) || rho == 0.0) { status = OR_BREAKDOWN; goto done; }
+            if (first) {                                           /* lines 6-11 */
+                memcpy(p, z, sizeof(double) * (size_t)n);
+            } else {
+                const double beta = rho / rho_prev;
+                for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+            }
+            first = 0;
+            or_spmv(A, p, q);                                      /* line 12 */
+            const double pq = or_dot(n, p, q);                     /* line 13 */
+            if (!(pq > 0.0) || !isfinite(pq)) { status = OR_BREAKDOWN; goto done; }
+            const double alpha = rho / pq;
+            for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];   /* line 14 */
+            for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];   /* line 15 */
+            it += 1;
+            rn = or_norm2(n, r);                                   /* line 16 */
+            if (hist && it - 1 < hist_len) hist[it - 1] = rn / bnorm;
+            rho_prev = rho;
+            if (rn <= tol) { converged = 1; break; }
+        }
+        if (!converged) {
+            /* out of iterations: the true residual decides */
+            memcpy(r, b, sizeof(double) * (size_t)n);
+            or_amxpby(-1.0, A, x, 1.0, r);
+            if (or_norm2(n, r) <= tol) status = OR_OK;
+            break;
+        }
+        /* recursive residual converged: confirm with the true residual */
+    }
+done:
+    memcpy(r, b, sizeof(double) * (size_t)n);
+    or_amxpby(-1.0, A, x, 1.0, r);
+    info->true_rel_res = bnorm > 0.0 ? or_norm2(n, r) / bnorm : 0.0;
+    info->implicit_rel_res = bnorm > 0.0 ? rn / bnorm : 0.0;
+    info->iters = it;
+    info->status = status;
+    free(r); free(z); free(p); free(q);
+    return status;
+}

@@ -96,6 +96,7 @@ SIGNATURES = [
                                   C.POINTER(SolveInfo)]),
     ("rs_solve_bicgstab", C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int32,
                                     C.POINTER(SolveInfo)]),
+    ("rs_solve_cg", C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int32, C.POINTER(SolveInfo)]),
     ("rs_net_num_params", C.c_int64, []),
     ("rs_net_create", C.c_int, [_vp, _f32p, C.c_int64, C.c_float, C.POINTER(_vp)]),
     ("rs_net_destroy", C.c_int, [C.POINTER(_vp)]),
@@ -448,6 +449,10 @@ def solve_fgmres(A: Mat, M, b: Vec, x: Vec, restart=30, rtol=1e-8, maxit=10000):
 
 def solve_bicgstab(A: Mat, M, b: Vec, x: Vec, rtol=1e-8, maxit=10000):
     return _solve(lib().rs_solve_bicgstab, A, M, b, x, rtol, maxit)
+
+
+def solve_cg(A: Mat, M, b: Vec, x: Vec, rtol=1e-8, maxit=10000):
+    return _solve(lib().rs_solve_cg, A, M, b, x, rtol, maxit)
 
 
 def vec_dot(x: Vec, y: Vec) -> float:

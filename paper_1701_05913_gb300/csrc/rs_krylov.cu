@@ -761,31 +761,238 @@ extern "C" int rs_solve_bicgstab(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs
             bool restart = false;
             while (!restart) {
                 for (int it = 0; it < batch; ++it) {
-                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(0, n, p, r, v, s, t, x, ph, sh, rh,
-                                                                   ctx->red_partials, ctx->red_ticket, d);
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(0, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                       ctx->red_partials, ctx->red_ticket, d);
+                    }
                     ctx->launches++;
                     if (M) st = rs_pc_apply_dev(M, p, ph, halt);
                     if (st) goto out;
                     st = rs_spmv_launch(A, ph, 1.0, 0.0, v, halt);
                     if (st) goto out;
-                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(3, n, p, r, v, s, t, x, ph, sh, rh,
-                                                                   ctx->red_partials, ctx->red_ticket, d);
-                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(1, n, p, r, v, s, t, x, ph, sh, rh,
-                                                                   ctx->red_partials, ctx->red_ticket, d);
-                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(5, n, p, r, v, s, t, x, ph, sh, rh,
-                                                                   ctx->red_partials, ctx->red_ticket, d);
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(3, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                       ctx->red_partials, ctx->red_ticket, d);
+                    }
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(1, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                       ctx->red_partials, ctx->red_ticket, d);
+                    }
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(5, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                       ctx->red_partials, ctx->red_ticket, d);
+                    }
                     ctx->launches += 3;
                     if (M) st = rs_pc_apply_dev(M, s, sh, halt);
                     if (st) goto out;
                     st = rs_spmv_launch(A, sh, 1.0, 0.0, t, halt);
                     if (st) goto out;
-                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(4, n, p, r, v, s, t, x, ph, sh, rh,
-                                                                   ctx->red_partials, ctx->red_ticket, d);
-                    k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(2, n, p, r, v, s, t, x, ph, sh, rh,
-                                                                   ctx->red_partials, ctx->red_ticket, d);
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(4, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                       ctx->red_partials, ctx->red_ticket, d);
+                    }
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_bicg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(2, n, p, r, v, s, t, x, ph, sh, rh,
+                                                                       ctx->red_partials, ctx->red_ticket, d);
+                    }
                     ctx->launches += 2;
                 }
                 BicgDev hd;
+                if (cudaMemcpyAsync(&hd, d, sizeof(hd), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+                    cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+                    st = RS_ERR_CUDA;
+                    goto out;
+                }
+                info->iters = hd.iters;
+                info->implicit_rel_res = hd.implicit / bnorm;
+                if (hd.status == 1) { status = RS_OK; goto done; }
+                if (hd.breakdown) { status = RS_ERR_BREAKDOWN; goto done; }
+                if (hd.fresh) { restart = true; break; }       // confirm with the true residual
+                if (hd.done || hd.iters >= maxit) { status = RS_NOT_CONVERGED; goto done; }
+            }
+        }
+    }
+done:
+    st = rs_collect_device_error(ctx, &info->bad_row);
+    if (st) goto out;
+    st = finish_info(ctx, A, b, x, r, bnorm, info);
+    if (st) goto out;
+    if (status == RS_OK && info->true_rel_res > rtol && bnorm > 0) status = RS_NOT_CONVERGED;
+    if (status == RS_NOT_CONVERGED && info->true_rel_res <= rtol && bnorm > 0) status = RS_OK;
+out:
+    rs_free(ctx, buf);
+    rs_free(ctx, d);
+    info->status = st ? st : status;
+    info->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return info->status;
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioned conjugate gradient (Alg. 2), device-resident like BiCGSTAB:
+// the scalars live in device memory and the last block of each reduction
+// forms beta or alpha; the host synchronises once per batch of iterations.
+// ---------------------------------------------------------------------------
+struct CgDev {
+    double red[2];
+    double rho, rho0, alpha, beta, tol, bnorm, implicit;
+    int iters, done, fresh, breakdown, maxit, status, first, pad;
+};
+
+//  op 0: red = {(r, z)}                 -> rho, beta = rho / rho_prev (0 on the first pass)
+//  op 1: p = z + beta p
+//  op 2: red = {(p, q)}                 -> alpha = rho / (p, q)
+//  op 3: x += alpha p; r -= alpha q; red = {||r||^2} -> convergence test
+__global__ void __launch_bounds__(RS_RED_THREADS)
+k_cg(int op, int n, double *x, double *r, const double *__restrict__ z, double *p,
+     const double *__restrict__ q, double *partials, unsigned *ticket, CgDev *d)
+{
+    if (*(volatile int *)&d->done) return;
+    const double alpha = d->alpha, beta = d->beta;
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        switch (op) {
+        case 0: acc[0] = fma(r[i], z[i], acc[0]); break;
+        case 1: p[i] = fma(beta, p[i], z[i]); break;
+        case 2: acc[0] = fma(p[i], q[i], acc[0]); break;
+        case 3: {
+            x[i] = fma(alpha, p[i], x[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            acc[0] = fma(ri, ri, acc[0]);
+            break;
+        }
+        }
+    }
+    if (op == 1) return;
+    if (!reduce_partials<1>(acc, 1, partials, ticket, d->red)) return;
+    if (threadIdx.x != 0) return;
+    switch (op) {
+    case 0: {
+        const double rho = d->red[0];
+        if (!(rho != 0.0) || !isfinite(rho)) { d->breakdown = 1; d->done = 1; break; }
+        d->beta = d->first ? 0.0 : rho / d->rho0;
+        d->first = 0;
+        d->rho = rho;
+        break;
+    }
+    case 2: {
+        const double pq = d->red[0];
+        if (!(pq > 0.0) || !isfinite(pq)) { d->breakdown = 1; d->done = 1; break; }
+        d->alpha = d->rho / pq;
+        break;
+    }
+    case 3: {
+        d->iters += 1;
+        d->rho0 = d->rho;
+        const double rn = sqrt(d->red[0]);
+        d->implicit = rn;
+        if (rn <= d->tol) { d->done = 1; d->fresh = 1; break; }
+        if (d->iters >= d->maxit) d->done = 1;
+        break;
+    }
+    }
+}
+
+// restart from the true residual (in r, ||r||^2 in *r2): p = 0, first pass
+__global__ void k_cg_restart(int n, double *p, CgDev *d, const double *r2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0.0;
+    if (blockIdx.x || threadIdx.x) return;
+    const double rn = sqrt(*r2);
+    d->implicit = rn;
+    d->fresh = 0;
+    d->done = 0;
+    d->first = 1;
+    d->beta = 0.0;
+    if (rn <= d->tol) { d->done = 1; d->status = 1; return; }   // status 1: converged
+    if (d->iters >= d->maxit) d->done = 1;
+}
+
+extern "C" int rs_solve_cg(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, double rtol, int32_t maxit,
+                           rs_solve_info *info)
+{
+    if (!A || !bv || !xv || !info) return RS_ERR_INVALID_ARG;
+    if (maxit < 0 || !(rtol >= 0)) return RS_ERR_INVALID_ARG;
+    if (bv->n != A->n || xv->n != A->n) return RS_ERR_SIZE_MISMATCH;
+    memset(info, 0, sizeof(*info));
+    info->bad_row = -1;
+    rs_ctx *ctx = A->ctx;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int n = A->n;
+    const int ld = (n + 31) / 32 * 32;
+    double *buf = nullptr;
+    CgDev *d = nullptr;
+    int st = rs_alloc(ctx, (void **)&buf, sizeof(double) * (size_t)ld * 4);
+    if (!st) st = rs_alloc(ctx, (void **)&d, sizeof(CgDev));
+    int status = RS_NOT_CONVERGED;
+    double bnorm = 0.0;
+    const double *b = bv->d;
+    double *x = xv->d;
+    double *r = buf, *z = buf + ld, *p = buf + 2 * (size_t)ld, *q = buf + 3 * (size_t)ld;
+    if (!M) z = r;       // no preconditioner: z = r
+    if (st) goto out;
+    {
+        st = rs_dot_launch(ctx, n, b, b, ctx->d_scalars);
+        if (st) goto out;
+        cudaMemcpyAsync(ctx->h_pinned, ctx->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { st = RS_ERR_CUDA; goto out; }
+        bnorm = sqrt(ctx->h_pinned[0]);
+        if (bnorm == 0.0) {
+            cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream);
+            status = RS_OK;
+            goto done;
+        }
+        CgDev h0;
+        memset(&h0, 0, sizeof(h0));
+        h0.tol = rtol * bnorm;
+        h0.bnorm = bnorm;
+        h0.maxit = maxit;
+        cudaMemcpyAsync(d, &h0, sizeof(h0), cudaMemcpyHostToDevice, ctx->stream);
+        const int gr = red_grid(ctx), gb = blas_grid(ctx, n);
+        int *halt = &d->done;
+        const int batch = 8;
+        for (;;) {
+            st = rs_residual_launch(A, b, x, r, &d->red[1], nullptr);
+            if (st) goto out;
+            k_cg_restart<<<gb, 256, 0, ctx->stream>>>(n, p, d, &d->red[1]);
+            ctx->launches++;
+            bool restart = false;
+            while (!restart) {
+                for (int it = 0; it < batch; ++it) {
+                    if (M) st = rs_pc_apply_dev(M, r, z, halt);
+                    if (st) goto out;
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_cg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(0, n, x, r, z, p, q, ctx->red_partials,
+                                                                     ctx->red_ticket, d);
+                    }
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_cg<<<gb, RS_RED_THREADS, 0, ctx->stream>>>(1, n, x, r, z, p, q, ctx->red_partials,
+                                                                     ctx->red_ticket, d);
+                    }
+                    ctx->launches += 2;
+                    st = rs_spmv_launch(A, p, 1.0, 0.0, q, halt);
+                    if (st) goto out;
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_cg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(2, n, x, r, z, p, q, ctx->red_partials,
+                                                                     ctx->red_ticket, d);
+                    }
+                    {
+                        RsProfScope prof(ctx, RS_PROF_BLAS1);
+                        k_cg<<<gr, RS_RED_THREADS, 0, ctx->stream>>>(3, n, x, r, z, p, q, ctx->red_partials,
+                                                                     ctx->red_ticket, d);
+                    }
+                    ctx->launches += 2;
+                }
+                CgDev hd;
                 if (cudaMemcpyAsync(&hd, d, sizeof(hd), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
                     cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
                     st = RS_ERR_CUDA;

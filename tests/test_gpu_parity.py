@@ -389,6 +389,38 @@ def test_fgmres_cpr_bsr(rs, ctx, orc, prec):
     assert rel(xs, xo) <= 1e-6
 
 
+@pytest.mark.parametrize("shape", [(12, 10, 8), (31, 17, 9)])
+@pytest.mark.parametrize("pc", ["none", "ilu0"])
+def test_cg_parity(rs, ctx, orc, shape, pc):
+    """Alg. 2 on the SPD pressure matrix: iterations within 2 of the oracle,
+    true residual and solution within the benchmark spec's tolerances."""
+    g = synth.Grid(*shape)
+    d = synth.pressure_7pt(g, 33, kz_scale=0.1)
+    Ao = orc.Mat.csr(d)
+    b = orc.spmv(Ao, synth.x_true(g.n, 33))
+    xo, io, _ = orc.cg(Ao, orc.PC(Ao, pc), b, rtol=1e-8)
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "ilu0") if pc == "ilu0" else None
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_cg(A, M, vec(rs, ctx, b), x, rtol=1e-8)
+    assert info["status"] == 0 and io["status"] == 0
+    assert abs(info["iters"] - io["iters"]) <= 2, (info["iters"], io["iters"])
+    assert orc.norm2(b - orc.spmv(Ao, x.numpy())) / orc.norm2(b) <= 1e-8
+    assert within_conditioning_bound(orc, Ao, b, x.numpy(), xo) or rel(x.numpy(), xo) <= 1e-6
+
+
+def test_cg_breakdown_and_zero_rhs(rs, ctx):
+    d = dict(n=2, rowptr=np.array([0, 2, 4], np.int32), col=np.array([0, 1, 0, 1], np.int32),
+             val=np.array([0.0, 1.0, 1.0, 0.0]))    # indefinite: (p, A p) = 0 on the first step
+    A = rs.Mat.csr(ctx, d)
+    x = rs.Vec.zeros(ctx, 2)
+    info = rs.solve_cg(A, None, rs.Vec(ctx, np.array([1.0, 0.0])), x, rtol=1e-8)
+    assert info["status"] == rs.ERR_BREAKDOWN
+    x = rs.Vec(ctx, np.ones(2))
+    info = rs.solve_cg(A, None, rs.Vec.zeros(ctx, 2), x)
+    assert info["status"] == 0 and np.all(x.numpy() == 0.0)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("form", ["fp", "fpf", "ffpf"])
 def test_cpr_forms_apply(rs, ctx, orc, form, prec):

@@ -609,6 +609,49 @@ def test_bicgstab_single_eigvec_and_spd_count(orc):
     assert info["iters"] == 1 and np.allclose(x, v / lam, rtol=1e-12, atol=1e-13)
 
 
+# ----------------------------------------------------------------------------
+# CG (Alg. 2)
+# ----------------------------------------------------------------------------
+def test_cg_eigenvectors_and_finite_termination(orc):
+    """Unpreconditioned CG on the 1-D Dirichlet Poisson matrix: one step for
+    an eigenvector (x = v / lambda), q steps for q eigenvectors, at most n
+    steps for any right-hand side (finite termination on SPD systems)."""
+    n = 50
+    A = orc.Mat.csr(csr_dict(poisson1d(n)))
+    v, lam = eig1d(n, 7)
+    x, info, _ = orc.cg(A, None, v, rtol=1e-12)
+    assert info["iters"] == 1 and info["status"] == 0
+    assert np.allclose(x, v / lam, rtol=1e-12, atol=1e-13)
+    ks, cs = (2, 5, 11, 30), (1.0, -0.5, 2.0, 0.25)
+    b = sum(eig1d(n, k)[0] * c for k, c in zip(ks, cs))
+    x, info, hist = orc.cg(A, None, b, rtol=1e-8, hist_len=4)
+    assert info["iters"] == 4 and hist[2] > 1e-3
+    xr = sum(eig1d(n, k)[0] * c / eig1d(n, k)[1] for k, c in zip(ks, cs))
+    assert np.allclose(x, xr, rtol=1e-6, atol=1e-6 * np.abs(xr).max())
+    b = np.random.default_rng(31).standard_normal(n)
+    x, info, _ = orc.cg(A, None, b, rtol=1e-10, maxit=10 * n)
+    assert info["status"] == 0 and info["iters"] <= n
+    assert np.allclose(poisson1d(n) @ x, b, rtol=1e-9, atol=1e-9)
+
+
+def test_cg_exact_preconditioner_and_breakdown(orc):
+    """With M = A (dense solve as the preconditioner) CG converges in one
+    step; on an indefinite matrix (p, A p) = 0 is reported as a breakdown."""
+    d = synth.pressure_7pt(synth.Grid(6, 5, 4), 32)
+    A = orc.Mat.csr(d)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"])).tocsc()
+    lu = spla.splu(S)
+    b = orc.spmv(A, synth.x_true(d["n"], 32))
+    x, info, _ = orc.cg(A, orc.PC(A, "callback", fn=lambda r: lu.solve(r)), b, rtol=1e-12)
+    assert info["iters"] == 1 and info["status"] == 0
+    assert np.allclose(x, lu.solve(b), rtol=1e-10, atol=1e-12)
+    x, info, _ = orc.cg(A, orc.PC(A, "ilu0"), b, rtol=1e-10)
+    assert info["status"] == 0 and info["true_rel_res"] <= 1e-10
+    B = orc.Mat.csr(csr_dict(np.array([[0.0, 1.0], [1.0, 0.0]])))
+    _, info, _ = orc.cg(B, None, np.array([1.0, 0.0]))
+    assert info["status"] == orc.BREAKDOWN
+
+
 def test_mixed_precision_preconditioners_converge(orc):
     d = synth.pressure_7pt(synth.Grid(12, 12, 8), 23, kz_scale=0.1)
     A = orc.Mat.csr(d)
