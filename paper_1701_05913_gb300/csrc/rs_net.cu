@@ -246,6 +246,107 @@ k_conv3(int D, int H, int W, const bf16 *__restrict__ X, const bf16 *__restrict_
 }
 
 // ---------------------------------------------------------------------------
+// first layer: 2 input channels (r / rms(r) and log k).  The 27 taps x 2
+// channels form the K dimension of the implicit GEMM (54, padded to 64):
+// each voxel's im2col row is gathered once from a 2-channel halo, so the
+// tensor cores see 4 k-steps per row instead of 27 taps padded to 16
+// channels each.
+// ---------------------------------------------------------------------------
+#define FK 64            // packed K: k = 2 t + c
+#define FKS (FK + 8)     // shared-memory row stride (bf16) of the im2col and weight tiles
+__global__ void __launch_bounds__(CONV_THREADS)
+k_conv3_first(int D, int H, int W, const double *__restrict__ r, const double *__restrict__ logk,
+              const double *__restrict__ rscale, const bf16 *__restrict__ Wp, const float *__restrict__ bias,
+              bf16 *__restrict__ Y, const int *skip)
+{
+    if (skipped(skip)) return;
+    __shared__ __align__(16) bf16 sa[TX * TY * TZ * FKS];
+    __shared__ __align__(16) bf16 sb[16 * FKS];
+    __shared__ unsigned sh[HVOX];
+    const int ntx = (W + TX - 1) / TX, nty = (H + TY - 1) / TY;
+    int b = blockIdx.x;
+    const int tx0 = (b % ntx) * TX;
+    b /= ntx;
+    const int ty0 = (b % nty) * TY, tz0 = (b / nty) * TZ;
+    // weights: sb[co][2 t + c] = W[t][co][c] (forward layout [27][16][16], c < 2)
+    for (int i = threadIdx.x; i < 16 * FK; i += blockDim.x) {
+        const int co = i / FK, k = i % FK;
+        sb[co * FKS + k] = k < 54 ? Wp[((k >> 1) * 16 + co) * 16 + (k & 1)] : __float2bfloat16_rn(0.f);
+    }
+    // halo: (r * rscale, log k) as bfloat16 pairs, zero outside the grid
+    const double rsc = *rscale;
+    for (int hv = threadIdx.x; hv < HVOX; hv += blockDim.x) {
+        const int hx = hv % HX, hy = (hv / HX) % HY, hz = hv / (HX * HY);
+        const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
+        unsigned val = 0u;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D) {
+            const int64_t vi = ((int64_t)gz * H + gy) * W + gx;
+            __nv_bfloat162 pr = __floats2bfloat162_rn((float)(r[vi] * rsc), (float)logk[vi]);
+            val = *(unsigned *)&pr;
+        }
+        sh[hv] = val;
+    }
+    __syncthreads();
+    // im2col: thread v builds the row of brick voxel v = (lz TY + ly) TX + lx
+    {
+        const int v = threadIdx.x;
+        const int lx = v % TX, ly = (v / TX) % TY, lz = v / (TX * TY);
+        unsigned *row = (unsigned *)(sa + v * FKS);
+#pragma unroll
+        for (int t = 0; t < 27; ++t) {
+            const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+            row[t] = sh[((lz + dz) * HY + (ly + dy)) * HX + lx + dx];
+        }
+#pragma unroll
+        for (int t = 27; t < FK / 2; ++t) row[t] = 0u;
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane >> 3, rr = lane & 7;
+    float acc[2][2][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[m][n][j] = 0.f;
+#pragma unroll
+    for (int kc = 0; kc < FK / 16; ++kc) {
+        unsigned b00, b01, b10, b11;
+        ldsm_x4(b00, b01, b10, b11, sb + ((q >> 1) * 8 + rr) * FKS + kc * 16 + (q & 1) * 8);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int row = warp * 2 + m;
+            unsigned a0, a1, a2, a3;
+            ldsm_x4(a0, a1, a2, a3, sa + (row * TX + rr + (q & 1) * 8) * FKS + kc * 16 + (q >> 1) * 8);
+            mma_bf16(acc[m][0], a0, a1, a2, a3, b00, b01);
+            mma_bf16(acc[m][1], a0, a1, a2, a3, b10, b11);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int row = warp * 2 + m;
+        const int gy = ty0 + row % TY, gz = tz0 + row / TY;
+        if (gy >= H || gz >= D) continue;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int gx = tx0 + (lane >> 2) + half * 8;
+            if (gx >= W) continue;
+            const int64_t vi = ((int64_t)gz * H + gy) * W + gx;
+#pragma unroll
+            for (int n = 0; n < 2; ++n) {
+                const int co = n * 8 + (lane & 3) * 2;
+                float v0 = acc[m][n][half * 2] + bias[co], v1 = acc[m][n][half * 2 + 1] + bias[co + 1];
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+                *(__nv_bfloat162 *)(Y + vi * 16 + co) = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // weight gradient: partial[blk][t][co][ci] = sum over the brick of
 // G[v][co] * X[v + off_t][ci];  partial[blk][27*16*CIN + co] = sum_v G[v][co]
 // ---------------------------------------------------------------------------
@@ -714,8 +815,8 @@ static int conv_forward(rs_net *net, int l, const bf16 *X, const bf16 *U, const 
     RsProfScope prof(c, RS_PROF_NET);
     switch (kLayers[l].mode) {
     case IN_FIRST:
-        k_conv3<16, 16, IN_FIRST><<<grid, CONV_THREADS, conv_smem(16, 16), c->stream>>>(
-            L.nz, L.ny, L.nx, nullptr, nullptr, r, logk, net->scal + 1, net->wf[l], bias, 1, Y, skip);
+        k_conv3_first<<<grid, CONV_THREADS, 0, c->stream>>>(L.nz, L.ny, L.nx, r, logk, net->scal + 1, net->wf[l],
+                                                            bias, Y, skip);
         break;
     case IN_CATUP:
         k_conv3<32, 16, IN_CATUP><<<grid, CONV_THREADS, conv_smem(32, 16), c->stream>>>(
