@@ -13,9 +13,11 @@
 // fragments loaded with ldmatrix.  The data gradient is the same kernel with
 // flipped, transposed weights; the weight gradient multiplies the output
 // gradient (transposed with ldmatrix.trans) by the shifted input per tap.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -78,6 +80,7 @@ struct rs_net {
     int nx, ny, nz;
     Level lv[NET_LEVELS];
     bf16 *act[NET_NLAYERS];                 // layer outputs
+    bf16 *up0;                              // the coarse decoder input upsampled to the finest level
     bf16 *pool[NET_LEVELS];                 // pooled inputs of e1a, e2a, e3a
     bf16 *g16a[NET_LEVELS], *g16b[NET_LEVELS], *g32[NET_LEVELS];
     float *partials;                        // weight-gradient partials
@@ -343,6 +346,279 @@ k_conv3_first(int D, int H, int W, const double *__restrict__ r, const double *_
                 *(__nv_bfloat162 *)(Y + vi * 16 + co) = __floats2bfloat162_rn(v0, v1);
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3x3x3 convolution on the tcgen05 tensor cores (16 output channels), used
+// for the finest level.
+//
+// Implicit GEMM: D[voxel][co] = sum over taps t and input channels ci of
+// X[voxel + off_t][ci] W[t][co][ci].  A brick is 8 x 16 y BZ z output voxels;
+// per (tap, 16-channel chunk, z-plane) one tcgen05.mma with M = 128 (the
+// 8 x 16 voxels of a plane), N = 16, K = 16 accumulates in tensor memory.
+//
+// Operands sit in shared memory in the canonical no-swizzle K-major layout
+// (core matrix: 8 rows of 16 bytes).  The brick's input halo (10 x, 18 y,
+// BZ + 2 z) is one TMA box per 8-channel plane, stored [z][y][x][8 channels]:
+// a core matrix is 8 consecutive x of one y row (128 contiguous bytes), the
+// next core matrix along M is the next y row (160 bytes on) and the next 8
+// channels are the next plane.  A tap only moves the start address (by
+// 16 dx + 160 dy + one z slab dz), so one copy of the halo serves all 27.
+//
+// A single thread issues one M = 128 MMA every ~150 cycles whatever N is;
+// at N = 16 that is a quarter of what the tensor pipe takes, so four warps
+// issue.  Warp roles, coupled only by mbarriers:
+//   warps 0-3   MMA issue (lane 0).  Warp w owns accumulator w of each TMEM
+//               set: a z-plane and half of the taps (16 input channels), or a
+//               quarter of the taps (32); the partial sums meet in the epilogue.
+//   warps 4-11  epilogue: tcgen05.ld of the partials, bias, ReLU, bf16 stores;
+//               a warp reads TMEM lanes 32 (warp mod 4) + 0..31.
+//   warp 12     producer (lane 0): TMA box loads into an NBUF-slot ring.
+// Barriers: full[slot] (TMA bytes), empty[slot] (the four issuers' MMAs
+// that read the slot completed), tfull[set] (accumulators ready), tempty[set]
+// (the epilogue has read them).  Every wait is bounded.
+// ---------------------------------------------------------------------------
+template <int CIN>
+struct TcCfg {
+    static constexpr int BX = 8, BY = 16, BZ = CIN == 16 ? 2 : 1;
+    static constexpr int HXb = BX + 2, HYb = BY + 2, HZb = BZ + 2;
+    static constexpr int RS = HXb * 16;                      // bytes of one halo row (10 x, 8 channels)
+    static constexpr int BOX = HZb * HYb * RS;               // bytes of one plane's TMA box
+    static constexpr int PB = (BOX + 127) / 128 * 128;      // plane stride in shared memory
+    static constexpr int NP = CIN / 8, KC = CIN / 16;
+    static constexpr int SLOT = NP * PB;
+    static constexpr int NBUF = CIN == 16 ? 6 : 5;
+    static constexpr int WB = 27 * KC * 512;                // weights [t][kc][k half][co][8]
+    static constexpr int SMEM = NBUF * SLOT + WB;
+    static constexpr int NGR = CIN == 16 ? 2 : 4;           // tap groups per z-plane (one issuer each)
+    static constexpr int TPG = (27 + NGR - 1) / NGR;        // taps per group
+    static constexpr int NSET = 4, SET_COLS = 64, TMEM_COLS = 256;
+    static constexpr int THREADS = 13 * 32;
+};
+
+__device__ __forceinline__ uint64_t tc_desc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    // shared-memory matrix descriptor: start, leading (K) and stride (M/N)
+    // byte offsets in 16-byte units; descriptor version 1; no swizzle
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = 16, M = 128
+#define TC_IDESC ((1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24))
+
+// TMA: one box of a 4-D tensor map (coordinates innermost first) into shared memory
+__device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                          unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+                 "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tacc, uint64_t da, uint64_t db, unsigned accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tacc),
+                 "l"(da), "l"(db), "r"(TC_IDESC), "r"(accumulate)
+                 : "memory");
+}
+
+// the MMAs of issuer WI for one brick: z-plane WI / NGR, taps of group WI % NGR;
+// fully unrolled, so each descriptor is the slot's base plus a constant
+template <int CIN, int WI>
+__device__ __forceinline__ void tc_issue(uint32_t tacc, uint64_t dA0, uint64_t dB0)
+{
+    typedef TcCfg<CIN> C;
+    constexpr int z = WI / C::NGR, g = WI % C::NGR;
+#pragma unroll
+    for (int i = 0; i < C::TPG; ++i) {
+        const int t = g * C::TPG + i;
+        if (t < 27) {
+            const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+#pragma unroll
+            for (int kc = 0; kc < C::KC; ++kc) {
+                const uint64_t da = dA0 + (uint64_t)((2 * kc * C::PB + ((z + dz) * C::HYb + dy) * C::RS + dx * 16) >> 4);
+                const uint64_t db = dB0 + (uint64_t)(((t * C::KC + kc) * 512) >> 4);
+                tc_mma(tacc, da, db, (i | kc) ? 1u : 0u);
+            }
+        }
+    }
+}
+
+template <int CIN>
+__global__ void __launch_bounds__(TcCfg<CIN>::THREADS, 1)
+k_conv3_tc(int D, int H, int W, const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap umap,
+           const bf16 *__restrict__ Wp, const float *__restrict__ bias, bf16 *__restrict__ Y, int *err,
+           long long limit, const int *skip)
+{
+    typedef TcCfg<CIN> C;
+    if (skipped(skip)) return;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char *bufs = tc_smem;                         // NBUF x SLOT
+    unsigned char *wts = tc_smem + C::NBUF * C::SLOT;      // WB
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) unsigned long long full[C::NBUF], empty[C::NBUF], tfull[C::NSET], tempty[C::NSET];
+    __shared__ float sbias[16];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nbx = (W + C::BX - 1) / C::BX, nby = (H + C::BY - 1) / C::BY, nbz = (D + C::BZ - 1) / C::BZ;
+    const int nbricks = nbx * nby * nbz;
+    const int nmine = blockIdx.x < nbricks ? (nbricks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    for (int i = tid; i < 27 * 16 * C::NP; i += blockDim.x) {
+        const int t = i / (16 * C::NP), co = (i / C::NP) % 16, pl = i % C::NP;
+        const uint4 v = *(const uint4 *)(Wp + ((size_t)t * 16 + co) * CIN + pl * 8);
+        *(uint4 *)(wts + (t * C::KC + (pl >> 1)) * 512 + (pl & 1) * 256 + (co >> 3) * 128 + (co & 7) * 16) = v;
+    }
+    if (tid < 16) sbias[tid] = bias[tid];
+    if (tid == 0) {
+        for (int k = 0; k < C::NBUF; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], 4);
+        }
+        for (int k = 0; k < C::NSET; ++k) {
+            mbar_init(&tfull[k], 4);
+            mbar_init(&tempty[k], 256);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(C::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the weights, for the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    if (warp == 12) {
+        // producer
+        if (lane == 0) {
+            for (int k = 0; k < nmine; ++k) {
+                const int slot = k % C::NBUF, b = blockIdx.x + k * gridDim.x;
+                if (k >= C::NBUF) mbar_wait(&empty[slot], (unsigned)((k / C::NBUF - 1) & 1), limit, err);
+                const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+                mbar_arrive_expect_tx(&full[slot], (unsigned)(C::NP * C::BOX));
+#pragma unroll
+                for (int pl = 0; pl < C::NP; ++pl) {
+                    // 16 input channels: both planes from X; 32: planes 0, 1 from the
+                    // upsampled coarse tensor, 2, 3 from X (the skip connection)
+                    const CUtensorMap *map = (CIN == 32 && pl < 2) ? &umap : &xmap;
+                    tma_load4(bufs + slot * C::SLOT + pl * C::PB, map, (pl & 1) * 8, bx * C::BX - 1, by * C::BY - 1,
+                              bz * C::BZ - 1, &full[slot]);
+                }
+            }
+            // the copies of the last bricks have landed before this block can end
+            for (int k = nmine > C::NBUF ? nmine - C::NBUF : 0; k < nmine; ++k)
+                mbar_wait(&full[k % C::NBUF], (unsigned)((k / C::NBUF) & 1), limit, err);
+        }
+    } else if (warp < 4) {
+        // MMA issue
+        if (lane == 0) {
+            const uint64_t dB0 = tc_desc(smem_u32(wts), 256, 128);
+            for (int k = 0; k < nmine; ++k) {
+                const int slot = k % C::NBUF, set = k % C::NSET;
+                mbar_wait(&full[slot], (unsigned)((k / C::NBUF) & 1), limit, err);
+                if (k >= C::NSET) mbar_wait(&tempty[set], (unsigned)((k / C::NSET - 1) & 1), limit, err);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tacc = tmem_base + set * C::SET_COLS + warp * 16;
+                const uint64_t dA0 = tc_desc(smem_u32(bufs + slot * C::SLOT), C::PB, C::RS);
+                switch (warp) {
+                case 0: tc_issue<CIN, 0>(tacc, dA0, dB0); break;
+                case 1: tc_issue<CIN, 1>(tacc, dA0, dB0); break;
+                case 2: tc_issue<CIN, 2>(tacc, dA0, dB0); break;
+                default: tc_issue<CIN, 3>(tacc, dA0, dB0); break;
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&empty[slot]))
+                             : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&tfull[set]))
+                             : "memory");
+            }
+            // this issuer's last MMAs have completed before TMEM is released
+            if (nmine > 0)
+                mbar_wait(&tfull[(nmine - 1) % C::NSET], (unsigned)(((nmine - 1) / C::NSET) & 1), limit, err);
+        }
+    } else {
+        // epilogue: warps 4..11
+        const int e = warp - 4, q = warp & 3;
+        const int row = q * 32 + lane;                      // M row = TMEM lane
+        const int x = row & 7, y = row >> 3;
+        const int z = C::BZ == 2 ? (e >> 2) : 0;
+        const int c0 = C::BZ == 2 ? 0 : (e >> 2) * 8;      // 32 input channels: two warps per quadrant
+        constexpr int NCOL = C::BZ == 2 ? 16 : 8;
+        for (int k = 0; k < nmine; ++k) {
+            const int set = k % C::NSET, b = blockIdx.x + k * gridDim.x;
+            mbar_wait(&tfull[set], (unsigned)((k / C::NSET) & 1), limit, err);
+            __syncwarp();   // the TMEM loads below are warp-collective
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float f[NCOL];
+#pragma unroll
+            for (int j = 0; j < NCOL; ++j) f[j] = sbias[c0 + j];
+#pragma unroll
+            for (int g = 0; g < C::NGR; ++g) {
+                const uint32_t ta =
+                    tmem_base + ((uint32_t)(q * 32) << 16) + set * C::SET_COLS + (z * C::NGR + g) * 16 + c0;
+                uint32_t v[16];
+                if constexpr (NCOL == 16) {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                                   "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                                   "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                                 : "r"(ta));
+                } else {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                                   "=r"(v[6]), "=r"(v[7])
+                                 : "r"(ta));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < NCOL; ++j) f[j] += __uint_as_float(v[j]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&tempty[set]);
+            const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+            const int gx = bx * C::BX + x, gy = by * C::BY + y, gz = bz * C::BZ + z;
+            if (gx < W && gy < H && gz < D) {
+                const int64_t vi = ((int64_t)gz * H + gy) * W + gx;
+                unsigned packed[NCOL / 2];
+#pragma unroll
+                for (int j = 0; j < NCOL / 2; ++j) {
+                    __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(f[2 * j], 0.f), fmaxf(f[2 * j + 1], 0.f));
+                    packed[j] = *(unsigned *)&h;
+                }
+                uint4 *dst = (uint4 *)(Y + vi * 16 + c0);
+                dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                if constexpr (NCOL == 16) dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(C::TMEM_COLS));
+    }
+}
+
+// nearest-neighbour x2 upsampling of a 16-channel tensor: Uf[z][y][x] = Uc[z/2][y/2][x/2]
+__global__ void k_upsample2(int D, int H, int W, const bf16 *__restrict__ Uc, bf16 *__restrict__ Uf, const int *skip)
+{
+    if (skipped(skip)) return;
+    const int64_t n = (int64_t)D * H * W;
+    const int W2 = W >> 1, H2 = H >> 1;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % W), y = (int)((v / W) % H), z = (int)(v / ((int64_t)W * H));
+        const int64_t c = ((int64_t)(z >> 1) * H2 + (y >> 1)) * W2 + (x >> 1);
+        const uint4 *s = (const uint4 *)(Uc + c * 16);
+        uint4 *d = (uint4 *)(Uf + v * 16);
+        d[0] = s[0];
+        d[1] = s[1];
     }
 }
 
@@ -731,13 +1007,57 @@ static void ensure_attrs()
     set_attr_dw<16, IN_PLAIN>();
     set_attr_dw<16, IN_FIRST>();
     set_attr_dw<32, IN_CATUP>();
+    cudaFuncSetAttribute(k_conv3_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<16>::SMEM);
+    cudaFuncSetAttribute(k_conv3_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<32>::SMEM);
     g_attrs_set = true;
+}
+
+// TMA tensor map of an NDHWC bf16 tensor [D][H][W][C]: boxes of 8 channels
+// x bx x by y x bz z, zero fill outside; the encoder comes from the driver
+// through the runtime's versioned entry-point query
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static int make_tmap(CUtensorMap *m, const bf16 *base, int C, int W, int H, int D, int bx, int by, int bz)
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return RS_ERR_CUDA;
+        fn = (EncodeTiledFn)p;
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? RS_OK : RS_ERR_CUDA;
+}
+
+// the finest level runs on the tcgen05 kernel (RS_NET_TC=0 selects the
+// mma.sync kernel everywhere, for comparison)
+static bool use_tc()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("RS_NET_TC");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
 }
 
 static void free_workspace(rs_net *net)
 {
     rs_ctx *c = net->ctx;
     for (int l = 0; l < NET_NLAYERS; ++l) { rs_free(c, net->act[l]); net->act[l] = nullptr; }
+    rs_free(c, net->up0);
+    net->up0 = nullptr;
     for (int l = 0; l < NET_LEVELS; ++l) {
         rs_free(c, net->pool[l]);
         rs_free(c, net->g16a[l]);
@@ -771,6 +1091,7 @@ static int ensure_workspace(rs_net *net, int nx, int ny, int nz)
     int st = RS_OK;
     for (int l = 0; l < NET_NLAYERS && !st; ++l)
         st = rs_alloc(c, (void **)&net->act[l], sizeof(bf16) * 16 * net->lv[kLayers[l].level].nvox);
+    if (!st) st = rs_alloc(c, (void **)&net->up0, sizeof(bf16) * 16 * net->lv[0].nvox);
     int64_t maxp = 0;
     for (int l = 0; l < NET_LEVELS && !st; ++l) {
         const int64_t nv = net->lv[l].nvox;
@@ -813,6 +1134,27 @@ static int conv_forward(rs_net *net, int l, const bf16 *X, const bf16 *U, const 
     const int grid = (int)nbricks(L);
     const float *bias = net->p + net->boff[l];
     RsProfScope prof(c, RS_PROF_NET);
+    if (kLayers[l].level == 0 && kLayers[l].mode != IN_FIRST && use_tc()) {
+        CUtensorMap xmap, umap;
+        if (kLayers[l].mode == IN_CATUP) {
+            // the coarse input, upsampled to this level, is the first half of the concatenation
+            typedef TcCfg<32> TC;
+            k_upsample2<<<ew_grid(c, L.nvox), 256, 0, c->stream>>>(L.nz, L.ny, L.nx, U, net->up0, skip);
+            RS_TRY(rs_check_launch(c));
+            RS_TRY(make_tmap(&umap, net->up0, 16, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
+            RS_TRY(make_tmap(&xmap, X, 16, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
+            const int nb = ((L.nx + TC::BX - 1) / TC::BX) * ((L.ny + TC::BY - 1) / TC::BY) * ((L.nz + TC::BZ - 1) / TC::BZ);
+            k_conv3_tc<32><<<std::min(nb, c->num_sms), TC::THREADS, TC::SMEM, c->stream>>>(
+                L.nz, L.ny, L.nx, xmap, umap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip);
+        } else {
+            typedef TcCfg<16> TC;
+            RS_TRY(make_tmap(&xmap, X, 16, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
+            const int nb = ((L.nx + TC::BX - 1) / TC::BX) * ((L.ny + TC::BY - 1) / TC::BY) * ((L.nz + TC::BZ - 1) / TC::BZ);
+            k_conv3_tc<16><<<std::min(nb, c->num_sms), TC::THREADS, TC::SMEM, c->stream>>>(
+                L.nz, L.ny, L.nx, xmap, xmap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip);
+        }
+        return rs_check_launch(c);
+    }
     switch (kLayers[l].mode) {
     case IN_FIRST:
         k_conv3_first<<<grid, CONV_THREADS, 0, c->stream>>>(L.nz, L.ny, L.nx, r, logk, net->scal + 1, net->wf[l],
