@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, NOT_CONVERGED, INVALID, ZERO_PIVOT, BREAKDOWN = 0, 1, -1, -3, -4
-PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CALLBACK = 0, 1, 2, 3, 4
+PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CALLBACK, PC_RAS = 0, 1, 2, 3, 4, 5
 
 
 def build(force: bool = False) -> str:
@@ -71,7 +71,8 @@ class _PC(C.Structure):
                 ("blu", _f64p), ("bdinv", _f64p), ("blu32", _f32p), ("bdinv32", _f32p),
                 ("A", C.POINTER(_Mat)), ("w", _f64p),
                 ("pstage", APPLY_FN), ("pstage_user", C.c_void_p),
-                ("fn", APPLY_FN), ("user", C.c_void_p), ("form", C.c_int32)]
+                ("fn", APPLY_FN), ("user", C.c_void_p), ("form", C.c_int32),
+                ("ras", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -106,6 +107,14 @@ def _declare(L):
     L.or_qimpes_restrict.argtypes = [C.c_int32, C.c_int32, _f64p, _f64p, _f64p]
     L.or_prolong.argtypes = [C.c_int32, C.c_int32, _f64p, _f64p]
     L.or_pc_apply.argtypes = [C.POINTER(_PC), C.c_int64, _f64p, _f64p]
+    L.or_iluk_symbolic.argtypes = [C.c_int32, _i32p, _i32p, C.c_int32, C.POINTER(_i32p), C.POINTER(_i32p)]
+    L.or_ras_setup.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _i32p, C.c_int32, C.c_int32,
+                               C.POINTER(C.c_void_p), _i32p]
+    L.or_ras_free.argtypes = [C.c_void_p]
+    L.or_ras_apply.argtypes = [C.c_void_p, _f64p, _f64p]
+    L.or_ras_sizes.argtypes = [C.c_void_p, _i32p, C.POINTER(C.c_int64)]
+    L.or_ras_export.argtypes = [C.c_void_p, _i32p, _i32p, _i32p, _f64p]
+    L.free.argtypes = [C.c_void_p]
     L.or_orthogonalise.argtypes = [C.c_int64, C.c_int32, _f64p, _f64p, _f64p, C.c_int32]
     L.or_gmres.argtypes = [mp, C.POINTER(_PC), _f64p, _f64p, C.c_int32, C.c_double, C.c_int32,
                            C.c_int32, C.c_int32, C.c_int32, _f64p, C.c_int32, C.POINTER(Info)]
@@ -285,11 +294,74 @@ def orthogonalise(V, w, i, mgs=False):
     return w, h
 
 
+def iluk_pattern(n, ptr, col, p):
+    """ILU(p) pattern by level of fill: (ptr, col) of the kept entries."""
+    ptr, col = _i32(ptr), _i32(col)
+    op, oc = _i32p(), _i32p()
+    lib().or_iluk_symbolic(n, _p(ptr, C.c_int32), _p(col, C.c_int32), p, C.byref(op), C.byref(oc))
+    optr = np.ctypeslib.as_array(op, shape=(n + 1,)).copy()
+    ocol = np.ctypeslib.as_array(oc, shape=(max(int(optr[-1]), 1),))[:int(optr[-1])].copy()
+    lib().free(C.cast(op, C.c_void_p))
+    lib().free(C.cast(oc, C.c_void_p))
+    return optr, ocol
+
+
+def contiguous_partition(n, nsub):
+    """Row i -> subdomain floor(i nsub / n): contiguous blocks of rows, the
+    way the paper's MAP gives each process a range of rows."""
+    return (np.arange(n, dtype=np.int64) * nsub // max(n, 1)).astype(np.int32)
+
+
+class Ras:
+    """Restricted additive Schwarz with ILU(level) local solvers (scalar A)."""
+
+    def __init__(self, A: Mat, nsub: int, part=None, overlap: int = 1, level: int = 0):
+        assert A.bs == 1
+        self.A = A
+        self.part = _i32(contiguous_partition(A.nrows, nsub) if part is None else part)
+        h = C.c_void_p()
+        bad = C.c_int32(-1)
+        self.status = lib().or_ras_setup(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
+                                         _p(A.val, C.c_double), nsub, _p(self.part, C.c_int32), overlap,
+                                         level, C.byref(h), C.byref(bad))
+        self.bad = bad.value
+        self.h = h
+
+    def apply(self, r):
+        r = _f64(r)
+        z = np.empty_like(r)
+        lib().or_ras_apply(self.h, _p(r, C.c_double), _p(z, C.c_double))
+        return z
+
+    def structure(self):
+        """The stacked block-diagonal local problems: (gidx, ptr, col, lu)."""
+        ne = C.c_int32()
+        nz = C.c_int64()
+        lib().or_ras_sizes(self.h, C.byref(ne), C.byref(nz))
+        gidx = np.empty(ne.value, np.int32)
+        ptr = np.empty(ne.value + 1, np.int32)
+        col = np.empty(nz.value, np.int32)
+        lu = np.empty(nz.value)
+        lib().or_ras_export(self.h, _p(gidx, C.c_int32), _p(ptr, C.c_int32), _p(col, C.c_int32),
+                            _p(lu, C.c_double))
+        return gidx, ptr, col, lu
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().or_ras_free(self.h)
+        except Exception:
+            pass
+
+
 # ----------------------------------------------------------------------------
 # Preconditioners
 # ----------------------------------------------------------------------------
 class PC:
-    """Oracle preconditioner: none / ilu0 / bilu0 / cpr / callback.
+    """Oracle preconditioner: none / ilu0 / bilu0 / cpr / callback / ras.
+
+    kind='ras': restricted additive Schwarz, `ras` = dict(nsub=, part=,
+    overlap=, level=) as for Ras.
 
     kind='cpr' on a BSR matrix: quasi-IMPES restriction, ILU(0) of App'
     (or `pstage`, a callable rp -> zp), prolongation, residual, block ILU(0).
@@ -302,7 +374,8 @@ class PC:
 
     FORMS = ("pf", "fp", "fpf", "ffpf")   # Algs. 6, 5, 7, 8
 
-    def __init__(self, A: Mat, kind: str = "ilu0", mixed: bool = False, pstage=None, fn=None, form: str = "pf"):
+    def __init__(self, A: Mat, kind: str = "ilu0", mixed: bool = False, pstage=None, fn=None, form: str = "pf",
+                 ras=None):
         self.A = A
         self.kind = kind
         self._keep = []
@@ -343,6 +416,11 @@ class PC:
         elif kind == "callback":
             s.fn = self._wrap(fn)
             s.type = PC_CALLBACK
+        elif kind == "ras":
+            self.ras = Ras(A, **(ras or {}))
+            self.status, self.bad = self.ras.status, self.ras.bad
+            s.ras = self.ras.h
+            s.type = PC_RAS
         else:
             raise ValueError(kind)
         self.s = s

@@ -394,11 +394,262 @@ void or_prolong(int32_t nb, int32_t bs, const double *p, double *z)
 }
 
 /* ------------------------------------------------------------------------ */
+/* ILU(k) pattern by level of fill (Sec. 4.1 names ILU(k) as the default     */
+/* local solver of RAS; the rule is the textbook one, Saad, "Iterative       */
+/* methods for sparse linear systems", Sec. 10.3.3): entries of A have       */
+/* level 0; eliminating with pivot row k produces (i, j), j > k, at level    */
+/* lev(i,k) + lev(k,j) + 1, keeping the smallest level met; entries whose    */
+/* level is at most p are kept.  The numeric ILU(k) is then ILU(0) on this   */
+/* pattern with zeros at the new positions.                                  */
+/* On return *optr (n+1) and *ocol (sorted rows) are malloc'ed.               */
+/* ------------------------------------------------------------------------ */
+int or_iluk_symbolic(int32_t n, const int32_t *ptr, const int32_t *col, int32_t p,
+                     int32_t **optr, int32_t **ocol)
+{
+    const int32_t NONE = -1;
+    int32_t *rp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int64_t cap = ptr[n] > 16 ? 2 * (int64_t)ptr[n] : 32, len = 0;
+    int32_t *rc = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    int32_t *rl = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);   /* level of each kept entry */
+    int32_t *lev = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *nxt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int32_t j = 0; j < n; ++j) lev[j] = NONE;
+    rp[0] = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        /* the row as a sorted linked list: head, nxt[], ending at NONE */
+        int32_t head = NONE, tail = NONE;
+        for (int32_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+            const int32_t c = col[q];
+            lev[c] = 0;
+            nxt[c] = NONE;
+            if (tail == NONE) head = c; else nxt[tail] = c;
+            tail = c;
+        }
+        for (int32_t k = head; k != NONE && k < i; k = nxt[k]) {
+            /* the upper part of the kept row k */
+            for (int64_t q = rp[k]; q < rp[k + 1]; ++q) {
+                const int32_t j = rc[q];
+                if (j <= k) continue;
+                const int32_t l = lev[k] + rl[q] + 1;
+                if (l > p) continue;
+                if (lev[j] != NONE) {
+                    if (l < lev[j]) lev[j] = l;
+                    continue;
+                }
+                /* insert j after the last entry below it, searching from k */
+                int32_t a = k;
+                while (nxt[a] != NONE && nxt[a] < j) a = nxt[a];
+                nxt[j] = nxt[a];
+                nxt[a] = j;
+                lev[j] = l;
+            }
+        }
+        for (int32_t c = head; c != NONE; c = nxt[c]) {
+            if (len == cap) {
+                cap *= 2;
+                rc = (int32_t *)realloc(rc, sizeof(int32_t) * (size_t)cap);
+                rl = (int32_t *)realloc(rl, sizeof(int32_t) * (size_t)cap);
+            }
+            rc[len] = c;
+            rl[len] = lev[c];
+            ++len;
+        }
+        for (int32_t c = head; c != NONE; c = nxt[c]) lev[c] = NONE;
+        rp[i + 1] = (int32_t)len;
+    }
+    free(rl);
+    free(lev);
+    free(nxt);
+    *optr = rp;
+    *ocol = rc;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restricted additive Schwarz (Sec. 4.1, after Cai and Sarkis).             */
+/* part[i] in [0, nsub) assigns row i to a subdomain.  Subdomain s is        */
+/* extended by `overlap` layers of the graph of A (layer m+1 = the columns   */
+/* of the rows of layer m); its local matrix A_s keeps the entries of A      */
+/* whose row and column both lie in the extended set, in ascending global    */
+/* order; the local solver is ILU(level) of A_s.  Apply:                     */
+/*   z_i = ( ILU(A_s)^{-1} r|ext(s) )_i  for s = part[i],                    */
+/* i.e. every subdomain solves on its extended rows and only the rows it     */
+/* owns are written (the restricted prolongation).                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n, nsub;
+    int32_t *part;           /* copy of the partition */
+    int32_t *ext_ptr;        /* nsub + 1 offsets into ext */
+    int32_t *ext;            /* extended rows of each subdomain, ascending */
+    int32_t **lptr, **lcol;  /* local ILU(k) pattern per subdomain */
+    double **llu;            /* local factors */
+} or_ras;
+
+void or_ras_free(or_ras *R)
+{
+    if (!R) return;
+    for (int32_t s = 0; s < R->nsub; ++s) {
+        free(R->lptr[s]);
+        free(R->lcol[s]);
+        free(R->llu[s]);
+    }
+    free(R->lptr);
+    free(R->lcol);
+    free(R->llu);
+    free(R->part);
+    free(R->ext_ptr);
+    free(R->ext);
+    free(R);
+}
+
+int or_ras_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, int32_t nsub,
+                 const int32_t *part, int32_t overlap, int32_t level, or_ras **out, int32_t *bad_row)
+{
+    *out = NULL;
+    *bad_row = -1;
+    if (nsub < 1 || overlap < 0 || level < 0) return OR_INVALID;
+    for (int32_t i = 0; i < n; ++i)
+        if (part[i] < 0 || part[i] >= nsub) return OR_INVALID;
+    or_ras *R = (or_ras *)calloc(1, sizeof(or_ras));
+    R->n = n;
+    R->nsub = nsub;
+    R->part = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    memcpy(R->part, part, sizeof(int32_t) * (size_t)n);
+    R->ext_ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nsub + 1));
+    R->lptr = (int32_t **)calloc((size_t)nsub, sizeof(int32_t *));
+    R->lcol = (int32_t **)calloc((size_t)nsub, sizeof(int32_t *));
+    R->llu = (double **)calloc((size_t)nsub, sizeof(double *));
+    int64_t cap = n > 0 ? n : 1, len = 0;
+    R->ext = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    char *in = (char *)malloc((size_t)(n > 0 ? n : 1));
+    int32_t *loc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int st = OR_OK;
+    R->ext_ptr[0] = 0;
+    for (int32_t s = 0; s < nsub && st == OR_OK; ++s) {
+        /* the extended set, by `overlap` rounds over the whole set */
+        for (int32_t i = 0; i < n; ++i) in[i] = part[i] == s;
+        for (int32_t m = 0; m < overlap; ++m) {
+            char *add = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+            for (int32_t i = 0; i < n; ++i)
+                if (in[i])
+                    for (int32_t q = ptr[i]; q < ptr[i + 1]; ++q) add[col[q]] = 1;
+            for (int32_t i = 0; i < n; ++i) in[i] = in[i] | add[i];
+            free(add);
+        }
+        int32_t ns = 0;
+        for (int32_t i = 0; i < n; ++i)
+            if (in[i]) {
+                if (len == cap) {
+                    cap *= 2;
+                    R->ext = (int32_t *)realloc(R->ext, sizeof(int32_t) * (size_t)cap);
+                }
+                loc[i] = ns++;
+                R->ext[len++] = i;
+            }
+        R->ext_ptr[s + 1] = (int32_t)len;
+        const int32_t *er = R->ext + R->ext_ptr[s];
+        /* local matrix A_s */
+        int32_t *ap = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ns + 1));
+        int64_t nz = 0;
+        for (int32_t a = 0; a < ns; ++a)
+            for (int32_t q = ptr[er[a]]; q < ptr[er[a] + 1]; ++q) nz += in[col[q]] ? 1 : 0;
+        int32_t *ac = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nz > 0 ? nz : 1));
+        double *av = (double *)malloc(sizeof(double) * (size_t)(nz > 0 ? nz : 1));
+        ap[0] = 0;
+        nz = 0;
+        for (int32_t a = 0; a < ns; ++a) {
+            for (int32_t q = ptr[er[a]]; q < ptr[er[a] + 1]; ++q)
+                if (in[col[q]]) {
+                    ac[nz] = loc[col[q]];
+                    av[nz] = val[q];
+                    ++nz;
+                }
+            ap[a + 1] = (int32_t)nz;
+        }
+        /* the ILU(level) pattern of A_s, with A_s's values and zeros at fill */
+        int32_t *kp, *kc;
+        or_iluk_symbolic(ns, ap, ac, level, &kp, &kc);
+        double *kv = (double *)malloc(sizeof(double) * (size_t)(kp[ns] > 0 ? kp[ns] : 1));
+        for (int32_t a = 0; a < ns; ++a) {
+            int32_t q = ap[a];
+            for (int32_t t = kp[a]; t < kp[a + 1]; ++t) {
+                while (q < ap[a + 1] && ac[q] < kc[t]) ++q;
+                kv[t] = (q < ap[a + 1] && ac[q] == kc[t]) ? av[q] : 0.0;
+            }
+        }
+        double *lu = (double *)malloc(sizeof(double) * (size_t)(kp[ns] > 0 ? kp[ns] : 1));
+        int32_t bad = -1;
+        st = or_ilu0(ns, kp, kc, kv, lu, &bad);
+        if (st != OR_OK) *bad_row = bad >= 0 ? er[bad] : -1;
+        R->lptr[s] = kp;
+        R->lcol[s] = kc;
+        R->llu[s] = lu;
+        free(ap);
+        free(ac);
+        free(av);
+        free(kv);
+    }
+    free(in);
+    free(loc);
+    if (st != OR_OK) {
+        or_ras_free(R);
+        return st;
+    }
+    *out = R;
+    return OR_OK;
+}
+
+void or_ras_apply(const or_ras *R, const double *r, double *z)
+{
+    for (int32_t s = 0; s < R->nsub; ++s) {
+        const int32_t *er = R->ext + R->ext_ptr[s];
+        const int32_t ns = R->ext_ptr[s + 1] - R->ext_ptr[s];
+        double *rl = (double *)malloc(sizeof(double) * (size_t)(ns > 0 ? ns : 1));
+        double *zl = (double *)malloc(sizeof(double) * (size_t)(ns > 0 ? ns : 1));
+        for (int32_t a = 0; a < ns; ++a) rl[a] = r[er[a]];
+        or_ilu0_solve(ns, R->lptr[s], R->lcol[s], R->llu[s], rl, zl);
+        for (int32_t a = 0; a < ns; ++a)
+            if (R->part[er[a]] == s) z[er[a]] = zl[a];
+        free(rl);
+        free(zl);
+    }
+}
+
+/* Sizes of the block-diagonal matrix that stacks the local problems in
+ * subdomain order: extended rows and stored entries. */
+void or_ras_sizes(const or_ras *R, int32_t *next, int64_t *nnz)
+{
+    *next = R->ext_ptr[R->nsub];
+    int64_t t = 0;
+    for (int32_t s = 0; s < R->nsub; ++s) t += R->lptr[s][R->ext_ptr[s + 1] - R->ext_ptr[s]];
+    *nnz = t;
+}
+
+/* That matrix: global row of every extended row, its pattern (columns
+ * numbered in the stacked order) and the factor values. */
+void or_ras_export(const or_ras *R, int32_t *gidx, int32_t *ptr, int32_t *col, double *lu)
+{
+    int64_t q = 0;
+    ptr[0] = 0;
+    for (int32_t s = 0; s < R->nsub; ++s) {
+        const int32_t base = R->ext_ptr[s], ns = R->ext_ptr[s + 1] - base;
+        for (int32_t a = 0; a < ns; ++a) {
+            gidx[base + a] = R->ext[base + a];
+            for (int32_t t = R->lptr[s][a]; t < R->lptr[s][a + 1]; ++t, ++q) {
+                col[q] = base + R->lcol[s][t];
+                lu[q] = R->llu[s][t];
+            }
+            ptr[base + a + 1] = (int32_t)q;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Preconditioner object (Sec. 3, Fig. 29: setup / solve / destroy).         */
 /* ------------------------------------------------------------------------ */
 typedef int (*or_apply_fn)(void *user, int64_t n, const double *r, double *z);
 
-enum { OR_PC_NONE = 0, OR_PC_ILU0 = 1, OR_PC_BILU0 = 2, OR_PC_CPR = 3, OR_PC_CALLBACK = 4 };
+enum { OR_PC_NONE = 0, OR_PC_ILU0 = 1, OR_PC_BILU0 = 2, OR_PC_CPR = 3, OR_PC_CALLBACK = 4, OR_PC_RAS = 5 };
 
 typedef struct {
     int32_t type;
@@ -424,6 +675,8 @@ typedef struct {
     /* CPR form: 0 PF (Alg. 6, read as below), 1 FP (Alg. 5), 2 FPF (Alg. 7),
      * 3 FFPF (Alg. 8) */
     int32_t form;
+    /* restricted additive Schwarz (type RAS) */
+    const or_ras *ras;
 } or_pc;
 
 /* One stage of a CPR-like preconditioner on a right-hand side v:
@@ -472,6 +725,9 @@ int or_pc_apply(const or_pc *M, int64_t n, const double *r, double *z)
         return OR_OK;
     case OR_PC_CALLBACK:
         return M->fn(M->user, n, r, z);
+    case OR_PC_RAS:
+        or_ras_apply(M->ras, r, z);
+        return OR_OK;
     case OR_PC_CPR: {
         /* CPR-like preconditioners, Algs. 5-8, each step in the printed
          * order: the first stage maps f to x; every later stage forms

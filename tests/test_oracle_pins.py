@@ -660,3 +660,178 @@ def test_mixed_precision_preconditioners_converge(orc):
     x32, i32, _ = orc.gmres(A, orc.PC(A, "ilu0", mixed=True), b)
     assert i32["status"] == 0 and i32["true_rel_res"] <= 1e-8
     assert abs(i32["iters"] - i64["iters"]) <= 3
+
+
+# ----------------------------------------------------------------------------
+# ILU(k) patterns and restricted additive Schwarz (Sec. 4.1)
+# ----------------------------------------------------------------------------
+def _fill_path_pattern(P, p):
+    """Brute force of the fill-path theorem (Rose-Tarjan; Hysom-Pothen for the
+    sum rule of levels): (i, j) has level <= p iff the directed graph of P
+    holds a path i -> j of at most p + 1 edges whose inner vertices are all
+    numbered below min(i, j)."""
+    n = P.shape[0]
+    keep = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        for j in range(n):
+            m = min(i, j)
+            found = bool(P[i, j]) or i == j
+            seen, frontier, d = {i}, [i], 0
+            while frontier and not found and d < p + 1:
+                d += 1
+                nxt = []
+                for u in frontier:
+                    for v in np.nonzero(P[u])[0]:
+                        if v == j:
+                            found = True
+                        elif v < m and v not in seen:
+                            seen.add(v)
+                            nxt.append(v)
+                frontier = nxt
+            keep[i, j] = found
+    return keep
+
+
+def test_iluk_pattern_is_the_fill_path_pattern(orc):
+    rng = np.random.default_rng(40)
+    for trial in range(4):
+        n = 24
+        P = (rng.random((n, n)) < 0.09) | np.eye(n, dtype=bool)
+        d = csr_dict(sp.csr_matrix(P.astype(float)))
+        for p in (0, 1, 2, 3):
+            ptr, col = orc.iluk_pattern(n, d["rowptr"], d["col"], p)
+            got = np.zeros((n, n), dtype=bool)
+            for i in range(n):
+                cols = col[ptr[i]:ptr[i + 1]]
+                assert (np.diff(cols) > 0).all()                     # sorted, no duplicates
+                got[i, cols] = True
+            assert np.array_equal(got, _fill_path_pattern(P, p)), (trial, p)
+
+
+def _ilu_on_pattern(orc, d, level):
+    """ILU(level) of d through the one-subdomain Schwarz object (no overlap):
+    the stacked matrix is then the matrix itself."""
+    R = orc.Ras(orc.Mat.csr(d), 1, overlap=0, level=level)
+    assert R.status == 0
+    gidx, ptr, col, lu = R.structure()
+    assert np.array_equal(gidx, np.arange(d["n"]))
+    return ptr, col, lu
+
+
+def test_iluk_numeric_invariant_7pt(orc):
+    g = synth.Grid(5, 4, 3)
+    d = synth.pressure_7pt(g, 41)
+    A = sp.csr_matrix((d["val"], d["col"], d["rowptr"]), shape=(g.n, g.n)).toarray()
+    prev = A != 0
+    for level in (1, 2):
+        ptr, col, lu = _ilu_on_pattern(orc, d, level)
+        e = dict(n=g.n, rowptr=ptr, col=col)
+        L, U = lu_dense_from_ilu(e, lu)
+        P = np.zeros_like(prev)
+        for i in range(g.n):
+            P[i, col[ptr[i]:ptr[i + 1]]] = True
+        assert (P & prev == prev).all() and P.sum() > prev.sum()      # the pattern only grows
+        LU = L @ U
+        assert np.allclose(LU[P], A[P], rtol=1e-13, atol=1e-13)       # (LU)_ij = a_ij on the ILU(k) pattern
+        assert (np.tril(L, -1)[~P] == 0).all() and (U[~P] == 0).all()
+        prev = P
+    # a 1-D chain has no fill at any level: ILU(k) = ILU(0) = the exact LU
+    d1 = csr_dict(poisson1d(30))
+    ptr, col, lu = _ilu_on_pattern(orc, d1, 3)
+    assert np.array_equal(ptr, d1["rowptr"]) and np.array_equal(col, d1["col"])
+    L, U = lu_dense_from_ilu(d1, lu)
+    assert np.allclose(L @ U, poisson1d(30).toarray(), atol=1e-14)
+
+
+def test_ras_one_subdomain_without_overlap_is_ilu0(orc):
+    d = synth.pressure_7pt(synth.Grid(6, 5, 4), 42)
+    A = orc.Mat.csr(d)
+    r = synth.x_true(d["n"], 43)
+    _, _, lu = orc.ilu0(A)
+    z = orc.Ras(A, 1, overlap=0, level=0).apply(r)
+    assert np.array_equal(z, orc.ilu0_solve(A, lu, r))
+
+
+def test_ras_one_row_per_subdomain_is_jacobi(orc):
+    d = synth.pressure_7pt(synth.Grid(5, 4, 3), 44)
+    n = d["n"]
+    A = orc.Mat.csr(d)
+    diag = sp.csr_matrix((d["val"], d["col"], d["rowptr"]), shape=(n, n)).diagonal()
+    r = synth.x_true(n, 45)
+    z = orc.Ras(A, n, part=np.arange(n, dtype=np.int32), overlap=0).apply(r)
+    assert np.array_equal(z, r / diag)
+
+
+def _extended_sets(S, part, nsub, overlap):
+    G = (S != 0).toarray()
+    sets = []
+    for s in range(nsub):
+        m = part == s
+        for _ in range(overlap):
+            m = m | G[m].any(axis=0)
+        sets.append(np.nonzero(m)[0])
+    return sets
+
+
+def test_ras_on_a_chain_is_the_restricted_block_solve(orc):
+    # on a tridiagonal matrix every local ILU(0) is the exact LU of the local
+    # matrix, so RAS is: solve densely on each extended set, keep owned rows
+    rng = np.random.default_rng(46)
+    n = 50
+    D = np.diag(3 + rng.random(n)) + np.diag(-rng.random(n - 1), 1) + np.diag(-rng.random(n - 1), -1)
+    S = sp.csr_matrix(D)
+    A = orc.Mat.csr(csr_dict(D))
+    r = rng.standard_normal(n)
+    parts = [orc.contiguous_partition(n, 4), rng.integers(0, 5, n).astype(np.int32)]
+    for part in parts:
+        nsub = int(part.max()) + 1
+        for overlap in (0, 1, 3):
+            z = orc.Ras(A, nsub, part=part, overlap=overlap).apply(r)
+            want = np.empty(n)
+            for s, e in enumerate(_extended_sets(S, part, nsub, overlap)):
+                if e.size == 0:
+                    continue
+                ze = np.linalg.solve(D[np.ix_(e, e)], r[e])
+                own = part[e] == s
+                want[e[own]] = ze[own]
+            assert np.allclose(z, want, rtol=1e-13, atol=1e-13), (nsub, overlap)
+    # overlap reaching every row: each subdomain solves the whole system
+    z = orc.Ras(A, 3, overlap=n, level=0).apply(r)
+    assert np.allclose(z, np.linalg.solve(D, r), rtol=1e-12, atol=1e-12)
+
+
+def test_ras_structure_and_invalid_inputs(orc):
+    d = synth.pressure_7pt(synth.Grid(6, 6, 4), 47)
+    n = d["n"]
+    A = orc.Mat.csr(d)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"]), shape=(n, n))
+    part = orc.contiguous_partition(n, 3)
+    R = orc.Ras(A, 3, part=part, overlap=2, level=1)
+    gidx, ptr, col, lu = R.structure()
+    sets = _extended_sets(S, part, 3, 2)
+    assert np.array_equal(gidx, np.concatenate(sets))
+    base = np.cumsum([0] + [len(e) for e in sets])
+    for s in range(3):                                   # columns stay inside their block
+        rows = slice(base[s], base[s + 1])
+        c = col[ptr[base[s]]:ptr[base[s + 1]]]
+        assert c.min() >= base[s] and c.max() < base[s + 1]
+        assert rows.stop - rows.start == len(sets[s])
+    assert orc.Ras(A, 3, part=np.full(n, 3, np.int32)).status == orc.INVALID
+    assert orc.Ras(A, 0).status == orc.INVALID
+    assert orc.Ras(A, 2, overlap=-1).status == orc.INVALID
+
+
+def test_ras_gmres_converges_and_overlap_helps(orc):
+    d = synth.pressure_7pt(synth.Grid(12, 12, 12), 48)
+    A = orc.Mat.csr(d)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"]))
+    b = S @ synth.x_true(d["n"], 48)
+    its = {}
+    for overlap in (0, 2):
+        for level in (0, 1):
+            M = orc.PC(A, "ras", ras=dict(nsub=8, overlap=overlap, level=level))
+            x, info, _ = orc.gmres(A, M, b, restart=30, rtol=1e-10)
+            assert info["status"] == 0
+            assert np.linalg.norm(b - S @ x) <= 1e-10 * np.linalg.norm(b) * 1.0001
+            its[overlap, level] = info["iters"]
+    assert its[2, 0] < its[0, 0] and its[2, 1] < its[0, 1]
