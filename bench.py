@@ -61,6 +61,10 @@ WORKLOADS = {
                                          precond="cpr_learned", prec="mixed"),
     "cg_ilu0_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="cg", precond="ilu0",
                                prec="fp64"),
+    # restricted additive Schwarz (Sec. 4.1) with the paper's defaults (Fig. 31): one layer of
+    # overlap, ILU(1) local solver; 8 x 8 x 4 boxes of 16^3 cells
+    "gmres_ras_ilu1_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="gmres", precond="ras",
+                                      prec="fp64", ras=dict(parts=(8, 8, 4), overlap=1, level=1)),
     # the paper's production pairing (Examples 2 and 4): BiCGSTAB + CPR-FPF (Alg. 7)
     "cpr_fpf_bicgstab_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="bicgstab",
                                              precond="cpr", prec="mixed", form="fpf"),
@@ -137,7 +141,9 @@ def net_flops(grid):
     return f + 2 * 16 * nx * ny * nz
 
 
-def kernel_model(w, A_host):
+def kernel_model(w, A_host, ras_sizes=None):
+    """Algorithmic bytes per launch of each kernel class.  For RAS the sweeps
+    run over the stacked extended subdomains (ras_sizes = rows, entries)."""
     vb = 4 if w["prec"] == "mixed" else 8
     if w["kind"] in ("bsr", "bsr_learned"):
         nb, nnzb = A_host["nb"], A_host["bcol"].size
@@ -147,8 +153,16 @@ def kernel_model(w, A_host):
         return mod, 3 * nb
     n, nnz = A_host["n"], A_host["col"].size
     mod = {"spmv": 12 * nnz + 4 * (n + 1) + 16 * n}
-    mod.update(scalar_ilu_bytes(n, nnz, vb))
+    mod.update(scalar_ilu_bytes(*(ras_sizes or (n, nnz)), vb))
     return mod, n
+
+
+def ras_kwargs(w):
+    """Precond arguments of a RAS workload: box subdomains of the grid."""
+    import paper_1701_05913_gb300 as rs
+    r = w["ras"]
+    return dict(nparts=int(np.prod(r["parts"])), part=rs.box_partition(w["grid"], r["parts"]),
+                overlap=r["overlap"], level=r["level"])
 
 
 def executed_launches(w, infos):
@@ -304,6 +318,9 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
         M = oracle.PC(A, "cpr", mixed=mixed, pstage=_oracle_net_stage(params, scale, w["grid"], A_host["logk"]))
     elif w["precond"] == "cpr_learned":
         M = oracle.PC(A, "cpr", mixed=mixed)      # block system: ILU(0) pressure stage in the oracle
+    elif w["precond"] == "ras":
+        k = ras_kwargs(w)
+        M = oracle.PC(A, "ras", ras=dict(nsub=k["nparts"], part=k["part"], overlap=k["overlap"], level=k["level"]))
     else:
         M = oracle.PC(A, w["precond"], mixed=mixed, form=w.get("form", "pf"))
     setup = time.perf_counter() - t0
@@ -413,6 +430,8 @@ class Case:
         kw = dict(form=w["form"]) if "form" in w else {}
         if w["precond"] == "cpr_learned":
             kw.update(net=net, log_perm=A_host["logk"], grid=w["grid"])
+        if w["precond"] == "ras":
+            kw.update(ras_kwargs(w))
         self.M = rs.Precond(ctx, self.A, w["precond"], prec=w["prec"], **kw)
         ctx.sync()
         self.setup_s = time.perf_counter() - t0
@@ -527,7 +546,7 @@ def run_gpu(args, w, rank, world, local):
 
     # roofline of the dominant kernel class, from the live profile
     hbm, bf16, peak_src = measured_peaks()
-    model, nunk = kernel_model(w, cases[0].A_host)
+    model, nunk = kernel_model(w, cases[0].A_host, cases[0].M.ras_info() if w["precond"] == "ras" else None)
     iters = [i["iters"] for i in infos]
     cb = cgs_bytes(nunk, iters)
     kern_ms = {k: v[0] for k, v in prof.items() if v[1] > 0}
@@ -580,7 +599,8 @@ def run_gpu(args, w, rank, world, local):
                        "precond": w["precond"] + ("-" + w["form"] if "form" in w else ""),
                        "precision": w["prec"], "rtol": RTOL, "seeds": [seeds[0], seeds[-1]],
                        "l2": "flushed between steps (512 MB write)",
-                       "parallelism": "replicas" if world > 1 else "1 gpu"},
+                       "parallelism": "replicas" if world > 1 else "1 gpu",
+                       **({"ras": dict(w["ras"], stacked_rows=cases[0].M.ras_info()[0])} if "ras" in w else {})},
             "iters": statistics.median(iters),
             "true_rel_res": max(i["true_rel_res"] for i in infos),
             "setup_s": statistics.median(c.setup_s for c in cases),

@@ -60,7 +60,9 @@ typedef enum {
     RS_PC_ILU0 = 1,       /* ILU(0) of a CSR matrix (Sec. 4.1, Eq. 3)        */
     RS_PC_BILU0 = 2,      /* block ILU(0) of a BSR matrix                     */
     RS_PC_CPR = 3,        /* two-stage CPR, pressure stage ILU(0) (Alg. 6)    */
-    RS_PC_CPR_LEARNED = 4 /* two-stage CPR, pressure stage = learned network  */
+    RS_PC_CPR_LEARNED = 4, /* two-stage CPR, pressure stage = learned network */
+    RS_PC_RAS = 5         /* restricted additive Schwarz, ILU(k) local solver
+                             (Sec. 4.1)                                        */
 } rs_pc_type;
 
 typedef enum {
@@ -85,6 +87,15 @@ typedef struct {
     const rs_net *net;    /* trained network (RS_PC_CPR_LEARNED)              */
     const double *log_perm; /* device pointer, nx*ny*nz log-permeabilities    */
     int32_t cpr_form;     /* rs_cpr_form (RS_PC_CPR, RS_PC_CPR_LEARNED); 0 = PF */
+    /* RS_PC_RAS (Sec. 4.1, Figs. 30-31).  A zeroed field takes the value
+     * in brackets. */
+    int32_t ras_nparts;   /* subdomains, >= 1 [1]                               */
+    int32_t ras_overlap;  /* layers of the graph of A added to each, >= 0 [0]   */
+    int32_t ilu_level;    /* k of the local ILU(k), 0..8 [0]                    */
+    const int32_t *ras_part; /* host array: subdomain of each (block) row, in
+                                [0, ras_nparts); NULL = contiguous ranges of
+                                rows, row i in floor(i nparts / n), like the
+                                paper's row distribution (Sec. 2.1, Eq. 1) */
 } rs_pc_opts;
 
 typedef struct {
@@ -181,6 +192,9 @@ int rs_mat_amxpby(double a, const rs_mat *A, const rs_vec *x, double b, rs_vec *
 /* ---- preconditioners (Sec. 3 Fig. 29, Sec. 4) -------------------------- */
 
 /* Builds M for A.  RS_PC_ILU0 needs a CSR matrix; RS_PC_BILU0 a BSR matrix;
+ * RS_PC_RAS either (on a BSR matrix the subdomains hold block rows and the
+ * local solver is block ILU(k)), set by the opts->ras_* fields and
+ * opts->ilu_level (RS_ERR_INVALID_ARG when out of range);
  * RS_PC_CPR a BSR matrix (quasi-IMPES pressure restriction, ILU(0) of the
  * decoupled pressure matrix, block ILU(0) of A) or a CSR matrix (pressure
  * stage on A itself, second stage ILU(0)); opts->cpr_form picks the order
@@ -204,6 +218,17 @@ int rs_precond_get_bilu(const rs_pc *M, double *lu_host, double *dinv_host);
 int rs_precond_get_cpr(const rs_pc *M, double *w_host, double *app_host);
 /* Row of the last zero pivot met by setup, or -1. */
 int32_t rs_precond_bad_row(const rs_pc *M);
+/* RS_PC_RAS: the extended subdomains are stacked, subdomain after
+ * subdomain, into one block-diagonal matrix (rows of a subdomain in
+ * ascending global order).  *next = its (block) rows, *nnz = its stored
+ * (block) entries: A's entries inside each extended set plus the ILU(k)
+ * fill. */
+int rs_precond_ras_info(const rs_pc *M, int32_t *next, int64_t *nnz);
+/* RS_PC_RAS: that matrix to host memory: gidx[next] = global (block) row of
+ * each stacked row; ptr[next+1], col[nnz] its pattern (stacked numbering);
+ * lu[nnz*bs*bs] the FP64 factor in that pattern (strict lower part of L,
+ * then U with its diagonal).  Any pointer may be NULL. */
+int rs_precond_get_ras(const rs_pc *M, int32_t *gidx, int32_t *ptr, int32_t *col, double *lu);
 /* Critical-path length of the triangular sweeps of the full-system factor
  * (ILU(0), block ILU(0), or the second stage of CPR): the number of segment
  * levels of the L and of the U sweep, where a segment is a run of at most 32

@@ -24,11 +24,22 @@ OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_BAD_PATTERN, ERR_ZERO_PIVOT, ERR_BREAKDOWN = -1, -2, -3, -4
 ERR_DEVICE_TIMEOUT, ERR_CUDA, ERR_OOM, ERR_SIZE_MISMATCH = -5, -6, -7, -8
 MEM_HOST, MEM_DEVICE = 0, 1
-PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CPR_LEARNED = 0, 1, 2, 3, 4
+PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CPR_LEARNED, PC_RAS = 0, 1, 2, 3, 4, 5
 FP64, MIXED = 0, 1
 
 _PC_KIND = {"none": PC_NONE, "ilu0": PC_ILU0, "bilu0": PC_BILU0, "cpr": PC_CPR,
-            "cpr_learned": PC_CPR_LEARNED}
+            "cpr_learned": PC_CPR_LEARNED, "ras": PC_RAS}
+
+
+def box_partition(grid, parts):
+    """Subdomain of every cell of an nx x ny x nz grid (x fastest) cut into
+    px x py x pz boxes of near-equal size: the row partition that gives
+    restricted additive Schwarz compact subdomains."""
+    (nx, ny, nz), (px, py, pz) = grid, parts
+    bx = np.arange(nx) * px // nx
+    by = np.arange(ny) * py // ny
+    bz = np.arange(nz) * pz // nz
+    return ((bz[:, None, None] * py + by[None, :, None]) * px + bx[None, None, :]).reshape(-1).astype(np.int32)
 
 _i32p = C.POINTER(C.c_int32)
 _f64p = C.POINTER(C.c_double)
@@ -47,7 +58,9 @@ class SolveInfo(C.Structure):
 
 class PcOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("net", _vp), ("log_perm", _vp), ("cpr_form", C.c_int32)]
+                ("net", _vp), ("log_perm", _vp), ("cpr_form", C.c_int32),
+                ("ras_nparts", C.c_int32), ("ras_overlap", C.c_int32), ("ilu_level", C.c_int32),
+                ("ras_part", _vp)]
 
 
 CPR_FORMS = ("pf", "fp", "fpf", "ffpf")   # rs_cpr_form: Algs. 6, 5, 7, 8
@@ -89,6 +102,9 @@ SIGNATURES = [
     ("rs_precond_get_cpr", C.c_int, [_vp, _f64p, _f64p]),
     ("rs_precond_bad_row", C.c_int32, [_vp]),
     ("rs_precond_sweep_levels", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    ("rs_precond_ras_info", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    ("rs_precond_get_ras", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     _f64p]),
     ("rs_precond_destroy", C.c_int, [C.POINTER(_vp)]),
     ("rs_solve_gmres", C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_double, C.c_int32,
                                  C.POINTER(SolveInfo)]),
@@ -291,7 +307,8 @@ class Precond:
     """rs_precond_setup / apply / destroy."""
 
     def __init__(self, ctx: Context, A: Mat, kind: str = "ilu0", prec: str = "fp64",
-                 net=None, log_perm=None, grid=None, form: str = "pf"):
+                 net=None, log_perm=None, grid=None, form: str = "pf", nparts: int = 1, part=None,
+                 overlap: int = 0, level: int = 0):
         self.ctx, self.A, self.kind = ctx, A, kind
         opts = PcOpts()
         opts.prec = MIXED if prec == "mixed" else FP64
@@ -303,6 +320,12 @@ class Precond:
             self._keep += [net, lp]
             opts.log_perm = lp.data_ptr()
             opts.nx, opts.ny, opts.nz = grid
+        # restricted additive Schwarz: subdomains, overlap layers, ILU(k) level
+        opts.ras_nparts, opts.ras_overlap, opts.ilu_level = nparts, overlap, level
+        if part is not None:
+            part = np.ascontiguousarray(part, dtype=np.int32)
+            self._keep.append(part)
+            opts.ras_part = part.ctypes.data
         self.h = _vp()
         self.status = lib().rs_precond_setup(ctx.h, A.h, _PC_KIND[kind], C.byref(opts), C.byref(self.h))
         self.bad_row = lib().rs_precond_bad_row(self.h) if self.h else -1
@@ -332,6 +355,26 @@ class Precond:
         _check(lib().rs_precond_get_cpr(self.h, w.ctypes.data_as(_f64p), app.ctypes.data_as(_f64p)),
                "rs_precond_get_cpr")
         return w, app
+
+    def ras_info(self):
+        """RAS: (stacked rows, stored entries) of the extended subdomains."""
+        ne, nz = C.c_int32(), C.c_int64()
+        _check(lib().rs_precond_ras_info(self.h, C.byref(ne), C.byref(nz)), "rs_precond_ras_info")
+        return ne.value, nz.value
+
+    def ras_structure(self):
+        """RAS: (gidx, ptr, col, lu) of the stacked extended subdomains."""
+        ne, nz = C.c_int32(), C.c_int64()
+        _check(lib().rs_precond_ras_info(self.h, C.byref(ne), C.byref(nz)), "rs_precond_ras_info")
+        bs = self.A.bs
+        gidx = np.empty(ne.value, np.int32)
+        ptr = np.empty(ne.value + 1, np.int32)
+        col = np.empty(nz.value, np.int32)
+        lu = np.empty(nz.value * bs * bs)
+        i32 = C.POINTER(C.c_int32)
+        _check(lib().rs_precond_get_ras(self.h, gidx.ctypes.data_as(i32), ptr.ctypes.data_as(i32),
+                                        col.ctypes.data_as(i32), lu.ctypes.data_as(_f64p)), "rs_precond_get_ras")
+        return gidx, ptr, col, lu
 
     def sweep_levels(self):
         """(L levels, U levels) of the full-system factor's triangular sweeps."""

@@ -170,6 +170,25 @@ struct IluFactor {
     void *zwork = nullptr;   // [nrows*bs] values of the U sweep
 };
 
+// Restricted additive Schwarz (rs_ras.cu): the extended subdomains stacked
+// into one block-diagonal matrix with its ILU(level) factor.
+#define RS_RAS_MAX_LEVEL 8
+struct RasData {
+    rs_ctx *ctx = nullptr;
+    int bs = 1, nrows = 0;       // block size, block rows of A
+    int next = 0;                // block rows of the stacked matrix
+    int64_t nnz = 0;             // its stored blocks
+    int nparts = 0, overlap = 0, level = 0;
+    int *ptr = nullptr, *col = nullptr;   // stacked pattern (device)
+    int *src = nullptr;          // [nnz] block of A behind each entry, -1 at fill
+    int *gidx = nullptr;         // [next] global block row of each stacked row
+    int *own = nullptr;          // [nrows] stacked row that owns each block row
+    double *val = nullptr;       // [nnz*bs*bs] stacked values
+    double *rhat = nullptr, *zhat = nullptr;   // [next*bs] work vectors
+    std::vector<int> h_gidx;
+    IluFactor *f = nullptr;
+};
+
 struct rs_pc {
     rs_ctx *ctx;
     int type;
@@ -189,6 +208,7 @@ struct rs_pc {
     int nx, ny, nz;
     int bad_row;
     int form;                // rs_cpr_form: order of the CPR stages
+    RasData *ras;            // RS_PC_RAS
 };
 
 // ---------------------------------------------------------------------------
@@ -218,6 +238,10 @@ int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row);
 int rs_ilu_apply(IluFactor *f, const double *r, double *z, const double *scale_dev,
                  const int *skip);
 void rs_ilu_destroy(IluFactor *f);
+int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part, int overlap, int level, int fp32,
+                  RasData **out, int *bad_row);
+int rs_ras_apply(RasData *R, const double *r, double *z, const int *skip);
+void rs_ras_destroy(RasData *R);
 
 // CPR / learned pressure stage
 int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip);

@@ -113,6 +113,8 @@ int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip)
         return rs_ilu_apply(M->ilu, r, z, nullptr, skip);
     case RS_PC_BILU0:
         return rs_ilu_apply(M->bilu, r, z, nullptr, skip);
+    case RS_PC_RAS:
+        return rs_ras_apply(M->ras, r, z, skip);
     case RS_PC_CPR:
     case RS_PC_CPR_LEARNED: {
         // Algs. 5-8: the first stage maps f to z; every later stage forms
@@ -139,6 +141,7 @@ static void pc_free(rs_pc *M)
     rs_ctx *ctx = M->ctx;
     if (M->ilu && M->ilu != M->bilu) rs_ilu_destroy(M->ilu);
     if (M->bilu) rs_ilu_destroy(M->bilu);
+    if (M->ras) rs_ras_destroy(M->ras);
     rs_free(ctx, M->app_val);
     rs_free(ctx, M->w);
     rs_free(ctx, M->rp);
@@ -179,6 +182,12 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         st = rs_ilu_create(ctx, A->bs, A->nrows, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
         if (!st) st = rs_ilu_factor(M->bilu, A->val, &bad);
         break;
+    case RS_PC_RAS: {
+        const int nparts = opts && opts->ras_nparts ? opts->ras_nparts : 1;
+        st = rs_ras_create(ctx, A, nparts, opts ? opts->ras_part : nullptr, opts ? opts->ras_overlap : 0,
+                           opts ? opts->ilu_level : 0, fp32, &M->ras, &bad);
+        break;
+    }
     case RS_PC_CPR:
     case RS_PC_CPR_LEARNED: {
         const int nb = A->nrows, bs = A->bs;
@@ -283,11 +292,37 @@ extern "C" int32_t rs_precond_bad_row(const rs_pc *M) { return M ? M->bad_row : 
 extern "C" int rs_precond_sweep_levels(const rs_pc *M, int32_t *levels_l, int32_t *levels_u)
 {
     if (!M || !levels_l || !levels_u) return RS_ERR_INVALID_ARG;
-    // the full-system factor: ILU(0) alone, or the second stage of CPR
-    const IluFactor *f = M->bilu ? M->bilu : M->ilu;
+    // the full-system factor: ILU(0) alone, the stacked RAS factor, or the
+    // second stage of CPR
+    const IluFactor *f = M->ras ? M->ras->f : M->bilu ? M->bilu : M->ilu;
     if (!f) return RS_ERR_INVALID_ARG;
     *levels_l = f->SL.nlevels;
     *levels_u = f->SU.nlevels;
+    return RS_OK;
+}
+
+extern "C" int rs_precond_ras_info(const rs_pc *M, int32_t *next, int64_t *nnz)
+{
+    if (!M || !M->ras || !next || !nnz) return RS_ERR_INVALID_ARG;
+    *next = M->ras->next;
+    *nnz = M->ras->nnz;
+    return RS_OK;
+}
+
+extern "C" int rs_precond_get_ras(const rs_pc *M, int32_t *gidx, int32_t *ptr, int32_t *col, double *lu)
+{
+    if (!M || !M->ras) return RS_ERR_INVALID_ARG;
+    const RasData *R = M->ras;
+    cudaStream_t sm = M->ctx->stream;
+    const size_t b2 = (size_t)R->bs * R->bs;
+    if (gidx && R->next > 0)
+        RS_CUDA_TRY(cudaMemcpyAsync(gidx, R->gidx, sizeof(int) * R->next, cudaMemcpyDeviceToHost, sm));
+    if (ptr) RS_CUDA_TRY(cudaMemcpyAsync(ptr, R->ptr, sizeof(int) * (R->next + 1), cudaMemcpyDeviceToHost, sm));
+    if (col && R->nnz > 0)
+        RS_CUDA_TRY(cudaMemcpyAsync(col, R->col, sizeof(int) * R->nnz, cudaMemcpyDeviceToHost, sm));
+    if (lu && R->nnz > 0)
+        RS_CUDA_TRY(cudaMemcpyAsync(lu, R->f->lu, sizeof(double) * b2 * R->nnz, cudaMemcpyDeviceToHost, sm));
+    RS_CUDA_TRY(cudaStreamSynchronize(sm));
     return RS_OK;
 }
 
