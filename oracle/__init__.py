@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, NOT_CONVERGED, INVALID, ZERO_PIVOT, BREAKDOWN = 0, 1, -1, -3, -4
-PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CALLBACK, PC_RAS = 0, 1, 2, 3, 4, 5
+PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CALLBACK, PC_RAS, PC_AMG = 0, 1, 2, 3, 4, 5, 6
 
 
 def build(force: bool = False) -> str:
@@ -72,7 +72,7 @@ class _PC(C.Structure):
                 ("A", C.POINTER(_Mat)), ("w", _f64p),
                 ("pstage", APPLY_FN), ("pstage_user", C.c_void_p),
                 ("fn", APPLY_FN), ("user", C.c_void_p), ("form", C.c_int32),
-                ("ras", C.c_void_p)]
+                ("ras", C.c_void_p), ("amg", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -115,6 +115,15 @@ def _declare(L):
     L.or_ras_sizes.argtypes = [C.c_void_p, _i32p, C.POINTER(C.c_int64)]
     L.or_ras_export.argtypes = [C.c_void_p, _i32p, _i32p, _i32p, _f64p]
     L.free.argtypes = [C.c_void_p]
+    L.or_amg_setup.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, C.c_int32, C.c_int32, C.c_int32,
+                               C.POINTER(C.c_void_p)]
+    L.or_amg_free.argtypes = [C.c_void_p]
+    L.or_amg_apply.argtypes = [C.c_void_p, _f64p, _f64p]
+    L.or_amg_nlevels.argtypes = [C.c_void_p]
+    L.or_amg_nlevels.restype = C.c_int32
+    L.or_amg_level_sizes.argtypes = [C.c_void_p, C.c_int32, _i32p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.or_amg_level.argtypes = [C.c_void_p, C.c_int32, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p]
+    L.or_amg_cidx.argtypes = [C.c_void_p, C.c_int32, _i32p]
     L.or_orthogonalise.argtypes = [C.c_int64, C.c_int32, _f64p, _f64p, _f64p, C.c_int32]
     L.or_gmres.argtypes = [mp, C.POINTER(_PC), _f64p, _f64p, C.c_int32, C.c_double, C.c_int32,
                            C.c_int32, C.c_int32, C.c_int32, _f64p, C.c_int32, C.POINTER(Info)]
@@ -354,6 +363,57 @@ class Ras:
             pass
 
 
+class Amg:
+    """Algebraic multigrid V-cycle (Algs. 3-4): classical strength (theta),
+    Ruge-Stueben first-pass coarsening, direct interpolation, Galerkin coarse
+    matrices, nu l1-Jacobi sweeps before and after, dense coarsest solve."""
+
+    def __init__(self, A: Mat, theta=0.5, max_levels=16, max_coarse=256, nu=2):
+        assert A.bs == 1
+        self.A = A
+        h = C.c_void_p()
+        self.status = lib().or_amg_setup(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
+                                         _p(A.val, C.c_double), theta, max_levels, max_coarse, nu, C.byref(h))
+        self.h = h
+
+    def apply(self, r):
+        r = _f64(r)
+        z = np.empty_like(r)
+        lib().or_amg_apply(self.h, _p(r, C.c_double), _p(z, C.c_double))
+        return z
+
+    def cidx(self, l=0):
+        """Coarse index of every point of level l (-1 for F points)."""
+        n = self.levels()[l][0][0].size - 1
+        out = np.empty(n, np.int32)
+        lib().or_amg_cidx(self.h, l, _p(out, C.c_int32))
+        return out
+
+    def levels(self):
+        """[(A_l as (ptr, col, val), P_l as (ptr, col, val) or None)] per level."""
+        out = []
+        L = lib()
+        nl = L.or_amg_nlevels(self.h)
+        for l in range(nl):
+            n, na, np_ = C.c_int32(), C.c_int64(), C.c_int64()
+            L.or_amg_level_sizes(self.h, l, C.byref(n), C.byref(na), C.byref(np_))
+            a = (np.empty(n.value + 1, np.int32), np.empty(na.value, np.int32), np.empty(na.value))
+            p = (np.empty(n.value + 1, np.int32), np.empty(np_.value, np.int32), np.empty(np_.value)) \
+                if l + 1 < nl else None
+            L.or_amg_level(self.h, l, _p(a[0], C.c_int32), _p(a[1], C.c_int32), _p(a[2], C.c_double),
+                           _p(p[0], C.c_int32) if p else None, _p(p[1], C.c_int32) if p else None,
+                           _p(p[2], C.c_double) if p else None)
+            out.append((a, p))
+        return out
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().or_amg_free(self.h)
+        except Exception:
+            pass
+
+
 # ----------------------------------------------------------------------------
 # Preconditioners
 # ----------------------------------------------------------------------------
@@ -362,6 +422,7 @@ class PC:
 
     kind='ras': restricted additive Schwarz, `ras` = dict(nsub=, part=,
     overlap=, level=) as for Ras.
+    kind='amg': one AMG V-cycle, `amg` = keyword arguments of Amg.
 
     kind='cpr' on a BSR matrix: quasi-IMPES restriction, ILU(0) of App'
     (or `pstage`, a callable rp -> zp), prolongation, residual, block ILU(0).
@@ -375,7 +436,7 @@ class PC:
     FORMS = ("pf", "fp", "fpf", "ffpf")   # Algs. 6, 5, 7, 8
 
     def __init__(self, A: Mat, kind: str = "ilu0", mixed: bool = False, pstage=None, fn=None, form: str = "pf",
-                 ras=None):
+                 ras=None, amg=None):
         self.A = A
         self.kind = kind
         self._keep = []
@@ -421,6 +482,11 @@ class PC:
             self.status, self.bad = self.ras.status, self.ras.bad
             s.ras = self.ras.h
             s.type = PC_RAS
+        elif kind == "amg":
+            self.amg = Amg(A, **(amg or {}))
+            self.status = self.amg.status
+            s.amg = self.amg.h
+            s.type = PC_AMG
         else:
             raise ValueError(kind)
         self.s = s

@@ -645,11 +645,485 @@ void or_ras_export(const or_ras *R, int32_t *gidx, int32_t *ptr, int32_t *col, d
 }
 
 /* ------------------------------------------------------------------------ */
+/* Algebraic multigrid (Sec. 4.2: Alg. 3 setup, Alg. 4 V-cycle, Eq. 4).      */
+/* Setup of level l, in Alg. 3's order:                                      */
+/*  1. strength: j strongly influences i (j in S_i) when j != i and          */
+/*     -a_ij >= theta max_{k != i} (-a_ik) (none when that max is <= 0);      */
+/*  2. coarse points by the Ruge-Stueben first pass: lambda_i = number of    */
+/*     points that i strongly influences; repeatedly the undecided point of  */
+/*     largest lambda (ties: lowest index) becomes C, the undecided points   */
+/*     that it strongly influences become F, lambda_k + 1 for the undecided  */
+/*     k in S_j of each new F point j and lambda_k - 1 for the undecided k   */
+/*     in S_i of the new C point i; points with neither strong connections   */
+/*     nor points depending on them are F from the start;                    */
+/*  3. direct interpolation: C points copy their coarse value; an F point i  */
+/*     takes w_ik = -alpha_i a_ik / a_ii over its strong C neighbours k with */
+/*     a_ik < 0 and -beta_i a_ik / a_ii over those with a_ik > 0, where      */
+/*     alpha_i (beta_i) is the sum of all negative (positive) off-diagonal   */
+/*     a_ij over the sum of those of its strong C neighbours; without a      */
+/*     positive strong C coupling the positive couplings join a_ii;          */
+/*  4. R = P^T;  5. A_{l+1} = R A_l P (Eq. 4);                               */
+/*  6. smoother: l1-Jacobi, x <- x + (b - A x) / d with d_i = sum_j |a_ij|.  */
+/* Levels stop at <= max_coarse rows, at max_levels, or when coarsening      */
+/* stalls; the coarsest system is solved with a dense inverse.               */
+/* V-cycle from x = 0 (Alg. 4): nu smoothing sweeps, residual, restriction,  */
+/* the next level, prolongation and correction, nu smoothing sweeps.         */
+/* ------------------------------------------------------------------------ */
+#define OR_AMG_MAXLEV 16
+
+typedef struct {
+    int32_t n, m;            /* rows, columns */
+    int32_t *ptr, *col;
+    double *val;
+} or_csr;
+
+typedef struct {
+    int32_t nlev, nu;
+    or_csr A[OR_AMG_MAXLEV], P[OR_AMG_MAXLEV], R[OR_AMG_MAXLEV];
+    double *d[OR_AMG_MAXLEV];    /* l1-Jacobi diagonal */
+    int32_t *cidx[OR_AMG_MAXLEV]; /* coarse index of each point of level l, -1 for F */
+    double *cinv;                /* dense inverse of the coarsest matrix, row-major */
+} or_amg;
+
+static void csr_free(or_csr *M)
+{
+    free(M->ptr);
+    free(M->col);
+    free(M->val);
+    memset(M, 0, sizeof(*M));
+}
+
+/* C = A B (both CSR, B with A.m rows), rows accumulated in a dense row of
+ * B.m entries, columns then sorted. */
+static void csr_mul(const or_csr *A, const or_csr *B, or_csr *C)
+{
+    double *acc = (double *)calloc((size_t)(B->m > 0 ? B->m : 1), sizeof(double));
+    int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * (size_t)(B->m > 0 ? B->m : 1));
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * (size_t)(B->m > 0 ? B->m : 1));
+    for (int32_t c = 0; c < B->m; ++c) mark[c] = -1;
+    int64_t cap = 16, len = 0;
+    C->n = A->n;
+    C->m = B->m;
+    C->ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(A->n + 1));
+    C->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    C->val = (double *)malloc(sizeof(double) * (size_t)cap);
+    C->ptr[0] = 0;
+    for (int32_t i = 0; i < A->n; ++i) {
+        int32_t nc = 0;
+        for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
+            const int32_t j = A->col[p];
+            for (int32_t q = B->ptr[j]; q < B->ptr[j + 1]; ++q) {
+                const int32_t c = B->col[q];
+                if (mark[c] != i) {
+                    mark[c] = i;
+                    acc[c] = 0.0;
+                    cols[nc++] = c;
+                }
+                acc[c] = acc[c] + A->val[p] * B->val[q];
+            }
+        }
+        /* insertion sort of the row's columns (rows are short) */
+        for (int32_t a = 1; a < nc; ++a) {
+            const int32_t v = cols[a];
+            int32_t b = a - 1;
+            while (b >= 0 && cols[b] > v) { cols[b + 1] = cols[b]; --b; }
+            cols[b + 1] = v;
+        }
+        while (len + nc > cap) {
+            cap *= 2;
+            C->col = (int32_t *)realloc(C->col, sizeof(int32_t) * (size_t)cap);
+            C->val = (double *)realloc(C->val, sizeof(double) * (size_t)cap);
+        }
+        for (int32_t a = 0; a < nc; ++a) {
+            C->col[len] = cols[a];
+            C->val[len] = acc[cols[a]];
+            ++len;
+        }
+        C->ptr[i + 1] = (int32_t)len;
+    }
+    free(acc);
+    free(mark);
+    free(cols);
+}
+
+static void csr_transpose(const or_csr *A, or_csr *T)
+{
+    T->n = A->m;
+    T->m = A->n;
+    const int64_t nnz = A->ptr[A->n];
+    T->ptr = (int32_t *)calloc((size_t)(A->m + 1), sizeof(int32_t));
+    T->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    T->val = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    for (int64_t p = 0; p < nnz; ++p) T->ptr[A->col[p] + 1]++;
+    for (int32_t c = 0; c < A->m; ++c) T->ptr[c + 1] += T->ptr[c];
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(A->m > 0 ? A->m : 1));
+    memcpy(fill, T->ptr, sizeof(int32_t) * (size_t)A->m);
+    for (int32_t i = 0; i < A->n; ++i)          /* rows in order: columns of T come out sorted */
+        for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
+            const int32_t q = fill[A->col[p]]++;
+            T->col[q] = i;
+            T->val[q] = A->val[p];
+        }
+    free(fill);
+}
+
+/* binary max-heap of (lambda, -index) with stale entries skipped on pop */
+typedef struct { int32_t lam, idx; } or_hent;
+static int hent_less(or_hent a, or_hent b) { return a.lam < b.lam || (a.lam == b.lam && a.idx > b.idx); }
+static void heap_push(or_hent **h, int64_t *len, int64_t *cap, or_hent e)
+{
+    if (*len == *cap) {
+        *cap *= 2;
+        *h = (or_hent *)realloc(*h, sizeof(or_hent) * (size_t)*cap);
+    }
+    int64_t i = (*len)++;
+    while (i > 0) {
+        const int64_t p = (i - 1) / 2;
+        if (!hent_less((*h)[p], e)) break;
+        (*h)[i] = (*h)[p];
+        i = p;
+    }
+    (*h)[i] = e;
+}
+static or_hent heap_pop(or_hent *h, int64_t *len)
+{
+    const or_hent top = h[0];
+    const or_hent last = h[--(*len)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= *len) break;
+        if (c + 1 < *len && hent_less(h[c], h[c + 1])) ++c;
+        if (!hent_less(last, h[c])) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*len > 0) h[i] = last;
+    return top;
+}
+
+/* one level of Alg. 3: P (n x nc) from A and the coarse index of every
+ * point (-1 for F, into cidx_out[n]); returns nc */
+static int32_t amg_coarsen(const or_csr *A, double theta, or_csr *P, int32_t *cidx_out)
+{
+    const int32_t n = A->n;
+    /* 1. strength */
+    int32_t *sp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t *sc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(A->ptr[n] > 0 ? A->ptr[n] : 1));
+    sp[0] = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        double mx = 0.0;
+        for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p)
+            if (A->col[p] != i && -A->val[p] > mx) mx = -A->val[p];
+        int32_t k = sp[i];
+        if (mx > 0.0)
+            for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p)
+                if (A->col[p] != i && -A->val[p] >= theta * mx) sc[k++] = A->col[p];
+        sp[i + 1] = k;
+    }
+    /* S^T: the points each point strongly influences */
+    or_csr S = {n, n, sp, sc, NULL}, ST;
+    S.val = (double *)calloc((size_t)(sp[n] > 0 ? sp[n] : 1), sizeof(double));
+    csr_transpose(&S, &ST);
+    /* 2. Ruge-Stueben first pass */
+    enum { U = 0, CPT = 1, FPT = 2 };
+    int32_t *lam = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    char *st = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t hcap = n > 0 ? 2 * (int64_t)n : 2, hlen = 0;
+    or_hent *heap = (or_hent *)malloc(sizeof(or_hent) * (size_t)hcap);
+    for (int32_t i = 0; i < n; ++i) {
+        lam[i] = ST.ptr[i + 1] - ST.ptr[i];
+        if (lam[i] == 0 && sp[i + 1] == sp[i]) st[i] = FPT;
+        else heap_push(&heap, &hlen, &hcap, (or_hent){lam[i], i});
+    }
+    while (hlen > 0) {
+        const or_hent e = heap_pop(heap, &hlen);
+        const int32_t i = e.idx;
+        if (st[i] != U || e.lam != lam[i]) continue;
+        st[i] = CPT;
+        for (int32_t q = ST.ptr[i]; q < ST.ptr[i + 1]; ++q) {
+            const int32_t j = ST.col[q];
+            if (st[j] != U) continue;
+            st[j] = FPT;
+            for (int32_t r = sp[j]; r < sp[j + 1]; ++r) {
+                const int32_t k = sc[r];
+                if (st[k] == U) {
+                    lam[k] += 1;
+                    heap_push(&heap, &hlen, &hcap, (or_hent){lam[k], k});
+                }
+            }
+        }
+        for (int32_t r = sp[i]; r < sp[i + 1]; ++r) {
+            const int32_t k = sc[r];
+            if (st[k] == U) {
+                lam[k] -= 1;
+                heap_push(&heap, &hlen, &hcap, (or_hent){lam[k], k});
+            }
+        }
+    }
+    /* coarse numbering */
+    int32_t *cidx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t nc = 0;
+    for (int32_t i = 0; i < n; ++i) cidx[i] = st[i] == CPT ? nc++ : -1;
+    /* 3. direct interpolation */
+    P->n = n;
+    P->m = nc;
+    P->ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    P->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(sp[n] + n + 1));
+    P->val = (double *)malloc(sizeof(double) * (size_t)(sp[n] + n + 1));
+    int64_t len = 0;
+    P->ptr[0] = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (st[i] == CPT) {
+            P->col[len] = cidx[i];
+            P->val[len] = 1.0;
+            ++len;
+        } else {
+            double aii = 0.0, neg = 0.0, pos = 0.0, negc = 0.0, posc = 0.0;
+            for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
+                const double v = A->val[p];
+                if (A->col[p] == i) aii = v;
+                else if (v < 0.0) neg += v;
+                else pos += v;
+            }
+            for (int32_t r = sp[i]; r < sp[i + 1]; ++r) {
+                if (st[sc[r]] != CPT) continue;
+                /* the value a_ik of this strong C neighbour */
+                for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p)
+                    if (A->col[p] == sc[r]) {
+                        if (A->val[p] < 0.0) negc += A->val[p];
+                        else posc += A->val[p];
+                    }
+            }
+            double diag = aii, beta = 0.0;
+            if (posc == 0.0) diag += pos;
+            else beta = pos / posc;
+            const double alpha = negc != 0.0 ? neg / negc : 0.0;
+            /* strong C neighbours in ascending column order = ascending coarse index */
+            for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
+                const int32_t k = A->col[p];
+                if (k == i || st[k] != CPT) continue;
+                int strong = 0;
+                for (int32_t r = sp[i]; r < sp[i + 1]; ++r) strong |= sc[r] == k;
+                if (!strong) continue;
+                P->col[len] = cidx[k];
+                P->val[len] = -(A->val[p] < 0.0 ? alpha : beta) * A->val[p] / diag;
+                ++len;
+            }
+        }
+        P->ptr[i + 1] = (int32_t)len;
+    }
+    memcpy(cidx_out, cidx, sizeof(int32_t) * (size_t)n);
+    free(lam);
+    free(st);
+    free(heap);
+    free(cidx);
+    free(S.val);
+    csr_free(&ST);
+    free(sp);
+    free(sc);
+    return nc;
+}
+
+/* inverse of a dense n x n row-major matrix by Gauss-Jordan elimination with
+ * partial pivoting; returns 0 on a zero or non-finite pivot */
+static int dense_inverse(int32_t n, const double *a, double *inv)
+{
+    double *m = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n * n : 1));
+    memcpy(m, a, sizeof(double) * (size_t)n * n);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < n; ++j) inv[(size_t)i * n + j] = i == j ? 1.0 : 0.0;
+    int ok = 1;
+    for (int32_t c = 0; c < n && ok; ++c) {
+        int32_t p = c;
+        for (int32_t r = c + 1; r < n; ++r)
+            if (fabs(m[(size_t)r * n + c]) > fabs(m[(size_t)p * n + c])) p = r;
+        const double piv = m[(size_t)p * n + c];
+        if (!(piv != 0.0) || !isfinite(piv)) { ok = 0; break; }
+        if (p != c)
+            for (int32_t j = 0; j < n; ++j) {
+                double t = m[(size_t)c * n + j]; m[(size_t)c * n + j] = m[(size_t)p * n + j]; m[(size_t)p * n + j] = t;
+                t = inv[(size_t)c * n + j]; inv[(size_t)c * n + j] = inv[(size_t)p * n + j]; inv[(size_t)p * n + j] = t;
+            }
+        for (int32_t j = 0; j < n; ++j) {
+            m[(size_t)c * n + j] /= piv;
+            inv[(size_t)c * n + j] /= piv;
+        }
+        for (int32_t r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = m[(size_t)r * n + c];
+            if (f == 0.0) continue;
+            for (int32_t j = 0; j < n; ++j) {
+                m[(size_t)r * n + j] -= f * m[(size_t)c * n + j];
+                inv[(size_t)r * n + j] -= f * inv[(size_t)c * n + j];
+            }
+        }
+    }
+    free(m);
+    return ok;
+}
+
+void or_amg_free(or_amg *M)
+{
+    if (!M) return;
+    for (int32_t l = 0; l < M->nlev; ++l) {
+        csr_free(&M->A[l]);
+        csr_free(&M->P[l]);
+        csr_free(&M->R[l]);
+        free(M->d[l]);
+        free(M->cidx[l]);
+    }
+    free(M->cinv);
+    free(M);
+}
+
+int or_amg_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, double theta,
+                 int32_t max_levels, int32_t max_coarse, int32_t nu, or_amg **out)
+{
+    *out = NULL;
+    if (n < 1 || max_levels < 1 || max_levels > OR_AMG_MAXLEV || max_coarse < 1 || nu < 1 || !(theta >= 0.0))
+        return OR_INVALID;
+    or_amg *M = (or_amg *)calloc(1, sizeof(or_amg));
+    M->nu = nu;
+    or_csr *A0 = &M->A[0];
+    A0->n = A0->m = n;
+    A0->ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    A0->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ptr[n] > 0 ? ptr[n] : 1));
+    A0->val = (double *)malloc(sizeof(double) * (size_t)(ptr[n] > 0 ? ptr[n] : 1));
+    memcpy(A0->ptr, ptr, sizeof(int32_t) * (size_t)(n + 1));
+    memcpy(A0->col, col, sizeof(int32_t) * (size_t)ptr[n]);
+    memcpy(A0->val, val, sizeof(double) * (size_t)ptr[n]);
+    int32_t l = 0;
+    for (;;) {
+        const or_csr *A = &M->A[l];
+        M->d[l] = (double *)malloc(sizeof(double) * (size_t)A->n);
+        for (int32_t i = 0; i < A->n; ++i) {
+            double s = 0.0;
+            for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) s += fabs(A->val[p]);
+            M->d[l][i] = s;
+        }
+        if (A->n <= max_coarse || l + 1 >= max_levels) break;
+        or_csr P;
+        M->cidx[l] = (int32_t *)malloc(sizeof(int32_t) * (size_t)A->n);
+        const int32_t nc = amg_coarsen(A, theta, &P, M->cidx[l]);
+        if (nc == 0 || nc >= A->n) {
+            csr_free(&P);
+            break;
+        }
+        M->P[l] = P;
+        csr_transpose(&M->P[l], &M->R[l]);
+        or_csr AP;
+        csr_mul(A, &M->P[l], &AP);
+        csr_mul(&M->R[l], &AP, &M->A[l + 1]);
+        csr_free(&AP);
+        ++l;
+    }
+    M->nlev = l + 1;
+    /* dense inverse of the coarsest matrix */
+    const or_csr *C = &M->A[l];
+    double *dense = (double *)calloc((size_t)C->n * C->n, sizeof(double));
+    for (int32_t i = 0; i < C->n; ++i)
+        for (int32_t p = C->ptr[i]; p < C->ptr[i + 1]; ++p) dense[(size_t)i * C->n + C->col[p]] = C->val[p];
+    M->cinv = (double *)malloc(sizeof(double) * (size_t)C->n * C->n);
+    const int ok = dense_inverse(C->n, dense, M->cinv);
+    free(dense);
+    if (!ok) {
+        or_amg_free(M);
+        return OR_ZERO_PIVOT;
+    }
+    *out = M;
+    return OR_OK;
+}
+
+static void csr_mv(const or_csr *A, const double *x, double *y)
+{
+    for (int32_t i = 0; i < A->n; ++i) {
+        double s = 0.0;
+        for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) s += A->val[p] * x[A->col[p]];
+        y[i] = s;
+    }
+}
+
+/* x <- x + (b - A x) / d (Jacobi: every row reads the old x) */
+static void l1_jacobi(const or_csr *A, const double *d, const double *b, double *x, double *t)
+{
+    csr_mv(A, x, t);
+    for (int32_t i = 0; i < A->n; ++i) t[i] = b[i] - t[i];
+    for (int32_t i = 0; i < A->n; ++i) x[i] = x[i] + t[i] / d[i];
+}
+
+static void amg_vcycle(const or_amg *M, int32_t l, const double *b, double *x)
+{
+    const or_csr *A = &M->A[l];
+    const int32_t n = A->n;
+    if (l == M->nlev - 1) {
+        for (int32_t i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int32_t j = 0; j < n; ++j) s += M->cinv[(size_t)i * n + j] * b[j];
+            x[i] = s;
+        }
+        return;
+    }
+    double *t = (double *)malloc(sizeof(double) * (size_t)n);
+    const int32_t nc = M->A[l + 1].n;
+    double *bc = (double *)malloc(sizeof(double) * (size_t)nc);
+    double *xc = (double *)malloc(sizeof(double) * (size_t)nc);
+    /* pre-smoothing from x = 0: the first sweep is x = b / d */
+    for (int32_t i = 0; i < n; ++i) x[i] = b[i] / M->d[l][i];
+    for (int32_t s = 1; s < M->nu; ++s) l1_jacobi(A, M->d[l], b, x, t);
+    csr_mv(A, x, t);
+    for (int32_t i = 0; i < n; ++i) t[i] = b[i] - t[i];
+    csr_mv(&M->R[l], t, bc);
+    amg_vcycle(M, l + 1, bc, xc);
+    csr_mv(&M->P[l], xc, t);
+    for (int32_t i = 0; i < n; ++i) x[i] = x[i] + t[i];
+    for (int32_t s = 0; s < M->nu; ++s) l1_jacobi(A, M->d[l], b, x, t);
+    free(t);
+    free(bc);
+    free(xc);
+}
+
+void or_amg_apply(const or_amg *M, const double *r, double *z) { amg_vcycle(M, 0, r, z); }
+
+int32_t or_amg_nlevels(const or_amg *M) { return M->nlev; }
+
+/* sizes of level l: rows of A_l, entries of A_l, entries of P_l (0 on the coarsest) */
+void or_amg_level_sizes(const or_amg *M, int32_t l, int32_t *n, int64_t *nnz_a, int64_t *nnz_p)
+{
+    *n = M->A[l].n;
+    *nnz_a = M->A[l].ptr[M->A[l].n];
+    *nnz_p = l + 1 < M->nlev ? M->P[l].ptr[M->P[l].n] : 0;
+}
+
+/* coarse index of every point of level l (-1 for F); l below the coarsest */
+void or_amg_cidx(const or_amg *M, int32_t l, int32_t *cidx)
+{
+    memcpy(cidx, M->cidx[l], sizeof(int32_t) * (size_t)M->A[l].n);
+}
+
+/* copies of A_l and (if l is not the coarsest) P_l; any pointer may be NULL */
+void or_amg_level(const or_amg *M, int32_t l, int32_t *aptr, int32_t *acol, double *aval, int32_t *pptr,
+                  int32_t *pcol, double *pval)
+{
+    const or_csr *A = &M->A[l];
+    if (aptr) memcpy(aptr, A->ptr, sizeof(int32_t) * (size_t)(A->n + 1));
+    if (acol) memcpy(acol, A->col, sizeof(int32_t) * (size_t)A->ptr[A->n]);
+    if (aval) memcpy(aval, A->val, sizeof(double) * (size_t)A->ptr[A->n]);
+    if (l + 1 < M->nlev) {
+        const or_csr *P = &M->P[l];
+        if (pptr) memcpy(pptr, P->ptr, sizeof(int32_t) * (size_t)(P->n + 1));
+        if (pcol) memcpy(pcol, P->col, sizeof(int32_t) * (size_t)P->ptr[P->n]);
+        if (pval) memcpy(pval, P->val, sizeof(double) * (size_t)P->ptr[P->n]);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Preconditioner object (Sec. 3, Fig. 29: setup / solve / destroy).         */
 /* ------------------------------------------------------------------------ */
 typedef int (*or_apply_fn)(void *user, int64_t n, const double *r, double *z);
 
-enum { OR_PC_NONE = 0, OR_PC_ILU0 = 1, OR_PC_BILU0 = 2, OR_PC_CPR = 3, OR_PC_CALLBACK = 4, OR_PC_RAS = 5 };
+enum { OR_PC_NONE = 0, OR_PC_ILU0 = 1, OR_PC_BILU0 = 2, OR_PC_CPR = 3, OR_PC_CALLBACK = 4, OR_PC_RAS = 5,
+       OR_PC_AMG = 6 };
 
 typedef struct {
     int32_t type;
@@ -677,6 +1151,8 @@ typedef struct {
     int32_t form;
     /* restricted additive Schwarz (type RAS) */
     const or_ras *ras;
+    /* algebraic multigrid V-cycle (type AMG) */
+    const or_amg *amg;
 } or_pc;
 
 /* One stage of a CPR-like preconditioner on a right-hand side v:
@@ -727,6 +1203,9 @@ int or_pc_apply(const or_pc *M, int64_t n, const double *r, double *z)
         return M->fn(M->user, n, r, z);
     case OR_PC_RAS:
         or_ras_apply(M->ras, r, z);
+        return OR_OK;
+    case OR_PC_AMG:
+        or_amg_apply(M->amg, r, z);
         return OR_OK;
     case OR_PC_CPR: {
         /* CPR-like preconditioners, Algs. 5-8, each step in the printed

@@ -835,3 +835,162 @@ def test_ras_gmres_converges_and_overlap_helps(orc):
             assert np.linalg.norm(b - S @ x) <= 1e-10 * np.linalg.norm(b) * 1.0001
             its[overlap, level] = info["iters"]
     assert its[2, 0] < its[0, 0] and its[2, 1] < its[0, 1]
+
+
+# ----------------------------------------------------------------------------
+# Algebraic multigrid (Sec. 4.2, Algs. 3-4, Eq. 4)
+# ----------------------------------------------------------------------------
+def _csr_dense(t, m=None):
+    ptr, col, val = t
+    n = ptr.size - 1
+    return sp.csr_matrix((val, col, ptr), shape=(n, m if m is not None else n)).toarray()
+
+
+def test_amg_poisson1d_is_geometric_multigrid(orc):
+    # 1-D Poisson, 2^4 - 1 points: Ruge-Stueben picks every other point,
+    # direct interpolation is linear interpolation and the Galerkin matrix is
+    # (1/2) tridiag(-1, 2, -1): each level is the previous one halved
+    M = orc.Amg(orc.Mat.csr(csr_dict(poisson1d(15))), max_coarse=1)
+    assert M.status == 0
+    lv = M.levels()
+    assert [a[0].size - 1 for a, _ in lv] == [15, 7, 3, 1]
+    for l, (a, p) in enumerate(lv[:-1]):
+        n = a[0].size - 1
+        nc = (n - 1) // 2
+        Pd = _csr_dense(p, nc)
+        want = np.zeros((n, nc))
+        for k in range(nc):                       # coarse point k is fine point 2k + 1
+            want[2 * k + 1, k] = 1.0
+            want[2 * k, k] = want[2 * k + 2, k] = 0.5
+        assert np.array_equal(Pd, want)
+        Ac = _csr_dense(lv[l + 1][0])
+        assert np.allclose(Ac, 0.5 ** (l + 1) * poisson1d(nc).toarray(), rtol=0, atol=1e-15)
+
+
+def test_amg_anisotropy_gives_semicoarsening(orc):
+    # 2-D Laplacian with weak y couplings (eps = 0.1 < theta = 0.5): only x
+    # couplings are strong, so every x-line is coarsened alone, every other
+    # point (Ruge-Stueben's textbook semicoarsening)
+    nx, ny, eps = 9, 6, 0.1
+    Ax = poisson1d(nx)
+    Ay = poisson1d(ny)
+    A = (sp.kron(sp.eye(ny), Ax) + eps * sp.kron(Ay, sp.eye(nx))).tocsr()
+    M = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1)
+    a, p = M.levels()[0]
+    Pd = _csr_dense(p, 4 * ny)
+    C = [i for i in range(nx * ny) if (Pd[i] != 0).sum() == 1 and Pd[i].max() == 1.0]   # injected points
+    assert C == [y * nx + x for y in range(ny) for x in (1, 3, 5, 7)]
+
+
+def test_amg_galerkin_and_constant_interpolation(orc):
+    # A_{l+1} = P^T A_l P on every level (Eq. 4); on a zero-row-sum matrix
+    # direct interpolation reproduces constants: every row of P sums to 1
+    g = synth.Grid(7, 6, 5)
+    d = synth.pressure_7pt(g, 60, accum=0.0)
+    n = g.n
+    d["val"] = d["val"].copy()
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"]), shape=(n, n))
+    assert np.abs(S.sum(axis=1)).max() < 1e-12
+    # pin the singular matrix's coarsest level away from it: add 1e-3 to one diagonal entry
+    dd = np.nonzero(d["col"] == np.repeat(np.arange(n), np.diff(d["rowptr"])))[0]
+    d["val"][dd[0]] += 1e-3
+    M = orc.Amg(orc.Mat.csr(d), max_coarse=8)
+    assert M.status == 0
+    lv = M.levels()
+    assert len(lv) >= 3
+    for l, (a, p) in enumerate(lv[:-1]):
+        Ad = _csr_dense(a)
+        nc = lv[l + 1][0][0].size - 1
+        Pd = _csr_dense(p, nc)
+        assert np.allclose(_csr_dense(lv[l + 1][0]), Pd.T @ Ad @ Pd, rtol=0, atol=1e-12 * np.abs(Ad).max())
+        # rows of A_l that sum to zero (all but those the shift reaches) interpolate constants exactly
+        zero = np.abs(Ad.sum(axis=1)) <= 1e-12 * np.abs(Ad).max()
+        rows = zero & (Pd != 0).any(axis=1)
+        assert rows.sum() > (0.5 * Pd.shape[0] if l == 0 else 0)
+        assert np.allclose(Pd.sum(axis=1)[rows], 1.0, rtol=0, atol=1e-12)
+
+
+def test_amg_vcycle_is_symmetric_positive_definite(orc):
+    # pre- and post-smoothing by the same l1-Jacobi sweeps and R = P^T make
+    # the V-cycle a symmetric positive definite operator for SPD A
+    g = synth.Grid(6, 5, 4)
+    d = synth.pressure_7pt(g, 61)
+    M = orc.Amg(orc.Mat.csr(d), max_coarse=10)
+    assert len(M.levels()) >= 3
+    B = np.column_stack([M.apply(e) for e in np.eye(g.n)])
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+
+
+def test_amg_pcg_iterations_do_not_grow_with_the_grid(orc):
+    its = []
+    for m in (10, 20):
+        A = poisson3d_dirichlet(m, m, m)
+        d = csr_dict(A)
+        Ao = orc.Mat.csr(d)
+        b = A @ np.random.default_rng(62).standard_normal(m ** 3)
+        Mo = orc.PC(Ao, "amg", amg=dict(max_coarse=32))
+        x, info, _ = orc.cg(Ao, Mo, b, rtol=1e-8)
+        assert info["status"] == 0
+        assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b) * 1.0001
+        its.append(info["iters"])
+    assert its[1] <= its[0] + 3 and its[1] <= 20, its
+
+
+def test_amg_invalid_inputs(orc):
+    A = orc.Mat.csr(csr_dict(poisson1d(10)))
+    assert orc.Amg(A, max_levels=0).status == orc.INVALID
+    assert orc.Amg(A, nu=0).status == orc.INVALID
+    assert orc.Amg(A, theta=-1.0).status == orc.INVALID
+
+
+def _rs_first_pass_by_definition(A, theta):
+    """The Ruge-Stueben first pass from its definition, recomputing the
+    measure of every undecided point at every step instead of updating it:
+    lambda_i = |S_i^T n U| + 2 |S_i^T n F| (S_i = points strongly influencing
+    i); pick the largest lambda, lowest index on ties; the new C point's
+    undecided dependents become F.  Points with no strong connection in
+    either direction are F from the start."""
+    D = A.toarray()
+    n = D.shape[0]
+    S = np.zeros((n, n), dtype=bool)                  # S[i, j]: j strongly influences i
+    for i in range(n):
+        off = -np.delete(D[i], i)
+        mx = off.max() if n > 1 else 0.0
+        if mx > 0:
+            for j in range(n):
+                if j != i and -D[i, j] >= theta * mx:
+                    S[i, j] = True
+    U, Cp, Fp = 0, 1, 2
+    st = np.zeros(n, int)
+    for i in range(n):
+        if not S[i].any() and not S[:, i].any():
+            st[i] = Fp
+    while (st == U).any():
+        lam = np.array([(S[:, i] & (st == U)).sum() + 2 * (S[:, i] & (st == Fp)).sum() for i in range(n)])
+        lam[st != U] = -1
+        i = int(np.argmax(lam))                       # first maximum = lowest index
+        st[i] = Cp
+        for j in np.nonzero(S[:, i] & (st == U))[0]:
+            st[j] = Fp
+    return st == Cp
+
+
+def test_amg_coarsening_follows_the_first_pass_definition(orc):
+    rng = np.random.default_rng(63)
+    for trial in range(12):
+        n = 40
+        W = rng.random((n, n)) < 0.1                        # nonsymmetric strength: the measure's
+        D = np.where(W, -rng.random((n, n)), 0.0)           # decrements for the new C point matter
+        np.fill_diagonal(D, 0.0)
+        np.fill_diagonal(D, -D.sum(axis=1) + 0.1)
+        A = sp.csr_matrix(D)
+        M = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1)
+        assert M.status == 0
+        assert np.array_equal(M.cidx(0) >= 0, _rs_first_pass_by_definition(A, 0.5)), trial
+    # the isotropic 5-point Laplacian coarsens red-black
+    nx, ny = 8, 7
+    A = (sp.kron(sp.eye(ny), poisson1d(nx)) + sp.kron(poisson1d(ny), sp.eye(nx))).tocsr()
+    c = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1).cidx(0) >= 0
+    x, y = np.meshgrid(np.arange(nx), np.arange(ny))
+    assert np.array_equal(c, ((x + y) % 2 == 0).reshape(-1))
