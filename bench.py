@@ -61,6 +61,12 @@ WORKLOADS = {
                                          precond="cpr_learned", prec="mixed"),
     "cg_ilu0_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="cg", precond="ilu0",
                                prec="fp64"),
+    # algebraic multigrid (Sec. 4.2, Algs. 3-4): PCG with one V-cycle per iteration
+    "cg_amg_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="cg", precond="amg", prec="fp64",
+                              amg=dict()),
+    # the paper's CPR with an AMG pressure stage (Sec. 4.2.1, Alg. 6 with M_p = one V-cycle)
+    "cpr_amg_fgmres_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="fgmres",
+                                           precond="cpr", prec="mixed", pstage="amg", amg=dict()),
     # restricted additive Schwarz (Sec. 4.1) with the paper's defaults (Fig. 31): one layer of
     # overlap, ILU(1) local solver; 8 x 8 x 4 boxes of 16^3 cells
     "gmres_ras_ilu1_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="gmres", precond="ras",
@@ -165,7 +171,23 @@ def ras_kwargs(w):
                 overlap=r["overlap"], level=r["level"])
 
 
-def executed_launches(w, infos):
+def amg_vcycle_model(w, sizes):
+    """SpMV launches and algorithmic bytes of one V-cycle: on every level
+    above the coarsest, 2 nu residuals with A_l, one restriction, one
+    prolongation (bytes of an r x c operator with z entries: 12 z + 4 (r+1)
+    + 8 r + 8 c)."""
+    nu = w.get("amg", {}).get("nu", 2)
+    launches, nbytes = 0, 0
+    for l in range(len(sizes) - 1):
+        n, za, zp = sizes[l]
+        nc = sizes[l + 1][0]
+        launches += 2 * nu + 2
+        nbytes += 2 * nu * (12 * za + 4 * (n + 1) + 16 * n)
+        nbytes += (12 * zp + 4 * (nc + 1) + 8 * nc + 8 * n) + (12 * zp + 4 * (n + 1) + 8 * n + 8 * nc)
+    return {"launches": launches, "bytes": nbytes}
+
+
+def executed_launches(w, infos, amg_vc=None, spmv_bytes=None):
     """Launches that did work (the rest returned at once on the device's
     cycle-done flag), per kernel class, from each solve's iteration and
     cycle counts.  GMRES: one SpMV and one preconditioner apply per Arnoldi
@@ -191,6 +213,12 @@ def executed_launches(w, infos):
         if cpr:
             spmv += applies * (len(form) - 1)
         cnt["spmv"] += spmv
+        if amg_vc:
+            # every AMG V-cycle (the preconditioner, or CPR's pressure stage)
+            # adds its SpMVs on all levels to the SpMV class
+            vcs = applies * (nP if cpr else 1)
+            cnt["spmv"] += vcs * amg_vc["launches"]
+            cnt["_spmv_bytes"] = cnt.get("_spmv_bytes", 0) + spmv * spmv_bytes + vcs * amg_vc["bytes"]
         if w["precond"] == "cpr_learned":
             cnt["net"] += applies * nP
         if block:
@@ -318,6 +346,10 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
         M = oracle.PC(A, "cpr", mixed=mixed, pstage=_oracle_net_stage(params, scale, w["grid"], A_host["logk"]))
     elif w["precond"] == "cpr_learned":
         M = oracle.PC(A, "cpr", mixed=mixed)      # block system: ILU(0) pressure stage in the oracle
+    elif w["precond"] == "amg":
+        M = oracle.PC(A, "amg", amg=w["amg"])
+    elif w.get("pstage") == "amg":
+        M = oracle.PC(A, "cpr", mixed=mixed, form=w.get("form", "pf"), amg=w["amg"])
     elif w["precond"] == "ras":
         k = ras_kwargs(w)
         M = oracle.PC(A, "ras", ras=dict(nsub=k["nparts"], part=k["part"], overlap=k["overlap"], level=k["level"]))
@@ -432,6 +464,8 @@ class Case:
             kw.update(net=net, log_perm=A_host["logk"], grid=w["grid"])
         if w["precond"] == "ras":
             kw.update(ras_kwargs(w))
+        if "amg" in w:
+            kw.update(amg=w["amg"], **({"pstage": w["pstage"]} if "pstage" in w else {}))
         self.M = rs.Precond(ctx, self.A, w["precond"], prec=w["prec"], **kw)
         ctx.sync()
         self.setup_s = time.perf_counter() - t0
@@ -552,8 +586,11 @@ def run_gpu(args, w, rank, world, local):
     kern_ms = {k: v[0] for k, v in prof.items() if v[1] > 0}
     kern_n = {k: v[1] for k, v in prof.items() if v[1] > 0}
     total_prof = sum(kern_ms.values())
-    done = executed_launches(w, infos)
+    amg_vc = amg_vcycle_model(w, cases[0].M.amg_sizes()) if "amg" in w else None
+    done = executed_launches(w, infos, amg_vc, model["spmv"])
     work = {k: model[k] * done[k] for k in model if k in kern_n and done.get(k)}
+    if amg_vc and "spmv" in work:
+        work["spmv"] = done["_spmv_bytes"]
     work.update({k: cb[k] for k in cb if k in kern_n})
     rate = {k: work[k] / (kern_ms[k] * 1e-3) / 1e9 for k in work}
     net_fl = None
@@ -596,7 +633,8 @@ def run_gpu(args, w, rank, world, local):
             "config": {"workload": args.workload, "grid": list(w["grid"]), "unknowns": cases[0].A.n,
                        "nnz": int(cases[0].A.nnz), "block_size": cases[0].A.bs,
                        "solver": w["solver"] + "(30)" if "gmres" in w["solver"] else w["solver"],
-                       "precond": w["precond"] + ("-" + w["form"] if "form" in w else ""),
+                       "precond": w["precond"] + ("-" + w["form"] if "form" in w else "")
+                       + ("+amg" if w.get("pstage") == "amg" else ""),
                        "precision": w["prec"], "rtol": RTOL, "seeds": [seeds[0], seeds[-1]],
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": "replicas" if world > 1 else "1 gpu",

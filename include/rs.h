@@ -61,8 +61,9 @@ typedef enum {
     RS_PC_BILU0 = 2,      /* block ILU(0) of a BSR matrix                     */
     RS_PC_CPR = 3,        /* two-stage CPR, pressure stage ILU(0) (Alg. 6)    */
     RS_PC_CPR_LEARNED = 4, /* two-stage CPR, pressure stage = learned network */
-    RS_PC_RAS = 5         /* restricted additive Schwarz, ILU(k) local solver
+    RS_PC_RAS = 5,        /* restricted additive Schwarz, ILU(k) local solver
                              (Sec. 4.1)                                        */
+    RS_PC_AMG = 6         /* algebraic multigrid V-cycle (Sec. 4.2, Algs. 3-4) */
 } rs_pc_type;
 
 typedef enum {
@@ -96,6 +97,14 @@ typedef struct {
                                 [0, ras_nparts); NULL = contiguous ranges of
                                 rows, row i in floor(i nparts / n), like the
                                 paper's row distribution (Sec. 2.1, Eq. 1) */
+    /* RS_PC_AMG, and the AMG pressure stage of CPR (Sec. 4.2, Fig. 34).  A
+     * zeroed field takes the value in brackets. */
+    double amg_theta;       /* strength threshold, 0 < theta <= 1 [0.5]      */
+    int32_t amg_max_levels; /* 1..16 [16]                                     */
+    int32_t amg_max_coarse; /* rows at which coarsening stops, >= 1 [256]     */
+    int32_t amg_nu;         /* l1-Jacobi sweeps before and after, >= 1 [2]    */
+    int32_t cpr_pstage;     /* RS_PC_CPR pressure stage: 0 ILU(0) of the
+                               decoupled matrix, 1 one AMG V-cycle on it     */
 } rs_pc_opts;
 
 typedef struct {
@@ -192,6 +201,9 @@ int rs_mat_amxpby(double a, const rs_mat *A, const rs_vec *x, double b, rs_vec *
 /* ---- preconditioners (Sec. 3 Fig. 29, Sec. 4) -------------------------- */
 
 /* Builds M for A.  RS_PC_ILU0 needs a CSR matrix; RS_PC_BILU0 a BSR matrix;
+ * RS_PC_AMG needs a CSR matrix (setup of the hierarchy on the host, the
+ * V-cycle on the GPU; RS_ERR_INVALID_ARG when coarsening stalls above 4096
+ * rows or an option is out of range);
  * RS_PC_RAS either (on a BSR matrix the subdomains hold block rows and the
  * local solver is block ILU(k)), set by the opts->ras_* fields and
  * opts->ilu_level (RS_ERR_INVALID_ARG when out of range);
@@ -218,6 +230,17 @@ int rs_precond_get_bilu(const rs_pc *M, double *lu_host, double *dinv_host);
 int rs_precond_get_cpr(const rs_pc *M, double *w_host, double *app_host);
 /* Row of the last zero pivot met by setup, or -1. */
 int32_t rs_precond_bad_row(const rs_pc *M);
+/* RS_PC_AMG (or RS_PC_CPR with cpr_pstage = 1): number of levels of the
+ * hierarchy; sizes of level l: rows of A_l, stored entries of A_l and of the
+ * interpolation P_l (0 on the coarsest level). */
+int rs_precond_amg_levels(const rs_pc *M, int32_t *nlevels);
+int rs_precond_amg_level_sizes(const rs_pc *M, int32_t l, int32_t *n, int64_t *nnz_a, int64_t *nnz_p);
+/* Level l to host memory: A_l (aptr[n+1], acol, aval), P_l (pptr[n+1],
+ * pcol, pval; n x n_{l+1}) and cidx[n], the coarse index of each point
+ * (-1 for F points); P_l and cidx only below the coarsest level.  Any
+ * pointer may be NULL. */
+int rs_precond_get_amg_level(const rs_pc *M, int32_t l, int32_t *aptr, int32_t *acol, double *aval,
+                             int32_t *pptr, int32_t *pcol, double *pval, int32_t *cidx);
 /* RS_PC_RAS: the extended subdomains are stacked, subdomain after
  * subdomain, into one block-diagonal matrix (rows of a subdomain in
  * ascending global order).  *next = its (block) rows, *nnz = its stored

@@ -422,7 +422,8 @@ class PC:
 
     kind='ras': restricted additive Schwarz, `ras` = dict(nsub=, part=,
     overlap=, level=) as for Ras.
-    kind='amg': one AMG V-cycle, `amg` = keyword arguments of Amg.
+    kind='amg': one AMG V-cycle, `amg` = keyword arguments of Amg; with
+    kind='cpr', `amg` makes the pressure stage one AMG V-cycle on App'.
 
     kind='cpr' on a BSR matrix: quasi-IMPES restriction, ILU(0) of App'
     (or `pstage`, a callable rp -> zp), prolongation, residual, block ILU(0).
@@ -464,6 +465,11 @@ class PC:
                 self.w = np.zeros(0)
                 self.app_val = A.val.copy()
             self.App = Mat(A.ptr, A.col, self.app_val, 1)
+            if amg is not None:                     # AMG V-cycle pressure stage (Sec. 4.2)
+                self.amg = Amg(self.App, **amg)
+                if self.amg.status != OK:
+                    self.status = self.amg.status
+                s.amg = self.amg.h
             st, bad, lu = ilu0(self.App)
             if st != OK:
                 self.status, self.bad = st, bad

@@ -1172,6 +1172,7 @@ static int cpr_stage(const or_pc *M, char kind, int64_t n, const double *v, doub
     int st = OR_OK;
     or_qimpes_restrict(nb, bs, M->w, v, rp);
     if (M->pstage) st = M->pstage(M->pstage_user, nb, rp, zp);
+    else if (M->amg) or_amg_apply(M->amg, rp, zp);
     else if (M->mixed) or_ilu0_solve_f32(M->n, M->ptr, M->col, M->lu32, rp, zp);
     else or_ilu0_solve(M->n, M->ptr, M->col, M->lu, rp, zp);
     or_prolong(nb, bs, zp, out);

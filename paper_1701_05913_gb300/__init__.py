@@ -24,11 +24,11 @@ OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_BAD_PATTERN, ERR_ZERO_PIVOT, ERR_BREAKDOWN = -1, -2, -3, -4
 ERR_DEVICE_TIMEOUT, ERR_CUDA, ERR_OOM, ERR_SIZE_MISMATCH = -5, -6, -7, -8
 MEM_HOST, MEM_DEVICE = 0, 1
-PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CPR_LEARNED, PC_RAS = 0, 1, 2, 3, 4, 5
+PC_NONE, PC_ILU0, PC_BILU0, PC_CPR, PC_CPR_LEARNED, PC_RAS, PC_AMG = 0, 1, 2, 3, 4, 5, 6
 FP64, MIXED = 0, 1
 
 _PC_KIND = {"none": PC_NONE, "ilu0": PC_ILU0, "bilu0": PC_BILU0, "cpr": PC_CPR,
-            "cpr_learned": PC_CPR_LEARNED, "ras": PC_RAS}
+            "cpr_learned": PC_CPR_LEARNED, "ras": PC_RAS, "amg": PC_AMG}
 
 
 def box_partition(grid, parts):
@@ -60,7 +60,8 @@ class PcOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("net", _vp), ("log_perm", _vp), ("cpr_form", C.c_int32),
                 ("ras_nparts", C.c_int32), ("ras_overlap", C.c_int32), ("ilu_level", C.c_int32),
-                ("ras_part", _vp)]
+                ("ras_part", _vp), ("amg_theta", C.c_double), ("amg_max_levels", C.c_int32),
+                ("amg_max_coarse", C.c_int32), ("amg_nu", C.c_int32), ("cpr_pstage", C.c_int32)]
 
 
 CPR_FORMS = ("pf", "fp", "fpf", "ffpf")   # rs_cpr_form: Algs. 6, 5, 7, 8
@@ -103,6 +104,12 @@ SIGNATURES = [
     ("rs_precond_bad_row", C.c_int32, [_vp]),
     ("rs_precond_sweep_levels", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("rs_precond_ras_info", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    ("rs_precond_amg_levels", C.c_int, [_vp, C.POINTER(C.c_int32)]),
+    ("rs_precond_amg_level_sizes", C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                             C.POINTER(C.c_int64)]),
+    ("rs_precond_get_amg_level", C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _f64p,
+                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32), _f64p,
+                                           C.POINTER(C.c_int32)]),
     ("rs_precond_get_ras", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      _f64p]),
     ("rs_precond_destroy", C.c_int, [C.POINTER(_vp)]),
@@ -308,7 +315,7 @@ class Precond:
 
     def __init__(self, ctx: Context, A: Mat, kind: str = "ilu0", prec: str = "fp64",
                  net=None, log_perm=None, grid=None, form: str = "pf", nparts: int = 1, part=None,
-                 overlap: int = 0, level: int = 0):
+                 overlap: int = 0, level: int = 0, amg=None, pstage: str = "ilu0"):
         self.ctx, self.A, self.kind = ctx, A, kind
         opts = PcOpts()
         opts.prec = MIXED if prec == "mixed" else FP64
@@ -322,6 +329,13 @@ class Precond:
             opts.nx, opts.ny, opts.nz = grid
         # restricted additive Schwarz: subdomains, overlap layers, ILU(k) level
         opts.ras_nparts, opts.ras_overlap, opts.ilu_level = nparts, overlap, level
+        # algebraic multigrid (kind "amg", or the CPR pressure stage with pstage="amg")
+        a = amg or {}
+        opts.amg_theta = a.get("theta", 0.0)
+        opts.amg_max_levels = a.get("max_levels", 0)
+        opts.amg_max_coarse = a.get("max_coarse", 0)
+        opts.amg_nu = a.get("nu", 0)
+        opts.cpr_pstage = {"ilu0": 0, "amg": 1}[pstage]
         if part is not None:
             part = np.ascontiguousarray(part, dtype=np.int32)
             self._keep.append(part)
@@ -355,6 +369,44 @@ class Precond:
         _check(lib().rs_precond_get_cpr(self.h, w.ctypes.data_as(_f64p), app.ctypes.data_as(_f64p)),
                "rs_precond_get_cpr")
         return w, app
+
+    def amg_sizes(self):
+        """AMG hierarchy sizes: [(rows of A_l, entries of A_l, entries of P_l)]."""
+        L = lib()
+        nl = C.c_int32()
+        _check(L.rs_precond_amg_levels(self.h, C.byref(nl)), "rs_precond_amg_levels")
+        out = []
+        for l in range(nl.value):
+            n, na, np_ = C.c_int32(), C.c_int64(), C.c_int64()
+            _check(L.rs_precond_amg_level_sizes(self.h, l, C.byref(n), C.byref(na), C.byref(np_)),
+                   "rs_precond_amg_level_sizes")
+            out.append((n.value, na.value, np_.value))
+        return out
+
+    def amg_levels(self):
+        """AMG hierarchy: per level dict(A=(ptr, col, val), P=(ptr, col, val)
+        or None, cidx=coarse index per point or None)."""
+        L = lib()
+        nl = C.c_int32()
+        _check(L.rs_precond_amg_levels(self.h, C.byref(nl)), "rs_precond_amg_levels")
+        i32 = C.POINTER(C.c_int32)
+        out = []
+        for l in range(nl.value):
+            n, na, np_ = C.c_int32(), C.c_int64(), C.c_int64()
+            _check(L.rs_precond_amg_level_sizes(self.h, l, C.byref(n), C.byref(na), C.byref(np_)),
+                   "rs_precond_amg_level_sizes")
+            last = l + 1 == nl.value
+            a = (np.empty(n.value + 1, np.int32), np.empty(na.value, np.int32), np.empty(na.value))
+            p = None if last else (np.empty(n.value + 1, np.int32), np.empty(np_.value, np.int32),
+                                   np.empty(np_.value))
+            cidx = None if last else np.empty(n.value, np.int32)
+            _check(L.rs_precond_get_amg_level(
+                self.h, l, a[0].ctypes.data_as(i32), a[1].ctypes.data_as(i32), a[2].ctypes.data_as(_f64p),
+                p[0].ctypes.data_as(i32) if p else None, p[1].ctypes.data_as(i32) if p else None,
+                p[2].ctypes.data_as(_f64p) if p else None, cidx.ctypes.data_as(i32) if cidx is not None else None),
+                "rs_precond_get_amg_level")
+            out.append(dict(A=a, P=p, cidx=cidx))
+        return out
 
     def ras_info(self):
         """RAS: (stacked rows, stored entries) of the extended subdomains."""

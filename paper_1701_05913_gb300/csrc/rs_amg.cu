@@ -1,0 +1,472 @@
+// Algebraic multigrid preconditioner (Sec. 4.2: Alg. 3 setup, Alg. 4
+// V-cycle, Eq. 4).
+//
+// Setup (once per matrix, on the host, like the setup phase of the AMG
+// package the paper calls), level by level in Alg. 3's order:
+//   1. strength: j strongly influences i when j != i and
+//      -a_ij >= theta max_{k != i} (-a_ik) (theta = 0.5 by default, Fig. 34);
+//   2. coarse points: the Ruge-Stueben first pass.  The measure of a point
+//      is the number of undecided points it strongly influences plus twice
+//      the number of F points it strongly influences; the undecided point
+//      of largest measure (lowest index on ties) becomes C and the
+//      undecided points it strongly influences become F.  Points with no
+//      strong connection in either direction are F from the start;
+//   3. direct interpolation: C points inject; an F point i interpolates from
+//      its strong C neighbours k with w_ik = -alpha a_ik / a_ii (a_ik < 0) or
+//      -beta a_ik / a_ii (a_ik > 0), alpha (beta) = the row's sum of negative
+//      (positive) off-diagonal entries over that of its strong C neighbours;
+//      with no positive strong C coupling the positive couplings join a_ii;
+//   4. R = P^T;  5. A_{l+1} = R A_l P (Eq. 4);
+//   6. smoother: l1-Jacobi, x <- x + (b - A x) / d, d_i = sum_j |a_ij|.
+// Levels stop at max_coarse rows, max_levels, or when coarsening stalls;
+// the coarsest matrix is inverted densely.
+//
+// Apply (on the GPU): one V-cycle from x = 0 (Alg. 4): nu sweeps, residual,
+// restriction, the next level, prolongation and correction, nu sweeps;
+// the coarsest level is one dense matrix-vector product.  Every operator is
+// an rs_mat, so the products run in the library's SpMV kernels.
+#include <algorithm>
+#include <cmath>
+#include <queue>
+#include <vector>
+
+#include "rs_internal.cuh"
+
+namespace {
+
+struct HCsr {
+    int n = 0, m = 0;
+    std::vector<int> ptr, col;
+    std::vector<double> val;
+};
+
+// strong influences of every row: S[i] = { j : j strongly influences i }
+void strength(const HCsr &A, double theta, std::vector<int> &sp, std::vector<int> &sc)
+{
+    sp.assign(A.n + 1, 0);
+    sc.clear();
+    for (int i = 0; i < A.n; ++i) {
+        double mx = 0.0;
+        for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+            if (A.col[p] != i) mx = std::max(mx, -A.val[p]);
+        if (mx > 0.0)
+            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+                if (A.col[p] != i && -A.val[p] >= theta * mx) sc.push_back(A.col[p]);
+        sp[i + 1] = (int)sc.size();
+    }
+}
+
+// coarse index of every point (-1 = F) by the Ruge-Stueben first pass
+int first_pass(int n, const std::vector<int> &sp, const std::vector<int> &sc, std::vector<int> &cidx)
+{
+    // transpose of S: the points each point strongly influences
+    std::vector<int> tp(n + 1, 0), tc(sc.size());
+    for (int c : sc) ++tp[c + 1];
+    for (int i = 0; i < n; ++i) tp[i + 1] += tp[i];
+    {
+        std::vector<int> f(tp.begin(), tp.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (int q = sp[i]; q < sp[i + 1]; ++q) tc[f[sc[q]]++] = i;
+    }
+    enum : char { UND = 0, CP = 1, FP = 2 };
+    std::vector<char> st(n, UND);
+    std::vector<int> lam(n);
+    // max-heap on (measure, -index); stale entries are skipped when popped
+    std::priority_queue<std::pair<int, int>> heap;
+    for (int i = 0; i < n; ++i) {
+        lam[i] = tp[i + 1] - tp[i];
+        if (lam[i] == 0 && sp[i + 1] == sp[i]) st[i] = FP;
+        else heap.push({lam[i], -i});
+    }
+    while (!heap.empty()) {
+        const auto e = heap.top();
+        heap.pop();
+        const int i = -e.second;
+        if (st[i] != UND || e.first != lam[i]) continue;
+        st[i] = CP;
+        for (int q = tp[i]; q < tp[i + 1]; ++q) {
+            const int j = tc[q];
+            if (st[j] != UND) continue;
+            st[j] = FP;
+            for (int r = sp[j]; r < sp[j + 1]; ++r) {
+                const int k = sc[r];
+                if (st[k] == UND) heap.push({++lam[k], -k});
+            }
+        }
+        for (int r = sp[i]; r < sp[i + 1]; ++r) {
+            const int k = sc[r];
+            if (st[k] == UND) heap.push({--lam[k], -k});
+        }
+    }
+    cidx.assign(n, -1);
+    int nc = 0;
+    for (int i = 0; i < n; ++i)
+        if (st[i] == CP) cidx[i] = nc++;
+    return nc;
+}
+
+void direct_interpolation(const HCsr &A, const std::vector<int> &sp, const std::vector<int> &sc,
+                          const std::vector<int> &cidx, int nc, HCsr &P)
+{
+    P.n = A.n;
+    P.m = nc;
+    P.ptr.assign(1, 0);
+    P.col.clear();
+    P.val.clear();
+    std::vector<char> strongc(A.n, 0);
+    for (int i = 0; i < A.n; ++i) {
+        if (cidx[i] >= 0) {
+            P.col.push_back(cidx[i]);
+            P.val.push_back(1.0);
+        } else {
+            for (int r = sp[i]; r < sp[i + 1]; ++r)
+                if (cidx[sc[r]] >= 0) strongc[sc[r]] = 1;
+            double aii = 0.0, neg = 0.0, pos = 0.0, negc = 0.0, posc = 0.0;
+            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+                const int j = A.col[p];
+                const double v = A.val[p];
+                if (j == i) { aii = v; continue; }
+                (v < 0.0 ? neg : pos) += v;
+                if (strongc[j]) (v < 0.0 ? negc : posc) += v;
+            }
+            double diag = aii, beta = 0.0;
+            if (posc == 0.0) diag += pos;
+            else beta = pos / posc;
+            const double alpha = negc != 0.0 ? neg / negc : 0.0;
+            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+                const int k = A.col[p];
+                if (k == i || !strongc[k]) continue;
+                P.col.push_back(cidx[k]);
+                P.val.push_back(-(A.val[p] < 0.0 ? alpha : beta) * A.val[p] / diag);
+            }
+            for (int r = sp[i]; r < sp[i + 1]; ++r) strongc[sc[r]] = 0;
+        }
+        P.ptr.push_back((int)P.col.size());
+    }
+}
+
+void transpose(const HCsr &A, HCsr &T)
+{
+    T.n = A.m;
+    T.m = A.n;
+    T.ptr.assign(A.m + 1, 0);
+    T.col.resize(A.col.size());
+    T.val.resize(A.val.size());
+    for (int c : A.col) ++T.ptr[c + 1];
+    for (int c = 0; c < A.m; ++c) T.ptr[c + 1] += T.ptr[c];
+    std::vector<int> f(T.ptr.begin(), T.ptr.end() - 1);
+    for (int i = 0; i < A.n; ++i)
+        for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+            const int q = f[A.col[p]]++;
+            T.col[q] = i;
+            T.val[q] = A.val[p];
+        }
+}
+
+// C = A B by rows (Gustavson), columns sorted
+void multiply(const HCsr &A, const HCsr &B, HCsr &C)
+{
+    C.n = A.n;
+    C.m = B.m;
+    C.ptr.assign(1, 0);
+    C.col.clear();
+    C.val.clear();
+    std::vector<int> mark(B.m, -1), cols;
+    std::vector<double> acc(B.m, 0.0);
+    for (int i = 0; i < A.n; ++i) {
+        cols.clear();
+        for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+            const int j = A.col[p];
+            const double a = A.val[p];
+            for (int q = B.ptr[j]; q < B.ptr[j + 1]; ++q) {
+                const int c = B.col[q];
+                if (mark[c] != i) {
+                    mark[c] = i;
+                    acc[c] = 0.0;
+                    cols.push_back(c);
+                }
+                acc[c] += a * B.val[q];
+            }
+        }
+        std::sort(cols.begin(), cols.end());
+        for (int c : cols) {
+            C.col.push_back(c);
+            C.val.push_back(acc[c]);
+        }
+        C.ptr.push_back((int)C.col.size());
+    }
+}
+
+// dense inverse by Gauss-Jordan elimination with partial pivoting
+bool invert(int n, std::vector<double> a, std::vector<double> &inv)
+{
+    inv.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)p * n + c])) p = r;
+        const double piv = a[(size_t)p * n + c];
+        if (!(piv != 0.0) || !std::isfinite(piv)) return false;
+        if (p != c)
+            for (int j = 0; j < n; ++j) {
+                std::swap(a[(size_t)c * n + j], a[(size_t)p * n + j]);
+                std::swap(inv[(size_t)c * n + j], inv[(size_t)p * n + j]);
+            }
+        for (int j = 0; j < n; ++j) {
+            a[(size_t)c * n + j] /= piv;
+            inv[(size_t)c * n + j] /= piv;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = a[(size_t)r * n + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                a[(size_t)r * n + j] -= f * a[(size_t)c * n + j];
+                inv[(size_t)r * n + j] -= f * inv[(size_t)c * n + j];
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+// the host hierarchy, kept for export
+struct AmgHost {
+    std::vector<HCsr> A, P;
+    std::vector<std::vector<int>> cidx;
+};
+
+// first sweep from x = 0:  x_i = b_i / d_i
+__global__ void k_amg_first(int n, const double *__restrict__ b, const double *__restrict__ d,
+                            double *__restrict__ x, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = b[i] / d[i];
+}
+
+// x_i += t_i / d_i  with t = b - A x
+__global__ void k_amg_correct(int n, const double *__restrict__ t, const double *__restrict__ d,
+                              double *__restrict__ x, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] = x[i] + t[i] / d[i];
+}
+
+// coarsest level: x = Ainv b, one warp per row
+__global__ void k_amg_dense(int n, const double *__restrict__ inv, const double *__restrict__ b,
+                            double *__restrict__ x, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+        double s = 0.0;
+        for (int j = lane; j < n; j += 32) s = fma(inv[(size_t)i * n + j], b[j], s);
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[i] = s;
+    }
+}
+
+static int amg_grid(rs_ctx *ctx, int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8));
+}
+
+void rs_amg_destroy(AmgData *M)
+{
+    if (!M) return;
+    rs_ctx *ctx = M->ctx;
+    for (int l = 0; l < M->nlev; ++l) {
+        if (l > 0 || M->own0) rs_mat_destroy(&M->A[l]);   // level 0 may be the caller's matrix
+        rs_mat_destroy(&M->P[l]);
+        rs_mat_destroy(&M->R[l]);
+        rs_free(ctx, M->d[l]);
+        rs_free(ctx, M->b[l]);
+        rs_free(ctx, M->x[l]);
+        rs_free(ctx, M->t[l]);
+    }
+    rs_free(ctx, M->cinv);
+    delete M->host;
+    delete M;
+}
+
+int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::vector<int> &hcol,
+                  const double *d_val, const rs_mat *A0, double theta, int max_levels, int max_coarse, int nu,
+                  AmgData **out)
+{
+    *out = nullptr;
+    if (n < 1 || max_levels < 1 || max_levels > RS_AMG_MAXLEV || max_coarse < 1 || nu < 1 || !(theta >= 0.0))
+        return RS_ERR_INVALID_ARG;
+    AmgData *M = new AmgData();
+    M->ctx = ctx;
+    M->nu = nu;
+    M->host = new AmgHost();
+    AmgHost &H = *M->host;
+    H.A.emplace_back();
+    HCsr &F = H.A[0];
+    F.n = F.m = n;
+    F.ptr = hptr;
+    F.col = hcol;
+    F.val.resize(hcol.size());
+    if (!hcol.empty()) {
+        RS_CUDA_TRY(cudaMemcpyAsync(F.val.data(), d_val, sizeof(double) * hcol.size(), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+        RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    // the hierarchy (Alg. 3)
+    std::vector<int> sp, sc;
+    for (int l = 0;; ++l) {
+        if (H.A[l].n <= max_coarse || l + 1 >= max_levels) break;
+        strength(H.A[l], theta, sp, sc);
+        std::vector<int> cidx;
+        const int nc = first_pass(H.A[l].n, sp, sc, cidx);
+        if (nc == 0 || nc >= H.A[l].n) break;
+        HCsr P, R, AP, Ac;
+        direct_interpolation(H.A[l], sp, sc, cidx, nc, P);
+        transpose(P, R);
+        multiply(H.A[l], P, AP);
+        multiply(R, AP, Ac);
+        H.P.push_back(std::move(P));
+        H.cidx.push_back(std::move(cidx));
+        H.A.push_back(std::move(Ac));
+    }
+    M->nlev = (int)H.A.size();
+    if (H.A.back().n > RS_AMG_MAX_DENSE) {     // coarsening stalled: no small coarsest level
+        rs_amg_destroy(M);
+        return RS_ERR_INVALID_ARG;
+    }
+    std::vector<double> inv;
+    {
+        const HCsr &C = H.A.back();
+        std::vector<double> dense((size_t)C.n * C.n, 0.0);
+        for (int i = 0; i < C.n; ++i)
+            for (int p = C.ptr[i]; p < C.ptr[i + 1]; ++p) dense[(size_t)i * C.n + C.col[p]] = C.val[p];
+        if (!invert(C.n, std::move(dense), inv)) {
+            rs_amg_destroy(M);
+            return RS_ERR_ZERO_PIVOT;
+        }
+    }
+    // device objects
+    int st = RS_OK;
+    for (int l = 0; l < M->nlev && !st; ++l) {
+        const HCsr &A = H.A[l];
+        if (l == 0 && A0) {
+            M->A[0] = const_cast<rs_mat *>(A0);
+        } else {
+            M->own0 = M->own0 || l == 0;
+            st = rs_mat_create_rect(ctx, A.n, A.n, A.ptr.data(), A.col.data(), A.val.data(), &M->A[l]);
+            if (st) break;
+        }
+        if (l + 1 < M->nlev) {
+            HCsr R;
+            transpose(H.P[l], R);
+            st = rs_mat_create_rect(ctx, H.P[l].n, H.P[l].m, H.P[l].ptr.data(), H.P[l].col.data(),
+                                    H.P[l].val.data(), &M->P[l]);
+            if (!st) st = rs_mat_create_rect(ctx, R.n, R.m, R.ptr.data(), R.col.data(), R.val.data(), &M->R[l]);
+            if (st) break;
+        }
+        std::vector<double> d(A.n);
+        for (int i = 0; i < A.n; ++i) {
+            double s = 0.0;
+            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) s += std::fabs(A.val[p]);
+            d[i] = s;
+        }
+        st = rs_alloc(ctx, (void **)&M->d[l], sizeof(double) * A.n);
+        if (!st) st = rs_alloc(ctx, (void **)&M->b[l], sizeof(double) * A.n);
+        if (!st) st = rs_alloc(ctx, (void **)&M->x[l], sizeof(double) * A.n);
+        if (!st) st = rs_alloc(ctx, (void **)&M->t[l], sizeof(double) * A.n);
+        if (!st && cudaMemcpyAsync(M->d[l], d.data(), sizeof(double) * A.n, cudaMemcpyHostToDevice, ctx->stream) !=
+                       cudaSuccess)
+            st = RS_ERR_CUDA;
+    }
+    const int nc = H.A.back().n;
+    if (!st) st = rs_alloc(ctx, (void **)&M->cinv, sizeof(double) * (size_t)nc * nc);
+    if (!st && cudaMemcpyAsync(M->cinv, inv.data(), sizeof(double) * (size_t)nc * nc, cudaMemcpyHostToDevice,
+                               ctx->stream) != cudaSuccess)
+        st = RS_ERR_CUDA;
+    if (!st && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = RS_ERR_CUDA;
+    if (st) {
+        rs_amg_destroy(M);
+        return st;
+    }
+    *out = M;
+    return RS_OK;
+}
+
+// one V-cycle on level l: x_l = B_l b_l (Alg. 4 from x = 0)
+static int vcycle(AmgData *M, int l, const double *b, double *x, const int *skip)
+{
+    rs_ctx *ctx = M->ctx;
+    const rs_mat *A = M->A[l];
+    const int n = A->n;
+    if (l == M->nlev - 1) {
+        RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
+        k_amg_dense<<<std::max(1, std::min((n + 7) / 8, ctx->num_sms * 4)), 256, 0, ctx->stream>>>(n, M->cinv, b, x,
+                                                                                                  skip);
+        return rs_check_launch(ctx);
+    }
+    const int g = amg_grid(ctx, n);
+    double *t = M->t[l];
+    {
+        RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
+        k_amg_first<<<g, 256, 0, ctx->stream>>>(n, b, M->d[l], x, skip);
+    }
+    RS_TRY(rs_check_launch(ctx));
+    for (int s = 1; s < M->nu; ++s) {
+        RS_TRY(rs_residual_launch(A, b, x, t, nullptr, skip));
+        {
+            RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
+            k_amg_correct<<<g, 256, 0, ctx->stream>>>(n, t, M->d[l], x, skip);
+        }
+        RS_TRY(rs_check_launch(ctx));
+    }
+    RS_TRY(rs_residual_launch(A, b, x, t, nullptr, skip));
+    RS_TRY(rs_spmv_launch(M->R[l], t, 1.0, 0.0, M->b[l + 1], skip));
+    RS_TRY(vcycle(M, l + 1, M->b[l + 1], M->x[l + 1], skip));
+    RS_TRY(rs_spmv_launch(M->P[l], M->x[l + 1], 1.0, 1.0, x, skip));
+    for (int s = 0; s < M->nu; ++s) {
+        RS_TRY(rs_residual_launch(A, b, x, t, nullptr, skip));
+        {
+            RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
+            k_amg_correct<<<g, 256, 0, ctx->stream>>>(n, t, M->d[l], x, skip);
+        }
+        RS_TRY(rs_check_launch(ctx));
+    }
+    return RS_OK;
+}
+
+int rs_amg_apply(AmgData *M, const double *r, double *z, const int *skip)
+{
+    return vcycle(M, 0, r, z, skip);
+}
+
+int rs_amg_level_sizes(const AmgData *M, int l, int32_t *n, int64_t *nnz_a, int64_t *nnz_p)
+{
+    if (l < 0 || l >= M->nlev) return RS_ERR_INVALID_ARG;
+    const AmgHost &H = *M->host;
+    *n = H.A[l].n;
+    *nnz_a = (int64_t)H.A[l].col.size();
+    *nnz_p = l + 1 < M->nlev ? (int64_t)H.P[l].col.size() : 0;
+    return RS_OK;
+}
+
+int rs_amg_get_level(const AmgData *M, int l, int32_t *aptr, int32_t *acol, double *aval, int32_t *pptr,
+                     int32_t *pcol, double *pval, int32_t *cidx)
+{
+    if (l < 0 || l >= M->nlev) return RS_ERR_INVALID_ARG;
+    const AmgHost &H = *M->host;
+    const HCsr &A = H.A[l];
+    if (aptr) std::copy(A.ptr.begin(), A.ptr.end(), aptr);
+    if (acol) std::copy(A.col.begin(), A.col.end(), acol);
+    if (aval) std::copy(A.val.begin(), A.val.end(), aval);
+    if (l + 1 < M->nlev) {
+        const HCsr &P = H.P[l];
+        if (pptr) std::copy(P.ptr.begin(), P.ptr.end(), pptr);
+        if (pcol) std::copy(P.col.begin(), P.col.end(), pcol);
+        if (pval) std::copy(P.val.begin(), P.val.end(), pval);
+        if (cidx) std::copy(H.cidx[l].begin(), H.cidx[l].end(), cidx);
+    }
+    return RS_OK;
+}

@@ -125,10 +125,8 @@ extern "C" int rs_init(rs_ctx **out, int device, void *stream)
     return RS_OK;
 }
 
-extern "C" int rs_finalize(rs_ctx **pc)
+static void ctx_free(rs_ctx *c)
 {
-    if (!pc || !*pc) return RS_OK;
-    rs_ctx *c = *pc;
     cudaStreamSynchronize(c->stream);
     rs_free(c, c->red_partials);
     rs_free(c, c->red_ticket);
@@ -139,7 +137,26 @@ extern "C" int rs_finalize(rs_ctx **pc)
     for (const RsProfRec &r : c->prof_pending) { cudaEventDestroy(r.ev0); cudaEventDestroy(r.ev1); }
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
     delete c;
+}
+
+void rs_ctx_retain(rs_ctx *c) { ++c->live; }
+
+void rs_ctx_release(rs_ctx *c)
+{
+    if (--c->live == 0 && c->closing) ctx_free(c);
+}
+
+extern "C" int rs_finalize(rs_ctx **pc)
+{
+    if (!pc || !*pc) return RS_OK;
+    rs_ctx *c = *pc;
     *pc = nullptr;
+    if (c->live > 0) {
+        c->closing = true;      // released with the last handle
+        cudaStreamSynchronize(c->stream);
+        return RS_OK;
+    }
+    ctx_free(c);
     return RS_OK;
 }
 
@@ -341,6 +358,7 @@ extern "C" int rs_vec_create(rs_ctx *ctx, int32_t n, rs_vec **v)
     int st = rs_alloc(ctx, (void **)&x->d, sizeof(double) * (size_t)(n > 0 ? n : 1));
     if (st) { delete x; return st; }
     cudaMemsetAsync(x->d, 0, sizeof(double) * (size_t)n, ctx->stream);
+    rs_ctx_retain(ctx);
     *v = x;
     return RS_OK;
 }
@@ -353,6 +371,7 @@ extern "C" int rs_vec_wrap(rs_ctx *ctx, int32_t n, double *dev, rs_vec **v)
     x->n = n;
     x->d = dev;
     x->owns = 0;
+    rs_ctx_retain(ctx);
     *v = x;
     return RS_OK;
 }
@@ -360,9 +379,11 @@ extern "C" int rs_vec_wrap(rs_ctx *ctx, int32_t n, double *dev, rs_vec **v)
 extern "C" int rs_vec_destroy(rs_vec **v)
 {
     if (!v || !*v) return RS_OK;
-    if ((*v)->owns) rs_free((*v)->ctx, (*v)->d);
+    rs_ctx *ctx = (*v)->ctx;
+    if ((*v)->owns) rs_free(ctx, (*v)->d);
     delete *v;
     *v = nullptr;
+    rs_ctx_release(ctx);
     return RS_OK;
 }
 
@@ -696,7 +717,7 @@ int rs_residual_launch(const rs_mat *A, const double *b, const double *x, double
 // matrices
 // ---------------------------------------------------------------------------
 static int validate_pattern(int nrows, int ncols, const std::vector<int> &ptr,
-                            const std::vector<int> &col)
+                            const std::vector<int> &col, bool need_diag = true)
 {
     if ((int)ptr.size() != nrows + 1 || ptr[0] != 0) return RS_ERR_BAD_PATTERN;
     for (int i = 0; i < nrows; ++i) {
@@ -708,14 +729,14 @@ static int validate_pattern(int nrows, int ncols, const std::vector<int> &ptr,
             if (p > ptr[i] && col[p - 1] >= c) return RS_ERR_BAD_PATTERN;
             if (c == i) diag = true;
         }
-        if (!diag) return RS_ERR_BAD_PATTERN;
+        if (!diag && need_diag) return RS_ERR_BAD_PATTERN;
     }
     if ((size_t)ptr[nrows] != col.size()) return RS_ERR_BAD_PATTERN;
     return RS_OK;
 }
 
 static int mat_create(rs_ctx *ctx, int nrows, int bs, const int32_t *ptr, const int32_t *col,
-                      const double *val, int mem, rs_mat **out)
+                      const double *val, int mem, rs_mat **out, int ncols = -1)
 {
     if (!ctx || !out || nrows < 0 || bs < 1 || bs > 8 || !ptr) return RS_ERR_INVALID_ARG;
     if ((int64_t)nrows * bs > 0x7fffffffLL) return RS_ERR_INVALID_ARG;
@@ -742,7 +763,9 @@ static int mat_create(rs_ctx *ctx, int nrows, int bs, const int32_t *ptr, const 
         RS_CUDA_TRY(cudaMemcpyAsync(A->h_col.data(), col, sizeof(int) * nnzb, d2h, ctx->stream));
         RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     }
-    int st = validate_pattern(nrows, nrows, A->h_ptr, A->h_col);
+    // square matrices need every diagonal entry; rectangular operators
+    // (interpolation, restriction) only sorted, in-range columns
+    int st = validate_pattern(nrows, ncols < 0 ? nrows : ncols, A->h_ptr, A->h_col, ncols < 0);
     if (st) { delete A; return st; }
     // RS_MAT_PAD zeroed elements after each array: the SpMV's bulk copies
     // widen their ranges to 16-byte boundaries
@@ -764,6 +787,7 @@ static int mat_create(rs_ctx *ctx, int nrows, int bs, const int32_t *ptr, const 
     int L = 1;
     while (L < 32 && L * 1.5 < mean) L <<= 1;
     A->lanes = L;
+    rs_ctx_retain(ctx);
     *out = A;
     return RS_OK;
 }
@@ -772,6 +796,13 @@ extern "C" int rs_mat_create_csr(rs_ctx *ctx, int32_t n, const int32_t *rowptr,
                                  const int32_t *col, const double *val, int mem, rs_mat **A)
 {
     return mat_create(ctx, n, 1, rowptr, col, val, mem, A);
+}
+
+int rs_mat_create_rect(rs_ctx *ctx, int nrows, int ncols, const int32_t *ptr, const int32_t *col,
+                       const double *val, rs_mat **A)
+{
+    if (ncols < 0) return RS_ERR_INVALID_ARG;
+    return mat_create(ctx, nrows, 1, ptr, col, val, RS_MEM_HOST, A, ncols);
 }
 
 extern "C" int rs_mat_create_bsr(rs_ctx *ctx, int32_t nb, int32_t bs, const int32_t *browptr,
@@ -784,11 +815,13 @@ extern "C" int rs_mat_destroy(rs_mat **pA)
 {
     if (!pA || !*pA) return RS_OK;
     rs_mat *A = *pA;
-    rs_free(A->ctx, A->ptr);
-    rs_free(A->ctx, A->col);
-    rs_free(A->ctx, A->val);
+    rs_ctx *ctx = A->ctx;
+    rs_free(ctx, A->ptr);
+    rs_free(ctx, A->col);
+    rs_free(ctx, A->val);
     delete A;
     *pA = nullptr;
+    rs_ctx_release(ctx);
     return RS_OK;
 }
 

@@ -82,6 +82,11 @@ struct rs_ctx {
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[RS_PROF_NKINDS];
     long long prof_count[RS_PROF_NKINDS];
+    // handles (vectors, matrices, preconditioners, networks) alive on this
+    // context: rs_finalize releases the context when the last one goes, so
+    // handles and context may be destroyed in any order
+    int live = 0;
+    bool closing = false;
 };
 
 // Records an event pair around the launches in its scope when profiling is on.
@@ -189,6 +194,21 @@ struct RasData {
     IluFactor *f = nullptr;
 };
 
+// Algebraic multigrid (rs_amg.cu): operators of every level as rs_mat,
+// l1-Jacobi diagonals, work vectors, dense inverse of the coarsest matrix.
+#define RS_AMG_MAXLEV 16
+#define RS_AMG_MAX_DENSE 4096
+struct AmgHost;
+struct AmgData {
+    rs_ctx *ctx = nullptr;
+    int nlev = 0, nu = 2;
+    bool own0 = false;           // level-0 matrix built here (not the caller's)
+    rs_mat *A[RS_AMG_MAXLEV] = {}, *P[RS_AMG_MAXLEV] = {}, *R[RS_AMG_MAXLEV] = {};
+    double *d[RS_AMG_MAXLEV] = {}, *b[RS_AMG_MAXLEV] = {}, *x[RS_AMG_MAXLEV] = {}, *t[RS_AMG_MAXLEV] = {};
+    double *cinv = nullptr;
+    AmgHost *host = nullptr;     // the hierarchy on the host (export)
+};
+
 struct rs_pc {
     rs_ctx *ctx;
     int type;
@@ -209,15 +229,22 @@ struct rs_pc {
     int bad_row;
     int form;                // rs_cpr_form: order of the CPR stages
     RasData *ras;            // RS_PC_RAS
+    AmgData *amg;            // RS_PC_AMG, or the pressure stage of CPR
 };
 
 // ---------------------------------------------------------------------------
 // internal entry points shared across translation units
 // ---------------------------------------------------------------------------
 int rs_count_launch(rs_ctx *ctx);
+void rs_ctx_retain(rs_ctx *ctx);
+void rs_ctx_release(rs_ctx *ctx);
 int rs_check_launch(rs_ctx *ctx);
 int rs_alloc(rs_ctx *ctx, void **p, size_t bytes);
 void rs_free(rs_ctx *ctx, void *p);
+
+// an nrows x ncols CSR operator from host arrays (no diagonal required)
+int rs_mat_create_rect(rs_ctx *ctx, int nrows, int ncols, const int32_t *ptr, const int32_t *col,
+                       const double *val, rs_mat **A);
 
 // y = alpha * A x + beta * y (beta == 0: y not read).  Kernels given a
 // non-null `skip` return at once when *skip != 0 (a device flag).
@@ -242,6 +269,16 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
                   RasData **out, int *bad_row);
 int rs_ras_apply(RasData *R, const double *r, double *z, const int *skip);
 void rs_ras_destroy(RasData *R);
+// A0: the level-0 matrix when the caller has one as an rs_mat (else built
+// from the host pattern and the device values d_val)
+int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::vector<int> &hcol,
+                  const double *d_val, const rs_mat *A0, double theta, int max_levels, int max_coarse, int nu,
+                  AmgData **out);
+int rs_amg_apply(AmgData *M, const double *r, double *z, const int *skip);
+void rs_amg_destroy(AmgData *M);
+int rs_amg_level_sizes(const AmgData *M, int l, int32_t *n, int64_t *nnz_a, int64_t *nnz_p);
+int rs_amg_get_level(const AmgData *M, int l, int32_t *aptr, int32_t *acol, double *aval, int32_t *pptr,
+                     int32_t *pcol, double *pval, int32_t *cidx);
 
 // CPR / learned pressure stage
 int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip);

@@ -1401,6 +1401,7 @@ extern "C" int rs_net_create(rs_ctx *ctx, const float *params, int64_t nparams, 
     st = pack_all(net);
     if (st) { net_free(net); return st; }
     RS_CUDA_TRY(cudaStreamSynchronize(s));
+    rs_ctx_retain(ctx);
     *out = net;
     return RS_OK;
 }
@@ -1408,9 +1409,11 @@ extern "C" int rs_net_create(rs_ctx *ctx, const float *params, int64_t nparams, 
 extern "C" int rs_net_destroy(rs_net **net)
 {
     if (!net || !*net) return RS_OK;
-    cudaStreamSynchronize((*net)->ctx->stream);
+    rs_ctx *ctx = (*net)->ctx;
+    cudaStreamSynchronize(ctx->stream);
     net_free(*net);
     *net = nullptr;
+    rs_ctx_release(ctx);
     return RS_OK;
 }
 

@@ -93,6 +93,7 @@ static int cpr_stage(rs_pc *M, char kind, const double *v, double *out, const in
     }
     double *zp = bs > 1 ? M->zp : out;
     if (M->type == RS_PC_CPR_LEARNED) RS_TRY(rs_net_apply_pressure(M, rp, zp, skip));
+    else if (M->amg) RS_TRY(rs_amg_apply(M->amg, rp, zp, skip));
     else RS_TRY(rs_ilu_apply(M->ilu, rp, zp, nullptr, skip));
     if (bs > 1) {
         k_prolong<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(nb, bs, M->zp, out, skip);
@@ -115,6 +116,8 @@ int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip)
         return rs_ilu_apply(M->bilu, r, z, nullptr, skip);
     case RS_PC_RAS:
         return rs_ras_apply(M->ras, r, z, skip);
+    case RS_PC_AMG:
+        return rs_amg_apply(M->amg, r, z, skip);
     case RS_PC_CPR:
     case RS_PC_CPR_LEARNED: {
         // Algs. 5-8: the first stage maps f to z; every later stage forms
@@ -142,6 +145,7 @@ static void pc_free(rs_pc *M)
     if (M->ilu && M->ilu != M->bilu) rs_ilu_destroy(M->ilu);
     if (M->bilu) rs_ilu_destroy(M->bilu);
     if (M->ras) rs_ras_destroy(M->ras);
+    if (M->amg) rs_amg_destroy(M->amg);
     rs_free(ctx, M->app_val);
     rs_free(ctx, M->w);
     rs_free(ctx, M->rp);
@@ -149,6 +153,19 @@ static void pc_free(rs_pc *M)
     rs_free(ctx, M->t1);
     rs_free(ctx, M->t2);
     delete M;
+}
+
+// AMG options, zeroed fields taking their defaults (Fig. 34's strength 0.5
+// and two relaxation sweeps; up to 16 levels down to 256 rows)
+static int amg_params(const rs_pc_opts *o, double *theta, int *lev, int *coarse, int *nu)
+{
+    *theta = o && o->amg_theta != 0.0 ? o->amg_theta : 0.5;
+    *lev = o && o->amg_max_levels ? o->amg_max_levels : RS_AMG_MAXLEV;
+    *coarse = o && o->amg_max_coarse ? o->amg_max_coarse : 256;
+    *nu = o && o->amg_nu ? o->amg_nu : 2;
+    if (!(*theta > 0.0 && *theta <= 1.0) || *lev < 1 || *lev > RS_AMG_MAXLEV || *coarse < 1 || *nu < 1)
+        return RS_ERR_INVALID_ARG;
+    return RS_OK;
 }
 
 extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs_pc_opts *opts,
@@ -182,6 +199,16 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         st = rs_ilu_create(ctx, A->bs, A->nrows, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
         if (!st) st = rs_ilu_factor(M->bilu, A->val, &bad);
         break;
+    case RS_PC_AMG: {
+        double th;
+        int lev, nc, nu;
+        if (A->bs != 1 || (st = amg_params(opts, &th, &lev, &nc, &nu))) {
+            st = RS_ERR_INVALID_ARG;
+            break;
+        }
+        st = rs_amg_create(ctx, A->nrows, A->h_ptr, A->h_col, A->val, A, th, lev, nc, nu, &M->amg);
+        break;
+    }
     case RS_PC_RAS: {
         const int nparts = opts && opts->ras_nparts ? opts->ras_nparts : 1;
         st = rs_ras_create(ctx, A, nparts, opts ? opts->ras_part : nullptr, opts ? opts->ras_overlap : 0,
@@ -202,6 +229,13 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
             M->ny = opts->ny;
             M->nz = opts->nz;
         }
+        const int pstage = opts ? opts->cpr_pstage : 0;
+        double th;
+        int lev, ncoarse, nu;
+        if (pstage < 0 || pstage > 1 || (pstage == 1 && amg_params(opts, &th, &lev, &ncoarse, &nu))) {
+            st = RS_ERR_INVALID_ARG;
+            break;
+        }
         st = rs_ilu_create(ctx, bs, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
         if (!st) st = rs_ilu_factor(M->bilu, A->val, &bad);
         if (st) break;
@@ -209,7 +243,11 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         if (!st) st = rs_alloc(ctx, (void **)&M->t2, sizeof(double) * (A->n > 0 ? A->n : 1));
         if (st) break;
         if (bs == 1) {
-            M->ilu = M->bilu;     // pressure stage = ILU(0) of A itself
+            // pressure stage on A itself: its ILU(0), or an AMG V-cycle
+            if (pstage == 1 && type == RS_PC_CPR)
+                st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, A->val, A, th, lev, ncoarse, nu, &M->amg);
+            else
+                M->ilu = M->bilu;
             break;
         }
         st = rs_alloc(ctx, (void **)&M->w, sizeof(double) * (size_t)nb * (bs - 1));
@@ -223,7 +261,13 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
             st = rs_check_launch(ctx);
             ctx->launches++;
         }
-        if (!st) st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
+        if (st) break;
+        if (pstage == 1 && type == RS_PC_CPR) {
+            // AMG V-cycle on the decoupled pressure matrix (the paper's CPR pressure stage)
+            st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, M->app_val, nullptr, th, lev, ncoarse, nu, &M->amg);
+            break;
+        }
+        st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
         if (!st) st = rs_ilu_factor(M->ilu, M->app_val, &bad);
         break;
     }
@@ -232,6 +276,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
     }
     M->bad_row = bad;
     if (st == RS_ERR_ZERO_PIVOT) {
+        rs_ctx_retain(ctx);
         *out = M;          // keep the handle so the caller can query the row
         return st;
     }
@@ -239,6 +284,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         pc_free(M);
         return st;
     }
+    rs_ctx_retain(ctx);
     *out = M;
     return RS_OK;
 }
@@ -301,6 +347,26 @@ extern "C" int rs_precond_sweep_levels(const rs_pc *M, int32_t *levels_l, int32_
     return RS_OK;
 }
 
+extern "C" int rs_precond_amg_levels(const rs_pc *M, int32_t *nlevels)
+{
+    if (!M || !M->amg || !nlevels) return RS_ERR_INVALID_ARG;
+    *nlevels = M->amg->nlev;
+    return RS_OK;
+}
+
+extern "C" int rs_precond_amg_level_sizes(const rs_pc *M, int32_t l, int32_t *n, int64_t *nnz_a, int64_t *nnz_p)
+{
+    if (!M || !M->amg || !n || !nnz_a || !nnz_p) return RS_ERR_INVALID_ARG;
+    return rs_amg_level_sizes(M->amg, l, n, nnz_a, nnz_p);
+}
+
+extern "C" int rs_precond_get_amg_level(const rs_pc *M, int32_t l, int32_t *aptr, int32_t *acol, double *aval,
+                                        int32_t *pptr, int32_t *pcol, double *pval, int32_t *cidx)
+{
+    if (!M || !M->amg) return RS_ERR_INVALID_ARG;
+    return rs_amg_get_level(M->amg, l, aptr, acol, aval, pptr, pcol, pval, cidx);
+}
+
 extern "C" int rs_precond_ras_info(const rs_pc *M, int32_t *next, int64_t *nnz)
 {
     if (!M || !M->ras || !next || !nnz) return RS_ERR_INVALID_ARG;
@@ -329,7 +395,9 @@ extern "C" int rs_precond_get_ras(const rs_pc *M, int32_t *gidx, int32_t *ptr, i
 extern "C" int rs_precond_destroy(rs_pc **M)
 {
     if (!M || !*M) return RS_OK;
+    rs_ctx *ctx = (*M)->ctx;
     pc_free(*M);
     *M = nullptr;
+    rs_ctx_release(ctx);
     return RS_OK;
 }

@@ -500,3 +500,24 @@ def test_full_size_spmv_sampled_and_solve(rs, ctx, orc):
             true = orc.norm2(b - orc.spmv(Ao, xs)) / orc.norm2(b)
             assert info["status"] == 0 and true <= 1e-8, (prec, fn.__name__, info)
             assert rel(xs, xt) <= 1e-3
+
+
+def test_handles_may_outlive_their_context(rs, orc):
+    """rs_finalize with live handles defers the release of the context to
+    the last handle's destroy: destruction order is free (as with garbage
+    collection of reference cycles)."""
+    import gc
+    c2 = rs.Context(0)
+    g = synth.Grid(9, 8, 7)
+    d = synth.pressure_7pt(g, 80)
+    A = rs.Mat.csr(c2, d)
+    M = rs.Precond(c2, A, "amg")
+    import torch
+    r = synth.x_true(g.n, 80)
+    rv, z = rs.Vec(c2, r), rs.Vec.zeros(c2, g.n)
+    c2.close()                                   # handles still alive: deferred
+    M.apply(rv, z)                               # and still usable
+    torch.cuda.synchronize()
+    assert rel(z.t.cpu().numpy(), orc.Amg(orc.Mat.csr(d)).apply(r)) <= 1e-12
+    del M, A, z, rv
+    gc.collect()                                 # the last handle releases the context

@@ -994,3 +994,16 @@ def test_amg_coarsening_follows_the_first_pass_definition(orc):
     c = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1).cidx(0) >= 0
     x, y = np.meshgrid(np.arange(nx), np.arange(ny))
     assert np.array_equal(c, ((x + y) % 2 == 0).reshape(-1))
+
+
+def test_cpr_with_amg_pressure_stage_is_the_composition(orc):
+    # CPR-PF on a scalar matrix with an AMG pressure stage: z1 = AMG(f),
+    # t = f - A z1, z = z1 + ILU(0)^{-1} t, from the separately pinned pieces
+    d = synth.pressure_7pt(synth.Grid(9, 8, 7), 64)
+    A = orc.Mat.csr(d)
+    f = synth.x_true(d["n"], 64)
+    M = orc.PC(A, "cpr", amg=dict(max_coarse=20))
+    z1 = orc.Amg(A, max_coarse=20).apply(f)
+    _, _, lu = orc.ilu0(A)
+    want = z1 + orc.ilu0_solve(A, lu, f - orc.spmv(A, z1))
+    assert np.allclose(M.apply(f), want, rtol=1e-14, atol=1e-14)
