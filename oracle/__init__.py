@@ -131,6 +131,8 @@ def _declare(L):
                               _f64p, C.c_int32, C.POINTER(Info)]
     L.or_cg.argtypes = [mp, C.POINTER(_PC), _f64p, _f64p, C.c_double, C.c_int32,
                         _f64p, C.c_int32, C.POINTER(Info)]
+    L.or_lgmres.argtypes = [mp, C.POINTER(_PC), _f64p, _f64p, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                            C.POINTER(Info)]
 
 
 def _p(a, ct):
@@ -555,6 +557,18 @@ def gmres(A: Mat, M: PC | None, b, x0=None, restart=30, rtol=1e-8, maxit=10000,
 
 def fgmres(A, M, b, x0=None, restart=30, rtol=1e-8, maxit=10000, hist_len=0):
     return gmres(A, M, b, x0, restart, rtol, maxit, "right", True, False, hist_len)
+
+
+def lgmres(A: Mat, M: PC | None, b, x0=None, restart=30, aug_k=2, rtol=1e-8, maxit=10000):
+    """LGMRES(restart, aug_k): flexible GMRES augmented with the last aug_k
+    normalised corrections.  Returns (x, info)."""
+    b = _f64(b)
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    info = Info()
+    pc = M.s if M is not None else PC(A, "none").s
+    lib().or_lgmres(C.byref(A.s), C.byref(pc), _p(b, C.c_double), _p(x, C.c_double), restart, aug_k, rtol,
+                    maxit, C.byref(info))
+    return x, info.as_dict()
 
 
 def cg(A: Mat, M: PC | None, b, x0=None, rtol=1e-8, maxit=10000, hist_len=0):

@@ -1413,6 +1413,118 @@ done:
     return status;
 }
 
+/* LGMRES(m, k), the augmented restarted GMRES behind the `aug_k` setting of
+ * Sec. 3's solver (Baker, Jessup and Manteuffel 2005; the paper prints no
+ * algorithm).  Flexible GMRES whose cycle space is extended by the
+ * normalised corrections x_new - x_old of the last k cycles, newest first:
+ * a cycle takes m Arnoldi steps with z_i = M^{-1} v_i and then one step per
+ * stored correction with z_i = that correction; w = A z_i, CGS2, Givens
+ * rotations and stopping tests as in or_gmres; x += Z y, and Z y / ||Z y||
+ * joins the stored corrections.  k = 0 is FGMRES(m).  An iteration is one
+ * Arnoldi step. */
+int or_lgmres(const or_mat *A, const or_pc *M, const double *b, double *x, int32_t m, int32_t k,
+              double rtol, int32_t maxit, or_info *info)
+{
+    const int64_t n = mat_n(A);
+    memset(info, 0, sizeof(*info));
+    if (m < 1 || k < 0 || m + k > 500 || n < 1) { info->status = OR_INVALID; return OR_INVALID; }
+    const int32_t mk = m + k;
+    double *V = (double *)malloc(sizeof(double) * (size_t)n * (mk + 1));
+    double *Z = (double *)malloc(sizeof(double) * (size_t)n * mk);
+    double *aug = (double *)malloc(sizeof(double) * (size_t)n * (k > 0 ? k : 1));   /* aug[0] newest */
+    double *H = (double *)calloc((size_t)(mk + 1) * mk, sizeof(double));
+    double *cs = (double *)malloc(sizeof(double) * mk);
+    double *sn = (double *)malloc(sizeof(double) * mk);
+    double *g = (double *)malloc(sizeof(double) * (mk + 1));
+    double *y = (double *)malloc(sizeof(double) * (mk + 1));
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    const double bnorm = or_norm2(n, b);
+    int status = OR_NOT_CONVERGED;
+    int32_t iters = 0, cycles = 0, naug = 0;
+    double implicit = 0.0;
+    if (bnorm == 0.0) {
+        or_set(n, 0.0, x);
+        status = OR_OK;
+        goto done;
+    }
+    const double tol = rtol * bnorm;
+    for (;;) {
+        memcpy(r, b, sizeof(double) * (size_t)n);
+        or_amxpby(-1.0, A, x, 1.0, r);
+        const double beta = or_norm2(n, r);
+        implicit = beta;
+        if (beta <= tol) { status = OR_OK; break; }
+        if (iters >= maxit) break;
+        const int32_t dim = m + naug;
+        for (int64_t q = 0; q < n; ++q) V[q] = r[q] / beta;
+        g[0] = beta;
+        for (int32_t q = 1; q <= dim; ++q) g[q] = 0.0;
+        int32_t kdim = 0;
+        for (int32_t i = 0; i < dim; ++i) {
+            double *vi = V + (size_t)i * n;
+            double *zi = Z + (size_t)i * n;
+            if (i < m) or_pc_apply(M, n, vi, zi);
+            else memcpy(zi, aug + (size_t)(i - m) * n, sizeof(double) * (size_t)n);
+            or_spmv(A, zi, w);
+            const double w0 = or_norm2(n, w);
+            double *h = H + (size_t)i * (dim + 1);
+            or_orthogonalise(n, i, V, w, h, 0);
+            for (int32_t q = 0; q < i; ++q) {
+                const double a = h[q], c = h[q + 1];
+                h[q] = cs[q] * a + sn[q] * c;
+                h[q + 1] = -sn[q] * a + cs[q] * c;
+            }
+            const double hnext = h[i + 1];
+            const double rho = hypot(h[i], hnext);
+            cs[i] = h[i] / rho;
+            sn[i] = hnext / rho;
+            h[i] = rho;
+            h[i + 1] = 0.0;
+            g[i + 1] = -sn[i] * g[i];
+            g[i] = cs[i] * g[i];
+            ++iters;
+            kdim = i + 1;
+            implicit = fabs(g[i + 1]);
+            const int happy = hnext <= 1e-14 * w0;
+            if (implicit <= tol || iters >= maxit || happy || i == dim - 1) break;
+            double *vn = V + (size_t)(i + 1) * n;
+            for (int64_t q = 0; q < n; ++q) vn[q] = w[q] / hnext;
+        }
+        for (int32_t q = kdim - 1; q >= 0; --q) {
+            double s2 = g[q];
+            for (int32_t j = q + 1; j < kdim; ++j) s2 -= H[(size_t)j * (dim + 1) + q] * y[j];
+            y[q] = s2 / H[(size_t)q * (dim + 1) + q];
+        }
+        /* the correction dx = Z y (in w), then x += dx */
+        for (int64_t q = 0; q < n; ++q) {
+            double s2 = 0.0;
+            for (int32_t j = 0; j < kdim; ++j) s2 += Z[(size_t)j * n + q] * y[j];
+            w[q] = s2;
+        }
+        for (int64_t q = 0; q < n; ++q) x[q] = x[q] + w[q];
+        if (k > 0) {
+            const double nrm = or_norm2(n, w);
+            if (naug == k) --naug;                 /* the oldest correction drops out */
+            memmove(aug + (size_t)n, aug, sizeof(double) * (size_t)n * naug);
+            for (int64_t q = 0; q < n; ++q) aug[q] = nrm > 0.0 ? w[q] / nrm : 0.0;
+            ++naug;
+        }
+        ++cycles;
+    }
+done:
+    memcpy(r, b, sizeof(double) * (size_t)n);
+    or_amxpby(-1.0, A, x, 1.0, r);
+    info->true_rel_res = bnorm > 0.0 ? or_norm2(n, r) / bnorm : 0.0;
+    info->implicit_rel_res = bnorm > 0.0 ? implicit / bnorm : 0.0;
+    if (status == OR_OK && info->true_rel_res > rtol) status = OR_NOT_CONVERGED;
+    info->iters = iters;
+    info->restarts = cycles;
+    info->status = status;
+    free(V); free(Z); free(aug); free(H); free(cs); free(sn); free(g); free(y); free(r); free(w);
+    return status;
+}
+
 /* Right-preconditioned BiCGSTAB (named in Sec. 3 and used in Examples 2, 4
  * and 5; the paper does not print it, so this is van der Vorst's 1992
  * algorithm as given in Saad's book, with z = M^{-1} applied to p and s).

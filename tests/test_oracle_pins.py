@@ -1007,3 +1007,57 @@ def test_cpr_with_amg_pressure_stage_is_the_composition(orc):
     _, _, lu = orc.ilu0(A)
     want = z1 + orc.ilu0_solve(A, lu, f - orc.spmv(A, z1))
     assert np.allclose(M.apply(f), want, rtol=1e-14, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# LGMRES (the aug_k of Sec. 3's solver settings)
+# ----------------------------------------------------------------------------
+def _nonsymmetric(n, seed):
+    rng = np.random.default_rng(seed)
+    D = rng.standard_normal((n, n)) / np.sqrt(n) + 2.5 * np.eye(n)
+    return D, csr_dict(D)
+
+
+def test_lgmres_without_augmentation_is_fgmres(orc):
+    D, d = _nonsymmetric(60, 90)
+    A = orc.Mat.csr(d)
+    b = np.random.default_rng(91).standard_normal(60)
+    M = orc.PC(A, "ilu0")
+    x1, i1 = orc.lgmres(A, M, b, restart=7, aug_k=0, rtol=1e-10)
+    x2, i2, _ = orc.gmres(A, M, b, restart=7, rtol=1e-10, flexible=True)
+    assert i1["iters"] == i2["iters"] and np.array_equal(x1, x2)
+
+
+def test_lgmres_second_cycle_minimises_over_the_augmented_space(orc):
+    # cycle 2 minimises ||b - A x|| over x1 + K_m(A, r1) + span{x1 - x0}: the
+    # dense least-squares solution over that space, computed from scratch
+    n, m = 40, 4
+    D, d = _nonsymmetric(n, 92)
+    A = orc.Mat.csr(d)
+    b = np.random.default_rng(93).standard_normal(n)
+    x0 = np.random.default_rng(95).standard_normal(n)
+    x1, i1 = orc.lgmres(A, None, b, x0=x0, restart=m, aug_k=1, rtol=1e-15, maxit=m)
+    assert i1["iters"] == m
+    x2, i2 = orc.lgmres(A, None, b, x0=x0, restart=m, aug_k=1, rtol=1e-15, maxit=2 * m + 1)
+    assert i2["iters"] == 2 * m + 1
+    r1 = b - D @ x1
+    K = [r1]
+    for _ in range(m - 1):
+        K.append(D @ K[-1])
+    B = np.column_stack(K + [x1 - x0])
+    y = np.linalg.lstsq(D @ B, r1, rcond=None)[0]
+    want = x1 + B @ y
+    assert np.linalg.norm(x2 - want) <= 1e-9 * np.linalg.norm(want)
+    # and it is at least as good as plain GMRES over the Krylov part alone
+    y0 = np.linalg.lstsq(D @ B[:, :m], r1, rcond=None)[0]
+    assert np.linalg.norm(b - D @ x2) <= np.linalg.norm(r1 - D @ B[:, :m] @ y0) * (1 + 1e-12)
+
+
+def test_lgmres_converges_with_ilu0(orc):
+    d = synth.pressure_7pt(synth.Grid(12, 10, 8), 94, kz_scale=0.1)
+    A = orc.Mat.csr(d)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"]))
+    b = S @ synth.x_true(d["n"], 94)
+    x, info = orc.lgmres(A, orc.PC(A, "ilu0"), b, restart=10, aug_k=3, rtol=1e-10)
+    assert info["status"] == 0
+    assert np.linalg.norm(b - S @ x) <= 1e-10 * np.linalg.norm(b) * 1.0001
