@@ -61,6 +61,9 @@ WORKLOADS = {
                                          precond="cpr_learned", prec="mixed"),
     "cg_ilu0_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="cg", precond="ilu0",
                                prec="fp64"),
+    # LGMRES (the aug_k setting of Sec. 3): GMRES(30) cycles augmented with the last 3 corrections
+    "lgmres_ilu0_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="lgmres", precond="ilu0",
+                                   prec="fp64", aug_k=3),
     # algebraic multigrid (Sec. 4.2, Algs. 3-4): PCG with one V-cycle per iteration
     "cg_amg_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="cg", precond="amg", prec="fp64",
                               amg=dict()),
@@ -203,6 +206,12 @@ def executed_launches(w, infos, amg_vc=None, spmv_bytes=None):
             applies, spmv = 2 * I, 2 * I + 1
         elif w["solver"] == "cg":
             applies, spmv = I, I + C + 1
+        elif w["solver"] == "lgmres":
+            # cycle c (from 0) ends with min(c, aug_k) augmented steps, which
+            # take an SpMV but no preconditioner apply (the last, converging
+            # cycle is counted as if complete)
+            aug = sum(min(c, w["aug_k"]) for c in range(C + 1))
+            applies, spmv = max(I - aug, C + 1), I + C + 1
         else:
             applies = I + (0 if w["solver"] == "fgmres" else C)
             spmv = I + C + 1
@@ -357,6 +366,9 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
         M = oracle.PC(A, w["precond"], mixed=mixed, form=w.get("form", "pf"))
     setup = time.perf_counter() - t0
     t0 = time.perf_counter()
+    if w["solver"] == "lgmres":
+        _, info = oracle.lgmres(A, M, b, restart=30, aug_k=w["aug_k"], rtol=RTOL, maxit=maxit)
+        return time.perf_counter() - t0, setup, info["iters"]
     if w["solver"] == "bicgstab":
         _, info, _ = oracle.bicgstab(A, M, b, rtol=RTOL, maxit=maxit)
     elif w["solver"] == "cg":
@@ -484,6 +496,8 @@ def solve_fn(rs, w):
         return lambda c, M: rs.solve_cg(c.A, M, c.b, c.x, rtol=RTOL)
     if w["solver"] == "fgmres":
         return lambda c, M: rs.solve_fgmres(c.A, M, c.b, c.x, restart=30, rtol=RTOL)
+    if w["solver"] == "lgmres":
+        return lambda c, M: rs.solve_lgmres(c.A, M, c.b, c.x, restart=30, aug_k=w["aug_k"], rtol=RTOL)
     return lambda c, M: rs.solve_gmres(c.A, M, c.b, c.x, restart=30, rtol=RTOL)
 
 
@@ -632,7 +646,8 @@ def run_gpu(args, w, rank, world, local):
             "data": "synthetic",
             "config": {"workload": args.workload, "grid": list(w["grid"]), "unknowns": cases[0].A.n,
                        "nnz": int(cases[0].A.nnz), "block_size": cases[0].A.bs,
-                       "solver": w["solver"] + "(30)" if "gmres" in w["solver"] else w["solver"],
+                       "solver": w["solver"] + ("(30,%d)" % w["aug_k"] if "aug_k" in w else "(30)")
+                       if "gmres" in w["solver"] else w["solver"],
                        "precond": w["precond"] + ("-" + w["form"] if "form" in w else "")
                        + ("+amg" if w.get("pstage") == "amg" else ""),
                        "precision": w["prec"], "rtol": RTOL, "seeds": [seeds[0], seeds[-1]],

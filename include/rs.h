@@ -276,6 +276,15 @@ int rs_solve_gmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_
  * (the learned pressure stage). */
 int rs_solve_fgmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_t restart,
                     double rtol, int32_t maxit, rs_solve_info *info);
+/* LGMRES(restart, aug_k): flexible GMRES whose cycle space is extended by
+ * the normalised corrections x_new - x_old of the last aug_k cycles, newest
+ * first (the `aug_k` of the paper's solver settings, Sec. 3; Baker, Jessup
+ * and Manteuffel 2005).  A cycle takes `restart` preconditioned Arnoldi
+ * steps plus one step per stored correction; an iteration is one Arnoldi
+ * step.  aug_k = 0 is FGMRES.  1 <= restart, 0 <= aug_k,
+ * restart + aug_k <= 64. */
+int rs_solve_lgmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_t restart, int32_t aug_k,
+                    double rtol, int32_t maxit, rs_solve_info *info);
 /* BiCGSTAB (named in Sec. 3; used in Examples 2, 4, 5). */
 int rs_solve_bicgstab(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, double rtol,
                       int32_t maxit, rs_solve_info *info);

@@ -117,6 +117,8 @@ SIGNATURES = [
                                  C.POINTER(SolveInfo)]),
     ("rs_solve_fgmres", C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_double, C.c_int32,
                                   C.POINTER(SolveInfo)]),
+    ("rs_solve_lgmres", C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                  C.POINTER(SolveInfo)]),
     ("rs_solve_bicgstab", C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int32,
                                     C.POINTER(SolveInfo)]),
     ("rs_solve_cg", C.c_int, [_vp, _vp, _vp, _vp, C.c_double, C.c_int32, C.POINTER(SolveInfo)]),
@@ -540,6 +542,10 @@ def solve_gmres(A: Mat, M, b: Vec, x: Vec, restart=30, rtol=1e-8, maxit=10000):
 
 def solve_fgmres(A: Mat, M, b: Vec, x: Vec, restart=30, rtol=1e-8, maxit=10000):
     return _solve(lib().rs_solve_fgmres, A, M, b, x, restart, rtol, maxit)
+
+
+def solve_lgmres(A: Mat, M, b: Vec, x: Vec, restart=30, aug_k=2, rtol=1e-8, maxit=10000):
+    return _solve(lib().rs_solve_lgmres, A, M, b, x, restart, aug_k, rtol, maxit)
 
 
 def solve_bicgstab(A: Mat, M, b: Vec, x: Vec, rtol=1e-8, maxit=10000):

@@ -31,6 +31,7 @@ struct GmresDev {
     double h1[RS_MAX_RESTART + 2], h2[RS_MAX_RESTART + 2];
     double bnorm, tol, beta, hdiv, w0sq, implicit, r2;
     int iters, k, cycle_done, converged, maxit, m, noupd, status;
+    double augn2;           // ||Z y||^2 of the last cycle (LGMRES)
 };
 
 // ---------------------------------------------------------------------------
@@ -328,6 +329,16 @@ __global__ void k_scale_dev(int n, const double *__restrict__ r, const double *_
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = r[i] * a;
 }
 
+// y = x / sqrt(*n2) (0 when *n2 = 0): the normalised LGMRES correction
+__global__ void k_scale_rsqrt(int n, const double *__restrict__ x, const double *__restrict__ n2,
+                              double *__restrict__ y, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    const double s = *n2;
+    const double a = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = x[i] * a;
+}
+
 __global__ void k_axpy_skip(int n, const double *__restrict__ x, double *__restrict__ y, const int *skip)
 {
     if (skip && *(volatile const int *)skip) return;
@@ -431,11 +442,17 @@ static int finish_info(rs_ctx *ctx, const rs_mat *A, const double *b, const doub
     return RS_OK;
 }
 
-static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, int m, double rtol,
+// GMRES(m) (Alg. 1 with right preconditioning and CGS2), FGMRES(m), and
+// with aug_k > 0 (flexible only) LGMRES(m, aug_k): each cycle then adds one
+// Arnoldi step per stored correction of the last aug_k cycles (newest
+// first, held in a ring), and the cycle's correction Z y, normalised, joins
+// the ring.
+static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, int m, int aug_k, double rtol,
                       int maxit, int flexible, rs_solve_info *info)
 {
     if (!A || !bv || !xv || !info) return RS_ERR_INVALID_ARG;
-    if (m < 1 || m > RS_MAX_RESTART || maxit < 0 || !(rtol >= 0)) return RS_ERR_INVALID_ARG;
+    if (m < 1 || aug_k < 0 || m + aug_k > RS_MAX_RESTART || (aug_k > 0 && !flexible) || maxit < 0 || !(rtol >= 0))
+        return RS_ERR_INVALID_ARG;
     if (bv->n != A->n || xv->n != A->n) return RS_ERR_SIZE_MISMATCH;
     if (M && M->A->n != A->n) return RS_ERR_SIZE_MISMATCH;
     memset(info, 0, sizeof(*info));
@@ -444,10 +461,12 @@ static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, i
     const auto t0 = std::chrono::steady_clock::now();
     const int n = A->n;
     const int ld = (n + 31) / 32 * 32;
-    double *V = nullptr, *Z = nullptr, *r = nullptr, *t = nullptr;
+    double *V = nullptr, *Z = nullptr, *r = nullptr, *t = nullptr, *Aug = nullptr;
     GmresDev *d = nullptr;
-    int st = rs_alloc(ctx, (void **)&V, sizeof(double) * (size_t)ld * (m + 1));
-    if (!st && flexible) st = rs_alloc(ctx, (void **)&Z, sizeof(double) * (size_t)ld * m);
+    int naug = 0, head = 0;      // stored corrections; the next ring slot
+    int st = rs_alloc(ctx, (void **)&V, sizeof(double) * (size_t)ld * (m + aug_k + 1));
+    if (!st && flexible) st = rs_alloc(ctx, (void **)&Z, sizeof(double) * (size_t)ld * (m + aug_k));
+    if (!st && aug_k > 0) st = rs_alloc(ctx, (void **)&Aug, sizeof(double) * (size_t)ld * aug_k);
     if (!st) st = rs_alloc(ctx, (void **)&r, sizeof(double) * ld);
     if (!st) st = rs_alloc(ctx, (void **)&t, sizeof(double) * ld);
     if (!st) st = rs_alloc(ctx, (void **)&d, sizeof(GmresDev));
@@ -484,6 +503,13 @@ static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, i
         int *noupd = &d->noupd;
         int first = 1;
         for (;;) {
+            // this cycle's Arnoldi dimension: m, plus the stored corrections
+            const int dim = m + naug;
+            if (aug_k > 0 &&
+                cudaMemcpyAsync(&d->m, &dim, sizeof(int), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+                st = RS_ERR_CUDA;
+                goto out;
+            }
             // true residual and cycle start
             st = rs_residual_launch(A, b, x, r, &d->r2, nullptr);
             if (st) goto out;
@@ -502,23 +528,47 @@ static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, i
             if (hs[2]) { status = RS_NOT_CONVERGED; break; }
             k_scale_dev<<<gb, 256, 0, ctx->stream>>>(n, r, &d->hdiv, V, nullptr);
             ctx->launches++;
-            for (int i = 0; i < m; ++i) {
+            for (int i = 0; i < dim; ++i) {
                 double *vi = V + (size_t)i * ld;
                 double *zi = flexible ? Z + (size_t)i * ld : t;
                 double *w = V + (size_t)(i + 1) * ld;
-                if (M) st = rs_pc_apply_dev(M, vi, zi, cycle_done);
-                else zi = vi;
+                if (i >= m) {
+                    // augmented step: the (i - m)-th newest stored correction
+                    const int slot = ((head - 1 - (i - m)) % aug_k + aug_k) % aug_k;
+                    if (cudaMemcpyAsync(zi, Aug + (size_t)slot * ld, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                        ctx->stream) != cudaSuccess)
+                        st = RS_ERR_CUDA;
+                } else if (M) {
+                    st = rs_pc_apply_dev(M, vi, zi, cycle_done);
+                } else if (flexible) {
+                    if (cudaMemcpyAsync(zi, vi, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream) !=
+                        cudaSuccess)
+                        st = RS_ERR_CUDA;
+                } else {
+                    zi = vi;
+                }
                 if (!st) st = rs_spmv_launch(A, zi, 1.0, 0.0, w, cycle_done);
                 if (!st) st = cgs_step(ctx, n, ld, i + 1, V, d);
                 if (st) goto out;
-                if (i + 1 < m) {
+                if (i + 1 < dim) {
                     k_scale_dev<<<gb, 256, 0, ctx->stream>>>(n, w, &d->hdiv, w, cycle_done);
                     ctx->launches++;
                 }
             }
             k_gmres_backsolve<<<1, 32, 0, ctx->stream>>>(d);
             ctx->launches++;
-            if (flexible) {
+            if (flexible && aug_k > 0) {
+                // the correction t = Z y; x += t; t / ||t|| joins the ring
+                k_basis_combine<<<gb, 256, 0, ctx->stream>>>(n, ld, Z, d, t, 0);
+                k_axpy_skip<<<gb, 256, 0, ctx->stream>>>(n, t, x, noupd);
+                ctx->launches += 2;
+                st = rs_dot_launch(ctx, n, t, t, &d->augn2);
+                if (st) goto out;
+                k_scale_rsqrt<<<gb, 256, 0, ctx->stream>>>(n, t, &d->augn2, Aug + (size_t)head * ld, noupd);
+                ctx->launches++;
+                head = (head + 1) % aug_k;
+                naug = std::min(naug + 1, aug_k);
+            } else if (flexible) {
                 k_basis_combine<<<gb, 256, 0, ctx->stream>>>(n, ld, Z, d, x, 1);
                 ctx->launches++;
             } else {
@@ -551,6 +601,7 @@ done:
 out:
     rs_free(ctx, V);
     rs_free(ctx, Z);
+    rs_free(ctx, Aug);
     rs_free(ctx, r);
     rs_free(ctx, t);
     rs_free(ctx, d);
@@ -562,13 +613,19 @@ out:
 extern "C" int rs_solve_gmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_t restart,
                               double rtol, int32_t maxit, rs_solve_info *info)
 {
-    return gmres_impl(A, M, b, x, restart, rtol, maxit, 0, info);
+    return gmres_impl(A, M, b, x, restart, 0, rtol, maxit, 0, info);
 }
 
 extern "C" int rs_solve_fgmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_t restart,
                                double rtol, int32_t maxit, rs_solve_info *info)
 {
-    return gmres_impl(A, M, b, x, restart, rtol, maxit, 1, info);
+    return gmres_impl(A, M, b, x, restart, 0, rtol, maxit, 1, info);
+}
+
+extern "C" int rs_solve_lgmres(const rs_mat *A, rs_pc *M, const rs_vec *b, rs_vec *x, int32_t restart,
+                               int32_t aug_k, double rtol, int32_t maxit, rs_solve_info *info)
+{
+    return gmres_impl(A, M, b, x, restart, aug_k, rtol, maxit, 1, info);
 }
 
 // ---------------------------------------------------------------------------

@@ -521,3 +521,52 @@ def test_handles_may_outlive_their_context(rs, orc):
     assert rel(z.t.cpu().numpy(), orc.Amg(orc.Mat.csr(d)).apply(r)) <= 1e-12
     del M, A, z, rv
     gc.collect()                                 # the last handle releases the context
+
+
+@pytest.mark.parametrize("aug_k,restart,pc", [(0, 10, "ilu0"), (2, 10, "ilu0"), (3, 20, "ilu0"), (2, 8, None)])
+def test_lgmres_parity(rs, ctx, orc, aug_k, restart, pc):
+    g, d = _problem((24, 20, 17), 81, 0.1)
+    if pc is None:
+        # without a preconditioner: a well-conditioned matrix, so that the
+        # iteration count is not thousands of rounding-sensitive restarts
+        d = synth.pressure_7pt(g, 81, kz_scale=0.1, accum=0.5)
+    Ao = orc.Mat.csr(d)
+    b = orc.spmv(Ao, synth.x_true(g.n, 81))
+    Mo = orc.PC(Ao, pc) if pc else None
+    xo, io = orc.lgmres(Ao, Mo, b, restart=restart, aug_k=aug_k, rtol=1e-8, maxit=5000)
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, pc) if pc else None
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_lgmres(A, M, vec(rs, ctx, b), x, restart=restart, aug_k=aug_k, rtol=1e-8, maxit=5000)
+    xs = x.numpy()
+    assert info["status"] == 0 and io["status"] == 0
+    assert orc.norm2(b - orc.spmv(Ao, xs)) / orc.norm2(b) <= 1e-8
+    assert abs(info["iters"] - io["iters"]) <= 2, (info, io)
+    assert rel(xs, xo) <= 1e-6
+    if aug_k == 0:
+        # LGMRES without augmentation is FGMRES
+        x2 = rs.Vec.zeros(ctx, g.n)
+        i2 = rs.solve_fgmres(A, M, vec(rs, ctx, b), x2, restart=restart, rtol=1e-8, maxit=5000)
+        assert i2["iters"] == info["iters"] and np.array_equal(x2.numpy(), xs)
+
+
+def test_fgmres_without_preconditioner(rs, ctx, orc):
+    g = synth.Grid(12, 10, 8)
+    d = synth.pressure_7pt(g, 82, accum=0.5)
+    Ao = orc.Mat.csr(d)
+    b = orc.spmv(Ao, synth.x_true(g.n, 82))
+    xo, io, _ = orc.gmres(Ao, None, b, restart=20, rtol=1e-8, flexible=True)
+    A = rs.Mat.csr(ctx, d)
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_fgmres(A, None, vec(rs, ctx, b), x, restart=20, rtol=1e-8, maxit=10000)
+    assert info["status"] == 0 and abs(info["iters"] - io["iters"]) <= 2
+    assert rel(x.numpy(), xo) <= 1e-6
+
+
+def test_lgmres_invalid_arguments(rs, ctx):
+    g, d = _problem((6, 5, 4), 83, 1.0)
+    A = rs.Mat.csr(ctx, d)
+    b, x = rs.Vec.zeros(ctx, g.n), rs.Vec.zeros(ctx, g.n)
+    for kw in (dict(restart=60, aug_k=5), dict(restart=10, aug_k=-1)):
+        with pytest.raises(rs.RsError):
+            rs.solve_lgmres(A, None, b, x, rtol=1e-8, **kw)
