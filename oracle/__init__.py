@@ -108,7 +108,7 @@ def _declare(L):
     L.or_prolong.argtypes = [C.c_int32, C.c_int32, _f64p, _f64p]
     L.or_pc_apply.argtypes = [C.POINTER(_PC), C.c_int64, _f64p, _f64p]
     L.or_iluk_symbolic.argtypes = [C.c_int32, _i32p, _i32p, C.c_int32, C.POINTER(_i32p), C.POINTER(_i32p)]
-    L.or_ras_setup.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _i32p, C.c_int32, C.c_int32,
+    L.or_ras_setup.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _i32p, C.c_int32, C.c_int32,
                                C.POINTER(C.c_void_p), _i32p]
     L.or_ras_free.argtypes = [C.c_void_p]
     L.or_ras_apply.argtypes = [C.c_void_p, _f64p, _f64p]
@@ -324,15 +324,15 @@ def contiguous_partition(n, nsub):
 
 
 class Ras:
-    """Restricted additive Schwarz with ILU(level) local solvers (scalar A)."""
+    """Restricted additive Schwarz with ILU(level) local solvers; on a block
+    matrix the subdomains hold block rows and the local solver is block ILU."""
 
     def __init__(self, A: Mat, nsub: int, part=None, overlap: int = 1, level: int = 0):
-        assert A.bs == 1
         self.A = A
         self.part = _i32(contiguous_partition(A.nrows, nsub) if part is None else part)
         h = C.c_void_p()
         bad = C.c_int32(-1)
-        self.status = lib().or_ras_setup(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
+        self.status = lib().or_ras_setup(A.nrows, A.bs, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
                                          _p(A.val, C.c_double), nsub, _p(self.part, C.c_int32), overlap,
                                          level, C.byref(h), C.byref(bad))
         self.bad = bad.value
@@ -352,7 +352,7 @@ class Ras:
         gidx = np.empty(ne.value, np.int32)
         ptr = np.empty(ne.value + 1, np.int32)
         col = np.empty(nz.value, np.int32)
-        lu = np.empty(nz.value)
+        lu = np.empty(nz.value * self.A.bs * self.A.bs)
         lib().or_ras_export(self.h, _p(gidx, C.c_int32), _p(ptr, C.c_int32), _p(col, C.c_int32),
                             _p(lu, C.c_double))
         return gidx, ptr, col, lu
@@ -425,7 +425,8 @@ class PC:
     kind='ras': restricted additive Schwarz, `ras` = dict(nsub=, part=,
     overlap=, level=) as for Ras.
     kind='amg': one AMG V-cycle, `amg` = keyword arguments of Amg; with
-    kind='cpr', `amg` makes the pressure stage one AMG V-cycle on App'.
+    kind='cpr', `amg` makes the pressure stage one AMG V-cycle on App' and
+    `ras` makes the F stage restricted additive Schwarz on A.
 
     kind='cpr' on a BSR matrix: quasi-IMPES restriction, ILU(0) of App'
     (or `pstage`, a callable rp -> zp), prolongation, residual, block ILU(0).
@@ -467,6 +468,11 @@ class PC:
                 self.w = np.zeros(0)
                 self.app_val = A.val.copy()
             self.App = Mat(A.ptr, A.col, self.app_val, 1)
+            if ras is not None:                     # RAS as the F stage R(A)^{-1} (Sec. 4.2.1)
+                self.fras = Ras(A, **ras)
+                if self.fras.status != OK:
+                    self.status = self.fras.status
+                s.ras = self.fras.h
             if amg is not None:                     # AMG V-cycle pressure stage (Sec. 4.2)
                 self.amg = Amg(self.App, **amg)
                 if self.amg.status != OK:

@@ -467,6 +467,8 @@ int or_iluk_symbolic(int32_t n, const int32_t *ptr, const int32_t *col, int32_t 
 
 /* ------------------------------------------------------------------------ */
 /* Restricted additive Schwarz (Sec. 4.1, after Cai and Sarkis).             */
+/* On a block matrix (bs > 1) rows are block rows and the local solver is    */
+/* block ILU(level) (block ILU(0) on the level-of-fill block pattern).       */
 /* part[i] in [0, nsub) assigns row i to a subdomain.  Subdomain s is        */
 /* extended by `overlap` layers of the graph of A (layer m+1 = the columns   */
 /* of the rows of layer m); its local matrix A_s keeps the entries of A      */
@@ -477,12 +479,13 @@ int or_iluk_symbolic(int32_t n, const int32_t *ptr, const int32_t *col, int32_t 
 /* owns are written (the restricted prolongation).                           */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int32_t n, nsub;
+    int32_t n, nsub, bs;
     int32_t *part;           /* copy of the partition */
     int32_t *ext_ptr;        /* nsub + 1 offsets into ext */
     int32_t *ext;            /* extended rows of each subdomain, ascending */
     int32_t **lptr, **lcol;  /* local ILU(k) pattern per subdomain */
     double **llu;            /* local factors */
+    double **ldinv;          /* inverted diagonal blocks (bs > 1) */
 } or_ras;
 
 void or_ras_free(or_ras *R)
@@ -492,33 +495,38 @@ void or_ras_free(or_ras *R)
         free(R->lptr[s]);
         free(R->lcol[s]);
         free(R->llu[s]);
+        free(R->ldinv[s]);
     }
     free(R->lptr);
     free(R->lcol);
     free(R->llu);
+    free(R->ldinv);
     free(R->part);
     free(R->ext_ptr);
     free(R->ext);
     free(R);
 }
 
-int or_ras_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, int32_t nsub,
+int or_ras_setup(int32_t n, int32_t bs, const int32_t *ptr, const int32_t *col, const double *val, int32_t nsub,
                  const int32_t *part, int32_t overlap, int32_t level, or_ras **out, int32_t *bad_row)
 {
     *out = NULL;
     *bad_row = -1;
-    if (nsub < 1 || overlap < 0 || level < 0) return OR_INVALID;
+    if (nsub < 1 || overlap < 0 || level < 0 || bs < 1 || bs > 8) return OR_INVALID;
+    const size_t b2 = (size_t)bs * bs;
     for (int32_t i = 0; i < n; ++i)
         if (part[i] < 0 || part[i] >= nsub) return OR_INVALID;
     or_ras *R = (or_ras *)calloc(1, sizeof(or_ras));
     R->n = n;
     R->nsub = nsub;
+    R->bs = bs;
     R->part = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     memcpy(R->part, part, sizeof(int32_t) * (size_t)n);
     R->ext_ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nsub + 1));
     R->lptr = (int32_t **)calloc((size_t)nsub, sizeof(int32_t *));
     R->lcol = (int32_t **)calloc((size_t)nsub, sizeof(int32_t *));
     R->llu = (double **)calloc((size_t)nsub, sizeof(double *));
+    R->ldinv = (double **)calloc((size_t)nsub, sizeof(double *));
     int64_t cap = n > 0 ? n : 1, len = 0;
     R->ext = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
     char *in = (char *)malloc((size_t)(n > 0 ? n : 1));
@@ -554,14 +562,14 @@ int or_ras_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double
         for (int32_t a = 0; a < ns; ++a)
             for (int32_t q = ptr[er[a]]; q < ptr[er[a] + 1]; ++q) nz += in[col[q]] ? 1 : 0;
         int32_t *ac = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nz > 0 ? nz : 1));
-        double *av = (double *)malloc(sizeof(double) * (size_t)(nz > 0 ? nz : 1));
+        double *av = (double *)malloc(sizeof(double) * b2 * (size_t)(nz > 0 ? nz : 1));
         ap[0] = 0;
         nz = 0;
         for (int32_t a = 0; a < ns; ++a) {
             for (int32_t q = ptr[er[a]]; q < ptr[er[a] + 1]; ++q)
                 if (in[col[q]]) {
                     ac[nz] = loc[col[q]];
-                    av[nz] = val[q];
+                    memcpy(av + (size_t)nz * b2, val + (size_t)q * b2, sizeof(double) * b2);
                     ++nz;
                 }
             ap[a + 1] = (int32_t)nz;
@@ -569,17 +577,23 @@ int or_ras_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double
         /* the ILU(level) pattern of A_s, with A_s's values and zeros at fill */
         int32_t *kp, *kc;
         or_iluk_symbolic(ns, ap, ac, level, &kp, &kc);
-        double *kv = (double *)malloc(sizeof(double) * (size_t)(kp[ns] > 0 ? kp[ns] : 1));
+        double *kv = (double *)malloc(sizeof(double) * b2 * (size_t)(kp[ns] > 0 ? kp[ns] : 1));
         for (int32_t a = 0; a < ns; ++a) {
             int32_t q = ap[a];
             for (int32_t t = kp[a]; t < kp[a + 1]; ++t) {
                 while (q < ap[a + 1] && ac[q] < kc[t]) ++q;
-                kv[t] = (q < ap[a + 1] && ac[q] == kc[t]) ? av[q] : 0.0;
+                const int hit = q < ap[a + 1] && ac[q] == kc[t];
+                for (size_t e = 0; e < b2; ++e) kv[(size_t)t * b2 + e] = hit ? av[(size_t)q * b2 + e] : 0.0;
             }
         }
-        double *lu = (double *)malloc(sizeof(double) * (size_t)(kp[ns] > 0 ? kp[ns] : 1));
+        double *lu = (double *)malloc(sizeof(double) * b2 * (size_t)(kp[ns] > 0 ? kp[ns] : 1));
         int32_t bad = -1;
-        st = or_ilu0(ns, kp, kc, kv, lu, &bad);
+        if (bs == 1) {
+            st = or_ilu0(ns, kp, kc, kv, lu, &bad);
+        } else {
+            R->ldinv[s] = (double *)malloc(sizeof(double) * b2 * (size_t)(ns > 0 ? ns : 1));
+            st = or_bilu0(ns, bs, kp, kc, kv, lu, R->ldinv[s], &bad);
+        }
         if (st != OR_OK) *bad_row = bad >= 0 ? er[bad] : -1;
         R->lptr[s] = kp;
         R->lcol[s] = kc;
@@ -601,15 +615,19 @@ int or_ras_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double
 
 void or_ras_apply(const or_ras *R, const double *r, double *z)
 {
+    const int32_t bs = R->bs;
     for (int32_t s = 0; s < R->nsub; ++s) {
         const int32_t *er = R->ext + R->ext_ptr[s];
         const int32_t ns = R->ext_ptr[s + 1] - R->ext_ptr[s];
-        double *rl = (double *)malloc(sizeof(double) * (size_t)(ns > 0 ? ns : 1));
-        double *zl = (double *)malloc(sizeof(double) * (size_t)(ns > 0 ? ns : 1));
-        for (int32_t a = 0; a < ns; ++a) rl[a] = r[er[a]];
-        or_ilu0_solve(ns, R->lptr[s], R->lcol[s], R->llu[s], rl, zl);
+        double *rl = (double *)malloc(sizeof(double) * (size_t)bs * (ns > 0 ? ns : 1));
+        double *zl = (double *)malloc(sizeof(double) * (size_t)bs * (ns > 0 ? ns : 1));
         for (int32_t a = 0; a < ns; ++a)
-            if (R->part[er[a]] == s) z[er[a]] = zl[a];
+            for (int32_t c = 0; c < bs; ++c) rl[(size_t)a * bs + c] = r[(size_t)er[a] * bs + c];
+        if (bs == 1) or_ilu0_solve(ns, R->lptr[s], R->lcol[s], R->llu[s], rl, zl);
+        else or_bilu0_solve(ns, bs, R->lptr[s], R->lcol[s], R->llu[s], R->ldinv[s], rl, zl);
+        for (int32_t a = 0; a < ns; ++a)
+            if (R->part[er[a]] == s)
+                for (int32_t c = 0; c < bs; ++c) z[(size_t)er[a] * bs + c] = zl[(size_t)a * bs + c];
         free(rl);
         free(zl);
     }
@@ -629,6 +647,7 @@ void or_ras_sizes(const or_ras *R, int32_t *next, int64_t *nnz)
  * numbered in the stacked order) and the factor values. */
 void or_ras_export(const or_ras *R, int32_t *gidx, int32_t *ptr, int32_t *col, double *lu)
 {
+    const size_t b2 = (size_t)R->bs * R->bs;
     int64_t q = 0;
     ptr[0] = 0;
     for (int32_t s = 0; s < R->nsub; ++s) {
@@ -637,7 +656,7 @@ void or_ras_export(const or_ras *R, int32_t *gidx, int32_t *ptr, int32_t *col, d
             gidx[base + a] = R->ext[base + a];
             for (int32_t t = R->lptr[s][a]; t < R->lptr[s][a + 1]; ++t, ++q) {
                 col[q] = base + R->lcol[s][t];
-                lu[q] = R->llu[s][t];
+                memcpy(lu + (size_t)q * b2, R->llu[s] + (size_t)t * b2, sizeof(double) * b2);
             }
             ptr[base + a + 1] = (int32_t)q;
         }
@@ -1149,7 +1168,7 @@ typedef struct {
     /* CPR form: 0 PF (Alg. 6, read as below), 1 FP (Alg. 5), 2 FPF (Alg. 7),
      * 3 FFPF (Alg. 8) */
     int32_t form;
-    /* restricted additive Schwarz (type RAS) */
+    /* restricted additive Schwarz (type RAS; with type CPR, the F stage) */
     const or_ras *ras;
     /* algebraic multigrid V-cycle (type AMG) */
     const or_amg *amg;
@@ -1163,7 +1182,8 @@ static int cpr_stage(const or_pc *M, char kind, int64_t n, const double *v, doub
 {
     const int32_t nb = M->nb, bs = M->bs;
     if (kind == 'F') {
-        if (M->mixed) or_bilu0_solve_f32(nb, bs, M->bptr, M->bcol, M->blu32, M->bdinv32, v, out);
+        if (M->ras) or_ras_apply(M->ras, v, out);
+        else if (M->mixed) or_bilu0_solve_f32(nb, bs, M->bptr, M->bcol, M->blu32, M->bdinv32, v, out);
         else or_bilu0_solve(nb, bs, M->bptr, M->bcol, M->blu, M->bdinv, v, out);
         return OR_OK;
     }

@@ -1061,3 +1061,71 @@ def test_lgmres_converges_with_ilu0(orc):
     x, info = orc.lgmres(A, orc.PC(A, "ilu0"), b, restart=10, aug_k=3, rtol=1e-10)
     assert info["status"] == 0
     assert np.linalg.norm(b - S @ x) <= 1e-10 * np.linalg.norm(b) * 1.0001
+
+
+def _block_chain(nb, bs, seed):
+    """Block-tridiagonal, block diagonally dominant matrix (1-D chain of blocks)."""
+    rng = np.random.default_rng(seed)
+    ptr, col, val = [0], [], []
+    for I in range(nb):
+        for J in (I - 1, I, I + 1):
+            if 0 <= J < nb:
+                B = -0.3 * rng.random((bs, bs))
+                if I == J:
+                    B = B + 4.0 * np.eye(bs)
+                col.append(J)
+                val.append(B)
+        ptr.append(len(col))
+    return dict(nb=nb, bs=bs, browptr=np.array(ptr, np.int32), bcol=np.array(col, np.int32),
+                bval=np.array(val).reshape(-1))
+
+
+def test_block_ras_special_cases(orc):
+    nb, bs = 30, 3
+    m = _block_chain(nb, bs, 100)
+    A = orc.Mat.bsr(m)
+    D = sp.bsr_matrix((m["bval"].reshape(-1, bs, bs), m["bcol"], m["browptr"]), shape=(nb * bs, nb * bs)).toarray()
+    r = np.random.default_rng(101).standard_normal(nb * bs)
+    # one subdomain without overlap is block ILU(0), bit for bit
+    _, _, blu, bdinv = orc.bilu0(A)
+    assert np.array_equal(orc.Ras(A, 1, overlap=0).apply(r), orc.bilu0_solve(A, blu, bdinv, r))
+    # on a block chain every local block ILU(0) is an exact block LU: RAS is the
+    # restricted dense solve on each extended set of blocks
+    part = np.random.default_rng(102).integers(0, 4, nb).astype(np.int32)
+    P = np.zeros((nb, nb), dtype=bool)
+    for I in range(nb):
+        P[I, m["bcol"][m["browptr"][I]:m["browptr"][I + 1]]] = True
+    for overlap in (0, 1, 2):
+        z = orc.Ras(A, 4, part=part, overlap=overlap).apply(r)
+        want = np.empty(nb * bs)
+        for s in range(4):
+            e = part == s
+            for _ in range(overlap):
+                e = e | P[e].any(axis=0)
+            blocks = np.nonzero(e)[0]
+            if blocks.size == 0:
+                continue
+            idx = (blocks[:, None] * bs + np.arange(bs)).reshape(-1)
+            ze = np.linalg.solve(D[np.ix_(idx, idx)], r[idx])
+            own = np.repeat(part[blocks] == s, bs)
+            want[idx[own]] = ze[own]
+        assert np.allclose(z, want, rtol=1e-13, atol=1e-13), overlap
+
+
+def test_cpr_with_ras_f_stage_is_the_composition(orc):
+    # CPR-PF with R(A)^{-1} = RAS: z1 = Pi_p ILU0(App')^{-1} Pi_r f,
+    # t = f - A z1, z = z1 + RAS(A)^{-1} t, from the separately pinned pieces
+    g = synth.Grid(7, 6, 5)
+    m = synth.black_oil_bsr3(g, 103)
+    A = orc.Mat.bsr(m)
+    nb, bs = g.n, 3
+    part = (np.arange(nb) * 3 // nb).astype(np.int32)
+    ras = dict(nsub=3, part=part, overlap=1)
+    f = synth.x_true(nb * bs, 103)
+    M = orc.PC(A, "cpr", ras=ras)
+    w = orc.qimpes_weights(A)
+    App = orc.Mat(m["browptr"], m["bcol"], orc.qimpes_app(A, w), 1)
+    _, _, lu = orc.ilu0(App)
+    z1 = orc.prolong(nb, bs, orc.ilu0_solve(App, lu, orc.qimpes_restrict(nb, bs, w, f)))
+    want = z1 + orc.Ras(A, **ras).apply(f - orc.spmv(A, z1))
+    assert np.allclose(M.apply(f), want, rtol=1e-14, atol=1e-14)
