@@ -70,6 +70,12 @@ WORKLOADS = {
     # the paper's CPR with an AMG pressure stage (Sec. 4.2.1, Alg. 6 with M_p = one V-cycle)
     "cpr_amg_fgmres_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="fgmres",
                                            precond="cpr", prec="mixed", pstage="amg", amg=dict()),
+    # the paper's production preconditioner (Example 4): BiCGSTAB + CPR-FPF (Alg. 7) whose F stage
+    # is RAS with one layer of overlap (4 x 4 x 2 block subdomains) and whose P stage is AMG
+    "cpr_fpf_ras_amg_bicgstab_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0,
+                                                     solver="bicgstab", precond="cpr", prec="mixed", form="fpf",
+                                                     pstage="amg", amg=dict(),
+                                                     ras=dict(parts=(4, 4, 2), overlap=1, level=0)),
     # restricted additive Schwarz (Sec. 4.1) with the paper's defaults (Fig. 31): one layer of
     # overlap, ILU(1) local solver; 8 x 8 x 4 boxes of 16^3 cells
     "gmres_ras_ilu1_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="gmres", precond="ras",
@@ -158,7 +164,7 @@ def kernel_model(w, A_host, ras_sizes=None):
         nb, nnzb = A_host["nb"], A_host["bcol"].size
         mod = {"spmv": 76 * nnzb + 4 * (nb + 1) + 48 * nb}
         mod.update(scalar_ilu_bytes(nb, nnzb, vb))
-        mod.update(block_ilu_bytes(nb, nnzb, vb))
+        mod.update(block_ilu_bytes(*(ras_sizes or (nb, nnzb)), vb))
         return mod, 3 * nb
     n, nnz = A_host["n"], A_host["col"].size
     mod = {"spmv": 12 * nnz + 4 * (n + 1) + 16 * n}
@@ -166,11 +172,17 @@ def kernel_model(w, A_host, ras_sizes=None):
     return mod, n
 
 
+def box_partition(grid, parts):
+    """Subdomain of every cell (x fastest) for px x py x pz boxes of the grid."""
+    (nx, ny, nz), (px, py, pz) = grid, parts
+    bx, by, bz = np.arange(nx) * px // nx, np.arange(ny) * py // ny, np.arange(nz) * pz // nz
+    return ((bz[:, None, None] * py + by[None, :, None]) * px + bx[None, None, :]).reshape(-1).astype(np.int32)
+
+
 def ras_kwargs(w):
     """Precond arguments of a RAS workload: box subdomains of the grid."""
-    import paper_1701_05913_gb300 as rs
     r = w["ras"]
-    return dict(nparts=int(np.prod(r["parts"])), part=rs.box_partition(w["grid"], r["parts"]),
+    return dict(nparts=int(np.prod(r["parts"])), part=box_partition(w["grid"], r["parts"]),
                 overlap=r["overlap"], level=r["level"])
 
 
@@ -358,7 +370,11 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
     elif w["precond"] == "amg":
         M = oracle.PC(A, "amg", amg=w["amg"])
     elif w.get("pstage") == "amg":
-        M = oracle.PC(A, "cpr", mixed=mixed, form=w.get("form", "pf"), amg=w["amg"])
+        kr = {}
+        if "ras" in w:
+            k = ras_kwargs(w)
+            kr = dict(ras=dict(nsub=k["nparts"], part=k["part"], overlap=k["overlap"], level=k["level"]))
+        M = oracle.PC(A, "cpr", mixed=mixed, form=w.get("form", "pf"), amg=w["amg"], **kr)
     elif w["precond"] == "ras":
         k = ras_kwargs(w)
         M = oracle.PC(A, "ras", ras=dict(nsub=k["nparts"], part=k["part"], overlap=k["overlap"], level=k["level"]))
@@ -474,7 +490,7 @@ class Case:
         kw = dict(form=w["form"]) if "form" in w else {}
         if w["precond"] == "cpr_learned":
             kw.update(net=net, log_perm=A_host["logk"], grid=w["grid"])
-        if w["precond"] == "ras":
+        if "ras" in w:
             kw.update(ras_kwargs(w))
         if "amg" in w:
             kw.update(amg=w["amg"], **({"pstage": w["pstage"]} if "pstage" in w else {}))
@@ -594,7 +610,7 @@ def run_gpu(args, w, rank, world, local):
 
     # roofline of the dominant kernel class, from the live profile
     hbm, bf16, peak_src = measured_peaks()
-    model, nunk = kernel_model(w, cases[0].A_host, cases[0].M.ras_info() if w["precond"] == "ras" else None)
+    model, nunk = kernel_model(w, cases[0].A_host, cases[0].M.ras_info() if "ras" in w else None)
     iters = [i["iters"] for i in infos]
     cb = cgs_bytes(nunk, iters)
     kern_ms = {k: v[0] for k, v in prof.items() if v[1] > 0}
@@ -649,7 +665,8 @@ def run_gpu(args, w, rank, world, local):
                        "solver": w["solver"] + ("(30,%d)" % w["aug_k"] if "aug_k" in w else "(30)")
                        if "gmres" in w["solver"] else w["solver"],
                        "precond": w["precond"] + ("-" + w["form"] if "form" in w else "")
-                       + ("+amg" if w.get("pstage") == "amg" else ""),
+                       + ("+amg" if w.get("pstage") == "amg" else "")
+                       + ("+ras" if "ras" in w and w["precond"] != "ras" else ""),
                        "precision": w["prec"], "rtol": RTOL, "seeds": [seeds[0], seeds[-1]],
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": "replicas" if world > 1 else "1 gpu",

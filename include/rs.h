@@ -210,7 +210,9 @@ int rs_mat_amxpby(double a, const rs_mat *A, const rs_vec *x, double b, rs_vec *
  * RS_PC_CPR a BSR matrix (quasi-IMPES pressure restriction, ILU(0) of the
  * decoupled pressure matrix, block ILU(0) of A) or a CSR matrix (pressure
  * stage on A itself, second stage ILU(0)); opts->cpr_form picks the order
- * of the stages (Algs. 5-8).  opts may be NULL (FP64, CPR-PF).
+ * of the stages (Algs. 5-8), opts->cpr_pstage the pressure stage, and
+ * opts->ras_nparts > 1 (or ras_part) makes the F stage R(A)^{-1} restricted
+ * additive Schwarz over those (block) subdomains instead of block ILU(0).  opts may be NULL (FP64, CPR-PF).
  * Returns RS_ERR_ZERO_PIVOT when a factorisation meets a zero pivot and
  * RS_ERR_INVALID_ARG for an unknown cpr_form. */
 int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs_pc_opts *opts,

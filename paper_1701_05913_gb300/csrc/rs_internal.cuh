@@ -220,6 +220,7 @@ struct rs_pc {
     int *app_ptr_unused;
     double *app_val;         // decoupled pressure matrix values (block pattern)
     double *w;               // quasi-IMPES weights [nb*(bs-1)]
+    int *diagA;              // diagonal block positions of A (CPR with a RAS F stage)
     double *rp, *zp;         // pressure-stage vectors [nb]
     double *t1, *t2;         // full-size work vectors [n]
     // learned pressure stage

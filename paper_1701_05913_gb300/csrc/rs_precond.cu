@@ -83,7 +83,8 @@ static int cpr_stage(rs_pc *M, char kind, const double *v, double *out, const in
 {
     rs_ctx *ctx = M->ctx;
     const rs_mat *A = M->A;
-    if (kind == 'F') return rs_ilu_apply(M->bilu, v, out, nullptr, skip);
+    if (kind == 'F')
+        return M->ras ? rs_ras_apply(M->ras, v, out, skip) : rs_ilu_apply(M->bilu, v, out, nullptr, skip);
     const int nb = A->nrows, bs = A->bs;
     const double *rp = v;
     if (bs > 1) {
@@ -147,6 +148,7 @@ static void pc_free(rs_pc *M)
     if (M->ras) rs_ras_destroy(M->ras);
     if (M->amg) rs_amg_destroy(M->amg);
     rs_free(ctx, M->app_val);
+    rs_free(ctx, M->diagA);
     rs_free(ctx, M->w);
     rs_free(ctx, M->rp);
     rs_free(ctx, M->zp);
@@ -236,18 +238,29 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
             st = RS_ERR_INVALID_ARG;
             break;
         }
-        st = rs_ilu_create(ctx, bs, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
-        if (!st) st = rs_ilu_factor(M->bilu, A->val, &bad);
+        // the F stage R(A)^{-1}: block ILU(0) of A, or restricted additive
+        // Schwarz over block subdomains when subdomains are given
+        const bool fras = opts && (opts->ras_nparts > 1 || opts->ras_part);
+        if (fras)
+            st = rs_ras_create(ctx, A, opts->ras_nparts ? opts->ras_nparts : 1, opts->ras_part, opts->ras_overlap,
+                               opts->ilu_level, fp32, &M->ras, &bad);
+        else
+            st = rs_ilu_create(ctx, bs, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
+        if (!st && !fras) st = rs_ilu_factor(M->bilu, A->val, &bad);
         if (st) break;
         st = rs_alloc(ctx, (void **)&M->t1, sizeof(double) * (A->n > 0 ? A->n : 1));
         if (!st) st = rs_alloc(ctx, (void **)&M->t2, sizeof(double) * (A->n > 0 ? A->n : 1));
         if (st) break;
         if (bs == 1) {
             // pressure stage on A itself: its ILU(0), or an AMG V-cycle
-            if (pstage == 1 && type == RS_PC_CPR)
+            if (pstage == 1 && type == RS_PC_CPR) {
                 st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, A->val, A, th, lev, ncoarse, nu, &M->amg);
-            else
+            } else if (fras) {
+                st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
+                if (!st) st = rs_ilu_factor(M->ilu, A->val, &bad);
+            } else {
                 M->ilu = M->bilu;
+            }
             break;
         }
         st = rs_alloc(ctx, (void **)&M->w, sizeof(double) * (size_t)nb * (bs - 1));
@@ -255,8 +268,23 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         if (!st) st = rs_alloc(ctx, (void **)&M->rp, sizeof(double) * (nb > 0 ? nb : 1));
         if (!st) st = rs_alloc(ctx, (void **)&M->zp, sizeof(double) * (nb > 0 ? nb : 1));
         if (st) break;
+        if (!st && fras) {
+            // positions of the diagonal blocks, for the quasi-IMPES weights
+            std::vector<int> dp(nb, 0);
+            for (int I = 0; I < nb; ++I)
+                for (int q = A->h_ptr[I]; q < A->h_ptr[I + 1]; ++q)
+                    if (A->h_col[q] == I) dp[I] = q;
+            st = rs_alloc(ctx, (void **)&M->diagA, sizeof(int) * (nb > 0 ? nb : 1));
+            if (!st && nb > 0 &&
+                cudaMemcpyAsync(M->diagA, dp.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, ctx->stream) !=
+                    cudaSuccess)
+                st = RS_ERR_CUDA;
+            if (!st && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = RS_ERR_CUDA;
+        }
+        if (st) break;
         if (nb > 0) {
-            k_qimpes_weights<<<grid_for(ctx, nb), 256, 0, ctx->stream>>>(nb, bs, M->bilu->diagpos, A->val, M->w);
+            k_qimpes_weights<<<grid_for(ctx, nb), 256, 0, ctx->stream>>>(nb, bs, fras ? M->diagA : M->bilu->diagpos,
+                                                                        A->val, M->w);
             k_qimpes_app<<<grid_for(ctx, nb), 256, 0, ctx->stream>>>(nb, bs, A->ptr, A->val, M->w, M->app_val);
             st = rs_check_launch(ctx);
             ctx->launches++;

@@ -174,3 +174,27 @@ def test_ras_invalid_arguments(rs, ctx):
         with pytest.raises(rs.RsError) as e:
             rs.Precond(ctx, A, "ras", **kw)
         assert e.value.status == rs.ERR_INVALID_ARG, kw
+
+
+@pytest.mark.parametrize("form,pstage", [("pf", "ilu0"), ("fpf", "ilu0"), ("fpf", "amg")])
+def test_cpr_with_ras_f_stage(rs, ctx, orc, form, pstage):
+    """CPR whose F stage R(A)^{-1} is RAS over block subdomains (the paper's
+    CPR arrangement, Sec. 4.2.1), against the oracle's."""
+    g = synth.Grid(11, 9, 7)
+    m = synth.black_oil_bsr3(g, 57)
+    part = rs.box_partition((g.nx, g.ny, g.nz), (2, 2, 1))
+    Ao = orc.Mat.bsr(m)
+    kw = dict(amg=dict()) if pstage == "amg" else {}
+    Mo = orc.PC(Ao, "cpr", form=form, ras=dict(nsub=4, part=part, overlap=1), **kw)
+    A = rs.Mat.bsr(ctx, m)
+    M = rs.Precond(ctx, A, "cpr", form=form, nparts=4, part=part, overlap=1, pstage=pstage)
+    r = np.random.default_rng(58).standard_normal(A.n)
+    z = rs.Vec.zeros(ctx, A.n)
+    M.apply(rs.Vec(ctx, r), z)
+    assert rel(z.numpy(), Mo.apply(r)) <= 1e-12
+    b = orc.spmv(Ao, synth.x_true(A.n, 58))
+    xo, io, _ = orc.gmres(Ao, Mo, b, restart=30, rtol=1e-8, flexible=True)
+    x = rs.Vec.zeros(ctx, A.n)
+    info = rs.solve_fgmres(A, M, rs.Vec(ctx, b), x, restart=30, rtol=1e-8, maxit=10000)
+    assert info["status"] == 0 and io["status"] == 0 and info["true_rel_res"] <= 1e-8
+    assert abs(info["iters"] - io["iters"]) <= 2, (info, io)
