@@ -238,21 +238,23 @@ struct AmgHost {
     std::vector<std::vector<int>> cidx;
 };
 
+// The smoother multiplies by dinv = 1/d, formed once at setup: a divide on
+// every sweep would cost this GPU's FP64 pipe about ten times as much.
 // first sweep from x = 0:  x_i = b_i / d_i
-__global__ void k_amg_first(int n, const double *__restrict__ b, const double *__restrict__ d,
+__global__ void k_amg_first(int n, const double *__restrict__ b, const double *__restrict__ dinv,
                             double *__restrict__ x, const int *skip)
 {
     if (skip && *(volatile const int *)skip) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = b[i] / d[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = b[i] * dinv[i];
 }
 
 // x_i += t_i / d_i  with t = b - A x
-__global__ void k_amg_correct(int n, const double *__restrict__ t, const double *__restrict__ d,
+__global__ void k_amg_correct(int n, const double *__restrict__ t, const double *__restrict__ dinv,
                               double *__restrict__ x, const int *skip)
 {
     if (skip && *(volatile const int *)skip) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        x[i] = x[i] + t[i] / d[i];
+        x[i] = fma(t[i], dinv[i], x[i]);
 }
 
 // coarsest level: x = Ainv b, one warp per row
@@ -367,11 +369,11 @@ int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::v
             if (!st) st = rs_mat_create_rect(ctx, R.n, R.m, R.ptr.data(), R.col.data(), R.val.data(), &M->R[l]);
             if (st) break;
         }
-        std::vector<double> d(A.n);
+        std::vector<double> d(A.n);      // 1 / d_i, d_i = sum_j |a_ij|
         for (int i = 0; i < A.n; ++i) {
             double s = 0.0;
             for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) s += std::fabs(A.val[p]);
-            d[i] = s;
+            d[i] = 1.0 / s;
         }
         st = rs_alloc(ctx, (void **)&M->d[l], sizeof(double) * A.n);
         if (!st) st = rs_alloc(ctx, (void **)&M->b[l], sizeof(double) * A.n);

@@ -468,6 +468,9 @@ extern "C" int rs_vec_norm2(const rs_vec *x, double *out)
 // CSR: L lanes per row; each lane strides over the row's nonzeros, the group
 // adds its lanes with shuffles.  mode 0: y = alpha*Ax + beta*y;
 // mode 1: y = b - Ax (residual, b passed in `bvec`).
+// CSR, medium and long rows: L lanes per row, each lane taking 4 entries
+// per round with all their loads issued before the multiply-adds, so that a
+// row of up to 4 L entries needs one round of memory latency.
 template <int L>
 __global__ void __launch_bounds__(256)
 k_spmv_csr(int n, const int *__restrict__ ptr, const int *__restrict__ col,
@@ -482,7 +485,20 @@ k_spmv_csr(int n, const int *__restrict__ ptr, const int *__restrict__ col,
     double acc = 0.0;
     if (active) {
         const int s = ptr[row], e = ptr[row + 1];
-        for (int p = s + lane; p < e; p += L) acc = fma(val[p], __ldg(x + col[p]), acc);
+        for (int p0 = s + lane; p0 < e; p0 += 4 * L) {
+            int c[4];
+            double v[4], xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + u * L;
+                c[u] = p < e ? col[p] : -1;
+                v[u] = p < e ? val[p] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc = fma(v[u], xv[u], acc);
+        }
     }
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
@@ -652,7 +668,7 @@ static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double 
     rs_ctx *ctx = A->ctx;
     if (A->n == 0) return RS_OK;
     RsProfScope prof(ctx, RS_PROF_SPMV);
-    if (A->bs == 1 && A->lanes <= 8) {
+    if (A->bs == 1 && A->lanes == 1) {
         static unsigned long long raised = 0;   // devices whose shared-memory limit was raised
         const unsigned long long bit = 1ull << (ctx->device & 63);
         if (!(raised & bit)) {
@@ -782,10 +798,13 @@ static int mat_create(rs_ctx *ctx, int nrows, int bs, const int32_t *ptr, const 
         RS_CUDA_TRY(cudaMemcpyAsync(A->val, val, sizeof(double) * nnzb * bs * bs, h2d, ctx->stream));
     }
     if (mem == RS_MEM_HOST) RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    // lanes per row of the CSR kernel: the power of two nearest the mean row length
+    // rows of at most 12 entries on average go to the pipelined row-per-thread
+    // kernel (lanes = 1); longer ones to the lane kernel with the smallest
+    // power of two L for which 4 L entries cover the mean row
     const double mean = nrows ? (double)nnzb / nrows : 1.0;
     int L = 1;
-    while (L < 32 && L * 1.5 < mean) L <<= 1;
+    if (mean > 12.0)
+        while (L < 32 && 4.0 * L < mean) L <<= 1;
     A->lanes = L;
     rs_ctx_retain(ctx);
     *out = A;

@@ -107,7 +107,7 @@ struct rs_mat {
     int *ptr, *col;
     double *val;
     std::vector<int> h_ptr, h_col;   // host copy of the pattern (analysis)
-    int lanes;               // SpMV lanes per row (CSR)
+    int lanes;               // SpMV lanes per row (CSR; 1 = the pipelined row-per-thread kernel)
 };
 
 struct rs_vec {
@@ -195,7 +195,8 @@ struct RasData {
 };
 
 // Algebraic multigrid (rs_amg.cu): operators of every level as rs_mat,
-// l1-Jacobi diagonals, work vectors, dense inverse of the coarsest matrix.
+// reciprocals of the l1-Jacobi diagonals (d), work vectors, dense inverse of
+// the coarsest matrix.
 #define RS_AMG_MAXLEV 16
 #define RS_AMG_MAX_DENSE 4096
 struct AmgHost;
