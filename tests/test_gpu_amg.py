@@ -136,3 +136,33 @@ def test_amg_invalid_arguments(rs, ctx):
     with pytest.raises(rs.RsError) as e:
         rs.Precond(ctx, B, "amg")
     assert e.value.status == rs.ERR_INVALID_ARG
+
+
+def test_amg_degenerate_cases(rs, ctx, orc):
+    # below max_coarse: one level, the V-cycle is the dense solve
+    g = synth.Grid(6, 5, 4)
+    d = synth.pressure_7pt(g, 76)
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "amg")
+    assert len(M.amg_sizes()) == 1
+    r = np.random.default_rng(77).standard_normal(g.n)
+    z = rs.Vec.zeros(ctx, g.n)
+    M.apply(rs.Vec(ctx, r), z)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"]), shape=(g.n, g.n)).toarray()
+    assert rel(z.numpy(), np.linalg.solve(S, r)) <= 1e-12
+    # a diagonal matrix has no strong connections: no coarse points.  Up to
+    # 4096 rows the single level is solved densely; above, setup refuses it
+    for n, ok in ((3000, True), (5000, False)):
+        dg = dict(n=n, rowptr=np.arange(n + 1, dtype=np.int32), col=np.arange(n, dtype=np.int32),
+                  val=1.0 + np.arange(n, dtype=float))
+        D = rs.Mat.csr(ctx, dg)
+        if ok:
+            Md = rs.Precond(ctx, D, "amg")
+            rr = np.random.default_rng(78).standard_normal(n)
+            zz = rs.Vec.zeros(ctx, n)
+            Md.apply(rs.Vec(ctx, rr), zz)
+            assert rel(zz.numpy(), rr / dg["val"]) <= 1e-14
+        else:
+            with pytest.raises(rs.RsError) as e:
+                rs.Precond(ctx, D, "amg")
+            assert e.value.status == rs.ERR_INVALID_ARG

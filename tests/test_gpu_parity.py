@@ -570,3 +570,18 @@ def test_lgmres_invalid_arguments(rs, ctx):
     for kw in (dict(restart=60, aug_k=5), dict(restart=10, aug_k=-1)):
         with pytest.raises(rs.RsError):
             rs.solve_lgmres(A, None, b, x, rtol=1e-8, **kw)
+
+
+def test_lgmres_maxit_and_zero_rhs(rs, ctx, orc):
+    g, d = _problem((12, 10, 8), 84, 1.0)
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "ilu0")
+    b = synth.x_true(g.n, 84)
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_lgmres(A, M, vec(rs, ctx, b), x, restart=5, aug_k=2, rtol=1e-14, maxit=9)
+    assert info["status"] == rs.NOT_CONVERGED and info["iters"] == 9
+    xo, io = orc.lgmres(orc.Mat.csr(d), orc.PC(orc.Mat.csr(d), "ilu0"), b, restart=5, aug_k=2, rtol=1e-14, maxit=9)
+    assert io["iters"] == 9 and rel(x.numpy(), xo) <= 1e-10
+    x0 = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_lgmres(A, M, rs.Vec.zeros(ctx, g.n), x0, restart=5, aug_k=2, rtol=1e-8)
+    assert info["status"] == 0 and not x0.numpy().any()

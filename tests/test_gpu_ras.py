@@ -198,3 +198,44 @@ def test_cpr_with_ras_f_stage(rs, ctx, orc, form, pstage):
     info = rs.solve_fgmres(A, M, rs.Vec(ctx, b), x, restart=30, rtol=1e-8, maxit=10000)
     assert info["status"] == 0 and io["status"] == 0 and info["true_rel_res"] <= 1e-8
     assert abs(info["iters"] - io["iters"]) <= 2, (info, io)
+
+
+def test_ras_degenerate_cases(rs, ctx, orc):
+    g = synth.Grid(7, 6, 5)
+    d = synth.pressure_7pt(g, 59)
+    A = rs.Mat.csr(ctx, d)
+    Ao = orc.Mat.csr(d)
+    r = np.random.default_rng(60).standard_normal(g.n)
+    # more subdomains than used: empty parts are skipped
+    part = (np.arange(g.n) % 5 * 2).astype(np.int32)            # parts 0, 2, 4, 6, 8 of 10
+    for overlap in (0, 1):
+        M = rs.Precond(ctx, A, "ras", nparts=10, part=part, overlap=overlap)
+        z = rs.Vec.zeros(ctx, g.n)
+        M.apply(rs.Vec(ctx, r), z)
+        assert rel(z.numpy(), orc.Ras(Ao, 10, part=part, overlap=overlap).apply(r)) <= 1e-12
+    # overlap beyond the graph's diameter: every subdomain is the whole matrix,
+    # so every row takes the global ILU(0) solution
+    M = rs.Precond(ctx, A, "ras", nparts=3, overlap=50)
+    z = rs.Vec.zeros(ctx, g.n)
+    M.apply(rs.Vec(ctx, r), z)
+    _, _, lu = orc.ilu0(Ao)
+    assert rel(z.numpy(), orc.ilu0_solve(Ao, lu, r)) <= 1e-12
+    # a 1 x 1 system
+    one = dict(n=1, rowptr=np.array([0, 1], np.int32), col=np.array([0], np.int32), val=np.array([4.0]))
+    M1 = rs.Precond(ctx, rs.Mat.csr(ctx, one), "ras", nparts=1, overlap=1, level=1)
+    z1 = rs.Vec.zeros(ctx, 1)
+    M1.apply(rs.Vec(ctx, np.array([2.0])), z1)
+    assert z1.numpy()[0] == 0.5
+
+
+def test_cpr_ras_f_stage_on_a_scalar_matrix(rs, ctx, orc):
+    g = synth.Grid(10, 8, 6)
+    d = synth.pressure_7pt(g, 61, kz_scale=0.1)
+    part = rs.box_partition((g.nx, g.ny, g.nz), (2, 2, 2))
+    Ao = orc.Mat.csr(d)
+    Mo = orc.PC(Ao, "cpr", ras=dict(nsub=8, part=part, overlap=1))
+    M = rs.Precond(ctx, rs.Mat.csr(ctx, d), "cpr", nparts=8, part=part, overlap=1)
+    r = np.random.default_rng(62).standard_normal(g.n)
+    z = rs.Vec.zeros(ctx, g.n)
+    M.apply(rs.Vec(ctx, r), z)
+    assert rel(z.numpy(), Mo.apply(r)) <= 1e-12
