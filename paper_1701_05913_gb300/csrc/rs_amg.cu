@@ -24,7 +24,9 @@
 // Apply (on the GPU): one V-cycle from x = 0 (Alg. 4): nu sweeps, residual,
 // restriction, the next level, prolongation and correction, nu sweeps;
 // the coarsest level is one dense matrix-vector product.  Every operator is
-// an rs_mat, so the products run in the library's SpMV kernels.
+// an rs_mat, so the products run in the library's SpMV kernels; a smoothing
+// sweep is one SpMV whose epilogue forms x + (b - A x) / d into a second
+// buffer.
 #include <algorithm>
 #include <cmath>
 #include <queue>
@@ -248,13 +250,10 @@ __global__ void k_amg_first(int n, const double *__restrict__ b, const double *_
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = b[i] * dinv[i];
 }
 
-// x_i += t_i / d_i  with t = b - A x
-__global__ void k_amg_correct(int n, const double *__restrict__ t, const double *__restrict__ dinv,
-                              double *__restrict__ x, const int *skip)
+__global__ void k_amg_copy(int n, const double *__restrict__ a, double *__restrict__ x, const int *skip)
 {
     if (skip && *(volatile const int *)skip) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        x[i] = fma(t[i], dinv[i], x[i]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = a[i];
 }
 
 // coarsest level: x = Ainv b, one warp per row
@@ -288,6 +287,7 @@ void rs_amg_destroy(AmgData *M)
         rs_free(ctx, M->b[l]);
         rs_free(ctx, M->x[l]);
         rs_free(ctx, M->t[l]);
+        rs_free(ctx, M->y[l]);
     }
     rs_free(ctx, M->cinv);
     delete M->host;
@@ -379,6 +379,7 @@ int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::v
         if (!st) st = rs_alloc(ctx, (void **)&M->b[l], sizeof(double) * A.n);
         if (!st) st = rs_alloc(ctx, (void **)&M->x[l], sizeof(double) * A.n);
         if (!st) st = rs_alloc(ctx, (void **)&M->t[l], sizeof(double) * A.n);
+        if (!st && l > 0) st = rs_alloc(ctx, (void **)&M->y[l], sizeof(double) * A.n);
         if (!st && cudaMemcpyAsync(M->d[l], d.data(), sizeof(double) * A.n, cudaMemcpyHostToDevice, ctx->stream) !=
                        cudaSuccess)
             st = RS_ERR_CUDA;
@@ -410,29 +411,35 @@ static int vcycle(AmgData *M, int l, const double *b, double *x, const int *skip
         return rs_check_launch(ctx);
     }
     const int g = amg_grid(ctx, n);
+    const int nu = M->nu;
     double *t = M->t[l];
+    // Jacobi sweeps alternate between x and a second buffer; the first sweep
+    // (from x = 0) is placed so that the last pre-smoothing sweep lands in x
+    double *X = x, *Y = l == 0 ? M->x[0] : M->y[l];
+    double *cur = (nu - 1) % 2 == 0 ? X : Y, *oth = cur == X ? Y : X;
     {
         RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
-        k_amg_first<<<g, 256, 0, ctx->stream>>>(n, b, M->d[l], x, skip);
+        k_amg_first<<<g, 256, 0, ctx->stream>>>(n, b, M->d[l], cur, skip);
     }
     RS_TRY(rs_check_launch(ctx));
-    for (int s = 1; s < M->nu; ++s) {
-        RS_TRY(rs_residual_launch(A, b, x, t, nullptr, skip));
-        {
-            RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
-            k_amg_correct<<<g, 256, 0, ctx->stream>>>(n, t, M->d[l], x, skip);
-        }
-        RS_TRY(rs_check_launch(ctx));
+    for (int s = 1; s < nu; ++s) {
+        RS_TRY(rs_jacobi_launch(A, b, cur, M->d[l], oth, skip));
+        std::swap(cur, oth);
     }
-    RS_TRY(rs_residual_launch(A, b, x, t, nullptr, skip));
+    RS_TRY(rs_residual_launch(A, b, X, t, nullptr, skip));
     RS_TRY(rs_spmv_launch(M->R[l], t, 1.0, 0.0, M->b[l + 1], skip));
     RS_TRY(vcycle(M, l + 1, M->b[l + 1], M->x[l + 1], skip));
-    RS_TRY(rs_spmv_launch(M->P[l], M->x[l + 1], 1.0, 1.0, x, skip));
-    for (int s = 0; s < M->nu; ++s) {
-        RS_TRY(rs_residual_launch(A, b, x, t, nullptr, skip));
+    RS_TRY(rs_spmv_launch(M->P[l], M->x[l + 1], 1.0, 1.0, X, skip));
+    cur = X;
+    oth = Y;
+    for (int s = 0; s < nu; ++s) {
+        RS_TRY(rs_jacobi_launch(A, b, cur, M->d[l], oth, skip));
+        std::swap(cur, oth);
+    }
+    if (cur != X) {       // an odd number of post-smoothing sweeps
         {
             RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
-            k_amg_correct<<<g, 256, 0, ctx->stream>>>(n, t, M->d[l], x, skip);
+            k_amg_copy<<<g, 256, 0, ctx->stream>>>(n, cur, X, skip);
         }
         RS_TRY(rs_check_launch(ctx));
     }

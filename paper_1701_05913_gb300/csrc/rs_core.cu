@@ -475,7 +475,8 @@ template <int L>
 __global__ void __launch_bounds__(256)
 k_spmv_csr(int n, const int *__restrict__ ptr, const int *__restrict__ col,
            const double *__restrict__ val, const double *__restrict__ x, double alpha, double beta,
-           const double *__restrict__ bvec, double *__restrict__ y, const int *skip)
+           const double *__restrict__ bvec, double *__restrict__ y, const int *skip,
+           const double *__restrict__ dinv)
 {
     if (skip && *(volatile const int *)skip) return;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -503,7 +504,8 @@ k_spmv_csr(int n, const int *__restrict__ ptr, const int *__restrict__ col,
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
     if (active && lane == 0) {
-        if (bvec) y[row] = __dsub_rn(bvec[row], acc);
+        if (dinv) y[row] = fma(__dsub_rn(bvec[row], acc), dinv[row], x[row]);   // Jacobi-type sweep
+        else if (bvec) y[row] = __dsub_rn(bvec[row], acc);
         else if (beta == 0.0) y[row] = alpha == 1.0 ? acc : __dmul_rn(alpha, acc);
         else y[row] = fma(alpha, acc, beta * y[row]);
     }
@@ -535,7 +537,8 @@ static_assert(sizeof(SpmvStage) % 16 == 0, "stages stay 16-byte aligned");
 __global__ void __launch_bounds__(RS_SPMV_THREADS)
 k_spmv_csr_pipe(int n, const int *__restrict__ ptr, const int *__restrict__ col, const double *__restrict__ val,
                 const double *__restrict__ x, double alpha, double beta, const double *__restrict__ bvec,
-                double *__restrict__ y, const int *skip, int *err, long long limit)
+                double *__restrict__ y, const int *skip, int *err, long long limit,
+                const double *__restrict__ dinv)
 {
     if (skip && *(volatile const int *)skip) return;
     extern __shared__ __align__(128) unsigned char spmv_smem[];
@@ -609,7 +612,8 @@ k_spmv_csr_pipe(int n, const int *__restrict__ ptr, const int *__restrict__ col,
                 if (R.a + q < R.b) acc = fma(direct ? val[R.a + q] : st.val[R.a + q - va], R.xv[q], acc);
             for (int p = R.a + 8; p < R.b; ++p)   // rows longer than 8
                 acc = fma(direct ? val[p] : st.val[p - va], __ldg(x + (direct ? col[p] : st.col[p - ca])), acc);
-            if (bvec) y[r] = __dsub_rn(bvec[r], acc);
+            if (dinv) y[r] = fma(__dsub_rn(bvec[r], acc), dinv[r], x[r]);   // Jacobi-type sweep
+            else if (bvec) y[r] = __dsub_rn(bvec[r], acc);
             else if (beta == 0.0) y[r] = alpha == 1.0 ? acc : __dmul_rn(alpha, acc);
             else y[r] = fma(alpha, acc, beta * y[r]);
         }
@@ -662,8 +666,10 @@ k_spmv_bsr(int nb, int bsr, const int *__restrict__ ptr, const int *__restrict__
     else y[t] = fma(alpha, acc, beta * y[t]);
 }
 
+// y = alpha A x + beta y, y = b - A x (bvec), or with dinv the sweep
+// y = x + (b - A x) dinv (y must not alias x)
 static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double beta,
-                         const double *bvec, double *y, const int *skip)
+                         const double *bvec, double *y, const int *skip, const double *dinv = nullptr)
 {
     rs_ctx *ctx = A->ctx;
     if (A->n == 0) return RS_OK;
@@ -679,7 +685,7 @@ static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double 
         const int tiles = (A->n + RS_SPMV_TILE - 1) / RS_SPMV_TILE;
         const int grid = std::max(1, std::min(tiles, 3 * ctx->num_sms));
         k_spmv_csr_pipe<<<grid, RS_SPMV_THREADS, RS_SPMV_SMEM, ctx->stream>>>(
-            A->n, A->ptr, A->col, A->val, x, alpha, beta, bvec, y, skip, ctx->d_err, ctx->spin_limit);
+            A->n, A->ptr, A->col, A->val, x, alpha, beta, bvec, y, skip, ctx->d_err, ctx->spin_limit, dinv);
     } else if (A->bs == 1) {
         const int L = A->lanes;
         const int64_t threads = (int64_t)A->n * L;
@@ -688,7 +694,7 @@ static int spmv_dispatch(const rs_mat *A, const double *x, double alpha, double 
 #define RS_SPMV_CASE(LL)                                                                    \
     case LL:                                                                                \
         k_spmv_csr<LL><<<grid, 256, 0, ctx->stream>>>(A->n, A->ptr, A->col, A->val, x, alpha, \
-                                                      beta, bvec, y, skip);                 \
+                                                      beta, bvec, y, skip, dinv);           \
         break;
             RS_SPMV_CASE(1)
             RS_SPMV_CASE(2)
@@ -719,6 +725,13 @@ int rs_spmv_launch(const rs_mat *A, const double *x, double alpha, double beta, 
                    const int *skip)
 {
     return spmv_dispatch(A, x, alpha, beta, nullptr, y, skip);
+}
+
+int rs_jacobi_launch(const rs_mat *A, const double *b, const double *x, const double *dinv, double *xnew,
+                     const int *skip)
+{
+    if (A->bs != 1) return RS_ERR_INVALID_ARG;
+    return spmv_dispatch(A, x, 1.0, 0.0, b, xnew, skip, dinv);
 }
 
 int rs_residual_launch(const rs_mat *A, const double *b, const double *x, double *r,

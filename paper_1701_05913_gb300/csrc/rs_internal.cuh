@@ -206,6 +206,7 @@ struct AmgData {
     bool own0 = false;           // level-0 matrix built here (not the caller's)
     rs_mat *A[RS_AMG_MAXLEV] = {}, *P[RS_AMG_MAXLEV] = {}, *R[RS_AMG_MAXLEV] = {};
     double *d[RS_AMG_MAXLEV] = {}, *b[RS_AMG_MAXLEV] = {}, *x[RS_AMG_MAXLEV] = {}, *t[RS_AMG_MAXLEV] = {};
+    double *y[RS_AMG_MAXLEV] = {};   // second smoothing buffer (level 0 uses x[0])
     double *cinv = nullptr;
     AmgHost *host = nullptr;     // the hierarchy on the host (export)
 };
@@ -252,6 +253,10 @@ int rs_mat_create_rect(rs_ctx *ctx, int nrows, int ncols, const int32_t *ptr, co
 // non-null `skip` return at once when *skip != 0 (a device flag).
 int rs_spmv_launch(const rs_mat *A, const double *x, double alpha, double beta, double *y,
                    const int *skip);
+// one sweep xnew = x + (b - A x) dinv, fused into the SpMV (CSR; xnew must
+// not alias x)
+int rs_jacobi_launch(const rs_mat *A, const double *b, const double *x, const double *dinv, double *xnew,
+                     const int *skip);
 // r = b - A x and, if norm2_out != nullptr, *norm2_out (device) = ||r||^2
 int rs_residual_launch(const rs_mat *A, const double *b, const double *x, double *r,
                        double *norm2_out, const int *skip);
