@@ -290,6 +290,8 @@ void rs_amg_destroy(AmgData *M)
         rs_free(ctx, M->y[l]);
     }
     rs_free(ctx, M->cinv);
+    for (const AmgGraph &g : M->graphs) cudaGraphExecDestroy(g.exec);
+    if (M->capture) cudaStreamDestroy(M->capture);
     delete M->host;
     delete M;
 }
@@ -446,9 +448,54 @@ static int vcycle(AmgData *M, int l, const double *b, double *x, const int *skip
     return RS_OK;
 }
 
+// A V-cycle is some 60 small launches on its coarse levels; after the first
+// apply, each (r, z, skip) address triple is captured once into a CUDA
+// graph and replayed.  Capture runs on a private stream (the caller's may be
+// the legacy default stream, which cannot be captured); replays go to the
+// caller's stream.  With the profiler on, or if a capture fails, the
+// V-cycle is launched kernel by kernel.
 int rs_amg_apply(AmgData *M, const double *r, double *z, const int *skip)
 {
-    return vcycle(M, 0, r, z, skip);
+    rs_ctx *ctx = M->ctx;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (ctx->prof_on || M->nograph || cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone)
+        return vcycle(M, 0, r, z, skip);
+    for (const AmgGraph &g : M->graphs)
+        if (g.r == r && g.z == z && g.skip == skip) {
+            if (cudaGraphLaunch(g.exec, ctx->stream) != cudaSuccess) return RS_ERR_CUDA;
+            ctx->launches += g.nlaunch;
+            return RS_OK;
+        }
+    if (M->applies++ == 0 || (int)M->graphs.size() >= RS_AMG_MAX_GRAPHS) return vcycle(M, 0, r, z, skip);
+    if (!M->capture && cudaStreamCreateWithFlags(&M->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        M->nograph = true;
+        return vcycle(M, 0, r, z, skip);
+    }
+    const long long l0 = ctx->launches;
+    cudaStream_t user = ctx->stream;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int st = RS_ERR_CUDA;
+    if (cudaStreamBeginCapture(M->capture, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        ctx->stream = M->capture;
+        st = vcycle(M, 0, r, z, skip);
+        ctx->stream = user;
+        const cudaError_t e = cudaStreamEndCapture(M->capture, &graph);
+        if (e != cudaSuccess) st = RS_ERR_CUDA;
+    }
+    if (!st && (!graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)) st = RS_ERR_CUDA;
+    if (graph) cudaGraphDestroy(graph);
+    if (st) {
+        cudaGetLastError();
+        M->nograph = true;
+        ctx->launches = l0;
+        return vcycle(M, 0, r, z, skip);
+    }
+    M->graphs.push_back({r, z, skip, exec, ctx->launches - l0});
+    // the capture has counted the graph's launches once; this is their run
+    return cudaGraphLaunch(exec, user) == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
 int rs_amg_level_sizes(const AmgData *M, int l, int32_t *n, int64_t *nnz_a, int64_t *nnz_p)

@@ -200,6 +200,16 @@ struct RasData {
 #define RS_AMG_MAXLEV 16
 #define RS_AMG_MAX_DENSE 4096
 struct AmgHost;
+// one captured V-cycle: its input, output and skip flag addresses, the
+// executable graph and the number of kernels it launches
+struct AmgGraph {
+    const double *r;
+    double *z;
+    const int *skip;
+    cudaGraphExec_t exec;
+    long long nlaunch;
+};
+#define RS_AMG_MAX_GRAPHS 64
 struct AmgData {
     rs_ctx *ctx = nullptr;
     int nlev = 0, nu = 2;
@@ -209,6 +219,10 @@ struct AmgData {
     double *y[RS_AMG_MAXLEV] = {};   // second smoothing buffer (level 0 uses x[0])
     double *cinv = nullptr;
     AmgHost *host = nullptr;     // the hierarchy on the host (export)
+    std::vector<AmgGraph> graphs;
+    cudaStream_t capture = nullptr;   // private stream for stream capture
+    long long applies = 0;
+    bool nograph = false;        // a capture failed: launch directly from then on
 };
 
 struct rs_pc {
