@@ -125,6 +125,17 @@ int rs_init(rs_ctx **ctx, int device, void *cuda_stream);
 int rs_finalize(rs_ctx **ctx);
 /* Waits for all work enqueued on the context's stream. */
 int rs_sync(rs_ctx *ctx);
+/* Every device-side wait of the library (a kernel polling for a value, a
+ * level or a copy) gives up after this many clock cycles, records
+ * RS_ERR_DEVICE_TIMEOUT in the context's device error word and returns; the
+ * context stays usable.  cycles = 0 restores the default (about two
+ * seconds); negative is RS_ERR_INVALID_ARG. */
+int rs_set_spin_limit(rs_ctx *ctx, int64_t cycles);
+/* Synchronises the stream, then reads and clears the device error word:
+ * RS_OK, RS_ERR_DEVICE_TIMEOUT (a bounded wait gave up since the last
+ * check), RS_ERR_ZERO_PIVOT or RS_ERR_CUDA.  The solvers check it
+ * themselves; a caller of the preconditioner applies alone uses this. */
+int rs_check_device(rs_ctx *ctx);
 const char *rs_status_str(int status);
 /* Number of kernels this library has launched on the context so far. */
 int64_t rs_launch_count(const rs_ctx *ctx);

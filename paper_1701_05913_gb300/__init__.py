@@ -72,6 +72,8 @@ SIGNATURES = [
     ("rs_init", C.c_int, [C.POINTER(_vp), C.c_int, _vp]),
     ("rs_finalize", C.c_int, [C.POINTER(_vp)]),
     ("rs_sync", C.c_int, [_vp]),
+    ("rs_set_spin_limit", C.c_int, [_vp, C.c_int64]),
+    ("rs_check_device", C.c_int, [_vp]),
     ("rs_status_str", C.c_char_p, [C.c_int]),
     ("rs_launch_count", C.c_int64, [_vp]),
     ("rs_prof_enable", C.c_int, [_vp, C.c_int]),
@@ -231,6 +233,14 @@ class Context:
         cnt = (C.c_int64 * k)()
         _check(lib().rs_prof_read(self.h, ms, cnt, k, int(reset)), "rs_prof_read")
         return {name: (ms[i], cnt[i]) for i, name in enumerate(self.PROF_KINDS)}
+
+    def set_spin_limit(self, cycles: int):
+        """Clock cycles a device-side wait may take before it gives up (0: default)."""
+        _check(lib().rs_set_spin_limit(self.h, cycles), "rs_set_spin_limit")
+
+    def check(self) -> int:
+        """Read and clear the device error word: OK or ERR_DEVICE_TIMEOUT, ..."""
+        return lib().rs_check_device(self.h)
 
     def close(self):
         if self.h:

@@ -160,6 +160,25 @@ extern "C" int rs_finalize(rs_ctx **pc)
     return RS_OK;
 }
 
+extern "C" int rs_set_spin_limit(rs_ctx *ctx, int64_t cycles)
+{
+    if (!ctx || cycles < 0) return RS_ERR_INVALID_ARG;
+    if (cycles > 0) {
+        ctx->spin_limit = cycles;
+    } else {
+        int clock_khz = 2000000;
+        cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, ctx->device);
+        ctx->spin_limit = (long long)clock_khz * 1000LL * 2;
+    }
+    return RS_OK;
+}
+
+extern "C" int rs_check_device(rs_ctx *ctx)
+{
+    if (!ctx) return RS_ERR_INVALID_ARG;
+    return rs_collect_device_error(ctx, nullptr);
+}
+
 extern "C" int rs_sync(rs_ctx *ctx)
 {
     if (!ctx) return RS_ERR_INVALID_ARG;

@@ -585,3 +585,30 @@ def test_lgmres_maxit_and_zero_rhs(rs, ctx, orc):
     x0 = rs.Vec.zeros(ctx, g.n)
     info = rs.solve_lgmres(A, M, rs.Vec.zeros(ctx, g.n), x0, restart=5, aug_k=2, rtol=1e-8)
     assert info["status"] == 0 and not x0.numpy().any()
+
+
+def test_device_wait_timeout_is_reported_and_the_context_survives(rs, ctx, orc):
+    """Failure detection without a GPU fault: with a one-cycle limit the
+    sweeps' polls give up at their second look, record the timeout and
+    return (the values carried on are NaN, the indices come from the
+    layout); the status reaches the host and the context stays usable."""
+    g, d = _problem((48, 48, 24), 85, 0.1)
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "ilu0")
+    r = synth.x_true(g.n, 85)
+    assert ctx.check() == rs.OK
+    ctx.set_spin_limit(1)
+    try:
+        M.apply(vec(rs, ctx, r), rs.Vec.zeros(ctx, g.n))     # triangular sweeps only
+        st = ctx.check()
+    finally:
+        ctx.set_spin_limit(0)
+    assert st == rs.ERR_DEVICE_TIMEOUT
+    assert ctx.check() == rs.OK                               # read and cleared
+    M2 = rs.Precond(ctx, A, "ilu0")
+    z = rs.Vec.zeros(ctx, g.n)
+    M2.apply(vec(rs, ctx, r), z)
+    Ao = orc.Mat.csr(d)
+    _, _, lu = orc.ilu0(Ao)
+    assert rel(z.numpy(), orc.ilu0_solve(Ao, lu, r)) <= 1e-12
+    assert ctx.check() == rs.OK
