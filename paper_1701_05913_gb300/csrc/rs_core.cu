@@ -94,9 +94,10 @@ extern "C" int rs_init(rs_ctx **out, int device, void *stream)
         const int v = atoi(e);
         if (v >= 0 && v <= 100000) c->sleep_cap_ns = (unsigned)v;
     }
+    c->sweep_blocks_fixed = 0;
     if (const char *e = getenv("RS_SWEEP_BLOCKS_PER_SM")) {
         const int v = atoi(e);
-        if (v >= 1 && v <= 16) c->sweep_blocks = v * c->num_sms;
+        if (v >= 1 && v <= 16) c->sweep_blocks = v * c->num_sms, c->sweep_blocks_fixed = 1;
     }
     // the stream-ordered pool keeps freed blocks for reuse
     cudaMemPool_t pool;

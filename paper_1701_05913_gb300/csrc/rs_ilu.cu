@@ -980,6 +980,19 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
     int st = build_layout(ctx, nrows, h_ptr, h_col, diag, f->L);
     st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, f->SL);
     st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, f->SU);
+    // sweep blocks: a single dependency chain (global ILU in natural order)
+    // gains nothing from more warps, which only add polling; many
+    // independent chains (the stacked subdomains of RAS) do.  Aim at three
+    // warps per segment of a level, between 4 and 8 blocks per SM.
+    for (SegLayout *S : {&f->SL, &f->SU}) {
+        const int wpb = RS_SWEEP_THREADS / 32;
+        const int64_t per_level = S->nlevels > 0 ? (int64_t)S->nseg / S->nlevels : 0;
+        int64_t g = (3 * per_level + wpb - 1) / wpb;
+        g = std::max<int64_t>(g, ctx->sweep_blocks);
+        if (!ctx->sweep_blocks_fixed) g = std::min<int64_t>(g, (int64_t)8 * ctx->num_sms);
+        else g = ctx->sweep_blocks;
+        S->grid = (int)g;
+    }
     st = st ? st : rs_alloc(ctx, &f->SL.val, esz * b2 * (f->SL.nent > 0 ? f->SL.nent : 1));
     st = st ? st : rs_alloc(ctx, &f->SU.val, esz * b2 * (f->SU.nent > 0 ? f->SU.nent : 1));
     st = st ? st : rs_alloc(ctx, &f->SU.rdiag, esz * b2 * ((size_t)f->SU.nseg * 32 > 0 ? (size_t)f->SU.nseg * 32 : 1));
@@ -1121,8 +1134,8 @@ static int apply_seg(IluFactor *f, const double *r, double *z, const double *sca
     rs_ctx *ctx = f->ctx;
     T *y = (T *)f->ywork, *zt = (T *)f->zwork;
     const int wpb = RS_SWEEP_THREADS / 32;
-    const int gl = std::max(1, std::min((f->SL.nseg + wpb - 1) / wpb, ctx->sweep_blocks));
-    const int gu = std::max(1, std::min((f->SU.nseg + wpb - 1) / wpb, ctx->sweep_blocks));
+    const int gl = std::max(1, std::min((f->SL.nseg + wpb - 1) / wpb, f->SL.grid));
+    const int gu = std::max(1, std::min((f->SU.nseg + wpb - 1) / wpb, f->SU.grid));
     size_t sl = 0, su = 0;
     {
         const int e1 = sweep_smem<BS, T>(ctx, k_lsolve_seg<BS, T>, &sl);

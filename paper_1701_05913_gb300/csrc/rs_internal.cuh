@@ -74,7 +74,8 @@ struct rs_ctx {
     double *h_pinned;        // pinned host staging (64 doubles)
     long long launches;
     long long spin_limit;    // clock cycles a device-side wait may take
-    int sweep_blocks;        // resident blocks of the persistent triangular sweeps
+    int sweep_blocks;        // resident blocks of the persistent triangular sweeps (at least)
+    int sweep_blocks_fixed;  // set from the environment: overrides the per-factor choice
     unsigned sleep_cap_ns;   // longest back-off of a polling warp (0: none)
     // event profiler (off unless rs_prof_enable)
     int prof_on;
@@ -155,6 +156,7 @@ struct SegLayout {
     void *rdiag = nullptr;         // [bs*bs][nseg*32] U: 1 / u_ii or inv(U_II) by row
     int *adjsrc = nullptr;         // [nrows] index of the in-segment adjacent entry or -1
     void *mul = nullptr;           // [nseg][5][bs*bs][32] multipliers of the scan steps
+    int grid = 0;                  // sweep blocks: follows the segments per level
 };
 
 // ILU(0) / block ILU(0) of one matrix pattern.
