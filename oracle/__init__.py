@@ -109,7 +109,9 @@ def _declare(L):
     L.or_pc_apply.argtypes = [C.POINTER(_PC), C.c_int64, _f64p, _f64p]
     L.or_iluk_symbolic.argtypes = [C.c_int32, _i32p, _i32p, C.c_int32, C.POINTER(_i32p), C.POINTER(_i32p)]
     L.or_ras_setup.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _i32p, C.c_int32, C.c_int32,
-                               C.POINTER(C.c_void_p), _i32p]
+                               C.c_int32, C.c_int32, C.c_double, C.POINTER(C.c_void_p), _i32p]
+    L.or_ilut.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, C.c_double, C.POINTER(_i32p),
+                          C.POINTER(_i32p), C.POINTER(_f64p), _i32p]
     L.or_ras_free.argtypes = [C.c_void_p]
     L.or_ras_apply.argtypes = [C.c_void_p, _f64p, _f64p]
     L.or_ras_sizes.argtypes = [C.c_void_p, _i32p, C.POINTER(C.c_int64)]
@@ -317,6 +319,26 @@ def iluk_pattern(n, ptr, col, p):
     return optr, ocol
 
 
+def ilut(A: Mat, p: int, tol: float):
+    """ILUT(p, tol) of a CSR matrix: (status, bad_row, ptr, col, lu) in the
+    factor's own pattern (strict L, then U with its diagonal)."""
+    assert A.bs == 1
+    op, oc, ov = _i32p(), _i32p(), _f64p()
+    bad = C.c_int32(-1)
+    st = lib().or_ilut(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32), _p(A.val, C.c_double), p, tol,
+                       C.byref(op), C.byref(oc), C.byref(ov), C.byref(bad))
+    if st != OK:
+        return st, bad.value, None, None, None
+    n = A.nrows
+    ptr = np.ctypeslib.as_array(op, shape=(n + 1,)).copy()
+    nz = int(ptr[-1])
+    col = np.ctypeslib.as_array(oc, shape=(max(nz, 1),))[:nz].copy()
+    lu = np.ctypeslib.as_array(ov, shape=(max(nz, 1),))[:nz].copy()
+    for q in (op, oc, ov):
+        lib().free(C.cast(q, C.c_void_p))
+    return st, bad.value, ptr, col, lu
+
+
 def contiguous_partition(n, nsub):
     """Row i -> subdomain floor(i nsub / n): contiguous blocks of rows, the
     way the paper's MAP gives each process a range of rows."""
@@ -327,14 +349,16 @@ class Ras:
     """Restricted additive Schwarz with ILU(level) local solvers; on a block
     matrix the subdomains hold block rows and the local solver is block ILU."""
 
-    def __init__(self, A: Mat, nsub: int, part=None, overlap: int = 1, level: int = 0):
+    def __init__(self, A: Mat, nsub: int, part=None, overlap: int = 1, level: int = 0, ilut=None):
+        """ilut = (p, tol) selects ILUT(p, tol) local solvers instead of ILU(level)."""
         self.A = A
         self.part = _i32(contiguous_partition(A.nrows, nsub) if part is None else part)
         h = C.c_void_p()
         bad = C.c_int32(-1)
+        p, tol = ilut if ilut is not None else (0, 0.0)
         self.status = lib().or_ras_setup(A.nrows, A.bs, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
                                          _p(A.val, C.c_double), nsub, _p(self.part, C.c_int32), overlap,
-                                         level, C.byref(h), C.byref(bad))
+                                         level, 1 if ilut is not None else 0, p, tol, C.byref(h), C.byref(bad))
         self.bad = bad.value
         self.h = h
 

@@ -466,6 +466,130 @@ int or_iluk_symbolic(int32_t n, const int32_t *ptr, const int32_t *col, int32_t 
 }
 
 /* ------------------------------------------------------------------------ */
+/* ILUT(p, tol), a local solver of RAS (Sec. 4.1, Fig. 31: default p = -1,   */
+/* tol = 1e-3), as in Saad's book (the ILUT algorithm).  Row i:              */
+/*   w = a_i*;  tau = tol * ||a_i*||_2;                                     */
+/*   for k < i with w_k != 0, ascending: w_k = w_k / u_kk; if |w_k| < tau    */
+/*     drop it, else w_j -= w_k u_kj for the entries j > k of U row k;       */
+/*   drop the off-diagonal w_j with |w_j| < tau; keep the p largest of the   */
+/*   L part and of the U part (ties to the lower column), and the diagonal.  */
+/* p < 0: p_L and p_U are the numbers of entries row i of A has in each part.*/
+/* The factor is returned in its own pattern (sorted rows): strict lower     */
+/* part of L (unit diagonal implied), then U with its diagonal.              */
+/* ------------------------------------------------------------------------ */
+typedef struct { int32_t c; double v; } or_cv;
+static int cv_by_magnitude(const void *a, const void *b)
+{
+    const or_cv *x = (const or_cv *)a, *y = (const or_cv *)b;
+    const double ax = fabs(x->v), ay = fabs(y->v);
+    if (ax != ay) return ax > ay ? -1 : 1;
+    return x->c < y->c ? -1 : (x->c > y->c);
+}
+static int cv_by_column(const void *a, const void *b)
+{
+    const or_cv *x = (const or_cv *)a, *y = (const or_cv *)b;
+    return x->c < y->c ? -1 : (x->c > y->c);
+}
+
+int or_ilut(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, int32_t p, double tol,
+            int32_t **optr, int32_t **ocol, double **olu, int32_t *bad_row)
+{
+    *bad_row = -1;
+    int64_t cap = ptr[n] > 16 ? 2 * (int64_t)ptr[n] : 32, len = 0;
+    int32_t *rp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t *rc = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    double *rv = (double *)malloc(sizeof(double) * (size_t)cap);
+    int32_t *udiag = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));   /* position of u_kk */
+    double *w = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    char *nz = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    or_cv *buf = (or_cv *)malloc(sizeof(or_cv) * (size_t)(n > 0 ? n : 1));
+    int32_t *lowers = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));   /* sorted */
+    int st = OR_OK;
+    rp[0] = 0;
+    for (int32_t i = 0; i < n && st == OR_OK; ++i) {
+        int32_t cnt = 0, plo = 0, pup = 0, nlow = 0;
+        double nrm = 0.0;
+        for (int32_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+            const int32_t c = col[q];
+            w[c] = val[q];
+            nz[c] = 1;
+            list[cnt++] = c;
+            nrm += val[q] * val[q];
+            if (c < i) ++plo, lowers[nlow++] = c;
+            else if (c > i) ++pup;
+        }
+        nrm = sqrt(nrm);
+        const double tau = tol * nrm;
+        if (p >= 0) plo = pup = p;
+        /* elimination in ascending k over the row's lower entries, fill included:
+         * a new lower entry j > k is inserted behind k in sorted position */
+        for (int32_t t = 0; t < nlow; ++t) {
+            const int32_t k = lowers[t];
+            if (w[k] == 0.0) continue;
+            w[k] = w[k] / rv[udiag[k]];
+            if (fabs(w[k]) < tau) { w[k] = 0.0; continue; }
+            for (int32_t q = udiag[k] + 1; q < rp[k + 1]; ++q) {
+                const int32_t j = rc[q];
+                if (!nz[j]) {
+                    nz[j] = 1;
+                    w[j] = 0.0;
+                    list[cnt++] = j;
+                    if (j < i) {
+                        int32_t a = nlow++;
+                        while (lowers[a - 1] > j) { lowers[a] = lowers[a - 1]; --a; }
+                        lowers[a] = j;
+                    }
+                }
+                w[j] = w[j] - w[k] * rv[q];
+            }
+        }
+        /* dropping: the surviving lower entries go to buf[0 .. nl), the upper
+         * ones to buf[n - nu .. n) */
+        int32_t nl = 0, nu = 0;
+        double diag = 0.0;
+        for (int32_t a = 0; a < cnt; ++a) {
+            const int32_t c = list[a];
+            if (c == i) diag = w[c];
+            else if (w[c] != 0.0 && fabs(w[c]) >= tau) {
+                if (c < i) buf[nl++] = (or_cv){c, w[c]};
+                else buf[n - 1 - nu++] = (or_cv){c, w[c]};
+            }
+        }
+        /* the p largest of each part (ties to the lower column) */
+        qsort(buf, (size_t)nl, sizeof(or_cv), cv_by_magnitude);
+        qsort(buf + (n - nu), (size_t)nu, sizeof(or_cv), cv_by_magnitude);
+        const int32_t ul = n - nu;              /* first upper entry */
+        if (nl > plo) nl = plo;
+        if (nu > pup) nu = pup;
+        for (int32_t a = 0; a < nu; ++a) buf[nl + a] = buf[ul + a];   /* nl + a <= ul + a */
+        for (int32_t a = 0; a < cnt; ++a) { w[list[a]] = 0.0; nz[list[a]] = 0; }
+        if (!(diag != 0.0) || !isfinite(diag)) { *bad_row = i; st = OR_ZERO_PIVOT; break; }
+        while (len + nl + nu + 1 > cap) {
+            cap *= 2;
+            rc = (int32_t *)realloc(rc, sizeof(int32_t) * (size_t)cap);
+            rv = (double *)realloc(rv, sizeof(double) * (size_t)cap);
+        }
+        qsort(buf, (size_t)nl, sizeof(or_cv), cv_by_column);
+        for (int32_t a = 0; a < nl; ++a) { rc[len] = buf[a].c; rv[len] = buf[a].v; ++len; }
+        udiag[i] = (int32_t)len;
+        rc[len] = i;
+        rv[len] = diag;
+        ++len;
+        /* the kept upper entries, by column */
+        qsort(buf + nl, (size_t)nu, sizeof(or_cv), cv_by_column);
+        for (int32_t a = 0; a < nu; ++a) { rc[len] = buf[nl + a].c; rv[len] = buf[nl + a].v; ++len; }
+        rp[i + 1] = (int32_t)len;
+    }
+    free(w); free(nz); free(list); free(buf); free(udiag); free(lowers);
+    if (st != OR_OK) { free(rp); free(rc); free(rv); return st; }
+    *optr = rp;
+    *ocol = rc;
+    *olu = rv;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Restricted additive Schwarz (Sec. 4.1, after Cai and Sarkis).             */
 /* On a block matrix (bs > 1) rows are block rows and the local solver is    */
 /* block ILU(level) (block ILU(0) on the level-of-fill block pattern).       */
@@ -507,12 +631,16 @@ void or_ras_free(or_ras *R)
     free(R);
 }
 
+/* local = 0: ILU(level) local solvers; local = 1: ILUT(ilut_p, ilut_tol)
+ * (scalar matrices only) */
 int or_ras_setup(int32_t n, int32_t bs, const int32_t *ptr, const int32_t *col, const double *val, int32_t nsub,
-                 const int32_t *part, int32_t overlap, int32_t level, or_ras **out, int32_t *bad_row)
+                 const int32_t *part, int32_t overlap, int32_t level, int32_t local, int32_t ilut_p,
+                 double ilut_tol, or_ras **out, int32_t *bad_row)
 {
     *out = NULL;
     *bad_row = -1;
     if (nsub < 1 || overlap < 0 || level < 0 || bs < 1 || bs > 8) return OR_INVALID;
+    if (local != 0 && (local != 1 || bs != 1 || !(ilut_tol >= 0.0))) return OR_INVALID;
     const size_t b2 = (size_t)bs * bs;
     for (int32_t i = 0; i < n; ++i)
         if (part[i] < 0 || part[i] >= nsub) return OR_INVALID;
@@ -573,6 +701,16 @@ int or_ras_setup(int32_t n, int32_t bs, const int32_t *ptr, const int32_t *col, 
                     ++nz;
                 }
             ap[a + 1] = (int32_t)nz;
+        }
+        if (local == 1) {
+            /* ILUT: the factor and its pattern come from the values */
+            int32_t bad = -1;
+            st = or_ilut(ns, ap, ac, av, ilut_p, ilut_tol, &R->lptr[s], &R->lcol[s], &R->llu[s], &bad);
+            if (st != OR_OK) *bad_row = bad >= 0 ? er[bad] : -1;
+            free(ap);
+            free(ac);
+            free(av);
+            continue;
         }
         /* the ILU(level) pattern of A_s, with A_s's values and zeros at fill */
         int32_t *kp, *kc;

@@ -1129,3 +1129,79 @@ def test_cpr_with_ras_f_stage_is_the_composition(orc):
     z1 = orc.prolong(nb, bs, orc.ilu0_solve(App, lu, orc.qimpes_restrict(nb, bs, w, f)))
     want = z1 + orc.Ras(A, **ras).apply(f - orc.spmv(A, z1))
     assert np.allclose(M.apply(f), want, rtol=1e-14, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# ILUT(p, tol), the other local solver of RAS (Fig. 31)
+# ----------------------------------------------------------------------------
+def _ilut_dense(n, ptr, col, lu):
+    L, U = np.eye(n), np.zeros((n, n))
+    for i in range(n):
+        for q in range(ptr[i], ptr[i + 1]):
+            (L if col[q] < i else U)[i, col[q]] = lu[q]
+    return L, U
+
+
+def test_ilut_without_dropping_is_the_exact_lu(orc):
+    rng = np.random.default_rng(110)
+    n = 40
+    D = np.where(rng.random((n, n)) < 0.08, -rng.random((n, n)), 0.0)
+    np.fill_diagonal(D, 0.0)
+    np.fill_diagonal(D, np.abs(D).sum(axis=1) + 1.0)
+    st, _, ptr, col, lu = orc.ilut(orc.Mat.csr(csr_dict(D)), n, 0.0)
+    assert st == 0
+    L, U = _ilut_dense(n, ptr, col, lu)
+    P, Lr, Ur = sla.lu(D)
+    assert np.array_equal(P, np.eye(n))
+    assert np.allclose(L, Lr, atol=1e-14) and np.allclose(U, Ur, atol=1e-13)
+    assert ptr[-1] > csr_dict(D)["col"].size            # the fill was kept
+
+
+def test_ilut_special_cases(orc):
+    d = synth.pressure_7pt(synth.Grid(6, 5, 4), 111)
+    n = d["n"]
+    A = orc.Mat.csr(d)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"]), shape=(n, n)).toarray()
+    # every multiplier below a huge threshold: no elimination, no off-diagonal: Jacobi
+    st, _, ptr, col, lu = orc.ilut(A, 5, 1e30)
+    assert st == 0 and np.array_equal(col, np.arange(n)) and np.array_equal(lu, np.diag(S))
+    # a first row has nothing to eliminate: its U part keeps exactly its p largest entries
+    row = np.array([5.0, -0.5, 0.0, -2.0, 0.0, -1.0, -3.0, 0.0])
+    D = np.diag(np.full(8, 10.0))
+    D[0] = row
+    st, _, ptr, col, lu = orc.ilut(orc.Mat.csr(csr_dict(D)), 2, 0.0)
+    assert st == 0 and list(col[ptr[0]:ptr[1]]) == [0, 3, 6] and list(lu[ptr[0]:ptr[1]]) == [5.0, -2.0, -3.0]
+    # the dropping rule on a 3-D problem: kept entries reach tol ||a_i||, at most p per part
+    tol, p = 0.05, 2
+    st, _, ptr, col, lu = orc.ilut(A, p, tol)
+    assert st == 0
+    for i in range(n):
+        c, v = col[ptr[i]:ptr[i + 1]], lu[ptr[i]:ptr[i + 1]]
+        assert (np.diff(c) > 0).all() and i in c
+        off = c != i
+        assert (np.abs(v[off]) >= tol * np.linalg.norm(S[i])).all()
+        assert (c < i).sum() <= p and (c > i).sum() <= p
+    # a chain: ILUT without dropping is the exact LU (the Thomas algorithm)
+    d1 = csr_dict(poisson1d(30))
+    st, _, ptr, col, lu = orc.ilut(orc.Mat.csr(d1), -1, 0.0)
+    L, U = _ilut_dense(30, ptr, col, lu)
+    assert np.allclose(L @ U, poisson1d(30).toarray(), atol=1e-14)
+
+
+def test_ras_with_ilut_local_solvers(orc):
+    d = synth.pressure_7pt(synth.Grid(12, 10, 8), 112, kz_scale=0.1)
+    A = orc.Mat.csr(d)
+    S = sp.csr_matrix((d["val"], d["col"], d["rowptr"]))
+    r = synth.x_true(d["n"], 112)
+    # one subdomain without overlap is global ILUT
+    st, _, ptr, col, lu = orc.ilut(A, -1, 1e-3)
+    R = orc.Ras(A, 1, overlap=0, ilut=(-1, 1e-3))
+    gidx, ptr2, col2, lu2 = R.structure()
+    assert np.array_equal(ptr, ptr2) and np.array_equal(col, col2) and np.array_equal(lu, lu2)
+    # RAS with ILUT local solvers preconditions GMRES
+    b = S @ r
+    M = orc.PC(A, "ras", ras=dict(nsub=8, overlap=1, ilut=(-1, 1e-3)))
+    x, info, _ = orc.gmres(A, M, b, restart=30, rtol=1e-10)
+    assert info["status"] == 0
+    assert np.linalg.norm(b - S @ x) <= 1e-10 * np.linalg.norm(b) * 1.0001
+    assert orc.Ras(A, 2, ilut=(-1, -1.0)).status == orc.INVALID
