@@ -80,6 +80,9 @@ WORKLOADS = {
     # overlap, ILU(1) local solver; 8 x 8 x 4 boxes of 16^3 cells
     "gmres_ras_ilu1_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="gmres", precond="ras",
                                       prec="fp64", ras=dict(parts=(8, 8, 4), overlap=1, level=1)),
+    # the same boxes with ILUT(p, tol) local solvers at Fig. 31's defaults (p = -1, tol = 1e-3)
+    "gmres_ras_ilut_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="gmres", precond="ras",
+                                      prec="fp64", ras=dict(parts=(8, 8, 4), overlap=1, level=0, ilut=(-1, 1e-3))),
     # the paper's production pairing (Examples 2 and 4): BiCGSTAB + CPR-FPF (Alg. 7)
     "cpr_fpf_bicgstab_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="bicgstab",
                                              precond="cpr", prec="mixed", form="fpf"),
@@ -183,7 +186,7 @@ def ras_kwargs(w):
     """Precond arguments of a RAS workload: box subdomains of the grid."""
     r = w["ras"]
     return dict(nparts=int(np.prod(r["parts"])), part=box_partition(w["grid"], r["parts"]),
-                overlap=r["overlap"], level=r["level"])
+                overlap=r["overlap"], level=r["level"], **({"ilut": r["ilut"]} if "ilut" in r else {}))
 
 
 def amg_vcycle_model(w, sizes):
@@ -377,7 +380,8 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
         M = oracle.PC(A, "cpr", mixed=mixed, form=w.get("form", "pf"), amg=w["amg"], **kr)
     elif w["precond"] == "ras":
         k = ras_kwargs(w)
-        M = oracle.PC(A, "ras", ras=dict(nsub=k["nparts"], part=k["part"], overlap=k["overlap"], level=k["level"]))
+        M = oracle.PC(A, "ras", ras=dict(nsub=k["nparts"], part=k["part"], overlap=k["overlap"], level=k["level"],
+                                         **({"ilut": k["ilut"]} if "ilut" in k else {})))
     else:
         M = oracle.PC(A, w["precond"], mixed=mixed, form=w.get("form", "pf"))
     setup = time.perf_counter() - t0

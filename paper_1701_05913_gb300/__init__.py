@@ -61,7 +61,8 @@ class PcOpts(C.Structure):
                 ("net", _vp), ("log_perm", _vp), ("cpr_form", C.c_int32),
                 ("ras_nparts", C.c_int32), ("ras_overlap", C.c_int32), ("ilu_level", C.c_int32),
                 ("ras_part", _vp), ("amg_theta", C.c_double), ("amg_max_levels", C.c_int32),
-                ("amg_max_coarse", C.c_int32), ("amg_nu", C.c_int32), ("cpr_pstage", C.c_int32)]
+                ("amg_max_coarse", C.c_int32), ("amg_nu", C.c_int32), ("cpr_pstage", C.c_int32),
+                ("ras_local", C.c_int32), ("ilut_p", C.c_int32), ("ilut_tol", C.c_double)]
 
 
 CPR_FORMS = ("pf", "fp", "fpf", "ffpf")   # rs_cpr_form: Algs. 6, 5, 7, 8
@@ -327,7 +328,7 @@ class Precond:
 
     def __init__(self, ctx: Context, A: Mat, kind: str = "ilu0", prec: str = "fp64",
                  net=None, log_perm=None, grid=None, form: str = "pf", nparts: int = 1, part=None,
-                 overlap: int = 0, level: int = 0, amg=None, pstage: str = "ilu0"):
+                 overlap: int = 0, level: int = 0, amg=None, pstage: str = "ilu0", ilut=None):
         self.ctx, self.A, self.kind = ctx, A, kind
         opts = PcOpts()
         opts.prec = MIXED if prec == "mixed" else FP64
@@ -341,6 +342,8 @@ class Precond:
             opts.nx, opts.ny, opts.nz = grid
         # restricted additive Schwarz: subdomains, overlap layers, ILU(k) level
         opts.ras_nparts, opts.ras_overlap, opts.ilu_level = nparts, overlap, level
+        if ilut is not None:           # (p, tol): ILUT local solvers instead of ILU(level)
+            opts.ras_local, opts.ilut_p, opts.ilut_tol = 1, ilut[0], ilut[1]
         # algebraic multigrid (kind "amg", or the CPR pressure stage with pstage="amg")
         a = amg or {}
         opts.amg_theta = a.get("theta", 0.0)

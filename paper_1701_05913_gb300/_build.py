@@ -13,8 +13,10 @@ INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUTDIR, "librs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I", INCLUDE, "-I", CSRC]
+# host code keeps every multiply and add separately rounded (-ffp-contract=off),
+# so that host-side setup arithmetic rounds the same on x86-64 and AArch64
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 
 def _nvcc():

@@ -1112,6 +1112,18 @@ int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row)
     }
 }
 
+// A factor computed elsewhere (ILUT on the host), FP64 in the pattern of f:
+// strict lower part of L, then U with its diagonal (scalar only).  Builds
+// the sweeps' data from it, as after a factorisation.
+int rs_ilu_set_factors(IluFactor *f, const double *d_lu, int *bad_row)
+{
+    if (f->bs != 1) return RS_ERR_INVALID_ARG;
+    if (bad_row) *bad_row = -1;
+    if (f->nrows == 0) return RS_OK;
+    RS_CUDA_TRY(cudaMemcpyAsync(f->lu, d_lu, sizeof(double) * f->nnzb, cudaMemcpyDeviceToDevice, f->ctx->stream));
+    return f->fp32 ? gather_sweep_data<1, float>(f, bad_row) : gather_sweep_data<1, double>(f, bad_row);
+}
+
 // Dynamic shared memory of a sweep block: one scan stage per warp.  Above the
 // default 48 KB the kernel's limit is raised once per device.
 template <int BS, typename T, class K>

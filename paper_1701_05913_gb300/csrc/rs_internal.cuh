@@ -288,8 +288,10 @@ int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row);
 int rs_ilu_apply(IluFactor *f, const double *r, double *z, const double *scale_dev,
                  const int *skip);
 void rs_ilu_destroy(IluFactor *f);
-int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part, int overlap, int level, int fp32,
-                  RasData **out, int *bad_row);
+int rs_ilu_set_factors(IluFactor *f, const double *d_lu, int *bad_row);
+// local: 0 = ILU(level), 1 = ILUT(ilut_p, ilut_tol) (scalar matrices)
+int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part, int overlap, int level, int local,
+                  int ilut_p, double ilut_tol, int fp32, RasData **out, int *bad_row);
 int rs_ras_apply(RasData *R, const double *r, double *z, const int *skip);
 void rs_ras_destroy(RasData *R);
 // A0: the level-0 matrix when the caller has one as an rs_mat (else built

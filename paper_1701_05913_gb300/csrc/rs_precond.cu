@@ -214,7 +214,9 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
     case RS_PC_RAS: {
         const int nparts = opts && opts->ras_nparts ? opts->ras_nparts : 1;
         st = rs_ras_create(ctx, A, nparts, opts ? opts->ras_part : nullptr, opts ? opts->ras_overlap : 0,
-                           opts ? opts->ilu_level : 0, fp32, &M->ras, &bad);
+                           opts ? opts->ilu_level : 0, opts ? opts->ras_local : 0,
+                           opts && opts->ilut_p ? opts->ilut_p : -1,
+                           opts && opts->ilut_tol != 0.0 ? opts->ilut_tol : 1e-3, fp32, &M->ras, &bad);
         break;
     }
     case RS_PC_CPR:
@@ -243,7 +245,8 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         const bool fras = opts && (opts->ras_nparts > 1 || opts->ras_part);
         if (fras)
             st = rs_ras_create(ctx, A, opts->ras_nparts ? opts->ras_nparts : 1, opts->ras_part, opts->ras_overlap,
-                               opts->ilu_level, fp32, &M->ras, &bad);
+                               opts->ilu_level, opts->ras_local, opts->ilut_p ? opts->ilut_p : -1,
+                               opts->ilut_tol != 0.0 ? opts->ilut_tol : 1e-3, fp32, &M->ras, &bad);
         else
             st = rs_ilu_create(ctx, bs, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
         if (!st && !fras) st = rs_ilu_factor(M->bilu, A->val, &bad);

@@ -17,6 +17,7 @@
 //         it (the restricted prolongation).
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <vector>
 
 #include "rs_internal.cuh"
@@ -110,13 +111,103 @@ static void iluk_rows(int n, const std::vector<int> &lptr, const std::vector<int
     }
 }
 
-int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part, int overlap, int level, int fp32,
-                  RasData **out, int *bad_row)
+// ILUT(p, tol) of one local matrix (rows 0..n-1, sorted columns, values
+// lval), Saad's algorithm row by row: the row in a dense work array; its
+// lower entries eliminated in ascending order (fill included), each
+// multiplier w_k = w_k / u_kk dropped below tau = tol ||a_i||_2, else
+// w_j -= w_k u_kj over the stored U row k; then off-diagonal entries below
+// tau dropped and the p largest kept in each part (ties to the lower
+// column; p < 0: as many as row i has there).  Appends the factor rows
+// (strict L, then U with its diagonal, columns + base) to optr/ocol/olu.
+// Returns the local row of a zero pivot, or -1.
+static int ilut_rows(int n, const std::vector<int> &lptr, const std::vector<int> &lcol, const std::vector<double> &lval,
+                     int p, double tol, int base, std::vector<int> &optr, std::vector<int> &ocol,
+                     std::vector<double> &olu)
+{
+    std::vector<int> up(n + 1), uc;          // U rows kept so far (diagonal first)
+    std::vector<double> uv;
+    std::vector<double> w(n, 0.0);
+    std::vector<char> in(n, 0);
+    std::vector<int> touched, lower;
+    std::vector<std::pair<int, double>> lo, hi;
+    auto larger = [](const std::pair<int, double> &a, const std::pair<int, double> &b) {
+        const double x = std::fabs(a.second), y = std::fabs(b.second);
+        return x != y ? x > y : a.first < b.first;
+    };
+    for (int i = 0; i < n; ++i) {
+        touched.clear();
+        lower.clear();
+        int pl = 0, pu = 0;
+        double sq = 0.0;
+        for (int q = lptr[i]; q < lptr[i + 1]; ++q) {
+            const int c = lcol[q];
+            w[c] = lval[q];
+            in[c] = 1;
+            touched.push_back(c);
+            sq += lval[q] * lval[q];
+            if (c < i) { ++pl; lower.push_back(c); }
+            else if (c > i) ++pu;
+        }
+        const double tau = tol * std::sqrt(sq);
+        if (p >= 0) pl = pu = p;
+        for (size_t t = 0; t < lower.size(); ++t) {
+            const int k = lower[t];
+            if (w[k] == 0.0) continue;
+            w[k] = w[k] / uv[up[k]];
+            if (std::fabs(w[k]) < tau) { w[k] = 0.0; continue; }
+            for (int q = up[k] + 1; q < up[k + 1]; ++q) {
+                const int j = uc[q];
+                if (!in[j]) {
+                    in[j] = 1;
+                    w[j] = 0.0;
+                    touched.push_back(j);
+                    if (j < i) lower.insert(std::upper_bound(lower.begin() + t + 1, lower.end(), j), j);
+                }
+                w[j] = w[j] - w[k] * uv[q];
+            }
+        }
+        lo.clear();
+        hi.clear();
+        double diag = 0.0;
+        for (int c : touched) {
+            if (c == i) diag = w[c];
+            else if (w[c] != 0.0 && std::fabs(w[c]) >= tau) (c < i ? lo : hi).push_back({c, w[c]});
+            w[c] = 0.0;
+            in[c] = 0;
+        }
+        if (!(diag != 0.0) || !std::isfinite(diag)) return i;
+        std::sort(lo.begin(), lo.end(), larger);
+        std::sort(hi.begin(), hi.end(), larger);
+        if ((int)lo.size() > pl) lo.resize(pl);
+        if ((int)hi.size() > pu) hi.resize(pu);
+        std::sort(lo.begin(), lo.end());
+        std::sort(hi.begin(), hi.end());
+        for (const auto &e : lo) { ocol.push_back(base + e.first); olu.push_back(e.second); }
+        ocol.push_back(base + i);
+        olu.push_back(diag);
+        up[i] = (int)uc.size();
+        uc.push_back(i);
+        uv.push_back(diag);
+        for (const auto &e : hi) {
+            ocol.push_back(base + e.first);
+            olu.push_back(e.second);
+            uc.push_back(e.first);
+            uv.push_back(e.second);
+        }
+        up[i + 1] = (int)uc.size();
+        optr.push_back((int)ocol.size());
+    }
+    return -1;
+}
+
+int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part, int overlap, int level, int local,
+                  int ilut_p, double ilut_tol, int fp32, RasData **out, int *bad_row)
 {
     *out = nullptr;
     if (bad_row) *bad_row = -1;
     const int n = A->nrows, bs = A->bs;
     if (nparts < 1 || overlap < 0 || level < 0 || level > RS_RAS_MAX_LEVEL) return RS_ERR_INVALID_ARG;
+    if (local != 0 && (local != 1 || bs != 1 || !(ilut_tol >= 0.0))) return RS_ERR_INVALID_ARG;
     // subdomain of each block row: the caller's, or contiguous ranges of rows
     std::vector<int> pt(n);
     for (int i = 0; i < n; ++i) {
@@ -124,6 +215,16 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
         if (pt[i] < 0 || pt[i] >= nparts) return RS_ERR_INVALID_ARG;
     }
     const std::vector<int> &ap = A->h_ptr, &ac = A->h_col;
+    std::vector<double> av;                    // A's values, for ILUT on the host
+    if (local == 1 && !ac.empty()) {
+        av.resize(ac.size());
+        if (cudaMemcpyAsync(av.data(), A->val, sizeof(double) * ac.size(), cudaMemcpyDeviceToHost, ctx->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            return RS_ERR_CUDA;
+    }
+    std::vector<double> hlu;                   // ILUT: the stacked factor
+    int ilut_bad = -1;
     // rows of each subdomain, ascending
     std::vector<int> pstart(nparts + 1, 0), prow(n);
     for (int i = 0; i < n; ++i) ++pstart[pt[i] + 1];
@@ -168,7 +269,16 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
                 }
             lptr.push_back((int)lcol.size());
         }
-        if (level == 0) {
+        if (local == 1) {
+            std::vector<double> lval(lsrc.size());
+            for (size_t q = 0; q < lsrc.size(); ++q) lval[q] = av[lsrc[q]];
+            const int b = ilut_rows(ns, lptr, lcol, lval, ilut_p, ilut_tol, base, hptr, hcol, hlu);
+            if (b >= 0) {
+                ilut_bad = set[b];
+                break;
+            }
+            hsrc.resize(hcol.size(), -1);
+        } else if (level == 0) {
             for (int a = 0; a < ns; ++a) {
                 for (int q = lptr[a]; q < lptr[a + 1]; ++q) {
                     hcol.push_back(base + lcol[q]);
@@ -183,6 +293,10 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
         if (total_nnz > INT_MAX) return RS_ERR_INVALID_ARG;
         gidx.insert(gidx.end(), set.begin(), set.end());
         for (int r = pstart[s]; r < pstart[s + 1]; ++r) own[prow[r]] = base + loc[prow[r]];
+    }
+    if (ilut_bad >= 0) {
+        if (bad_row) *bad_row = ilut_bad;
+        return RS_ERR_ZERO_PIVOT;
     }
     const int nx = (int)gidx.size();
     RasData *R = new RasData();
@@ -219,14 +333,20 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
         rs_ras_destroy(R);
         return RS_ERR_CUDA;
     }
-    if (total_nnz > 0) {
+    if (local == 1) {
+        // the factor itself was formed on the host
+        if (total_nnz > 0 &&
+            cudaMemcpyAsync(R->val, hlu.data(), sizeof(double) * total_nnz, cudaMemcpyHostToDevice, sm) != cudaSuccess)
+            st = RS_ERR_CUDA;
+    } else if (total_nnz > 0) {
         k_ras_values<<<ras_grid(ctx, total_nnz * (int64_t)b2), 256, 0, sm>>>(total_nnz, (int)b2, R->src, A->val, R->val);
         st = rs_check_launch(ctx);
     }
     // the stacked pattern's host copy is only needed by the analysis below
     int bad = -1;
     st = st ? st : rs_ilu_create(ctx, bs, nx, total_nnz, R->ptr, R->col, hptr, hcol, fp32, &R->f, &bad);
-    st = st ? st : rs_ilu_factor(R->f, R->val, &bad);
+    if (local == 1) st = st ? st : rs_ilu_set_factors(R->f, R->val, &bad);
+    else st = st ? st : rs_ilu_factor(R->f, R->val, &bad);
     if (bad >= 0 && bad < nx && bad_row) *bad_row = gidx[bad];
     if (st == RS_ERR_ZERO_PIVOT) {
         *out = R;            // the caller keeps the object to report the row

@@ -239,3 +239,43 @@ def test_cpr_ras_f_stage_on_a_scalar_matrix(rs, ctx, orc):
     z = rs.Vec.zeros(ctx, g.n)
     M.apply(rs.Vec(ctx, r), z)
     assert rel(z.numpy(), Mo.apply(r)) <= 1e-12
+
+
+@pytest.mark.parametrize("shape,parts,overlap,ilut", [
+    ((20, 16, 12), (2, 2, 2), 1, (-1, 1e-3)),
+    ((24, 20, 17), (3, 2, 1), 2, (3, 1e-2)),
+    ((16, 16, 16), (1, 1, 1), 0, (-1, 1e-4)),
+])
+def test_ras_ilut_parity(rs, ctx, orc, shape, parts, overlap, ilut):
+    g = synth.Grid(*shape)
+    d = synth.pressure_7pt(g, 63, kz_scale=0.1)
+    part = rs.box_partition(shape, parts)
+    nparts = int(np.prod(parts))
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "ras", nparts=nparts, part=part, overlap=overlap, ilut=ilut)
+    Ao = orc.Mat.csr(d)
+    R = orc.Ras(Ao, nparts, part=part, overlap=overlap, ilut=ilut)
+    assert R.status == 0
+    gidx, ptr, col, lu = M.ras_structure()
+    ogidx, optr, ocol, olu = R.structure()
+    # the dropping decisions agree, so the patterns are identical
+    assert np.array_equal(gidx, ogidx) and np.array_equal(ptr, optr) and np.array_equal(col, ocol)
+    assert np.max(np.abs(lu - olu) / np.maximum(np.abs(olu), 1e-300)) <= 1e-12
+    r = np.random.default_rng(64).standard_normal(g.n)
+    z = rs.Vec.zeros(ctx, g.n)
+    M.apply(rs.Vec(ctx, r), z)
+    assert rel(z.numpy(), R.apply(r)) <= 1e-12
+    b = orc.spmv(Ao, synth.x_true(g.n, 64))
+    Mo = orc.PC(Ao, "ras", ras=dict(nsub=nparts, part=part, overlap=overlap, ilut=ilut))
+    xo, io, _ = orc.gmres(Ao, Mo, b, restart=30, rtol=1e-8)
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_gmres(A, M, rs.Vec(ctx, b), x, restart=30, rtol=1e-8, maxit=10000)
+    assert info["status"] == 0 and io["status"] == 0 and info["true_rel_res"] <= 1e-8
+    assert abs(info["iters"] - io["iters"]) <= 2, (info, io)
+
+
+def test_ras_ilut_rejected_on_blocks(rs, ctx):
+    m = synth.black_oil_bsr3(synth.Grid(6, 5, 4), 65)
+    with pytest.raises(rs.RsError) as e:
+        rs.Precond(ctx, rs.Mat.bsr(ctx, m), "ras", nparts=2, ilut=(-1, 1e-3))
+    assert e.value.status == rs.ERR_INVALID_ARG
