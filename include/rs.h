@@ -282,6 +282,16 @@ int rs_precond_get_ras(const rs_pc *M, int32_t *gidx, int32_t *ptr, int32_t *col
  * row in dependency order).  RS_ERR_INVALID_ARG for RS_PC_NONE or NULL
  * arguments. */
 int rs_precond_sweep_levels(const rs_pc *M, int32_t *levels_l, int32_t *levels_u);
+/* Runs of the same sweeps: a run is a sequence of segments that one warp
+ * solves in turn, each segment reading the one before it from the warp's
+ * registers (scalar factors only; block factors have one segment per run).
+ * runs_l / runs_u: the number of runs of the L / U sweep, i.e. the tickets
+ * the warps take; longest_l / longest_u: the segments of the longest run.
+ * The number of runs never exceeds the number of segments.  Runs change the
+ * schedule, not the arithmetic: results are those of one segment per run.
+ * RS_ERR_INVALID_ARG for RS_PC_NONE or NULL arguments. */
+int rs_precond_sweep_runs(const rs_pc *M, int32_t *runs_l, int32_t *runs_u, int32_t *longest_l,
+                          int32_t *longest_u);
 int rs_precond_destroy(rs_pc **M);
 
 /* ---- Krylov solvers (Sec. 3, Alg. 1) ----------------------------------- */

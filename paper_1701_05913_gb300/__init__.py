@@ -106,6 +106,7 @@ SIGNATURES = [
     ("rs_precond_get_cpr", C.c_int, [_vp, _f64p, _f64p]),
     ("rs_precond_bad_row", C.c_int32, [_vp]),
     ("rs_precond_sweep_levels", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    ("rs_precond_sweep_runs", C.c_int, [_vp] + [C.POINTER(C.c_int32)] * 4),
     ("rs_precond_ras_info", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     ("rs_precond_amg_levels", C.c_int, [_vp, C.POINTER(C.c_int32)]),
     ("rs_precond_amg_level_sizes", C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
@@ -448,6 +449,12 @@ class Precond:
         a, b = C.c_int32(), C.c_int32()
         _check(lib().rs_precond_sweep_levels(self.h, C.byref(a), C.byref(b)), "rs_precond_sweep_levels")
         return a.value, b.value
+
+    def sweep_runs(self):
+        """(L runs, U runs, longest L run, longest U run) of the same sweeps."""
+        v = [C.c_int32() for _ in range(4)]
+        _check(lib().rs_precond_sweep_runs(self.h, *[C.byref(x) for x in v]), "rs_precond_sweep_runs")
+        return tuple(x.value for x in v)
 
     def __del__(self):
         try:

@@ -20,11 +20,17 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "rs_internal.cuh"
 
 #define RS_SWEEP_THREADS 128
+#define RS_RUN_CH 4        // widest segment (entries per row) a run continues with
+#define RS_RUN_P 6                       // segments staged ahead
+#define RS_RUN_SLOTS (RS_RUN_P + 1)      // the slot being read is never refilled
+#define RS_RUN_WORDS (RS_RUN_CH + 5 + 2) // per lane: values, multipliers, r or y, D
+#define RS_RUN_RING (RS_RUN_SLOTS * RS_RUN_WORDS * 32)   // 8-byte words per warp
 
 // ---------------------------------------------------------------------------
 // host analysis
@@ -85,7 +91,7 @@ static int build_layout(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
 // segments holding the columns it reads outside itself.
 static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
                           const std::vector<int> &col, const std::vector<int> &diag, bool lower,
-                          SegLayout &S)
+                          int run_cap, SegLayout &S)
 {
     // does row i read row j = i-1 (L) / i+1 (U)?  (the entry next to the diagonal)
     auto reads_prev = [&](int i) { return i > 0 && diag[i] > ptr[i] && col[diag[i] - 1] == i - 1; };
@@ -162,11 +168,104 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
             }
         }
     }
+    // Runs.  A warp that has finished segment p may go on with a segment s
+    // of the next level that reads p, taking p's values from its registers
+    // instead of from memory.  s joins p's run when
+    //  * s is p shifted by a fixed number of rows (same length, width and
+    //    kind; every column shifted by the same amount), and the run's
+    //    segment, row and entry strides stay constant, so that the warp
+    //    computes every later segment's addresses without loads;
+    //  * every other segment s reads lies in an earlier run or earlier in
+    //    this one.
+    // Runs take tickets in the order they were opened, i.e. in the level
+    // order of their first segments, so a warp only waits for runs held by
+    // warps that took earlier tickets, as before.  Among the candidates p
+    // (segments of the previous level that feed at least half of s's rows),
+    // the one s reads most often comes first, then the nearest: on a grid in
+    // natural order a run follows one x-segment through the y-lines of a
+    // plane.
+    std::vector<int> run_of(nseg, -1), rlast, rdesc;
+    {
+        std::vector<std::pair<int, int>> deps;   // (segment, entries of s that read it)
+        for (int t = 0; t < nseg; ++t) {
+            const int sg = order[t];
+            const int r0 = r0v[sg], len = r0v[sg + 1] - r0;
+            int R = -1;
+            if (run_cap > 1 && kind[sg] && width[sg] > 0 && width[sg] <= RS_RUN_CH) {
+                deps.clear();
+                for (int i = r0; i < r0 + len; ++i) {
+                    const int q0 = lower ? ptr[i] : diag[i] + 1;
+                    const int q1 = lower ? diag[i] : ptr[i + 1];
+                    for (int q = q0; q < q1; ++q) {
+                        const int c = col[q];
+                        if (c >= r0 && c < r0 + len) continue;
+                        const int d = seg_of[c];
+                        auto it = std::find_if(deps.begin(), deps.end(), [&](const std::pair<int, int> &x) { return x.first == d; });
+                        if (it == deps.end()) deps.push_back({d, 1});
+                        else ++it->second;
+                    }
+                }
+                std::stable_sort(deps.begin(), deps.end(), [&](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+                    if (a.second != b.second) return a.second > b.second;
+                    return std::abs(r0v[a.first] - r0) < std::abs(r0v[b.first] - r0);
+                });
+                for (const auto &cand : deps) {
+                    if (2 * cand.second < len) break;   // p must feed at least half of s's rows
+                    const int p = cand.first, Rp = run_of[p];
+                    const int *d = &rdesc[5 * Rp];
+                    if (rlast[Rp] != p || d[1] >= run_cap || lev[p] != lev[sg] - 1 || !kind[p]) continue;
+                    if (r0v[p + 1] - r0v[p] != len || width[p] != width[sg]) continue;
+                    const int dseg = sg - p, drow = r0 - r0v[p], dent = sptr[sg] - sptr[p];
+                    if (d[1] >= 2 && (dseg != d[2] || drow != d[3] || dent != d[4])) continue;
+                    bool ok = true;
+                    for (int e = 0; e < width[sg] * 32 && ok; ++e) {
+                        const int a = ecol[sptr[p] + e], b = ecol[sptr[sg] + e];
+                        ok = (a < 0) == (b < 0) && (a < 0 || b == a + drow);
+                    }
+                    for (const auto &o : deps) ok = ok && (o.first == p || run_of[o.first] <= Rp);
+                    if (!ok) continue;
+                    R = Rp;
+                    break;
+                }
+            }
+            if (R >= 0) {
+                int *d = &rdesc[5 * R];
+                if (d[1] == 1) {
+                    d[2] = sg - d[0];
+                    d[3] = r0 - r0v[d[0]];
+                    d[4] = sptr[sg] - sptr[d[0]];
+                }
+                ++d[1];
+                rlast[R] = sg;
+                run_of[sg] = R;
+            } else {
+                run_of[sg] = (int)rlast.size();
+                rlast.push_back(sg);
+                rdesc.insert(rdesc.end(), {sg, 1, 0, 0, 0});
+            }
+        }
+    }
+    // Runs pay for their shared-memory ring (which limits a sweep block to
+    // two per SM) only where they take over most of the segments; otherwise
+    // every segment stays a run of its own.
+    if (2 * (int64_t)rlast.size() > nseg) {
+        rlast.clear();
+        rdesc.clear();
+        for (int t = 0; t < nseg; ++t) {
+            rlast.push_back(order[t]);
+            rdesc.insert(rdesc.end(), {order[t], 1, 0, 0, 0});
+        }
+    }
+    const int nrun = (int)rlast.size();
+    int max_run = 0;
+    for (int R = 0; R < nrun; ++R) max_run = std::max(max_run, rdesc[5 * R + 1]);
     S.nseg = nseg;
     S.nlevels = nlev;
     S.nent = nent;
+    S.nrun = nrun;
+    S.max_run = max_run;
     int st = RS_OK;
-    st = st ? st : rs_alloc(ctx, (void **)&S.order, sizeof(int) * (nseg > 0 ? nseg : 1));
+    st = st ? st : rs_alloc(ctx, (void **)&S.runs, sizeof(int) * 5 * (nrun > 0 ? nrun : 1));
     st = st ? st : rs_alloc(ctx, (void **)&S.sptr, sizeof(int) * (nseg + 1));
     st = st ? st : rs_alloc(ctx, (void **)&S.col, sizeof(int) * (nent > 0 ? nent : 1));
     st = st ? st : rs_alloc(ctx, (void **)&S.src, sizeof(int) * (nent > 0 ? nent : 1));
@@ -176,7 +275,7 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     if (st) return st;
     cudaStream_t sm = ctx->stream;
     if (nseg) {
-        RS_CUDA_TRY(cudaMemcpyAsync(S.order, order.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, sm));
+        RS_CUDA_TRY(cudaMemcpyAsync(S.runs, rdesc.data(), sizeof(int) * 5 * nrun, cudaMemcpyHostToDevice, sm));
         RS_CUDA_TRY(cudaMemcpyAsync(S.kind, kind.data(), nseg, cudaMemcpyHostToDevice, sm));
     }
     RS_CUDA_TRY(cudaMemcpyAsync(S.sptr, sptr.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, sm));
@@ -193,7 +292,7 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
 
 static void free_segments(rs_ctx *ctx, SegLayout &S)
 {
-    rs_free(ctx, S.order);
+    rs_free(ctx, S.runs);
     rs_free(ctx, S.sptr);
     rs_free(ctx, S.col);
     rs_free(ctx, S.src);
@@ -643,9 +742,9 @@ __device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a,
 // its subtractions and five multiply-adds of bs-vectors; any other
 // in-segment pattern is resolved lane by lane with broadcasts.
 struct SegArgs {
-    int nrows, nseg;
+    int nrows, nrun;
     unsigned sleep_cap;
-    const int *order, *sptr, *ecol, *row0;
+    const int *runs, *sptr, *ecol, *row0;
     const unsigned char *kind;
     int64_t nent;
     int npr;                 // padded row count of the diagonal arrays
@@ -659,9 +758,9 @@ static SegArgs seg_args(rs_ctx *ctx, const SegLayout &S, int nrows, SweepState *
 {
     SegArgs a;
     a.nrows = nrows;
-    a.nseg = S.nseg;
+    a.nrun = S.nrun;
     a.sleep_cap = ctx->sleep_cap_ns;
-    a.order = S.order;
+    a.runs = S.runs;
     a.sptr = S.sptr;
     a.ecol = S.col;
     a.row0 = S.row0;
@@ -771,9 +870,11 @@ __device__ __forceinline__ void stage_mul(const T *__restrict__ mul, int seg, T 
 // x_t = c_t + A_t x_{t-/+1} over the warp: five steps of
 // acc_t += A^{(k)}_t acc_{t-/+o} with the staged multipliers A^{(k)}.
 template <int BS, typename T, bool LOWER>
-__device__ __forceinline__ void scan_staged(const T *stage, T (&acc)[BS], int lane)
+__device__ __forceinline__ void scan_staged(const T *stage, T (&acc)[BS], int lane, bool run = false)
 {
-    cp_async_wait_all();
+    // a run keeps its RS_RUN_P staged segments in flight
+    if (run) asm volatile("cp.async.wait_group %0;" ::"n"(RS_RUN_P) : "memory");
+    else cp_async_wait_all();
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -805,6 +906,180 @@ __device__ __forceinline__ void seg_end(const SegArgs &g)
     }
 }
 
+// ---------------------------------------------------------------------------
+// runs: the later segments of a run (scalar factors only)
+// ---------------------------------------------------------------------------
+// Segment k of a run is its first segment shifted by k row strides: its
+// rows, entries, multipliers and columns follow from the first segment and
+// the run's strides.  A warp copies the factor values, multipliers and
+// right-hand side of segment k + RS_RUN_P into a ring of shared-memory
+// slots (cp.async, one group per segment) while it finishes segment k, so
+// the HBM latency stays off the run's path; it takes a first look at the
+// values segment k + 1 reads from other warps one segment ahead.  Entries
+// that read segment k - 1 take its values from the warp's registers (a
+// shuffle) instead of polling memory.  The arithmetic is that of the first
+// segment's path, in the same order, so a run changes no result.
+
+struct RunCtx {
+    int seg0, dseg, drow, dent, row0, len, off0, w;
+    int c0[RS_RUN_CH];   // this lane's columns in the first segment, or -1
+    int sl[RS_RUN_CH];   // the lane of the previous segment holding that column
+};
+
+template <typename T>
+struct RunLook {         // first look at the values a segment reads from memory
+    typename Sentinel<T>::bits_t b[RS_RUN_CH];
+    unsigned ext, prv;   // entries read from memory / from the previous segment
+};
+
+__device__ __forceinline__ RunCtx run_ctx(const SegArgs &g, const int *rd, int row0, int len, int off, int w, int lane)
+{
+    RunCtx rc;
+    rc.seg0 = rd[0];
+    rc.dseg = rd[2];
+    rc.drow = rd[3];
+    rc.dent = rd[4];
+    rc.row0 = row0;
+    rc.len = len;
+    rc.off0 = off;
+    rc.w = w;
+#pragma unroll
+    for (int j = 0; j < RS_RUN_CH; ++j) {
+        rc.c0[j] = j < w ? g.ecol[off + j * 32 + lane] : -1;
+        rc.sl[j] = (rc.c0[j] - row0 + rc.drow) & 31;
+    }
+    return rc;
+}
+
+__device__ __forceinline__ void cp_async_n(void *smem, const void *gmem, int bytes)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// copy segment k's per-lane data into its ring slot (one cp.async group,
+// committed by the caller); L: r_i and the U work vector's reset;
+// U: y_i and D_i
+template <typename T, bool LOWER>
+__device__ __forceinline__ void run_stage(const RunCtx &rc, int k, int lane, unsigned long long *ring,
+                                          const T *__restrict__ val, const T *__restrict__ mul,
+                                          const double *__restrict__ r, const T *yin, T *reset,
+                                          const T *__restrict__ dinv)
+{
+    const int row = rc.row0 + k * rc.drow + lane;
+    const int64_t off = rc.off0 + (int64_t)k * rc.dent;
+    unsigned long long *sl = ring + (k % RS_RUN_SLOTS) * RS_RUN_WORDS * 32 + lane;
+#pragma unroll
+    for (int j = 0; j < RS_RUN_CH; ++j)
+        if (rc.c0[j] >= 0) cp_async_n(sl + j * 32, val + off + j * 32 + lane, sizeof(T));
+    const T *ms = mul + (size_t)(rc.seg0 + k * rc.dseg) * ScanStage<1, T>::N + lane;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) cp_async_n(sl + (RS_RUN_CH + q) * 32, ms + q * 32, sizeof(T));
+    if (lane < rc.len) {
+        if (LOWER) {
+            cp_async_n(sl + (RS_RUN_CH + 5) * 32, r + row, 8);
+            reset[row] = bits_to(T(), Sentinel<T>::bits);
+        } else {
+            cp_async_n(sl + (RS_RUN_CH + 5) * 32, yin + row, sizeof(T));
+            cp_async_n(sl + (RS_RUN_CH + 6) * 32, dinv + row, sizeof(T));
+        }
+    }
+}
+
+// first look at segment k's values from memory (k >= 1); x is the vector
+// the sweep produces
+template <typename T>
+__device__ __forceinline__ void run_look(const RunCtx &rc, int k, const T *x, RunLook<T> &s)
+{
+    const int r0 = rc.row0 + k * rc.drow;
+    s.ext = 0;
+    s.prv = 0;
+#pragma unroll
+    for (int j = 0; j < RS_RUN_CH; ++j) {
+        const int c = rc.c0[j] >= 0 ? rc.c0[j] + k * rc.drow : -1;
+        const bool own = c >= r0 && c < r0 + rc.len;
+        const bool prv = c >= r0 - rc.drow && c < r0 - rc.drow + rc.len;
+        const bool ext = c >= 0 && !own && !prv;
+        s.ext |= (unsigned)ext << j;
+        s.prv |= (unsigned)(c >= 0 && prv) << j;
+        s.b[j] = ext ? ld_relaxed_bits(x + c) : 0;
+    }
+}
+
+// finish segment k of the run from its staged slot: wait for the values
+// read from memory, subtract, scan, store; returns this lane's value (the
+// next segment's prev)
+template <typename T, bool LOWER>
+__device__ __forceinline__ T run_finish(const SegArgs &g, const RunCtx &rc, int k, int lane,
+                                        const unsigned long long *ring, RunLook<T> &s, T prev, T *x, T *yin,
+                                        double *__restrict__ out, double sc, bool &late)
+{
+    const int r0 = rc.row0 + k * rc.drow, row = r0 + lane;
+    const bool active = lane < rc.len;
+    const unsigned long long *sl = ring + (k % RS_RUN_SLOTS) * RS_RUN_WORDS * 32 + lane;
+    T v[RS_RUN_CH], m[5];
+#pragma unroll
+    for (int j = 0; j < RS_RUN_CH; ++j) v[j] = *(const T *)(sl + j * 32);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) m[q] = *(const T *)(sl + (RS_RUN_CH + q) * 32);
+    T acc = T(0);
+    if (active) {
+        if (LOWER) {
+            const double rv = *(const double *)(sl + (RS_RUN_CH + 5) * 32);
+            acc = (T)(sc == 1.0 ? rv : rv * sc);
+        } else {
+            const T yv = *(const T *)(sl + (RS_RUN_CH + 5) * 32);
+            acc = mad(*(const T *)(sl + (RS_RUN_CH + 6) * 32), yv, T(0));
+            yin[row] = bits_to(T(), Sentinel<T>::bits);   // the copy of y_i is complete
+        }
+    }
+    unsigned ns = 0;
+    long long t0 = 0;
+    for (bool first = true;; first = false) {
+        bool pend = false;
+#pragma unroll
+        for (int j = 0; j < RS_RUN_CH; ++j) pend |= ((s.ext >> j) & 1u) && s.b[j] == Sentinel<T>::bits;
+        if (!__any_sync(0xffffffffu, pend)) break;
+        if (first) {
+            t0 = clock64();
+        } else {
+            // one expired wait ends the waiting for the rest of the run
+            if (late || clock64() - t0 > g.limit) {
+                if (pend) atomicOr(g.err, RS_DEVERR_TIMEOUT);
+                late = true;
+                break;
+            }
+            if (ns) __nanosleep(ns);
+        }
+        ns = first ? min(16u, g.sleep_cap) : min(ns * 2, g.sleep_cap);
+#pragma unroll
+        for (int j = 0; j < RS_RUN_CH; ++j)
+            if (((s.ext >> j) & 1u) && s.b[j] == Sentinel<T>::bits) s.b[j] = ld_relaxed_bits(x + (rc.c0[j] + k * rc.drow));
+    }
+#pragma unroll
+    for (int j = 0; j < RS_RUN_CH; ++j) {
+        if (j >= rc.w) break;
+        const T xp = __shfl_sync(0xffffffffu, prev, rc.sl[j]);
+        if ((s.ext >> j) & 1u) acc = msub(acc, v[j], bits_to(T(), s.b[j]));
+        else if ((s.prv >> j) & 1u) acc = msub(acc, v[j], xp);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int o = 1 << q;
+        const T bp = LOWER ? __shfl_up_sync(0xffffffffu, acc, o) : __shfl_down_sync(0xffffffffu, acc, o);
+        if (LOWER ? lane >= o : lane + o < 32) acc = mad(m[q], bp, acc);
+    }
+    if (active) {
+        st_relaxed(x + row, acc);
+        if (!LOWER) out[row] = (double)acc;
+    }
+    return acc;
+}
+
 // L y = r (unit lower).  scale (device, optional) multiplies r on load;
 // zreset is the U sweep's work vector.
 template <int BS, typename T>
@@ -816,13 +1091,17 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
     if (g.skip && *(volatile const int *)g.skip) return;
     const int lane = threadIdx.x & 31;
     T *stage = (T *)sweep_smem + (threadIdx.x >> 5) * ScanStage<BS, T>::N;
+    unsigned long long *ring = (unsigned long long *)((T *)sweep_smem + (RS_SWEEP_THREADS / 32) * ScanStage<BS, T>::N) +
+                               (threadIdx.x >> 5) * RS_RUN_RING;
     const double sc = scale ? *scale : 1.0;
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(&g.st->ticket, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= g.nseg) break;
-        const int seg = g.order[t];
+        if (t >= g.nrun) break;
+        const int *rd = g.runs + 5 * t;
+        const int seg = rd[0];
+        const int count = BS == 1 ? rd[1] : 1;
         const int row0 = g.row0[seg], len = g.row0[seg + 1] - row0, row = row0 + lane;
         const bool active = lane < len;
         const int off = g.sptr[seg];
@@ -838,9 +1117,22 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
                 zreset[(size_t)row * BS + k] = bits_to(T(), Sentinel<T>::bits);
             }
         }
+        RunCtx rc;
+        RunLook<T> nx;
+        if constexpr (BS == 1) {
+            if (count > 1) {
+                rc = run_ctx(g, rd, row0, len, off, w, lane);
+                cp_async_commit();   // the first segment's multipliers
+                for (int k = 1; k <= RS_RUN_P; ++k) {
+                    if (k < count) run_stage<T, true>(rc, k, lane, ring, val, mul, r, nullptr, zreset, nullptr);
+                    cp_async_commit();
+                }
+                run_look<T>(rc, 1, y, nx);
+            }
+        }
         seg_external<BS, T>(g, val, y, off, w, lane, row0, row0 + len, acc);
         if (chain) {
-            scan_staged<BS, T, true>(stage, acc, lane);
+            scan_staged<BS, T, true>(stage, acc, lane, count > 1);
         } else {
             // lane k is final once lanes 0..k-1 have been applied
             for (int k = 0; k < 31; ++k) {
@@ -863,6 +1155,19 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
 #pragma unroll
             for (int k = 0; k < BS; ++k) st_relaxed(y + (size_t)row * BS + k, acc[k]);
         }
+        if constexpr (BS == 1) {
+            T prev = acc[0];
+            bool late = false;
+            for (int k = 1; k < count; ++k) {
+                cp_async_wait<RS_RUN_P - 1>();   // segment k's slot has arrived
+                if (k + RS_RUN_P < count)
+                    run_stage<T, true>(rc, k + RS_RUN_P, lane, ring, val, mul, r, nullptr, zreset, nullptr);
+                cp_async_commit();
+                RunLook<T> cur = nx;
+                if (k + 1 < count) run_look<T>(rc, k + 1, y, nx);
+                prev = run_finish<T, true>(g, rc, k, lane, ring, cur, prev, y, nullptr, nullptr, sc, late);
+            }
+        }
     }
     seg_end<BS, T>(g);
 }
@@ -880,12 +1185,16 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
     if (g.skip && *(volatile const int *)g.skip) return;
     const int lane = threadIdx.x & 31;
     T *stage = (T *)sweep_smem + (threadIdx.x >> 5) * ScanStage<BS, T>::N;
+    unsigned long long *ring = (unsigned long long *)((T *)sweep_smem + (RS_SWEEP_THREADS / 32) * ScanStage<BS, T>::N) +
+                               (threadIdx.x >> 5) * RS_RUN_RING;
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(&g.st->ticket, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= g.nseg) break;
-        const int seg = g.order[t];
+        if (t >= g.nrun) break;
+        const int *rd = g.runs + 5 * t;
+        const int seg = rd[0];
+        const int count = BS == 1 ? rd[1] : 1;
         const int row0 = g.row0[seg], len = g.row0[seg + 1] - row0, row = row0 + lane;
         const bool active = lane < len;
         const int off = g.sptr[seg];
@@ -908,9 +1217,22 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
             for (int k = 0; k < BS; ++k) sum = mad(active ? dinv[(size_t)(i * BS + k) * g.npr + row] : T(0), yv[k], sum);
             acc[i] = sum;
         }
+        RunCtx rc;
+        RunLook<T> nx;
+        if constexpr (BS == 1) {
+            if (count > 1) {
+                rc = run_ctx(g, rd, row0, len, off, w, lane);
+                cp_async_commit();   // the first segment's multipliers
+                for (int k = 1; k <= RS_RUN_P; ++k) {
+                    if (k < count) run_stage<T, false>(rc, k, lane, ring, val, mul, nullptr, y, nullptr, dinv);
+                    cp_async_commit();
+                }
+                run_look<T>(rc, 1, z, nx);
+            }
+        }
         seg_external<BS, T>(g, val, z, off, w, lane, row0, row0 + len, acc);
         if (chain) {
-            scan_staged<BS, T, false>(stage, acc, lane);
+            scan_staged<BS, T, false>(stage, acc, lane, count > 1);
         } else {
             // lane k is final once lanes k+1..31 have been applied
             for (int k = 31; k > 0; --k) {
@@ -934,6 +1256,19 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
             for (int k = 0; k < BS; ++k) {
                 st_relaxed(z + (size_t)row * BS + k, acc[k]);
                 out[(size_t)row * BS + k] = (double)acc[k];
+            }
+        }
+        if constexpr (BS == 1) {
+            T prev = acc[0];
+            bool late = false;
+            for (int k = 1; k < count; ++k) {
+                cp_async_wait<RS_RUN_P - 1>();   // segment k's slot has arrived
+                if (k + RS_RUN_P < count)
+                    run_stage<T, false>(rc, k + RS_RUN_P, lane, ring, val, mul, nullptr, y, nullptr, dinv);
+                cp_async_commit();
+                RunLook<T> cur = nx;
+                if (k + 1 < count) run_look<T>(rc, k + 1, z, nx);
+                prev = run_finish<T, false>(g, rc, k, lane, ring, cur, prev, z, y, out, 1.0, late);
             }
         }
     }
@@ -978,8 +1313,19 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
     const size_t esz = fp32 ? sizeof(float) : sizeof(double);
     // row-level schedule of the factorisation; segment layouts of the sweeps
     int st = build_layout(ctx, nrows, h_ptr, h_col, diag, f->L);
-    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, f->SL);
-    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, f->SU);
+    // runs are taken by the scalar FP64 sweeps.  In FP32 a hop between
+    // warps already costs about what a step of a run does (0.8 against
+    // 0.7 us at 128 x 128 x 64), and waiting inside a run adds more than
+    // that saves.  RS_SWEEP_RUN caps the length for either precision (1:
+    // every segment is a run of its own).
+    int run_cap = fp32 ? 1 : 1 << 30;
+    if (const char *e = getenv("RS_SWEEP_RUN")) {
+        const int v = atoi(e);
+        if (v >= 1) run_cap = v;
+    }
+    if (bs != 1) run_cap = 1;
+    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, run_cap, f->SL);
+    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, run_cap, f->SU);
     // sweep blocks: a single dependency chain (global ILU in natural order)
     // gains nothing from more warps, which only add polling; many
     // independent chains (the stacked subdomains of RAS) do.  Aim at three
@@ -1127,14 +1473,17 @@ int rs_ilu_set_factors(IluFactor *f, const double *d_lu, int *bad_row)
 // Dynamic shared memory of a sweep block: one scan stage per warp.  Above the
 // default 48 KB the kernel's limit is raised once per device.
 template <int BS, typename T, class K>
-static int sweep_smem(rs_ctx *ctx, K kernel, size_t *bytes)
+static int sweep_smem(rs_ctx *ctx, K kernel, bool runs, size_t *bytes)
 {
     static unsigned long long raised = 0;
-    *bytes = (size_t)(RS_SWEEP_THREADS / 32) * ScanStage<BS, T>::N * sizeof(T);
-    if (*bytes <= 48 * 1024) return RS_OK;
+    const size_t stage = (size_t)(RS_SWEEP_THREADS / 32) * ScanStage<BS, T>::N * sizeof(T);
+    const size_t ring = BS == 1 ? (size_t)(RS_SWEEP_THREADS / 32) * RS_RUN_RING * sizeof(unsigned long long) : 0;
+    *bytes = stage + (runs ? ring : 0);
+    const size_t most = stage + ring;
+    if (most <= 48 * 1024) return RS_OK;
     const unsigned long long bit = 1ull << (ctx->device & 63);
     if (!(raised & bit)) {
-        RS_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes));
+        RS_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most));
         raised |= bit;
     }
     return RS_OK;
@@ -1146,12 +1495,12 @@ static int apply_seg(IluFactor *f, const double *r, double *z, const double *sca
     rs_ctx *ctx = f->ctx;
     T *y = (T *)f->ywork, *zt = (T *)f->zwork;
     const int wpb = RS_SWEEP_THREADS / 32;
-    const int gl = std::max(1, std::min((f->SL.nseg + wpb - 1) / wpb, f->SL.grid));
-    const int gu = std::max(1, std::min((f->SU.nseg + wpb - 1) / wpb, f->SU.grid));
+    const int gl = std::max(1, std::min((f->SL.nrun + wpb - 1) / wpb, f->SL.grid));
+    const int gu = std::max(1, std::min((f->SU.nrun + wpb - 1) / wpb, f->SU.grid));
     size_t sl = 0, su = 0;
     {
-        const int e1 = sweep_smem<BS, T>(ctx, k_lsolve_seg<BS, T>, &sl);
-        const int e2 = e1 ? e1 : sweep_smem<BS, T>(ctx, k_usolve_seg<BS, T>, &su);
+        const int e1 = sweep_smem<BS, T>(ctx, k_lsolve_seg<BS, T>, f->SL.max_run > 1, &sl);
+        const int e2 = e1 ? e1 : sweep_smem<BS, T>(ctx, k_usolve_seg<BS, T>, f->SU.max_run > 1, &su);
         if (e2) return e2;
     }
     {

@@ -146,7 +146,9 @@ struct SegLayout {
     int nseg = 0;
     int nlevels = 0;
     int64_t nent = 0;
-    int *order = nullptr;          // [nseg] segment ids in processing order
+    int nrun = 0;                  // runs: segments one warp takes in turn
+    int max_run = 0;               // segments of the longest run
+    int *runs = nullptr;           // [nrun][5] first segment, count, segment / row / entry strides
     int *sptr = nullptr;           // [nseg+1] first entry of each segment (by id)
     int *col = nullptr;            // [nent] column or -1
     int *src = nullptr;            // [nent] index of the entry in the CSR value array or -1

@@ -378,6 +378,19 @@ extern "C" int rs_precond_sweep_levels(const rs_pc *M, int32_t *levels_l, int32_
     return RS_OK;
 }
 
+extern "C" int rs_precond_sweep_runs(const rs_pc *M, int32_t *runs_l, int32_t *runs_u, int32_t *longest_l,
+                                     int32_t *longest_u)
+{
+    if (!M || !runs_l || !runs_u || !longest_l || !longest_u) return RS_ERR_INVALID_ARG;
+    const IluFactor *f = M->ras ? M->ras->f : M->bilu ? M->bilu : M->ilu;
+    if (!f) return RS_ERR_INVALID_ARG;
+    *runs_l = f->SL.nrun;
+    *runs_u = f->SU.nrun;
+    *longest_l = f->SL.max_run;
+    *longest_u = f->SU.max_run;
+    return RS_OK;
+}
+
 extern "C" int rs_precond_amg_levels(const rs_pc *M, int32_t *nlevels)
 {
     if (!M || !M->amg || !nlevels) return RS_ERR_INVALID_ARG;

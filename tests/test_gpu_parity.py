@@ -175,6 +175,52 @@ def test_sweep_levels_structured(rs, ctx, shape):
         assert M.sweep_levels() == (expect, expect)
 
 
+@pytest.mark.parametrize("shape", [(64, 16, 8), (40, 12, 6), (7, 5, 3), (128, 128, 64)])
+def test_sweep_runs_change_no_result(rs, ctx, orc, shape, monkeypatch):
+    """Runs: on a 7-point grid in natural order a warp follows one x-segment
+    through the y-lines of a plane (the y = 0 line of each x-segment runs
+    through the planes instead), reading the previous segment from its
+    registers.  The schedule changes, the arithmetic does not: results are
+    bit-identical to one segment per ticket, for both precisions and for a
+    capped run length."""
+    nx, ny, nz = shape
+    g = synth.Grid(nx, ny, nz)
+    d = synth.pressure_7pt(g, 9, kz_scale=0.1)
+    A = rs.Mat.csr(ctx, d)
+    Ao = orc.Mat.csr(d)
+    _, _, lu = orc.ilu0(Ao)
+    r = np.random.default_rng(10).standard_normal(g.n)
+    xsegs = -(-nx // 32)
+    nseg = xsegs * ny * nz
+    for prec in ("fp64", "mixed"):
+        monkeypatch.setenv("RS_SWEEP_RUN", "1")
+        M1 = rs.Precond(ctx, A, "ilu0", prec=prec)
+        monkeypatch.setenv("RS_SWEEP_RUN", "4")
+        M4 = rs.Precond(ctx, A, "ilu0", prec=prec)
+        monkeypatch.delenv("RS_SWEEP_RUN")
+        if prec == "mixed":
+            # FP32 sweeps take one segment per ticket unless asked otherwise
+            assert rs.Precond(ctx, A, "ilu0", prec=prec).sweep_runs() == (nseg, nseg, 1, 1)
+            monkeypatch.setenv("RS_SWEEP_RUN", "1000000")
+        M = rs.Precond(ctx, A, "ilu0", prec=prec)
+        monkeypatch.delenv("RS_SWEEP_RUN", raising=False)
+        assert M1.sweep_runs() == (nseg, nseg, 1, 1)
+        runs = M.sweep_runs()
+        # y-runs of ny - 1 segments per (x-segment, plane), z-runs of nz - 1
+        # along the first y-line, single segments on the first line
+        assert runs == (xsegs * (nz + 2),) * 2 + (max(ny, nz) - 1,) * 2, runs
+        assert M4.sweep_runs()[2:] == (4, 4)
+        z1 = rs.Vec.zeros(ctx, g.n)
+        M1.apply(vec(rs, ctx, r), z1)
+        ref = orc.ilu0_solve(Ao, lu, r, fp32=(prec == "mixed"))
+        assert rel(z1.numpy(), ref) <= (1e-12 if prec == "fp64" else 1e-5)
+        for P in (M, M4):
+            z = rs.Vec.zeros(ctx, g.n)
+            for _ in range(2):
+                P.apply(vec(rs, ctx, r), z)
+                assert np.array_equal(z.numpy(), z1.numpy())
+
+
 def test_ilu0_general_pattern(rs, ctx, orc):
     """A random nonsymmetric pattern: in-segment dependencies other than the
     adjacent row take the lane-by-lane path of the sweeps."""
