@@ -30,7 +30,7 @@
 #define RS_RUN_P 6                       // segments staged ahead
 #define RS_RUN_SLOTS (RS_RUN_P + 1)      // the slot being read is never refilled
 #define RS_RUN_WORDS (RS_RUN_CH + 5 + 2) // per lane: values, multipliers, r or y, D
-#define RS_RUN_RING (RS_RUN_SLOTS * RS_RUN_WORDS * 32)   // 8-byte words per warp
+#define RS_RUN_RING ((RS_RUN_SLOTS + 1) * RS_RUN_WORDS * 32)   // 8-byte words per warp, with a spare slot
 
 // ---------------------------------------------------------------------------
 // host analysis
@@ -91,7 +91,7 @@ static int build_layout(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
 // segments holding the columns it reads outside itself.
 static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
                           const std::vector<int> &col, const std::vector<int> &diag, bool lower,
-                          int run_cap, SegLayout &S)
+                          int run_cap, int64_t run_slots, SegLayout &S)
 {
     // does row i read row j = i-1 (L) / i+1 (U)?  (the entry next to the diagonal)
     auto reads_prev = [&](int i) { return i > 0 && diag[i] > ptr[i] && col[diag[i] - 1] == i - 1; };
@@ -171,10 +171,12 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     // Runs.  A warp that has finished segment p may go on with a segment s
     // of the next level that reads p, taking p's values from its registers
     // instead of from memory.  s joins p's run when
-    //  * s is p shifted by a fixed number of rows (same length, width and
-    //    kind; every column shifted by the same amount), and the run's
-    //    segment, row and entry strides stay constant, so that the warp
-    //    computes every later segment's addresses without loads;
+    //  * s is p shifted by a fixed number of rows (same length; from the
+    //    run's second segment on also the same width and kind, every column
+    //    shifted by the same amount), and the run's segment and row strides,
+    //    and from the second segment on its entry stride, stay constant, so
+    //    that the warp computes every later segment's addresses without
+    //    loads;
     //  * every other segment s reads lies in an earlier run or earlier in
     //    this one.
     // Runs take tickets in the order they were opened, i.e. in the level
@@ -213,12 +215,16 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
                     if (2 * cand.second < len) break;   // p must feed at least half of s's rows
                     const int p = cand.first, Rp = run_of[p];
                     const int *d = &rdesc[5 * Rp];
-                    if (rlast[Rp] != p || d[1] >= run_cap || lev[p] != lev[sg] - 1 || !kind[p]) continue;
-                    if (r0v[p + 1] - r0v[p] != len || width[p] != width[sg]) continue;
+                    if (rlast[Rp] != p || d[1] >= run_cap || lev[p] != lev[sg] - 1) continue;
+                    if (r0v[p + 1] - r0v[p] != len) continue;
                     const int dseg = sg - p, drow = r0 - r0v[p], dent = sptr[sg] - sptr[p];
-                    if (d[1] >= 2 && (dseg != d[2] || drow != d[3] || dent != d[4])) continue;
+                    // the run's first segment takes the general path, so
+                    // only its rows need to fit; the entries of the later
+                    // segments shift by the row stride from the second on
+                    if (d[1] >= 2 && (dseg != d[2] || drow != d[3] || !kind[p] || width[p] != width[sg])) continue;
+                    if (d[1] >= 3 && dent != d[4]) continue;
                     bool ok = true;
-                    for (int e = 0; e < width[sg] * 32 && ok; ++e) {
+                    for (int e = 0; d[1] >= 2 && e < width[sg] * 32 && ok; ++e) {
                         const int a = ecol[sptr[p] + e], b = ecol[sptr[sg] + e];
                         ok = (a < 0) == (b < 0) && (a < 0 || b == a + drow);
                     }
@@ -233,7 +239,8 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
                 if (d[1] == 1) {
                     d[2] = sg - d[0];
                     d[3] = r0 - r0v[d[0]];
-                    d[4] = sptr[sg] - sptr[d[0]];
+                } else if (d[1] == 2) {
+                    d[4] = sptr[sg] - sptr[rlast[R]];
                 }
                 ++d[1];
                 rlast[R] = sg;
@@ -246,14 +253,17 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
         }
     }
     // Runs pay for their shared-memory ring (which limits a sweep block to
-    // two per SM) only where they take over most of the segments; otherwise
-    // every segment stays a run of its own.
-    if (2 * (int64_t)rlast.size() > nseg) {
+    // two per SM) only where they take over most of the segments and every
+    // run can hold a resident warp at once (many independent chains, as in
+    // the stacked subdomains of RAS, need the warps more); otherwise every
+    // segment stays a run of its own.
+    if (2 * (int64_t)rlast.size() > nseg || (int64_t)rlast.size() > run_slots) {
         rlast.clear();
         rdesc.clear();
         for (int t = 0; t < nseg; ++t) {
             rlast.push_back(order[t]);
             rdesc.insert(rdesc.end(), {order[t], 1, 0, 0, 0});
+            run_of[order[t]] = t;
         }
     }
     const int nrun = (int)rlast.size();
@@ -921,8 +931,8 @@ __device__ __forceinline__ void seg_end(const SegArgs &g)
 // segment's path, in the same order, so a run changes no result.
 
 struct RunCtx {
-    int seg0, dseg, drow, dent, row0, len, off0, w;
-    int c0[RS_RUN_CH];   // this lane's columns in the first segment, or -1
+    int seg0, dseg, drow, dent, row0, len, off1, w;
+    int c1[RS_RUN_CH];   // this lane's columns in the second segment, or -1
     int sl[RS_RUN_CH];   // the lane of the previous segment holding that column
 };
 
@@ -932,7 +942,10 @@ struct RunLook {         // first look at the values a segment reads from memory
     unsigned ext, prv;   // entries read from memory / from the previous segment
 };
 
-__device__ __forceinline__ RunCtx run_ctx(const SegArgs &g, const int *rd, int row0, int len, int off, int w, int lane)
+
+// segment k >= 1 of a run: rows row0 + k drow, segment seg0 + k dseg,
+// entries from off1 + (k - 1) dent, columns c1 + (k - 1) drow
+__device__ __forceinline__ RunCtx run_ctx(const SegArgs &g, const int *rd, int row0, int len, int lane)
 {
     RunCtx rc;
     rc.seg0 = rd[0];
@@ -941,12 +954,13 @@ __device__ __forceinline__ RunCtx run_ctx(const SegArgs &g, const int *rd, int r
     rc.dent = rd[4];
     rc.row0 = row0;
     rc.len = len;
-    rc.off0 = off;
-    rc.w = w;
+    const int s1 = rc.seg0 + rc.dseg;
+    rc.off1 = g.sptr[s1];
+    rc.w = (g.sptr[s1 + 1] - rc.off1) >> 5;
 #pragma unroll
     for (int j = 0; j < RS_RUN_CH; ++j) {
-        rc.c0[j] = j < w ? g.ecol[off + j * 32 + lane] : -1;
-        rc.sl[j] = (rc.c0[j] - row0 + rc.drow) & 31;
+        rc.c1[j] = j < rc.w ? g.ecol[rc.off1 + j * 32 + lane] : -1;
+        rc.sl[j] = (rc.c1[j] - row0) & 31;
     }
     return rc;
 }
@@ -965,17 +979,17 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // committed by the caller); L: r_i and the U work vector's reset;
 // U: y_i and D_i
 template <typename T, bool LOWER>
-__device__ __forceinline__ void run_stage(const RunCtx &rc, int k, int lane, unsigned long long *ring,
+__device__ __forceinline__ void run_stage(const RunCtx &rc, int k, int slot, int lane, unsigned long long *ring,
                                           const T *__restrict__ val, const T *__restrict__ mul,
                                           const double *__restrict__ r, const T *yin, T *reset,
                                           const T *__restrict__ dinv)
 {
     const int row = rc.row0 + k * rc.drow + lane;
-    const int64_t off = rc.off0 + (int64_t)k * rc.dent;
-    unsigned long long *sl = ring + (k % RS_RUN_SLOTS) * RS_RUN_WORDS * 32 + lane;
+    const int64_t off = rc.off1 + (int64_t)(k - 1) * rc.dent;
+    unsigned long long *sl = ring + slot * RS_RUN_WORDS * 32 + lane;
 #pragma unroll
     for (int j = 0; j < RS_RUN_CH; ++j)
-        if (rc.c0[j] >= 0) cp_async_n(sl + j * 32, val + off + j * 32 + lane, sizeof(T));
+        if (rc.c1[j] >= 0) cp_async_n(sl + j * 32, val + off + j * 32 + lane, sizeof(T));
     const T *ms = mul + (size_t)(rc.seg0 + k * rc.dseg) * ScanStage<1, T>::N + lane;
 #pragma unroll
     for (int q = 0; q < 5; ++q) cp_async_n(sl + (RS_RUN_CH + q) * 32, ms + q * 32, sizeof(T));
@@ -1000,9 +1014,9 @@ __device__ __forceinline__ void run_look(const RunCtx &rc, int k, const T *x, Ru
     s.prv = 0;
 #pragma unroll
     for (int j = 0; j < RS_RUN_CH; ++j) {
-        const int c = rc.c0[j] >= 0 ? rc.c0[j] + k * rc.drow : -1;
+        const int c = rc.c1[j] >= 0 ? rc.c1[j] + (k - 1) * rc.drow : -1;
         const bool own = c >= r0 && c < r0 + rc.len;
-        const bool prv = c >= r0 - rc.drow && c < r0 - rc.drow + rc.len;
+        const bool prv = !own && c >= r0 - rc.drow && c < r0 - rc.drow + rc.len;
         const bool ext = c >= 0 && !own && !prv;
         s.ext |= (unsigned)ext << j;
         s.prv |= (unsigned)(c >= 0 && prv) << j;
@@ -1058,7 +1072,7 @@ __device__ __forceinline__ T run_finish(const SegArgs &g, const RunCtx &rc, int 
         ns = first ? min(16u, g.sleep_cap) : min(ns * 2, g.sleep_cap);
 #pragma unroll
         for (int j = 0; j < RS_RUN_CH; ++j)
-            if (((s.ext >> j) & 1u) && s.b[j] == Sentinel<T>::bits) s.b[j] = ld_relaxed_bits(x + (rc.c0[j] + k * rc.drow));
+            if (((s.ext >> j) & 1u) && s.b[j] == Sentinel<T>::bits) s.b[j] = ld_relaxed_bits(x + (rc.c1[j] + (k - 1) * rc.drow));
     }
 #pragma unroll
     for (int j = 0; j < RS_RUN_CH; ++j) {
@@ -1080,9 +1094,11 @@ __device__ __forceinline__ T run_finish(const SegArgs &g, const RunCtx &rc, int 
     return acc;
 }
 
+
+
 // L y = r (unit lower).  scale (device, optional) multiplies r on load;
 // zreset is the U sweep's work vector.
-template <int BS, typename T>
+template <int BS, typename T, bool RUNS>
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
 k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, const double *__restrict__ r,
              const double *__restrict__ scale, T *y, T *zreset)
@@ -1101,7 +1117,7 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
         if (t >= g.nrun) break;
         const int *rd = g.runs + 5 * t;
         const int seg = rd[0];
-        const int count = BS == 1 ? rd[1] : 1;
+        const int count = RUNS ? rd[1] : 1;
         const int row0 = g.row0[seg], len = g.row0[seg + 1] - row0, row = row0 + lane;
         const bool active = lane < len;
         const int off = g.sptr[seg];
@@ -1119,12 +1135,12 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
         }
         RunCtx rc;
         RunLook<T> nx;
-        if constexpr (BS == 1) {
+        if constexpr (RUNS) {
             if (count > 1) {
-                rc = run_ctx(g, rd, row0, len, off, w, lane);
+                rc = run_ctx(g, rd, row0, len, lane);
                 cp_async_commit();   // the first segment's multipliers
                 for (int k = 1; k <= RS_RUN_P; ++k) {
-                    if (k < count) run_stage<T, true>(rc, k, lane, ring, val, mul, r, nullptr, zreset, nullptr);
+                    if (k < count) run_stage<T, true>(rc, k, k % RS_RUN_SLOTS, lane, ring, val, mul, r, nullptr, zreset, nullptr);
                     cp_async_commit();
                 }
                 run_look<T>(rc, 1, y, nx);
@@ -1155,17 +1171,21 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
 #pragma unroll
             for (int k = 0; k < BS; ++k) st_relaxed(y + (size_t)row * BS + k, acc[k]);
         }
-        if constexpr (BS == 1) {
+        if constexpr (RUNS) {
             T prev = acc[0];
             bool late = false;
             for (int k = 1; k < count; ++k) {
-                cp_async_wait<RS_RUN_P - 1>();   // segment k's slot has arrived
-                if (k + RS_RUN_P < count)
-                    run_stage<T, true>(rc, k + RS_RUN_P, lane, ring, val, mul, r, nullptr, zreset, nullptr);
-                cp_async_commit();
                 RunLook<T> cur = nx;
-                if (k + 1 < count) run_look<T>(rc, k + 1, y, nx);
+                run_look<T>(rc, min(k + 1, count - 1), y, nx);
+                cp_async_wait<RS_RUN_P - 1>();   // segment k's slot has arrived
                 prev = run_finish<T, true>(g, rc, k, lane, ring, cur, prev, y, nullptr, nullptr, sc, late);
+                // segment k + RS_RUN_P into its slot, or (past the run's end,
+                // so that no branch splits this block from the scan) the last
+                // segment again into the spare slot
+                const bool in = k + RS_RUN_P < count;
+                run_stage<T, true>(rc, in ? k + RS_RUN_P : count - 1, in ? (k + RS_RUN_P) % RS_RUN_SLOTS : RS_RUN_SLOTS,
+                                   lane, ring, val, mul, r, nullptr, zreset, nullptr);
+                cp_async_commit();
             }
         }
     }
@@ -1176,7 +1196,7 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
 // D_i per row, plane-major, so z_i = D_i y_i - sum_j (D_i U_ij) z_j; z carries
 // values between rows and is reset to the sentinel by the next L sweep; out
 // (FP64) receives the result; y is reset for the next L sweep.
-template <int BS, typename T>
+template <int BS, typename T, bool RUNS>
 __global__ void __launch_bounds__(RS_SWEEP_THREADS)
 k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, const T *__restrict__ dinv, T *y,
              T *z, double *__restrict__ out)
@@ -1194,7 +1214,7 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
         if (t >= g.nrun) break;
         const int *rd = g.runs + 5 * t;
         const int seg = rd[0];
-        const int count = BS == 1 ? rd[1] : 1;
+        const int count = RUNS ? rd[1] : 1;
         const int row0 = g.row0[seg], len = g.row0[seg + 1] - row0, row = row0 + lane;
         const bool active = lane < len;
         const int off = g.sptr[seg];
@@ -1219,12 +1239,12 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
         }
         RunCtx rc;
         RunLook<T> nx;
-        if constexpr (BS == 1) {
+        if constexpr (RUNS) {
             if (count > 1) {
-                rc = run_ctx(g, rd, row0, len, off, w, lane);
+                rc = run_ctx(g, rd, row0, len, lane);
                 cp_async_commit();   // the first segment's multipliers
                 for (int k = 1; k <= RS_RUN_P; ++k) {
-                    if (k < count) run_stage<T, false>(rc, k, lane, ring, val, mul, nullptr, y, nullptr, dinv);
+                    if (k < count) run_stage<T, false>(rc, k, k % RS_RUN_SLOTS, lane, ring, val, mul, nullptr, y, nullptr, dinv);
                     cp_async_commit();
                 }
                 run_look<T>(rc, 1, z, nx);
@@ -1258,17 +1278,18 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
                 out[(size_t)row * BS + k] = (double)acc[k];
             }
         }
-        if constexpr (BS == 1) {
+        if constexpr (RUNS) {
             T prev = acc[0];
             bool late = false;
             for (int k = 1; k < count; ++k) {
-                cp_async_wait<RS_RUN_P - 1>();   // segment k's slot has arrived
-                if (k + RS_RUN_P < count)
-                    run_stage<T, false>(rc, k + RS_RUN_P, lane, ring, val, mul, nullptr, y, nullptr, dinv);
-                cp_async_commit();
                 RunLook<T> cur = nx;
-                if (k + 1 < count) run_look<T>(rc, k + 1, z, nx);
+                run_look<T>(rc, min(k + 1, count - 1), z, nx);
+                cp_async_wait<RS_RUN_P - 1>();   // segment k's slot has arrived
                 prev = run_finish<T, false>(g, rc, k, lane, ring, cur, prev, z, y, out, 1.0, late);
+                const bool in = k + RS_RUN_P < count;
+                run_stage<T, false>(rc, in ? k + RS_RUN_P : count - 1, in ? (k + RS_RUN_P) % RS_RUN_SLOTS : RS_RUN_SLOTS,
+                                    lane, ring, val, mul, nullptr, y, nullptr, dinv);
+                cp_async_commit();
             }
         }
     }
@@ -1324,8 +1345,12 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
         if (v >= 1) run_cap = v;
     }
     if (bs != 1) run_cap = 1;
-    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, run_cap, f->SL);
-    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, run_cap, f->SU);
+    // warps resident at once in sweep blocks that carry the runs' ring
+    const int64_t run_block = (int64_t)(RS_SWEEP_THREADS / 32) *
+                              (5 * 32 * (fp32 ? sizeof(float) : sizeof(double)) + RS_RUN_RING * sizeof(unsigned long long));
+    const int64_t run_slots = std::max<int64_t>(1, (int64_t)227 * 1024 / run_block) * (RS_SWEEP_THREADS / 32) * ctx->num_sms;
+    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, run_cap, run_slots, f->SL);
+    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, run_cap, run_slots, f->SU);
     // sweep blocks: a single dependency chain (global ILU in natural order)
     // gains nothing from more warps, which only add polling; many
     // independent chains (the stacked subdomains of RAS) do.  Aim at three
@@ -1472,13 +1497,14 @@ int rs_ilu_set_factors(IluFactor *f, const double *d_lu, int *bad_row)
 
 // Dynamic shared memory of a sweep block: one scan stage per warp.  Above the
 // default 48 KB the kernel's limit is raised once per device.
-template <int BS, typename T, class K>
-static int sweep_smem(rs_ctx *ctx, K kernel, bool runs, size_t *bytes)
+template <int BS, typename T, bool RUNS, bool LOWER, class K>
+static int sweep_smem(rs_ctx *ctx, K kernel, size_t *bytes)
 {
-    static unsigned long long raised = 0;
-    const size_t stage = (size_t)(RS_SWEEP_THREADS / 32) * ScanStage<BS, T>::N * sizeof(T);
-    const size_t ring = BS == 1 ? (size_t)(RS_SWEEP_THREADS / 32) * RS_RUN_RING * sizeof(unsigned long long) : 0;
-    *bytes = stage + (runs ? ring : 0);
+    static unsigned long long raised = 0;   // one per kernel instantiation
+    const size_t wpb = RS_SWEEP_THREADS / 32;
+    const size_t stage = wpb * ScanStage<BS, T>::N * sizeof(T);
+    const size_t ring = RUNS ? wpb * RS_RUN_RING * sizeof(unsigned long long) : 0;
+    *bytes = stage + ring;
     const size_t most = stage + ring;
     if (most <= 48 * 1024) return RS_OK;
     const unsigned long long bit = 1ull << (ctx->device & 63);
@@ -1497,23 +1523,38 @@ static int apply_seg(IluFactor *f, const double *r, double *z, const double *sca
     const int wpb = RS_SWEEP_THREADS / 32;
     const int gl = std::max(1, std::min((f->SL.nrun + wpb - 1) / wpb, f->SL.grid));
     const int gu = std::max(1, std::min((f->SU.nrun + wpb - 1) / wpb, f->SU.grid));
+    // layouts with runs (scalar factors only) take the kernels that carry
+    // the run code and the ring; the others keep the leaner kernels, whose
+    // register count lets more sweep blocks share an SM
+    const bool rl = BS == 1 && f->SL.max_run > 1, ru = BS == 1 && f->SU.max_run > 1;
     size_t sl = 0, su = 0;
     {
-        const int e1 = sweep_smem<BS, T>(ctx, k_lsolve_seg<BS, T>, f->SL.max_run > 1, &sl);
-        const int e2 = e1 ? e1 : sweep_smem<BS, T>(ctx, k_usolve_seg<BS, T>, f->SU.max_run > 1, &su);
+        const int e1 = rl ? sweep_smem<BS, T, true, true>(ctx, k_lsolve_seg<BS, T, BS == 1>, &sl)
+                          : sweep_smem<BS, T, false, true>(ctx, k_lsolve_seg<BS, T, false>, &sl);
+        const int e2 = e1 ? e1
+                          : ru ? sweep_smem<BS, T, true, false>(ctx, k_usolve_seg<BS, T, BS == 1>, &su)
+                               : sweep_smem<BS, T, false, false>(ctx, k_usolve_seg<BS, T, false>, &su);
         if (e2) return e2;
     }
     {
         RsProfScope prof(ctx, BS == 1 ? RS_PROF_LSWEEP : RS_PROF_BLSWEEP);
-        k_lsolve_seg<BS, T><<<gl, RS_SWEEP_THREADS, sl, ctx->stream>>>(
-            seg_args(ctx, f->SL, f->nrows, f->state, skip), (const T *)f->SL.val, (const T *)f->SL.mul, r, scale, y,
-            zt);
+        const SegArgs a = seg_args(ctx, f->SL, f->nrows, f->state, skip);
+        if (rl)
+            k_lsolve_seg<BS, T, BS == 1><<<gl, RS_SWEEP_THREADS, sl, ctx->stream>>>(
+                a, (const T *)f->SL.val, (const T *)f->SL.mul, r, scale, y, zt);
+        else
+            k_lsolve_seg<BS, T, false><<<gl, RS_SWEEP_THREADS, sl, ctx->stream>>>(
+                a, (const T *)f->SL.val, (const T *)f->SL.mul, r, scale, y, zt);
     }
     RS_TRY(rs_check_launch(ctx));
     RsProfScope prof(ctx, BS == 1 ? RS_PROF_USWEEP : RS_PROF_BUSWEEP);
-    k_usolve_seg<BS, T><<<gu, RS_SWEEP_THREADS, su, ctx->stream>>>(
-        seg_args(ctx, f->SU, f->nrows, f->state, skip), (const T *)f->SU.val, (const T *)f->SU.mul,
-        (const T *)f->SU.rdiag, y, zt, z);
+    const SegArgs a = seg_args(ctx, f->SU, f->nrows, f->state, skip);
+    if (ru)
+        k_usolve_seg<BS, T, BS == 1><<<gu, RS_SWEEP_THREADS, su, ctx->stream>>>(
+            a, (const T *)f->SU.val, (const T *)f->SU.mul, (const T *)f->SU.rdiag, y, zt, z);
+    else
+        k_usolve_seg<BS, T, false><<<gu, RS_SWEEP_THREADS, su, ctx->stream>>>(
+            a, (const T *)f->SU.val, (const T *)f->SU.mul, (const T *)f->SU.rdiag, y, zt, z);
     return rs_check_launch(ctx);
 }
 

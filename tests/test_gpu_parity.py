@@ -178,11 +178,11 @@ def test_sweep_levels_structured(rs, ctx, shape):
 @pytest.mark.parametrize("shape", [(64, 16, 8), (40, 12, 6), (7, 5, 3), (128, 128, 64)])
 def test_sweep_runs_change_no_result(rs, ctx, orc, shape, monkeypatch):
     """Runs: on a 7-point grid in natural order a warp follows one x-segment
-    through the y-lines of a plane (the y = 0 line of each x-segment runs
-    through the planes instead), reading the previous segment from its
+    through all y-lines of a plane, reading the previous segment from its
     registers.  The schedule changes, the arithmetic does not: results are
     bit-identical to one segment per ticket, for both precisions and for a
-    capped run length."""
+    capped run length.  Where the capped runs would outnumber the warps that
+    can be resident at once, every segment stays a run of its own."""
     nx, ny, nz = shape
     g = synth.Grid(nx, ny, nz)
     d = synth.pressure_7pt(g, 9, kz_scale=0.1)
@@ -192,10 +192,14 @@ def test_sweep_runs_change_no_result(rs, ctx, orc, shape, monkeypatch):
     r = np.random.default_rng(10).standard_normal(g.n)
     xsegs = -(-nx // 32)
     nseg = xsegs * ny * nz
+    nrun = xsegs * nz
     for prec in ("fp64", "mixed"):
         monkeypatch.setenv("RS_SWEEP_RUN", "1")
         M1 = rs.Precond(ctx, A, "ilu0", prec=prec)
-        monkeypatch.setenv("RS_SWEEP_RUN", "4")
+        # capped runs; kept while every run can hold a resident warp (at
+        # most 1216 here: two ring-carrying blocks of four warps per SM)
+        cap = 32 if ny * nz > 4096 else 4
+        monkeypatch.setenv("RS_SWEEP_RUN", str(cap))
         M4 = rs.Precond(ctx, A, "ilu0", prec=prec)
         monkeypatch.delenv("RS_SWEEP_RUN")
         if prec == "mixed":
@@ -205,11 +209,9 @@ def test_sweep_runs_change_no_result(rs, ctx, orc, shape, monkeypatch):
         M = rs.Precond(ctx, A, "ilu0", prec=prec)
         monkeypatch.delenv("RS_SWEEP_RUN", raising=False)
         assert M1.sweep_runs() == (nseg, nseg, 1, 1)
-        runs = M.sweep_runs()
-        # y-runs of ny - 1 segments per (x-segment, plane), z-runs of nz - 1
-        # along the first y-line, single segments on the first line
-        assert runs == (xsegs * (nz + 2),) * 2 + (max(ny, nz) - 1,) * 2, runs
-        assert M4.sweep_runs()[2:] == (4, 4)
+        # a y-run of ny segments per (x-segment, plane)
+        assert M.sweep_runs() == (nrun, nrun, ny, ny), M.sweep_runs()
+        assert M4.sweep_runs()[2:] == (cap, cap)
         z1 = rs.Vec.zeros(ctx, g.n)
         M1.apply(vec(rs, ctx, r), z1)
         ref = orc.ilu0_solve(Ao, lu, r, fp32=(prec == "mixed"))
