@@ -934,12 +934,15 @@ struct RunCtx {
     int seg0, dseg, drow, dent, row0, len, off1, w;
     int c1[RS_RUN_CH];   // this lane's columns in the second segment, or -1
     int sl[RS_RUN_CH];   // the lane of the previous segment holding that column
+    // entries read from memory / from the previous segment: the same at
+    // every step, since columns and rows shift together
+    unsigned ext, prv;
+    bool any_ext;        // does any lane read from memory (warp-uniform)
 };
 
 template <typename T>
 struct RunLook {         // first look at the values a segment reads from memory
     typename Sentinel<T>::bits_t b[RS_RUN_CH];
-    unsigned ext, prv;   // entries read from memory / from the previous segment
 };
 
 
@@ -957,11 +960,21 @@ __device__ __forceinline__ RunCtx run_ctx(const SegArgs &g, const int *rd, int r
     const int s1 = rc.seg0 + rc.dseg;
     rc.off1 = g.sptr[s1];
     rc.w = (g.sptr[s1 + 1] - rc.off1) >> 5;
+    rc.ext = 0;
+    rc.prv = 0;
 #pragma unroll
     for (int j = 0; j < RS_RUN_CH; ++j) {
-        rc.c1[j] = j < rc.w ? g.ecol[rc.off1 + j * 32 + lane] : -1;
-        rc.sl[j] = (rc.c1[j] - row0) & 31;
+        const int c = j < rc.w ? g.ecol[rc.off1 + j * 32 + lane] : -1;
+        rc.c1[j] = c;
+        rc.sl[j] = (c - row0) & 31;
+        // at step k the segment is [row0 + k drow, + len) and the previous
+        // one [row0 + (k - 1) drow, + len); the column is c + (k - 1) drow
+        const bool own = c - row0 - rc.drow >= 0 && c - row0 - rc.drow < len;
+        const bool prv = !own && c - row0 >= 0 && c - row0 < len;
+        rc.ext |= (unsigned)(c >= 0 && !own && !prv) << j;
+        rc.prv |= (unsigned)(c >= 0 && prv) << j;
     }
+    rc.any_ext = __any_sync(0xffffffffu, rc.ext != 0);
     return rc;
 }
 
@@ -1009,19 +1022,9 @@ __device__ __forceinline__ void run_stage(const RunCtx &rc, int k, int slot, int
 template <typename T>
 __device__ __forceinline__ void run_look(const RunCtx &rc, int k, const T *x, RunLook<T> &s)
 {
-    const int r0 = rc.row0 + k * rc.drow;
-    s.ext = 0;
-    s.prv = 0;
 #pragma unroll
-    for (int j = 0; j < RS_RUN_CH; ++j) {
-        const int c = rc.c1[j] >= 0 ? rc.c1[j] + (k - 1) * rc.drow : -1;
-        const bool own = c >= r0 && c < r0 + rc.len;
-        const bool prv = !own && c >= r0 - rc.drow && c < r0 - rc.drow + rc.len;
-        const bool ext = c >= 0 && !own && !prv;
-        s.ext |= (unsigned)ext << j;
-        s.prv |= (unsigned)(c >= 0 && prv) << j;
-        s.b[j] = ext ? ld_relaxed_bits(x + c) : 0;
-    }
+    for (int j = 0; j < RS_RUN_CH; ++j)
+        s.b[j] = ((rc.ext >> j) & 1u) ? ld_relaxed_bits(x + (rc.c1[j] + (k - 1) * rc.drow)) : 0;
 }
 
 // finish segment k of the run from its staged slot: wait for the values
@@ -1053,10 +1056,10 @@ __device__ __forceinline__ T run_finish(const SegArgs &g, const RunCtx &rc, int 
     }
     unsigned ns = 0;
     long long t0 = 0;
-    for (bool first = true;; first = false) {
+    for (bool first = true; rc.any_ext; first = false) {
         bool pend = false;
 #pragma unroll
-        for (int j = 0; j < RS_RUN_CH; ++j) pend |= ((s.ext >> j) & 1u) && s.b[j] == Sentinel<T>::bits;
+        for (int j = 0; j < RS_RUN_CH; ++j) pend |= ((rc.ext >> j) & 1u) && s.b[j] == Sentinel<T>::bits;
         if (!__any_sync(0xffffffffu, pend)) break;
         if (first) {
             t0 = clock64();
@@ -1072,14 +1075,15 @@ __device__ __forceinline__ T run_finish(const SegArgs &g, const RunCtx &rc, int 
         ns = first ? min(16u, g.sleep_cap) : min(ns * 2, g.sleep_cap);
 #pragma unroll
         for (int j = 0; j < RS_RUN_CH; ++j)
-            if (((s.ext >> j) & 1u) && s.b[j] == Sentinel<T>::bits) s.b[j] = ld_relaxed_bits(x + (rc.c1[j] + (k - 1) * rc.drow));
+            if (((rc.ext >> j) & 1u) && s.b[j] == Sentinel<T>::bits) s.b[j] = ld_relaxed_bits(x + (rc.c1[j] + (k - 1) * rc.drow));
     }
+
 #pragma unroll
     for (int j = 0; j < RS_RUN_CH; ++j) {
         if (j >= rc.w) break;
         const T xp = __shfl_sync(0xffffffffu, prev, rc.sl[j]);
-        if ((s.ext >> j) & 1u) acc = msub(acc, v[j], bits_to(T(), s.b[j]));
-        else if ((s.prv >> j) & 1u) acc = msub(acc, v[j], xp);
+        if ((rc.ext >> j) & 1u) acc = msub(acc, v[j], bits_to(T(), s.b[j]));
+        else if ((rc.prv >> j) & 1u) acc = msub(acc, v[j], xp);
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -1107,7 +1111,7 @@ k_lsolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
     if (g.skip && *(volatile const int *)g.skip) return;
     const int lane = threadIdx.x & 31;
     T *stage = (T *)sweep_smem + (threadIdx.x >> 5) * ScanStage<BS, T>::N;
-    unsigned long long *ring = (unsigned long long *)((T *)sweep_smem + (RS_SWEEP_THREADS / 32) * ScanStage<BS, T>::N) +
+    unsigned long long *ring = (unsigned long long *)((T *)sweep_smem + (blockDim.x >> 5) * ScanStage<BS, T>::N) +
                                (threadIdx.x >> 5) * RS_RUN_RING;
     const double sc = scale ? *scale : 1.0;
     for (;;) {
@@ -1205,7 +1209,7 @@ k_usolve_seg(SegArgs g, const T *__restrict__ val, const T *__restrict__ mul, co
     if (g.skip && *(volatile const int *)g.skip) return;
     const int lane = threadIdx.x & 31;
     T *stage = (T *)sweep_smem + (threadIdx.x >> 5) * ScanStage<BS, T>::N;
-    unsigned long long *ring = (unsigned long long *)((T *)sweep_smem + (RS_SWEEP_THREADS / 32) * ScanStage<BS, T>::N) +
+    unsigned long long *ring = (unsigned long long *)((T *)sweep_smem + (blockDim.x >> 5) * ScanStage<BS, T>::N) +
                                (threadIdx.x >> 5) * RS_RUN_RING;
     for (;;) {
         int t = 0;
@@ -1345,6 +1349,13 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
         if (v >= 1) run_cap = v;
     }
     if (bs != 1) run_cap = 1;
+    // one run per block by default: the runs of a sweep then spread over
+    // more SMs (83.4 against 84.3 ms per GMRES(30)+ILU(0) solve at
+    // 128 x 128 x 64 with four per block); RS_SWEEP_RUN_WARPS = 1, 2 or 4
+    if (const char *e = getenv("RS_SWEEP_RUN_WARPS")) {
+        const int v = atoi(e);
+        if (v == 1 || v == 2 || v == 4) f->run_warps = v;
+    }
     // warps resident at once in sweep blocks that carry the runs' ring
     const int64_t run_block = (int64_t)(RS_SWEEP_THREADS / 32) *
                               (5 * 32 * (fp32 ? sizeof(float) : sizeof(double)) + RS_RUN_RING * sizeof(unsigned long long));
@@ -1498,14 +1509,12 @@ int rs_ilu_set_factors(IluFactor *f, const double *d_lu, int *bad_row)
 // Dynamic shared memory of a sweep block: one scan stage per warp.  Above the
 // default 48 KB the kernel's limit is raised once per device.
 template <int BS, typename T, bool RUNS, bool LOWER, class K>
-static int sweep_smem(rs_ctx *ctx, K kernel, size_t *bytes)
+static int sweep_smem(rs_ctx *ctx, K kernel, int wpb, size_t *bytes)
 {
     static unsigned long long raised = 0;   // one per kernel instantiation
-    const size_t wpb = RS_SWEEP_THREADS / 32;
-    const size_t stage = wpb * ScanStage<BS, T>::N * sizeof(T);
-    const size_t ring = RUNS ? wpb * RS_RUN_RING * sizeof(unsigned long long) : 0;
-    *bytes = stage + ring;
-    const size_t most = stage + ring;
+    const size_t per_warp = ScanStage<BS, T>::N * sizeof(T) + (RUNS ? RS_RUN_RING * sizeof(unsigned long long) : 0);
+    *bytes = (size_t)wpb * per_warp;
+    const size_t most = (size_t)(RS_SWEEP_THREADS / 32) * per_warp;
     if (most <= 48 * 1024) return RS_OK;
     const unsigned long long bit = 1ull << (ctx->device & 63);
     if (!(raised & bit)) {
@@ -1520,40 +1529,41 @@ static int apply_seg(IluFactor *f, const double *r, double *z, const double *sca
 {
     rs_ctx *ctx = f->ctx;
     T *y = (T *)f->ywork, *zt = (T *)f->zwork;
-    const int wpb = RS_SWEEP_THREADS / 32;
-    const int gl = std::max(1, std::min((f->SL.nrun + wpb - 1) / wpb, f->SL.grid));
-    const int gu = std::max(1, std::min((f->SU.nrun + wpb - 1) / wpb, f->SU.grid));
     // layouts with runs (scalar factors only) take the kernels that carry
-    // the run code and the ring; the others keep the leaner kernels, whose
-    // register count lets more sweep blocks share an SM
+    // the run code and the ring, in blocks of run_warps warps, one run per
+    // warp; the others keep the leaner kernels, whose register count lets
+    // more sweep blocks share an SM
     const bool rl = BS == 1 && f->SL.max_run > 1, ru = BS == 1 && f->SU.max_run > 1;
+    const int wl = rl ? f->run_warps : RS_SWEEP_THREADS / 32, wu = ru ? f->run_warps : RS_SWEEP_THREADS / 32;
+    const int gl = std::max(1, rl ? (f->SL.nrun + wl - 1) / wl : std::min((f->SL.nrun + wl - 1) / wl, f->SL.grid));
+    const int gu = std::max(1, ru ? (f->SU.nrun + wu - 1) / wu : std::min((f->SU.nrun + wu - 1) / wu, f->SU.grid));
     size_t sl = 0, su = 0;
     {
-        const int e1 = rl ? sweep_smem<BS, T, true, true>(ctx, k_lsolve_seg<BS, T, BS == 1>, &sl)
-                          : sweep_smem<BS, T, false, true>(ctx, k_lsolve_seg<BS, T, false>, &sl);
+        const int e1 = rl ? sweep_smem<BS, T, true, true>(ctx, k_lsolve_seg<BS, T, BS == 1>, wl, &sl)
+                          : sweep_smem<BS, T, false, true>(ctx, k_lsolve_seg<BS, T, false>, wl, &sl);
         const int e2 = e1 ? e1
-                          : ru ? sweep_smem<BS, T, true, false>(ctx, k_usolve_seg<BS, T, BS == 1>, &su)
-                               : sweep_smem<BS, T, false, false>(ctx, k_usolve_seg<BS, T, false>, &su);
+                          : ru ? sweep_smem<BS, T, true, false>(ctx, k_usolve_seg<BS, T, BS == 1>, wu, &su)
+                               : sweep_smem<BS, T, false, false>(ctx, k_usolve_seg<BS, T, false>, wu, &su);
         if (e2) return e2;
     }
     {
         RsProfScope prof(ctx, BS == 1 ? RS_PROF_LSWEEP : RS_PROF_BLSWEEP);
         const SegArgs a = seg_args(ctx, f->SL, f->nrows, f->state, skip);
         if (rl)
-            k_lsolve_seg<BS, T, BS == 1><<<gl, RS_SWEEP_THREADS, sl, ctx->stream>>>(
+            k_lsolve_seg<BS, T, BS == 1><<<gl, 32 * wl, sl, ctx->stream>>>(
                 a, (const T *)f->SL.val, (const T *)f->SL.mul, r, scale, y, zt);
         else
-            k_lsolve_seg<BS, T, false><<<gl, RS_SWEEP_THREADS, sl, ctx->stream>>>(
+            k_lsolve_seg<BS, T, false><<<gl, 32 * wl, sl, ctx->stream>>>(
                 a, (const T *)f->SL.val, (const T *)f->SL.mul, r, scale, y, zt);
     }
     RS_TRY(rs_check_launch(ctx));
     RsProfScope prof(ctx, BS == 1 ? RS_PROF_USWEEP : RS_PROF_BUSWEEP);
     const SegArgs a = seg_args(ctx, f->SU, f->nrows, f->state, skip);
     if (ru)
-        k_usolve_seg<BS, T, BS == 1><<<gu, RS_SWEEP_THREADS, su, ctx->stream>>>(
+        k_usolve_seg<BS, T, BS == 1><<<gu, 32 * wu, su, ctx->stream>>>(
             a, (const T *)f->SU.val, (const T *)f->SU.mul, (const T *)f->SU.rdiag, y, zt, z);
     else
-        k_usolve_seg<BS, T, false><<<gu, RS_SWEEP_THREADS, su, ctx->stream>>>(
+        k_usolve_seg<BS, T, false><<<gu, 32 * wu, su, ctx->stream>>>(
             a, (const T *)f->SU.val, (const T *)f->SU.mul, (const T *)f->SU.rdiag, y, zt, z);
     return rs_check_launch(ctx);
 }

@@ -168,6 +168,7 @@ struct IluFactor {
     int nrows = 0;
     int64_t nnzb = 0;
     int fp32 = 0;            // apply precision
+    int run_warps = 1;       // warps per block of the sweeps with runs
     const int *ptr = nullptr, *col = nullptr;  // pattern (device, borrowed)
     int *diagpos = nullptr;  // [nrows]
     double *lu = nullptr;    // [nnzb*bs*bs] FP64 factors in the matrix pattern
