@@ -252,6 +252,20 @@ struct rs_pc {
     int form;                // rs_cpr_form: order of the CPR stages
     RasData *ras;            // RS_PC_RAS
     AmgData *amg;            // RS_PC_AMG, or the pressure stage of CPR
+    // CUDA graphs of whole CPR applies, one per (r, z, skip) address triple;
+    // gen is the network workspace's generation at capture
+    struct Graph {
+        const double *r;
+        double *z;
+        const int *skip;
+        unsigned gen;
+        cudaGraphExec_t exec;
+        long long nlaunch;
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t capture;
+    int applies;
+    bool nograph;
 };
 
 // ---------------------------------------------------------------------------
@@ -311,6 +325,10 @@ int rs_amg_get_level(const AmgData *M, int l, int32_t *aptr, int32_t *acol, doub
 // CPR / learned pressure stage
 int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip);
 int rs_net_apply_pressure(rs_pc *M, const double *rp, double *zp, const int *skip);
+// the learned stage's workspace for M's grid, allocated if needed; gen
+// changes whenever the workspace is reallocated; same_ctx: the network runs
+// on M's context (and stream)
+int rs_net_prepare(rs_pc *M, unsigned *gen, bool *same_ctx);
 
 // reads back and clears the device error word; maps it to a status
 int rs_collect_device_error(rs_ctx *ctx, int *bad_row);

@@ -89,6 +89,7 @@ struct rs_net {
     double *red;                            // per-block reduction partials
     unsigned *ticket;
     int *flag;                              // non-finite output flag
+    unsigned gen;                           // workspace generation: bumped on every (re)allocation
     double *gout;                           // dL/d(output) (per voxel)
     double *outb;                           // network output during training
     float *headpart;                        // head gradient partials
@@ -1110,6 +1111,7 @@ static int ensure_workspace(rs_net *net, int nx, int ny, int nz)
     net->nx = nx;
     net->ny = ny;
     net->nz = nz;
+    ++net->gen;
     return RS_OK;
 }
 
@@ -1544,6 +1546,15 @@ static int rs_ilu_fallback(rs_pc *M, const double *rp, double *zp, int *flag, co
     k_fallback_flag<<<1, 1, 0, c->stream>>>(flag, skip);
     RS_TRY(rs_check_launch(c));
     return rs_ilu_apply(M->ilu, rp, zp, nullptr, flag + 1);
+}
+
+int rs_net_prepare(rs_pc *M, unsigned *gen, bool *same_ctx)
+{
+    rs_net *net = const_cast<rs_net *>(M->net);
+    RS_TRY(ensure_workspace(net, M->nx, M->ny, M->nz));
+    *gen = net->gen;
+    *same_ctx = net->ctx == M->ctx;
+    return RS_OK;
 }
 
 // pressure stage of the learned CPR preconditioner: zp = net(rp, log k); if

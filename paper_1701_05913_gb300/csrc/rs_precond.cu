@@ -103,6 +103,85 @@ static int cpr_stage(rs_pc *M, char kind, const double *v, double *out, const in
     return RS_OK;
 }
 
+// Algs. 5-8: the first stage maps f to z; every later stage forms
+// t1 = f - A z and adds its correction t2 = stage(t1) to z
+static int cpr_apply(rs_pc *M, const double *r, double *z, const int *skip)
+{
+    rs_ctx *ctx = M->ctx;
+    const rs_mat *A = M->A;
+    static const char *forms[4] = {"PF", "FP", "FPF", "FFPF"};
+    const char *seq = forms[M->form];
+    RS_TRY(cpr_stage(M, seq[0], r, z, skip));
+    for (int k = 1; seq[k]; ++k) {
+        RS_TRY(rs_residual_launch(A, r, z, M->t1, nullptr, skip));
+        RS_TRY(cpr_stage(M, seq[k], M->t1, M->t2, skip));
+        k_copy_add<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(A->n, M->t2, z, 1, skip);
+        RS_TRY(rs_check_launch(ctx));
+    }
+    return RS_OK;
+}
+
+// A CPR apply is a few dozen launches (with the learned stage, the U-Net's
+// layers).  After the first apply, each (r, z, skip) address triple is
+// captured once into a CUDA graph and replayed; a nested AMG V-cycle then
+// runs inside the capture.  Capture runs on a private stream (the caller's
+// may be the legacy default stream, which cannot be captured); replays go to
+// the caller's stream.  A graph of the learned stage is dropped when the
+// network's workspace has been reallocated since (another grid).  With the
+// profiler on, a network on another context, or if a capture fails, the
+// apply is launched kernel by kernel.
+static int cpr_apply_graph(rs_pc *M, const double *r, double *z, const int *skip)
+{
+    rs_ctx *ctx = M->ctx;
+    unsigned gen = 0;
+    bool same = true;
+    if (M->type == RS_PC_CPR_LEARNED) RS_TRY(rs_net_prepare(M, &gen, &same));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!same || ctx->prof_on || M->nograph || cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone)
+        return cpr_apply(M, r, z, skip);
+    for (size_t i = 0; i < M->graphs.size(); ++i) {
+        rs_pc::Graph &g = M->graphs[i];
+        if (g.r != r || g.z != z || g.skip != skip) continue;
+        if (g.gen == gen) {
+            if (cudaGraphLaunch(g.exec, ctx->stream) != cudaSuccess) return RS_ERR_CUDA;
+            ctx->launches += g.nlaunch;
+            return RS_OK;
+        }
+        cudaGraphExecDestroy(g.exec);
+        M->graphs.erase(M->graphs.begin() + i);
+        break;
+    }
+    if (M->applies++ == 0 || M->graphs.size() >= 64) return cpr_apply(M, r, z, skip);
+    if (!M->capture && cudaStreamCreateWithFlags(&M->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        M->nograph = true;
+        return cpr_apply(M, r, z, skip);
+    }
+    const long long l0 = ctx->launches;
+    cudaStream_t user = ctx->stream;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int st = RS_ERR_CUDA;
+    if (cudaStreamBeginCapture(M->capture, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        ctx->stream = M->capture;
+        st = cpr_apply(M, r, z, skip);
+        ctx->stream = user;
+        if (cudaStreamEndCapture(M->capture, &graph) != cudaSuccess) st = RS_ERR_CUDA;
+    }
+    if (!st && (!graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)) st = RS_ERR_CUDA;
+    if (graph) cudaGraphDestroy(graph);
+    if (st) {
+        cudaGetLastError();
+        M->nograph = true;
+        ctx->launches = l0;
+        return cpr_apply(M, r, z, skip);
+    }
+    M->graphs.push_back({r, z, skip, gen, exec, ctx->launches - l0});
+    // the capture has counted the graph's launches once; this is their run
+    return cudaGraphLaunch(exec, user) == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
 int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip)
 {
     rs_ctx *ctx = M->ctx;
@@ -120,20 +199,8 @@ int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip)
     case RS_PC_AMG:
         return rs_amg_apply(M->amg, r, z, skip);
     case RS_PC_CPR:
-    case RS_PC_CPR_LEARNED: {
-        // Algs. 5-8: the first stage maps f to z; every later stage forms
-        // t1 = f - A z and adds its correction t2 = stage(t1) to z
-        static const char *forms[4] = {"PF", "FP", "FPF", "FFPF"};
-        const char *seq = forms[M->form];
-        RS_TRY(cpr_stage(M, seq[0], r, z, skip));
-        for (int k = 1; seq[k]; ++k) {
-            RS_TRY(rs_residual_launch(A, r, z, M->t1, nullptr, skip));
-            RS_TRY(cpr_stage(M, seq[k], M->t1, M->t2, skip));
-            k_copy_add<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(A->n, M->t2, z, 1, skip);
-            RS_TRY(rs_check_launch(ctx));
-        }
-        return RS_OK;
-    }
+    case RS_PC_CPR_LEARNED:
+        return cpr_apply_graph(M, r, z, skip);
     default:
         return RS_ERR_INVALID_ARG;
     }
@@ -143,6 +210,8 @@ static void pc_free(rs_pc *M)
 {
     if (!M) return;
     rs_ctx *ctx = M->ctx;
+    for (const rs_pc::Graph &g : M->graphs) cudaGraphExecDestroy(g.exec);
+    if (M->capture) cudaStreamDestroy(M->capture);
     if (M->ilu && M->ilu != M->bilu) rs_ilu_destroy(M->ilu);
     if (M->bilu) rs_ilu_destroy(M->bilu);
     if (M->ras) rs_ras_destroy(M->ras);
