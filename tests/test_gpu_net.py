@@ -152,3 +152,30 @@ def test_trained_checkpoint_gain_over_ilu0(rs, ctx, orc):
         assert orc.norm2(b - orc.spmv(Ao, x.numpy())) / orc.norm2(b) <= 1e-8
         its[name] = info["iters"]
     assert its["learned"] <= 0.5 * its["ilu0"], its
+
+
+def test_learned_cpr_graph_replays_match_the_direct_apply(rs, ctx):
+    """From the second apply on, a CPR apply is replayed from a CUDA graph.
+    Replays give the first (direct) apply's result bit for bit, also after a
+    forward pass on another grid has reallocated the network's workspace,
+    which the graph captured (the graph is then captured again)."""
+    import torch
+    g = synth.Grid(32, 32, 16)
+    d = synth.pressure_7pt(g, 9)
+    A = rs.Mat.csr(ctx, d)
+    net = rs.Net(ctx, _params(7), out_scale=1.0)
+    M = rs.Precond(ctx, A, "cpr_learned", net=net, log_perm=d["logk"], grid=(g.nx, g.ny, g.nz))
+    r = rs.Vec(ctx, np.random.default_rng(3).standard_normal(g.n))
+    outs = []
+    for i in range(5):
+        if i == 3:
+            shape = (16, 8, 8)
+            rr, lk, _ = _fields(shape, 1)
+            out = torch.zeros(rr.size, dtype=torch.float64, device="cuda")
+            net.forward(shape, _dev(rr), _dev(lk), out)
+        z = rs.Vec.zeros(ctx, g.n) if i == 0 else z
+        M.apply(r, z)
+        outs.append(z.numpy().copy())
+    assert np.isfinite(outs[0]).all()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
