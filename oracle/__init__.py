@@ -118,7 +118,8 @@ def _declare(L):
     L.or_ras_export.argtypes = [C.c_void_p, _i32p, _i32p, _i32p, _f64p]
     L.free.argtypes = [C.c_void_p]
     L.or_amg_setup.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, C.c_int32, C.c_int32, C.c_int32,
-                               C.POINTER(C.c_void_p)]
+                               C.c_int32, C.POINTER(C.c_void_p)]
+    L.or_hgs_sweep.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_int32, C.c_int32, _f64p]
     L.or_amg_free.argtypes = [C.c_void_p]
     L.or_amg_apply.argtypes = [C.c_void_p, _f64p, _f64p]
     L.or_amg_nlevels.argtypes = [C.c_void_p]
@@ -389,17 +390,32 @@ class Ras:
             pass
 
 
+def hgs_sweep(A: Mat, b, x, chunk=32, backward=False):
+    """One hybrid Gauss-Seidel sweep (Fig. 34's relaxation): Gauss-Seidel in
+    row order (backward: reverse order) inside chunks of `chunk` consecutive
+    rows, Jacobi between chunks.  Returns (status, new x)."""
+    assert A.bs == 1
+    b, x = _f64(b), _f64(x)
+    out = np.empty_like(x)
+    st = lib().or_hgs_sweep(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32), _p(A.val, C.c_double),
+                            _p(b, C.c_double), _p(x, C.c_double), chunk, int(backward), _p(out, C.c_double))
+    return st, out
+
+
 class Amg:
     """Algebraic multigrid V-cycle (Algs. 3-4): classical strength (theta),
     Ruge-Stueben first-pass coarsening, direct interpolation, Galerkin coarse
-    matrices, nu l1-Jacobi sweeps before and after, dense coarsest solve."""
+    matrices, nu smoothing sweeps before and after (smoother 0: l1-Jacobi;
+    1: hybrid Gauss-Seidel over 32-row chunks, forward before and backward
+    after the coarse correction), dense coarsest solve."""
 
-    def __init__(self, A: Mat, theta=0.5, max_levels=16, max_coarse=256, nu=2):
+    def __init__(self, A: Mat, theta=0.5, max_levels=16, max_coarse=256, nu=2, smoother=0):
         assert A.bs == 1
         self.A = A
         h = C.c_void_p()
         self.status = lib().or_amg_setup(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
-                                         _p(A.val, C.c_double), theta, max_levels, max_coarse, nu, C.byref(h))
+                                         _p(A.val, C.c_double), theta, max_levels, max_coarse, nu, smoother,
+                                         C.byref(h))
         self.h = h
 
     def apply(self, r):

@@ -820,7 +820,11 @@ void or_ras_export(const or_ras *R, int32_t *gidx, int32_t *ptr, int32_t *col, d
 /*     a_ij over the sum of those of its strong C neighbours; without a      */
 /*     positive strong C coupling the positive couplings join a_ii;          */
 /*  4. R = P^T;  5. A_{l+1} = R A_l P (Eq. 4);                               */
-/*  6. smoother: l1-Jacobi, x <- x + (b - A x) / d with d_i = sum_j |a_ij|.  */
+/*  6. smoother: l1-Jacobi, x <- x + (b - A x) / d with d_i = sum_j |a_ij|, */
+/*     or hybrid Gauss-Seidel (Fig. 34's relaxation: Gauss-Seidel inside a  */
+/*     process, Jacobi between processes), read on one device as chunks of */
+/*     32 consecutive rows: forward sweeps before the coarse correction,    */
+/*     backward sweeps after it, so that the V-cycle stays symmetric.       */
 /* Levels stop at <= max_coarse rows, at max_levels, or when coarsening      */
 /* stalls; the coarsest system is solved with a dense inverse.               */
 /* V-cycle from x = 0 (Alg. 4): nu smoothing sweeps, residual, restriction,  */
@@ -834,8 +838,10 @@ typedef struct {
     double *val;
 } or_csr;
 
+#define OR_HGS_CHUNK 32
+
 typedef struct {
-    int32_t nlev, nu;
+    int32_t nlev, nu, smoother;  /* smoother: 0 l1-Jacobi, 1 hybrid Gauss-Seidel */
     or_csr A[OR_AMG_MAXLEV], P[OR_AMG_MAXLEV], R[OR_AMG_MAXLEV];
     double *d[OR_AMG_MAXLEV];    /* l1-Jacobi diagonal */
     int32_t *cidx[OR_AMG_MAXLEV]; /* coarse index of each point of level l, -1 for F */
@@ -1134,14 +1140,49 @@ void or_amg_free(or_amg *M)
     free(M);
 }
 
+/* One hybrid Gauss-Seidel sweep: the rows are cut into chunks of `chunk`
+ * consecutive rows; inside a chunk, rows are taken in increasing order
+ * (backward: decreasing) and each reads the newest values of its chunk,
+ * while values of other chunks are those of x (Jacobi between chunks):
+ *   out_i = (b_i - sum_{j != i} a_ij v_j) / a_ii,
+ * v_j = out_j for j in i's chunk and already taken, x_j otherwise.
+ * chunk = 1 is Jacobi, chunk >= n plain Gauss-Seidel.  Returns OR_ZERO_PIVOT
+ * (out untouched from that row on) at a row without a nonzero diagonal. */
+int or_hgs_sweep(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, const double *b,
+                 const double *x, int32_t chunk, int32_t backward, double *out)
+{
+    if (chunk < 1) return OR_INVALID;
+    for (int32_t i = 0; i < n; ++i) out[i] = x[i];
+    for (int32_t c0 = 0; c0 < n; c0 += chunk) {
+        const int32_t c1 = c0 + chunk < n ? c0 + chunk : n;
+        for (int32_t t = 0; t < c1 - c0; ++t) {
+            const int32_t i = backward ? c1 - 1 - t : c0 + t;
+            double s = b[i], d = 0.0;
+            for (int32_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+                const int32_t j = col[p];
+                if (j == i) {
+                    d = val[p];
+                    continue;
+                }
+                s -= val[p] * (j >= c0 && j < c1 ? out[j] : x[j]);
+            }
+            if (d == 0.0) return OR_ZERO_PIVOT;
+            out[i] = s / d;
+        }
+    }
+    return OR_OK;
+}
+
 int or_amg_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, double theta,
-                 int32_t max_levels, int32_t max_coarse, int32_t nu, or_amg **out)
+                 int32_t max_levels, int32_t max_coarse, int32_t nu, int32_t smoother, or_amg **out)
 {
     *out = NULL;
-    if (n < 1 || max_levels < 1 || max_levels > OR_AMG_MAXLEV || max_coarse < 1 || nu < 1 || !(theta >= 0.0))
+    if (n < 1 || max_levels < 1 || max_levels > OR_AMG_MAXLEV || max_coarse < 1 || nu < 1 || !(theta >= 0.0) ||
+        smoother < 0 || smoother > 1)
         return OR_INVALID;
     or_amg *M = (or_amg *)calloc(1, sizeof(or_amg));
     M->nu = nu;
+    M->smoother = smoother;
     or_csr *A0 = &M->A[0];
     A0->n = A0->m = n;
     A0->ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
@@ -1154,10 +1195,20 @@ int or_amg_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double
     for (;;) {
         const or_csr *A = &M->A[l];
         M->d[l] = (double *)malloc(sizeof(double) * (size_t)A->n);
+        int nodiag = 0;
         for (int32_t i = 0; i < A->n; ++i) {
-            double s = 0.0;
-            for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) s += fabs(A->val[p]);
+            double s = 0.0, dg = 0.0;
+            for (int32_t p = A->ptr[i]; p < A->ptr[i + 1]; ++p) {
+                s += fabs(A->val[p]);
+                if (A->col[p] == i) dg = A->val[p];
+            }
             M->d[l][i] = s;
+            nodiag |= dg == 0.0;
+        }
+        if (smoother == 1 && nodiag) {   /* Gauss-Seidel divides by a_ii */
+            M->nlev = l + 1;
+            or_amg_free(M);
+            return OR_ZERO_PIVOT;
         }
         if (A->n <= max_coarse || l + 1 >= max_levels) break;
         or_csr P;
@@ -1225,16 +1276,32 @@ static void amg_vcycle(const or_amg *M, int32_t l, const double *b, double *x)
     const int32_t nc = M->A[l + 1].n;
     double *bc = (double *)malloc(sizeof(double) * (size_t)nc);
     double *xc = (double *)malloc(sizeof(double) * (size_t)nc);
-    /* pre-smoothing from x = 0: the first sweep is x = b / d */
-    for (int32_t i = 0; i < n; ++i) x[i] = b[i] / M->d[l][i];
-    for (int32_t s = 1; s < M->nu; ++s) l1_jacobi(A, M->d[l], b, x, t);
+    if (M->smoother == 1) {
+        /* pre-smoothing from x = 0: forward hybrid Gauss-Seidel sweeps */
+        for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
+        for (int32_t s = 0; s < M->nu; ++s) {
+            or_hgs_sweep(n, A->ptr, A->col, A->val, b, x, OR_HGS_CHUNK, 0, t);
+            memcpy(x, t, sizeof(double) * (size_t)n);
+        }
+    } else {
+        /* pre-smoothing from x = 0: the first sweep is x = b / d */
+        for (int32_t i = 0; i < n; ++i) x[i] = b[i] / M->d[l][i];
+        for (int32_t s = 1; s < M->nu; ++s) l1_jacobi(A, M->d[l], b, x, t);
+    }
     csr_mv(A, x, t);
     for (int32_t i = 0; i < n; ++i) t[i] = b[i] - t[i];
     csr_mv(&M->R[l], t, bc);
     amg_vcycle(M, l + 1, bc, xc);
     csr_mv(&M->P[l], xc, t);
     for (int32_t i = 0; i < n; ++i) x[i] = x[i] + t[i];
-    for (int32_t s = 0; s < M->nu; ++s) l1_jacobi(A, M->d[l], b, x, t);
+    for (int32_t s = 0; s < M->nu; ++s) {
+        if (M->smoother == 1) {     /* backward sweeps: the adjoint of the forward ones */
+            or_hgs_sweep(n, A->ptr, A->col, A->val, b, x, OR_HGS_CHUNK, 1, t);
+            memcpy(x, t, sizeof(double) * (size_t)n);
+        } else {
+            l1_jacobi(A, M->d[l], b, x, t);
+        }
+    }
     free(t);
     free(bc);
     free(xc);
