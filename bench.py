@@ -67,6 +67,9 @@ WORKLOADS = {
     # algebraic multigrid (Sec. 4.2, Algs. 3-4): PCG with one V-cycle per iteration
     "cg_amg_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="cg", precond="amg", prec="fp64",
                               amg=dict()),
+    # the same with Fig. 34's hybrid Gauss-Seidel relaxation (32-row chunks)
+    "cg_amg_hgs_128x128x64": dict(kind="csr", grid=(128, 128, 64), kz=0.1, solver="cg", precond="amg",
+                                  prec="fp64", amg=dict(smoother=1)),
     # the paper's CPR with an AMG pressure stage (Sec. 4.2.1, Alg. 6 with M_p = one V-cycle)
     "cpr_amg_fgmres_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="fgmres",
                                            precond="cpr", prec="mixed", pstage="amg", amg=dict()),
@@ -191,16 +194,20 @@ def ras_kwargs(w):
 
 def amg_vcycle_model(w, sizes):
     """SpMV launches and algorithmic bytes of one V-cycle: on every level
-    above the coarsest, 2 nu residuals with A_l, one restriction, one
+    above the coarsest, 2 nu residuals with A_l (one with hybrid
+    Gauss-Seidel smoothing), one restriction, one
     prolongation (bytes of an r x c operator with z entries: 12 z + 4 (r+1)
     + 8 r + 8 c)."""
     nu = w.get("amg", {}).get("nu", 2)
+    # with hybrid Gauss-Seidel the sweeps are their own kernel, not of the
+    # SpMV class: only the residual remains there
+    nres = 1 if w.get("amg", {}).get("smoother", 0) == 1 else 2 * nu
     launches, nbytes = 0, 0
     for l in range(len(sizes) - 1):
         n, za, zp = sizes[l]
         nc = sizes[l + 1][0]
-        launches += 2 * nu + 2
-        nbytes += 2 * nu * (12 * za + 4 * (n + 1) + 16 * n)
+        launches += nres + 2
+        nbytes += nres * (12 * za + 4 * (n + 1) + 16 * n)
         nbytes += (12 * zp + 4 * (nc + 1) + 8 * nc + 8 * n) + (12 * zp + 4 * (n + 1) + 8 * n + 8 * nc)
     return {"launches": launches, "bytes": nbytes}
 

@@ -102,7 +102,7 @@ typedef struct {
     double amg_theta;       /* strength threshold, 0 < theta <= 1 [0.5]      */
     int32_t amg_max_levels; /* 1..16 [16]                                     */
     int32_t amg_max_coarse; /* rows at which coarsening stops, >= 1 [256]     */
-    int32_t amg_nu;         /* l1-Jacobi sweeps before and after, >= 1 [2]    */
+    int32_t amg_nu;         /* smoothing sweeps before and after, >= 1 [2]    */
     int32_t cpr_pstage;     /* RS_PC_CPR pressure stage: 0 ILU(0) of the
                                decoupled matrix, 1 one AMG V-cycle on it     */
     /* RAS local solver (Fig. 31): 0 ILU(ilu_level), 1 ILUT(ilut_p, ilut_tol)
@@ -114,6 +114,12 @@ typedef struct {
     int32_t ras_local;
     int32_t ilut_p;
     double ilut_tol;
+    /* AMG smoother: 0 l1-Jacobi, x <- x + (b - A x) / d with d_i the row's
+     * absolute sum [0]; 1 hybrid Gauss-Seidel (Fig. 34's relaxation), read
+     * as Gauss-Seidel inside chunks of 32 consecutive rows and Jacobi between
+     * chunks, forward before the coarse correction and backward after it;
+     * it needs a nonzero diagonal on every level (else RS_ERR_ZERO_PIVOT). */
+    int32_t amg_smoother;
 } rs_pc_opts;
 
 typedef struct {

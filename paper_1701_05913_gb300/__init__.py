@@ -62,7 +62,8 @@ class PcOpts(C.Structure):
                 ("ras_nparts", C.c_int32), ("ras_overlap", C.c_int32), ("ilu_level", C.c_int32),
                 ("ras_part", _vp), ("amg_theta", C.c_double), ("amg_max_levels", C.c_int32),
                 ("amg_max_coarse", C.c_int32), ("amg_nu", C.c_int32), ("cpr_pstage", C.c_int32),
-                ("ras_local", C.c_int32), ("ilut_p", C.c_int32), ("ilut_tol", C.c_double)]
+                ("ras_local", C.c_int32), ("ilut_p", C.c_int32), ("ilut_tol", C.c_double),
+                ("amg_smoother", C.c_int32)]
 
 
 CPR_FORMS = ("pf", "fp", "fpf", "ffpf")   # rs_cpr_form: Algs. 6, 5, 7, 8
@@ -351,6 +352,7 @@ class Precond:
         opts.amg_max_levels = a.get("max_levels", 0)
         opts.amg_max_coarse = a.get("max_coarse", 0)
         opts.amg_nu = a.get("nu", 0)
+        opts.amg_smoother = a.get("smoother", 0)
         opts.cpr_pstage = {"ilu0": 0, "amg": 1}[pstage]
         if part is not None:
             part = np.ascontiguousarray(part, dtype=np.int32)

@@ -256,6 +256,89 @@ __global__ void k_amg_copy(int n, const double *__restrict__ a, double *__restri
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = a[i];
 }
 
+// One hybrid Gauss-Seidel sweep (Fig. 34's relaxation): a warp per chunk of
+// 32 consecutive rows.  Each lane subtracts from b_i the terms its row takes
+// from xold (null: zero), i.e. columns outside the chunk (Jacobi between
+// chunks) and those of the chunk that the sweep reaches later, keeps its
+// couplings to the chunk's earlier rows in registers (up to RS_HGS_REG; a
+// row with more rescans the rest) and inverts its diagonal.  The lanes then
+// finish in sweep order (increasing rows, BACKWARD: decreasing), each from
+// the new values before it, kept in shared memory: per step one lane's few
+// multiply-adds, so that the FP64 work stays that of one pass over the
+// matrix.
+#define RS_HGS_WARPS 8
+#define RS_HGS_REG 8
+template <bool BACKWARD>
+__global__ void __launch_bounds__(32 * RS_HGS_WARPS)
+k_amg_hgs(int n, const int *__restrict__ ptr, const int *__restrict__ col, const double *__restrict__ val,
+          const double *__restrict__ b, const double *__restrict__ xold, double *__restrict__ xnew, const int *skip)
+{
+    __shared__ double xs[RS_HGS_WARPS][32];
+    if (skip && *(volatile const int *)skip) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nchunk = (n + 31) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunk; c += (gridDim.x * blockDim.x) >> 5) {
+        const int c0 = c << 5, c1 = min(c0 + 32, n), i = c0 + lane;
+        const bool active = i < c1;
+        double s = 0.0, d = 1.0;
+        int ej[RS_HGS_REG];
+        double ev[RS_HGS_REG];
+        int ne = 0;
+        bool over = false;
+#pragma unroll
+        for (int q = 0; q < RS_HGS_REG; ++q) {
+            ej[q] = 0;
+            ev[q] = 0.0;
+        }
+        const int p0 = active ? ptr[i] : 0, p1 = active ? ptr[i + 1] : 0;
+        if (active) {
+            s = b[i];
+            for (int p = p0; p < p1; ++p) {
+                const int j = col[p];
+                const double v = val[p];
+                if (j == i) {
+                    d = v;
+                } else if (j >= c0 && j < c1 && (BACKWARD ? j > i : j < i)) {
+                    if (ne < RS_HGS_REG) {
+#pragma unroll
+                        for (int q = 0; q < RS_HGS_REG; ++q)
+                            if (q == ne) {
+                                ej[q] = j - c0;
+                                ev[q] = v;
+                            }
+                        ++ne;
+                    } else {
+                        over = true;
+                    }
+                } else if (xold) {
+                    s = fma(-v, xold[j], s);
+                }
+            }
+        }
+        const double rd = 1.0 / d;
+        for (int t = 0; t < 32; ++t) {
+            const int k = BACKWARD ? 31 - t : t;
+            if (lane == k && active) {
+#pragma unroll
+                for (int q = 0; q < RS_HGS_REG; ++q)
+                    if (q < ne) s = fma(-ev[q], xs[w][ej[q]], s);
+                if (over) {   // couplings past the first RS_HGS_REG, in row order
+                    int seen = 0;
+                    for (int p = p0; p < p1; ++p) {
+                        const int j = col[p];
+                        if (j >= c0 && j < c1 && (BACKWARD ? j > i : j < i) && seen++ >= RS_HGS_REG)
+                            s = fma(-val[p], xs[w][j - c0], s);
+                    }
+                }
+                xs[w][lane] = s * rd;
+            }
+            __syncwarp();
+        }
+        if (active) xnew[i] = xs[w][lane];
+        __syncwarp();
+    }
+}
+
 // coarsest level: x = Ainv b, one warp per row
 __global__ void k_amg_dense(int n, const double *__restrict__ inv, const double *__restrict__ b,
                             double *__restrict__ x, const int *skip)
@@ -298,14 +381,16 @@ void rs_amg_destroy(AmgData *M)
 
 int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::vector<int> &hcol,
                   const double *d_val, const rs_mat *A0, double theta, int max_levels, int max_coarse, int nu,
-                  AmgData **out)
+                  int smoother, AmgData **out)
 {
     *out = nullptr;
-    if (n < 1 || max_levels < 1 || max_levels > RS_AMG_MAXLEV || max_coarse < 1 || nu < 1 || !(theta >= 0.0))
+    if (n < 1 || max_levels < 1 || max_levels > RS_AMG_MAXLEV || max_coarse < 1 || nu < 1 || !(theta >= 0.0) ||
+        smoother < 0 || smoother > 1)
         return RS_ERR_INVALID_ARG;
     AmgData *M = new AmgData();
     M->ctx = ctx;
     M->nu = nu;
+    M->smoother = smoother;
     M->host = new AmgHost();
     AmgHost &H = *M->host;
     H.A.emplace_back();
@@ -340,6 +425,20 @@ int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::v
     if (H.A.back().n > RS_AMG_MAX_DENSE) {     // coarsening stalled: no small coarsest level
         rs_amg_destroy(M);
         return RS_ERR_INVALID_ARG;
+    }
+    if (smoother == 1) {   // Gauss-Seidel divides by a_ii on every smoothed level
+        for (int l = 0; l + 1 < M->nlev; ++l) {
+            const HCsr &A = H.A[l];
+            for (int i = 0; i < A.n; ++i) {
+                double dg = 0.0;
+                for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+                    if (A.col[p] == i) dg = A.val[p];
+                if (dg == 0.0) {
+                    rs_amg_destroy(M);
+                    return RS_ERR_ZERO_PIVOT;
+                }
+            }
+        }
     }
     std::vector<double> inv;
     {
@@ -415,18 +514,35 @@ static int vcycle(AmgData *M, int l, const double *b, double *x, const int *skip
     const int g = amg_grid(ctx, n);
     const int nu = M->nu;
     double *t = M->t[l];
-    // Jacobi sweeps alternate between x and a second buffer; the first sweep
-    // (from x = 0) is placed so that the last pre-smoothing sweep lands in x
+    // sweeps alternate between x and a second buffer; the first sweep (from
+    // x = 0) is placed so that the last pre-smoothing sweep lands in x
     double *X = x, *Y = l == 0 ? M->x[0] : M->y[l];
     double *cur = (nu - 1) % 2 == 0 ? X : Y, *oth = cur == X ? Y : X;
-    {
-        RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
-        k_amg_first<<<g, 256, 0, ctx->stream>>>(n, b, M->d[l], cur, skip);
-    }
-    RS_TRY(rs_check_launch(ctx));
-    for (int s = 1; s < nu; ++s) {
-        RS_TRY(rs_jacobi_launch(A, b, cur, M->d[l], oth, skip));
-        std::swap(cur, oth);
+    const int gh = std::max(1, std::min((n + 32 * RS_HGS_WARPS - 1) / (32 * RS_HGS_WARPS), ctx->num_sms * 16));
+    if (M->smoother == 1) {
+        {
+            RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
+            k_amg_hgs<false><<<gh, 32 * RS_HGS_WARPS, 0, ctx->stream>>>(n, A->ptr, A->col, A->val, b, nullptr, cur, skip);
+        }
+        RS_TRY(rs_check_launch(ctx));
+        for (int s = 1; s < nu; ++s) {
+            {
+                RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
+                k_amg_hgs<false><<<gh, 32 * RS_HGS_WARPS, 0, ctx->stream>>>(n, A->ptr, A->col, A->val, b, cur, oth, skip);
+            }
+            RS_TRY(rs_check_launch(ctx));
+            std::swap(cur, oth);
+        }
+    } else {
+        {
+            RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
+            k_amg_first<<<g, 256, 0, ctx->stream>>>(n, b, M->d[l], cur, skip);
+        }
+        RS_TRY(rs_check_launch(ctx));
+        for (int s = 1; s < nu; ++s) {
+            RS_TRY(rs_jacobi_launch(A, b, cur, M->d[l], oth, skip));
+            std::swap(cur, oth);
+        }
     }
     RS_TRY(rs_residual_launch(A, b, X, t, nullptr, skip));
     RS_TRY(rs_spmv_launch(M->R[l], t, 1.0, 0.0, M->b[l + 1], skip));
@@ -435,7 +551,15 @@ static int vcycle(AmgData *M, int l, const double *b, double *x, const int *skip
     cur = X;
     oth = Y;
     for (int s = 0; s < nu; ++s) {
-        RS_TRY(rs_jacobi_launch(A, b, cur, M->d[l], oth, skip));
+        if (M->smoother == 1) {   // backward sweeps: the adjoint of the forward ones
+            {
+                RsProfScope prof(ctx, RS_PROF_PRECOND_OTHER);
+                k_amg_hgs<true><<<gh, 32 * RS_HGS_WARPS, 0, ctx->stream>>>(n, A->ptr, A->col, A->val, b, cur, oth, skip);
+            }
+            RS_TRY(rs_check_launch(ctx));
+        } else {
+            RS_TRY(rs_jacobi_launch(A, b, cur, M->d[l], oth, skip));
+        }
         std::swap(cur, oth);
     }
     if (cur != X) {       // an odd number of post-smoothing sweeps

@@ -218,6 +218,7 @@ struct AmgGraph {
 struct AmgData {
     rs_ctx *ctx = nullptr;
     int nlev = 0, nu = 2;
+    int smoother = 0;            // 0 l1-Jacobi, 1 hybrid Gauss-Seidel over 32-row chunks
     bool own0 = false;           // level-0 matrix built here (not the caller's)
     rs_mat *A[RS_AMG_MAXLEV] = {}, *P[RS_AMG_MAXLEV] = {}, *R[RS_AMG_MAXLEV] = {};
     double *d[RS_AMG_MAXLEV] = {}, *b[RS_AMG_MAXLEV] = {}, *x[RS_AMG_MAXLEV] = {}, *t[RS_AMG_MAXLEV] = {};
@@ -315,7 +316,7 @@ void rs_ras_destroy(RasData *R);
 // from the host pattern and the device values d_val)
 int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::vector<int> &hcol,
                   const double *d_val, const rs_mat *A0, double theta, int max_levels, int max_coarse, int nu,
-                  AmgData **out);
+                  int smoother, AmgData **out);
 int rs_amg_apply(AmgData *M, const double *r, double *z, const int *skip);
 void rs_amg_destroy(AmgData *M);
 int rs_amg_level_sizes(const AmgData *M, int l, int32_t *n, int64_t *nnz_a, int64_t *nnz_p);

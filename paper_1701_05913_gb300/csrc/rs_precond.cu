@@ -197,6 +197,7 @@ int rs_pc_apply_dev(rs_pc *M, const double *r, double *z, const int *skip)
     case RS_PC_RAS:
         return rs_ras_apply(M->ras, r, z, skip);
     case RS_PC_AMG:
+        if (!M->amg) return RS_ERR_INVALID_ARG;
         return rs_amg_apply(M->amg, r, z, skip);
     case RS_PC_CPR:
     case RS_PC_CPR_LEARNED:
@@ -228,13 +229,15 @@ static void pc_free(rs_pc *M)
 
 // AMG options, zeroed fields taking their defaults (Fig. 34's strength 0.5
 // and two relaxation sweeps; up to 16 levels down to 256 rows)
-static int amg_params(const rs_pc_opts *o, double *theta, int *lev, int *coarse, int *nu)
+static int amg_params(const rs_pc_opts *o, double *theta, int *lev, int *coarse, int *nu, int *smoother)
 {
     *theta = o && o->amg_theta != 0.0 ? o->amg_theta : 0.5;
     *lev = o && o->amg_max_levels ? o->amg_max_levels : RS_AMG_MAXLEV;
     *coarse = o && o->amg_max_coarse ? o->amg_max_coarse : 256;
     *nu = o && o->amg_nu ? o->amg_nu : 2;
-    if (!(*theta > 0.0 && *theta <= 1.0) || *lev < 1 || *lev > RS_AMG_MAXLEV || *coarse < 1 || *nu < 1)
+    *smoother = o ? o->amg_smoother : 0;
+    if (!(*theta > 0.0 && *theta <= 1.0) || *lev < 1 || *lev > RS_AMG_MAXLEV || *coarse < 1 || *nu < 1 ||
+        *smoother < 0 || *smoother > 1)
         return RS_ERR_INVALID_ARG;
     return RS_OK;
 }
@@ -272,12 +275,12 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         break;
     case RS_PC_AMG: {
         double th;
-        int lev, nc, nu;
-        if (A->bs != 1 || (st = amg_params(opts, &th, &lev, &nc, &nu))) {
+        int lev, nc, nu, sm;
+        if (A->bs != 1 || (st = amg_params(opts, &th, &lev, &nc, &nu, &sm))) {
             st = RS_ERR_INVALID_ARG;
             break;
         }
-        st = rs_amg_create(ctx, A->nrows, A->h_ptr, A->h_col, A->val, A, th, lev, nc, nu, &M->amg);
+        st = rs_amg_create(ctx, A->nrows, A->h_ptr, A->h_col, A->val, A, th, lev, nc, nu, sm, &M->amg);
         break;
     }
     case RS_PC_RAS: {
@@ -304,8 +307,8 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         }
         const int pstage = opts ? opts->cpr_pstage : 0;
         double th;
-        int lev, ncoarse, nu;
-        if (pstage < 0 || pstage > 1 || (pstage == 1 && amg_params(opts, &th, &lev, &ncoarse, &nu))) {
+        int lev, ncoarse, nu, sm;
+        if (pstage < 0 || pstage > 1 || (pstage == 1 && amg_params(opts, &th, &lev, &ncoarse, &nu, &sm))) {
             st = RS_ERR_INVALID_ARG;
             break;
         }
@@ -326,7 +329,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         if (bs == 1) {
             // pressure stage on A itself: its ILU(0), or an AMG V-cycle
             if (pstage == 1 && type == RS_PC_CPR) {
-                st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, A->val, A, th, lev, ncoarse, nu, &M->amg);
+                st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, A->val, A, th, lev, ncoarse, nu, sm, &M->amg);
             } else if (fras) {
                 st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
                 if (!st) st = rs_ilu_factor(M->ilu, A->val, &bad);
@@ -364,7 +367,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         if (st) break;
         if (pstage == 1 && type == RS_PC_CPR) {
             // AMG V-cycle on the decoupled pressure matrix (the paper's CPR pressure stage)
-            st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, M->app_val, nullptr, th, lev, ncoarse, nu, &M->amg);
+            st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, M->app_val, nullptr, th, lev, ncoarse, nu, sm, &M->amg);
             break;
         }
         st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
@@ -375,9 +378,13 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         st = RS_ERR_INVALID_ARG;
     }
     M->bad_row = bad;
-    if (st == RS_ERR_ZERO_PIVOT) {
+    // a zero pivot of an ILU factor keeps the handle, so that the caller can
+    // query the row; an AMG hierarchy that could not be built leaves none
+    const bool amg_missing =
+        !M->amg && (type == RS_PC_AMG || (type == RS_PC_CPR && opts && opts->cpr_pstage == 1));
+    if (st == RS_ERR_ZERO_PIVOT && !amg_missing) {
         rs_ctx_retain(ctx);
-        *out = M;          // keep the handle so the caller can query the row
+        *out = M;
         return st;
     }
     if (st) {

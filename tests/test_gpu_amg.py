@@ -3,7 +3,8 @@ oracle, through the C ABI.
 
 The hierarchy must match the oracle's: the C/F splitting and the patterns of
 every A_l and P_l bit for bit, values within 1e-12 relative (the Galerkin
-sums run in another order).  The V-cycle apply within 1e-12 relative; PCG /
+sums run in another order).  The V-cycle apply within 1e-12 relative, with
+either smoother; PCG /
 GMRES with AMG within 2 iterations of the oracle, true relative residual
 <= 1e-8, solution within 1e-6 relative.  The test matrices have random
 coefficients so that no strength comparison sits exactly on the threshold.
@@ -53,10 +54,15 @@ def _matrix(kind, shape, kz, seed=70):
     return synth.pressure_7pt(synth.Grid(*shape), seed, kz_scale=kz)
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("kind,shape,kz,kw", PROBLEMS)
-def test_amg_hierarchy_and_vcycle(rs, ctx, orc, kind, shape, kz, kw):
+def test_amg_hierarchy_and_vcycle(rs, ctx, orc, kind, shape, kz, kw, smoother):
+    """smoother 0: l1-Jacobi; 1: hybrid Gauss-Seidel over 32-row chunks
+    (Fig. 34's relaxation), forward before and backward after the coarse
+    correction."""
     d = _matrix(kind, shape, kz)
     n = d["n"]
+    kw = dict(kw, smoother=smoother)
     A = rs.Mat.csr(ctx, d)
     M = rs.Precond(ctx, A, "amg", amg=kw)
     R = orc.Amg(orc.Mat.csr(d), **kw)
@@ -80,16 +86,17 @@ def test_amg_hierarchy_and_vcycle(rs, ctx, orc, kind, shape, kz, kw):
     assert np.array_equal(z.numpy(), z2.numpy())
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("solver", ["cg", "gmres"])
 @pytest.mark.parametrize("shape,kz", [((32, 32, 32), 1.0), ((30, 22, 13), 0.1)])
-def test_amg_krylov_parity(rs, ctx, orc, solver, shape, kz):
+def test_amg_krylov_parity(rs, ctx, orc, solver, shape, kz, smoother):
     g = synth.Grid(*shape)
     d = synth.pressure_7pt(g, 72, kz_scale=kz)
     Ao = orc.Mat.csr(d)
     b = orc.spmv(Ao, synth.x_true(g.n, 72))
-    Mo = orc.PC(Ao, "amg", amg=dict())
+    Mo = orc.PC(Ao, "amg", amg=dict(smoother=smoother))
     A = rs.Mat.csr(ctx, d)
-    M = rs.Precond(ctx, A, "amg")
+    M = rs.Precond(ctx, A, "amg", amg=dict(smoother=smoother))
     x = rs.Vec.zeros(ctx, g.n)
     if solver == "cg":
         xo, io, _ = orc.cg(Ao, Mo, b, rtol=1e-8)
@@ -105,14 +112,15 @@ def test_amg_krylov_parity(rs, ctx, orc, solver, shape, kz):
     assert rel(xs, xo) <= 1e-6
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("form", ["pf", "fpf"])
-def test_cpr_amg_pressure_stage(rs, ctx, orc, form):
+def test_cpr_amg_pressure_stage(rs, ctx, orc, form, smoother):
     g = synth.Grid(14, 12, 9)
     m = synth.black_oil_bsr3(g, 73)
     Ao = orc.Mat.bsr(m)
-    Mo = orc.PC(Ao, "cpr", form=form, amg=dict())
+    Mo = orc.PC(Ao, "cpr", form=form, amg=dict(smoother=smoother))
     A = rs.Mat.bsr(ctx, m)
-    M = rs.Precond(ctx, A, "cpr", form=form, pstage="amg")
+    M = rs.Precond(ctx, A, "cpr", form=form, pstage="amg", amg=dict(smoother=smoother))
     r = np.random.default_rng(74).standard_normal(A.n)
     z = rs.Vec.zeros(ctx, A.n)
     M.apply(rs.Vec(ctx, r), z)
@@ -128,7 +136,8 @@ def test_cpr_amg_pressure_stage(rs, ctx, orc, form):
 def test_amg_invalid_arguments(rs, ctx):
     g = synth.Grid(8, 7, 6)
     A = rs.Mat.csr(ctx, synth.pressure_7pt(g, 75))
-    for kw in (dict(theta=1.5), dict(theta=-0.1), dict(max_levels=17), dict(nu=-1), dict(max_coarse=-3)):
+    for kw in (dict(theta=1.5), dict(theta=-0.1), dict(max_levels=17), dict(nu=-1), dict(max_coarse=-3),
+               dict(smoother=2), dict(smoother=-1)):
         with pytest.raises(rs.RsError) as e:
             rs.Precond(ctx, A, "amg", amg=kw)
         assert e.value.status == rs.ERR_INVALID_ARG, kw
@@ -136,6 +145,16 @@ def test_amg_invalid_arguments(rs, ctx):
     with pytest.raises(rs.RsError) as e:
         rs.Precond(ctx, B, "amg")
     assert e.value.status == rs.ERR_INVALID_ARG
+    # Gauss-Seidel needs a nonzero diagonal on every smoothed level
+    d = _poisson1d(40)
+    dz = dict(d, val=d["val"].copy())
+    dz["val"][d["rowptr"][7] + 1] = 0.0             # a_77 = 0 (row 7: entries 6, 7, 8)
+    Z = rs.Mat.csr(ctx, dz)
+    Mz = rs.Precond(ctx, Z, "amg", amg=dict(smoother=1, max_coarse=4))
+    assert Mz.status == rs.ERR_ZERO_PIVOT and not Mz.h    # no hierarchy, no handle
+    with pytest.raises(rs.RsError):
+        Mz.apply(rs.Vec.zeros(ctx, 40), rs.Vec.zeros(ctx, 40))
+    assert rs.Precond(ctx, Z, "amg", amg=dict(smoother=0, max_coarse=4)).status == rs.OK
 
 
 def test_amg_degenerate_cases(rs, ctx, orc):
