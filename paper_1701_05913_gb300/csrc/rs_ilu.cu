@@ -13,7 +13,9 @@
 //  * Sweeps: rows are grouped into segments of up to 32 consecutive (block)
 //    rows, one warp each, taken in segment-level order; a row's value is its
 //    own ready flag (a sentinel NaN pattern until written); the in-segment
-//    recurrence is solved with a warp scan (details at the kernels).
+//    recurrence is solved with a warp scan (details at the kernels).  In
+//    FP64 scalar sweeps a warp carries a run of segments, each reading the
+//    one before it from the warp's registers (details at the runs).
 //  * Every wait is bounded in time and reports RS_ERR_DEVICE_TIMEOUT instead
 //    of hanging; every schedule is deadlock-free because a warp only waits for
 //    rows held by warps that took earlier tickets and are already running.
@@ -919,16 +921,17 @@ __device__ __forceinline__ void seg_end(const SegArgs &g)
 // ---------------------------------------------------------------------------
 // runs: the later segments of a run (scalar factors only)
 // ---------------------------------------------------------------------------
-// Segment k of a run is its first segment shifted by k row strides: its
-// rows, entries, multipliers and columns follow from the first segment and
-// the run's strides.  A warp copies the factor values, multipliers and
-// right-hand side of segment k + RS_RUN_P into a ring of shared-memory
-// slots (cp.async, one group per segment) while it finishes segment k, so
-// the HBM latency stays off the run's path; it takes a first look at the
-// values segment k + 1 reads from other warps one segment ahead.  Entries
-// that read segment k - 1 take its values from the warp's registers (a
-// shuffle) instead of polling memory.  The arithmetic is that of the first
-// segment's path, in the same order, so a run changes no result.
+// Segment k of a run is its first segment shifted by k row strides; from
+// the second segment on, its entries and columns follow by the run's strides
+// as well (the first segment, which may differ, takes the general path).  A
+// warp copies the factor values, multipliers and right-hand side of segment
+// k + RS_RUN_P into a ring of shared-memory slots (cp.async, one group per
+// segment) after it has scanned segment k, so the HBM latency stays off the
+// run's path; it takes a first look at the values segment k + 1 reads from
+// other warps one segment ahead.  Entries that read segment k - 1 take its
+// values from the warp's registers (a shuffle) instead of polling memory.
+// The arithmetic is that of the general path, in the same order, so a run
+// changes no result.
 
 struct RunCtx {
     int seg0, dseg, drow, dent, row0, len, off1, w;
@@ -944,7 +947,6 @@ template <typename T>
 struct RunLook {         // first look at the values a segment reads from memory
     typename Sentinel<T>::bits_t b[RS_RUN_CH];
 };
-
 
 // segment k >= 1 of a run: rows row0 + k drow, segment seg0 + k dseg,
 // entries from off1 + (k - 1) dent, columns c1 + (k - 1) drow
