@@ -261,11 +261,10 @@ __global__ void k_amg_copy(int n, const double *__restrict__ a, double *__restri
 // from xold (null: zero), i.e. columns outside the chunk (Jacobi between
 // chunks) and those of the chunk that the sweep reaches later, keeps its
 // couplings to the chunk's earlier rows in registers (up to RS_HGS_REG; a
-// row with more rescans the rest) and inverts its diagonal.  The lanes then
-// finish in sweep order (increasing rows, BACKWARD: decreasing), each from
-// the new values before it, kept in shared memory: per step one lane's few
-// multiply-adds, so that the FP64 work stays that of one pass over the
-// matrix.
+// row with more rescans the rest) and inverts its diagonal.  A chunk whose
+// rows couple only to their predecessor is solved by a warp scan; otherwise
+// the lanes finish in sweep order (increasing rows, BACKWARD: decreasing),
+// each from the new values before it, kept in shared memory.
 #define RS_HGS_WARPS 8
 #define RS_HGS_REG 8
 template <bool BACKWARD>
@@ -316,6 +315,24 @@ k_amg_hgs(int n, const int *__restrict__ ptr, const int *__restrict__ col, const
             }
         }
         const double rd = 1.0 / d;
+        // a chunk whose rows couple at most to the row before them in sweep
+        // order (a grid line in natural order) is a first-order recurrence
+        // x_i = c_i + m_i x_{i-/+1}: five steps of a warp scan of affine maps
+        const bool chain_lane = !over && (ne == 0 || (ne == 1 && ej[0] == (BACKWARD ? lane + 1 : lane - 1)));
+        if (__all_sync(0xffffffffu, chain_lane)) {
+            double m = ne == 1 ? -ev[0] * rd : 0.0, cc = s * rd;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double mp = BACKWARD ? __shfl_down_sync(0xffffffffu, m, o) : __shfl_up_sync(0xffffffffu, m, o);
+                const double cp = BACKWARD ? __shfl_down_sync(0xffffffffu, cc, o) : __shfl_up_sync(0xffffffffu, cc, o);
+                if (BACKWARD ? lane + o < 32 : lane >= o) {
+                    cc = fma(m, cp, cc);
+                    m *= mp;
+                }
+            }
+            if (active) xnew[i] = cc;
+            continue;
+        }
         for (int t = 0; t < 32; ++t) {
             const int k = BACKWARD ? 31 - t : t;
             if (lane == k && active) {
