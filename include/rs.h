@@ -298,6 +298,24 @@ int rs_precond_sweep_levels(const rs_pc *M, int32_t *levels_l, int32_t *levels_u
  * RS_ERR_INVALID_ARG for RS_PC_NONE or NULL arguments. */
 int rs_precond_sweep_runs(const rs_pc *M, int32_t *runs_l, int32_t *runs_u, int32_t *longest_l,
                           int32_t *longest_u);
+/* The schedule of one triangular sweep of a pattern, computed on the host
+ * only (no device, no context): the analysis rs_precond_setup runs for the
+ * sweeps of an ILU(0) factor in FP64.  ptr[nrows+1], col[ptr[nrows]]: a
+ * square CSR pattern, columns strictly increasing within a row, every row
+ * with its diagonal (else RS_ERR_BAD_PATTERN).  lower: 1 for the L sweep
+ * (rows in increasing order, reading the strictly lower entries), 0 for the
+ * U sweep.  run_cap: the longest run allowed (1: no runs); run_slots: the
+ * most runs kept (a layout with more, or whose runs would not halve the
+ * segments, takes one segment per run).  Outputs: nseg segments of up to 32
+ * consecutive rows, seg_row0[nseg+1] their first rows (a caller array of
+ * nrows+1), seg_level[nseg] their levels (a segment's level is one more than
+ * the highest level of the segments it reads; array of nrows), nlevels,
+ * and nrun runs in the order their tickets are taken, runs[nrun][5] = first
+ * segment, segments, segment stride, row stride, entry stride (array of
+ * 5 nrows).  The output arrays may be NULL. */
+int rs_sweep_schedule(int32_t nrows, const int32_t *ptr, const int32_t *col, int32_t lower, int32_t run_cap,
+                      int64_t run_slots, int32_t *nseg, int32_t *nlevels, int32_t *nrun, int32_t *seg_row0,
+                      int32_t *seg_level, int32_t *runs);
 int rs_precond_destroy(rs_pc **M);
 
 /* ---- Krylov solvers (Sec. 3, Alg. 1) ----------------------------------- */

@@ -108,6 +108,9 @@ SIGNATURES = [
     ("rs_precond_bad_row", C.c_int32, [_vp]),
     ("rs_precond_sweep_levels", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("rs_precond_sweep_runs", C.c_int, [_vp] + [C.POINTER(C.c_int32)] * 4),
+    ("rs_sweep_schedule", C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32, C.c_int32,
+                                    C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("rs_precond_ras_info", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     ("rs_precond_amg_levels", C.c_int, [_vp, C.POINTER(C.c_int32)]),
     ("rs_precond_amg_level_sizes", C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
@@ -494,6 +497,26 @@ def net_unflatten(flat) -> dict:
     out["head.W"] = flat[off:off + 16].reshape(1, 16)
     out["head.b"] = flat[off + 16:off + 17].copy()
     return out
+
+
+def sweep_schedule(ptr, col, lower=True, run_cap=1 << 30, run_slots=1 << 40):
+    """The host-side schedule of one triangular sweep of a CSR pattern
+    (rs_sweep_schedule): segment first rows and levels, and the runs as
+    rows of (first segment, segments, segment stride, row stride, entry
+    stride), in ticket order.  Needs no GPU."""
+    ptr = np.ascontiguousarray(ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = ptr.size - 1
+    nseg, nlev, nrun = C.c_int32(), C.c_int32(), C.c_int32()
+    row0 = np.zeros(n + 1, np.int32)
+    lev = np.zeros(max(n, 1), np.int32)
+    runs = np.zeros(5 * max(n, 1), np.int32)
+    i32 = C.POINTER(C.c_int32)
+    _check(lib().rs_sweep_schedule(n, ptr.ctypes.data_as(i32), col.ctypes.data_as(i32), int(lower), run_cap,
+                                   run_slots, C.byref(nseg), C.byref(nlev), C.byref(nrun), row0.ctypes.data_as(i32),
+                                   lev.ctypes.data_as(i32), runs.ctypes.data_as(i32)), "rs_sweep_schedule")
+    return dict(row0=row0[:nseg.value + 1].copy(), level=lev[:nseg.value].copy(), nlevels=nlev.value,
+                runs=runs[:5 * nrun.value].reshape(-1, 5).copy())
 
 
 class Net:

@@ -91,9 +91,17 @@ static int build_layout(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
 // structured grids segments never straddle grid lines whatever their
 // length.  A segment's level is one more than the highest level of the
 // segments holding the columns it reads outside itself.
-static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
-                          const std::vector<int> &col, const std::vector<int> &diag, bool lower,
-                          int run_cap, int64_t run_slots, SegLayout &S)
+// The host analysis of one sweep: segments, their levels and kinds, the
+// entry layout, and the runs (no device work; rs_sweep_schedule exposes it)
+struct SegHost {
+    int nseg = 0, nlev = 0, nrun = 0, max_run = 0;
+    int64_t nent = 0;
+    std::vector<int> r0v, lev, order, sptr, adjsrc, ecol, esrc, rdesc;
+    std::vector<unsigned char> kind;
+};
+
+static int seg_schedule(int nrows, const std::vector<int> &ptr, const std::vector<int> &col,
+                        const std::vector<int> &diag, bool lower, int run_cap, int64_t run_slots, SegHost &H)
 {
     // does row i read row j = i-1 (L) / i+1 (U)?  (the entry next to the diagonal)
     auto reads_prev = [&](int i) { return i > 0 && diag[i] > ptr[i] && col[diag[i] - 1] == i - 1; };
@@ -271,11 +279,39 @@ static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
     const int nrun = (int)rlast.size();
     int max_run = 0;
     for (int R = 0; R < nrun; ++R) max_run = std::max(max_run, rdesc[5 * R + 1]);
+    H.nseg = nseg;
+    H.nlev = nlev;
+    H.nent = nent;
+    H.nrun = nrun;
+    H.max_run = max_run;
+    H.r0v.swap(r0v);
+    H.lev.swap(lev);
+    H.order.swap(order);
+    H.sptr.swap(sptr);
+    H.adjsrc.swap(adjsrc);
+    H.ecol.swap(ecol);
+    H.esrc.swap(esrc);
+    H.rdesc.swap(rdesc);
+    H.kind.swap(kind);
+    return RS_OK;
+}
+
+static int build_segments(rs_ctx *ctx, int nrows, const std::vector<int> &ptr,
+                          const std::vector<int> &col, const std::vector<int> &diag, bool lower,
+                          int run_cap, int64_t run_slots, SegLayout &S)
+{
+    SegHost H;
+    RS_TRY(seg_schedule(nrows, ptr, col, diag, lower, run_cap, run_slots, H));
+    const int nseg = H.nseg, nrun = H.nrun;
+    const int64_t nent = H.nent;
+    const std::vector<int> &r0v = H.r0v, &sptr = H.sptr, &adjsrc = H.adjsrc, &ecol = H.ecol, &esrc = H.esrc,
+                           &rdesc = H.rdesc;
+    const std::vector<unsigned char> &kind = H.kind;
     S.nseg = nseg;
-    S.nlevels = nlev;
+    S.nlevels = H.nlev;
     S.nent = nent;
     S.nrun = nrun;
-    S.max_run = max_run;
+    S.max_run = H.max_run;
     int st = RS_OK;
     st = st ? st : rs_alloc(ctx, (void **)&S.runs, sizeof(int) * 5 * (nrun > 0 ? nrun : 1));
     st = st ? st : rs_alloc(ctx, (void **)&S.sptr, sizeof(int) * (nseg + 1));
@@ -1318,6 +1354,33 @@ __global__ void k_gather_dinv(int nrows, int npr, int b2, const int *__restrict_
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// The sweep schedule of a pattern, host only (see rs.h).
+extern "C" int rs_sweep_schedule(int32_t nrows, const int32_t *ptr, const int32_t *col, int32_t lower,
+                                 int32_t run_cap, int64_t run_slots, int32_t *nseg, int32_t *nlevels,
+                                 int32_t *nrun, int32_t *seg_row0, int32_t *seg_level, int32_t *runs)
+{
+    if (nrows < 0 || !ptr || !nseg || !nlevels || !nrun || run_cap < 1 || run_slots < 1) return RS_ERR_INVALID_ARG;
+    if (ptr[0] != 0 || (ptr[nrows] > 0 && !col)) return RS_ERR_INVALID_ARG;
+    std::vector<int> hp(ptr, ptr + nrows + 1), hc(col, col + ptr[nrows]), diag(nrows, -1);
+    for (int i = 0; i < nrows; ++i) {
+        if (hp[i + 1] < hp[i]) return RS_ERR_BAD_PATTERN;
+        for (int q = hp[i]; q < hp[i + 1]; ++q) {
+            if (hc[q] < 0 || hc[q] >= nrows || (q > hp[i] && hc[q] <= hc[q - 1])) return RS_ERR_BAD_PATTERN;
+            if (hc[q] == i) diag[i] = q;
+        }
+        if (diag[i] < 0) return RS_ERR_BAD_PATTERN;
+    }
+    SegHost H;
+    RS_TRY(seg_schedule(nrows, hp, hc, diag, lower != 0, run_cap, run_slots, H));
+    *nseg = H.nseg;
+    *nlevels = H.nlev;
+    *nrun = H.nrun;
+    if (seg_row0) std::copy(H.r0v.begin(), H.r0v.end(), seg_row0);
+    if (seg_level) std::copy(H.lev.begin(), H.lev.end(), seg_level);
+    if (runs) std::copy(H.rdesc.begin(), H.rdesc.end(), runs);
+    return RS_OK;
+}
+
 int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr, const int *d_col,
                   const std::vector<int> &h_ptr, const std::vector<int> &h_col, int fp32,
                   IluFactor **out, int *bad_row)
