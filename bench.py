@@ -1,18 +1,21 @@
 """Benchmark: time to a 1e-8 relative residual for preconditioned Krylov solves.
 
-Default workload (one GPU): the 3-D 7-point pressure matrix on a 128x128x64
-grid (1,048,576 cells, vertical permeability x0.1, log-normal permeability,
-seed 1), b = A x_true, GMRES(30) right-preconditioned by ILU(0), all FP64,
-rtol 1e-8, x0 = 0.  One step = one complete solve; matrices, right-hand
+Default workload (one GPU): the largest configuration of the metric, the
+black-oil-like 3x3-block system on a 128^3 grid (2,097,152 cells, 6,291,456
+unknowns, seed 1), b = A x_true, FGMRES(30) right-preconditioned by the
+two-stage CPR whose pressure stage is the learned U-Net (BF16), block ILU(0)
+second stage with FP32 factors, FP64 outer iteration, rtol 1e-8, x0 = 0.
+The same line times the same solve with the ILU(0) pressure stage
+(`baseline_method`).  One step = one complete solve; matrices, right-hand
 sides and preconditioners are resident in HBM before the timed region
 (setup is timed separately).  A 512 MB buffer is written between timed
 steps to flush the 129 MB L2.
 
-Other workloads (--workload): the 32^3 system; mixed precision; BiCGSTAB;
-the learned pressure stage on 64^3 held-out fields (FGMRES(30), learned
-two-stage CPR vs GMRES(30)+ILU(0)); the 100x100x50 black-oil-like 3x3-block
-system with CPR-FGMRES(30); the 128^3 block system with the learned vs the
-ILU(0) pressure stage.
+Other workloads (--workload): the 32^3 and 128x128x64 scalar systems with
+GMRES(30)/BiCGSTAB/CG + ILU(0), FP64 or mixed; the learned pressure stage on
+64^3 held-out fields (FGMRES(30), learned two-stage CPR vs
+GMRES(30)+ILU(0)); the 100x100x50 black-oil-like 3x3-block system with
+CPR-FGMRES(30); RAS, AMG and LGMRES variants.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -31,6 +34,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the CPU oracle is timed on one host core: numpy's BLAS (the oracle
+# network's channel contractions) must not start threads of its own
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import numpy as np  # noqa: E402
 
@@ -90,7 +97,7 @@ WORKLOADS = {
     "cpr_fpf_bicgstab_bsr3_100x100x50": dict(kind="bsr", grid=(100, 100, 50), kz=1.0, solver="bicgstab",
                                              precond="cpr", prec="mixed", form="fpf"),
 }
-DEFAULT = "gmres_ilu0_128x128x64"
+DEFAULT = "cpr_learned_bsr3_128x128x128"
 SEED = 1
 
 
@@ -349,20 +356,34 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ----------------------------------------------------------------------------
-def _oracle_net_stage(net_params, out_scale, grid, logk):
+def _oracle_net_stage(net_params, out_scale, grid, logk, slab=None, clock=None):
+    """The numpy network as the oracle's pressure stage.  With slab = k the
+    network runs on the first k z-planes only (the rest of the correction is
+    zero), so that a timing sample stays bounded: the network is fully
+    convolutional and its cost is proportional to the voxels it covers.
+    clock (a one-element list) accumulates the seconds spent in the network."""
     from oracle import convnet as cn
     nx, ny, nz = grid
+    # the U-Net pools three times: a slab holds a multiple of 8 planes
+    zs = nz if slab is None else max(8, min(int(slab) // 8 * 8, nz))
 
     def stage(rp):
-        out, _ = cn.forward(net_params, rp.reshape(nz, ny, nx), logk.reshape(nz, ny, nx),
-                            out_scale=out_scale, bf16=True)
+        t0 = time.perf_counter()
+        r3, k3 = rp.reshape(nz, ny, nx), logk.reshape(nz, ny, nx)
+        out = np.zeros_like(r3)
+        out[:zs], _ = cn.forward(net_params, r3[:zs], k3[:zs], out_scale=out_scale, bf16=True)
+        if clock is not None:
+            clock[0] += time.perf_counter() - t0
         return out.reshape(-1)
     return stage
 
 
-def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
+def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH, net_slab=None):
     """One oracle solve of the workload's system, at most maxit iterations:
-    returns (solve seconds, setup seconds, iterations)."""
+    returns (solve seconds, setup seconds, iterations, seconds of the solve
+    spent in the network, network volume factor).  With the learned stage
+    the network runs on net_slab z-planes (all if None); the volume factor
+    nz / net_slab scales its time to the full grid."""
     import oracle
     oracle.build()
     if w["kind"] in ("bsr", "bsr_learned"):
@@ -371,12 +392,15 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
         A = oracle.Mat.csr(A_host)
     b = oracle.spmv(A, xt)
     mixed = w["prec"] == "mixed"
+    clock, vol = [0.0], 1.0
     t0 = time.perf_counter()
-    if w["precond"] == "cpr_learned" and w["kind"] == "learned":
+    if w["precond"] == "cpr_learned":
         params, scale = load_net_host(net_file)
-        M = oracle.PC(A, "cpr", mixed=mixed, pstage=_oracle_net_stage(params, scale, w["grid"], A_host["logk"]))
-    elif w["precond"] == "cpr_learned":
-        M = oracle.PC(A, "cpr", mixed=mixed)      # block system: ILU(0) pressure stage in the oracle
+        nz = w["grid"][2]
+        if net_slab is not None:
+            vol = nz / max(8, min(int(net_slab) // 8 * 8, nz))
+        M = oracle.PC(A, "cpr", mixed=mixed,
+                      pstage=_oracle_net_stage(params, scale, w["grid"], A_host["logk"], net_slab, clock))
     elif w["precond"] == "amg":
         M = oracle.PC(A, "amg", amg=w["amg"])
     elif w.get("pstage") == "amg":
@@ -395,14 +419,14 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH):
     t0 = time.perf_counter()
     if w["solver"] == "lgmres":
         _, info = oracle.lgmres(A, M, b, restart=30, aug_k=w["aug_k"], rtol=RTOL, maxit=maxit)
-        return time.perf_counter() - t0, setup, info["iters"]
+        return time.perf_counter() - t0, setup, info["iters"], clock[0], vol
     if w["solver"] == "bicgstab":
         _, info, _ = oracle.bicgstab(A, M, b, rtol=RTOL, maxit=maxit)
     elif w["solver"] == "cg":
         _, info, _ = oracle.cg(A, M, b, rtol=RTOL, maxit=maxit)
     else:
         _, info, _ = oracle.gmres(A, M, b, restart=30, rtol=RTOL, maxit=maxit, flexible=w["solver"] == "fgmres")
-    return time.perf_counter() - t0, setup, info["iters"]
+    return time.perf_counter() - t0, setup, info["iters"], clock[0], vol
 
 
 def load_net_host(path):
@@ -416,22 +440,41 @@ def load_net_host(path):
     return net_unflatten(flat), float(out_scale)
 
 
-def oracle_baseline(w, A_host, xt, gpu_iters):
+# z-planes the numpy network covers in a timing sample of the learned
+# stage (its time is then scaled by nz / planes): the CPU baseline of the
+# bench line, and each step of the reference arm
+NET_SLAB = {"bsr_learned": 16}
+NET_SLAB_REF = {"bsr_learned": 8}
+# iteration counts of the GPU solves, taken by the reference arm, which
+# does not run the GPU (a full oracle solve of these systems takes minutes
+# to hours on one core)
+GPU_ITERS = {"learned": 26, "bsr": 30, "bsr_learned": 33}
+
+
+def oracle_baseline(w, A_host, xt, gpu_iters, slab_table=NET_SLAB):
     """The oracle on a bounded sample, scaled to the iteration count."""
     n = A_host["n"] if "n" in A_host else 3 * A_host["nb"]
     if w["kind"] == "csr" and n <= 1_100_000:
-        t, s, it = oracle_run(w, A_host, xt, 10000)
+        t, s, it, _, _ = oracle_run(w, A_host, xt, 10000)
         return {"value": t + s, "unit": "s", "cores": 1, "kind": "oracle",
                 "sample": "one full solve of the same system on one host core (%d iterations, setup %.3f s)"
                           % (it, s)}
-    sample = {"learned": 1, "bsr": 6, "bsr_learned": 2}.get(w["kind"], 30)
-    t, s, it = oracle_run(w, A_host, xt, sample)
-    v = t / max(it, 1) * gpu_iters + s
-    what = "with the numpy network as pressure stage" if w["kind"] == "learned" else \
-        ("with the ILU(0) pressure stage" if w["kind"] == "bsr_learned" else "")
+    sample = {"learned": 1, "bsr": 6, "bsr_learned": 1}.get(w["kind"], 30)
+    slab = slab_table.get(w["kind"])
+    t, s, it, tnet, vol = oracle_run(w, A_host, xt, sample, net_slab=slab)
+    per_it = ((t - tnet) + tnet * vol) / max(it, 1)
+    v = per_it * gpu_iters + s
+    if w["precond"] == "cpr_learned":
+        nx, ny, nz = w["grid"]
+        what = "with the numpy network (bf16-rounded) as the pressure stage"
+        if slab is not None and vol != 1.0:
+            what += (", the network run on a %dx%dx%d slab of the grid and its time scaled by %g (it is fully "
+                     "convolutional: cost proportional to voxels)" % (nx, ny, nz / vol, vol))
+    else:
+        what = ""
     return {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": "%d iteration(s) of the same solve %s on one host core, scaled to %s iterations, plus "
-                      "setup %.2f s" % (it, what, gpu_iters, s)}
+            "sample": "%d iteration(s) of the same solve %s on one host core (%.2f s per iteration), scaled to %s "
+                      "iterations, plus setup %.2f s" % (it, what, per_it, gpu_iters, s)}
 
 
 def run_reference(args, w, rank, world):
@@ -439,10 +482,10 @@ def run_reference(args, w, rank, world):
         return
     g, A_host, xt = host_problem(w, w.get("seeds", [SEED])[0])
     if w["kind"] == "csr":
-        full_t, full_s, full_it = oracle_run(w, A_host, xt, 10000)
+        full_t, full_s, full_it, _, _ = oracle_run(w, A_host, xt, 10000)
         per = []
         for s in range(max(args.warmup - 1, 0) + args.steps):
-            t, su, done = oracle_run(w, A_host, xt, 30)
+            t, su, done, _, _ = oracle_run(w, A_host, xt, 30)
             if s >= args.warmup - 1:
                 per.append(t / done * full_it + su)
         sample = ("one full solve (%d iterations, %.2f s) then, per step, 30 iterations of the same solve "
@@ -451,15 +494,15 @@ def run_reference(args, w, rank, world):
         per = []
         cb = None
         for s in range(args.warmup + args.steps):
-            cb = oracle_baseline(w, A_host, xt, {"learned": 26, "bsr": 30, "bsr_learned": 30}[w["kind"]])
+            cb = oracle_baseline(w, A_host, xt, GPU_ITERS[w["kind"]], NET_SLAB_REF)
             if s >= args.warmup:
                 per.append(cb["value"])
         sample = cb["sample"] + " (iteration count of the GPU arm's solve assumed)"
-    v = statistics.median(per)
+    v = statistics.mean(per)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if w["prec"] == "fp64" else "f64+f32", "data": "synthetic",
         "config": {"workload": args.workload, "grid": list(w["grid"]), "solver": w["solver"],
                    "precond": w["precond"], "precision": w["prec"], "rtol": RTOL},
         "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
@@ -619,7 +662,8 @@ def run_gpu(args, w, rank, world, local):
         solve(c, c.M)
         L.rs_vec_get(c.x.h, rs._vp(hx.data_ptr()), rs.MEM_HOST)
         e2e.append(time.perf_counter() - t1)
-    e2e_s = statistics.median(e2e)
+    # the same statistic as the device-timed value (the mean of the K steps)
+    e2e_s = statistics.mean(e2e)
 
     if world > 1:
         ms, ms_prof, e2e_s, wall = max_over_ranks([ms, ms_prof, e2e_s, wall], device="cuda")
