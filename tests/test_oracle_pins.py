@@ -85,6 +85,47 @@ def test_generator_pressure_matrix_properties():
     assert np.array_equal(m["val"], m2["val"]) and not np.array_equal(m["val"], m3["val"])
 
 
+def test_generator_splitmix64_published_outputs():
+    """SplitMix64 (Steele, Lea, Flood 2014) from state 0: the first three
+    outputs of the published generator are 0xE220A8397B1DCDAF,
+    0x6E789E6AA1B965F4 and 0x06C45D188009454F (state advanced by the
+    golden gamma 0x9E3779B97F4A7C15 before each output)."""
+    gamma = 0x9E3779B97F4A7C15
+    states = np.array([0, gamma, (2 * gamma) % 2 ** 64], dtype=np.uint64)
+    out = [int(v) for v in synth.splitmix64(states)]
+    assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_generator_determinism_pin():
+    """The generator's output is the committed one (tests/golden/synth_pin.txt,
+    written by make_synth_pin.py): patterns by SHA-256, values within 1e-13."""
+    import hashlib
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_synth_pin", os.path.join(GOLDEN, "make_synth_pin.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    pinned = {}
+    for line in open(os.path.join(GOLDEN, "synth_pin.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, key, kind, rest = line.split(" ", 3)
+        pinned[(name, key)] = (kind, rest.split())
+    seen = 0
+    for name, d in mk.cases():
+        for key in sorted(d):
+            a = np.asarray(d[key])
+            if (name, key) not in pinned:
+                continue
+            kind, rest = pinned[(name, key)]
+            if kind == "sha256":
+                assert hashlib.sha256(a.astype("<i4").tobytes()).hexdigest() == rest[0], (name, key)
+            else:
+                ref = np.array([float(v) for v in rest])
+                assert a.shape == ref.shape and np.allclose(a, ref, rtol=1e-13, atol=0), (name, key)
+            seen += 1
+    assert seen == len(pinned) and seen >= 19
+
+
 def test_generator_bsr_properties():
     g = synth.Grid(4, 3, 3)
     m = synth.black_oil_bsr3(g, 3)
@@ -228,6 +269,56 @@ def test_ilu0_solve_inverts_lu(orc):
     z32 = orc.ilu0_solve(A, lu, r, fp32=True)
     assert np.linalg.norm(z32 - z) <= 1e-5 * np.linalg.norm(z)
     assert np.linalg.norm(z32 - z) > 0
+
+
+def _read_golden_kv(name):
+    """key = values lines of a golden file (values as hex or decimal floats)."""
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#")[0]
+        if "=" not in line:
+            continue
+        k, v = line.split("=", 1)
+        out[k.strip()] = [float.fromhex(t) if "x" in t else float(t) for t in v.split()]
+    return out
+
+
+def test_ilu0_solve_f32_golden(orc):
+    """The FP32 ILU(0) solve against a four-row example worked by hand
+    (tests/golden/ilu0_solve_f32_four_rows.txt): every product and every
+    difference rounded to binary32.  The example is built so that the
+    plausible slips give other bits: an FP64 accumulator with FP32 factors
+    (a tie in the product of row 1 goes the other way, and that changes
+    rows 0 and 3 too), or one rounding per row (row 3)."""
+    g = _read_golden_kv("ilu0_solve_f32_four_rows.txt")
+    n = int(g["n"][0])
+    A = orc.Mat(np.array(g["rowptr"], np.int32), np.array(g["col"], np.int32), np.zeros(len(g["col"])), 1)
+    lu = np.array(g["lu"], np.float32)
+    assert np.array_equal(lu.astype(np.float64), np.array(g["lu"]))   # the factors are binary32 values
+    r = np.array(g["r"])
+    z = orc.ilu0_solve(A, lu, r, fp32=True)
+    assert z.shape == (n,) and np.array_equal(z, np.array(g["z"])), (z, g["z"])
+    # the FP64 solve with the same factors, rounded to binary32 at the end,
+    # differs in every row but row 2
+    z64 = orc.ilu0_solve(A, lu.astype(np.float64), r).astype(np.float32).astype(np.float64)
+    assert [bool(a != b) for a, b in zip(z64, g["z"])] == [True, True, False, True], z64
+
+
+def test_bilu0_solve_f32_golden(orc):
+    """The FP32 block ILU(0) solve (2x2 blocks) against an example worked by
+    hand (tests/golden/bilu0_solve_f32_three_blocks.txt); an FP64 accumulator
+    or one rounding per row gives other bits."""
+    g = _read_golden_kv("bilu0_solve_f32_three_blocks.txt")
+    nb, bs = int(g["nb"][0]), int(g["bs"][0])
+    A = orc.Mat(np.array(g["browptr"], np.int32), np.array(g["bcol"], np.int32),
+                np.zeros(len(g["bcol"]) * bs * bs), bs)
+    lu, dinv = np.array(g["lu"], np.float32), np.array(g["dinv"], np.float32)
+    r = np.array(g["r"])
+    z = orc.bilu0_solve(A, lu, dinv, r, fp32=True)
+    assert z.shape == (nb * bs,) and np.array_equal(z, np.array(g["z"])), (z, g["z"])
+    z64 = orc.bilu0_solve(A, lu.astype(np.float64), dinv.astype(np.float64), r)
+    z64 = z64.astype(np.float32).astype(np.float64)
+    assert [bool(a != b) for a, b in zip(z64, g["z"])] == [False, False, True, False, True, True], z64
 
 
 # ----------------------------------------------------------------------------
