@@ -140,6 +140,22 @@ int rs_init(rs_ctx **ctx, int device, void *cuda_stream);
 int rs_finalize(rs_ctx **ctx);
 /* Waits for all work enqueued on the context's stream. */
 int rs_sync(rs_ctx *ctx);
+/* Residual history of the solves (a diagnostic; the paper's solver reports
+ * only the final residual and the iteration count, Sec. 2.4).  While hist is
+ * set, every solve on this context writes, for each of its inner iterations
+ * k = 1, 2, ... up to len, the solver's own relative residual estimate after
+ * iteration k into hist[k-1]:
+ *   GMRES / FGMRES / LGMRES: |g_{k+1}| / ||b||, the residual of the rotated
+ *     least-squares problem of Alg. 1 (Givens rotations);
+ *   BiCGSTAB: ||r|| / ||b|| after the full loop, or ||s|| / ||b|| on a
+ *     half-step exit;
+ *   CG (Alg. 2): ||r|| / ||b|| of the recursive residual.
+ * hist is host memory of at least len doubles, owned by the caller and
+ * written when the solve returns; entries past the solve's iteration count
+ * are left as they were.  hist = NULL or len = 0 stops the recording;
+ * len < 0 is RS_ERR_INVALID_ARG.  Recording costs one device array of len
+ * doubles per solve and one copy at its end. */
+int rs_set_history(rs_ctx *ctx, double *hist, int32_t len);
 /* Every device-side wait of the library (a kernel polling for a value, a
  * level or a copy) gives up after this many clock cycles, records
  * RS_ERR_DEVICE_TIMEOUT in the context's device error word and returns; the

@@ -75,6 +75,7 @@ SIGNATURES = [
     ("rs_finalize", C.c_int, [C.POINTER(_vp)]),
     ("rs_sync", C.c_int, [_vp]),
     ("rs_set_spin_limit", C.c_int, [_vp, C.c_int64]),
+    ("rs_set_history", C.c_int, [_vp, C.POINTER(C.c_double), C.c_int32]),
     ("rs_check_device", C.c_int, [_vp]),
     ("rs_status_str", C.c_char_p, [C.c_int]),
     ("rs_launch_count", C.c_int64, [_vp]),
@@ -239,6 +240,19 @@ class Context:
         cnt = (C.c_int64 * k)()
         _check(lib().rs_prof_read(self.h, ms, cnt, k, int(reset)), "rs_prof_read")
         return {name: (ms[i], cnt[i]) for i, name in enumerate(self.PROF_KINDS)}
+
+    def set_history(self, length: int):
+        """Record the residual history of the following solves (up to
+        `length` iterations each); length = 0 stops.  Returns the numpy array
+        the solves write into (rs_set_history)."""
+        if length <= 0:
+            self._hist = None
+            _check(lib().rs_set_history(self.h, None, 0), "rs_set_history")
+            return None
+        self._hist = np.full(length, np.nan)
+        _check(lib().rs_set_history(self.h, self._hist.ctypes.data_as(C.POINTER(C.c_double)), length),
+               "rs_set_history")
+        return self._hist
 
     def set_spin_limit(self, cycles: int):
         """Clock cycles a device-side wait may take before it gives up (0: default)."""

@@ -161,6 +161,14 @@ extern "C" int rs_finalize(rs_ctx **pc)
     return RS_OK;
 }
 
+extern "C" int rs_set_history(rs_ctx *ctx, double *hist, int32_t len)
+{
+    if (!ctx || len < 0) return RS_ERR_INVALID_ARG;
+    ctx->hist_host = len > 0 ? hist : nullptr;
+    ctx->hist_len = hist ? len : 0;
+    return RS_OK;
+}
+
 extern "C" int rs_set_spin_limit(rs_ctx *ctx, int64_t cycles)
 {
     if (!ctx || cycles < 0) return RS_ERR_INVALID_ARG;

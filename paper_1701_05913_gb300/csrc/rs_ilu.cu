@@ -1360,10 +1360,14 @@ extern "C" int rs_sweep_schedule(int32_t nrows, const int32_t *ptr, const int32_
                                  int32_t *nrun, int32_t *seg_row0, int32_t *seg_level, int32_t *runs)
 {
     if (nrows < 0 || !ptr || !nseg || !nlevels || !nrun || run_cap < 1 || run_slots < 1) return RS_ERR_INVALID_ARG;
-    if (ptr[0] != 0 || (ptr[nrows] > 0 && !col)) return RS_ERR_INVALID_ARG;
+    if (ptr[0] != 0) return RS_ERR_INVALID_ARG;
+    // the whole of ptr first: it must not decrease (so ptr[nrows] >= 0 and
+    // no row reads past the column array) before any column is read
+    for (int i = 0; i < nrows; ++i)
+        if (ptr[i + 1] < ptr[i]) return RS_ERR_BAD_PATTERN;
+    if (ptr[nrows] > 0 && !col) return RS_ERR_INVALID_ARG;
     std::vector<int> hp(ptr, ptr + nrows + 1), hc(col, col + ptr[nrows]), diag(nrows, -1);
     for (int i = 0; i < nrows; ++i) {
-        if (hp[i + 1] < hp[i]) return RS_ERR_BAD_PATTERN;
         for (int q = hp[i]; q < hp[i + 1]; ++q) {
             if (hc[q] < 0 || hc[q] >= nrows || (q > hp[i] && hc[q] <= hc[q - 1])) return RS_ERR_BAD_PATTERN;
             if (hc[q] == i) diag[i] = q;

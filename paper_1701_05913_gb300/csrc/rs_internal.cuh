@@ -77,6 +77,9 @@ struct rs_ctx {
     int sweep_blocks;        // resident blocks of the persistent triangular sweeps (at least)
     int sweep_blocks_fixed;  // set from the environment: overrides the per-factor choice
     unsigned sleep_cap_ns;   // longest back-off of a polling warp (0: none)
+    // residual history of the solves (rs_set_history): caller's host array
+    double *hist_host = nullptr;
+    int hist_len = 0;
     // event profiler (off unless rs_prof_enable)
     int prof_on;
     std::vector<RsProfRec> prof_pending;

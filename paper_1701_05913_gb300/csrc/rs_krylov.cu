@@ -32,7 +32,42 @@ struct GmresDev {
     double bnorm, tol, beta, hdiv, w0sq, implicit, r2;
     int iters, k, cycle_done, converged, maxit, m, noupd, status;
     double augn2;           // ||Z y||^2 of the last cycle (LGMRES)
+    double *hist;           // residual history (device), hist_len entries
+    int hist_len, pad_;
 };
+
+// The solver's relative residual estimate after iteration it (from 1) into
+// the history, when one is recorded.
+__device__ __forceinline__ void record_hist(double *hist, int hist_len, int it, double res, double bnorm)
+{
+    if (hist && it >= 1 && it - 1 < hist_len) hist[it - 1] = res / bnorm;
+}
+
+// A device array for the residual history of one solve, when the context
+// records one (rs_set_history); null otherwise.
+static int hist_begin(rs_ctx *ctx, double **dh, int *len)
+{
+    *dh = nullptr;
+    *len = ctx->hist_host ? ctx->hist_len : 0;
+    if (*len == 0) return RS_OK;
+    return rs_alloc(ctx, (void **)dh, sizeof(double) * (size_t)*len);
+}
+
+// Copies the first min(len, iters) entries back to the caller's array and
+// frees the device array.
+static int hist_end(rs_ctx *ctx, double *dh, int len, int iters)
+{
+    int st = RS_OK;
+    const int k = std::min(len, iters);
+    if (dh && k > 0) {
+        if (cudaMemcpyAsync(ctx->hist_host, dh, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, ctx->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            st = RS_ERR_CUDA;
+    }
+    rs_free(ctx, dh);
+    return st;
+}
 
 // ---------------------------------------------------------------------------
 // block reduction of up to NC+1 per-thread sums with a last-block finish
@@ -295,6 +330,7 @@ k_cgs_pass(int n, int ld, int nc, const double *__restrict__ V, double *w, doubl
                 d->iters += 1;
                 d->k = i + 1;
                 d->implicit = fabs(d->g[i + 1]);
+                record_hist(d->hist, d->hist_len, d->iters, d->implicit, d->bnorm);
                 const bool happy = hnext <= 1e-14 * sqrt(d->w0sq);
                 if (d->implicit <= d->tol || d->iters >= d->maxit || happy || i == d->m - 1)
                     d->cycle_done = 1;
@@ -463,6 +499,8 @@ static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, i
     const int ld = (n + 31) / 32 * 32;
     double *V = nullptr, *Z = nullptr, *r = nullptr, *t = nullptr, *Aug = nullptr;
     GmresDev *d = nullptr;
+    double *dhist = nullptr;
+    int hlen = 0;
     int naug = 0, head = 0;      // stored corrections; the next ring slot
     int st = rs_alloc(ctx, (void **)&V, sizeof(double) * (size_t)ld * (m + aug_k + 1));
     if (!st && flexible) st = rs_alloc(ctx, (void **)&Z, sizeof(double) * (size_t)ld * (m + aug_k));
@@ -470,6 +508,7 @@ static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, i
     if (!st) st = rs_alloc(ctx, (void **)&r, sizeof(double) * ld);
     if (!st) st = rs_alloc(ctx, (void **)&t, sizeof(double) * ld);
     if (!st) st = rs_alloc(ctx, (void **)&d, sizeof(GmresDev));
+    if (!st) st = hist_begin(ctx, &dhist, &hlen);
     int status = RS_NOT_CONVERGED;
     double bnorm = 0.0;
     const double *b = bv->d;
@@ -481,6 +520,8 @@ static int gmres_impl(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *xv, i
         h0.m = m;
         h0.maxit = maxit;
         h0.noupd = 1;
+        h0.hist = dhist;
+        h0.hist_len = hlen;
         // ||b||
         st = rs_dot_launch(ctx, n, b, b, ctx->d_scalars);
         if (st) goto out;
@@ -599,6 +640,10 @@ done:
     if (st) goto out;
     if (status == RS_OK && info->true_rel_res > rtol && bnorm > 0) status = RS_NOT_CONVERGED;
 out:
+    {
+        const int hs = hist_end(ctx, dhist, hlen, info->iters);
+        if (!st) st = hs;
+    }
     rs_free(ctx, V);
     rs_free(ctx, Z);
     rs_free(ctx, Aug);
@@ -635,6 +680,8 @@ struct BicgDev {
     double red[8];          // reduction outputs
     double rho, rho0, alpha, omega, beta, tol, bnorm, implicit;
     int iters, done, half, fresh, breakdown, maxit, status, pad;
+    double *hist;           // residual history (device), hist_len entries
+    int hist_len, pad_;
 };
 
 // generic fused row kernel with up to 3 dot products and a scalar epilogue
@@ -700,13 +747,17 @@ k_bicg(int op, int n, double *p, double *r, const double *__restrict__ v, double
     case 1: {
         d->iters += 1;
         const double sn = sqrt(d->red[0]);
-        if (sn <= d->tol) { d->half = 1; d->implicit = sn; d->done = 1; d->fresh = 1; }
+        if (sn <= d->tol) {
+            d->half = 1; d->implicit = sn; d->done = 1; d->fresh = 1;
+            record_hist(d->hist, d->hist_len, d->iters, sn, d->bnorm);
+        }
         break;
     }
     case 2: {
         const double rho = d->red[0];
         const double rn = sqrt(d->red[1]);
         d->implicit = rn;
+        record_hist(d->hist, d->hist_len, d->iters, rn, d->bnorm);
         d->rho0 = d->rho;
         if (rn <= d->tol) { d->done = 1; d->fresh = 1; break; }
         if (!(d->omega != 0.0) || !isfinite(d->omega)) { d->breakdown = 1; d->done = 1; break; }
@@ -774,8 +825,11 @@ extern "C" int rs_solve_bicgstab(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs
     const int ld = (n + 31) / 32 * 32;
     double *buf = nullptr;
     BicgDev *d = nullptr;
+    double *dhist = nullptr;
+    int hlen = 0;
     int st = rs_alloc(ctx, (void **)&buf, sizeof(double) * (size_t)ld * 8);
     if (!st) st = rs_alloc(ctx, (void **)&d, sizeof(BicgDev));
+    if (!st) st = hist_begin(ctx, &dhist, &hlen);
     int status = RS_NOT_CONVERGED;
     double bnorm = 0.0;
     const double *b = bv->d;
@@ -804,6 +858,8 @@ extern "C" int rs_solve_bicgstab(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs
         h0.tol = rtol * bnorm;
         h0.bnorm = bnorm;
         h0.maxit = maxit;
+        h0.hist = dhist;
+        h0.hist_len = hlen;
         cudaMemcpyAsync(d, &h0, sizeof(h0), cudaMemcpyHostToDevice, ctx->stream);
         const int gr = red_grid(ctx), gb = blas_grid(ctx, n);
         int *halt = &d->done;
@@ -883,6 +939,10 @@ done:
     if (status == RS_OK && info->true_rel_res > rtol && bnorm > 0) status = RS_NOT_CONVERGED;
     if (status == RS_NOT_CONVERGED && info->true_rel_res <= rtol && bnorm > 0) status = RS_OK;
 out:
+    {
+        const int hs = hist_end(ctx, dhist, hlen, info->iters);
+        if (!st) st = hs;
+    }
     rs_free(ctx, buf);
     rs_free(ctx, d);
     info->status = st ? st : status;
@@ -899,6 +959,8 @@ struct CgDev {
     double red[2];
     double rho, rho0, alpha, beta, tol, bnorm, implicit;
     int iters, done, fresh, breakdown, maxit, status, first, pad;
+    double *hist;           // residual history (device), hist_len entries
+    int hist_len, pad_;
 };
 
 //  op 0: red = {(r, z)}                 -> rho, beta = rho / rho_prev (0 on the first pass)
@@ -949,6 +1011,7 @@ k_cg(int op, int n, double *x, double *r, const double *__restrict__ z, double *
         d->rho0 = d->rho;
         const double rn = sqrt(d->red[0]);
         d->implicit = rn;
+        record_hist(d->hist, d->hist_len, d->iters, rn, d->bnorm);
         if (rn <= d->tol) { d->done = 1; d->fresh = 1; break; }
         if (d->iters >= d->maxit) d->done = 1;
         break;
@@ -985,8 +1048,11 @@ extern "C" int rs_solve_cg(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *
     const int ld = (n + 31) / 32 * 32;
     double *buf = nullptr;
     CgDev *d = nullptr;
+    double *dhist = nullptr;
+    int hlen = 0;
     int st = rs_alloc(ctx, (void **)&buf, sizeof(double) * (size_t)ld * 4);
     if (!st) st = rs_alloc(ctx, (void **)&d, sizeof(CgDev));
+    if (!st) st = hist_begin(ctx, &dhist, &hlen);
     int status = RS_NOT_CONVERGED;
     double bnorm = 0.0;
     const double *b = bv->d;
@@ -1010,6 +1076,8 @@ extern "C" int rs_solve_cg(const rs_mat *A, rs_pc *M, const rs_vec *bv, rs_vec *
         h0.tol = rtol * bnorm;
         h0.bnorm = bnorm;
         h0.maxit = maxit;
+        h0.hist = dhist;
+        h0.hist_len = hlen;
         cudaMemcpyAsync(d, &h0, sizeof(h0), cudaMemcpyHostToDevice, ctx->stream);
         const int gr = red_grid(ctx), gb = blas_grid(ctx, n);
         int *halt = &d->done;
@@ -1072,6 +1140,10 @@ done:
     if (status == RS_OK && info->true_rel_res > rtol && bnorm > 0) status = RS_NOT_CONVERGED;
     if (status == RS_NOT_CONVERGED && info->true_rel_res <= rtol && bnorm > 0) status = RS_OK;
 out:
+    {
+        const int hs = hist_end(ctx, dhist, hlen, info->iters);
+        if (!st) st = hs;
+    }
     rs_free(ctx, buf);
     rs_free(ctx, d);
     info->status = st ? st : status;

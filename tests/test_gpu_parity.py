@@ -18,27 +18,33 @@ def ctx(rs):
     return rs.Context(0)
 
 
-ACCUM = 1e-3   # accumulation term of the generated pressure matrices
-
-
-def within_conditioning_bound(orc, Ao, b, x, xo, accum=ACCUM):
-    """||x - xo|| <= ||A^{-1}||_2 (||b - A x|| + ||b - A xo||), and for the SPD
-    pressure matrix (graph Laplacian + accum I) ||A^{-1}||_2 <= 1/accum."""
-    r = orc.norm2(b - orc.spmv(Ao, x))
-    ro = orc.norm2(b - orc.spmv(Ao, xo))
-    return np.linalg.norm(x - xo) <= (r + ro) / accum
-
-
 def bicg_iters_ok(orc, Ao, Mo, b, rtol, it_gpu, it_oracle):
-    """BiCGSTAB's residual is not monotone, so the step at which it first
-    drops below rtol moves by several steps under rounding-level changes.
-    Accept the GPU count if it is within 2 of the oracle's, or within 2 of
-    the window of counts the oracle itself needs for rtol/2 .. 2 rtol."""
+    """BiCGSTAB amplifies rounding-level differences: the GPU's residual
+    history equals the oracle's to 1e-10 over the first iterations and
+    leaves it (by 1e-6) where the oracle's own history leaves it when b is
+    perturbed by one ulp (test_bicgstab_history_is_the_oracles_up_to_rounding).
+    Its residual also plateaus near rtol, so the step at which it first drops
+    below rtol moves by several steps under such changes.  Accept the GPU
+    count if it is within 2 of the oracle's, or within 2 of the window of
+    counts the oracle itself needs for rtol/2 .. 2 rtol."""
     if abs(it_gpu - it_oracle) <= 2:
         return True
     lo = orc.bicgstab(Ao, Mo, b, rtol=2 * rtol)[1]["iters"]
     hi = orc.bicgstab(Ao, Mo, b, rtol=rtol / 2)[1]["iters"]
     return min(lo, hi) - 2 <= it_gpu <= max(lo, hi) + 2
+
+
+def bicg_solution_parity(rs, ctx, orc, A, M, Ao, Mo, b, rtol=1e-12):
+    """Relative distance of the GPU's and the oracle's BiCGSTAB solutions,
+    both solved to rtol.  At rtol = 1e-8 the method itself leaves its
+    solution only within about kappa(A) rtol of A^-1 b (the oracle's own
+    solution moves by 1e-5 when b is perturbed by one ulp), so solution
+    parity is measured where both solves reach 1e-12."""
+    xo, io, _ = orc.bicgstab(Ao, Mo, b, rtol=rtol)
+    x = rs.Vec.zeros(ctx, A.n)
+    info = rs.solve_bicgstab(A, M, rs.Vec(ctx, b), x, rtol=rtol)
+    assert info["status"] == 0 and io["status"] == 0, (info, io)
+    return rel(x.numpy(), xo)
 
 
 def rel(a, b):
@@ -347,27 +353,37 @@ def test_krylov_ilu0_fp64_parity(rs, ctx, orc, solver, shape, kz):
     else:
         assert abs(info["iters"] - io["iters"]) <= 2, (info, io)
     if solver == "bicgstab":
-        # BiCGSTAB's residual is not monotone and its iterates drift from the
-        # oracle's at the rounding level; both solutions meet the residual, so
-        # their distance is checked against the conditioning bound
-        assert within_conditioning_bound(orc, Ao, b, xs, xo), (rel(xs, xo), info, io)
+        assert bicg_solution_parity(rs, ctx, orc, A, M, Ao, Mo, b) <= 1e-6
     else:
         assert rel(xs, xo) <= 1e-6, (rel(xs, xo), info, io)
 
 
 def test_gmres_mixed_precision_error_vs_oracle(rs, ctx, orc):
+    """Mixed precision (FP32 factors and applies, FP64 outer iteration):
+    the solution's error against the all-FP64 oracle's solution is at most
+    1e-6 relative (GMRES(30) at rtol 1e-8 measures about 1e-7 here;
+    BiCGSTAB, whose iterates depend on rounding, is compared where both
+    solves reach rtol 1e-12), and the true FP64 residual meets rtol."""
     g, d = _problem((24, 24, 16), 2, 0.1)
     Ao = orc.Mat.csr(d)
     b = orc.spmv(Ao, synth.x_true(g.n, 2))
-    xo, io, _ = orc.gmres(Ao, orc.PC(Ao, "ilu0"), b)
+    Mo = orc.PC(Ao, "ilu0")
+    xo, io, _ = orc.gmres(Ao, Mo, b)
     A = rs.Mat.csr(ctx, d)
-    for solver in (rs.solve_gmres, rs.solve_bicgstab):
-        x = rs.Vec.zeros(ctx, g.n)
-        info = solver(A, rs.Precond(ctx, A, "ilu0", prec="mixed"), vec(rs, ctx, b), x)
-        xs = x.numpy()
-        assert info["status"] == 0
-        assert orc.norm2(b - orc.spmv(Ao, xs)) / orc.norm2(b) <= 1e-8
-        assert within_conditioning_bound(orc, Ao, b, xs, xo), rel(xs, xo)
+    Mm = rs.Precond(ctx, A, "ilu0", prec="mixed")
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_gmres(A, Mm, vec(rs, ctx, b), x)
+    xs = x.numpy()
+    assert info["status"] == 0
+    assert orc.norm2(b - orc.spmv(Ao, xs)) / orc.norm2(b) <= 1e-8
+    assert rel(xs, xo) <= 1e-6, rel(xs, xo)
+    # BiCGSTAB with the FP32 apply against the FP64 oracle, both at 1e-12
+    xo12, io12, _ = orc.bicgstab(Ao, Mo, b, rtol=1e-12)
+    x = rs.Vec.zeros(ctx, g.n)
+    info = rs.solve_bicgstab(A, Mm, vec(rs, ctx, b), x, rtol=1e-12)
+    assert info["status"] == 0 and io12["status"] == 0
+    assert orc.norm2(b - orc.spmv(Ao, x.numpy())) / orc.norm2(b) <= 1e-12
+    assert rel(x.numpy(), xo12) <= 1e-6, rel(x.numpy(), xo12)
 
 
 def test_unpreconditioned_and_edge_cases(rs, ctx, orc):
@@ -454,7 +470,7 @@ def test_cg_parity(rs, ctx, orc, shape, pc):
     assert info["status"] == 0 and io["status"] == 0
     assert abs(info["iters"] - io["iters"]) <= 2, (info["iters"], io["iters"])
     assert orc.norm2(b - orc.spmv(Ao, x.numpy())) / orc.norm2(b) <= 1e-8
-    assert within_conditioning_bound(orc, Ao, b, x.numpy(), xo) or rel(x.numpy(), xo) <= 1e-6
+    assert rel(x.numpy(), xo) <= 1e-6, rel(x.numpy(), xo)
 
 
 def test_cg_breakdown_and_zero_rhs(rs, ctx):

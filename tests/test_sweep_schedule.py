@@ -153,3 +153,12 @@ def test_bad_patterns_rejected(rs):
         with pytest.raises(rs.RsError) as e:
             rs.sweep_schedule(p, c)
         assert e.value.status == rs.ERR_BAD_PATTERN
+
+
+def test_malformed_row_pointers_rejected(rs):
+    """A decreasing row pointer array, or a negative last entry, is rejected
+    before any column index is read (no read past the column array)."""
+    for p, c in (([0, 5, 2], [0, 1]), ([0, 1, -3], [0]), ([0, 2, 1, 3], [0, 1, 2])):
+        with pytest.raises(rs.RsError) as e:
+            rs.sweep_schedule(np.array(p, np.int32), np.array(c, np.int32))
+        assert e.value.status == rs.ERR_BAD_PATTERN
