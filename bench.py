@@ -702,11 +702,13 @@ def run_gpu(args, w, rank, world, local):
     roofline["share_of_kernel_time"] = round(kern_ms[dom] / total_prof, 3)
     if dom in ("l_sweep", "u_sweep", "bl_sweep", "bu_sweep") and \
             dom.startswith("b") == (w["kind"] in ("bsr", "bsr_learned")):
-        # the sweeps are bound by their dependency chain, not by bytes: the
-        # number of segment levels and the time per level
+        # the sweeps are bound by their dependency chain, not by bytes: its
+        # length (wavefront cells nx + ny + nz - 2, or segment levels) and
+        # the time per step of it
         lv = cases[0].M.sweep_levels()[0 if dom in ("l_sweep", "bl_sweep") else 1]
-        roofline["critical_path"] = {"segment_levels": lv,
-                                     "us_per_level": round(roofline["avg_launch_us"] / lv, 3)}
+        kind = cases[0].M.sweep_kind()[0]
+        roofline["critical_path"] = {"kind": "wavefront cells" if kind == "wavefront" else "segment levels",
+                                     "length": lv, "us_per_step": round(roofline["avg_launch_us"] / lv, 4)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:

@@ -120,6 +120,17 @@ typedef struct {
      * chunks, forward before the coarse correction and backward after it;
      * it needs a nonzero diagonal on every level (else RS_ERR_ZERO_PIVOT). */
     int32_t amg_smoother;
+    /* Triangular sweeps of every ILU(0) / block ILU(0) factor of this
+     * preconditioner (Eq. 3).  0 [0]: the wavefront sweeps when the pattern
+     * is (a subset of) the 7-point stencil of a structured grid in natural
+     * order (x fastest; the grid is read off the pattern), else the segment
+     * sweeps; 1: always the segment sweeps.  RAS local factors always take
+     * the segment sweeps. */
+    int32_t sweep;
+    /* Segment sweeps: the longest run of segments one warp carries, > 0 (1:
+     * no runs).  0 [0]: no limit for FP64 scalar factors, no runs for FP32
+     * and block factors (runs serve scalar factors only). */
+    int32_t sweep_run_cap;
 } rs_pc_opts;
 
 typedef struct {
@@ -297,13 +308,20 @@ int rs_precond_ras_info(const rs_pc *M, int32_t *next, int64_t *nnz);
  * then U with its diagonal).  Any pointer may be NULL. */
 int rs_precond_get_ras(const rs_pc *M, int32_t *gidx, int32_t *ptr, int32_t *col, double *lu);
 /* Critical-path length of the triangular sweeps of the full-system factor
- * (ILU(0), block ILU(0), or the second stage of CPR): the number of segment
- * levels of the L and of the U sweep, where a segment is a run of at most 32
- * consecutive (block) rows solved by one warp and a segment's level is one
- * more than the highest level of the segments it reads (Eq. 3 solved row by
- * row in dependency order).  RS_ERR_INVALID_ARG for RS_PC_NONE or NULL
- * arguments. */
+ * (ILU(0), block ILU(0), or the second stage of CPR), L and U.  Segment
+ * sweeps: the number of segment levels, where a segment is a run of at most
+ * 32 consecutive (block) rows solved by one warp and a segment's level is
+ * one more than the highest level of the segments it reads (Eq. 3 solved
+ * row by row in dependency order).  Wavefront sweeps (a structured 7-point
+ * pattern on an nx x ny x nz grid): the cells on the longest dependency
+ * chain, nx + ny + nz - 2, each one step of the wavefront.  Which sweeps a
+ * factor takes: rs_precond_sweep_kind.  RS_ERR_INVALID_ARG for RS_PC_NONE
+ * or NULL arguments. */
 int rs_precond_sweep_levels(const rs_pc *M, int32_t *levels_l, int32_t *levels_u);
+/* The sweeps the full-system factor takes: *kind = 0 segment sweeps, 1
+ * wavefront sweeps; for wavefronts (nx, ny, nz) is the grid read off the
+ * pattern (else 0, 0, 0).  Any output but kind may be NULL. */
+int rs_precond_sweep_kind(const rs_pc *M, int32_t *kind, int32_t *nx, int32_t *ny, int32_t *nz);
 /* Runs of the same sweeps: a run is a sequence of segments that one warp
  * solves in turn, each segment reading the one before it from the warp's
  * registers (scalar factors only; block factors have one segment per run).

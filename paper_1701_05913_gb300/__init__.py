@@ -63,7 +63,7 @@ class PcOpts(C.Structure):
                 ("ras_part", _vp), ("amg_theta", C.c_double), ("amg_max_levels", C.c_int32),
                 ("amg_max_coarse", C.c_int32), ("amg_nu", C.c_int32), ("cpr_pstage", C.c_int32),
                 ("ras_local", C.c_int32), ("ilut_p", C.c_int32), ("ilut_tol", C.c_double),
-                ("amg_smoother", C.c_int32)]
+                ("amg_smoother", C.c_int32), ("sweep", C.c_int32), ("sweep_run_cap", C.c_int32)]
 
 
 CPR_FORMS = ("pf", "fp", "fpf", "ffpf")   # rs_cpr_form: Algs. 6, 5, 7, 8
@@ -108,6 +108,8 @@ SIGNATURES = [
     ("rs_precond_get_cpr", C.c_int, [_vp, _f64p, _f64p]),
     ("rs_precond_bad_row", C.c_int32, [_vp]),
     ("rs_precond_sweep_levels", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    ("rs_precond_sweep_kind", C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32)]),
     ("rs_precond_sweep_runs", C.c_int, [_vp] + [C.POINTER(C.c_int32)] * 4),
     ("rs_sweep_schedule", C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32, C.c_int32,
                                     C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -347,7 +349,8 @@ class Precond:
 
     def __init__(self, ctx: Context, A: Mat, kind: str = "ilu0", prec: str = "fp64",
                  net=None, log_perm=None, grid=None, form: str = "pf", nparts: int = 1, part=None,
-                 overlap: int = 0, level: int = 0, amg=None, pstage: str = "ilu0", ilut=None):
+                 overlap: int = 0, level: int = 0, amg=None, pstage: str = "ilu0", ilut=None,
+                 sweep: str = "auto", run_cap: int = 0):
         self.ctx, self.A, self.kind = ctx, A, kind
         opts = PcOpts()
         opts.prec = MIXED if prec == "mixed" else FP64
@@ -371,6 +374,9 @@ class Precond:
         opts.amg_nu = a.get("nu", 0)
         opts.amg_smoother = a.get("smoother", 0)
         opts.cpr_pstage = {"ilu0": 0, "amg": 1}[pstage]
+        # ILU sweeps: "auto" (wavefronts on structured 7-point grids) or "segments"
+        opts.sweep = {"auto": 0, "segments": 1}[sweep]
+        opts.sweep_run_cap = run_cap
         if part is not None:
             part = np.ascontiguousarray(part, dtype=np.int32)
             self._keep.append(part)
@@ -468,6 +474,13 @@ class Precond:
         a, b = C.c_int32(), C.c_int32()
         _check(lib().rs_precond_sweep_levels(self.h, C.byref(a), C.byref(b)), "rs_precond_sweep_levels")
         return a.value, b.value
+
+    def sweep_kind(self):
+        """("segments", None) or ("wavefront", (nx, ny, nz)) for the
+        full-system factor's triangular sweeps."""
+        v = [C.c_int32() for _ in range(4)]
+        _check(lib().rs_precond_sweep_kind(self.h, *[C.byref(x) for x in v]), "rs_precond_sweep_kind")
+        return ("wavefront", (v[1].value, v[2].value, v[3].value)) if v[0].value else ("segments", None)
 
     def sweep_runs(self):
         """(L runs, U runs, longest L run, longest U run) of the same sweeps."""

@@ -90,15 +90,6 @@ extern "C" int rs_init(rs_ctx **out, int device, void *stream)
     c->spin_limit = (long long)clock_khz * 1000LL * 2;   // about two seconds
     c->sweep_blocks = 4 * c->num_sms;
     c->sleep_cap_ns = 0;   // spin: a polling warp reissues its loads as soon as they return
-    if (const char *e = getenv("RS_SWEEP_SLEEP_CAP_NS")) {
-        const int v = atoi(e);
-        if (v >= 0 && v <= 100000) c->sleep_cap_ns = (unsigned)v;
-    }
-    c->sweep_blocks_fixed = 0;
-    if (const char *e = getenv("RS_SWEEP_BLOCKS_PER_SM")) {
-        const int v = atoi(e);
-        if (v >= 1 && v <= 16) c->sweep_blocks = v * c->num_sms, c->sweep_blocks_fixed = 1;
-    }
     // the stream-ordered pool keeps freed blocks for reuse
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {

@@ -725,54 +725,6 @@ __global__ void k_scan_mul(int nseg, const int *__restrict__ row0, const int *__
 // 4-byte) store, which is single-copy atomic.  The L sweep resets the U
 // sweep's work vector to the sentinel (row by row) and the U sweep resets the
 // L sweep's, so no clearing pass is needed.
-template <typename T> struct Sentinel;
-template <> struct Sentinel<double> {
-    typedef unsigned long long bits_t;
-    static constexpr bits_t bits = 0xFFF5A5A5A5A5A5A5ull;
-};
-template <> struct Sentinel<float> {
-    typedef unsigned int bits_t;
-    static constexpr bits_t bits = 0xFFB5A5A5u;
-};
-
-__device__ __forceinline__ unsigned long long ld_relaxed_bits(const double *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned int ld_relaxed_bits(const float *p)
-{
-    unsigned int v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed(double *p, double v)
-{
-    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
-}
-__device__ __forceinline__ void st_relaxed(float *p, float v)
-{
-    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-}
-__device__ __forceinline__ double bits_to(double, unsigned long long b) { return __longlong_as_double((long long)b); }
-__device__ __forceinline__ float bits_to(float, unsigned int b) { return __uint_as_float(b); }
-
-template <typename T>
-__global__ void k_fill_sentinel(int64_t n, T *v)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v[i] = bits_to(T(), Sentinel<T>::bits);
-}
-
-// Arithmetic of the sweeps.  FP64 uses fused multiply-adds (FP64
-// instructions are scarce on this GPU and sit on the critical path); FP32
-// (the mixed-precision apply) rounds the product and the difference
-// separately, in ascending column order.
-__device__ __forceinline__ double msub(double acc, double a, double b) { return fma(-a, b, acc); }
-__device__ __forceinline__ float msub(float acc, float a, float b) { return __fsub_rn(acc, __fmul_rn(a, b)); }
-__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
 
 // ---------------------------------------------------------------------------
 // segment sweeps
@@ -1386,8 +1338,8 @@ extern "C" int rs_sweep_schedule(int32_t nrows, const int32_t *ptr, const int32_
 }
 
 int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr, const int *d_col,
-                  const std::vector<int> &h_ptr, const std::vector<int> &h_col, int fp32,
-                  IluFactor **out, int *bad_row)
+                  const std::vector<int> &h_ptr, const std::vector<int> &h_col, int fp32, int sweep_mode,
+                  int run_cap, IluFactor **out, int *bad_row)
 {
     (void)bad_row;
     if (bs != 1 && bs != 2 && bs != 3 && bs != 4) return RS_ERR_INVALID_ARG;
@@ -1405,54 +1357,52 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
             if (h_col[q] == i) diag[i] = q;
     const size_t b2 = (size_t)bs * bs;
     const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-    // row-level schedule of the factorisation; segment layouts of the sweeps
+    // row-level schedule of the factorisation
     int st = build_layout(ctx, nrows, h_ptr, h_col, diag, f->L);
-    // runs are taken by the scalar FP64 sweeps.  In FP32 a hop between
-    // warps already costs about what a step of a run does (0.8 against
-    // 0.7 us at 128 x 128 x 64), and waiting inside a run adds more than
-    // that saves.  RS_SWEEP_RUN caps the length for either precision (1:
-    // every segment is a run of its own).
-    int run_cap = fp32 ? 1 : 1 << 30;
-    if (const char *e = getenv("RS_SWEEP_RUN")) {
-        const int v = atoi(e);
-        if (v >= 1) run_cap = v;
+    // the sweeps: wavefronts on a structured 7-point pattern, else segments
+    int gx = 0, gy = 0, gz = 0;
+    const bool wave = sweep_mode == 0 && rs_wave_detect(nrows, h_ptr, h_col, &gx, &gy, &gz);
+    if (!wave) {
+        // runs are taken by the scalar FP64 sweeps.  In FP32 a hop between
+        // warps already costs about what a step of a run does (0.8 against
+        // 0.7 us at 128 x 128 x 64), and waiting inside a run adds more than
+        // that saves; run_cap > 0 sets the longest run for either precision
+        // (1: every segment is a run of its own).
+        int cap = run_cap > 0 ? run_cap : fp32 ? 1 : 1 << 30;
+        if (bs != 1) cap = 1;
+        // warps resident at once in sweep blocks that carry the runs' ring
+        const int64_t run_block = (int64_t)(RS_SWEEP_THREADS / 32) *
+                                  (5 * 32 * (fp32 ? sizeof(float) : sizeof(double)) +
+                                   RS_RUN_RING * sizeof(unsigned long long));
+        const int64_t run_slots =
+            std::max<int64_t>(1, (int64_t)227 * 1024 / run_block) * (RS_SWEEP_THREADS / 32) * ctx->num_sms;
+        st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, cap, run_slots, f->SL);
+        st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, cap, run_slots, f->SU);
+        // sweep blocks: a single dependency chain (global ILU in natural
+        // order) gains nothing from more warps, which only add polling; many
+        // independent chains (the stacked subdomains of RAS) do.  Aim at
+        // three warps per segment of a level, between 4 and 8 blocks per SM.
+        for (SegLayout *S : {&f->SL, &f->SU}) {
+            const int wpb = RS_SWEEP_THREADS / 32;
+            const int64_t per_level = S->nlevels > 0 ? (int64_t)S->nseg / S->nlevels : 0;
+            int64_t g = (3 * per_level + wpb - 1) / wpb;
+            g = std::max<int64_t>(g, ctx->sweep_blocks);
+            S->grid = (int)std::min<int64_t>(g, (int64_t)8 * ctx->num_sms);
+        }
+        st = st ? st : rs_alloc(ctx, &f->SL.val, esz * b2 * (f->SL.nent > 0 ? f->SL.nent : 1));
+        st = st ? st : rs_alloc(ctx, &f->SU.val, esz * b2 * (f->SU.nent > 0 ? f->SU.nent : 1));
+        st = st ? st : rs_alloc(ctx, &f->SU.rdiag, esz * b2 * ((size_t)f->SU.nseg * 32 > 0 ? (size_t)f->SU.nseg * 32 : 1));
+        st = st ? st : rs_alloc(ctx, &f->SL.mul, esz * b2 * 5 * 32 * (f->SL.nseg > 0 ? (size_t)f->SL.nseg : 1));
+        st = st ? st : rs_alloc(ctx, &f->SU.mul, esz * b2 * 5 * 32 * (f->SU.nseg > 0 ? (size_t)f->SU.nseg : 1));
     }
-    if (bs != 1) run_cap = 1;
-    // one run per block by default: the runs of a sweep then spread over
-    // more SMs (83.4 against 84.3 ms per GMRES(30)+ILU(0) solve at
-    // 128 x 128 x 64 with four per block); RS_SWEEP_RUN_WARPS = 1, 2 or 4
-    if (const char *e = getenv("RS_SWEEP_RUN_WARPS")) {
-        const int v = atoi(e);
-        if (v == 1 || v == 2 || v == 4) f->run_warps = v;
-    }
-    // warps resident at once in sweep blocks that carry the runs' ring
-    const int64_t run_block = (int64_t)(RS_SWEEP_THREADS / 32) *
-                              (5 * 32 * (fp32 ? sizeof(float) : sizeof(double)) + RS_RUN_RING * sizeof(unsigned long long));
-    const int64_t run_slots = std::max<int64_t>(1, (int64_t)227 * 1024 / run_block) * (RS_SWEEP_THREADS / 32) * ctx->num_sms;
-    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, true, run_cap, run_slots, f->SL);
-    st = st ? st : build_segments(ctx, nrows, h_ptr, h_col, diag, false, run_cap, run_slots, f->SU);
-    // sweep blocks: a single dependency chain (global ILU in natural order)
-    // gains nothing from more warps, which only add polling; many
-    // independent chains (the stacked subdomains of RAS) do.  Aim at three
-    // warps per segment of a level, between 4 and 8 blocks per SM.
-    for (SegLayout *S : {&f->SL, &f->SU}) {
-        const int wpb = RS_SWEEP_THREADS / 32;
-        const int64_t per_level = S->nlevels > 0 ? (int64_t)S->nseg / S->nlevels : 0;
-        int64_t g = (3 * per_level + wpb - 1) / wpb;
-        g = std::max<int64_t>(g, ctx->sweep_blocks);
-        if (!ctx->sweep_blocks_fixed) g = std::min<int64_t>(g, (int64_t)8 * ctx->num_sms);
-        else g = ctx->sweep_blocks;
-        S->grid = (int)g;
-    }
-    st = st ? st : rs_alloc(ctx, &f->SL.val, esz * b2 * (f->SL.nent > 0 ? f->SL.nent : 1));
-    st = st ? st : rs_alloc(ctx, &f->SU.val, esz * b2 * (f->SU.nent > 0 ? f->SU.nent : 1));
-    st = st ? st : rs_alloc(ctx, &f->SU.rdiag, esz * b2 * ((size_t)f->SU.nseg * 32 > 0 ? (size_t)f->SU.nseg * 32 : 1));
-    st = st ? st : rs_alloc(ctx, &f->SL.mul, esz * b2 * 5 * 32 * (f->SL.nseg > 0 ? (size_t)f->SL.nseg : 1));
-    st = st ? st : rs_alloc(ctx, &f->SU.mul, esz * b2 * 5 * 32 * (f->SU.nseg > 0 ? (size_t)f->SU.nseg : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->diagpos, sizeof(int) * (nrows > 0 ? nrows : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->lu, sizeof(double) * b2 * (nnzb > 0 ? nnzb : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->dinv, sizeof(double) * b2 * (nrows > 0 ? nrows : 1));
     st = st ? st : rs_alloc(ctx, (void **)&f->state, sizeof(SweepState));
+    if (wave) {
+        st = st ? st : rs_wave_create(f, gx, gy, gz);
+        if (st) { rs_ilu_destroy(f); return st; }
+    } else {
     st = st ? st : rs_alloc(ctx, &f->ywork, esz * bs * (nrows > 0 ? nrows : 1));
     st = st ? st : rs_alloc(ctx, &f->zwork, esz * bs * (nrows > 0 ? nrows : 1));
     if (st) { rs_ilu_destroy(f); return st; }
@@ -1468,6 +1418,7 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
         }
         RS_TRY(rs_check_launch(ctx));
         ctx->launches++;
+    }
     }
     SweepState s0 = {0u, 0u, 1, 0};
     RS_CUDA_TRY(cudaMemcpyAsync(f->state, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->stream));
@@ -1485,6 +1436,7 @@ void rs_ilu_destroy(IluFactor *f)
     free_layout(ctx, f->L);
     free_segments(ctx, f->SL);
     free_segments(ctx, f->SU);
+    rs_wave_free(f);
     rs_free(ctx, f->diagpos);
     rs_free(ctx, f->lu);
     rs_free(ctx, f->dinv);
@@ -1555,6 +1507,10 @@ int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row)
     default: return RS_ERR_INVALID_ARG;
     }
     RS_TRY(rs_check_launch(ctx));
+    if (f->W.on) {
+        RS_TRY(rs_wave_gather(f));
+        return rs_collect_device_error(ctx, bad_row);
+    }
     switch (f->bs) {
     case 1: return f->fp32 ? gather_sweep_data<1, float>(f, bad_row) : gather_sweep_data<1, double>(f, bad_row);
     case 2: return f->fp32 ? gather_sweep_data<2, float>(f, bad_row) : gather_sweep_data<2, double>(f, bad_row);
@@ -1572,6 +1528,10 @@ int rs_ilu_set_factors(IluFactor *f, const double *d_lu, int *bad_row)
     if (bad_row) *bad_row = -1;
     if (f->nrows == 0) return RS_OK;
     RS_CUDA_TRY(cudaMemcpyAsync(f->lu, d_lu, sizeof(double) * f->nnzb, cudaMemcpyDeviceToDevice, f->ctx->stream));
+    if (f->W.on) {
+        RS_TRY(rs_wave_gather(f));
+        return rs_collect_device_error(f->ctx, bad_row);
+    }
     return f->fp32 ? gather_sweep_data<1, float>(f, bad_row) : gather_sweep_data<1, double>(f, bad_row);
 }
 
@@ -1640,6 +1600,7 @@ static int apply_seg(IluFactor *f, const double *r, double *z, const double *sca
 int rs_ilu_apply(IluFactor *f, const double *r, double *z, const double *scale, const int *skip)
 {
     if (f->nrows == 0) return RS_OK;
+    if (f->W.on) return rs_wave_apply(f, r, z, scale, skip);
     switch (f->bs) {
     case 1: return f->fp32 ? apply_seg<1, float>(f, r, z, scale, skip) : apply_seg<1, double>(f, r, z, scale, skip);
     case 2: return f->fp32 ? apply_seg<2, float>(f, r, z, scale, skip) : apply_seg<2, double>(f, r, z, scale, skip);

@@ -75,7 +75,6 @@ struct rs_ctx {
     long long launches;
     long long spin_limit;    // clock cycles a device-side wait may take
     int sweep_blocks;        // resident blocks of the persistent triangular sweeps (at least)
-    int sweep_blocks_fixed;  // set from the environment: overrides the per-factor choice
     unsigned sleep_cap_ns;   // longest back-off of a polling warp (0: none)
     // residual history of the solves (rs_set_history): caller's host array
     double *hist_host = nullptr;
@@ -165,6 +164,22 @@ struct SegLayout {
 };
 
 // ILU(0) / block ILU(0) of one matrix pattern.
+// Wavefront sweeps (rs_wave.cu) of a factor whose pattern is the 7-point
+// stencil of an nx x ny x nz grid: units of 32 y-lines of a plane, cells in
+// wave order inside a unit, every unit padded to whole chunks of cc cells.
+struct WaveLayout {
+    int on = 0;
+    int nx = 0, ny = 0, nz = 0;
+    int nyb = 0, nunits = 0, lastL = 0;   // units per plane and in all; lines of a plane's last unit
+    int cc = 0;                           // cells per chunk of the streaming ring
+    int sfull = 0;                        // padded cells of a unit of 32 lines
+    int64_t plane = 0, ncell = 0;         // padded cells of a plane, of all units
+    int *off = nullptr;                   // [2][nx + 33] first cell of each step
+    void *lrec = nullptr, *urec = nullptr;  // L and U records in wave order (apply precision)
+    void *rw = nullptr;                   // right-hand side in wave order
+    void *yw = nullptr, *zw = nullptr;    // values of the L and U sweeps (sentinel protocol)
+};
+
 struct IluFactor {
     rs_ctx *ctx = nullptr;
     int bs = 1;
@@ -177,7 +192,8 @@ struct IluFactor {
     double *lu = nullptr;    // [nnzb*bs*bs] FP64 factors in the matrix pattern
     double *dinv = nullptr;  // [nrows*bs*bs] inverted diagonal blocks (bs > 1)
     TriLayout L;             // row-level schedule of the factorisation
-    SegLayout SL, SU;        // segment layouts of the scalar sweeps
+    SegLayout SL, SU;        // segment layouts of the sweeps (when W is off)
+    WaveLayout W;            // wavefront layout (structured 7-point patterns)
     SweepState *state = nullptr;
     void *ywork = nullptr;   // [nrows*bs] intermediate of the L sweep
     void *zwork = nullptr;   // [nrows*bs] values of the U sweep
@@ -302,14 +318,24 @@ int rs_axpby_launch(rs_ctx *ctx, int n, double a, const double *x, double b, dou
 int rs_dot_launch(rs_ctx *ctx, int n, const double *x, const double *y, double *out_dev);
 
 // ILU
+// sweep_mode: 0 the wavefront sweeps when the pattern is a structured
+// 7-point grid (else segments), 1 always the segment sweeps.  run_cap: the
+// longest run of segments a warp carries (0: the default; scalar only).
 int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr,
                   const int *d_col, const std::vector<int> &h_ptr,
-                  const std::vector<int> &h_col, int fp32, IluFactor **out, int *bad_row);
+                  const std::vector<int> &h_col, int fp32, int sweep_mode, int run_cap,
+                  IluFactor **out, int *bad_row);
 int rs_ilu_factor(IluFactor *f, const double *d_val, int *bad_row);
 int rs_ilu_apply(IluFactor *f, const double *r, double *z, const double *scale_dev,
                  const int *skip);
 void rs_ilu_destroy(IluFactor *f);
 int rs_ilu_set_factors(IluFactor *f, const double *d_lu, int *bad_row);
+// wavefront sweeps (rs_wave.cu)
+bool rs_wave_detect(int n, const std::vector<int> &ptr, const std::vector<int> &col, int *nx, int *ny, int *nz);
+int rs_wave_create(IluFactor *f, int nx, int ny, int nz);
+int rs_wave_gather(IluFactor *f);
+int rs_wave_apply(IluFactor *f, const double *r, double *z, const double *scale, const int *skip);
+void rs_wave_free(IluFactor *f);
 // local: 0 = ILU(level), 1 = ILUT(ilut_p, ilut_tol) (scalar matrices)
 int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part, int overlap, int level, int local,
                   int ilut_p, double ilut_tol, int fp32, RasData **out, int *bad_row);
@@ -376,6 +402,63 @@ __device__ __forceinline__ bool wait_epoch(const int *flag, int epoch, long long
         if (clock64() - t0 > limit) return false;
     }
 }
+
+// ---------------------------------------------------------------------------
+// triangular sweeps: the value is its own ready flag (shared by the segment
+// sweeps of rs_ilu.cu and the wavefront sweeps of rs_wave.cu)
+// ---------------------------------------------------------------------------
+// Before a sweep every entry of its work vector holds a signalling-NaN bit
+// pattern that arithmetic never produces; a warp polls the entries it depends
+// on until they change, and publishes each value with one plain 8-byte (or
+// 4-byte) store, which is single-copy atomic.
+template <typename T> struct Sentinel;
+template <> struct Sentinel<double> {
+    typedef unsigned long long bits_t;
+    static constexpr bits_t bits = 0xFFF5A5A5A5A5A5A5ull;
+};
+template <> struct Sentinel<float> {
+    typedef unsigned int bits_t;
+    static constexpr bits_t bits = 0xFFB5A5A5u;
+};
+
+__device__ __forceinline__ unsigned long long ld_relaxed_bits(const double *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_relaxed_bits(const float *p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(double *p, double v)
+{
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(float *p, float v)
+{
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ double bits_to(double, unsigned long long b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ float bits_to(float, unsigned int b) { return __uint_as_float(b); }
+
+template <typename T>
+__global__ void k_fill_sentinel(int64_t n, T *v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = bits_to(T(), Sentinel<T>::bits);
+}
+
+// Arithmetic of the sweeps.  FP64 uses fused multiply-adds (FP64
+// instructions are scarce on this GPU and sit on the critical path); FP32
+// (the mixed-precision apply) rounds the product and the difference
+// separately, in ascending column order.
+__device__ __forceinline__ double msub(double acc, double a, double b) { return fma(-a, b, acc); }
+__device__ __forceinline__ float msub(float acc, float a, float b) { return __fsub_rn(acc, __fmul_rn(a, b)); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
 
 // ---------------------------------------------------------------------------
 // mbarrier and bulk-copy (TMA, 1-D) helpers shared by the streaming kernels

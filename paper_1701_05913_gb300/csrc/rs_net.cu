@@ -1041,17 +1041,6 @@ static int make_tmap(CUtensorMap *m, const bf16 *base, int C, int W, int H, int 
     return r == CUDA_SUCCESS ? RS_OK : RS_ERR_CUDA;
 }
 
-// the finest level runs on the tcgen05 kernel (RS_NET_TC=0 selects the
-// mma.sync kernel everywhere, for comparison)
-static bool use_tc()
-{
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("RS_NET_TC");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
-}
 
 static void free_workspace(rs_net *net)
 {
@@ -1136,7 +1125,7 @@ static int conv_forward(rs_net *net, int l, const bf16 *X, const bf16 *U, const 
     const int grid = (int)nbricks(L);
     const float *bias = net->p + net->boff[l];
     RsProfScope prof(c, RS_PROF_NET);
-    if (kLayers[l].level == 0 && kLayers[l].mode != IN_FIRST && use_tc()) {
+    if (kLayers[l].level == 0 && kLayers[l].mode != IN_FIRST) {
         CUtensorMap xmap, umap;
         if (kLayers[l].mode == IN_CATUP) {
             // the coarse input, upsampled to this level, is the first half of the concatenation

@@ -259,18 +259,24 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
     M->A = A;
     M->bad_row = -1;
     const int fp32 = M->prec == RS_MIXED;
+    // the ILU factors' triangular sweeps: wavefronts or segments, run length
+    const int sweep = opts ? opts->sweep : 0, run_cap = opts ? opts->sweep_run_cap : 0;
     int st = RS_OK;
     int bad = -1;
+    if (sweep < 0 || sweep > 1 || run_cap < 0) {
+        delete M;
+        return RS_ERR_INVALID_ARG;
+    }
     switch (type) {
     case RS_PC_NONE:
         break;
     case RS_PC_ILU0:
         if (A->bs != 1) { st = RS_ERR_INVALID_ARG; break; }
-        st = rs_ilu_create(ctx, 1, A->nrows, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
+        st = rs_ilu_create(ctx, 1, A->nrows, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, sweep, run_cap, &M->ilu, &bad);
         if (!st) st = rs_ilu_factor(M->ilu, A->val, &bad);
         break;
     case RS_PC_BILU0:
-        st = rs_ilu_create(ctx, A->bs, A->nrows, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
+        st = rs_ilu_create(ctx, A->bs, A->nrows, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, sweep, run_cap, &M->bilu, &bad);
         if (!st) st = rs_ilu_factor(M->bilu, A->val, &bad);
         break;
     case RS_PC_AMG: {
@@ -320,7 +326,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
                                opts->ilu_level, opts->ras_local, opts->ilut_p ? opts->ilut_p : -1,
                                opts->ilut_tol != 0.0 ? opts->ilut_tol : 1e-3, fp32, &M->ras, &bad);
         else
-            st = rs_ilu_create(ctx, bs, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->bilu, &bad);
+            st = rs_ilu_create(ctx, bs, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, sweep, run_cap, &M->bilu, &bad);
         if (!st && !fras) st = rs_ilu_factor(M->bilu, A->val, &bad);
         if (st) break;
         st = rs_alloc(ctx, (void **)&M->t1, sizeof(double) * (A->n > 0 ? A->n : 1));
@@ -331,7 +337,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
             if (pstage == 1 && type == RS_PC_CPR) {
                 st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, A->val, A, th, lev, ncoarse, nu, sm, &M->amg);
             } else if (fras) {
-                st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
+                st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, sweep, run_cap, &M->ilu, &bad);
                 if (!st) st = rs_ilu_factor(M->ilu, A->val, &bad);
             } else {
                 M->ilu = M->bilu;
@@ -370,7 +376,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
             st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, M->app_val, nullptr, th, lev, ncoarse, nu, sm, &M->amg);
             break;
         }
-        st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, &M->ilu, &bad);
+        st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, sweep, run_cap, &M->ilu, &bad);
         if (!st) st = rs_ilu_factor(M->ilu, M->app_val, &bad);
         break;
     }
@@ -449,8 +455,24 @@ extern "C" int rs_precond_sweep_levels(const rs_pc *M, int32_t *levels_l, int32_
     // second stage of CPR
     const IluFactor *f = M->ras ? M->ras->f : M->bilu ? M->bilu : M->ilu;
     if (!f) return RS_ERR_INVALID_ARG;
-    *levels_l = f->SL.nlevels;
-    *levels_u = f->SU.nlevels;
+    if (f->W.on) {
+        *levels_l = *levels_u = f->W.nx + f->W.ny + f->W.nz - 2;
+    } else {
+        *levels_l = f->SL.nlevels;
+        *levels_u = f->SU.nlevels;
+    }
+    return RS_OK;
+}
+
+extern "C" int rs_precond_sweep_kind(const rs_pc *M, int32_t *kind, int32_t *nx, int32_t *ny, int32_t *nz)
+{
+    if (!M || !kind) return RS_ERR_INVALID_ARG;
+    const IluFactor *f = M->ras ? M->ras->f : M->bilu ? M->bilu : M->ilu;
+    if (!f) return RS_ERR_INVALID_ARG;
+    *kind = f->W.on ? 1 : 0;
+    if (nx) *nx = f->W.nx;
+    if (ny) *ny = f->W.ny;
+    if (nz) *nz = f->W.nz;
     return RS_OK;
 }
 

@@ -344,7 +344,7 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
     }
     // the stacked pattern's host copy is only needed by the analysis below
     int bad = -1;
-    st = st ? st : rs_ilu_create(ctx, bs, nx, total_nnz, R->ptr, R->col, hptr, hcol, fp32, &R->f, &bad);
+    st = st ? st : rs_ilu_create(ctx, bs, nx, total_nnz, R->ptr, R->col, hptr, hcol, fp32, 1, 0, &R->f, &bad);
     if (local == 1) st = st ? st : rs_ilu_set_factors(R->f, R->val, &bad);
     else st = st ? st : rs_ilu_factor(R->f, R->val, &bad);
     if (bad >= 0 && bad < nx && bad_row) *bad_row = gidx[bad];

@@ -177,12 +177,18 @@ def test_sweep_levels_structured(rs, ctx, shape):
     A = rs.Mat.csr(ctx, d)
     expect = -(-nx // 32) + ny + nz - 2
     for prec in ("fp64", "mixed"):
-        M = rs.Precond(ctx, A, "ilu0", prec=prec)
+        M = rs.Precond(ctx, A, "ilu0", prec=prec, sweep="segments")
+        assert M.sweep_kind() == ("segments", None)
         assert M.sweep_levels() == (expect, expect)
+        # by default the wavefront sweeps take the grid read off the pattern:
+        # nx + ny + nz - 2 cells on the longest dependency chain
+        W = rs.Precond(ctx, A, "ilu0", prec=prec)
+        assert W.sweep_kind() == ("wavefront", (nx, ny, nz))
+        assert W.sweep_levels() == (nx + ny + nz - 2,) * 2
 
 
 @pytest.mark.parametrize("shape", [(64, 16, 8), (40, 12, 6), (7, 5, 3), (128, 128, 64), (50, 40, 1), (96, 3, 20)])
-def test_sweep_runs_change_no_result(rs, ctx, orc, shape, monkeypatch):
+def test_sweep_runs_change_no_result(rs, ctx, orc, shape):
     """Runs: on a 7-point grid in natural order a warp follows one x-segment
     through all y-lines of a plane, reading the previous segment from its
     registers.  The schedule changes, the arithmetic does not: results are
@@ -199,21 +205,19 @@ def test_sweep_runs_change_no_result(rs, ctx, orc, shape, monkeypatch):
     xsegs = -(-nx // 32)
     nseg = xsegs * ny * nz
     nrun = xsegs * nz
+    seg = dict(sweep="segments")
     for prec in ("fp64", "mixed"):
-        monkeypatch.setenv("RS_SWEEP_RUN", "1")
-        M1 = rs.Precond(ctx, A, "ilu0", prec=prec)
+        M1 = rs.Precond(ctx, A, "ilu0", prec=prec, run_cap=1, **seg)
         # capped runs; kept while every run can hold a resident warp (at
         # most 1216 here: two ring-carrying blocks of four warps per SM)
         cap = 32 if ny * nz > 4096 else 4
-        monkeypatch.setenv("RS_SWEEP_RUN", str(cap))
-        M4 = rs.Precond(ctx, A, "ilu0", prec=prec)
-        monkeypatch.delenv("RS_SWEEP_RUN")
+        M4 = rs.Precond(ctx, A, "ilu0", prec=prec, run_cap=cap, **seg)
         if prec == "mixed":
             # FP32 sweeps take one segment per ticket unless asked otherwise
-            assert rs.Precond(ctx, A, "ilu0", prec=prec).sweep_runs() == (nseg, nseg, 1, 1)
-            monkeypatch.setenv("RS_SWEEP_RUN", "1000000")
-        M = rs.Precond(ctx, A, "ilu0", prec=prec)
-        monkeypatch.delenv("RS_SWEEP_RUN", raising=False)
+            assert rs.Precond(ctx, A, "ilu0", prec=prec, **seg).sweep_runs() == (nseg, nseg, 1, 1)
+            M = rs.Precond(ctx, A, "ilu0", prec=prec, run_cap=1000000, **seg)
+        else:
+            M = rs.Precond(ctx, A, "ilu0", prec=prec, **seg)
         assert M1.sweep_runs() == (nseg, nseg, 1, 1)
         # a y-run of ny segments per (x-segment, plane)
         assert M.sweep_runs() == (nrun, nrun, ny, ny), M.sweep_runs()
@@ -651,14 +655,17 @@ def test_lgmres_maxit_and_zero_rhs(rs, ctx, orc):
     assert info["status"] == 0 and not x0.numpy().any()
 
 
-def test_device_wait_timeout_is_reported_and_the_context_survives(rs, ctx, orc):
+@pytest.mark.parametrize("sweep", ["auto", "segments"])
+def test_device_wait_timeout_is_reported_and_the_context_survives(rs, ctx, orc, sweep):
     """Failure detection without a GPU fault: with a one-cycle limit the
     sweeps' polls give up at their second look, record the timeout and
     return (the values carried on are NaN, the indices come from the
-    layout); the status reaches the host and the context stays usable."""
+    layout; the wavefront sweeps still wait for their own bulk copies); the
+    status reaches the host and the context stays usable."""
     g, d = _problem((48, 48, 24), 85, 0.1)
     A = rs.Mat.csr(ctx, d)
-    M = rs.Precond(ctx, A, "ilu0")
+    M = rs.Precond(ctx, A, "ilu0", sweep=sweep)
+    assert M.sweep_kind()[0] == ("wavefront" if sweep == "auto" else "segments")
     r = synth.x_true(g.n, 85)
     assert ctx.check() == rs.OK
     ctx.set_spin_limit(1)
@@ -669,7 +676,7 @@ def test_device_wait_timeout_is_reported_and_the_context_survives(rs, ctx, orc):
         ctx.set_spin_limit(0)
     assert st == rs.ERR_DEVICE_TIMEOUT
     assert ctx.check() == rs.OK                               # read and cleared
-    M2 = rs.Precond(ctx, A, "ilu0")
+    M2 = rs.Precond(ctx, A, "ilu0", sweep=sweep)
     z = rs.Vec.zeros(ctx, g.n)
     M2.apply(vec(rs, ctx, r), z)
     Ao = orc.Mat.csr(d)
