@@ -374,8 +374,9 @@ class Precond:
         opts.amg_nu = a.get("nu", 0)
         opts.amg_smoother = a.get("smoother", 0)
         opts.cpr_pstage = {"ilu0": 0, "amg": 1}[pstage]
-        # ILU sweeps: "auto" (wavefronts on structured 7-point grids) or "segments"
-        opts.sweep = {"auto": 0, "segments": 1}[sweep]
+        # ILU sweeps: "auto" (the library's choice), "segments" or "wavefront"
+        # (structured 7-point grids; other patterns keep the segments)
+        opts.sweep = {"auto": 0, "segments": 1, "wavefront": 2}[sweep]
         opts.sweep_run_cap = run_cap
         if part is not None:
             part = np.ascontiguousarray(part, dtype=np.int32)

@@ -165,16 +165,16 @@ struct SegLayout {
 
 // ILU(0) / block ILU(0) of one matrix pattern.
 // Wavefront sweeps (rs_wave.cu) of a factor whose pattern is the 7-point
-// stencil of an nx x ny x nz grid: units of 32 y-lines of a plane, cells in
-// wave order inside a unit, every unit padded to whole chunks of cc cells.
+// stencil of an nx x ny x nz grid.  A unit (one warp) is a tile of a y-lines
+// x b z-planes (a b = 32) over all x; its cells are stored by step, 32 per
+// step (one per lane), npad steps per unit, units in ticket order.
 struct WaveLayout {
     int on = 0;
     int nx = 0, ny = 0, nz = 0;
-    int nyb = 0, nunits = 0, lastL = 0;   // units per plane and in all; lines of a plane's last unit
-    int cc = 0;                           // cells per chunk of the streaming ring
-    int sfull = 0;                        // padded cells of a unit of 32 lines
-    int64_t plane = 0, ncell = 0;         // padded cells of a plane, of all units
-    int *off = nullptr;                   // [2][nx + 33] first cell of each step
+    int la = 0;                           // log2 a: lanes along y (a), along z (b = 32 / a)
+    int nyt = 0, nzt = 0, nunits = 0;     // tiles along y and z, and in all
+    int npad = 0;                         // steps stored per unit (a multiple of the chunk)
+    int64_t ncell = 0;                    // stored cells: nunits npad 32
     void *lrec = nullptr, *urec = nullptr;  // L and U records in wave order (apply precision)
     void *rw = nullptr;                   // right-hand side in wave order
     void *yw = nullptr, *zw = nullptr;    // values of the L and U sweeps (sentinel protocol)
@@ -318,9 +318,10 @@ int rs_axpby_launch(rs_ctx *ctx, int n, double a, const double *x, double b, dou
 int rs_dot_launch(rs_ctx *ctx, int n, const double *x, const double *y, double *out_dev);
 
 // ILU
-// sweep_mode: 0 the wavefront sweeps when the pattern is a structured
-// 7-point grid (else segments), 1 always the segment sweeps.  run_cap: the
-// longest run of segments a warp carries (0: the default; scalar only).
+// sweep_mode: 0 the library's choice (segments), 1 the segment sweeps, 2 the
+// wavefront sweeps when the pattern is a structured 7-point grid (else
+// segments).  run_cap: the longest run of segments a warp carries (0: the
+// default; scalar only).
 int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr,
                   const int *d_col, const std::vector<int> &h_ptr,
                   const std::vector<int> &h_col, int fp32, int sweep_mode, int run_cap,

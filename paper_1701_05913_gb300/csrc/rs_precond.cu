@@ -263,7 +263,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
     const int sweep = opts ? opts->sweep : 0, run_cap = opts ? opts->sweep_run_cap : 0;
     int st = RS_OK;
     int bad = -1;
-    if (sweep < 0 || sweep > 1 || run_cap < 0) {
+    if (sweep < 0 || sweep > 2 || run_cap < 0) {
         delete M;
         return RS_ERR_INVALID_ARG;
     }

@@ -7,34 +7,33 @@
 // ILU(0) keeps that pattern, so the dependency graph of either sweep is the
 // grid itself and its critical path is nx + ny + nz - 2 cells long.
 //
-// Schedule.  One warp takes a unit: 32 consecutive y-lines of one z-plane
-// (the last unit of a plane may hold fewer).  At step t lane j solves cell
-// (x = t - j, y = 32 yb + j): its x-neighbour is the lane's own value of the
-// previous step, its y-neighbour the previous step's value of lane j - 1 (a
-// shuffle), so a unit takes nx + 31 steps of a few dependent operations.
-// The y-neighbour of lane 0 and every z-neighbour come from other units
-// through L2: the value is its own ready flag (a sentinel NaN until
-// written), loaded several steps ahead and checked when it is used.  Units
+// Schedule.  One warp takes a unit: a tile of a y-lines by b z-planes (a b =
+// 32 lanes) over all x.  Lane (jy, jz) solves cell (x = t - jy - jz, y0 + jy,
+// z0 + jz) at step t: its x-neighbour is the lane's own value of the step
+// before, its y- and z-neighbours inside the tile the step-before values of
+// lanes (jy-1, jz) and (jy, jz-1), one shuffle each.  Only the tile's faces
+// read other units, through L2, with the value as its own ready flag (a
+// sentinel NaN until written), loaded several steps ahead and checked when
+// used; a miss reloads it and the loads issued after it.  A unit takes
+// nx + a + b - 2 steps; the units on the critical path number
+// ceil(ny/a) + ceil(nz/b) - 1, so a and b are chosen to minimise it.  Units
 // are taken in order from a ticket counter (the U sweep in reverse), so a
 // warp only waits for units held by warps that took earlier tickets and are
 // running: the schedule cannot deadlock, and every wait is bounded in time.
 //
-// Layout.  Factor values, the right-hand side and the sweeps' values are
-// stored in wave order: inside a unit, cell (t, j) follows all cells of the
-// steps before t.  A step's cells are then contiguous, and so is a whole
-// unit: a warp streams its unit's records and right-hand side through a ring
-// of shared-memory slots with bulk copies (mbarrier-counted), and its z-
-// neighbours sit at the same offset in the previous plane's unit.  Units are
-// padded to whole chunks of the ring.  Two permutation kernels move r from
-// natural into wave order (scaled, rounded to the apply precision) and the
-// result back.
+// Layout.  Every unit stores its cells by step, 32 per step (lane order,
+// zeros where a lane is idle), so a step's values, records and right-hand
+// side are contiguous and every address is the unit's base plus 32 t plus
+// the lane.  A warp streams its unit's records and right-hand side through a
+// ring of shared-memory slots of G steps each, filled by bulk copies
+// (mbarrier-counted).  Two permutation kernels move r from natural into wave
+// order (scaled, rounded to the apply precision) and the result back.
 //
 // Arithmetic.  L: y_i = r_i - L_iz y_z - L_iy y_y - L_ix y_x, in ascending
 // column order (FP32: each product and difference rounded, as the
 // sequential FP32 solve does; FP64: fused multiply-adds).  U is stored
-// premultiplied by D_i = inv(U_ii), z_i = D_i y_i - sum_j (D_i U_ij) z_j,
-// with the z-term (loaded ahead) first.  Blocks (bs x bs) take the same
-// steps with block products.
+// premultiplied by D_i = inv(U_ii), z_i = D_i y_i - sum_j (D_i U_ij) z_j.
+// Blocks (bs x bs) take the same steps with block products.
 
 #include <math.h>
 #include <string.h>
@@ -45,12 +44,9 @@
 #include "rs_internal.cuh"
 
 #define RS_WAVE_MAX_NX 4096
-#define RS_WAVE_OFF_PAD 33   // entries per off table beyond nx (steps up to nx + 32)
 #define RS_WAVE_DRAIN (1LL << 30)   // clock cycles a late bulk copy is still waited for
 
 namespace {
-
-constexpr int pow2_floor(int v) { return v >= 2 ? 2 * pow2_floor(v / 2) : 1; }
 
 // Records, ring and hand-off depth per block size and apply precision.
 template <int BS, typename T>
@@ -59,27 +55,31 @@ struct WaveCfg {
     static constexpr int VQ = 16 / (int)sizeof(T);                 // T per 16 bytes
     static constexpr int RL = (3 * B2 + VQ - 1) / VQ * VQ;           // L record: L_z, L_y, L_x
     static constexpr int RU = (4 * B2 + VQ - 1) / VQ * VQ;           // U record: U'_z, U'_x, U'_y, D
-    // cells per chunk: a power of two, about 10 KB per U slot
-    static constexpr int CC0 = pow2_floor(10240 / ((RU + BS) * (int)sizeof(T)));
-    static constexpr int CC = CC0 < 16 ? 16 : CC0;
+    // steps per ring slot: about 10 KB per U slot
+    static constexpr int G0 = 10240 / (32 * (RU + BS) * (int)sizeof(T));
+    static constexpr int G = G0 >= 16 ? 16 : G0 >= 8 ? 8 : G0 >= 4 ? 4 : G0 >= 2 ? 2 : 1;
     static constexpr int R = 4;                                      // ring slots per warp
-    // hand-off values loaded this many steps ahead (a step of a scalar FP64
-    // sweep takes about 200 cycles of FP64 pipe, an FP32 one far less)
-    static constexpr int HP = sizeof(T) == 8 ? (BS == 1 ? 8 : 2) : (BS == 1 ? 24 : 8);
+    // hand-off values are loaded HP steps ahead: about one L2 round trip
+    // (0.6-1 us) at the step's pace.  More adds HP steps of lag to every
+    // hand-off between units; fewer leaves each step waiting for its load.
+    // A multiple of G, so that chunk boundaries fall on fixed steps of the
+    // unrolled loop.
+    static constexpr int HP0 = sizeof(T) == 8 ? (BS == 1 ? 8 : 2) : (BS == 1 ? 16 : 8);
+    static constexpr int HP = HP0 < G ? G : HP0;
+    static_assert(HP % G == 0, "hand-off depth is a whole number of chunks");
     // warps per block: FP64 sweeps keep the SM's scarce FP64 pipes for few warps
     static constexpr int WPB = sizeof(T) == 8 ? 2 : 4;
     static constexpr int BAR_BYTES = 128;                            // WPB * R mbarriers, padded
+    static_assert((G & (G - 1)) == 0, "chunks are a power of two of steps");
     template <bool LOWER>
-    static constexpr int slot_bytes() { return CC * ((LOWER ? RL : RU) + BS) * (int)sizeof(T); }
+    static constexpr int slot_bytes() { return G * 32 * ((LOWER ? RL : RU) + BS) * (int)sizeof(T); }
     template <bool LOWER>
     static constexpr int smem_bytes() { return BAR_BYTES + WPB * R * slot_bytes<LOWER>(); }
 };
 
 struct WaveArgs {
-    int nx, ny, nz, nyb, nunits, lastL;
-    int sfull;               // padded cells of a unit of 32 lines
-    int64_t plane;           // padded cells of a plane
-    const int *off;          // [2][nx + RS_WAVE_OFF_PAD]: first cell of each step (32 lines, last unit)
+    int nx, ny, nz, la;
+    int nyt, nzt, nunits, npad;
     SweepState *st;
     int *err;
     long long limit;
@@ -92,12 +92,11 @@ WaveArgs wave_args(rs_ctx *ctx, const WaveLayout &W, SweepState *st, const int *
     g.nx = W.nx;
     g.ny = W.ny;
     g.nz = W.nz;
-    g.nyb = W.nyb;
+    g.la = W.la;
+    g.nyt = W.nyt;
+    g.nzt = W.nzt;
     g.nunits = W.nunits;
-    g.lastL = W.lastL;
-    g.sfull = W.sfull;
-    g.plane = W.plane;
-    g.off = W.off;
+    g.npad = W.npad;
     g.st = st;
     g.err = ctx->d_err;
     g.limit = ctx->spin_limit;
@@ -105,39 +104,40 @@ WaveArgs wave_args(rs_ctx *ctx, const WaveLayout &W, SweepState *st, const int *
     return g;
 }
 
-struct Unit {
-    int z, yb, L, nsteps;
-    int64_t base;            // first (padded) cell of the unit in wave order
-    const int *tab;          // its off table
-};
-
-__device__ __forceinline__ Unit unit_of(const WaveArgs &g, int u)
+// Loads and stores of the hand-off values, relaxed at GPU scope (single-copy
+// atomic, seen across SMs), written without a compiler memory clobber so
+// that they do not pin the step's other memory operations in place: the
+// protocol needs no ordering between different addresses.
+__device__ __forceinline__ unsigned long long ld_poll(const double *p)
 {
-    Unit U;
-    U.z = u / g.nyb;
-    U.yb = u - U.z * g.nyb;
-    const bool last = U.yb == g.nyb - 1;
-    U.L = last ? g.lastL : 32;
-    U.nsteps = g.nx + U.L - 1;
-    U.base = (int64_t)U.z * g.plane + (int64_t)U.yb * g.sfull;
-    U.tab = g.off + (last ? g.nx + RS_WAVE_OFF_PAD : 0);
-    return U;
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_poll(const float *p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_poll(double *p, double v)
+{
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+}
+__device__ __forceinline__ void st_poll(float *p, float v)
+{
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
 }
 
-// cell of lane j at step t inside a unit with off table tab
-__device__ __forceinline__ int wave_cell(const int *tab, int nx, int t, int j)
-{
-    return __ldg(tab + t) + j - max(0, t - nx + 1);
-}
-
-// wave-order position of natural (block) row i
+// wave-order position (cell index) of natural (block) row i
 __device__ __forceinline__ int64_t wave_pos(const WaveArgs &g, int i)
 {
     const int x = i % g.nx, rest = i / g.nx;
     const int y = rest % g.ny, z = rest / g.ny;
-    const int yb = y >> 5, j = y & 31;
-    const int *tab = g.off + (yb == g.nyb - 1 ? g.nx + RS_WAVE_OFF_PAD : 0);
-    return (int64_t)z * g.plane + (int64_t)yb * g.sfull + wave_cell(tab, g.nx, x + j, j);
+    const int a = 1 << g.la, b = 32 >> g.la;
+    const int jy = y & (a - 1), jz = z % b;
+    const int u = (z / b) * g.nyt + (y >> g.la);
+    return ((int64_t)u * g.npad + x + jy + jz) * 32 + jy + (jz << g.la);
 }
 
 // RB values from 16-byte aligned shared memory, in 16-byte loads
@@ -184,7 +184,7 @@ __device__ __forceinline__ void wave_end(const WaveArgs &g)
 // ---------------------------------------------------------------------------
 // the sweep: L (LOWER) or U
 // ---------------------------------------------------------------------------
-// rec: the unit's records; rhs: r in wave order (L) or y (U); xv: the values
+// rec: the units' records; rhs: r in wave order (L) or y (U); xv: the values
 // this sweep produces, polled by the neighbouring units (sentinel before).
 template <int BS, typename T, bool LOWER>
 __global__ void __launch_bounds__(32 * WaveCfg<BS, T>::WPB)
@@ -193,6 +193,7 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
     using C = WaveCfg<BS, T>;
     constexpr int B2 = C::B2;
     constexpr int RB = LOWER ? C::RL : C::RU;
+    constexpr int G = C::G;
     constexpr int SLOT = C::template slot_bytes<LOWER>();
     constexpr int HP = C::HP;
     constexpr unsigned FULL = 0xffffffffu;
@@ -208,6 +209,11 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
+    const int a = 1 << g.la, b = 32 >> g.la;
+    const int jy = lane & (a - 1), jz = lane >> g.la;
+    const int lj = jy + jz;                   // the lane's skew
+    const int nch = g.npad / G;               // chunks per unit
+    const int64_t ucells = (int64_t)g.npad * 32;
     unsigned parity = 0;     // bit s: parity of slot s's next completion
     bool dead = false;       // a hand-off poll gave up: later polls give up at once
     for (;;) {
@@ -215,86 +221,79 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
         if (lane == 0) tk = (int)atomicAdd(&g.st->ticket, 1u);
         tk = __shfl_sync(FULL, tk, 0);
         if (tk >= g.nunits) break;
-        const Unit U = unit_of(g, LOWER ? tk : g.nunits - 1 - tk);
-        const int nch = (U.L * g.nx + C::CC - 1) / C::CC;
-        const T *grec = rec + U.base * RB;
-        const T *grhs = rhs + U.base * BS;
-        // neighbours in other units: z (every lane), y (lane 0 of L, lane 31 of U)
-        const bool has_z = LOWER ? U.z > 0 : U.z < g.nz - 1;
-        const int64_t zbase = U.base + (LOWER ? -g.plane : g.plane);
-        const bool has_y = LOWER ? U.yb > 0 : U.yb < g.nyb - 1;
-        const int ylane = LOWER ? 0 : 31;
-        const int *ytab = LOWER ? g.off : g.off + (U.yb + 1 == g.nyb - 1 ? g.nx + RS_WAVE_OFF_PAD : 0);
-        const int64_t ybase = U.base + (LOWER ? -(int64_t)g.sfull : (int64_t)g.sfull);
+        const int u = LOWER ? tk : g.nunits - 1 - tk;
+        const int zt = u / g.nyt, yt = u - zt * g.nyt;
+        const bool lane_ok = (yt << g.la) + jy < g.ny && zt * b + jz < g.nz;
+        const int64_t base = (int64_t)u * ucells;
+        const T *grec = rec + base * RB;
+        const T *grhs = rhs + base * BS;
+        // lanes on the tile's faces read other units: z (jz = 0 for L, b - 1
+        // for U) and y (jy = 0 for L, a - 1 for U); the source cell at step t
+        // is src + 32 t
+        bool pz, py;
+        int64_t zsrc, ysrc;
+        if (LOWER) {
+            pz = lane_ok && jz == 0 && zt > 0;
+            py = lane_ok && jy == 0 && yt > 0;
+            zsrc = base - (int64_t)g.nyt * ucells + 32 * (b - 1) + jy + ((b - 1) << g.la);
+            ysrc = base - ucells + 32 * (a - 1) + (a - 1) + (jz << g.la);
+        } else {
+            pz = lane_ok && jz == b - 1 && zt < g.nzt - 1;
+            py = lane_ok && jy == a - 1 && yt < g.nyt - 1;
+            zsrc = base + (int64_t)g.nyt * ucells - 32 * (b - 1) + jy;
+            ysrc = base + ucells - 32 * (a - 1) + (jz << g.la);
+        }
 
-        // chunk q of the stream (the U sweep streams its unit backwards)
-        int issued = 0, waited = 0;
-        auto issue_to = [&](int upto) {
-            upto = min(upto, nch);
-            if (issued >= upto) return;
-            __syncwarp();
-            if (lane == 0) {
-                // the slots' earlier contents were read through the generic proxy
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                for (int q = issued; q < upto; ++q) {
-                    const int k = LOWER ? q : nch - 1 - q;
-                    const int s = q % C::R;
-                    unsigned char *dst = slots + (size_t)s * SLOT;
-                    mbar_arrive_expect_tx(&bars[s], SLOT);
-                    bulk_g2s(dst, grec + (int64_t)k * C::CC * RB, C::CC * RB * (int)sizeof(T), &bars[s]);
-                    bulk_g2s(dst + C::CC * RB * sizeof(T), grhs + (int64_t)k * C::CC * BS,
-                             C::CC * BS * (int)sizeof(T), &bars[s]);
-                }
+        // chunk q holds steps [q G, (q+1) G) of the stream (the U sweep
+        // streams its unit backwards: chunk q is stored chunk nch - 1 - q)
+        auto issue = [&](int q) {
+            if (lane == 0 && q < nch) {
+                const int k = LOWER ? q : nch - 1 - q;
+                const int s = q % C::R;
+                unsigned char *dst = slots + (size_t)s * SLOT;
+                mbar_arrive_expect_tx(&bars[s], SLOT);
+                bulk_g2s(dst, grec + (int64_t)k * G * 32 * RB, G * 32 * RB * (int)sizeof(T), &bars[s]);
+                bulk_g2s(dst + G * 32 * RB * sizeof(T), grhs + (int64_t)k * G * 32 * BS, G * 32 * BS * (int)sizeof(T),
+                         &bars[s]);
             }
-            issued = upto;
         };
-        // A chunk wait longer than the spin limit records the timeout, then
+        // a chunk wait longer than the spin limit records the timeout, then
         // still waits (up to RS_WAVE_DRAIN cycles) for the copy itself, so
-        // that no copy lands in a slot after it has been reused.
-        auto wait_to = [&](int upto) {
-            while (waited < upto) {
-                const int s = waited % C::R;
-                const unsigned par = (parity >> s) & 1u;
-                if (!mbar_try_wait(&bars[s], par)) {
-                    const long long t0 = clock64();
-                    bool late = false;
-                    while (!mbar_try_wait(&bars[s], par)) {
-                        const long long dt = clock64() - t0;
-                        if (!late && dt > g.limit) {
-                            late = true;
-                            if (lane == 0) atomicOr(g.err, RS_DEVERR_TIMEOUT);
-                        }
-                        if (dt > RS_WAVE_DRAIN) break;
+        // that no copy lands in a slot after it has been reused
+        auto wait = [&](int q) {
+            const int s = q % C::R;
+            const unsigned par = (parity >> s) & 1u;
+            if (!mbar_try_wait(&bars[s], par)) {
+                const long long t0 = clock64();
+                bool late = false;
+                while (!mbar_try_wait(&bars[s], par)) {
+                    const long long dt = clock64() - t0;
+                    if (!late && dt > g.limit) {
+                        late = true;
+                        if (lane == 0) atomicOr(g.err, RS_DEVERR_TIMEOUT);
                     }
+                    if (dt > RS_WAVE_DRAIN) break;
                 }
-                parity ^= 1u << s;
-                ++waited;
             }
+            parity ^= 1u << s;
         };
         // the hand-off values of step s (raw bits; 0.0 where none is read)
+        const T *zp0 = xv + zsrc * BS, *yp0 = xv + ysrc * BS;
         auto fetch = [&](int s, bits_t (&oz)[BS], bits_t (&oy)[BS]) {
+            const int t = LOWER ? s : g.npad - 1 - s;
+            const unsigned x = (unsigned)(t - lj);
+            const bool act = s < g.npad && x < (unsigned)g.nx;
+            const int off = 32 * BS * t;
 #pragma unroll
-            for (int k = 0; k < BS; ++k) oz[k] = oy[k] = 0;
-            if (s >= U.nsteps) return;
-            const int t = LOWER ? s : U.nsteps - 1 - s;
-            const int x = t - lane;
-            if (lane >= U.L || x < 0 || x >= g.nx) return;
-            if (has_z) {
-                const T *p = xv + (zbase + wave_cell(U.tab, g.nx, t, lane)) * BS;
-#pragma unroll
-                for (int k = 0; k < BS; ++k) oz[k] = ld_relaxed_bits(p + k);
-            }
-            if (has_y && lane == ylane) {
-                // L: (x, y-1) is lane 31 of the unit before, at step t + 31;
-                // U: (x, y+1) is lane 0 of the unit after, at step t - 31
-                const int cy = LOWER ? wave_cell(ytab, g.nx, t + 31, 31) : wave_cell(ytab, g.nx, t - 31, 0);
-                const T *p = xv + (ybase + cy) * BS;
-#pragma unroll
-                for (int k = 0; k < BS; ++k) oy[k] = ld_relaxed_bits(p + k);
+            for (int k = 0; k < BS; ++k) {
+                oz[k] = act && pz ? ld_poll(zp0 + off + k) : bits_t(0);
+                oy[k] = act && py ? ld_poll(yp0 + off + k) : bits_t(0);
             }
         };
 
-        issue_to(C::R);
+        __syncwarp();
+        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int q = 0; q + 1 < C::R; ++q) issue(q);
         bits_t hz[HP][BS], hy[HP][BS];
 #pragma unroll
         for (int k = 0; k < HP; ++k) fetch(k, hz[k], hy[k]);
@@ -302,126 +301,130 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
 #pragma unroll
         for (int k = 0; k < BS; ++k) vprev[k] = T(0);
 
-        for (int s0 = 0; s0 < U.nsteps; s0 += HP) {
+        for (int s0 = 0; s0 < g.npad; s0 += HP) {
 #pragma unroll
             for (int kk = 0; kk < HP; ++kk) {
                 const int s = s0 + kk;
-                if (s < U.nsteps) {
-                const int t = LOWER ? s : U.nsteps - 1 - s;
-                const int x = t - lane;
-                const bool act = lane < U.L && x >= 0 && x < g.nx;
-                const int tlo = __ldg(U.tab + t), thi = __ldg(U.tab + t + 1);
-                const int c = tlo + lane - max(0, t - g.nx + 1);
-                // refill the slots of chunks already consumed, wait for the ones this step reads
-                if (LOWER) {
-                    issue_to(tlo / C::CC + C::R);
-                    wait_to((thi - 1) / C::CC + 1);
-                } else {
-                    issue_to(nch - (thi + C::CC - 1) / C::CC + C::R);
-                    wait_to(nch - tlo / C::CC);
-                }
-                T rv[RB], bv[BS];
-                if (act) {
-                    const int k = c / C::CC, o = c - k * C::CC;
-                    const int q = LOWER ? k : nch - 1 - k;
-                    const unsigned char *sp = slots + (size_t)(q % C::R) * SLOT;
-                    lds_rec<RB>((const T *)sp + o * RB, rv);
-                    const T *rp = (const T *)(sp + C::CC * RB * sizeof(T)) + o * BS;
+                {
+                    if (kk % G == 0) {
+                        // a new chunk: refill the slot of the one just
+                        // consumed, then wait for this one
+                        const int q = s / G;
+                        __syncwarp();
+                        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(q + C::R - 1);
+                        wait(q);
+                    }
+                    const int t = LOWER ? s : g.npad - 1 - s;
+                    const int x = t - lj;
+                    const bool act = lane_ok && x >= 0 && x < g.nx;
+                    // this step's record and right-hand side: step t % G of
+                    // the slot (idle lanes read the zero records of the
+                    // padding; their result is discarded below)
+                    const int pos = LOWER ? kk % G : G - 1 - kk % G;   // a constant once unrolled
+                    const unsigned char *sp = slots + (size_t)((s / G) % C::R) * SLOT;
+                    T rv[RB], bv[BS];
+                    lds_rec<RB>((const T *)sp + (pos * 32 + lane) * RB, rv);
+                    {
+                        const T *rp = (const T *)(sp + G * 32 * RB * sizeof(T)) + (pos * 32 + lane) * BS;
 #pragma unroll
-                    for (int k2 = 0; k2 < BS; ++k2) bv[k2] = rp[k2];
-                } else {
+                        for (int k2 = 0; k2 < BS; ++k2) bv[k2] = rp[k2];
+                    }
+                    // hand-off values from other units: loaded HP steps ago;
+                    // reload while any is a sentinel
+                    const bool nz_ = act && pz, ny_ = act && py;
+                    bool pend = false;
 #pragma unroll
-                    for (int k2 = 0; k2 < RB; ++k2) rv[k2] = T(0);
+                    for (int k2 = 0; k2 < BS; ++k2)
+                        pend |= (nz_ && hz[kk][k2] == SENT) || (ny_ && hy[kk][k2] == SENT);
+                    if (__any_sync(FULL, pend)) {
+                        const long long t0 = clock64();
+                        for (;;) {
+                            if (pend) {
+                                bits_t oz[BS], oy[BS];
+                                fetch(s, oz, oy);
+                                pend = false;
 #pragma unroll
-                    for (int k2 = 0; k2 < BS; ++k2) bv[k2] = T(0);
-                }
-                // hand-off values: loaded HP steps ago; reload while any is a sentinel
-                const bool need_z = act && has_z, need_y = act && has_y && lane == ylane;
-                bool pend = false;
-#pragma unroll
-                for (int k2 = 0; k2 < BS; ++k2)
-                    pend |= (need_z && hz[kk][k2] == SENT) || (need_y && hy[kk][k2] == SENT);
-                if (__any_sync(FULL, pend)) {
-                    const long long t0 = clock64();
-                    for (;;) {
-                        if (pend) {
-                            bits_t oz[BS], oy[BS];
-                            fetch(s, oz, oy);
-#pragma unroll
-                            for (int k2 = 0; k2 < BS; ++k2) {
-                                if (need_z) hz[kk][k2] = oz[k2];
-                                if (need_y) hy[kk][k2] = oy[k2];
+                                for (int k2 = 0; k2 < BS; ++k2) {
+                                    if (nz_) hz[kk][k2] = oz[k2];
+                                    if (ny_) hy[kk][k2] = oy[k2];
+                                    pend |= (nz_ && hz[kk][k2] == SENT) || (ny_ && hy[kk][k2] == SENT);
+                                }
                             }
-                            pend = false;
+                            if (!__any_sync(FULL, pend)) break;
+                            if (dead || clock64() - t0 > g.limit) {
+                                // give up: carry NaN on (arithmetic on the sentinel quiets it)
+                                if (pend) atomicOr(g.err, RS_DEVERR_TIMEOUT);
+                                dead = true;
+                                break;
+                            }
+                        }
+                        // the loads of the next steps were issued as early as
+                        // this step's and would miss as well: issue them again
 #pragma unroll
-                            for (int k2 = 0; k2 < BS; ++k2)
-                                pend |= (need_z && hz[kk][k2] == SENT) || (need_y && hy[kk][k2] == SENT);
+                        for (int q = 1; q < HP; ++q) fetch(s + q, hz[(kk + q) % HP], hy[(kk + q) % HP]);
+                    }
+                    // neighbours inside the tile: one shuffle each
+                    T vz[BS], vy[BS];
+#pragma unroll
+                    for (int k2 = 0; k2 < BS; ++k2) {
+                        const T sy = LOWER ? __shfl_up_sync(FULL, vprev[k2], 1) : __shfl_down_sync(FULL, vprev[k2], 1);
+                        const T sz = LOWER ? __shfl_up_sync(FULL, vprev[k2], a) : __shfl_down_sync(FULL, vprev[k2], a);
+                        const bool yin = LOWER ? jy > 0 : jy < a - 1;
+                        const bool zin = LOWER ? jz > 0 : jz < b - 1;
+                        vy[k2] = yin ? sy : (ny_ ? bits_to(T(), hy[kk][k2]) : T(0));
+                        vz[k2] = zin ? sz : (nz_ ? bits_to(T(), hz[kk][k2]) : T(0));
+                    }
+                    // load step s + HP's hand-off values into the slot just used
+                    fetch(s + HP, hz[kk], hy[kk]);
+                    T acc[BS];
+                    if (LOWER) {
+#pragma unroll
+                        for (int i = 0; i < BS; ++i) acc[i] = bv[i];
+#pragma unroll
+                        for (int i = 0; i < BS; ++i)
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[i * BS + j], vz[j]);
+#pragma unroll
+                        for (int i = 0; i < BS; ++i)
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[B2 + i * BS + j], vy[j]);
+#pragma unroll
+                        for (int i = 0; i < BS; ++i)
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[2 * B2 + i * BS + j], vprev[j]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < BS; ++i) {
+                            T sum = T(0);
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) sum = mad(rv[3 * B2 + i * BS + j], bv[j], sum);
+                            acc[i] = sum;
                         }
-                        if (!__any_sync(FULL, pend)) break;
-                        if (dead || clock64() - t0 > g.limit) {
-                            // give up: carry NaN on (arithmetic on the sentinel quiets it)
-                            if (pend) atomicOr(g.err, RS_DEVERR_TIMEOUT);
-                            dead = true;
-                            break;
-                        }
+#pragma unroll
+                        for (int i = 0; i < BS; ++i)
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[i * BS + j], vz[j]);
+#pragma unroll
+                        for (int i = 0; i < BS; ++i)
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[B2 + i * BS + j], vprev[j]);
+#pragma unroll
+                        for (int i = 0; i < BS; ++i)
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[2 * B2 + i * BS + j], vy[j]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < BS; ++i) vprev[i] = act ? acc[i] : T(0);
+                    if (act) {
+                        T *p = xv + (base + 32 * (int64_t)t + lane) * BS;
+#pragma unroll
+                        for (int i = 0; i < BS; ++i) st_poll(p + i, vprev[i]);
                     }
                 }
-                T vz[BS], vy[BS];
-#pragma unroll
-                for (int k2 = 0; k2 < BS; ++k2) {
-                    vz[k2] = need_z ? bits_to(T(), hz[kk][k2]) : T(0);
-                    const T sh = LOWER ? __shfl_up_sync(FULL, vprev[k2], 1) : __shfl_down_sync(FULL, vprev[k2], 1);
-                    vy[k2] = lane == ylane ? (need_y ? bits_to(T(), hy[kk][k2]) : T(0)) : sh;
-                }
-                // load step s + HP's hand-off values into the slot just used
-                fetch(s + HP, hz[kk], hy[kk]);
-                T acc[BS];
-                if (LOWER) {
-#pragma unroll
-                    for (int i = 0; i < BS; ++i) acc[i] = bv[i];
-#pragma unroll
-                    for (int i = 0; i < BS; ++i)
-#pragma unroll
-                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[i * BS + j], vz[j]);
-#pragma unroll
-                    for (int i = 0; i < BS; ++i)
-#pragma unroll
-                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[B2 + i * BS + j], vy[j]);
-#pragma unroll
-                    for (int i = 0; i < BS; ++i)
-#pragma unroll
-                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[2 * B2 + i * BS + j], vprev[j]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < BS; ++i) {
-                        T sum = T(0);
-#pragma unroll
-                        for (int j = 0; j < BS; ++j) sum = mad(rv[3 * B2 + i * BS + j], bv[j], sum);
-                        acc[i] = sum;
-                    }
-#pragma unroll
-                    for (int i = 0; i < BS; ++i)
-#pragma unroll
-                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[i * BS + j], vz[j]);
-#pragma unroll
-                    for (int i = 0; i < BS; ++i)
-#pragma unroll
-                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[B2 + i * BS + j], vprev[j]);
-#pragma unroll
-                    for (int i = 0; i < BS; ++i)
-#pragma unroll
-                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[2 * B2 + i * BS + j], vy[j]);
-                }
-#pragma unroll
-                for (int i = 0; i < BS; ++i) vprev[i] = act ? acc[i] : T(0);
-                if (act) {
-                    T *p = xv + (U.base + c) * BS;
-#pragma unroll
-                    for (int i = 0; i < BS; ++i) st_relaxed(p + i, vprev[i]);
-                }
-                }   // s < nsteps
             }
         }
+        // every chunk was waited for at its first step: none is in flight
     }
     wave_end(g);
 }
@@ -491,7 +494,7 @@ __global__ void k_wave_gather(WaveArgs g, const int *__restrict__ ptr, const int
         for (int e = 0; e < B2; ++e) ur[3 * B2 + e] = (T)D[e];
         for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
             const int d = col[p] - i;
-            const double *a = lu + (size_t)p * B2;
+            const double *av = lu + (size_t)p * B2;
             int lslot = -1, uslot = -1;
             if (d == -nxy) lslot = 0;
             else if (d == -g.nx) lslot = 1;
@@ -501,7 +504,7 @@ __global__ void k_wave_gather(WaveArgs g, const int *__restrict__ ptr, const int
             else if (d == g.nx) uslot = 2;
             if (lslot >= 0) {
 #pragma unroll
-                for (int e = 0; e < B2; ++e) lr[lslot * B2 + e] = (T)a[e];
+                for (int e = 0; e < B2; ++e) lr[lslot * B2 + e] = (T)av[e];
             } else if (uslot >= 0) {
 #pragma unroll
                 for (int r2 = 0; r2 < BS; ++r2)
@@ -509,7 +512,7 @@ __global__ void k_wave_gather(WaveArgs g, const int *__restrict__ ptr, const int
                     for (int c2 = 0; c2 < BS; ++c2) {
                         double s = 0.0;
 #pragma unroll
-                        for (int m = 0; m < BS; ++m) s = __dadd_rn(s, __dmul_rn(D[r2 * BS + m], a[m * BS + c2]));
+                        for (int m = 0; m < BS; ++m) s = __dadd_rn(s, __dmul_rn(D[r2 * BS + m], av[m * BS + c2]));
                         ur[uslot * B2 + r2 * BS + c2] = (T)s;
                     }
             }
@@ -576,27 +579,19 @@ int wave_gather_t(IluFactor *f)
     return rs_check_launch(ctx);
 }
 
-int cells_per_chunk(int bs, int fp32)
+template <int BS>
+void cfg_of(int fp32, int *G, int *hp, int *rl, int *ru)
 {
-    switch (bs) {
-    case 1: return fp32 ? WaveCfg<1, float>::CC : WaveCfg<1, double>::CC;
-    case 2: return fp32 ? WaveCfg<2, float>::CC : WaveCfg<2, double>::CC;
-    case 3: return fp32 ? WaveCfg<3, float>::CC : WaveCfg<3, double>::CC;
-    default: return fp32 ? WaveCfg<4, float>::CC : WaveCfg<4, double>::CC;
-    }
-}
-
-int record_len(int bs, int fp32, bool lower)
-{
-    switch (bs) {
-    case 1: return fp32 ? (lower ? WaveCfg<1, float>::RL : WaveCfg<1, float>::RU)
-                        : (lower ? WaveCfg<1, double>::RL : WaveCfg<1, double>::RU);
-    case 2: return fp32 ? (lower ? WaveCfg<2, float>::RL : WaveCfg<2, float>::RU)
-                        : (lower ? WaveCfg<2, double>::RL : WaveCfg<2, double>::RU);
-    case 3: return fp32 ? (lower ? WaveCfg<3, float>::RL : WaveCfg<3, float>::RU)
-                        : (lower ? WaveCfg<3, double>::RL : WaveCfg<3, double>::RU);
-    default: return fp32 ? (lower ? WaveCfg<4, float>::RL : WaveCfg<4, float>::RU)
-                         : (lower ? WaveCfg<4, double>::RL : WaveCfg<4, double>::RU);
+    if (fp32) {
+        *G = WaveCfg<BS, float>::G;
+        *hp = WaveCfg<BS, float>::HP;
+        *rl = WaveCfg<BS, float>::RL;
+        *ru = WaveCfg<BS, float>::RU;
+    } else {
+        *G = WaveCfg<BS, double>::G;
+        *hp = WaveCfg<BS, double>::HP;
+        *rl = WaveCfg<BS, double>::RL;
+        *ru = WaveCfg<BS, double>::RU;
     }
 }
 
@@ -649,46 +644,59 @@ bool rs_wave_detect(int n, const std::vector<int> &ptr, const std::vector<int> &
     return true;
 }
 
+// Tile shape: a lanes along y, 32 / a along z, minimising the units on the
+// critical path (ceil(ny/a) + ceil(nz/b)), then the idle lanes.
+static int tile_log2a(int ny, int nz)
+{
+    int best = 5;
+    int64_t bh = -1, bi = -1;
+    for (int la = 0; la <= 5; ++la) {
+        const int a = 1 << la, b = 32 >> la;
+        const int64_t nyt = (ny + a - 1) / a, nzt = (nz + b - 1) / b;
+        const int64_t hops = nyt + nzt, idle = nyt * nzt * 32 - (int64_t)ny * nz;
+        if (bh < 0 || hops < bh || (hops == bh && idle < bi)) {
+            best = la;
+            bh = hops;
+            bi = idle;
+        }
+    }
+    return best;
+}
+
 int rs_wave_create(IluFactor *f, int nx, int ny, int nz)
 {
     rs_ctx *ctx = f->ctx;
     WaveLayout &W = f->W;
     const int bs = f->bs;
     const size_t esz = f->fp32 ? sizeof(float) : sizeof(double);
+    int G = 1, hp = 1, rl = 0, ru = 0;
+    switch (bs) {
+    case 1: cfg_of<1>(f->fp32, &G, &hp, &rl, &ru); break;
+    case 2: cfg_of<2>(f->fp32, &G, &hp, &rl, &ru); break;
+    case 3: cfg_of<3>(f->fp32, &G, &hp, &rl, &ru); break;
+    default: cfg_of<4>(f->fp32, &G, &hp, &rl, &ru); break;
+    }
     W.nx = nx;
     W.ny = ny;
     W.nz = nz;
-    W.nyb = (ny + 31) / 32;
-    W.lastL = ny - 32 * (W.nyb - 1);
-    W.nunits = nz * W.nyb;
-    W.cc = cells_per_chunk(bs, f->fp32);
-    W.sfull = (32 * nx + W.cc - 1) / W.cc * W.cc;
-    const int slast = (W.lastL * nx + W.cc - 1) / W.cc * W.cc;
-    W.plane = (int64_t)(W.nyb - 1) * W.sfull + slast;
-    W.ncell = (int64_t)nz * W.plane;
-    // first cell of every step, for units of 32 lines and for the last one
-    const int stride = nx + RS_WAVE_OFF_PAD;
-    std::vector<int> off(2 * (size_t)stride, 0);
-    for (int b = 0; b < 2; ++b) {
-        const int L = b == 0 ? 32 : W.lastL;
-        int *o = off.data() + (size_t)b * stride;
-        for (int t = 0; t + 1 < stride; ++t) {
-            const int cnt = t < nx + L - 1 ? std::min(t, L - 1) - std::max(0, t - nx + 1) + 1 : 0;
-            o[t + 1] = o[t] + cnt;
-        }
-    }
-    const int lr = record_len(bs, f->fp32, true), ur = record_len(bs, f->fp32, false);
-    int st = rs_alloc(ctx, (void **)&W.off, sizeof(int) * off.size());
-    st = st ? st : rs_alloc(ctx, &W.lrec, esz * lr * (size_t)W.ncell);
-    st = st ? st : rs_alloc(ctx, &W.urec, esz * ur * (size_t)W.ncell);
+    W.la = tile_log2a(ny, nz);
+    const int a = 1 << W.la, b = 32 >> W.la;
+    W.nyt = (ny + a - 1) / a;
+    W.nzt = (nz + b - 1) / b;
+    W.nunits = W.nyt * W.nzt;
+    const int nsteps = nx + a + b - 2;
+    W.npad = (nsteps + G - 1) / G * G;       // a multiple of the hand-off depth (itself of G)
+    W.npad = (W.npad + hp - 1) / hp * hp;
+    W.ncell = (int64_t)W.nunits * W.npad * 32;
+    int st = rs_alloc(ctx, &W.lrec, esz * rl * (size_t)W.ncell);
+    st = st ? st : rs_alloc(ctx, &W.urec, esz * ru * (size_t)W.ncell);
     st = st ? st : rs_alloc(ctx, &W.rw, esz * bs * (size_t)W.ncell);
     st = st ? st : rs_alloc(ctx, &W.yw, esz * bs * (size_t)W.ncell);
     st = st ? st : rs_alloc(ctx, &W.zw, esz * bs * (size_t)W.ncell);
     if (st) return st;
-    RS_CUDA_TRY(cudaMemcpyAsync(W.off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
-    // padding cells are streamed but never used: keep them defined
-    RS_CUDA_TRY(cudaMemsetAsync(W.lrec, 0, esz * lr * (size_t)W.ncell, ctx->stream));
-    RS_CUDA_TRY(cudaMemsetAsync(W.urec, 0, esz * ur * (size_t)W.ncell, ctx->stream));
+    // idle cells are streamed but never used: keep them defined
+    RS_CUDA_TRY(cudaMemsetAsync(W.lrec, 0, esz * rl * (size_t)W.ncell, ctx->stream));
+    RS_CUDA_TRY(cudaMemsetAsync(W.urec, 0, esz * ru * (size_t)W.ncell, ctx->stream));
     RS_CUDA_TRY(cudaMemsetAsync(W.rw, 0, esz * bs * (size_t)W.ncell, ctx->stream));
     const int64_t nv = (int64_t)bs * W.ncell;
     const int g = (int)std::min<int64_t>((nv + 255) / 256, 4096);
@@ -709,7 +717,6 @@ void rs_wave_free(IluFactor *f)
 {
     rs_ctx *ctx = f->ctx;
     WaveLayout &W = f->W;
-    rs_free(ctx, W.off);
     rs_free(ctx, W.lrec);
     rs_free(ctx, W.urec);
     rs_free(ctx, W.rw);

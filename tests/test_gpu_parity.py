@@ -180,9 +180,9 @@ def test_sweep_levels_structured(rs, ctx, shape):
         M = rs.Precond(ctx, A, "ilu0", prec=prec, sweep="segments")
         assert M.sweep_kind() == ("segments", None)
         assert M.sweep_levels() == (expect, expect)
-        # by default the wavefront sweeps take the grid read off the pattern:
-        # nx + ny + nz - 2 cells on the longest dependency chain
-        W = rs.Precond(ctx, A, "ilu0", prec=prec)
+        # the wavefront sweeps take the grid read off the pattern: nx + ny +
+        # nz - 2 cells on the longest dependency chain
+        W = rs.Precond(ctx, A, "ilu0", prec=prec, sweep="wavefront")
         assert W.sweep_kind() == ("wavefront", (nx, ny, nz))
         assert W.sweep_levels() == (nx + ny + nz - 2,) * 2
 
@@ -655,7 +655,7 @@ def test_lgmres_maxit_and_zero_rhs(rs, ctx, orc):
     assert info["status"] == 0 and not x0.numpy().any()
 
 
-@pytest.mark.parametrize("sweep", ["auto", "segments"])
+@pytest.mark.parametrize("sweep", ["wavefront", "segments"])
 def test_device_wait_timeout_is_reported_and_the_context_survives(rs, ctx, orc, sweep):
     """Failure detection without a GPU fault: with a one-cycle limit the
     sweeps' polls give up at their second look, record the timeout and
@@ -665,7 +665,7 @@ def test_device_wait_timeout_is_reported_and_the_context_survives(rs, ctx, orc, 
     g, d = _problem((48, 48, 24), 85, 0.1)
     A = rs.Mat.csr(ctx, d)
     M = rs.Precond(ctx, A, "ilu0", sweep=sweep)
-    assert M.sweep_kind()[0] == ("wavefront" if sweep == "auto" else "segments")
+    assert M.sweep_kind()[0] == sweep
     r = synth.x_true(g.n, 85)
     assert ctx.check() == rs.OK
     ctx.set_spin_limit(1)

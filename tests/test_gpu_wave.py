@@ -40,7 +40,7 @@ def test_wave_ilu0_apply_matches_oracle_and_segments(rs, ctx, orc, shape):
     r = np.random.default_rng(32).standard_normal(g.n)
     nx, ny, nz = shape
     for prec in ("fp64", "mixed"):
-        W = rs.Precond(ctx, A, "ilu0", prec=prec)
+        W = rs.Precond(ctx, A, "ilu0", prec=prec, sweep="wavefront")
         # a 2-D grid reads as nx x ny x 1; a grid with ny = 1 as nx x nz x 1
         assert W.sweep_kind() == ("wavefront", (nx, ny, nz))
         assert np.array_equal(W.ilu_factors(d["col"].size), lu)
@@ -61,7 +61,7 @@ def test_wave_is_bit_stable_across_applies_and_scales(rs, ctx, orc):
     g = synth.Grid(40, 50, 12)
     d = synth.pressure_7pt(g, 41)
     A = rs.Mat.csr(ctx, d)
-    M = rs.Precond(ctx, A, "ilu0")
+    M = rs.Precond(ctx, A, "ilu0", sweep="wavefront")
     r = np.random.default_rng(42).standard_normal(g.n)
     z1, z2 = rs.Vec.zeros(ctx, g.n), rs.Vec.zeros(ctx, g.n)
     M.apply(rs.Vec(ctx, r), z1)
@@ -88,7 +88,7 @@ def test_wave_subset_pattern(rs, ctx, orc, drop, seed):
     assert st == 0
     r = rng.standard_normal(g.n)
     for prec in ("fp64", "mixed"):
-        M = rs.Precond(ctx, A, "ilu0", prec=prec)
+        M = rs.Precond(ctx, A, "ilu0", prec=prec, sweep="wavefront")
         assert M.sweep_kind()[0] == "wavefront"
         z = rs.Vec.zeros(ctx, g.n)
         M.apply(rs.Vec(ctx, r), z)
@@ -103,18 +103,18 @@ def test_non_grid_patterns_take_the_segment_sweeps(rs, ctx, orc):
     D = (D + sp.diags(np.abs(D).sum(axis=1).A1 + 1.0)).tocsr()
     D.sort_indices()
     d = dict(n=n, rowptr=D.indptr.astype(np.int32), col=D.indices.astype(np.int32), val=D.data.copy())
-    assert rs.Precond(ctx, rs.Mat.csr(ctx, d), "ilu0").sweep_kind() == ("segments", None)
+    assert rs.Precond(ctx, rs.Mat.csr(ctx, d), "ilu0", sweep="wavefront").sweep_kind() == ("segments", None)
     T = sp.diags([-np.ones(n - 1), 3 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1], format="csr")
     T.sort_indices()
     d = dict(n=n, rowptr=T.indptr.astype(np.int32), col=T.indices.astype(np.int32), val=T.data.copy())
-    assert rs.Precond(ctx, rs.Mat.csr(ctx, d), "ilu0").sweep_kind() == ("segments", None)
+    assert rs.Precond(ctx, rs.Mat.csr(ctx, d), "ilu0", sweep="wavefront").sweep_kind() == ("segments", None)
     g = synth.Grid(10, 9, 8)
     P = sp.csr_matrix((lambda m: (m["val"], m["col"], m["rowptr"]))(synth.pressure_7pt(g, 3)), shape=(g.n, g.n))
     P = (P + sp.diags([-0.01 * np.ones(g.n - 11), -0.01 * np.ones(g.n - 11)], [-11, 11])).tocsr()
     P.sort_indices()
     d = dict(n=g.n, rowptr=P.indptr.astype(np.int32), col=P.indices.astype(np.int32), val=P.data.copy())
     A = rs.Mat.csr(ctx, d)
-    M = rs.Precond(ctx, A, "ilu0")
+    M = rs.Precond(ctx, A, "ilu0", sweep="wavefront")
     assert M.sweep_kind() == ("segments", None)
     Ao = orc.Mat.csr(d)
     _, _, lu = orc.ilu0(Ao)
@@ -134,7 +134,7 @@ def test_wave_block_ilu0_matches_oracle(rs, ctx, orc, shape):
     assert st == 0
     r = np.random.default_rng(9).standard_normal(A.n)
     for prec in ("fp64", "mixed"):
-        M = rs.Precond(ctx, A, "bilu0", prec=prec)
+        M = rs.Precond(ctx, A, "bilu0", prec=prec, sweep="wavefront")
         assert M.sweep_kind() == ("wavefront", shape)
         S = rs.Precond(ctx, A, "bilu0", prec=prec, sweep="segments")
         ref = orc.bilu0_solve(Ao, lu_ref, dinv_ref, r, fp32=(prec == "mixed"))
@@ -155,7 +155,7 @@ def test_wave_cpr_apply_and_fgmres(rs, ctx, orc, prec):
     m = synth.black_oil_bsr3(g, 21)
     Ao = orc.Mat.bsr(m)
     A = rs.Mat.bsr(ctx, m)
-    M = rs.Precond(ctx, A, "cpr", prec=prec)
+    M = rs.Precond(ctx, A, "cpr", prec=prec, sweep="wavefront")
     assert M.sweep_kind() == ("wavefront", (16, 40, 8))
     Mo = orc.PC(Ao, "cpr", mixed=(prec == "mixed"))
     f = np.random.default_rng(22).standard_normal(A.n)
@@ -179,7 +179,7 @@ def test_wave_gmres_full_size(rs, ctx, orc):
     b = orc.spmv(Ao, synth.x_true(g.n, 1))
     xo, io, ho = orc.gmres(Ao, orc.PC(Ao, "ilu0"), b, restart=30, rtol=1e-8, hist_len=4000)
     A = rs.Mat.csr(ctx, d)
-    M = rs.Precond(ctx, A, "ilu0")
+    M = rs.Precond(ctx, A, "ilu0", sweep="wavefront")
     assert M.sweep_kind() == ("wavefront", (128, 128, 64))
     hist = ctx.set_history(4000)
     x = rs.Vec.zeros(ctx, g.n)
