@@ -228,8 +228,11 @@ int rs_vec_norm2(const rs_vec *x, double *out);
  * Its scratch is a fixed static device array (512 KB per GPU that loads the
  * library, held until exit), shared by every call: calls that overlap on the
  * GPU race.  1 <= k <= 64 (larger k returns RS_ERR_INVALID_ARG); ld >= n.
- * The first call on a device looks up the array's device address; make it
- * before any stream capture. */
+ * The call runs on the device the stream belongs to (the current device for
+ * the default streams).  The first call on a device looks up the array's
+ * device address and keeps it for the life of the process; make it before
+ * any stream capture.  A reset of the device (cudaDeviceReset) makes that
+ * address stale: restart the process before calling again. */
 int rs_vec_mdot_noalloc(const double *V, int32_t ld, int32_t n, int32_t k, const double *w,
                         double *h, void *cuda_stream);
 

@@ -602,12 +602,19 @@ int rs_amg_apply(AmgData *M, const double *r, double *z, const int *skip)
     if (ctx->prof_on || M->nograph || cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess ||
         cs != cudaStreamCaptureStatusNone)
         return vcycle(M, 0, r, z, skip);
-    for (const AmgGraph &g : M->graphs)
-        if (g.r == r && g.z == z && g.skip == skip) {
+    for (size_t i = 0; i < M->graphs.size(); ++i) {
+        const AmgGraph &g = M->graphs[i];
+        if (g.r != r || g.z != z || g.skip != skip) continue;
+        if (g.limit == ctx->spin_limit) {
             if (cudaGraphLaunch(g.exec, ctx->stream) != cudaSuccess) return RS_ERR_CUDA;
             ctx->launches += g.nlaunch;
             return RS_OK;
         }
+        // captured with another device-wait limit (rs_set_spin_limit since)
+        cudaGraphExecDestroy(g.exec);
+        M->graphs.erase(M->graphs.begin() + i);
+        break;
+    }
     if (M->applies++ == 0 || (int)M->graphs.size() >= RS_AMG_MAX_GRAPHS) return vcycle(M, 0, r, z, skip);
     if (!M->capture && cudaStreamCreateWithFlags(&M->capture, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -634,7 +641,7 @@ int rs_amg_apply(AmgData *M, const double *r, double *z, const int *skip)
         ctx->launches = l0;
         return vcycle(M, 0, r, z, skip);
     }
-    M->graphs.push_back({r, z, skip, exec, ctx->launches - l0});
+    M->graphs.push_back({r, z, skip, ctx->spin_limit, exec, ctx->launches - l0});
     // the capture has counted the graph's launches once; this is their run
     return cudaGraphLaunch(exec, user) == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }

@@ -230,6 +230,7 @@ struct AmgGraph {
     const double *r;
     double *z;
     const int *skip;
+    long long limit;         // the spin limit its kernels were captured with
     cudaGraphExec_t exec;
     long long nlaunch;
 };
@@ -279,6 +280,7 @@ struct rs_pc {
         double *z;
         const int *skip;
         unsigned gen;
+        long long limit;     // the spin limit its kernels were captured with
         cudaGraphExec_t exec;
         long long nlaunch;
     };

@@ -112,30 +112,36 @@ __device__ __forceinline__ bool reduce_partials(double (&acc)[NV], int nv, doubl
 // Warp reduce-scatter of NC per-lane values (NC a power of two): after
 // log2(NC) exchange-and-add steps lane l holds complete sums of columns
 // [l*NC/32, (l+1)*NC/32) (NC >= 32) or of column l/(32/NC) (NC < 32), for
-// about NC FP64 additions per lane instead of 5 per column.
+// about NC FP64 additions per lane instead of 5 per column.  Each step is a
+// template instance, so every index is a compile-time constant and the
+// values stay in registers.
+template <int NC, int W, int M>
+struct ReduceScatter {
+    static __device__ __forceinline__ void run(double (&v)[NC], int lane)
+    {
+        if constexpr (M >= 1) {
+            if constexpr (W > 1) {
+                // split: keep one half of the live values, send the other to lane ^ M
+                const bool up = lane & M;
+#pragma unroll
+                for (int j = 0; j < W / 2; ++j) {
+                    const double send = up ? v[j] : v[j + W / 2];
+                    const double keep = up ? v[j + W / 2] : v[j];
+                    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+                }
+                ReduceScatter<NC, W / 2, M / 2>::run(v, lane);
+            } else {
+                v[0] += __shfl_xor_sync(0xffffffffu, v[0], M);
+                ReduceScatter<NC, 1, M / 2>::run(v, lane);
+            }
+        }
+    }
+};
+
 template <int NC>
 __device__ __forceinline__ void warp_reduce_scatter(double (&v)[NC], int lane)
 {
-    int width = NC;
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        if (NC >= 32 || m >= 32 / NC) {
-            // split: keep one half of the live values, send the other to lane ^ m
-            const bool up = lane & m;
-            const int h = width / 2;
-#pragma unroll
-            for (int j = 0; j < NC / 2; ++j) {
-                if (j < h) {
-                    const double send = up ? v[j] : v[j + h];
-                    const double keep = up ? v[j + h] : v[j];
-                    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-                }
-            }
-            width = h > 0 ? h : 1;
-        } else {
-            v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
-        }
-    }
+    ReduceScatter<NC, NC, 16>::run(v, lane);
 }
 
 // Block reduction of NC per-thread column sums (and one extra scalar) with a
@@ -214,8 +220,10 @@ struct CgsCfg {
 };
 
 // NC: columns of the ring and of the reduction (a power of two); NCC: the
-// unrolled bound of the multiply-add loops (nc rounded up to 4), so that a
-// row issues at most 3 multiply-adds that are predicated off.
+// unrolled bound of the multiply-add loops (nc rounded down to 4); the last
+// nc - NCC (0 to 3) columns take a warp-uniform branch, so that no FP64
+// multiply-add is issued for a column that does not exist (predicated-off
+// FP64 instructions still occupy the FP64 pipe on this GPU).
 template <int NC, int NCC, int MODE>
 __global__ void __launch_bounds__(CgsCfg<NC>::THREADS)
 k_cgs_pass(int n, int ld, int nc, const double *__restrict__ V, double *w, double *partials, unsigned *ticket,
@@ -270,16 +278,24 @@ k_cgs_pass(int n, int ld, int nc, const double *__restrict__ V, double *w, doubl
             const int r = tile * C::TILE + threadIdx.x;
             if (r < n) {
                 const double wr = st[NC * C::TILE];
+                const int rem = nc - NCC;   // 0..3, the same for the whole grid
                 if (MODE == CGS_DOTS) {
 #pragma unroll
-                    for (int k = 0; k < NCC; ++k)
-                        if (k < nc) acc[k] = fma(st[k * C::TILE], wr, acc[k]);
+                    for (int k = 0; k < NCC; ++k) acc[k] = fma(st[k * C::TILE], wr, acc[k]);
+#pragma unroll
+                    for (int k = NCC; k < NCC + 3 && k < NC; ++k)
+                        if (k - NCC < rem) acc[k] = fma(st[k * C::TILE], wr, acc[k]);
                     extra = fma(wr, wr, extra);
                 } else {
                     double s0 = 0.0, s1 = 0.0;
 #pragma unroll
                     for (int k = 0; k < NCC; ++k) {
-                        if (k < nc) {
+                        if (k & 1) s1 = fma(st[k * C::TILE], hs[k], s1);
+                        else s0 = fma(st[k * C::TILE], hs[k], s0);
+                    }
+#pragma unroll
+                    for (int k = NCC; k < NCC + 3 && k < NC; ++k) {
+                        if (k - NCC < rem) {
                             if (k & 1) s1 = fma(st[k * C::TILE], hs[k], s1);
                             else s0 = fma(st[k * C::TILE], hs[k], s0);
                         }
@@ -288,8 +304,10 @@ k_cgs_pass(int n, int ld, int nc, const double *__restrict__ V, double *w, doubl
                     w[r] = w1;
                     if (MODE == CGS_UPDATE_DOTS) {
 #pragma unroll
-                        for (int k = 0; k < NCC; ++k)
-                            if (k < nc) acc[k] = fma(st[k * C::TILE], w1, acc[k]);
+                        for (int k = 0; k < NCC; ++k) acc[k] = fma(st[k * C::TILE], w1, acc[k]);
+#pragma unroll
+                        for (int k = NCC; k < NCC + 3 && k < NC; ++k)
+                            if (k - NCC < rem) acc[k] = fma(st[k * C::TILE], w1, acc[k]);
                     } else {
                         extra = fma(w1, w1, extra);
                     }
@@ -439,10 +457,12 @@ static int launch_cgs_pass(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresD
     return rs_check_launch(ctx);
 }
 
+// NCC = nc rounded down to 4; the reduction and ring width NC (a power of
+// two) holds the up to 3 columns past it
 template <int NCC>
 static int launch_cgs(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
 {
-    constexpr int NC = NCC <= 8 ? 8 : NCC <= 16 ? 16 : NCC <= 32 ? 32 : 64;
+    constexpr int NC = NCC + 3 <= 8 ? 8 : NCC + 3 <= 16 ? 16 : NCC + 3 <= 32 ? 32 : 64;
     int st = launch_cgs_pass<NC, NCC, CGS_DOTS>(ctx, n, ld, nc, V, d);
     if (!st) st = launch_cgs_pass<NC, NCC, CGS_UPDATE_DOTS>(ctx, n, ld, nc, V, d);
     if (!st) st = launch_cgs_pass<NC, NCC, CGS_UPDATE_NORM>(ctx, n, ld, nc, V, d);
@@ -451,7 +471,8 @@ static int launch_cgs(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d
 
 static int cgs_step(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
 {
-    switch ((nc + 3) / 4) {
+    switch (nc / 4) {
+    case 0: return launch_cgs<0>(ctx, n, ld, nc, V, d);
     case 1: return launch_cgs<4>(ctx, n, ld, nc, V, d);
     case 2: return launch_cgs<8>(ctx, n, ld, nc, V, d);
     case 3: return launch_cgs<12>(ctx, n, ld, nc, V, d);
@@ -460,10 +481,14 @@ static int cgs_step(rs_ctx *ctx, int n, int ld, int nc, double *V, GmresDev *d)
     case 6: return launch_cgs<24>(ctx, n, ld, nc, V, d);
     case 7: return launch_cgs<28>(ctx, n, ld, nc, V, d);
     case 8: return launch_cgs<32>(ctx, n, ld, nc, V, d);
-    case 9: case 10: return launch_cgs<40>(ctx, n, ld, nc, V, d);
-    case 11: case 12: return launch_cgs<48>(ctx, n, ld, nc, V, d);
-    case 13: case 14: return launch_cgs<56>(ctx, n, ld, nc, V, d);
-    default: return launch_cgs<64>(ctx, n, ld, nc, V, d);
+    case 9: return launch_cgs<36>(ctx, n, ld, nc, V, d);
+    case 10: return launch_cgs<40>(ctx, n, ld, nc, V, d);
+    case 11: return launch_cgs<44>(ctx, n, ld, nc, V, d);
+    case 12: return launch_cgs<48>(ctx, n, ld, nc, V, d);
+    case 13: return launch_cgs<52>(ctx, n, ld, nc, V, d);
+    case 14: return launch_cgs<56>(ctx, n, ld, nc, V, d);
+    case 15: return launch_cgs<60>(ctx, n, ld, nc, V, d);
+    default: return nc <= 64 ? launch_cgs<64 - 3>(ctx, n, ld, nc, V, d) : RS_ERR_INVALID_ARG;
     }
 }
 

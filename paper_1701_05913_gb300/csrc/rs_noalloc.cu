@@ -18,9 +18,12 @@
 //
 // In host code the name of a __device__ array is only a host-side stand-in;
 // the kernel must be given the device address, which cudaGetSymbolAddress
-// returns.  The first call on each device looks that address up (with the
-// device current) and caches it; make that first call before capturing a
-// stream into a graph.
+// returns.  The first call on each device looks that address up (with that
+// device current) and caches it for the life of the process; make that
+// first call before capturing a stream into a graph.  The device is the one
+// the caller's stream belongs to.  A reset of that device (cudaDeviceReset)
+// unloads the array, so the cached address is stale afterwards: restart the
+// process before calling again.
 #include <mutex>
 
 #include "rs_internal.cuh"
@@ -44,11 +47,10 @@ struct NoallocSlot {
 static NoallocSlot g_slots[RS_NOALLOC_MAX_DEVICES];
 static std::mutex g_slots_mu;
 
-// Looks up the device addresses of the scratch arrays for the current device.
-static int noalloc_setup(NoallocSlot **out)
+// Looks up the device addresses of the scratch arrays for device dev (the
+// current device).
+static int noalloc_setup(int dev, NoallocSlot **out)
 {
-    int dev = 0;
-    RS_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= RS_NOALLOC_MAX_DEVICES) return RS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_slots_mu);
     NoallocSlot &s = g_slots[dev];
@@ -119,14 +121,26 @@ extern "C" int rs_vec_mdot_noalloc(const double *V, int32_t ld, int32_t n, int32
 {
     if (k < 1 || k > RS_NOALLOC_MAX_COLS) return RS_ERR_INVALID_ARG;
     if (n < 0 || ld < n || (n > 0 && (!V || !w)) || !h) return RS_ERR_INVALID_ARG;
-    NoallocSlot *s = nullptr;
-    RS_TRY(noalloc_setup(&s));
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    RS_CUDA_TRY(cudaMemsetAsync(s->ticket, 0, sizeof(unsigned), st));
-    int blocks = (n + RS_NOALLOC_THREADS - 1) / RS_NOALLOC_THREADS;
-    if (blocks > s->blocks) blocks = s->blocks;
-    if (blocks < 1) blocks = 1;
-    k_mdot_noalloc<<<blocks, RS_NOALLOC_THREADS, 0, st>>>(n, ld, k, V, w, s->partials, s->ticket, h);
-    RS_CUDA_TRY(cudaGetLastError());
-    return RS_OK;
+    // the device of the caller's stream (the current device for the
+    // default streams), made current for the call
+    int dev = 0, cur = 0;
+    RS_CUDA_TRY(cudaGetDevice(&cur));
+    RS_CUDA_TRY(cudaStreamGetDevice(st, &dev));
+    if (dev != cur) RS_CUDA_TRY(cudaSetDevice(dev));
+    NoallocSlot *s = nullptr;
+    int rc = noalloc_setup(dev, &s);
+    if (rc == RS_OK) {
+        int blocks = (n + RS_NOALLOC_THREADS - 1) / RS_NOALLOC_THREADS;
+        if (blocks > s->blocks) blocks = s->blocks;
+        if (blocks < 1) blocks = 1;
+        if (cudaMemsetAsync(s->ticket, 0, sizeof(unsigned), st) != cudaSuccess) {
+            rc = RS_ERR_CUDA;
+        } else {
+            k_mdot_noalloc<<<blocks, RS_NOALLOC_THREADS, 0, st>>>(n, ld, k, V, w, s->partials, s->ticket, h);
+            if (cudaGetLastError() != cudaSuccess) rc = RS_ERR_CUDA;
+        }
+    }
+    if (dev != cur) cudaSetDevice(cur);
+    return rc;
 }

@@ -126,8 +126,10 @@ static int cpr_apply(rs_pc *M, const double *r, double *z, const int *skip)
 // captured once into a CUDA graph and replayed; a nested AMG V-cycle then
 // runs inside the capture.  Capture runs on a private stream (the caller's
 // may be the legacy default stream, which cannot be captured); replays go to
-// the caller's stream.  A graph of the learned stage is dropped when the
-// network's workspace has been reallocated since (another grid).  With the
+// the caller's stream.  A graph is dropped when the device-wait limit has
+// changed since its capture (rs_set_spin_limit), and a graph of the learned
+// stage when the network's workspace has been reallocated since (another
+// grid).  With the
 // profiler on, a network on another context, or if a capture fails, the
 // apply is launched kernel by kernel.
 static int cpr_apply_graph(rs_pc *M, const double *r, double *z, const int *skip)
@@ -143,7 +145,7 @@ static int cpr_apply_graph(rs_pc *M, const double *r, double *z, const int *skip
     for (size_t i = 0; i < M->graphs.size(); ++i) {
         rs_pc::Graph &g = M->graphs[i];
         if (g.r != r || g.z != z || g.skip != skip) continue;
-        if (g.gen == gen) {
+        if (g.gen == gen && g.limit == ctx->spin_limit) {
             if (cudaGraphLaunch(g.exec, ctx->stream) != cudaSuccess) return RS_ERR_CUDA;
             ctx->launches += g.nlaunch;
             return RS_OK;
@@ -177,7 +179,7 @@ static int cpr_apply_graph(rs_pc *M, const double *r, double *z, const int *skip
         ctx->launches = l0;
         return cpr_apply(M, r, z, skip);
     }
-    M->graphs.push_back({r, z, skip, gen, exec, ctx->launches - l0});
+    M->graphs.push_back({r, z, skip, gen, ctx->spin_limit, exec, ctx->launches - l0});
     // the capture has counted the graph's launches once; this is their run
     return cudaGraphLaunch(exec, user) == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }

@@ -21,7 +21,7 @@ import numpy as np
 
 import synth
 
-from . import Context, Mat, Net, Precond, Vec, solve_fgmres, solve_gmres  # noqa: F401
+from . import Context, Mat, Net, Precond, Vec, solve_fgmres, solve_gmres, vec_axpbyz, vec_norm2  # noqa: F401
 
 
 def _torch():
@@ -58,7 +58,8 @@ def make_pairs(ctx: Context, seeds, grid=(64, 64, 64), kz=1.0, noise_rtol=1e-11,
             solve_gmres(A, M, b, x, restart=30, rtol=1e-14, maxit=k)
             rk = Vec(ctx, b.t.clone())
             A.amxpby(-1.0, x, 1.0, rk)          # r_k = b - A x_k
-            ek = Vec(ctx, xt.t - x.t)           # e_k = x_true - x_k
+            ek = Vec.zeros(ctx, g.n)
+            vec_axpbyz(1.0, xt, -1.0, x, ek)    # e_k = x_true - x_k
             rs_.append(rk.t.clone())
             es.append(ek.t.clone())
             fidx.append(fi)
@@ -67,12 +68,12 @@ def make_pairs(ctx: Context, seeds, grid=(64, 64, 64), kz=1.0, noise_rtol=1e-11,
                 field=torch.tensor(fidx), seconds=time.perf_counter() - t0)
 
 
-def output_scale(data) -> float:
-    """Median of rms(e) / rms(r) over the pairs (fixes the network's output scale)."""
-    torch = _torch()
-    rr = torch.sqrt(torch.mean(data["r"] ** 2, dim=1))
-    ee = torch.sqrt(torch.mean(data["e"] ** 2, dim=1))
-    return float(torch.median(ee / rr))
+def output_scale(ctx: Context, data) -> float:
+    """Median over the pairs of rms(e) / rms(r) = ||e|| / ||r|| (fixes the
+    network's output scale); the norms are the library's."""
+    ratios = [vec_norm2(Vec(ctx, data["e"][i])) / vec_norm2(Vec(ctx, data["r"][i]))
+              for i in range(data["r"].shape[0])]
+    return float(np.median(ratios))
 
 
 def he_params(seed: int = 0) -> dict:
@@ -94,7 +95,7 @@ def train_net(ctx: Context, data, epochs=8, batch=8, lr=2e-3, seed=0, net: Net |
     grid = data["grid"]
     P = data["r"].shape[0]
     if net is None:
-        net = Net(ctx, he_params(seed), out_scale=output_scale(data))
+        net = Net(ctx, he_params(seed), out_scale=output_scale(ctx, data))
     rng = np.random.default_rng(seed)
     steps = epochs * max(P // batch, 1)
     hist = []
@@ -149,7 +150,9 @@ def evaluate(ctx: Context, net: Net, seeds, grid=(64, 64, 64), kz=1.0, rtol=1e-8
                 torch.cuda.synchronize()
                 t = e0.elapsed_time(e1) / 1e3
                 best = t if best is None else min(best, t)
-            err = float(torch.linalg.norm(x.t - xt.t) / torch.linalg.norm(xt.t))
+            dx = Vec.zeros(ctx, g.n)
+            vec_axpbyz(1.0, x, -1.0, xt, dx)
+            err = vec_norm2(dx) / vec_norm2(xt)
             res[name] = dict(iters=info["iters"], seconds=best, true_rel_res=info["true_rel_res"],
                              status=info["status"], err_vs_xtrue=err)
         rows.append(dict(seed=s, **res))
@@ -190,7 +193,7 @@ def main(argv=None):
     lt = [r["learned_fgmres"]["seconds"] for r in rows]
     bt = [r["ilu0_gmres"]["seconds"] for r in rows]
     print(json.dumps(dict(grid=grid, train_fields=t1 - t0, pairs=int(data["r"].shape[0]),
-                          datagen_s=data["seconds"], train=hist, out_scale=output_scale(data),
+                          datagen_s=data["seconds"], train=hist, out_scale=output_scale(ctx, data),
                           eval=dict(seeds=[e0, e1], learned_iters_median=float(np.median(li)),
                                     ilu0_iters_median=float(np.median(bi)),
                                     learned_s_median=float(np.median(lt)), ilu0_s_median=float(np.median(bt)),

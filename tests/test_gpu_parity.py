@@ -683,3 +683,32 @@ def test_device_wait_timeout_is_reported_and_the_context_survives(rs, ctx, orc, 
     _, _, lu = orc.ilu0(Ao)
     assert rel(z.numpy(), orc.ilu0_solve(Ao, lu, r)) <= 1e-12
     assert ctx.check() == rs.OK
+
+
+def test_spin_limit_set_after_capture_reaches_cpr_replays(rs, ctx, orc):
+    """CPR applies are replayed from CUDA graphs after the first apply.  A
+    device-wait limit set later must reach the replayed kernels: with a
+    one-cycle limit the next apply reports the timeout (the graph captured
+    with the old limit is dropped and the apply recaptured)."""
+    g = synth.Grid(24, 20, 12)
+    m = synth.black_oil_bsr3(g, 86)
+    A = rs.Mat.bsr(ctx, m)
+    M = rs.Precond(ctx, A, "cpr", sweep="segments")
+    f = vec(rs, ctx, np.random.default_rng(87).standard_normal(A.n))
+    z = rs.Vec.zeros(ctx, A.n)
+    for _ in range(3):                     # the second and third applies replay a graph
+        M.apply(f, z)
+    assert ctx.check() == rs.OK
+    ctx.set_spin_limit(1)
+    try:
+        M.apply(f, z)
+        st = ctx.check()
+    finally:
+        ctx.set_spin_limit(0)
+    assert st == rs.ERR_DEVICE_TIMEOUT
+    assert ctx.check() == rs.OK
+    M2 = rs.Precond(ctx, A, "cpr", sweep="segments")
+    for _ in range(3):
+        M2.apply(f, z)
+    assert rel(z.numpy(), orc.PC(orc.Mat.bsr(m), "cpr").apply(f.numpy())) <= 1e-12
+    assert ctx.check() == rs.OK
