@@ -109,6 +109,9 @@ def parse():
     ap.add_argument("--impl", default="rs", choices=["rs", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", default=None,
+                    help="NX,NY,NZ: the workload's method on another grid (small cases for ncu captures; "
+                         "the config then names the grid after the workload)")
     return ap.parse_args()
 
 
@@ -795,6 +798,11 @@ def main():
     args = parse()
     rank, world, local = dist_env()
     w = WORKLOADS[args.workload]
+    if args.grid:
+        w = dict(w, grid=tuple(int(v) for v in args.grid.split(",")))
+        if len(w["grid"]) != 3 or min(w["grid"]) < 1:
+            raise SystemExit("--grid wants NX,NY,NZ")
+        args.workload = "%s@%dx%dx%d" % ((args.workload,) + w["grid"])
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return

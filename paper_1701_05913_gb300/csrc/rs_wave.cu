@@ -7,25 +7,30 @@
 // ILU(0) keeps that pattern, so the dependency graph of either sweep is the
 // grid itself and its critical path is nx + ny + nz - 2 cells long.
 //
-// Schedule.  One warp takes a unit: a tile of a y-lines by b z-planes (a b =
-// 32 lanes) over all x.  Lane (jy, jz) solves cell (x = t - jy - jz, y0 + jy,
-// z0 + jz) at step t: its x-neighbour is the lane's own value of the step
-// before, its y- and z-neighbours inside the tile the step-before values of
-// lanes (jy-1, jz) and (jy, jz-1), one shuffle each.  Only the tile's faces
-// read other units, through L2, with the value as its own ready flag (a
-// sentinel NaN until written), loaded several steps ahead and checked when
-// used; a miss reloads it and the loads issued after it.  A unit takes
-// nx + a + b - 2 steps; the units on the critical path number
-// ceil(ny/a) + ceil(nz/b) - 1, so a and b are chosen to minimise it.  Units
-// are taken in order from a ticket counter (the U sweep in reverse), so a
-// warp only waits for units held by warps that took earlier tickets and are
-// running: the schedule cannot deadlock, and every wait is bounded in time.
+// Schedule.  A block of two warps takes a unit: a tile of a y-lines by b
+// z-planes (a b = 32 lanes) over all x.  In the compute warp lane (jy, jz)
+// solves cell (x = t - jy - jz, y0 + jy, z0 + jz) at step t: its
+// x-neighbour is the lane's own value of the step before, its y- and
+// z-neighbours inside the tile the step-before values of lanes (jy-1, jz)
+// and (jy, jz-1), one shuffle each.  Only the tile's faces read other units,
+// through L2, with the value as its own ready flag (a sentinel NaN until
+// written).  The producer warp polls those values, several steps at a time
+// and continuously, so that each is seen about one L2 round trip after it is
+// written, and hands them to the compute warp through a shared-memory ring
+// with a step counter; it also streams the unit's records and right-hand
+// side into the compute warp's ring of bulk-copy slots.  The compute warp
+// thus runs only the step's arithmetic.  A unit takes nx + a + b - 2 steps;
+// the units on the critical path number ceil(ny/a) + ceil(nz/b) - 1, so a
+// and b are chosen to minimise it.  Units are taken in order from a ticket
+// counter (the U sweep in reverse), so a block only waits for units held by
+// blocks that took earlier tickets and are running: the schedule cannot
+// deadlock, and every wait is bounded in time.
 //
 // Layout.  Every unit stores its cells by step, 32 per step (lane order,
 // zeros where a lane is idle), so a step's values, records and right-hand
 // side are contiguous and every address is the unit's base plus 32 t plus
-// the lane.  A warp streams its unit's records and right-hand side through a
-// ring of shared-memory slots of G steps each, filled by bulk copies
+// the lane.  The records and right-hand side stream through a ring of
+// shared-memory slots of G steps each, filled by bulk copies
 // (mbarrier-counted).  Two permutation kernels move r from natural into wave
 // order (scaled, rounded to the apply precision) and the result back.
 //
@@ -48,33 +53,37 @@
 
 namespace {
 
-// Records, ring and hand-off depth per block size and apply precision.
+// Records, rings and hand-off depth per block size and apply precision.
 template <int BS, typename T>
 struct WaveCfg {
     static constexpr int B2 = BS * BS;
     static constexpr int VQ = 16 / (int)sizeof(T);                 // T per 16 bytes
     static constexpr int RL = (3 * B2 + VQ - 1) / VQ * VQ;           // L record: L_z, L_y, L_x
     static constexpr int RU = (4 * B2 + VQ - 1) / VQ * VQ;           // U record: U'_z, U'_x, U'_y, D
-    // steps per ring slot: about 10 KB per U slot
+    // steps per bulk-copy slot: about 10 KB per U slot
     static constexpr int G0 = 10240 / (32 * (RU + BS) * (int)sizeof(T));
     static constexpr int G = G0 >= 16 ? 16 : G0 >= 8 ? 8 : G0 >= 4 ? 4 : G0 >= 2 ? 2 : 1;
-    static constexpr int R = 4;                                      // ring slots per warp
-    // hand-off values are loaded HP steps ahead: about one L2 round trip
-    // (0.6-1 us) at the step's pace.  More adds HP steps of lag to every
-    // hand-off between units; fewer leaves each step waiting for its load.
-    // A multiple of G, so that chunk boundaries fall on fixed steps of the
-    // unrolled loop.
-    static constexpr int HP0 = sizeof(T) == 8 ? (BS == 1 ? 8 : 2) : (BS == 1 ? 16 : 8);
-    static constexpr int HP = HP0 < G ? G : HP0;
-    static_assert(HP % G == 0, "hand-off depth is a whole number of chunks");
-    // warps per block: FP64 sweeps keep the SM's scarce FP64 pipes for few warps
-    static constexpr int WPB = sizeof(T) == 8 ? 2 : 4;
-    static constexpr int BAR_BYTES = 128;                            // WPB * R mbarriers, padded
-    static_assert((G & (G - 1)) == 0, "chunks are a power of two of steps");
+    static constexpr int R = 4;                                      // bulk-copy slots (WaveHdr::bar)
+    // steps of hand-off values the producer polls at once: enough to keep
+    // ahead of the compute warp's pace over one L2 round trip
+    static constexpr int K = BS == 1 ? (sizeof(T) == 4 ? 16 : 8) : (sizeof(T) == 4 ? 8 : 4);
+    // hand-off ring (steps), a power of two
+    static constexpr int HR = 2 * K < 16 ? 16 : 2 * K;
+    static constexpr int HDR_BYTES = 128;                            // R mbarriers, ticket, counters
+    static_assert((G & (G - 1)) == 0 && (HR & (HR - 1)) == 0 && HR % G == 0, "rings are powers of two, chunks fit the hand-off ring");
     template <bool LOWER>
     static constexpr int slot_bytes() { return G * 32 * ((LOWER ? RL : RU) + BS) * (int)sizeof(T); }
+    static constexpr int ring_bytes() { return HR * 2 * 32 * BS * (int)sizeof(T); }
     template <bool LOWER>
-    static constexpr int smem_bytes() { return BAR_BYTES + WPB * R * slot_bytes<LOWER>(); }
+    static constexpr int smem_bytes() { return HDR_BYTES + R * slot_bytes<LOWER>() + ring_bytes(); }
+};
+
+// the block's shared header
+struct WaveHdr {
+    unsigned long long bar[4];    // bulk-copy slots' mbarriers
+    int tk;                       // the unit's ticket
+    unsigned prod;                // steps whose hand-off values are in the ring
+    unsigned cons;                // steps the compute warp has finished with
 };
 
 struct WaveArgs {
@@ -184,49 +193,95 @@ __device__ __forceinline__ void wave_end(const WaveArgs &g)
 // ---------------------------------------------------------------------------
 // the sweep: L (LOWER) or U
 // ---------------------------------------------------------------------------
+// shared-memory counters between the two warps of a block
+__device__ __forceinline__ unsigned ld_acq_cta(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)));
+    return v;
+}
+__device__ __forceinline__ void st_rel_cta(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+// The compute warp's progress.  A plain store: the slots it frees were read
+// by loads whose values the warp has already used (they fed the step
+// before's arithmetic, which fed this step's shuffles), so the loads are
+// complete when the store issues, and a release (which would wait for the
+// warp's outstanding global stores) is not needed.
+__device__ __forceinline__ void st_cons(unsigned *p, unsigned v)
+{
+    asm volatile("st.volatile.shared::cta.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v));
+}
+// hand-off values from the ring, after the acquire of the step counter (kept
+// in program order with it: both are volatile asm)
+__device__ __forceinline__ double lds_ho(const double *p)
+{
+    double v;
+    asm volatile("ld.shared::cta.f64 %0, [%1];" : "=d"(v) : "r"(smem_addr(p)));
+    return v;
+}
+__device__ __forceinline__ float lds_ho(const float *p)
+{
+    float v;
+    asm volatile("ld.shared::cta.f32 %0, [%1];" : "=f"(v) : "r"(smem_addr(p)));
+    return v;
+}
+
 // rec: the units' records; rhs: r in wave order (L) or y (U); xv: the values
 // this sweep produces, polled by the neighbouring units (sentinel before).
+// Warp 0 computes, warp 1 produces.  Waits inside the block (for a bulk
+// copy, for the ring) record a timeout after the spin limit and give up
+// after four limits plus RS_WAVE_DRAIN cycles; a poll of another unit's
+// value records it after the limit and carries the sentinel on from then.
 template <int BS, typename T, bool LOWER>
-__global__ void __launch_bounds__(32 * WaveCfg<BS, T>::WPB)
+__global__ void __launch_bounds__(64)
 k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T *xv)
 {
     using C = WaveCfg<BS, T>;
     constexpr int B2 = C::B2;
     constexpr int RB = LOWER ? C::RL : C::RU;
     constexpr int G = C::G;
+    constexpr int R = C::R;
+    constexpr int K = C::K;
+    constexpr int HR = C::HR;
     constexpr int SLOT = C::template slot_bytes<LOWER>();
-    constexpr int HP = C::HP;
     constexpr unsigned FULL = 0xffffffffu;
     typedef typename Sentinel<T>::bits_t bits_t;
     constexpr bits_t SENT = Sentinel<T>::bits;
     extern __shared__ __align__(128) unsigned char wave_smem[];
     if (g.skip && *(volatile const int *)g.skip) return;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned long long *bars = (unsigned long long *)wave_smem + wid * C::R;
-    unsigned char *slots = wave_smem + C::BAR_BYTES + (size_t)wid * C::R * SLOT;
-    if (lane == 0) {
-        for (int s = 0; s < C::R; ++s) mbar_init(&bars[s], 1);
+    const int lane = threadIdx.x & 31;
+    const bool producer = threadIdx.x >= 32;
+    WaveHdr *hd = (WaveHdr *)wave_smem;
+    unsigned char *slots = wave_smem + C::HDR_BYTES;
+    T *ring = (T *)(slots + R * SLOT);       // [HR steps][z, y][32 lanes][BS]
+    if (producer && lane == 0) {
+        for (int q = 0; q < R; ++q) mbar_init(&hd->bar[q], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncwarp();
     const int a = 1 << g.la, b = 32 >> g.la;
     const int jy = lane & (a - 1), jz = lane >> g.la;
     const int lj = jy + jz;                   // the lane's skew
     const int nch = g.npad / G;               // chunks per unit
     const int64_t ucells = (int64_t)g.npad * 32;
-    unsigned parity = 0;     // bit s: parity of slot s's next completion
-    bool dead = false;       // a hand-off poll gave up: later polls give up at once
+    const long long giveup = 4 * g.limit + RS_WAVE_DRAIN;
+    unsigned parity = 0;     // compute warp, bit q: parity of slot q's next completion
+    bool dead = false;       // producer: a poll gave up; later polls give up at once
     for (;;) {
-        int tk = 0;
-        if (lane == 0) tk = (int)atomicAdd(&g.st->ticket, 1u);
-        tk = __shfl_sync(FULL, tk, 0);
+        __syncthreads();     // both warps are done with the unit before
+        if (producer && lane == 0) {
+            hd->tk = (int)atomicAdd(&g.st->ticket, 1u);
+            hd->prod = 0;
+            hd->cons = 0;
+        }
+        __syncthreads();
+        const int tk = *(volatile int *)&hd->tk;
         if (tk >= g.nunits) break;
         const int u = LOWER ? tk : g.nunits - 1 - tk;
         const int zt = u / g.nyt, yt = u - zt * g.nyt;
         const bool lane_ok = (yt << g.la) + jy < g.ny && zt * b + jz < g.nz;
         const int64_t base = (int64_t)u * ucells;
-        const T *grec = rec + base * RB;
-        const T *grhs = rhs + base * BS;
         // lanes on the tile's faces read other units: z (jz = 0 for L, b - 1
         // for U) and y (jy = 0 for L, a - 1 for U); the source cell at step t
         // is src + 32 t
@@ -244,183 +299,245 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
             ysrc = base + ucells - 32 * (a - 1) + (jz << g.la);
         }
 
-        // chunk q holds steps [q G, (q+1) G) of the stream (the U sweep
-        // streams its unit backwards: chunk q is stored chunk nch - 1 - q)
-        auto issue = [&](int q) {
-            if (lane == 0 && q < nch) {
-                const int k = LOWER ? q : nch - 1 - q;
-                const int s = q % C::R;
-                unsigned char *dst = slots + (size_t)s * SLOT;
-                mbar_arrive_expect_tx(&bars[s], SLOT);
-                bulk_g2s(dst, grec + (int64_t)k * G * 32 * RB, G * 32 * RB * (int)sizeof(T), &bars[s]);
-                bulk_g2s(dst + G * 32 * RB * sizeof(T), grhs + (int64_t)k * G * 32 * BS, G * 32 * BS * (int)sizeof(T),
-                         &bars[s]);
+        if (producer) {
+            // ---------------------------------------------------------------
+            // producer: bulk copies of chunk q (steps [q G, (q+1) G); the U
+            // sweep streams its unit backwards: chunk q is stored chunk
+            // nch - 1 - q) into slot q % R once the compute warp has left
+            // chunk q - R; hand-off values of step s into ring slot s % HR
+            // once it has left step s - HR
+            // ---------------------------------------------------------------
+            const T *grec = rec + base * RB;
+            const T *grhs = rhs + base * BS;
+            const T *zp0 = xv + zsrc * BS, *yp0 = xv + ysrc * BS;
+            int qb = 0;                           // next chunk to copy
+            auto cons_now = [&]() -> int {
+                unsigned c = 0;
+                if (lane == 0) c = ld_acq_cta(&hd->cons);
+                return (int)__shfl_sync(FULL, c, 0);
+            };
+            auto issue_ready = [&](int c) {
+                while (qb < nch && (qb < R || c >= (qb - R + 1) * G)) {
+                    if (lane == 0) {
+                        const int k = LOWER ? qb : nch - 1 - qb;
+                        const int sl = qb % R;
+                        unsigned char *dst = slots + (size_t)sl * SLOT;
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        mbar_arrive_expect_tx(&hd->bar[sl], SLOT);
+                        bulk_g2s(dst, grec + (int64_t)k * G * 32 * RB, G * 32 * RB * (int)sizeof(T), &hd->bar[sl]);
+                        bulk_g2s(dst + G * 32 * RB * sizeof(T), grhs + (int64_t)k * G * 32 * BS,
+                                 G * 32 * BS * (int)sizeof(T), &hd->bar[sl]);
+                    }
+                    ++qb;
+                }
+            };
+            int sp = 0;                           // next step to hand over
+            long long tl = clock64();             // last progress
+            bool late = false;
+            while (sp < g.npad) {
+                const int c = cons_now();
+                issue_ready(c);
+                const int room = min(g.npad, c + HR) - sp;
+                if (room <= 0) {
+                    // the ring is full: wait for the compute warp
+                    const long long dt = clock64() - tl;
+                    if (!late && dt > g.limit) {
+                        late = true;
+                        if (lane == 0) atomicOr(g.err, RS_DEVERR_TIMEOUT);
+                    }
+                    if (dt > giveup) break;
+                    continue;
+                }
+                bits_t vz[K][BS], vy[K][BS];
+                unsigned miss = 0;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int s = sp + k;
+                    const int t = LOWER ? s : g.npad - 1 - s;
+                    const bool act = k < room && (unsigned)(t - lj) < (unsigned)g.nx;
+                    const int off = 32 * BS * t;
+#pragma unroll
+                    for (int k2 = 0; k2 < BS; ++k2) {
+                        vz[k][k2] = act && pz ? ld_poll(zp0 + off + k2) : bits_t(0);
+                        vy[k][k2] = act && py ? ld_poll(yp0 + off + k2) : bits_t(0);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    bool p = false;
+#pragma unroll
+                    for (int k2 = 0; k2 < BS; ++k2) p |= vz[k][k2] == SENT || vy[k][k2] == SENT;
+                    if (p) miss |= 1u << k;
+                }
+                miss = __reduce_or_sync(FULL, miss);
+                int ready = min(room, K);
+                if (miss && !dead) ready = min(ready, __ffs(miss) - 1);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if (k < ready) {
+                        T *hp = ring + ((size_t)(((sp + k) & (HR - 1)) * 2) * 32 + lane) * BS;
+#pragma unroll
+                        for (int k2 = 0; k2 < BS; ++k2) {
+                            hp[k2] = bits_to(T(), vz[k][k2]);
+                            hp[32 * BS + k2] = bits_to(T(), vy[k][k2]);
+                        }
+                    }
+                }
+                if (ready > 0) {
+                    __syncwarp();
+                    sp += ready;
+                    if (lane == 0) st_rel_cta(&hd->prod, (unsigned)sp);
+                    tl = clock64();
+                } else if (clock64() - tl > g.limit) {
+                    // give up: carry the sentinel on (arithmetic on it gives NaN)
+                    if (lane == 0) atomicOr(g.err, RS_DEVERR_TIMEOUT);
+                    dead = true;
+                }
             }
-        };
-        // a chunk wait longer than the spin limit records the timeout, then
-        // still waits (up to RS_WAVE_DRAIN cycles) for the copy itself, so
-        // that no copy lands in a slot after it has been reused
+            // the last chunks, as the compute warp frees their slots
+            tl = clock64();
+            while (qb < nch) {
+                issue_ready(cons_now());
+                if (qb < nch && clock64() - tl > giveup) {
+                    if (lane == 0) atomicOr(g.err, RS_DEVERR_TIMEOUT);
+                    break;
+                }
+            }
+            continue;
+        }
+
+        // -------------------------------------------------------------------
+        // compute warp
+        // -------------------------------------------------------------------
+        // waits for chunk q's bulk copies; past the limit it records the
+        // timeout, then still waits (up to the give-up bound) so that no copy
+        // lands in a slot after it has been reused
         auto wait = [&](int q) {
-            const int s = q % C::R;
-            const unsigned par = (parity >> s) & 1u;
-            if (!mbar_try_wait(&bars[s], par)) {
+            const int sl = q % R;
+            const unsigned par = (parity >> sl) & 1u;
+            if (!mbar_try_wait(&hd->bar[sl], par)) {
                 const long long t0 = clock64();
                 bool late = false;
-                while (!mbar_try_wait(&bars[s], par)) {
+                while (!mbar_try_wait(&hd->bar[sl], par)) {
                     const long long dt = clock64() - t0;
                     if (!late && dt > g.limit) {
                         late = true;
                         if (lane == 0) atomicOr(g.err, RS_DEVERR_TIMEOUT);
                     }
-                    if (dt > RS_WAVE_DRAIN) break;
+                    if (dt > giveup) break;
                 }
             }
-            parity ^= 1u << s;
+            parity ^= 1u << sl;
         };
-        // the hand-off values of step s (raw bits; 0.0 where none is read)
-        const T *zp0 = xv + zsrc * BS, *yp0 = xv + ysrc * BS;
-        auto fetch = [&](int s, bits_t (&oz)[BS], bits_t (&oy)[BS]) {
-            const int t = LOWER ? s : g.npad - 1 - s;
-            const unsigned x = (unsigned)(t - lj);
-            const bool act = s < g.npad && x < (unsigned)g.nx;
-            const int off = 32 * BS * t;
-#pragma unroll
-            for (int k = 0; k < BS; ++k) {
-                oz[k] = act && pz ? ld_poll(zp0 + off + k) : bits_t(0);
-                oy[k] = act && py ? ld_poll(yp0 + off + k) : bits_t(0);
+        // the producer's step counter, until it passes step s
+        auto wait_prod = [&](int s) -> unsigned {
+            unsigned v = __shfl_sync(FULL, ld_acq_cta(&hd->prod), 0);
+            if (v > (unsigned)s) return v;
+            const long long t0 = clock64();
+            bool late = false;
+            for (;;) {
+                v = __shfl_sync(FULL, ld_acq_cta(&hd->prod), 0);
+                if (v > (unsigned)s) return v;
+                const long long dt = clock64() - t0;
+                if (!late && dt > g.limit) {
+                    late = true;
+                    if (lane == 0) atomicOr(g.err, RS_DEVERR_TIMEOUT);
+                }
+                if (dt > giveup) return (unsigned)g.npad;
             }
         };
-
-        __syncwarp();
-        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int q = 0; q + 1 < C::R; ++q) issue(q);
-        bits_t hz[HP][BS], hy[HP][BS];
-#pragma unroll
-        for (int k = 0; k < HP; ++k) fetch(k, hz[k], hy[k]);
+        // The step is branch-free but for the hand-off counter: idle lanes
+        // (outside the grid, or x outside [0, nx)) read the zero records and
+        // right-hand side of the padding and zero hand-off values (the
+        // producer writes 0 where no value is read), so they compute 0 from
+        // finite inputs and store it into their own padding cells, which no
+        // lane reads; an active lane reads only active cells (its in-tile
+        // neighbours at the same x are active, and its hand-offs are the
+        // upstream unit's active face cells).
+        const bool yin = LOWER ? jy > 0 : jy < a - 1;
+        const bool zin = LOWER ? jz > 0 : jz < b - 1;
+        T *xout = xv + (base + lane) * BS;
+        unsigned avail = 0;
         T vprev[BS];
 #pragma unroll
         for (int k = 0; k < BS; ++k) vprev[k] = T(0);
-
-        for (int s0 = 0; s0 < g.npad; s0 += HP) {
+        for (int s0 = 0; s0 < g.npad; s0 += G) {
+            wait(s0 / G);
+            const unsigned char *sp = slots + (size_t)((s0 / G) % R) * SLOT;
+            const T *hring = ring + ((size_t)((s0 & (HR - 1)) * 2) * 32 + lane) * BS;
 #pragma unroll
-            for (int kk = 0; kk < HP; ++kk) {
+            for (int kk = 0; kk < G; ++kk) {
                 const int s = s0 + kk;
+                const int t = LOWER ? s : g.npad - 1 - s;
+                // this step's record and right-hand side: step t % G of the slot
+                const int pos = LOWER ? kk : G - 1 - kk;
+                T rv[RB], bv[BS];
+                lds_rec<RB>((const T *)sp + (pos * 32 + lane) * RB, rv);
                 {
-                    if (kk % G == 0) {
-                        // a new chunk: refill the slot of the one just
-                        // consumed, then wait for this one
-                        const int q = s / G;
-                        __syncwarp();
-                        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue(q + C::R - 1);
-                        wait(q);
-                    }
-                    const int t = LOWER ? s : g.npad - 1 - s;
-                    const int x = t - lj;
-                    const bool act = lane_ok && x >= 0 && x < g.nx;
-                    // this step's record and right-hand side: step t % G of
-                    // the slot (idle lanes read the zero records of the
-                    // padding; their result is discarded below)
-                    const int pos = LOWER ? kk % G : G - 1 - kk % G;   // a constant once unrolled
-                    const unsigned char *sp = slots + (size_t)((s / G) % C::R) * SLOT;
-                    T rv[RB], bv[BS];
-                    lds_rec<RB>((const T *)sp + (pos * 32 + lane) * RB, rv);
-                    {
-                        const T *rp = (const T *)(sp + G * 32 * RB * sizeof(T)) + (pos * 32 + lane) * BS;
+                    const T *rp = (const T *)(sp + G * 32 * RB * sizeof(T)) + (pos * 32 + lane) * BS;
 #pragma unroll
-                        for (int k2 = 0; k2 < BS; ++k2) bv[k2] = rp[k2];
-                    }
-                    // hand-off values from other units: loaded HP steps ago;
-                    // reload while any is a sentinel
-                    const bool nz_ = act && pz, ny_ = act && py;
-                    bool pend = false;
+                    for (int k2 = 0; k2 < BS; ++k2) bv[k2] = rp[k2];
+                }
+                // neighbours inside the tile: one shuffle each
+                T sy[BS], sz[BS];
 #pragma unroll
-                    for (int k2 = 0; k2 < BS; ++k2)
-                        pend |= (nz_ && hz[kk][k2] == SENT) || (ny_ && hy[kk][k2] == SENT);
-                    if (__any_sync(FULL, pend)) {
-                        const long long t0 = clock64();
-                        for (;;) {
-                            if (pend) {
-                                bits_t oz[BS], oy[BS];
-                                fetch(s, oz, oy);
-                                pend = false;
+                for (int k2 = 0; k2 < BS; ++k2) {
+                    sy[k2] = LOWER ? __shfl_up_sync(FULL, vprev[k2], 1) : __shfl_down_sync(FULL, vprev[k2], 1);
+                    sz[k2] = LOWER ? __shfl_up_sync(FULL, vprev[k2], a) : __shfl_down_sync(FULL, vprev[k2], a);
+                }
+                // steps before s are done with (every lane stores the same value)
+                st_cons(&hd->cons, (unsigned)s);
+                // hand-off values from other units (0 where none is read)
+                if (avail <= (unsigned)s) avail = wait_prod(s);
+                T vz[BS], vy[BS];
 #pragma unroll
-                                for (int k2 = 0; k2 < BS; ++k2) {
-                                    if (nz_) hz[kk][k2] = oz[k2];
-                                    if (ny_) hy[kk][k2] = oy[k2];
-                                    pend |= (nz_ && hz[kk][k2] == SENT) || (ny_ && hy[kk][k2] == SENT);
-                                }
-                            }
-                            if (!__any_sync(FULL, pend)) break;
-                            if (dead || clock64() - t0 > g.limit) {
-                                // give up: carry NaN on (arithmetic on the sentinel quiets it)
-                                if (pend) atomicOr(g.err, RS_DEVERR_TIMEOUT);
-                                dead = true;
-                                break;
-                            }
-                        }
-                        // the loads of the next steps were issued as early as
-                        // this step's and would miss as well: issue them again
+                for (int k2 = 0; k2 < BS; ++k2) {
+                    const T *hp = hring + (size_t)kk * 2 * 32 * BS;
+                    const T hz = lds_ho(hp + k2), hy = lds_ho(hp + 32 * BS + k2);
+                    vy[k2] = yin ? sy[k2] : hy;
+                    vz[k2] = zin ? sz[k2] : hz;
+                }
+                T acc[BS];
+                if (LOWER) {
 #pragma unroll
-                        for (int q = 1; q < HP; ++q) fetch(s + q, hz[(kk + q) % HP], hy[(kk + q) % HP]);
-                    }
-                    // neighbours inside the tile: one shuffle each
-                    T vz[BS], vy[BS];
+                    for (int i = 0; i < BS; ++i) acc[i] = bv[i];
 #pragma unroll
-                    for (int k2 = 0; k2 < BS; ++k2) {
-                        const T sy = LOWER ? __shfl_up_sync(FULL, vprev[k2], 1) : __shfl_down_sync(FULL, vprev[k2], 1);
-                        const T sz = LOWER ? __shfl_up_sync(FULL, vprev[k2], a) : __shfl_down_sync(FULL, vprev[k2], a);
-                        const bool yin = LOWER ? jy > 0 : jy < a - 1;
-                        const bool zin = LOWER ? jz > 0 : jz < b - 1;
-                        vy[k2] = yin ? sy : (ny_ ? bits_to(T(), hy[kk][k2]) : T(0));
-                        vz[k2] = zin ? sz : (nz_ ? bits_to(T(), hz[kk][k2]) : T(0));
-                    }
-                    // load step s + HP's hand-off values into the slot just used
-                    fetch(s + HP, hz[kk], hy[kk]);
-                    T acc[BS];
-                    if (LOWER) {
+                    for (int i = 0; i < BS; ++i)
 #pragma unroll
-                        for (int i = 0; i < BS; ++i) acc[i] = bv[i];
+                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[i * BS + j], vz[j]);
 #pragma unroll
-                        for (int i = 0; i < BS; ++i)
+                    for (int i = 0; i < BS; ++i)
 #pragma unroll
-                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[i * BS + j], vz[j]);
+                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[B2 + i * BS + j], vy[j]);
 #pragma unroll
-                        for (int i = 0; i < BS; ++i)
+                    for (int i = 0; i < BS; ++i)
 #pragma unroll
-                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[B2 + i * BS + j], vy[j]);
+                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[2 * B2 + i * BS + j], vprev[j]);
+                } else {
 #pragma unroll
-                        for (int i = 0; i < BS; ++i)
+                    for (int i = 0; i < BS; ++i) {
+                        T sum = T(0);
 #pragma unroll
-                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[2 * B2 + i * BS + j], vprev[j]);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < BS; ++i) {
-                            T sum = T(0);
-#pragma unroll
-                            for (int j = 0; j < BS; ++j) sum = mad(rv[3 * B2 + i * BS + j], bv[j], sum);
-                            acc[i] = sum;
-                        }
-#pragma unroll
-                        for (int i = 0; i < BS; ++i)
-#pragma unroll
-                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[i * BS + j], vz[j]);
-#pragma unroll
-                        for (int i = 0; i < BS; ++i)
-#pragma unroll
-                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[B2 + i * BS + j], vprev[j]);
-#pragma unroll
-                        for (int i = 0; i < BS; ++i)
-#pragma unroll
-                            for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[2 * B2 + i * BS + j], vy[j]);
+                        for (int j = 0; j < BS; ++j) sum = mad(rv[3 * B2 + i * BS + j], bv[j], sum);
+                        acc[i] = sum;
                     }
 #pragma unroll
-                    for (int i = 0; i < BS; ++i) vprev[i] = act ? acc[i] : T(0);
-                    if (act) {
-                        T *p = xv + (base + 32 * (int64_t)t + lane) * BS;
+                    for (int i = 0; i < BS; ++i)
 #pragma unroll
-                        for (int i = 0; i < BS; ++i) st_poll(p + i, vprev[i]);
-                    }
+                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[i * BS + j], vz[j]);
+#pragma unroll
+                    for (int i = 0; i < BS; ++i)
+#pragma unroll
+                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[B2 + i * BS + j], vprev[j]);
+#pragma unroll
+                    for (int i = 0; i < BS; ++i)
+#pragma unroll
+                        for (int j = 0; j < BS; ++j) acc[i] = msub(acc[i], rv[2 * B2 + i * BS + j], vy[j]);
+                }
+#pragma unroll
+                for (int i = 0; i < BS; ++i) {
+                    vprev[i] = acc[i];
+                    st_poll(xout + (int64_t)32 * BS * t + i, acc[i]);
                 }
             }
         }
@@ -429,22 +546,61 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
     wave_end(g);
 }
 
+// Permutations between natural order and wave order.  A block takes 32
+// steps of one unit: the 32 lanes' x-line segments (x = t - jy - jz for the
+// block's steps, contiguous in natural order) and the unit's 32 x 32 wave
+// cells of those steps (contiguous in wave order) go through a
+// shared-memory tile, so both sides are read and written in whole lines.
+constexpr int WAVE_PERM_THREADS = 256;
+
+// x of lane l's cell at step t0 + i, and whether the cell exists
+__device__ __forceinline__ bool perm_cell(const WaveArgs &g, int yt, int zt, int l, int t, int *x, int64_t *line)
+{
+    const int a = 1 << g.la, b = 32 >> g.la;
+    const int jy = l & (a - 1), jz = l >> g.la;
+    const int y = (yt << g.la) + jy, z = zt * b + jz;
+    *x = t - jy - jz;
+    *line = ((int64_t)z * g.ny + y) * g.nx;
+    return y < g.ny && z < g.nz && *x >= 0 && *x < g.nx && t < g.npad;
+}
+
 // r (natural order, FP64) -> wave order in the apply precision, times *scale;
 // the U sweep's values back to the sentinel
 template <int BS, typename T>
-__global__ void k_wave_in(WaveArgs g, const double *__restrict__ r, const double *__restrict__ scale,
-                          T *__restrict__ rw, T *__restrict__ zreset)
+__global__ void __launch_bounds__(WAVE_PERM_THREADS)
+k_wave_in(WaveArgs g, const double *__restrict__ r, const double *__restrict__ scale, T *__restrict__ rw,
+          T *__restrict__ zreset)
 {
+    constexpr int W = 32 * BS + 1;                 // tile row: one lane's 32 cells, padded
+    __shared__ double tile[32 * W];
     if (g.skip && *(volatile const int *)g.skip) return;
     const double sc = scale ? *scale : 1.0;
-    const int n = g.nx * g.ny * g.nz;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int64_t w = wave_pos(g, i);
+    const int nb = (g.npad + 31) / 32;
+    const int u = blockIdx.x / nb, t0 = (blockIdx.x - u * nb) * 32;
+    const int zt = u / g.nyt, yt = u - zt * g.nyt;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // the lanes' line segments, one warp per line
+    for (int l = wid; l < 32; l += WAVE_PERM_THREADS / 32) {
 #pragma unroll
         for (int k = 0; k < BS; ++k) {
-            const double v = r[(size_t)i * BS + k];
-            rw[w * BS + k] = (T)(sc == 1.0 ? v : v * sc);
-            zreset[w * BS + k] = bits_to(T(), Sentinel<T>::bits);
+            const int e = lane + 32 * k, i = e / BS, c = e - i * BS;
+            int x;
+            int64_t line;
+            if (perm_cell(g, yt, zt, l, t0 + i, &x, &line)) tile[l * W + e] = r[(line + x) * BS + c];
+        }
+    }
+    __syncthreads();
+    // the wave cells of the block's steps, contiguous
+    const int64_t wbase = ((int64_t)u * g.npad + t0) * 32 * BS;
+    for (int e = threadIdx.x; e < 32 * 32 * BS; e += WAVE_PERM_THREADS) {
+        const int i = e / (32 * BS), rem = e - i * 32 * BS;
+        const int l = rem / BS, c = rem - l * BS;
+        int x;
+        int64_t line;
+        if (perm_cell(g, yt, zt, l, t0 + i, &x, &line)) {
+            const double v = tile[l * W + i * BS + c];
+            rw[wbase + e] = (T)(sc == 1.0 ? v : v * sc);
+            zreset[wbase + e] = bits_to(T(), Sentinel<T>::bits);
         }
     }
 }
@@ -452,16 +608,35 @@ __global__ void k_wave_in(WaveArgs g, const double *__restrict__ r, const double
 // the U sweep's values -> natural order, FP64; the L sweep's values back to
 // the sentinel
 template <int BS, typename T>
-__global__ void k_wave_out(WaveArgs g, const T *__restrict__ zw, T *__restrict__ yreset, double *__restrict__ out)
+__global__ void __launch_bounds__(WAVE_PERM_THREADS)
+k_wave_out(WaveArgs g, const T *__restrict__ zw, T *__restrict__ yreset, double *__restrict__ out)
 {
+    constexpr int W = 32 * BS + 1;
+    __shared__ double tile[32 * W];
     if (g.skip && *(volatile const int *)g.skip) return;
-    const int n = g.nx * g.ny * g.nz;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int64_t w = wave_pos(g, i);
+    const int nb = (g.npad + 31) / 32;
+    const int u = blockIdx.x / nb, t0 = (blockIdx.x - u * nb) * 32;
+    const int zt = u / g.nyt, yt = u - zt * g.nyt;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t wbase = ((int64_t)u * g.npad + t0) * 32 * BS;
+    for (int e = threadIdx.x; e < 32 * 32 * BS; e += WAVE_PERM_THREADS) {
+        const int i = e / (32 * BS), rem = e - i * 32 * BS;
+        const int l = rem / BS, c = rem - l * BS;
+        int x;
+        int64_t line;
+        if (perm_cell(g, yt, zt, l, t0 + i, &x, &line)) {
+            tile[l * W + i * BS + c] = (double)zw[wbase + e];
+            yreset[wbase + e] = bits_to(T(), Sentinel<T>::bits);
+        }
+    }
+    __syncthreads();
+    for (int l = wid; l < 32; l += WAVE_PERM_THREADS / 32) {
 #pragma unroll
         for (int k = 0; k < BS; ++k) {
-            out[(size_t)i * BS + k] = (double)zw[w * BS + k];
-            yreset[w * BS + k] = bits_to(T(), Sentinel<T>::bits);
+            const int e = lane + 32 * k, i = e / BS, c = e - i * BS;
+            int x;
+            int64_t line;
+            if (perm_cell(g, yt, zt, l, t0 + i, &x, &line)) out[(line + x) * BS + c] = tile[l * W + e];
         }
     }
 }
@@ -544,24 +719,25 @@ int wave_apply_t(IluFactor *f, const double *r, double *z, const double *scale, 
     rs_ctx *ctx = f->ctx;
     const WaveLayout &W = f->W;
     const WaveArgs g = wave_args(ctx, W, f->state, skip);
-    const int n = f->nrows;
-    const int gp = std::max(1, std::min((n + 255) / 256, 8 * ctx->num_sms));
-    const int gw = std::max(1, std::min((W.nunits + C::WPB - 1) / C::WPB, ctx->num_sms));
+    const int gp = W.nunits * ((W.npad + 31) / 32);
+    // one unit per block at a time; as many blocks as fit (about four per SM)
+    const int per_sm = std::max(1, std::min(8, (200 * 1024) / C::template smem_bytes<false>()));
+    const int gw = std::max(1, std::min(W.nunits, per_sm * ctx->num_sms));
     constexpr int sl = C::template smem_bytes<true>(), su = C::template smem_bytes<false>();
     RS_TRY((raise_sweep_smem<BS, T, true>(ctx)));
     RS_TRY((raise_sweep_smem<BS, T, false>(ctx)));
     {
         RsProfScope prof(ctx, BS == 1 ? RS_PROF_LSWEEP : RS_PROF_BLSWEEP);
-        k_wave_in<BS, T><<<gp, 256, 0, ctx->stream>>>(g, r, scale, (T *)W.rw, (T *)W.zw);
-        k_wave_sweep<BS, T, true><<<gw, 32 * C::WPB, sl, ctx->stream>>>(g, (const T *)W.lrec, (const T *)W.rw,
+        k_wave_in<BS, T><<<gp, WAVE_PERM_THREADS, 0, ctx->stream>>>(g, r, scale, (T *)W.rw, (T *)W.zw);
+        k_wave_sweep<BS, T, true><<<gw, 64, sl, ctx->stream>>>(g, (const T *)W.lrec, (const T *)W.rw,
                                                                        (T *)W.yw);
     }
     RS_TRY(rs_check_launch(ctx));
     {
         RsProfScope prof(ctx, BS == 1 ? RS_PROF_USWEEP : RS_PROF_BUSWEEP);
-        k_wave_sweep<BS, T, false><<<gw, 32 * C::WPB, su, ctx->stream>>>(g, (const T *)W.urec, (const T *)W.yw,
+        k_wave_sweep<BS, T, false><<<gw, 64, su, ctx->stream>>>(g, (const T *)W.urec, (const T *)W.yw,
                                                                         (T *)W.zw);
-        k_wave_out<BS, T><<<gp, 256, 0, ctx->stream>>>(g, (const T *)W.zw, (T *)W.yw, z);
+        k_wave_out<BS, T><<<gp, WAVE_PERM_THREADS, 0, ctx->stream>>>(g, (const T *)W.zw, (T *)W.yw, z);
     }
     ctx->launches += 2;   // rs_check_launch counts one per call
     RS_TRY(rs_check_launch(ctx));
@@ -580,16 +756,14 @@ int wave_gather_t(IluFactor *f)
 }
 
 template <int BS>
-void cfg_of(int fp32, int *G, int *hp, int *rl, int *ru)
+void cfg_of(int fp32, int *G, int *rl, int *ru)
 {
     if (fp32) {
         *G = WaveCfg<BS, float>::G;
-        *hp = WaveCfg<BS, float>::HP;
         *rl = WaveCfg<BS, float>::RL;
         *ru = WaveCfg<BS, float>::RU;
     } else {
         *G = WaveCfg<BS, double>::G;
-        *hp = WaveCfg<BS, double>::HP;
         *rl = WaveCfg<BS, double>::RL;
         *ru = WaveCfg<BS, double>::RU;
     }
@@ -669,12 +843,12 @@ int rs_wave_create(IluFactor *f, int nx, int ny, int nz)
     WaveLayout &W = f->W;
     const int bs = f->bs;
     const size_t esz = f->fp32 ? sizeof(float) : sizeof(double);
-    int G = 1, hp = 1, rl = 0, ru = 0;
+    int G = 1, rl = 0, ru = 0;
     switch (bs) {
-    case 1: cfg_of<1>(f->fp32, &G, &hp, &rl, &ru); break;
-    case 2: cfg_of<2>(f->fp32, &G, &hp, &rl, &ru); break;
-    case 3: cfg_of<3>(f->fp32, &G, &hp, &rl, &ru); break;
-    default: cfg_of<4>(f->fp32, &G, &hp, &rl, &ru); break;
+    case 1: cfg_of<1>(f->fp32, &G, &rl, &ru); break;
+    case 2: cfg_of<2>(f->fp32, &G, &rl, &ru); break;
+    case 3: cfg_of<3>(f->fp32, &G, &rl, &ru); break;
+    default: cfg_of<4>(f->fp32, &G, &rl, &ru); break;
     }
     W.nx = nx;
     W.ny = ny;
@@ -685,8 +859,7 @@ int rs_wave_create(IluFactor *f, int nx, int ny, int nz)
     W.nzt = (nz + b - 1) / b;
     W.nunits = W.nyt * W.nzt;
     const int nsteps = nx + a + b - 2;
-    W.npad = (nsteps + G - 1) / G * G;       // a multiple of the hand-off depth (itself of G)
-    W.npad = (W.npad + hp - 1) / hp * hp;
+    W.npad = (nsteps + G - 1) / G * G;       // whole chunks
     W.ncell = (int64_t)W.nunits * W.npad * 32;
     int st = rs_alloc(ctx, &W.lrec, esz * rl * (size_t)W.ncell);
     st = st ? st : rs_alloc(ctx, &W.urec, esz * ru * (size_t)W.ncell);
