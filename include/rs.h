@@ -121,12 +121,13 @@ typedef struct {
      * it needs a nonzero diagonal on every level (else RS_ERR_ZERO_PIVOT). */
     int32_t amg_smoother;
     /* Triangular sweeps of every ILU(0) / block ILU(0) factor of this
-     * preconditioner (Eq. 3).  0 [0]: the library's choice (at present the
-     * segment sweeps, measured faster on every workload); 1: the segment
-     * sweeps; 2: the wavefront sweeps, taken when the pattern is (a subset
-     * of) the 7-point stencil of a structured grid in natural order (x
-     * fastest; the grid is read off the pattern), else the segment sweeps.
-     * RAS local factors always take the segment sweeps. */
+     * preconditioner (Eq. 3).  0 [0]: the library's choice, at present the
+     * same as 2 (measured faster than the segment sweeps on every grid
+     * workload); 1: the segment sweeps; 2: the wavefront sweeps, taken when
+     * the pattern is (a subset of) the 7-point stencil of a structured grid
+     * in natural order (x fastest; the grid is read off the pattern), else
+     * the segment sweeps.  RAS local factors always take the segment
+     * sweeps. */
     int32_t sweep;
     /* Segment sweeps: the longest run of segments one warp carries, > 0 (1:
      * no runs).  0 [0]: no limit for FP64 scalar factors, no runs for FP32

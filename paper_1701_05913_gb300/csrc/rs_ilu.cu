@@ -1361,7 +1361,7 @@ int rs_ilu_create(rs_ctx *ctx, int bs, int nrows, int64_t nnzb, const int *d_ptr
     int st = build_layout(ctx, nrows, h_ptr, h_col, diag, f->L);
     // the sweeps: wavefronts on a structured 7-point pattern, else segments
     int gx = 0, gy = 0, gz = 0;
-    const bool wave = sweep_mode == 2 && rs_wave_detect(nrows, h_ptr, h_col, &gx, &gy, &gz);
+    const bool wave = sweep_mode != 1 && rs_wave_detect(nrows, h_ptr, h_col, &gx, &gy, &gz);
     if (!wave) {
         // runs are taken by the scalar FP64 sweeps.  In FP32 a hop between
         // warps already costs about what a step of a run does (0.8 against

@@ -320,7 +320,8 @@ int rs_axpby_launch(rs_ctx *ctx, int n, double a, const double *x, double b, dou
 int rs_dot_launch(rs_ctx *ctx, int n, const double *x, const double *y, double *out_dev);
 
 // ILU
-// sweep_mode: 0 the library's choice (segments), 1 the segment sweeps, 2 the
+// sweep_mode: 0 the library's choice (the wavefront sweeps when the pattern
+// is a structured 7-point grid, else segments), 1 the segment sweeps, 2 the
 // wavefront sweeps when the pattern is a structured 7-point grid (else
 // segments).  run_cap: the longest run of segments a warp carries (0: the
 // default; scalar only).

@@ -65,8 +65,12 @@ struct WaveCfg {
     static constexpr int G = G0 >= 16 ? 16 : G0 >= 8 ? 8 : G0 >= 4 ? 4 : G0 >= 2 ? 2 : 1;
     static constexpr int R = 4;                                      // bulk-copy slots (WaveHdr::bar)
     // steps of hand-off values the producer polls at once: enough to keep
-    // ahead of the compute warp's pace over one L2 round trip
-    static constexpr int K = BS == 1 ? (sizeof(T) == 4 ? 16 : 8) : (sizeof(T) == 4 ? 8 : 4);
+    // ahead of the compute warp's pace over one L2 round trip, few enough
+    // that the round trip stays short (block records: 4 steps measured
+    // faster than 8)
+    static constexpr int K = BS == 1 ? (sizeof(T) == 4 ? 16 : 8) : (sizeof(T) == 4 ? 4 : 2);
+    // (step, position) pairs of a polling round per producer lane
+    static constexpr int JP = 4;
     // hand-off ring (steps), a power of two
     static constexpr int HR = 2 * K < 16 ? 16 : 2 * K;
     static constexpr int HDR_BYTES = 128;                            // R mbarriers, ticket, counters
@@ -245,6 +249,7 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
     constexpr int R = C::R;
     constexpr int K = C::K;
     constexpr int HR = C::HR;
+    constexpr int JP = C::JP;
     constexpr int SLOT = C::template slot_bytes<LOWER>();
     constexpr unsigned FULL = 0xffffffffu;
     typedef typename Sentinel<T>::bits_t bits_t;
@@ -262,7 +267,6 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
     }
     const int a = 1 << g.la, b = 32 >> g.la;
     const int jy = lane & (a - 1), jz = lane >> g.la;
-    const int lj = jy + jz;                   // the lane's skew
     const int nch = g.npad / G;               // chunks per unit
     const int64_t ucells = (int64_t)g.npad * 32;
     const long long giveup = 4 * g.limit + RS_WAVE_DRAIN;
@@ -280,24 +284,7 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
         if (tk >= g.nunits) break;
         const int u = LOWER ? tk : g.nunits - 1 - tk;
         const int zt = u / g.nyt, yt = u - zt * g.nyt;
-        const bool lane_ok = (yt << g.la) + jy < g.ny && zt * b + jz < g.nz;
         const int64_t base = (int64_t)u * ucells;
-        // lanes on the tile's faces read other units: z (jz = 0 for L, b - 1
-        // for U) and y (jy = 0 for L, a - 1 for U); the source cell at step t
-        // is src + 32 t
-        bool pz, py;
-        int64_t zsrc, ysrc;
-        if (LOWER) {
-            pz = lane_ok && jz == 0 && zt > 0;
-            py = lane_ok && jy == 0 && yt > 0;
-            zsrc = base - (int64_t)g.nyt * ucells + 32 * (b - 1) + jy + ((b - 1) << g.la);
-            ysrc = base - ucells + 32 * (a - 1) + (a - 1) + (jz << g.la);
-        } else {
-            pz = lane_ok && jz == b - 1 && zt < g.nzt - 1;
-            py = lane_ok && jy == a - 1 && yt < g.nyt - 1;
-            zsrc = base + (int64_t)g.nyt * ucells - 32 * (b - 1) + jy;
-            ysrc = base + ucells - 32 * (a - 1) + (jz << g.la);
-        }
 
         if (producer) {
             // ---------------------------------------------------------------
@@ -309,7 +296,6 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
             // ---------------------------------------------------------------
             const T *grec = rec + base * RB;
             const T *grhs = rhs + base * BS;
-            const T *zp0 = xv + zsrc * BS, *yp0 = xv + ysrc * BS;
             int qb = 0;                           // next chunk to copy
             auto cons_now = [&]() -> int {
                 unsigned c = 0;
@@ -331,6 +317,36 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
                     ++qb;
                 }
             };
+            // The unit's hand-off positions: p < a on the z face (the
+            // consumer lane with jy = p on the face row), p >= a on the y face
+            // (jz = p - a).  The pairs (step k of the round, position p) are
+            // spread over the lanes, JP per lane, so that a round of polls
+            // takes few load instructions.
+            const int F = a + b;
+            const int KE = min(K, (32 * JP) / F);        // steps per round, >= 1
+            int jk[JP], jring[JP], jskew[JP];
+            int64_t jsrc[JP];
+            bool jin[JP], jok[JP];
+#pragma unroll
+            for (int j = 0; j < JP; ++j) {
+                const int idx = lane + 32 * j;
+                const int k = idx / F, p = idx - k * F;
+                const bool zf = p < a;
+                const int cy = zf ? p : (LOWER ? 0 : a - 1);           // consumer lane (cy, cz)
+                const int cz = zf ? (LOWER ? 0 : b - 1) : p - a;
+                const bool has = zf ? (LOWER ? zt > 0 : zt < g.nzt - 1) : (LOWER ? yt > 0 : yt < g.nyt - 1);
+                const bool c_ok = (yt << g.la) + cy < g.ny && zt * b + cz < g.nz;
+                // the upstream unit's cell: same x, one step of the skew away
+                const int64_t uu = zf ? (LOWER ? (int64_t)u - g.nyt : (int64_t)u + g.nyt) : (LOWER ? u - 1 : u + 1);
+                const int sl = zf ? (LOWER ? cy + ((b - 1) << g.la) : cy) : (LOWER ? (a - 1) + (cz << g.la) : (cz << g.la));
+                const int so = zf ? (LOWER ? b - 1 : -(b - 1)) : (LOWER ? a - 1 : -(a - 1));
+                jin[j] = k < KE;
+                jok[j] = jin[j] && has && c_ok;
+                jk[j] = k;
+                jring[j] = ((zf ? 0 : 1) * 32 + cy + (cz << g.la)) * BS;
+                jskew[j] = cy + cz;
+                jsrc[j] = jok[j] ? uu * ucells + 32 * so + sl : 0;
+            }
             int sp = 0;                           // next step to hand over
             long long tl = clock64();             // last progress
             bool late = false;
@@ -348,39 +364,35 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
                     if (dt > giveup) break;
                     continue;
                 }
-                bits_t vz[K][BS], vy[K][BS];
+                bits_t v[JP][BS];
                 unsigned miss = 0;
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const int s = sp + k;
+                for (int j = 0; j < JP; ++j) {
+                    const int s = sp + jk[j];
                     const int t = LOWER ? s : g.npad - 1 - s;
-                    const bool act = k < room && (unsigned)(t - lj) < (unsigned)g.nx;
-                    const int off = 32 * BS * t;
+                    const bool act = jok[j] && jk[j] < room && (unsigned)(t - jskew[j]) < (unsigned)g.nx;
+                    const T *src = xv + (jsrc[j] + 32 * (int64_t)t) * BS;
 #pragma unroll
-                    for (int k2 = 0; k2 < BS; ++k2) {
-                        vz[k][k2] = act && pz ? ld_poll(zp0 + off + k2) : bits_t(0);
-                        vy[k][k2] = act && py ? ld_poll(yp0 + off + k2) : bits_t(0);
-                    }
+                    for (int k2 = 0; k2 < BS; ++k2) v[j][k2] = act ? ld_poll(src + k2) : bits_t(0);
                 }
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
+                for (int j = 0; j < JP; ++j) {
                     bool p = false;
 #pragma unroll
-                    for (int k2 = 0; k2 < BS; ++k2) p |= vz[k][k2] == SENT || vy[k][k2] == SENT;
-                    if (p) miss |= 1u << k;
+                    for (int k2 = 0; k2 < BS; ++k2) p |= v[j][k2] == SENT;
+                    if (p) miss |= 1u << jk[j];
                 }
                 miss = __reduce_or_sync(FULL, miss);
-                int ready = min(room, K);
+                int ready = min(room, KE);
                 if (miss && !dead) ready = min(ready, __ffs(miss) - 1);
+                // every position of the steps handed over is written: the
+                // value, or 0 where no value is read
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    if (k < ready) {
-                        T *hp = ring + ((size_t)(((sp + k) & (HR - 1)) * 2) * 32 + lane) * BS;
+                for (int j = 0; j < JP; ++j) {
+                    if (jin[j] && jk[j] < ready) {
+                        T *hp = ring + (size_t)((sp + jk[j]) & (HR - 1)) * 2 * 32 * BS + jring[j];
 #pragma unroll
-                        for (int k2 = 0; k2 < BS; ++k2) {
-                            hp[k2] = bits_to(T(), vz[k][k2]);
-                            hp[32 * BS + k2] = bits_to(T(), vy[k][k2]);
-                        }
+                        for (int k2 = 0; k2 < BS; ++k2) hp[k2] = bits_to(T(), v[j][k2]);
                     }
                 }
                 if (ready > 0) {

@@ -158,7 +158,7 @@ def test_ras_sweep_levels_shrink_with_subdomains(rs, ctx):
     g = synth.Grid(64, 64, 32)
     d = synth.pressure_7pt(g, 55)
     A = rs.Mat.csr(ctx, d)
-    l0, u0 = rs.Precond(ctx, A, "ilu0").sweep_levels()
+    l0, u0 = rs.Precond(ctx, A, "ilu0", sweep="segments").sweep_levels()
     M = rs.Precond(ctx, A, "ras", nparts=32, part=rs.box_partition((64, 64, 32), (4, 4, 2)), overlap=1)
     l1, u1 = M.sweep_levels()
     # one subdomain of 16 x 16 x 16 cells plus one layer: at most 1 + 18 + 18 - 2 segment levels

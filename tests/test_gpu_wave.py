@@ -95,6 +95,23 @@ def test_wave_subset_pattern(rs, ctx, orc, drop, seed):
         assert rel(z.numpy(), orc.ilu0_solve(Ao, lu, r, fp32=(prec == "mixed"))) <= (1e-12 if prec == "fp64" else 1e-5)
 
 
+def test_library_choice_is_the_wavefront_on_grids(rs, ctx):
+    """The default sweep option takes the wavefront sweeps on a structured
+    7-point pattern (scalar and block) and the segment sweeps elsewhere."""
+    g = synth.Grid(20, 12, 6)
+    A = rs.Mat.csr(ctx, synth.pressure_7pt(g, 60))
+    assert rs.Precond(ctx, A, "ilu0").sweep_kind() == ("wavefront", (20, 12, 6))
+    assert rs.Precond(ctx, A, "ilu0", sweep="segments").sweep_kind() == ("segments", None)
+    B = rs.Mat.bsr(ctx, synth.black_oil_bsr3(g, 61))
+    assert rs.Precond(ctx, B, "bilu0").sweep_kind() == ("wavefront", (20, 12, 6))
+    n = 300
+    D = sp.random(n, n, density=0.02, random_state=7, format="csr") * -1.0
+    D = (D + sp.diags(np.abs(D).sum(axis=1).A1 + 1.0)).tocsr()
+    D.sort_indices()
+    d = dict(n=n, rowptr=D.indptr.astype(np.int32), col=D.indices.astype(np.int32), val=D.data.copy())
+    assert rs.Precond(ctx, rs.Mat.csr(ctx, d), "ilu0").sweep_kind() == ("segments", None)
+
+
 def test_non_grid_patterns_take_the_segment_sweeps(rs, ctx, orc):
     """A pattern that is not a 7-point grid (a random one; a 1-D chain; a
     27-point-like extra diagonal) keeps the segment sweeps."""
