@@ -259,9 +259,11 @@ int rs_mat_amxpby(double a, const rs_mat *A, const rs_vec *x, double b, rs_vec *
 /* ---- preconditioners (Sec. 3 Fig. 29, Sec. 4) -------------------------- */
 
 /* Builds M for A.  RS_PC_ILU0 needs a CSR matrix; RS_PC_BILU0 a BSR matrix;
- * RS_PC_AMG needs a CSR matrix (setup of the hierarchy on the host, the
- * V-cycle on the GPU; RS_ERR_INVALID_ARG when coarsening stalls above 4096
- * rows or an option is out of range);
+ * RS_PC_AMG needs a CSR matrix (setup of the hierarchy and the V-cycle on
+ * the GPU: classical strength, PMIS coarsening with SplitMix64 weights keyed
+ * by level and row, direct interpolation, Galerkin products; RS_ERR_INVALID_ARG
+ * when coarsening stalls above 4096 rows, a Galerkin row has more than 2048
+ * candidate terms, or an option is out of range);
  * RS_PC_RAS either (on a BSR matrix the subdomains hold block rows and the
  * local solver is block ILU(k)), set by the opts->ras_* fields and
  * opts->ilu_level (RS_ERR_INVALID_ARG when out of range);

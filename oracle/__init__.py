@@ -118,7 +118,11 @@ def _declare(L):
     L.or_ras_export.argtypes = [C.c_void_p, _i32p, _i32p, _i32p, _f64p]
     L.free.argtypes = [C.c_void_p]
     L.or_amg_setup.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, C.c_int32, C.c_int32, C.c_int32,
-                               C.c_int32, C.POINTER(C.c_void_p)]
+                               C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]
+    L.or_splitmix64.argtypes = [C.c_uint64]
+    L.or_splitmix64.restype = C.c_uint64
+    L.or_pmis.argtypes = [C.c_int32, _i32p, _i32p, _i32p, _i32p, _f64p, C.c_char_p]
+    L.or_pmis.restype = C.c_int32
     L.or_hgs_sweep.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_int32, C.c_int32, _f64p]
     L.or_amg_free.argtypes = [C.c_void_p]
     L.or_amg_apply.argtypes = [C.c_void_p, _f64p, _f64p]
@@ -402,20 +406,48 @@ def hgs_sweep(A: Mat, b, x, chunk=32, backward=False):
     return st, out
 
 
+def splitmix64(k):
+    """The k-th output of SplitMix64 from state 0 (the PMIS weights' generator)."""
+    return int(lib().or_splitmix64(k))
+
+
+def pmis(n, sptr, scol, w):
+    """PMIS C/F splitting (Sec. 4.2's PMIS) of the strength graph S (sptr,
+    scol: the points each point strongly depends on) with weights w: returns
+    (states, rounds), states 1 for C and 2 for F."""
+    sptr, scol, w = np.ascontiguousarray(sptr, np.int32), np.ascontiguousarray(scol, np.int32), _f64(w)
+    # S^T by counting, rows in order
+    tptr = np.zeros(n + 1, np.int32)
+    np.add.at(tptr, scol + 1, 1)
+    tptr = np.cumsum(tptr).astype(np.int32)
+    tcol = np.empty(scol.size, np.int32)
+    fill = tptr[:-1].copy()
+    for i in range(n):
+        for q in range(sptr[i], sptr[i + 1]):
+            tcol[fill[scol[q]]] = i
+            fill[scol[q]] += 1
+    st = C.create_string_buffer(max(n, 1))
+    rounds = lib().or_pmis(n, _p(sptr, C.c_int32), _p(scol, C.c_int32), _p(tptr, C.c_int32), _p(tcol, C.c_int32),
+                           _p(w, C.c_double), st)
+    return np.frombuffer(st.raw[:n], np.int8).astype(np.int32), rounds
+
+
 class Amg:
     """Algebraic multigrid V-cycle (Algs. 3-4): classical strength (theta),
-    Ruge-Stueben first-pass coarsening, direct interpolation, Galerkin coarse
-    matrices, nu smoothing sweeps before and after (smoother 0: l1-Jacobi;
-    1: hybrid Gauss-Seidel over 32-row chunks, forward before and backward
-    after the coarse correction), dense coarsest solve."""
+    coarsening by PMIS (default; weights from SplitMix64 keyed by level and
+    point) or the Ruge-Stueben first pass (coarsen="rs"), direct
+    interpolation, Galerkin coarse matrices, nu smoothing sweeps before and
+    after (smoother 0: l1-Jacobi; 1: hybrid Gauss-Seidel over 32-row chunks,
+    forward before and backward after the coarse correction), dense coarsest
+    solve."""
 
-    def __init__(self, A: Mat, theta=0.5, max_levels=16, max_coarse=256, nu=2, smoother=0):
+    def __init__(self, A: Mat, theta=0.5, max_levels=16, max_coarse=256, nu=2, smoother=0, coarsen="pmis"):
         assert A.bs == 1
         self.A = A
         h = C.c_void_p()
         self.status = lib().or_amg_setup(A.nrows, _p(A.ptr, C.c_int32), _p(A.col, C.c_int32),
                                          _p(A.val, C.c_double), theta, max_levels, max_coarse, nu, smoother,
-                                         C.byref(h))
+                                         {"rs": 0, "pmis": 1}[coarsen], C.byref(h))
         self.h = h
 
     def apply(self, r):

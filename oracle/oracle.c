@@ -965,9 +965,77 @@ static or_hent heap_pop(or_hent *h, int64_t *len)
     return top;
 }
 
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014), used counter-based: the
+ * k-th output of the generator started from state 0, i.e. its finaliser
+ * applied to (k + 1) times the golden-ratio increment. */
+uint64_t or_splitmix64(uint64_t k)
+{
+    uint64_t z = (k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* the PMIS weight of point i on level l: uniform in [0, 1), 53 bits */
+static double pmis_weight(int32_t level, int32_t i)
+{
+    return (double)(or_splitmix64(((uint64_t)(uint32_t)level << 32) | (uint32_t)i) >> 11) * 0x1.0p-53;
+}
+
+/* PMIS coarsening (De Sterck, Yang and Heys, SIAM J. Matrix Anal. Appl.
+ * 2006), one of the coarsenings Sec. 4.2 names.  S (sp, sc): the points each
+ * point strongly depends on; ST (tp, tc): those it strongly influences.  The
+ * measure of i is lambda_i = |S_i^T| + w_i.  Points that influence no point
+ * are F from the start.  Then, in rounds until no point is undecided: every
+ * undecided point whose measure exceeds that of every undecided point of
+ * S_i and S_i^T (the states at the start of the round) becomes C; then every
+ * undecided point that strongly depends on a C point becomes F.  st[i]:
+ * 1 C, 2 F.  Returns the number of rounds. */
+int32_t or_pmis(int32_t n, const int32_t *sp, const int32_t *sc, const int32_t *tp, const int32_t *tc,
+                const double *w, char *st)
+{
+    double *lam = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    char *old = (char *)malloc((size_t)(n > 0 ? n : 1));
+    int32_t und = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        lam[i] = (double)(tp[i + 1] - tp[i]) + w[i];
+        st[i] = tp[i + 1] == tp[i] ? 2 : 0;
+        und += st[i] == 0;
+    }
+    int32_t rounds = 0;
+    while (und > 0) {
+        ++rounds;
+        memcpy(old, st, (size_t)n);
+        for (int32_t i = 0; i < n; ++i) {
+            if (old[i] != 0) continue;
+            int top = 1;
+            for (int32_t q = sp[i]; q < sp[i + 1] && top; ++q)
+                if (old[sc[q]] == 0 && !(lam[i] > lam[sc[q]])) top = 0;
+            for (int32_t q = tp[i]; q < tp[i + 1] && top; ++q)
+                if (old[tc[q]] == 0 && !(lam[i] > lam[tc[q]])) top = 0;
+            if (top) st[i] = 1;
+        }
+        for (int32_t j = 0; j < n; ++j) {
+            if (st[j] != 0) continue;
+            for (int32_t q = sp[j]; q < sp[j + 1]; ++q)
+                if (st[sc[q]] == 1) {
+                    st[j] = 2;
+                    break;
+                }
+        }
+        und = 0;
+        for (int32_t i = 0; i < n; ++i) und += st[i] == 0;
+    }
+    free(lam);
+    free(old);
+    return rounds;
+}
+
 /* one level of Alg. 3: P (n x nc) from A and the coarse index of every
- * point (-1 for F, into cidx_out[n]); returns nc */
-static int32_t amg_coarsen(const or_csr *A, double theta, or_csr *P, int32_t *cidx_out)
+ * point (-1 for F, into cidx_out[n]); coarsen 0: the Ruge-Stueben first
+ * pass, 1: PMIS with the weights of this level; returns nc */
+static int32_t amg_coarsen(const or_csr *A, double theta, int32_t coarsen, int32_t level, or_csr *P,
+                           int32_t *cidx_out)
 {
     const int32_t n = A->n;
     /* 1. strength */
@@ -988,41 +1056,49 @@ static int32_t amg_coarsen(const or_csr *A, double theta, or_csr *P, int32_t *ci
     or_csr S = {n, n, sp, sc, NULL}, ST;
     S.val = (double *)calloc((size_t)(sp[n] > 0 ? sp[n] : 1), sizeof(double));
     csr_transpose(&S, &ST);
-    /* 2. Ruge-Stueben first pass */
+    /* 2. the C/F splitting */
     enum { U = 0, CPT = 1, FPT = 2 };
     int32_t *lam = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     char *st = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
-    int64_t hcap = n > 0 ? 2 * (int64_t)n : 2, hlen = 0;
-    or_hent *heap = (or_hent *)malloc(sizeof(or_hent) * (size_t)hcap);
-    for (int32_t i = 0; i < n; ++i) {
-        lam[i] = ST.ptr[i + 1] - ST.ptr[i];
-        if (lam[i] == 0 && sp[i + 1] == sp[i]) st[i] = FPT;
-        else heap_push(&heap, &hlen, &hcap, (or_hent){lam[i], i});
-    }
-    while (hlen > 0) {
-        const or_hent e = heap_pop(heap, &hlen);
-        const int32_t i = e.idx;
-        if (st[i] != U || e.lam != lam[i]) continue;
-        st[i] = CPT;
-        for (int32_t q = ST.ptr[i]; q < ST.ptr[i + 1]; ++q) {
-            const int32_t j = ST.col[q];
-            if (st[j] != U) continue;
-            st[j] = FPT;
-            for (int32_t r = sp[j]; r < sp[j + 1]; ++r) {
+    if (coarsen == 1) {
+        double *w = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        for (int32_t i = 0; i < n; ++i) w[i] = pmis_weight(level, i);
+        or_pmis(n, sp, sc, ST.ptr, ST.col, w, st);
+        free(w);
+    } else {
+        int64_t hcap = n > 0 ? 2 * (int64_t)n : 2, hlen = 0;
+        or_hent *heap = (or_hent *)malloc(sizeof(or_hent) * (size_t)hcap);
+        for (int32_t i = 0; i < n; ++i) {
+            lam[i] = ST.ptr[i + 1] - ST.ptr[i];
+            if (lam[i] == 0 && sp[i + 1] == sp[i]) st[i] = FPT;
+            else heap_push(&heap, &hlen, &hcap, (or_hent){lam[i], i});
+        }
+        while (hlen > 0) {
+            const or_hent e = heap_pop(heap, &hlen);
+            const int32_t i = e.idx;
+            if (st[i] != U || e.lam != lam[i]) continue;
+            st[i] = CPT;
+            for (int32_t q = ST.ptr[i]; q < ST.ptr[i + 1]; ++q) {
+                const int32_t j = ST.col[q];
+                if (st[j] != U) continue;
+                st[j] = FPT;
+                for (int32_t r = sp[j]; r < sp[j + 1]; ++r) {
+                    const int32_t k = sc[r];
+                    if (st[k] == U) {
+                        lam[k] += 1;
+                        heap_push(&heap, &hlen, &hcap, (or_hent){lam[k], k});
+                    }
+                }
+            }
+            for (int32_t r = sp[i]; r < sp[i + 1]; ++r) {
                 const int32_t k = sc[r];
                 if (st[k] == U) {
-                    lam[k] += 1;
+                    lam[k] -= 1;
                     heap_push(&heap, &hlen, &hcap, (or_hent){lam[k], k});
                 }
             }
         }
-        for (int32_t r = sp[i]; r < sp[i + 1]; ++r) {
-            const int32_t k = sc[r];
-            if (st[k] == U) {
-                lam[k] -= 1;
-                heap_push(&heap, &hlen, &hcap, (or_hent){lam[k], k});
-            }
-        }
+        free(heap);
     }
     /* coarse numbering */
     int32_t *cidx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
@@ -1079,7 +1155,6 @@ static int32_t amg_coarsen(const or_csr *A, double theta, or_csr *P, int32_t *ci
     memcpy(cidx_out, cidx, sizeof(int32_t) * (size_t)n);
     free(lam);
     free(st);
-    free(heap);
     free(cidx);
     free(S.val);
     csr_free(&ST);
@@ -1174,11 +1249,12 @@ int or_hgs_sweep(int32_t n, const int32_t *ptr, const int32_t *col, const double
 }
 
 int or_amg_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double *val, double theta,
-                 int32_t max_levels, int32_t max_coarse, int32_t nu, int32_t smoother, or_amg **out)
+                 int32_t max_levels, int32_t max_coarse, int32_t nu, int32_t smoother, int32_t coarsen,
+                 or_amg **out)
 {
     *out = NULL;
     if (n < 1 || max_levels < 1 || max_levels > OR_AMG_MAXLEV || max_coarse < 1 || nu < 1 || !(theta >= 0.0) ||
-        smoother < 0 || smoother > 1)
+        smoother < 0 || smoother > 1 || coarsen < 0 || coarsen > 1)
         return OR_INVALID;
     or_amg *M = (or_amg *)calloc(1, sizeof(or_amg));
     M->nu = nu;
@@ -1213,7 +1289,7 @@ int or_amg_setup(int32_t n, const int32_t *ptr, const int32_t *col, const double
         if (A->n <= max_coarse || l + 1 >= max_levels) break;
         or_csr P;
         M->cidx[l] = (int32_t *)malloc(sizeof(int32_t) * (size_t)A->n);
-        const int32_t nc = amg_coarsen(A, theta, &P, M->cidx[l]);
+        const int32_t nc = amg_coarsen(A, theta, coarsen, l, &P, M->cidx[l]);
         if (nc == 0 || nc >= A->n) {
             csr_free(&P);
             break;

@@ -1,25 +1,12 @@
 // Algebraic multigrid preconditioner (Sec. 4.2: Alg. 3 setup, Alg. 4
 // V-cycle, Eq. 4).
 //
-// Setup (once per matrix, on the host, like the setup phase of the AMG
-// package the paper calls), level by level in Alg. 3's order:
-//   1. strength: j strongly influences i when j != i and
-//      -a_ij >= theta max_{k != i} (-a_ik) (theta = 0.5 by default, Fig. 34);
-//   2. coarse points: the Ruge-Stueben first pass.  The measure of a point
-//      is the number of undecided points it strongly influences plus twice
-//      the number of F points it strongly influences; the undecided point
-//      of largest measure (lowest index on ties) becomes C and the
-//      undecided points it strongly influences become F.  Points with no
-//      strong connection in either direction are F from the start;
-//   3. direct interpolation: C points inject; an F point i interpolates from
-//      its strong C neighbours k with w_ik = -alpha a_ik / a_ii (a_ik < 0) or
-//      -beta a_ik / a_ii (a_ik > 0), alpha (beta) = the row's sum of negative
-//      (positive) off-diagonal entries over that of its strong C neighbours;
-//      with no positive strong C coupling the positive couplings join a_ii;
-//   4. R = P^T;  5. A_{l+1} = R A_l P (Eq. 4);
-//   6. smoother: l1-Jacobi, x <- x + (b - A x) / d, d_i = sum_j |a_ij|.
-// Levels stop at max_coarse rows, max_levels, or when coarsening stalls;
-// the coarsest matrix is inverted densely.
+// Setup (once per matrix, on the GPU: rs_amg_setup.cu), level by level in
+// Alg. 3's order: classical strength (theta = 0.5 by default, Fig. 34), PMIS
+// coarsening, direct interpolation, R = P^T, A_{l+1} = R A_l P (Eq. 4), the
+// l1-Jacobi smoother's diagonal d_i = sum_j |a_ij|.  Levels stop at
+// max_coarse rows, max_levels, or when coarsening stalls; the coarsest
+// matrix is inverted densely.
 //
 // Apply (on the GPU): one V-cycle from x = 0 (Alg. 4): nu sweeps, residual,
 // restriction, the next level, prolongation and correction, nu sweeps;
@@ -29,216 +16,9 @@
 // buffer.
 #include <algorithm>
 #include <cmath>
-#include <queue>
 #include <vector>
 
 #include "rs_internal.cuh"
-
-namespace {
-
-struct HCsr {
-    int n = 0, m = 0;
-    std::vector<int> ptr, col;
-    std::vector<double> val;
-};
-
-// strong influences of every row: S[i] = { j : j strongly influences i }
-void strength(const HCsr &A, double theta, std::vector<int> &sp, std::vector<int> &sc)
-{
-    sp.assign(A.n + 1, 0);
-    sc.clear();
-    for (int i = 0; i < A.n; ++i) {
-        double mx = 0.0;
-        for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
-            if (A.col[p] != i) mx = std::max(mx, -A.val[p]);
-        if (mx > 0.0)
-            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
-                if (A.col[p] != i && -A.val[p] >= theta * mx) sc.push_back(A.col[p]);
-        sp[i + 1] = (int)sc.size();
-    }
-}
-
-// coarse index of every point (-1 = F) by the Ruge-Stueben first pass
-int first_pass(int n, const std::vector<int> &sp, const std::vector<int> &sc, std::vector<int> &cidx)
-{
-    // transpose of S: the points each point strongly influences
-    std::vector<int> tp(n + 1, 0), tc(sc.size());
-    for (int c : sc) ++tp[c + 1];
-    for (int i = 0; i < n; ++i) tp[i + 1] += tp[i];
-    {
-        std::vector<int> f(tp.begin(), tp.end() - 1);
-        for (int i = 0; i < n; ++i)
-            for (int q = sp[i]; q < sp[i + 1]; ++q) tc[f[sc[q]]++] = i;
-    }
-    enum : char { UND = 0, CP = 1, FP = 2 };
-    std::vector<char> st(n, UND);
-    std::vector<int> lam(n);
-    // max-heap on (measure, -index); stale entries are skipped when popped
-    std::priority_queue<std::pair<int, int>> heap;
-    for (int i = 0; i < n; ++i) {
-        lam[i] = tp[i + 1] - tp[i];
-        if (lam[i] == 0 && sp[i + 1] == sp[i]) st[i] = FP;
-        else heap.push({lam[i], -i});
-    }
-    while (!heap.empty()) {
-        const auto e = heap.top();
-        heap.pop();
-        const int i = -e.second;
-        if (st[i] != UND || e.first != lam[i]) continue;
-        st[i] = CP;
-        for (int q = tp[i]; q < tp[i + 1]; ++q) {
-            const int j = tc[q];
-            if (st[j] != UND) continue;
-            st[j] = FP;
-            for (int r = sp[j]; r < sp[j + 1]; ++r) {
-                const int k = sc[r];
-                if (st[k] == UND) heap.push({++lam[k], -k});
-            }
-        }
-        for (int r = sp[i]; r < sp[i + 1]; ++r) {
-            const int k = sc[r];
-            if (st[k] == UND) heap.push({--lam[k], -k});
-        }
-    }
-    cidx.assign(n, -1);
-    int nc = 0;
-    for (int i = 0; i < n; ++i)
-        if (st[i] == CP) cidx[i] = nc++;
-    return nc;
-}
-
-void direct_interpolation(const HCsr &A, const std::vector<int> &sp, const std::vector<int> &sc,
-                          const std::vector<int> &cidx, int nc, HCsr &P)
-{
-    P.n = A.n;
-    P.m = nc;
-    P.ptr.assign(1, 0);
-    P.col.clear();
-    P.val.clear();
-    std::vector<char> strongc(A.n, 0);
-    for (int i = 0; i < A.n; ++i) {
-        if (cidx[i] >= 0) {
-            P.col.push_back(cidx[i]);
-            P.val.push_back(1.0);
-        } else {
-            for (int r = sp[i]; r < sp[i + 1]; ++r)
-                if (cidx[sc[r]] >= 0) strongc[sc[r]] = 1;
-            double aii = 0.0, neg = 0.0, pos = 0.0, negc = 0.0, posc = 0.0;
-            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
-                const int j = A.col[p];
-                const double v = A.val[p];
-                if (j == i) { aii = v; continue; }
-                (v < 0.0 ? neg : pos) += v;
-                if (strongc[j]) (v < 0.0 ? negc : posc) += v;
-            }
-            double diag = aii, beta = 0.0;
-            if (posc == 0.0) diag += pos;
-            else beta = pos / posc;
-            const double alpha = negc != 0.0 ? neg / negc : 0.0;
-            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
-                const int k = A.col[p];
-                if (k == i || !strongc[k]) continue;
-                P.col.push_back(cidx[k]);
-                P.val.push_back(-(A.val[p] < 0.0 ? alpha : beta) * A.val[p] / diag);
-            }
-            for (int r = sp[i]; r < sp[i + 1]; ++r) strongc[sc[r]] = 0;
-        }
-        P.ptr.push_back((int)P.col.size());
-    }
-}
-
-void transpose(const HCsr &A, HCsr &T)
-{
-    T.n = A.m;
-    T.m = A.n;
-    T.ptr.assign(A.m + 1, 0);
-    T.col.resize(A.col.size());
-    T.val.resize(A.val.size());
-    for (int c : A.col) ++T.ptr[c + 1];
-    for (int c = 0; c < A.m; ++c) T.ptr[c + 1] += T.ptr[c];
-    std::vector<int> f(T.ptr.begin(), T.ptr.end() - 1);
-    for (int i = 0; i < A.n; ++i)
-        for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
-            const int q = f[A.col[p]]++;
-            T.col[q] = i;
-            T.val[q] = A.val[p];
-        }
-}
-
-// C = A B by rows (Gustavson), columns sorted
-void multiply(const HCsr &A, const HCsr &B, HCsr &C)
-{
-    C.n = A.n;
-    C.m = B.m;
-    C.ptr.assign(1, 0);
-    C.col.clear();
-    C.val.clear();
-    std::vector<int> mark(B.m, -1), cols;
-    std::vector<double> acc(B.m, 0.0);
-    for (int i = 0; i < A.n; ++i) {
-        cols.clear();
-        for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
-            const int j = A.col[p];
-            const double a = A.val[p];
-            for (int q = B.ptr[j]; q < B.ptr[j + 1]; ++q) {
-                const int c = B.col[q];
-                if (mark[c] != i) {
-                    mark[c] = i;
-                    acc[c] = 0.0;
-                    cols.push_back(c);
-                }
-                acc[c] += a * B.val[q];
-            }
-        }
-        std::sort(cols.begin(), cols.end());
-        for (int c : cols) {
-            C.col.push_back(c);
-            C.val.push_back(acc[c]);
-        }
-        C.ptr.push_back((int)C.col.size());
-    }
-}
-
-// dense inverse by Gauss-Jordan elimination with partial pivoting
-bool invert(int n, std::vector<double> a, std::vector<double> &inv)
-{
-    inv.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
-    for (int c = 0; c < n; ++c) {
-        int p = c;
-        for (int r = c + 1; r < n; ++r)
-            if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)p * n + c])) p = r;
-        const double piv = a[(size_t)p * n + c];
-        if (!(piv != 0.0) || !std::isfinite(piv)) return false;
-        if (p != c)
-            for (int j = 0; j < n; ++j) {
-                std::swap(a[(size_t)c * n + j], a[(size_t)p * n + j]);
-                std::swap(inv[(size_t)c * n + j], inv[(size_t)p * n + j]);
-            }
-        for (int j = 0; j < n; ++j) {
-            a[(size_t)c * n + j] /= piv;
-            inv[(size_t)c * n + j] /= piv;
-        }
-        for (int r = 0; r < n; ++r) {
-            if (r == c) continue;
-            const double f = a[(size_t)r * n + c];
-            if (f == 0.0) continue;
-            for (int j = 0; j < n; ++j) {
-                a[(size_t)r * n + j] -= f * a[(size_t)c * n + j];
-                inv[(size_t)r * n + j] -= f * inv[(size_t)c * n + j];
-            }
-        }
-    }
-    return true;
-}
-
-}  // namespace
-
-// the host hierarchy, kept for export
-struct AmgHost {
-    std::vector<HCsr> A, P;
-    std::vector<std::vector<int>> cidx;
-};
 
 // The smoother multiplies by dinv = 1/d, formed once at setup: a divide on
 // every sweep would cost this GPU's FP64 pipe about ten times as much.
@@ -379,7 +159,7 @@ void rs_amg_destroy(AmgData *M)
 {
     if (!M) return;
     rs_ctx *ctx = M->ctx;
-    for (int l = 0; l < M->nlev; ++l) {
+    for (int l = 0; l < RS_AMG_MAXLEV; ++l) {           // also the levels of a setup that failed
         if (l > 0 || M->own0) rs_mat_destroy(&M->A[l]);   // level 0 may be the caller's matrix
         rs_mat_destroy(&M->P[l]);
         rs_mat_destroy(&M->R[l]);
@@ -390,15 +170,14 @@ void rs_amg_destroy(AmgData *M)
         rs_free(ctx, M->y[l]);
     }
     rs_free(ctx, M->cinv);
+    for (int l = 0; l < RS_AMG_MAXLEV; ++l) rs_free(ctx, M->cidx[l]);
     for (const AmgGraph &g : M->graphs) cudaGraphExecDestroy(g.exec);
     if (M->capture) cudaStreamDestroy(M->capture);
-    delete M->host;
     delete M;
 }
 
-int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::vector<int> &hcol,
-                  const double *d_val, const rs_mat *A0, double theta, int max_levels, int max_coarse, int nu,
-                  int smoother, AmgData **out)
+int rs_amg_create(rs_ctx *ctx, int n, const int *d_ptr, const int *d_col, const double *d_val, const rs_mat *A0,
+                  double theta, int max_levels, int max_coarse, int nu, int smoother, AmgData **out)
 {
     *out = nullptr;
     if (n < 1 || max_levels < 1 || max_levels > RS_AMG_MAXLEV || max_coarse < 1 || nu < 1 || !(theta >= 0.0) ||
@@ -408,105 +187,23 @@ int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::v
     M->ctx = ctx;
     M->nu = nu;
     M->smoother = smoother;
-    M->host = new AmgHost();
-    AmgHost &H = *M->host;
-    H.A.emplace_back();
-    HCsr &F = H.A[0];
-    F.n = F.m = n;
-    F.ptr = hptr;
-    F.col = hcol;
-    F.val.resize(hcol.size());
-    if (!hcol.empty()) {
-        RS_CUDA_TRY(cudaMemcpyAsync(F.val.data(), d_val, sizeof(double) * hcol.size(), cudaMemcpyDeviceToHost,
-                                    ctx->stream));
-        RS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    }
-    // the hierarchy (Alg. 3)
-    std::vector<int> sp, sc;
-    for (int l = 0;; ++l) {
-        if (H.A[l].n <= max_coarse || l + 1 >= max_levels) break;
-        strength(H.A[l], theta, sp, sc);
-        std::vector<int> cidx;
-        const int nc = first_pass(H.A[l].n, sp, sc, cidx);
-        if (nc == 0 || nc >= H.A[l].n) break;
-        HCsr P, R, AP, Ac;
-        direct_interpolation(H.A[l], sp, sc, cidx, nc, P);
-        transpose(P, R);
-        multiply(H.A[l], P, AP);
-        multiply(R, AP, Ac);
-        H.P.push_back(std::move(P));
-        H.cidx.push_back(std::move(cidx));
-        H.A.push_back(std::move(Ac));
-    }
-    M->nlev = (int)H.A.size();
-    if (H.A.back().n > RS_AMG_MAX_DENSE) {     // coarsening stalled: no small coarsest level
-        rs_amg_destroy(M);
-        return RS_ERR_INVALID_ARG;
-    }
-    if (smoother == 1) {   // Gauss-Seidel divides by a_ii on every smoothed level
-        for (int l = 0; l + 1 < M->nlev; ++l) {
-            const HCsr &A = H.A[l];
-            for (int i = 0; i < A.n; ++i) {
-                double dg = 0.0;
-                for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
-                    if (A.col[p] == i) dg = A.val[p];
-                if (dg == 0.0) {
-                    rs_amg_destroy(M);
-                    return RS_ERR_ZERO_PIVOT;
-                }
-            }
-        }
-    }
-    std::vector<double> inv;
-    {
-        const HCsr &C = H.A.back();
-        std::vector<double> dense((size_t)C.n * C.n, 0.0);
-        for (int i = 0; i < C.n; ++i)
-            for (int p = C.ptr[i]; p < C.ptr[i + 1]; ++p) dense[(size_t)i * C.n + C.col[p]] = C.val[p];
-        if (!invert(C.n, std::move(dense), inv)) {
-            rs_amg_destroy(M);
-            return RS_ERR_ZERO_PIVOT;
-        }
-    }
-    // device objects
     int st = RS_OK;
-    for (int l = 0; l < M->nlev && !st; ++l) {
-        const HCsr &A = H.A[l];
-        if (l == 0 && A0) {
-            M->A[0] = const_cast<rs_mat *>(A0);
-        } else {
-            M->own0 = M->own0 || l == 0;
-            st = rs_mat_create_rect(ctx, A.n, A.n, A.ptr.data(), A.col.data(), A.val.data(), &M->A[l]);
-            if (st) break;
-        }
-        if (l + 1 < M->nlev) {
-            HCsr R;
-            transpose(H.P[l], R);
-            st = rs_mat_create_rect(ctx, H.P[l].n, H.P[l].m, H.P[l].ptr.data(), H.P[l].col.data(),
-                                    H.P[l].val.data(), &M->P[l]);
-            if (!st) st = rs_mat_create_rect(ctx, R.n, R.m, R.ptr.data(), R.col.data(), R.val.data(), &M->R[l]);
-            if (st) break;
-        }
-        std::vector<double> d(A.n);      // 1 / d_i, d_i = sum_j |a_ij|
-        for (int i = 0; i < A.n; ++i) {
-            double s = 0.0;
-            for (int p = A.ptr[i]; p < A.ptr[i + 1]; ++p) s += std::fabs(A.val[p]);
-            d[i] = 1.0 / s;
-        }
-        st = rs_alloc(ctx, (void **)&M->d[l], sizeof(double) * A.n);
-        if (!st) st = rs_alloc(ctx, (void **)&M->b[l], sizeof(double) * A.n);
-        if (!st) st = rs_alloc(ctx, (void **)&M->x[l], sizeof(double) * A.n);
-        if (!st) st = rs_alloc(ctx, (void **)&M->t[l], sizeof(double) * A.n);
-        if (!st && l > 0) st = rs_alloc(ctx, (void **)&M->y[l], sizeof(double) * A.n);
-        if (!st && cudaMemcpyAsync(M->d[l], d.data(), sizeof(double) * A.n, cudaMemcpyHostToDevice, ctx->stream) !=
-                       cudaSuccess)
-            st = RS_ERR_CUDA;
+    if (A0) {
+        M->A[0] = const_cast<rs_mat *>(A0);
+    } else {
+        M->own0 = true;
+        st = rs_mat_create_rect_dev(ctx, n, -1, d_ptr, d_col, d_val, &M->A[0]);
     }
-    const int nc = H.A.back().n;
-    if (!st) st = rs_alloc(ctx, (void **)&M->cinv, sizeof(double) * (size_t)nc * nc);
-    if (!st && cudaMemcpyAsync(M->cinv, inv.data(), sizeof(double) * (size_t)nc * nc, cudaMemcpyHostToDevice,
-                               ctx->stream) != cudaSuccess)
-        st = RS_ERR_CUDA;
+    // the hierarchy (Alg. 3), smoother diagonals and the coarsest inverse
+    if (!st) st = rs_amg_setup_device(M, theta, max_levels, max_coarse);
+    // work vectors
+    for (int l = 0; l < M->nlev && !st; ++l) {
+        const int nl = M->A[l]->n;
+        st = rs_alloc(ctx, (void **)&M->b[l], sizeof(double) * nl);
+        if (!st) st = rs_alloc(ctx, (void **)&M->x[l], sizeof(double) * nl);
+        if (!st) st = rs_alloc(ctx, (void **)&M->t[l], sizeof(double) * nl);
+        if (!st && l > 0) st = rs_alloc(ctx, (void **)&M->y[l], sizeof(double) * nl);
+    }
     if (!st && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = RS_ERR_CUDA;
     if (st) {
         rs_amg_destroy(M);
@@ -649,10 +346,9 @@ int rs_amg_apply(AmgData *M, const double *r, double *z, const int *skip)
 int rs_amg_level_sizes(const AmgData *M, int l, int32_t *n, int64_t *nnz_a, int64_t *nnz_p)
 {
     if (l < 0 || l >= M->nlev) return RS_ERR_INVALID_ARG;
-    const AmgHost &H = *M->host;
-    *n = H.A[l].n;
-    *nnz_a = (int64_t)H.A[l].col.size();
-    *nnz_p = l + 1 < M->nlev ? (int64_t)H.P[l].col.size() : 0;
+    *n = M->A[l]->n;
+    *nnz_a = M->A[l]->nnzb;
+    *nnz_p = l + 1 < M->nlev ? M->P[l]->nnzb : 0;
     return RS_OK;
 }
 
@@ -660,17 +356,24 @@ int rs_amg_get_level(const AmgData *M, int l, int32_t *aptr, int32_t *acol, doub
                      int32_t *pcol, double *pval, int32_t *cidx)
 {
     if (l < 0 || l >= M->nlev) return RS_ERR_INVALID_ARG;
-    const AmgHost &H = *M->host;
-    const HCsr &A = H.A[l];
-    if (aptr) std::copy(A.ptr.begin(), A.ptr.end(), aptr);
-    if (acol) std::copy(A.col.begin(), A.col.end(), acol);
-    if (aval) std::copy(A.val.begin(), A.val.end(), aval);
+    rs_ctx *ctx = M->ctx;
+    const cudaStream_t s = ctx->stream;
+    auto get = [&](void *dst, const void *src, size_t bytes) -> int {
+        if (!dst || !bytes) return RS_OK;
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+    };
+    const rs_mat *A = M->A[l];
+    RS_TRY(get(aptr, A->ptr, sizeof(int) * (A->n + 1)));
+    RS_TRY(get(acol, A->col, sizeof(int) * A->nnzb));
+    RS_TRY(get(aval, A->val, sizeof(double) * A->nnzb));
     if (l + 1 < M->nlev) {
-        const HCsr &P = H.P[l];
-        if (pptr) std::copy(P.ptr.begin(), P.ptr.end(), pptr);
-        if (pcol) std::copy(P.col.begin(), P.col.end(), pcol);
-        if (pval) std::copy(P.val.begin(), P.val.end(), pval);
-        if (cidx) std::copy(H.cidx[l].begin(), H.cidx[l].end(), cidx);
+        const rs_mat *P = M->P[l];
+        RS_TRY(get(pptr, P->ptr, sizeof(int) * (P->n + 1)));
+        RS_TRY(get(pcol, P->col, sizeof(int) * P->nnzb));
+        RS_TRY(get(pval, P->val, sizeof(double) * P->nnzb));
+        RS_TRY(get(cidx, M->cidx[l], sizeof(int) * A->n));
     }
+    RS_CUDA_TRY(cudaStreamSynchronize(s));
     return RS_OK;
 }
+

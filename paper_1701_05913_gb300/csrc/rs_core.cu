@@ -856,6 +856,13 @@ int rs_mat_create_rect(rs_ctx *ctx, int nrows, int ncols, const int32_t *ptr, co
     return mat_create(ctx, nrows, 1, ptr, col, val, RS_MEM_HOST, A, ncols);
 }
 
+// from device arrays (copied); ncols < 0: square, every diagonal entry present
+int rs_mat_create_rect_dev(rs_ctx *ctx, int nrows, int ncols, const int32_t *ptr, const int32_t *col,
+                           const double *val, rs_mat **A)
+{
+    return mat_create(ctx, nrows, 1, ptr, col, val, RS_MEM_DEVICE, A, ncols);
+}
+
 extern "C" int rs_mat_create_bsr(rs_ctx *ctx, int32_t nb, int32_t bs, const int32_t *browptr,
                                  const int32_t *bcol, const double *bval, int mem, rs_mat **A)
 {

@@ -223,7 +223,6 @@ struct RasData {
 // the coarsest matrix.
 #define RS_AMG_MAXLEV 16
 #define RS_AMG_MAX_DENSE 4096
-struct AmgHost;
 // one captured V-cycle: its input, output and skip flag addresses, the
 // executable graph and the number of kernels it launches
 struct AmgGraph {
@@ -244,7 +243,7 @@ struct AmgData {
     double *d[RS_AMG_MAXLEV] = {}, *b[RS_AMG_MAXLEV] = {}, *x[RS_AMG_MAXLEV] = {}, *t[RS_AMG_MAXLEV] = {};
     double *y[RS_AMG_MAXLEV] = {};   // second smoothing buffer (level 0 uses x[0])
     double *cinv = nullptr;
-    AmgHost *host = nullptr;     // the hierarchy on the host (export)
+    int *cidx[RS_AMG_MAXLEV] = {};   // coarse index of every point of level l (-1: F), device
     std::vector<AmgGraph> graphs;
     cudaStream_t capture = nullptr;   // private stream for stream capture
     long long applies = 0;
@@ -301,6 +300,8 @@ int rs_alloc(rs_ctx *ctx, void **p, size_t bytes);
 void rs_free(rs_ctx *ctx, void *p);
 
 // an nrows x ncols CSR operator from host arrays (no diagonal required)
+int rs_mat_create_rect_dev(rs_ctx *ctx, int nrows, int ncols, const int32_t *ptr, const int32_t *col,
+                           const double *val, rs_mat **A);
 int rs_mat_create_rect(rs_ctx *ctx, int nrows, int ncols, const int32_t *ptr, const int32_t *col,
                        const double *val, rs_mat **A);
 
@@ -347,9 +348,10 @@ int rs_ras_apply(RasData *R, const double *r, double *z, const int *skip);
 void rs_ras_destroy(RasData *R);
 // A0: the level-0 matrix when the caller has one as an rs_mat (else built
 // from the host pattern and the device values d_val)
-int rs_amg_create(rs_ctx *ctx, int n, const std::vector<int> &hptr, const std::vector<int> &hcol,
-                  const double *d_val, const rs_mat *A0, double theta, int max_levels, int max_coarse, int nu,
-                  int smoother, AmgData **out);
+int rs_amg_create(rs_ctx *ctx, int n, const int *d_ptr, const int *d_col, const double *d_val, const rs_mat *A0,
+                  double theta, int max_levels, int max_coarse, int nu, int smoother, AmgData **out);
+// the hierarchy of Alg. 3 on the device (rs_amg_setup.cu): from M->A[0]
+int rs_amg_setup_device(AmgData *M, double theta, int max_levels, int max_coarse);
 int rs_amg_apply(AmgData *M, const double *r, double *z, const int *skip);
 void rs_amg_destroy(AmgData *M);
 int rs_amg_level_sizes(const AmgData *M, int l, int32_t *n, int64_t *nnz_a, int64_t *nnz_p);

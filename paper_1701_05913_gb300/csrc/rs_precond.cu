@@ -288,7 +288,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
             st = RS_ERR_INVALID_ARG;
             break;
         }
-        st = rs_amg_create(ctx, A->nrows, A->h_ptr, A->h_col, A->val, A, th, lev, nc, nu, sm, &M->amg);
+        st = rs_amg_create(ctx, A->nrows, A->ptr, A->col, A->val, A, th, lev, nc, nu, sm, &M->amg);
         break;
     }
     case RS_PC_RAS: {
@@ -337,7 +337,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         if (bs == 1) {
             // pressure stage on A itself: its ILU(0), or an AMG V-cycle
             if (pstage == 1 && type == RS_PC_CPR) {
-                st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, A->val, A, th, lev, ncoarse, nu, sm, &M->amg);
+                st = rs_amg_create(ctx, nb, A->ptr, A->col, A->val, A, th, lev, ncoarse, nu, sm, &M->amg);
             } else if (fras) {
                 st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, sweep, run_cap, &M->ilu, &bad);
                 if (!st) st = rs_ilu_factor(M->ilu, A->val, &bad);
@@ -375,7 +375,7 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         if (st) break;
         if (pstage == 1 && type == RS_PC_CPR) {
             // AMG V-cycle on the decoupled pressure matrix (the paper's CPR pressure stage)
-            st = rs_amg_create(ctx, nb, A->h_ptr, A->h_col, M->app_val, nullptr, th, lev, ncoarse, nu, sm, &M->amg);
+            st = rs_amg_create(ctx, nb, A->ptr, A->col, M->app_val, nullptr, th, lev, ncoarse, nu, sm, &M->amg);
             break;
         }
         st = rs_ilu_create(ctx, 1, nb, A->nnzb, A->ptr, A->col, A->h_ptr, A->h_col, fp32, sweep, run_cap, &M->ilu, &bad);

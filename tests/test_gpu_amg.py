@@ -1,9 +1,11 @@
 """Algebraic multigrid (Sec. 4.2, Algs. 3-4) on the GPU against the CPU
 oracle, through the C ABI.
 
-The hierarchy must match the oracle's: the C/F splitting and the patterns of
-every A_l and P_l bit for bit, values within 1e-12 relative (the Galerkin
-sums run in another order).  The V-cycle apply within 1e-12 relative, with
+The hierarchy is built on the GPU (strength, PMIS coarsening with the
+SplitMix64 weights, direct interpolation, Galerkin products) and must match
+the oracle's bit for bit: the C/F splitting, the patterns and the values of
+every A_l and P_l (both sides sum every entry's terms in the same order,
+each product and sum rounded once).  The V-cycle apply within 1e-12 relative, with
 either smoother; PCG /
 GMRES with AMG within 2 iterations of the oracle, true relative residual
 <= 1e-8, solution within 1e-6 relative.  The test matrices have random
@@ -71,11 +73,11 @@ def test_amg_hierarchy_and_vcycle(rs, ctx, orc, kind, shape, kz, kw, smoother):
     assert len(got) == len(want) >= 2
     for l, (g, (wa, wp)) in enumerate(zip(got, want)):
         assert np.array_equal(g["A"][0], wa[0]) and np.array_equal(g["A"][1], wa[1]), l
-        assert relmax(g["A"][2], wa[2]) <= 1e-12, l
+        assert np.array_equal(g["A"][2], wa[2]), (l, relmax(g["A"][2], wa[2]))
         if wp is not None:
             assert np.array_equal(g["cidx"], R.cidx(l)), l
             assert np.array_equal(g["P"][0], wp[0]) and np.array_equal(g["P"][1], wp[1]), l
-            assert relmax(g["P"][2], wp[2]) <= 1e-12, l
+            assert np.array_equal(g["P"][2], wp[2]), (l, relmax(g["P"][2], wp[2]))
     r = np.random.default_rng(71).standard_normal(n)
     z = rs.Vec.zeros(ctx, n)
     M.apply(rs.Vec(ctx, r), z)
@@ -84,6 +86,23 @@ def test_amg_hierarchy_and_vcycle(rs, ctx, orc, kind, shape, kz, kw, smoother):
     z2 = rs.Vec.zeros(ctx, n)
     M.apply(rs.Vec(ctx, r), z2)
     assert np.array_equal(z.numpy(), z2.numpy())
+
+
+def test_amg_setup_at_full_size(rs, ctx, orc):
+    """The GPU setup at 128 x 128 x 64 (8 levels): the C/F splitting of every
+    level, the patterns and values of every A_l and P_l equal the oracle's."""
+    g = synth.Grid(128, 128, 64)
+    d = synth.pressure_7pt(g, 1, kz_scale=0.1)
+    A = rs.Mat.csr(ctx, d)
+    M = rs.Precond(ctx, A, "amg")
+    R = orc.Amg(orc.Mat.csr(d))
+    got, want = M.amg_levels(), R.levels()
+    assert len(got) == len(want) >= 5
+    for l, (gl, (wa, wp)) in enumerate(zip(got, want)):
+        assert all(np.array_equal(x, y) for x, y in zip(gl["A"], wa)), l
+        if wp is not None:
+            assert np.array_equal(gl["cidx"], R.cidx(l)), l
+            assert all(np.array_equal(x, y) for x, y in zip(gl["P"], wp)), l
 
 
 @pytest.mark.parametrize("smoother", [0, 1])

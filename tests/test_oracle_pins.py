@@ -941,7 +941,7 @@ def test_amg_poisson1d_is_geometric_multigrid(orc):
     # 1-D Poisson, 2^4 - 1 points: Ruge-Stueben picks every other point,
     # direct interpolation is linear interpolation and the Galerkin matrix is
     # (1/2) tridiag(-1, 2, -1): each level is the previous one halved
-    M = orc.Amg(orc.Mat.csr(csr_dict(poisson1d(15))), max_coarse=1)
+    M = orc.Amg(orc.Mat.csr(csr_dict(poisson1d(15))), max_coarse=1, coarsen="rs")
     assert M.status == 0
     lv = M.levels()
     assert [a[0].size - 1 for a, _ in lv] == [15, 7, 3, 1]
@@ -966,11 +966,104 @@ def test_amg_anisotropy_gives_semicoarsening(orc):
     Ax = poisson1d(nx)
     Ay = poisson1d(ny)
     A = (sp.kron(sp.eye(ny), Ax) + eps * sp.kron(Ay, sp.eye(nx))).tocsr()
-    M = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1)
+    M = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1, coarsen="rs")
     a, p = M.levels()[0]
     Pd = _csr_dense(p, 4 * ny)
     C = [i for i in range(nx * ny) if (Pd[i] != 0).sum() == 1 and Pd[i].max() == 1.0]   # injected points
     assert C == [y * nx + x for y in range(ny) for x in (1, 3, 5, 7)]
+
+
+def test_splitmix64_published_outputs(orc):
+    # SplitMix64 from state 0 (Steele, Lea and Flood 2014): its first outputs
+    assert [orc.splitmix64(k) for k in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def _chain_strength(n):
+    # 1-D Poisson with theta = 0.5: both neighbours of a point are strong
+    ptr, col = [0], []
+    for i in range(n):
+        col += [j for j in (i - 1, i + 1) if 0 <= j < n]
+        ptr.append(len(col))
+    return np.array(ptr, np.int32), np.array(col, np.int32)
+
+
+def test_pmis_hand_worked_chains(orc):
+    # 7 points in a chain; lambda_i = |S_i^T| + w_i = 2 + w_i inside, 1 + w_i
+    # at the ends.  (a) w = .1 .5 .2 .9 .3 .4 .8: lambda = 1.1 2.5 2.2 2.9
+    # 2.3 2.4 1.8; the local maxima 1, 3, 5 become C in the first round and
+    # their neighbours F.  (b) w rising .1 .2 ... .7: lambda = 1.1 2.2 2.3
+    # 2.4 2.5 2.6 1.7; round 1 takes 5 (4 and 6 become F), round 2 takes 3
+    # among the undecided 0..3 (2 becomes F), round 3 takes 1 (0 becomes F)
+    sptr, scol = _chain_strength(7)
+    st, rounds = orc.pmis(7, sptr, scol, [.1, .5, .2, .9, .3, .4, .8])
+    assert st.tolist() == [2, 1, 2, 1, 2, 1, 2] and rounds == 1
+    st, rounds = orc.pmis(7, sptr, scol, [.1, .2, .3, .4, .5, .6, .7])
+    assert st.tolist() == [2, 1, 2, 1, 2, 1, 2] and rounds == 3
+    # a point that influences nothing is F from the start, even with the
+    # largest weight; a point with no neighbour left undecided becomes C
+    sptr = np.array([0, 1, 2, 2], np.int32)
+    scol = np.array([1, 0], np.int32)          # 0 and 1 depend on each other; 2 is isolated
+    st, _ = orc.pmis(3, sptr, scol, [.3, .2, .99])
+    assert st.tolist() == [1, 2, 2]
+
+
+@pytest.mark.parametrize("shape,kz,seed", [((9, 8, 7), 1.0, 70), ((12, 10, 6), 0.1, 71)])
+def test_pmis_invariants(orc, shape, kz, seed):
+    """On 7-point systems with the SplitMix64 weights: every point is decided;
+    every F point either influences no point or depends strongly on a C
+    point; for two strongly coupled C points the one of smaller measure does
+    not depend strongly on the other (it stayed undecided after the other
+    became C, so it cannot depend on it)."""
+    g = synth.Grid(*shape)
+    d = synth.pressure_7pt(g, seed, kz_scale=kz)
+    A = sp.csr_matrix((d["val"], d["col"], d["rowptr"]), shape=(g.n, g.n))
+    n, theta = g.n, 0.5
+    S = []
+    for i in range(n):
+        row = A.getrow(i)
+        off = [(j, v) for j, v in zip(row.indices, row.data) if j != i]
+        mx = max([-v for _, v in off] + [0.0])
+        S.append(sorted(j for j, v in off if mx > 0 and -v >= theta * mx))
+    sptr = np.cumsum([0] + [len(x) for x in S]).astype(np.int32)
+    scol = np.array([j for x in S for j in x], np.int32)
+    w = np.array([(orc.splitmix64((0 << 32) | i) >> 11) * 2.0 ** -53 for i in range(n)])
+    st, rounds = orc.pmis(n, sptr, scol, w)
+    assert set(st.tolist()) <= {1, 2} and rounds >= 2
+    infl = np.zeros(n, int)
+    for x in S:
+        for j in x:
+            infl[j] += 1
+    lam = infl + w
+    for i in range(n):
+        if st[i] == 2:
+            assert infl[i] == 0 or any(st[j] == 1 for j in S[i]), i
+        else:
+            for j in S[i]:
+                if st[j] == 1:
+                    assert lam[j] > lam[i] or i not in S[j], (i, j)
+    # the C points of the oracle's first AMG level are these
+    M = orc.Amg(orc.Mat.csr(d), max_levels=2, max_coarse=1)
+    assert np.array_equal(M.cidx(0) >= 0, st == 1)
+
+
+def test_amg_pmis_galerkin_and_convergence(orc):
+    # with PMIS coarsening the coarse matrices are still P^T A P (Eq. 4) and
+    # PCG with one V-cycle converges in a bounded number of iterations
+    g = synth.Grid(16, 14, 12)
+    d = synth.pressure_7pt(g, 63)
+    M = orc.Amg(orc.Mat.csr(d), max_coarse=16)
+    assert M.status == 0
+    lv = M.levels()
+    assert len(lv) >= 3
+    for l, (a, p) in enumerate(lv[:-1]):
+        Ad = _csr_dense(a)
+        nc = lv[l + 1][0][0].size - 1
+        Pd = _csr_dense(p, nc)
+        assert np.allclose(_csr_dense(lv[l + 1][0]), Pd.T @ Ad @ Pd, rtol=0, atol=1e-12 * np.abs(Ad).max())
+    Ao = orc.Mat.csr(d)
+    b = orc.spmv(Ao, synth.x_true(g.n, 63))
+    x, info, _ = orc.cg(Ao, orc.PC(Ao, "amg", amg=dict(max_coarse=16)), b, rtol=1e-8)
+    assert info["status"] == 0 and info["iters"] <= 30, info
 
 
 def test_amg_galerkin_and_constant_interpolation(orc):
@@ -985,7 +1078,7 @@ def test_amg_galerkin_and_constant_interpolation(orc):
     # pin the singular matrix's coarsest level away from it: add 1e-3 to one diagonal entry
     dd = np.nonzero(d["col"] == np.repeat(np.arange(n), np.diff(d["rowptr"])))[0]
     d["val"][dd[0]] += 1e-3
-    M = orc.Amg(orc.Mat.csr(d), max_coarse=8)
+    M = orc.Amg(orc.Mat.csr(d), max_coarse=8, coarsen="rs")
     assert M.status == 0
     lv = M.levels()
     assert len(lv) >= 3
@@ -1151,13 +1244,13 @@ def test_amg_coarsening_follows_the_first_pass_definition(orc):
         np.fill_diagonal(D, 0.0)
         np.fill_diagonal(D, -D.sum(axis=1) + 0.1)
         A = sp.csr_matrix(D)
-        M = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1)
+        M = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1, coarsen="rs")
         assert M.status == 0
         assert np.array_equal(M.cidx(0) >= 0, _rs_first_pass_by_definition(A, 0.5)), trial
     # the isotropic 5-point Laplacian coarsens red-black
     nx, ny = 8, 7
     A = (sp.kron(sp.eye(ny), poisson1d(nx)) + sp.kron(poisson1d(ny), sp.eye(nx))).tocsr()
-    c = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1).cidx(0) >= 0
+    c = orc.Amg(orc.Mat.csr(csr_dict(A)), max_levels=2, max_coarse=1, coarsen="rs").cidx(0) >= 0
     x, y = np.meshgrid(np.arange(nx), np.arange(ny))
     assert np.array_equal(c, ((x + y) % 2 == 0).reshape(-1))
 
