@@ -403,12 +403,11 @@ def _oracle_net_stage(net_params, out_scale, grid, logk, slab=None, clock=None):
     return stage
 
 
-def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH, net_slab=None):
-    """One oracle solve of the workload's system, at most maxit iterations:
-    returns (solve seconds, setup seconds, iterations, seconds of the solve
-    spent in the network, network volume factor).  With the learned stage
-    the network runs on net_slab z-planes (all if None); the volume factor
-    nz / net_slab scales its time to the full grid."""
+def oracle_setup(w, A_host, xt, net_file=NET_PATH, net_slab=None):
+    """The oracle's system, right-hand side and preconditioner for the
+    workload.  With the learned stage the network runs on net_slab z-planes
+    (all if None); the volume factor nz / net_slab scales its time to the
+    full grid."""
     import oracle
     oracle.build()
     if w["kind"] in ("bsr", "bsr_learned"):
@@ -440,18 +439,33 @@ def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH, net_slab=None):
                                          **({"ilut": k["ilut"]} if "ilut" in k else {})))
     else:
         M = oracle.PC(A, w["precond"], mixed=mixed, form=w.get("form", "pf"))
-    setup = time.perf_counter() - t0
+    return dict(A=A, M=M, b=b, setup=time.perf_counter() - t0, clock=clock, vol=vol)
+
+
+def oracle_solve(o, w, maxit):
+    """One oracle solve from x0 = 0, at most maxit iterations: (seconds,
+    iterations, seconds of it spent in the network)."""
+    import oracle
+    A, M, b = o["A"], o["M"], o["b"]
+    o["clock"][0] = 0.0
     t0 = time.perf_counter()
     if w["solver"] == "lgmres":
         _, info = oracle.lgmres(A, M, b, restart=30, aug_k=w["aug_k"], rtol=RTOL, maxit=maxit)
-        return time.perf_counter() - t0, setup, info["iters"], clock[0], vol
-    if w["solver"] == "bicgstab":
+    elif w["solver"] == "bicgstab":
         _, info, _ = oracle.bicgstab(A, M, b, rtol=RTOL, maxit=maxit)
     elif w["solver"] == "cg":
         _, info, _ = oracle.cg(A, M, b, rtol=RTOL, maxit=maxit)
     else:
         _, info, _ = oracle.gmres(A, M, b, restart=30, rtol=RTOL, maxit=maxit, flexible=w["solver"] == "fgmres")
-    return time.perf_counter() - t0, setup, info["iters"], clock[0], vol
+    return time.perf_counter() - t0, info["iters"], o["clock"][0]
+
+
+def oracle_run(w, A_host, xt, maxit, net_file=NET_PATH, net_slab=None):
+    """Setup and one solve: (solve seconds, setup seconds, iterations, seconds
+    of the solve spent in the network, network volume factor)."""
+    o = oracle_setup(w, A_host, xt, net_file, net_slab)
+    t, it, tnet = oracle_solve(o, w, maxit)
+    return t, o["setup"], it, tnet, o["vol"]
 
 
 def load_net_host(path):
@@ -473,62 +487,87 @@ NET_SLAB_REF = {"bsr_learned": 8}
 # iteration counts of the GPU solves, taken by the reference arm, which
 # does not run the GPU (a full oracle solve of these systems takes minutes
 # to hours on one core)
-GPU_ITERS = {"learned": 26, "bsr": 30, "bsr_learned": 33}
+GPU_ITERS = {"learned": 26, "bsr": 30, "bsr_learned": 32}
+# iterations an oracle sample runs on systems too large for a full solve
+SAMPLE_ITERS = {"learned": 1, "bsr": 6, "bsr_learned": 1}
 
 
-def oracle_baseline(w, A_host, xt, gpu_iters, slab_table=NET_SLAB):
-    """The oracle on a bounded sample, scaled to the iteration count."""
+def _sample_words(w, o, slab):
+    if w["precond"] != "cpr_learned":
+        return ""
+    nx, ny, nz = w["grid"]
+    what = " with the numpy network (bf16-rounded) as the pressure stage"
+    if slab is not None and o["vol"] != 1.0:
+        what += (", the network run on a %dx%dx%d slab of the grid and its time scaled by %g (it is fully "
+                 "convolutional: cost proportional to voxels)" % (nx, ny, nz / o["vol"], o["vol"]))
+    return what
+
+
+def oracle_baseline(w, A_host, xt, gpu_iters, slab_table=NET_SLAB, o=None):
+    """The oracle's solve time (setup excluded, as in the GPU arm's steps) on
+    one host core: a full solve where that takes seconds, else a bounded
+    sample of iterations scaled to the iteration count."""
     n = A_host["n"] if "n" in A_host else 3 * A_host["nb"]
-    if w["kind"] == "csr" and n <= 1_100_000:
-        t, s, it, _, _ = oracle_run(w, A_host, xt, 10000)
-        return {"value": t + s, "unit": "s", "cores": 1, "kind": "oracle",
-                "sample": "one full solve of the same system on one host core (%d iterations, setup %.3f s)"
-                          % (it, s)}
-    sample = {"learned": 1, "bsr": 6, "bsr_learned": 1}.get(w["kind"], 30)
     slab = slab_table.get(w["kind"])
-    t, s, it, tnet, vol = oracle_run(w, A_host, xt, sample, net_slab=slab)
-    per_it = ((t - tnet) + tnet * vol) / max(it, 1)
-    v = per_it * gpu_iters + s
-    if w["precond"] == "cpr_learned":
-        nx, ny, nz = w["grid"]
-        what = "with the numpy network (bf16-rounded) as the pressure stage"
-        if slab is not None and vol != 1.0:
-            what += (", the network run on a %dx%dx%d slab of the grid and its time scaled by %g (it is fully "
-                     "convolutional: cost proportional to voxels)" % (nx, ny, nz / vol, vol))
-    else:
-        what = ""
-    return {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": "%d iteration(s) of the same solve %s on one host core (%.2f s per iteration), scaled to %s "
-                      "iterations, plus setup %.2f s" % (it, what, per_it, gpu_iters, s)}
+    if o is None:
+        o = oracle_setup(w, A_host, xt, net_slab=slab)
+    if w["kind"] == "csr" and n <= 1_100_000:
+        t, it, _ = oracle_solve(o, w, 10000)
+        return {"value": t, "unit": "s", "cores": 1, "kind": "oracle",
+                "sample": "one full solve of the same system on one host core (%d iterations; setup %.3f s, not "
+                          "included)" % (it, o["setup"])}
+    t, it, tnet = oracle_solve(o, w, SAMPLE_ITERS.get(w["kind"], 30))
+    per_it = ((t - tnet) + tnet * o["vol"]) / max(it, 1)
+    return {"value": per_it * gpu_iters, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": "%d iteration(s) of the same solve%s on one host core (%.2f s per iteration), scaled to %s "
+                      "iterations (setup %.2f s, not included)" % (it, _sample_words(w, o, slab), per_it, gpu_iters,
+                                                                  o["setup"])}
+
+
+# z-planes of the sub-grid a reference-arm step samples on the largest
+# systems: one iteration there, its time scaled by the volume (every part
+# of an iteration costs in proportion to the unknowns), so that the arm's
+# steps stay within minutes
+REF_SLAB_Z = {"bsr_learned": 16}
 
 
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
+    grid0 = w["grid"]
+    zs = REF_SLAB_Z.get(w["kind"])
+    vscale = 1.0
+    if zs is not None and zs < w["grid"][2]:
+        vscale = w["grid"][2] / zs
+        w = dict(w, grid=(w["grid"][0], w["grid"][1], zs))
     g, A_host, xt = host_problem(w, w.get("seeds", [SEED])[0])
+    o = oracle_setup(w, A_host, xt, net_slab=None if zs is not None else NET_SLAB_REF.get(w["kind"]))
+    per = []
     if w["kind"] == "csr":
-        full_t, full_s, full_it, _, _ = oracle_run(w, A_host, xt, 10000)
-        per = []
+        full_t, full_it, _ = oracle_solve(o, w, 10000)
         for s in range(max(args.warmup - 1, 0) + args.steps):
-            t, su, done, _, _ = oracle_run(w, A_host, xt, 30)
+            t, done, _ = oracle_solve(o, w, 30)
             if s >= args.warmup - 1:
-                per.append(t / done * full_it + su)
+                per.append(t / done * full_it)
         sample = ("one full solve (%d iterations, %.2f s) then, per step, 30 iterations of the same solve "
-                  "scaled to %d iterations plus setup" % (full_it, full_t + full_s, full_it))
+                  "scaled to %d iterations (setup %.2f s, once, not included)" % (full_it, full_t, full_it,
+                                                                                  o["setup"]))
     else:
-        per = []
         cb = None
         for s in range(args.warmup + args.steps):
-            cb = oracle_baseline(w, A_host, xt, GPU_ITERS[w["kind"]], NET_SLAB_REF)
+            cb = oracle_baseline(w, A_host, xt, GPU_ITERS[w["kind"]], NET_SLAB_REF, o=o)
             if s >= args.warmup:
-                per.append(cb["value"])
+                per.append(cb["value"] * vscale)
         sample = cb["sample"] + " (iteration count of the GPU arm's solve assumed)"
+        if vscale != 1.0:
+            sample = ("on the %dx%dx%d sub-grid of the same generator, scaled by the volume %g: " %
+                      (tuple(w["grid"]) + (vscale,))) + sample
     v = statistics.mean(per)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if w["prec"] == "fp64" else "f64+f32", "data": "synthetic",
-        "config": {"workload": args.workload, "grid": list(w["grid"]), "solver": w["solver"],
+        "config": {"workload": args.workload, "grid": list(grid0), "solver": w["solver"],
                    "precond": w["precond"], "precision": w["prec"], "rtol": RTOL},
         "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
