@@ -81,6 +81,13 @@ struct rs_net {
     Level lv[NET_LEVELS];
     bf16 *act[NET_NLAYERS];                 // layer outputs
     bf16 *up0;                              // the coarse decoder input upsampled to the finest level
+    // tensor maps of the finest-level inputs, encoded once per workspace
+    struct TmapEntry {
+        const void *base;
+        int box[3];
+        CUtensorMap m;
+    } tmaps[8];
+    int ntmaps;
     bf16 *pool[NET_LEVELS];                 // pooled inputs of e1a, e2a, e3a
     bf16 *g16a[NET_LEVELS], *g16b[NET_LEVELS], *g32[NET_LEVELS];
     float *partials;                        // weight-gradient partials
@@ -1041,10 +1048,34 @@ static int make_tmap(CUtensorMap *m, const bf16 *base, int C, int W, int H, int 
     return r == CUDA_SUCCESS ? RS_OK : RS_ERR_CUDA;
 }
 
+// the tensor map of a finest-level buffer, encoded on first use (the buffers
+// live as long as the workspace, which clears the cache)
+static int cached_tmap(rs_net *net, const CUtensorMap **out, const bf16 *base, int W, int H, int D, int bx, int by,
+                       int bz)
+{
+    for (int k = 0; k < net->ntmaps; ++k) {
+        const rs_net::TmapEntry &e = net->tmaps[k];
+        if (e.base == base && e.box[0] == bx && e.box[1] == by && e.box[2] == bz) {
+            *out = &e.m;
+            return RS_OK;
+        }
+    }
+    if (net->ntmaps == 8) net->ntmaps = 0;       // more maps than expected: start over
+    rs_net::TmapEntry &e = net->tmaps[net->ntmaps];
+    RS_TRY(make_tmap(&e.m, base, 16, W, H, D, bx, by, bz));
+    e.base = base;
+    e.box[0] = bx;
+    e.box[1] = by;
+    e.box[2] = bz;
+    ++net->ntmaps;
+    *out = &e.m;
+    return RS_OK;
+}
 
 static void free_workspace(rs_net *net)
 {
     rs_ctx *c = net->ctx;
+    net->ntmaps = 0;
     for (int l = 0; l < NET_NLAYERS; ++l) { rs_free(c, net->act[l]); net->act[l] = nullptr; }
     rs_free(c, net->up0);
     net->up0 = nullptr;
@@ -1124,25 +1155,24 @@ static int conv_forward(rs_net *net, int l, const bf16 *X, const bf16 *U, const 
     const Level &L = net->lv[kLayers[l].level];
     const int grid = (int)nbricks(L);
     const float *bias = net->p + net->boff[l];
-    RsProfScope prof(c, RS_PROF_NET);
     if (kLayers[l].level == 0 && kLayers[l].mode != IN_FIRST) {
-        CUtensorMap xmap, umap;
+        const CUtensorMap *xmap, *umap;
         if (kLayers[l].mode == IN_CATUP) {
             // the coarse input, upsampled to this level, is the first half of the concatenation
             typedef TcCfg<32> TC;
+            RS_TRY(cached_tmap(net, &umap, net->up0, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
+            RS_TRY(cached_tmap(net, &xmap, X, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
             k_upsample2<<<ew_grid(c, L.nvox), 256, 0, c->stream>>>(L.nz, L.ny, L.nx, U, net->up0, skip);
             RS_TRY(rs_check_launch(c));
-            RS_TRY(make_tmap(&umap, net->up0, 16, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
-            RS_TRY(make_tmap(&xmap, X, 16, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
             const int nb = ((L.nx + TC::BX - 1) / TC::BX) * ((L.ny + TC::BY - 1) / TC::BY) * ((L.nz + TC::BZ - 1) / TC::BZ);
             k_conv3_tc<32><<<std::min(nb, c->num_sms), TC::THREADS, TC::SMEM, c->stream>>>(
-                L.nz, L.ny, L.nx, xmap, umap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip);
+                L.nz, L.ny, L.nx, *xmap, *umap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip);
         } else {
             typedef TcCfg<16> TC;
-            RS_TRY(make_tmap(&xmap, X, 16, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
+            RS_TRY(cached_tmap(net, &xmap, X, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
             const int nb = ((L.nx + TC::BX - 1) / TC::BX) * ((L.ny + TC::BY - 1) / TC::BY) * ((L.nz + TC::BZ - 1) / TC::BZ);
             k_conv3_tc<16><<<std::min(nb, c->num_sms), TC::THREADS, TC::SMEM, c->stream>>>(
-                L.nz, L.ny, L.nx, xmap, xmap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip);
+                L.nz, L.ny, L.nx, *xmap, *xmap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip);
         }
         return rs_check_launch(c);
     }
@@ -1166,7 +1196,6 @@ static int pool_forward(rs_net *net, int lvl, const bf16 *X, bf16 *Y, const int 
 {
     rs_ctx *c = net->ctx;
     const Level &L = net->lv[lvl];
-    RsProfScope prof(c, RS_PROF_NET);
     k_avgpool<<<ew_grid(c, L.nvox * 16), 256, 0, c->stream>>>(L.nz, L.ny, L.nx, X, Y, skip);
     return rs_check_launch(c);
 }
@@ -1176,11 +1205,11 @@ static int net_forward(rs_net *net, const double *r, const double *logk, double 
 {
     rs_ctx *c = net->ctx;
     const int64_t n0 = net->lv[0].nvox;
-    {
-        RsProfScope prof(c, RS_PROF_NET);
-        k_rms<<<c->red_blocks, 256, 0, c->stream>>>(n0, r, net->red, net->ticket, net->scal, skip);
-        RS_TRY(rs_check_launch(c));
-    }
+    // one profiler interval over the whole pass: the kernels, without the
+    // host work between their launches
+    RsProfScope prof(c, RS_PROF_NET);
+    k_rms<<<c->red_blocks, 256, 0, c->stream>>>(n0, r, net->red, net->ticket, net->scal, skip);
+    RS_TRY(rs_check_launch(c));
     bf16 **A = net->act;
     RS_TRY(conv_forward(net, E0A, nullptr, nullptr, r, logk, A[E0A], skip));
     RS_TRY(conv_forward(net, E0B, A[E0A], nullptr, nullptr, nullptr, A[E0B], skip));
@@ -1199,7 +1228,6 @@ static int net_forward(rs_net *net, const double *r, const double *logk, double 
     RS_TRY(conv_forward(net, D1B, A[D1A], nullptr, nullptr, nullptr, A[D1B], skip));
     RS_TRY(conv_forward(net, D0A, A[E0B], A[D1B], nullptr, nullptr, A[D0A], skip));
     RS_TRY(conv_forward(net, D0B, A[D0A], nullptr, nullptr, nullptr, A[D0B], skip));
-    RsProfScope prof(c, RS_PROF_NET);
     k_head<<<ew_grid(c, n0), 256, 0, c->stream>>>(n0, A[D0B], net->p + net->hoff, net->scal, net->out_scale, out,
                                                  net->flag, skip);
     return rs_check_launch(c);
