@@ -106,8 +106,9 @@ typedef struct {
     int32_t cpr_pstage;     /* RS_PC_CPR pressure stage: 0 ILU(0) of the
                                decoupled matrix, 1 one AMG V-cycle on it     */
     /* RAS local solver (Fig. 31): 0 ILU(ilu_level), 1 ILUT(ilut_p, ilut_tol)
-     * (scalar matrices), computed on the host, since its pattern depends on
-     * the values.  ILUT drops entries below ilut_tol * ||a_i||_2 and keeps
+     * (scalar matrices), factorised on the GPU one subdomain per warp, since
+     * its pattern depends on the values.  ILUT drops entries below
+     * ilut_tol * ||a_i||_2 and keeps
      * the ilut_p largest of each part of a row (negative: as many as the
      * row of A has there).  Zeroed fields take the paper's defaults: p = -1,
      * tol = 1e-3. */

@@ -111,93 +111,325 @@ static void iluk_rows(int n, const std::vector<int> &lptr, const std::vector<int
     }
 }
 
-// ILUT(p, tol) of one local matrix (rows 0..n-1, sorted columns, values
-// lval), Saad's algorithm row by row: the row in a dense work array; its
-// lower entries eliminated in ascending order (fill included), each
-// multiplier w_k = w_k / u_kk dropped below tau = tol ||a_i||_2, else
+// ILUT(p, tol) of the stacked local matrices on the GPU, one thread per
+// subdomain (the subdomains are independent; a subdomain's rows depend on
+// each other, in order), Saad's algorithm row by row as the sequential
+// reading has it: the row in a dense work array w; its lower entries
+// eliminated in ascending order, fill included, each multiplier
+// w_k = w_k / u_kk dropped below tau = tol ||a_i||_2, else
 // w_j -= w_k u_kj over the stored U row k; then off-diagonal entries below
 // tau dropped and the p largest kept in each part (ties to the lower
-// column; p < 0: as many as row i has there).  Appends the factor rows
-// (strict L, then U with its diagonal, columns + base) to optr/ocol/olu.
-// Returns the local row of a zero pivot, or -1.
-static int ilut_rows(int n, const std::vector<int> &lptr, const std::vector<int> &lcol, const std::vector<double> &lval,
-                     int p, double tol, int base, std::vector<int> &optr, std::vector<int> &ocol,
-                     std::vector<double> &olu)
+// column; p < 0: as many as row i has there).  Every product and sum is
+// rounded once, in the sequential order, so the dropping decisions (and the
+// pattern) are those of a sequential run.
+//
+// Subdomain s owns stacked rows [sb[s], sb[s+1]) and, in the scratch arrays
+// indexed by stacked row, its w, flags and lists; its factor rows go to
+// [cap[s], cap[s+1]) of ocol/oval, row r at [rs[r], re[r]) with its diagonal
+// at rd[r].  st[s]: -1 done, >= 0 the local row of a zero pivot, -2 the
+// output region overflowed.
+__device__ __forceinline__ bool ilut_larger(int ca, double va, int cb, double vb)
 {
-    std::vector<int> up(n + 1), uc;          // U rows kept so far (diagonal first)
-    std::vector<double> uv;
-    std::vector<double> w(n, 0.0);
-    std::vector<char> in(n, 0);
-    std::vector<int> touched, lower;
-    std::vector<std::pair<int, double>> lo, hi;
-    auto larger = [](const std::pair<int, double> &a, const std::pair<int, double> &b) {
-        const double x = std::fabs(a.second), y = std::fabs(b.second);
-        return x != y ? x > y : a.first < b.first;
-    };
+    const double x = fabs(va), y = fabs(vb);
+    return x != y ? x > y : ca < cb;
+}
+
+__global__ void k_ilut(int nparts, const int *__restrict__ sb, const int *__restrict__ lptr,
+                       const int *__restrict__ lcol, const double *__restrict__ lval, int p, double tol,
+                       const int64_t *__restrict__ cap, int *__restrict__ ocol, double *__restrict__ oval,
+                       int64_t *__restrict__ rs_, int64_t *__restrict__ rd, int64_t *__restrict__ re,
+                       double *__restrict__ w_, char *__restrict__ in_, int *__restrict__ touched_,
+                       int *__restrict__ lower_, int *__restrict__ cc_, double *__restrict__ cv_, int *__restrict__ st)
+{
+    // one subdomain per warp, on its first lane: the rows are sequential and
+    // the subdomains' control flow diverges, so a warp each keeps them apart
+    const int s = blockIdx.x;
+    if (s >= nparts || threadIdx.x != 0) return;
+    const int b0 = sb[s], n = sb[s + 1] - b0;
+    double *w = w_ + b0;
+    char *in = in_ + b0;
+    int *touched = touched_ + b0, *lower = lower_ + b0, *cc = cc_ + b0;
+    double *cv = cv_ + b0;
+    int64_t o = cap[s];
+    const int64_t oend = cap[s + 1];
     for (int i = 0; i < n; ++i) {
-        touched.clear();
-        lower.clear();
-        int pl = 0, pu = 0;
+        const int r = b0 + i;
+        int nt = 0, nlow = 0, pl = 0, pu = 0;
         double sq = 0.0;
-        for (int q = lptr[i]; q < lptr[i + 1]; ++q) {
+        for (int q = lptr[r]; q < lptr[r + 1]; ++q) {
             const int c = lcol[q];
             w[c] = lval[q];
             in[c] = 1;
-            touched.push_back(c);
-            sq += lval[q] * lval[q];
-            if (c < i) { ++pl; lower.push_back(c); }
-            else if (c > i) ++pu;
+            touched[nt++] = c;
+            sq = __dadd_rn(sq, __dmul_rn(lval[q], lval[q]));
+            if (c < i) {
+                ++pl;
+                lower[nlow++] = c;
+            } else if (c > i) {
+                ++pu;
+            }
         }
-        const double tau = tol * std::sqrt(sq);
+        const double tau = __dmul_rn(tol, __dsqrt_rn(sq));
         if (p >= 0) pl = pu = p;
-        for (size_t t = 0; t < lower.size(); ++t) {
+        for (int t = 0; t < nlow; ++t) {
             const int k = lower[t];
             if (w[k] == 0.0) continue;
-            w[k] = w[k] / uv[up[k]];
-            if (std::fabs(w[k]) < tau) { w[k] = 0.0; continue; }
-            for (int q = up[k] + 1; q < up[k + 1]; ++q) {
-                const int j = uc[q];
+            w[k] = __ddiv_rn(w[k], oval[rd[b0 + k]]);
+            if (fabs(w[k]) < tau) {
+                w[k] = 0.0;
+                continue;
+            }
+            const double wk = w[k];
+            for (int64_t q = rd[b0 + k] + 1; q < re[b0 + k]; ++q) {
+                const int j = ocol[q];
                 if (!in[j]) {
                     in[j] = 1;
                     w[j] = 0.0;
-                    touched.push_back(j);
-                    if (j < i) lower.insert(std::upper_bound(lower.begin() + t + 1, lower.end(), j), j);
+                    touched[nt++] = j;
+                    if (j < i) {            // a new lower entry, in sorted position behind t
+                        int a = nlow++;
+                        while (a > t + 1 && lower[a - 1] > j) {
+                            lower[a] = lower[a - 1];
+                            --a;
+                        }
+                        lower[a] = j;
+                    }
                 }
-                w[j] = w[j] - w[k] * uv[q];
+                w[j] = __dsub_rn(w[j], __dmul_rn(wk, oval[q]));
             }
         }
-        lo.clear();
-        hi.clear();
+        // the surviving off-diagonal entries: lower ones at the front of the
+        // candidate buffer, upper ones at its back
+        int nl = 0, nu = 0;
         double diag = 0.0;
-        for (int c : touched) {
-            if (c == i) diag = w[c];
-            else if (w[c] != 0.0 && std::fabs(w[c]) >= tau) (c < i ? lo : hi).push_back({c, w[c]});
+        for (int a = 0; a < nt; ++a) {
+            const int c = touched[a];
+            if (c == i) {
+                diag = w[c];
+            } else if (w[c] != 0.0 && fabs(w[c]) >= tau) {
+                const int at = c < i ? nl++ : n - 1 - nu++;
+                cc[at] = c;
+                cv[at] = w[c];
+            }
             w[c] = 0.0;
             in[c] = 0;
         }
-        if (!(diag != 0.0) || !std::isfinite(diag)) return i;
-        std::sort(lo.begin(), lo.end(), larger);
-        std::sort(hi.begin(), hi.end(), larger);
-        if ((int)lo.size() > pl) lo.resize(pl);
-        if ((int)hi.size() > pu) hi.resize(pu);
-        std::sort(lo.begin(), lo.end());
-        std::sort(hi.begin(), hi.end());
-        for (const auto &e : lo) { ocol.push_back(base + e.first); olu.push_back(e.second); }
-        ocol.push_back(base + i);
-        olu.push_back(diag);
-        up[i] = (int)uc.size();
-        uc.push_back(i);
-        uv.push_back(diag);
-        for (const auto &e : hi) {
-            ocol.push_back(base + e.first);
-            olu.push_back(e.second);
-            uc.push_back(e.first);
-            uv.push_back(e.second);
+        if (!(diag != 0.0) || !isfinite(diag)) {
+            st[s] = i;
+            return;
         }
-        up[i + 1] = (int)uc.size();
-        optr.push_back((int)ocol.size());
+        // each part: the p largest (insertion sort by magnitude), then by column
+        const int ulo = n - nu;                 // first upper candidate
+        for (int part = 0; part < 2; ++part) {
+            const int lo = part ? ulo : 0, len = part ? nu : nl, lim = part ? pu : pl;
+            for (int a = lo + 1; a < lo + len; ++a) {
+                const int c = cc[a];
+                const double v = cv[a];
+                int b = a - 1;
+                while (b >= lo && ilut_larger(c, v, cc[b], cv[b])) {
+                    cc[b + 1] = cc[b];
+                    cv[b + 1] = cv[b];
+                    --b;
+                }
+                cc[b + 1] = c;
+                cv[b + 1] = v;
+            }
+            const int keep = len < lim ? len : lim;
+            for (int a = lo + 1; a < lo + keep; ++a) {
+                const int c = cc[a];
+                const double v = cv[a];
+                int b = a - 1;
+                while (b >= lo && cc[b] > c) {
+                    cc[b + 1] = cc[b];
+                    cv[b + 1] = cv[b];
+                    --b;
+                }
+                cc[b + 1] = c;
+                cv[b + 1] = v;
+            }
+            if (part) nu = keep;
+            else nl = keep;
+        }
+        if (o + nl + 1 + nu > oend) {
+            st[s] = -2;
+            return;
+        }
+        rs_[r] = o;
+        for (int a = 0; a < nl; ++a, ++o) {
+            ocol[o] = cc[a];
+            oval[o] = cv[a];
+        }
+        rd[r] = o;
+        ocol[o] = i;
+        oval[o] = diag;
+        ++o;
+        for (int a = 0; a < nu; ++a, ++o) {
+            ocol[o] = cc[ulo + a];
+            oval[o] = cv[ulo + a];
+        }
+        re[r] = o;
     }
-    return -1;
+    st[s] = -1;
+}
+
+// the factor rows, from their places in the scratch into the stacked CSR
+// (columns offset by the subdomain's first stacked row)
+__global__ void k_ilut_compact(int nx, const int64_t *__restrict__ rs_, const int64_t *__restrict__ re,
+                               const int *__restrict__ hptr, const int *__restrict__ rbase,
+                               const int *__restrict__ ocol, const double *__restrict__ oval, int *__restrict__ col,
+                               double *__restrict__ val)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nx; r += gridDim.x * blockDim.x) {
+        int d = hptr[r];
+        for (int64_t q = rs_[r]; q < re[r]; ++q, ++d) {
+            col[d] = ocol[q] + rbase[r];
+            val[d] = oval[q];
+        }
+    }
+}
+
+// ILUT of the stacked local matrices on the GPU (k_ilut): xptr/xcol the
+// stacked local pattern (local columns), xsrc the positions of its values in
+// A, sbase the subdomains' first stacked rows, rbase every stacked row's.
+// Fills hptr/hcol (host, stacked columns) and *val (device).  The output
+// regions start at 8 entries per local entry plus 2 per row and double
+// while a subdomain overflows its region.  RS_ERR_ZERO_PIVOT: *bad = the
+// stacked row of the first zero pivot (lowest subdomain).
+static int ilut_device(rs_ctx *ctx, const rs_mat *A, int nparts, const std::vector<int> &sbase,
+                       const std::vector<int> &xptr, const std::vector<int> &xcol, const std::vector<int> &xsrc,
+                       const std::vector<int> &rbase, int p, double tol, std::vector<int> &hptr,
+                       std::vector<int> &hcol, double **val, int *bad)
+{
+    const cudaStream_t sm = ctx->stream;
+    const int nx = (int)rbase.size();
+    const int64_t nnz = (int64_t)xcol.size();
+    std::vector<void *> tmp;
+    auto alloc = [&](void **ptr, size_t bytes) -> int {
+        *ptr = nullptr;
+        const int st = rs_alloc(ctx, ptr, std::max<size_t>(bytes, 16));
+        if (!st) tmp.push_back(*ptr);
+        return st;
+    };
+    auto up = [&](void *dst, const void *src, size_t bytes) -> int {
+        return !bytes || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, sm) == cudaSuccess ? RS_OK
+                                                                                                     : RS_ERR_CUDA;
+    };
+    int st = RS_OK;
+    int *d_sb, *d_ptr, *d_col, *d_src, *d_st, *d_touch, *d_low, *d_cc, *d_rbase;
+    double *d_val, *d_w, *d_cv;
+    char *d_in;
+    int64_t *d_rs, *d_rd, *d_re;
+    st = st ? st : alloc((void **)&d_sb, sizeof(int) * (nparts + 1));
+    st = st ? st : alloc((void **)&d_ptr, sizeof(int) * (nx + 1));
+    st = st ? st : alloc((void **)&d_col, sizeof(int) * nnz);
+    st = st ? st : alloc((void **)&d_src, sizeof(int) * nnz);
+    st = st ? st : alloc((void **)&d_val, sizeof(double) * nnz);
+    st = st ? st : alloc((void **)&d_st, sizeof(int) * nparts);
+    st = st ? st : alloc((void **)&d_w, sizeof(double) * nx);
+    st = st ? st : alloc((void **)&d_in, (size_t)nx);
+    st = st ? st : alloc((void **)&d_touch, sizeof(int) * nx);
+    st = st ? st : alloc((void **)&d_low, sizeof(int) * nx);
+    st = st ? st : alloc((void **)&d_cc, sizeof(int) * nx);
+    st = st ? st : alloc((void **)&d_cv, sizeof(double) * nx);
+    st = st ? st : alloc((void **)&d_rs, sizeof(int64_t) * nx);
+    st = st ? st : alloc((void **)&d_rd, sizeof(int64_t) * nx);
+    st = st ? st : alloc((void **)&d_re, sizeof(int64_t) * nx);
+    st = st ? st : alloc((void **)&d_rbase, sizeof(int) * nx);
+    st = st ? st : up(d_sb, sbase.data(), sizeof(int) * (nparts + 1));
+    st = st ? st : up(d_ptr, xptr.data(), sizeof(int) * (nx + 1));
+    st = st ? st : up(d_col, xcol.data(), sizeof(int) * nnz);
+    st = st ? st : up(d_src, xsrc.data(), sizeof(int) * nnz);
+    st = st ? st : up(d_rbase, rbase.data(), sizeof(int) * nx);
+    if (!st && nnz > 0) {
+        // the local values, gathered from A
+        k_ras_values<<<ras_grid(ctx, nnz), 256, 0, sm>>>(nnz, 1, d_src, A->val, d_val);
+        st = rs_check_launch(ctx);
+    }
+    if (!st && cudaMemsetAsync(d_w, 0, sizeof(double) * nx, sm) != cudaSuccess) st = RS_ERR_CUDA;
+    if (!st && cudaMemsetAsync(d_in, 0, (size_t)nx, sm) != cudaSuccess) st = RS_ERR_CUDA;
+    // output regions
+    std::vector<int64_t> mult(nparts, 1), cap(nparts + 1);
+    std::vector<int> hst(nparts, -1);
+    int *d_ocol = nullptr;
+    double *d_oval = nullptr;
+    int64_t *d_cap = nullptr;
+    for (int attempt = 0; !st; ++attempt) {
+        cap[0] = 0;
+        for (int s = 0; s < nparts; ++s) {
+            const int64_t ns = sbase[s + 1] - sbase[s];
+            const int64_t ln = xptr[sbase[s + 1]] - xptr[sbase[s]];
+            cap[s + 1] = cap[s] + std::min<int64_t>((8 * ln + 2 * ns) * mult[s], ns * ns + ns);
+        }
+        if (d_ocol) { rs_free(ctx, d_ocol); rs_free(ctx, d_oval); rs_free(ctx, d_cap); }
+        st = rs_alloc(ctx, (void **)&d_ocol, sizeof(int) * std::max<int64_t>(cap[nparts], 1));
+        st = st ? st : rs_alloc(ctx, (void **)&d_oval, sizeof(double) * std::max<int64_t>(cap[nparts], 1));
+        st = st ? st : rs_alloc(ctx, (void **)&d_cap, sizeof(int64_t) * (nparts + 1));
+        st = st ? st : up(d_cap, cap.data(), sizeof(int64_t) * (nparts + 1));
+        if (st) break;
+        k_ilut<<<nparts, 32, 0, sm>>>(nparts, d_sb, d_ptr, d_col, d_val, p, tol, d_cap, d_ocol, d_oval,
+                                                  d_rs, d_rd, d_re, d_w, d_in, d_touch, d_low, d_cc, d_cv, d_st);
+        st = rs_check_launch(ctx);
+        if (!st && (cudaMemcpyAsync(hst.data(), d_st, sizeof(int) * nparts, cudaMemcpyDeviceToHost, sm) !=
+                        cudaSuccess ||
+                    cudaStreamSynchronize(sm) != cudaSuccess))
+            st = RS_ERR_CUDA;
+        if (st) break;
+        bool over = false;
+        for (int s = 0; s < nparts && !st; ++s) {
+            if (hst[s] >= 0) {
+                *bad = sbase[s] + hst[s];
+                st = RS_ERR_ZERO_PIVOT;
+            } else if (hst[s] == -2) {
+                over = true;
+                mult[s] *= 2;
+            }
+        }
+        if (st || !over) break;
+        // an overflow leaves w and the flags as they were: clear them
+        if (cudaMemsetAsync(d_w, 0, sizeof(double) * nx, sm) != cudaSuccess ||
+            cudaMemsetAsync(d_in, 0, (size_t)nx, sm) != cudaSuccess)
+            st = RS_ERR_CUDA;
+        if (attempt > 40) st = RS_ERR_INVALID_ARG;
+    }
+    // the stacked pattern: row lengths on the host, the rows compacted on the GPU
+    if (!st) {
+        std::vector<int64_t> hrs(nx), hre(nx);
+        if (nx > 0 &&
+            (cudaMemcpyAsync(hrs.data(), d_rs, sizeof(int64_t) * nx, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+             cudaMemcpyAsync(hre.data(), d_re, sizeof(int64_t) * nx, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+             cudaStreamSynchronize(sm) != cudaSuccess))
+            st = RS_ERR_CUDA;
+        hptr.assign(1, 0);
+        for (int r = 0; r < nx && !st; ++r) {
+            if ((int64_t)hptr.back() + (hre[r] - hrs[r]) > INT_MAX) st = RS_ERR_INVALID_ARG;
+            else hptr.push_back(hptr.back() + (int)(hre[r] - hrs[r]));
+        }
+    }
+    int *d_hptr = nullptr, *d_fcol = nullptr;
+    const int64_t fnnz = st ? 0 : hptr.back();
+    if (!st) st = alloc((void **)&d_hptr, sizeof(int) * (nx + 1));
+    if (!st) st = alloc((void **)&d_fcol, sizeof(int) * fnnz);
+    if (!st) st = rs_alloc(ctx, (void **)val, sizeof(double) * std::max<int64_t>(fnnz, 1));
+    if (!st) st = up(d_hptr, hptr.data(), sizeof(int) * (nx + 1));
+    if (!st && nx > 0) {
+        k_ilut_compact<<<ras_grid(ctx, nx), 256, 0, sm>>>(nx, d_rs, d_re, d_hptr, d_rbase, d_ocol, d_oval, d_fcol,
+                                                          *val);
+        st = rs_check_launch(ctx);
+    }
+    if (!st) {
+        hcol.resize(fnnz);
+        if (fnnz > 0 &&
+            (cudaMemcpyAsync(hcol.data(), d_fcol, sizeof(int) * fnnz, cudaMemcpyDeviceToHost, sm) != cudaSuccess ||
+             cudaStreamSynchronize(sm) != cudaSuccess))
+            st = RS_ERR_CUDA;
+    }
+    if (d_ocol) { rs_free(ctx, d_ocol); rs_free(ctx, d_oval); rs_free(ctx, d_cap); }
+    for (void *q : tmp) rs_free(ctx, q);
+    if (st && *val) {
+        rs_free(ctx, *val);
+        *val = nullptr;
+    }
+    return st;
 }
 
 int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part, int overlap, int level, int local,
@@ -215,16 +447,9 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
         if (pt[i] < 0 || pt[i] >= nparts) return RS_ERR_INVALID_ARG;
     }
     const std::vector<int> &ap = A->h_ptr, &ac = A->h_col;
-    std::vector<double> av;                    // A's values, for ILUT on the host
-    if (local == 1 && !ac.empty()) {
-        av.resize(ac.size());
-        if (cudaMemcpyAsync(av.data(), A->val, sizeof(double) * ac.size(), cudaMemcpyDeviceToHost, ctx->stream) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-            return RS_ERR_CUDA;
-    }
-    std::vector<double> hlu;                   // ILUT: the stacked factor
-    int ilut_bad = -1;
+    // ILUT: the stacked local matrices (pattern, and the positions of their
+    // values in A), factorised on the GPU after the loop
+    std::vector<int> sbase(1, 0), xptr(1, 0), xcol, xsrc, rbase;
     // rows of each subdomain, ascending
     std::vector<int> pstart(nparts + 1, 0), prow(n);
     for (int i = 0; i < n; ++i) ++pstart[pt[i] + 1];
@@ -270,14 +495,16 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
             lptr.push_back((int)lcol.size());
         }
         if (local == 1) {
-            std::vector<double> lval(lsrc.size());
-            for (size_t q = 0; q < lsrc.size(); ++q) lval[q] = av[lsrc[q]];
-            const int b = ilut_rows(ns, lptr, lcol, lval, ilut_p, ilut_tol, base, hptr, hcol, hlu);
-            if (b >= 0) {
-                ilut_bad = set[b];
-                break;
+            for (int a = 0; a < ns; ++a) {
+                for (int q = lptr[a]; q < lptr[a + 1]; ++q) {
+                    xcol.push_back(lcol[q]);
+                    xsrc.push_back(lsrc[q]);
+                }
+                xptr.push_back((int)xcol.size());
+                rbase.push_back(base);
             }
-            hsrc.resize(hcol.size(), -1);
+            sbase.push_back(base + ns);
+            if ((int64_t)xcol.size() > INT_MAX) return RS_ERR_INVALID_ARG;
         } else if (level == 0) {
             for (int a = 0; a < ns; ++a) {
                 for (int q = lptr[a]; q < lptr[a + 1]; ++q) {
@@ -294,11 +521,17 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
         gidx.insert(gidx.end(), set.begin(), set.end());
         for (int r = pstart[s]; r < pstart[s + 1]; ++r) own[prow[r]] = base + loc[prow[r]];
     }
-    if (ilut_bad >= 0) {
-        if (bad_row) *bad_row = ilut_bad;
-        return RS_ERR_ZERO_PIVOT;
-    }
     const int nx = (int)gidx.size();
+    double *ilut_val = nullptr;                // ILUT: the stacked factor's values (device)
+    if (local == 1) {
+        int bad = -1;
+        const int st0 = ilut_device(ctx, A, nparts, sbase, xptr, xcol, xsrc, rbase, ilut_p, ilut_tol, hptr, hcol,
+                                    &ilut_val, &bad);
+        if (st0 == RS_ERR_ZERO_PIVOT && bad_row) *bad_row = gidx[bad];
+        if (st0) return st0;
+        hsrc.assign(hcol.size(), -1);
+        total_nnz = (int64_t)hcol.size();
+    }
     RasData *R = new RasData();
     R->ctx = ctx;
     R->bs = bs;
@@ -334,10 +567,11 @@ int rs_ras_create(rs_ctx *ctx, const rs_mat *A, int nparts, const int32_t *part,
         return RS_ERR_CUDA;
     }
     if (local == 1) {
-        // the factor itself was formed on the host
-        if (total_nnz > 0 &&
-            cudaMemcpyAsync(R->val, hlu.data(), sizeof(double) * total_nnz, cudaMemcpyHostToDevice, sm) != cudaSuccess)
+        // the factor formed on the GPU (ilut_device)
+        if (total_nnz > 0 && cudaMemcpyAsync(R->val, ilut_val, sizeof(double) * total_nnz, cudaMemcpyDeviceToDevice,
+                                             sm) != cudaSuccess)
             st = RS_ERR_CUDA;
+        rs_free(ctx, ilut_val);
     } else if (total_nnz > 0) {
         k_ras_values<<<ras_grid(ctx, total_nnz * (int64_t)b2), 256, 0, sm>>>(total_nnz, (int)b2, R->src, A->val, R->val);
         st = rs_check_launch(ctx);
