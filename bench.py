@@ -178,7 +178,10 @@ def kernel_model(w, A_host, ras_sizes=None):
     vb = 4 if w["prec"] == "mixed" else 8
     if w["kind"] in ("bsr", "bsr_learned"):
         nb, nnzb = A_host["nb"], A_host["bcol"].size
-        mod = {"spmv": 76 * nnzb + 4 * (nb + 1) + 48 * nb}
+        # the CPR residual after the pressure stage (PF form) reads only the
+        # pressure column of each block: 28 B a block, p, f and t
+        mod = {"spmv": 76 * nnzb + 4 * (nb + 1) + 48 * nb,
+               "cpr_resid": 28 * nnzb + 4 * (nb + 1) + 8 * nb + 48 * nb}
         mod.update(scalar_ilu_bytes(nb, nnzb, vb))
         mod.update(block_ilu_bytes(*(ras_sizes or (nb, nnzb)), vb))
         return mod, 3 * nb
@@ -231,7 +234,7 @@ def executed_launches(w, infos, amg_vc=None, spmv_bytes=None):
     SpMVs and two applies per iteration."""
     cpr = w["precond"] in ("cpr", "cpr_learned")
     block = w["kind"] in ("bsr", "bsr_learned")
-    cnt = {k: 0 for k in ("spmv", "l_sweep", "u_sweep", "bl_sweep", "bu_sweep", "net")}
+    cnt = {k: 0 for k in ("spmv", "l_sweep", "u_sweep", "bl_sweep", "bu_sweep", "net", "cpr_resid")}
     for info in infos:
         I, C = info["iters"], info["restarts"]
         if w["solver"] == "bicgstab":
@@ -253,6 +256,10 @@ def executed_launches(w, infos, amg_vc=None, spmv_bytes=None):
         nF, nP = form.count("F"), form.count("P")
         if cpr:
             spmv += applies * (len(form) - 1)
+            if block and form == "PF":
+                # that residual takes the pressure-column kernel instead
+                spmv -= applies
+                cnt["cpr_resid"] += applies
         cnt["spmv"] += spmv
         if amg_vc:
             # every AMG V-cycle (the preconditioner, or CPR's pressure stage)
@@ -306,7 +313,7 @@ def cgs_fmas(n, iters_list, m=30):
 
 
 def source_sha(kernel):
-    files = {"spmv": ["rs_core.cu"], "net": ["rs_net.cu"]}.get(
+    files = {"spmv": ["rs_core.cu"], "net": ["rs_net.cu"], "cpr_resid": ["rs_precond.cu"]}.get(
         kernel, ["rs_ilu.cu", "rs_wave.cu"] if "sweep" in kernel else ["rs_krylov.cu"])
     h = hashlib.sha256()
     for f in files:

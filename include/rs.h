@@ -190,7 +190,7 @@ int64_t rs_launch_count(const rs_ctx *ctx);
  * added to its class.  Classes, in order: SpMV, L sweep, U sweep, CGS dots,
  * CGS update+dots, CGS update+norm, BLAS-1, other preconditioner kernels,
  * factorisation, solver scalar kernels, network, block L sweep, block U
- * sweep.  nkinds >= 13. */
+ * sweep, CPR pressure-column residual.  nkinds >= 14. */
 int rs_prof_enable(rs_ctx *ctx, int on);
 /* Reads (and with reset != 0 clears) the accumulated milliseconds and launch
  * counts per class; synchronises the stream. */

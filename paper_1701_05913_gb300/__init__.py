@@ -231,7 +231,8 @@ class Context:
         return lib().rs_launch_count(self.h)
 
     PROF_KINDS = ("spmv", "l_sweep", "u_sweep", "cgs_dots", "cgs_update_dots", "cgs_update_norm",
-                  "blas1", "precond_other", "factor", "solver_scalar", "net", "bl_sweep", "bu_sweep")
+                  "blas1", "precond_other", "factor", "solver_scalar", "net", "bl_sweep", "bu_sweep",
+                  "cpr_resid")
 
     def prof_enable(self, on=True):
         _check(lib().rs_prof_enable(self.h, int(on)), "rs_prof_enable")

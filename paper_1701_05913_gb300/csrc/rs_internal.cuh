@@ -53,6 +53,7 @@ enum RsProfKind {
     RS_PROF_NET,
     RS_PROF_BLSWEEP,
     RS_PROF_BUSWEEP,
+    RS_PROF_CPR_RESID,
     RS_PROF_NKINDS
 };
 
@@ -264,6 +265,7 @@ struct rs_pc {
     int *diagA;              // diagonal block positions of A (CPR with a RAS F stage)
     double *rp, *zp;         // pressure-stage vectors [nb]
     double *t1, *t2;         // full-size work vectors [n]
+    double *pcol;            // PF form on blocks: column 0 of every block of A [nnzb*bs]
     // learned pressure stage
     const rs_net *net;
     const double *log_perm;

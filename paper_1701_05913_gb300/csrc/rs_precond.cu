@@ -70,6 +70,48 @@ __global__ void k_copy_add(int64_t n, const double *__restrict__ a, double *__re
         z[i] = add ? __dadd_rn(z[i], a[i]) : a[i];
 }
 
+// pcol[p bs + r] = A_p[r][0]: the pressure column of every block, the only
+// one a prolonged pressure correction (Eq. 8) meets
+__global__ void k_pcol_gather(int64_t nnzb, int bs, const double *__restrict__ val, double *__restrict__ pcol)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnzb * bs;
+         t += (int64_t)gridDim.x * blockDim.x)
+        pcol[t] = val[t * bs];
+}
+
+// t = f - A (Pi_p p): the residual after a pressure stage.  The prolonged
+// vector is zero outside the pressure unknowns, so only the pressure column
+// of each block contributes; the remaining terms of the full product are
+// exact zeros.  One thread per scalar row, multiply-adds in the block order
+// of the BSR SpMV, so the sums are those of the full product.
+template <int BS>
+__global__ void __launch_bounds__(256)
+k_cpr_presid(int nb, int bsr, const int *__restrict__ ptr, const int *__restrict__ col,
+             const double *__restrict__ pcol, const double *__restrict__ p, const double *__restrict__ f,
+             double *__restrict__ t, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    const int bs = BS > 0 ? BS : bsr;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nb * bs) return;
+    const int I = (int)(i / bs), r = (int)(i % bs);
+    double acc = 0.0;
+    for (int q = ptr[I]; q < ptr[I + 1]; ++q) acc = fma(pcol[(size_t)q * bs + r], __ldg(p + col[q]), acc);
+    t[i] = __dsub_rn(f[i], acc);
+}
+
+// z = Pi_p p + t: prolongation and the second stage's correction in one pass
+__global__ void k_prolong_add(int nb, int bs, const double *__restrict__ p, const double *__restrict__ t,
+                              double *__restrict__ z, const int *skip)
+{
+    if (skip && *(volatile const int *)skip) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nb * bs;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(i / bs), k = (int)(i % bs);
+        z[i] = k == 0 ? __dadd_rn(p[I], t[i]) : t[i];
+    }
+}
+
 static int grid_for(rs_ctx *ctx, int64_t n)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8));
@@ -79,7 +121,7 @@ static int grid_for(rs_ctx *ctx, int64_t n)
 // block ILU(0) of the full system; 'P' = Pi_p M_p^{-1} (Pi_r v), quasi-IMPES
 // restriction (the identity on a scalar matrix), the pressure solve (ILU(0)
 // of the decoupled matrix, or the network) and prolongation.
-static int cpr_stage(rs_pc *M, char kind, const double *v, double *out, const int *skip)
+static int cpr_stage(rs_pc *M, char kind, const double *v, double *out, const int *skip, bool prolong = true)
 {
     rs_ctx *ctx = M->ctx;
     const rs_mat *A = M->A;
@@ -96,11 +138,36 @@ static int cpr_stage(rs_pc *M, char kind, const double *v, double *out, const in
     if (M->type == RS_PC_CPR_LEARNED) RS_TRY(rs_net_apply_pressure(M, rp, zp, skip));
     else if (M->amg) RS_TRY(rs_amg_apply(M->amg, rp, zp, skip));
     else RS_TRY(rs_ilu_apply(M->ilu, rp, zp, nullptr, skip));
-    if (bs > 1) {
+    if (bs > 1 && prolong) {
         k_prolong<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(nb, bs, M->zp, out, skip);
         RS_TRY(rs_check_launch(ctx));
     }
     return RS_OK;
+}
+
+// Alg. 6 (PF) on a block matrix: z1 = Pi_p M_p^{-1} Pi_r r stays in the
+// pressure vector zp; t1 = r - A z1 takes the pressure column of A only;
+// z = z1 + R(A)^{-1} t1 in one pass.  Equal to the general sequence up to
+// the sign of zero results.
+static int cpr_apply_pf_blocks(rs_pc *M, const double *r, double *z, const int *skip)
+{
+    rs_ctx *ctx = M->ctx;
+    const rs_mat *A = M->A;
+    const int nb = A->nrows, bs = A->bs;
+    RS_TRY(cpr_stage(M, 'P', r, nullptr, skip, false));
+    {
+        RsProfScope prof(ctx, RS_PROF_CPR_RESID);
+        const int64_t threads = (int64_t)A->n;
+        const int grid = (int)((threads + 255) / 256);
+        if (bs == 3)
+            k_cpr_presid<3><<<grid, 256, 0, ctx->stream>>>(nb, 3, A->ptr, A->col, M->pcol, M->zp, r, M->t1, skip);
+        else
+            k_cpr_presid<0><<<grid, 256, 0, ctx->stream>>>(nb, bs, A->ptr, A->col, M->pcol, M->zp, r, M->t1, skip);
+        RS_TRY(rs_check_launch(ctx));
+    }
+    RS_TRY(cpr_stage(M, 'F', M->t1, M->t2, skip));
+    k_prolong_add<<<grid_for(ctx, A->n), 256, 0, ctx->stream>>>(nb, bs, M->zp, M->t2, z, skip);
+    return rs_check_launch(ctx);
 }
 
 // Algs. 5-8: the first stage maps f to z; every later stage forms
@@ -111,6 +178,7 @@ static int cpr_apply(rs_pc *M, const double *r, double *z, const int *skip)
     const rs_mat *A = M->A;
     static const char *forms[4] = {"PF", "FP", "FPF", "FFPF"};
     const char *seq = forms[M->form];
+    if (M->pcol) return cpr_apply_pf_blocks(M, r, z, skip);
     RS_TRY(cpr_stage(M, seq[0], r, z, skip));
     for (int k = 1; seq[k]; ++k) {
         RS_TRY(rs_residual_launch(A, r, z, M->t1, nullptr, skip));
@@ -226,6 +294,7 @@ static void pc_free(rs_pc *M)
     rs_free(ctx, M->zp);
     rs_free(ctx, M->t1);
     rs_free(ctx, M->t2);
+    rs_free(ctx, M->pcol);
     delete M;
 }
 
@@ -350,6 +419,13 @@ extern "C" int rs_precond_setup(rs_ctx *ctx, const rs_mat *A, int type, const rs
         if (!st) st = rs_alloc(ctx, (void **)&M->app_val, sizeof(double) * (A->nnzb > 0 ? A->nnzb : 1));
         if (!st) st = rs_alloc(ctx, (void **)&M->rp, sizeof(double) * (nb > 0 ? nb : 1));
         if (!st) st = rs_alloc(ctx, (void **)&M->zp, sizeof(double) * (nb > 0 ? nb : 1));
+        if (!st && M->form == RS_CPR_PF) {
+            st = rs_alloc(ctx, (void **)&M->pcol, sizeof(double) * bs * (A->nnzb > 0 ? A->nnzb : 1));
+            if (!st && A->nnzb > 0) {
+                k_pcol_gather<<<grid_for(ctx, A->nnzb * bs), 256, 0, ctx->stream>>>(A->nnzb, bs, A->val, M->pcol);
+                st = rs_check_launch(ctx);
+            }
+        }
         if (st) break;
         if (!st && fras) {
             // positions of the diagonal blocks, for the quasi-IMPES weights

@@ -310,6 +310,25 @@ def test_cpr_apply(rs, ctx, orc, prec):
     assert rel(z.numpy(), Mo.apply(f)) <= (1e-12 if prec == "fp64" else 1e-5)
 
 
+@pytest.mark.parametrize("form", ["pf", "fp"])
+def test_cpr_apply_two_unknowns_per_cell(rs, ctx, orc, form):
+    """CPR on 2x2 blocks (the leading 2x2 of the black-oil blocks): the PF
+    residual after the pressure stage takes the pressure column of A only,
+    on the kernel for any block size; FP keeps the full products."""
+    m3 = synth.black_oil_bsr3(synth.Grid(11, 7, 5), 31)
+    b3 = m3["bval"].reshape(-1, 3, 3)
+    m = dict(nb=m3["nb"], bs=2, browptr=m3["browptr"], bcol=m3["bcol"],
+             bval=np.ascontiguousarray(b3[:, :2, :2]).reshape(-1))
+    A = rs.Mat.bsr(ctx, m)
+    Ao = orc.Mat.bsr(m)
+    M = rs.Precond(ctx, A, "cpr", form=form)
+    Mo = orc.PC(Ao, "cpr", form=form)
+    f = np.random.default_rng(32).standard_normal(A.n)
+    z = rs.Vec.zeros(ctx, A.n)
+    M.apply(vec(rs, ctx, f), z)
+    assert rel(z.numpy(), Mo.apply(f)) <= 1e-12
+
+
 def test_cpr_scalar_matrix(rs, ctx, orc):
     d = synth.pressure_7pt(synth.Grid(12, 10, 9), 14)
     A = rs.Mat.csr(ctx, d)
