@@ -80,13 +80,14 @@ struct rs_net {
     int nx, ny, nz;
     Level lv[NET_LEVELS];
     bf16 *act[NET_NLAYERS];                 // layer outputs
-    bf16 *up0;                              // the coarse decoder input upsampled to the finest level
-    // tensor maps of the finest-level inputs, encoded once per workspace
+    bf16 *up0;                              // a decoder's coarse input, upsampled to its level
+    // tensor maps of the tcgen05 convolutions' inputs, encoded once per workspace
     struct TmapEntry {
         const void *base;
+        int dims[3];
         int box[3];
         CUtensorMap m;
-    } tmaps[8];
+    } tmaps[16];
     int ntmaps;
     bf16 *pool[NET_LEVELS];                 // pooled inputs of e1a, e2a, e3a
     bf16 *g16a[NET_LEVELS], *g16b[NET_LEVELS], *g32[NET_LEVELS];
@@ -257,102 +258,164 @@ k_conv3(int D, int H, int W, const bf16 *__restrict__ X, const bf16 *__restrict_
 }
 
 // ---------------------------------------------------------------------------
-// first layer: 2 input channels (r / rms(r) and log k).  The 27 taps x 2
-// channels form the K dimension of the implicit GEMM (54, padded to 64):
-// each voxel's im2col row is gathered once from a 2-channel halo, so the
-// tensor cores see 4 k-steps per row instead of 27 taps padded to 16
-// channels each.
+// first layer: 2 input channels (r / rms(r) and log k), packed per voxel as
+// a pair of bfloat16.  The 27 taps x 2 channels form the K dimension of the
+// implicit GEMM (k = 2 t + c: 54, padded to 64), so the tensor cores see 4
+// k-steps per voxel row instead of 27 taps padded to 16 channels each; a k
+// pair (2t, 2t+1) is the packed word of the voxel at tap t, so the A
+// fragments are read from the halo directly.  Persistent blocks: the
+// weights are staged once, and the next brick's halo is loaded into
+// registers while the current one is computed.
 // ---------------------------------------------------------------------------
 #define FK 64            // packed K: k = 2 t + c
-#define FKS (FK + 8)     // shared-memory row stride (bf16) of the im2col and weight tiles
-__global__ void __launch_bounds__(CONV_THREADS)
+#define FKS (FK + 8)     // shared-memory row stride (bf16) of the weight tile
+#define FHR ((HVOX + CONV_THREADS - 1) / CONV_THREADS)   // halo words per thread
+
+// halo words of brick b for this thread: hc[u] packs (hx, hy, hz) of its
+// element u (0xFFFFFFFF past the halo)
+__device__ __forceinline__ void first_halo(unsigned (&h)[FHR], const unsigned (&hc)[FHR], int b, int nbricks, int D,
+                                           int H, int W, int ntx, int nty, const double *__restrict__ r,
+                                           const double *__restrict__ logk, double rsc)
+{
+    const int tx0 = (b % ntx) * TX - 1, ty0 = ((b / ntx) % nty) * TY - 1, tz0 = (b / (ntx * nty)) * TZ - 1;
+    double a[FHR], c[FHR];
+    bool in[FHR];
+#pragma unroll
+    for (int u = 0; u < FHR; ++u) {
+        const int gx = tx0 + (int)(hc[u] & 0xFF), gy = ty0 + (int)((hc[u] >> 8) & 0xFF),
+                  gz = tz0 + (int)((hc[u] >> 16) & 0xFF);
+        in[u] = b < nbricks && hc[u] != 0xFFFFFFFFu && (unsigned)gx < (unsigned)W && (unsigned)gy < (unsigned)H &&
+                (unsigned)gz < (unsigned)D;
+        const int64_t vi = in[u] ? ((int64_t)gz * H + gy) * W + gx : 0;
+        a[u] = in[u] ? r[vi] : 0.0;
+        c[u] = in[u] ? logk[vi] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < FHR; ++u) {
+        __nv_bfloat162 pr = __floats2bfloat162_rn((float)(a[u] * rsc), (float)c[u]);
+        h[u] = in[u] ? *(unsigned *)&pr : 0u;
+    }
+}
+
+// zero words behind the halo: a padding tap (t >= 27) reads at FPAD past a
+// voxel's tap-0 index, which always lands there
+#define FPAD HVOX
+#define FSH (((TZ - 1) * HY + TY - 1) * HX + 15 + FPAD + 1)
+
+__global__ void __launch_bounds__(CONV_THREADS, 4)
 k_conv3_first(int D, int H, int W, const double *__restrict__ r, const double *__restrict__ logk,
               const double *__restrict__ rscale, const bf16 *__restrict__ Wp, const float *__restrict__ bias,
               bf16 *__restrict__ Y, const int *skip)
 {
     if (skipped(skip)) return;
-    __shared__ __align__(16) bf16 sa[TX * TY * TZ * FKS];
     __shared__ __align__(16) bf16 sb[16 * FKS];
-    __shared__ unsigned sh[HVOX];
+    __shared__ unsigned sh[FSH];            // the halo, then zeros for the padding taps
+    __shared__ __align__(16) bf16 so[TVOX * 16];   // the output brick, [row][x][channel]
+    __shared__ float sbias[16];
     const int ntx = (W + TX - 1) / TX, nty = (H + TY - 1) / TY;
-    int b = blockIdx.x;
-    const int tx0 = (b % ntx) * TX;
-    b /= ntx;
-    const int ty0 = (b % nty) * TY, tz0 = (b / nty) * TZ;
+    const int nbricks = ntx * nty * ((D + TZ - 1) / TZ);
     // weights: sb[co][2 t + c] = W[t][co][c] (forward layout [27][16][16], c < 2)
-    for (int i = threadIdx.x; i < 16 * FK; i += blockDim.x) {
-        const int co = i / FK, k = i % FK;
-        sb[co * FKS + k] = k < 54 ? Wp[((k >> 1) * 16 + co) * 16 + (k & 1)] : __float2bfloat16_rn(0.f);
-    }
-    // halo: (r * rscale, log k) as bfloat16 pairs, zero outside the grid
-    const double rsc = *rscale;
-    for (int hv = threadIdx.x; hv < HVOX; hv += blockDim.x) {
-        const int hx = hv % HX, hy = (hv / HX) % HY, hz = hv / (HX * HY);
-        const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
-        unsigned val = 0u;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D) {
-            const int64_t vi = ((int64_t)gz * H + gy) * W + gx;
-            __nv_bfloat162 pr = __floats2bfloat162_rn((float)(r[vi] * rsc), (float)logk[vi]);
-            val = *(unsigned *)&pr;
-        }
-        sh[hv] = val;
-    }
-    __syncthreads();
-    // im2col: thread v builds the row of brick voxel v = (lz TY + ly) TX + lx
     {
-        const int v = threadIdx.x;
-        const int lx = v % TX, ly = (v / TX) % TY, lz = v / (TX * TY);
-        unsigned *row = (unsigned *)(sa + v * FKS);
+        bf16 wv[16 * FK / CONV_THREADS];
 #pragma unroll
-        for (int t = 0; t < 27; ++t) {
-            const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-            row[t] = sh[((lz + dz) * HY + (ly + dy)) * HX + lx + dx];
+        for (int u = 0; u < 16 * FK / CONV_THREADS; ++u) {
+            const int i = threadIdx.x + u * CONV_THREADS, co = i / FK, k = i % FK;
+            wv[u] = k < 54 ? Wp[((k >> 1) * 16 + co) * 16 + (k & 1)] : __float2bfloat16_rn(0.f);
         }
 #pragma unroll
-        for (int t = 27; t < FK / 2; ++t) row[t] = 0u;
+        for (int u = 0; u < 16 * FK / CONV_THREADS; ++u) {
+            const int i = threadIdx.x + u * CONV_THREADS;
+            sb[(i / FK) * FKS + i % FK] = wv[u];
+        }
     }
-    __syncthreads();
+    if (threadIdx.x < 16) sbias[threadIdx.x] = bias[threadIdx.x];
+    for (int i = HVOX + threadIdx.x; i < FSH; i += blockDim.x) sh[i] = 0u;
+    const double rsc = *rscale;
+    // brick-invariant: this thread's halo elements and fragment offsets
+    unsigned hc[FHR];
+#pragma unroll
+    for (int u = 0; u < FHR; ++u) {
+        const int hv = threadIdx.x + u * CONV_THREADS;
+        hc[u] = hv < HVOX ? (unsigned)(hv % HX) | ((unsigned)((hv / HX) % HY) << 8) | ((unsigned)(hv / (HX * HY)) << 16)
+                          : 0xFFFFFFFFu;
+    }
+    unsigned hreg[FHR];
+    first_halo(hreg, hc, blockIdx.x, nbricks, D, H, W, ntx, nty, r, logk, rsc);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = lane >> 3, rr = lane & 7;
-    float acc[2][2][4];
+    const int g = lane >> 2, tq = lane & 3;
+    // tap offsets of this thread's k pairs, per k-step and half (padding taps: FPAD)
+    int toff[FK / 16][2];
 #pragma unroll
-    for (int m = 0; m < 2; ++m)
+    for (int kc = 0; kc < FK / 16; ++kc)
 #pragma unroll
-        for (int n = 0; n < 2; ++n)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[m][n][j] = 0.f;
-#pragma unroll
-    for (int kc = 0; kc < FK / 16; ++kc) {
-        unsigned b00, b01, b10, b11;
-        ldsm_x4(b00, b01, b10, b11, sb + ((q >> 1) * 8 + rr) * FKS + kc * 16 + (q & 1) * 8);
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const int row = warp * 2 + m;
-            unsigned a0, a1, a2, a3;
-            ldsm_x4(a0, a1, a2, a3, sa + (row * TX + rr + (q & 1) * 8) * FKS + kc * 16 + (q >> 1) * 8);
-            mma_bf16(acc[m][0], a0, a1, a2, a3, b00, b01);
-            mma_bf16(acc[m][1], a0, a1, a2, a3, b10, b11);
+        for (int h = 0; h < 2; ++h) {
+            const int t = 8 * kc + tq + 4 * h;
+            toff[kc][h] = t < 27 ? ((t / 9) * HY + (t / 3) % 3) * HX + t % 3 : FPAD;
         }
-    }
+    int vbase[2];                            // halo index of voxel x = g at tap 0, per M tile
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
         const int row = warp * 2 + m;
-        const int gy = ty0 + row % TY, gz = tz0 + row / TY;
-        if (gy >= H || gz >= D) continue;
+        vbase[m] = ((row / TY) * HY + row % TY) * HX + g;
+    }
+    for (int b = blockIdx.x; b < nbricks; b += gridDim.x) {
+        const int tx0 = (b % ntx) * TX, ty0 = ((b / ntx) % nty) * TY, tz0 = (b / (ntx * nty)) * TZ;
+        __syncthreads();                     // the previous brick's reads of sh and so are done
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int gx = tx0 + (lane >> 2) + half * 8;
-            if (gx >= W) continue;
-            const int64_t vi = ((int64_t)gz * H + gy) * W + gx;
+        for (int u = 0; u < FHR; ++u) {
+            const int hv = threadIdx.x + u * CONV_THREADS;
+            if (hv < HVOX) sh[hv] = hreg[u];
+        }
+        __syncthreads();
+        first_halo(hreg, hc, b + gridDim.x, nbricks, D, H, W, ntx, nty, r, logk, rsc);   // in flight during the MMAs
+
+        float acc[2][2][4];
 #pragma unroll
-            for (int n = 0; n < 2; ++n) {
-                const int co = n * 8 + (lane & 3) * 2;
-                float v0 = acc[m][n][half * 2] + bias[co], v1 = acc[m][n][half * 2 + 1] + bias[co + 1];
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
-                *(__nv_bfloat162 *)(Y + vi * 16 + co) = __floats2bfloat162_rn(v0, v1);
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int n = 0; n < 2; ++n)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[m][n][j] = 0.f;
+#pragma unroll
+        for (int kc = 0; kc < FK / 16; ++kc) {
+            unsigned b00, b01, b10, b11;
+            ldsm_x4(b00, b01, b10, b11, sb + ((q >> 1) * 8 + rr) * FKS + kc * 16 + (q & 1) * 8);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                // A fragment: rows g and g + 8 (x), k pairs 2 tq and 2 tq + 8
+                const unsigned *p0 = sh + vbase[m] + toff[kc][0], *p1 = sh + vbase[m] + toff[kc][1];
+                mma_bf16(acc[m][0], p0[0], p0[8], p1[0], p1[8], b00, b01);
+                mma_bf16(acc[m][1], p0[0], p0[8], p1[0], p1[8], b10, b11);
             }
+        }
+        // bias and ReLU into the staged brick, then 16-byte stores: a row of
+        // 16 x is 512 contiguous bytes of Y
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int row = warp * 2 + m;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int lx = (lane >> 2) + half * 8;
+#pragma unroll
+                for (int n = 0; n < 2; ++n) {
+                    const int co = n * 8 + (lane & 3) * 2;
+                    float v0 = acc[m][n][half * 2] + sbias[co], v1 = acc[m][n][half * 2 + 1] + sbias[co + 1];
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                    *(__nv_bfloat162 *)(so + (row * TX + lx) * 16 + co) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < TVOX * 2 / CONV_THREADS; ++u) {
+            const int c = threadIdx.x + u * CONV_THREADS;
+            const int v = c >> 1, row = v / TX, lx = v % TX;
+            const int gx = tx0 + lx, gy = ty0 + row % TY, gz = tz0 + row / TY;
+            if (gx < W && gy < H && gz < D)
+                *(uint4 *)(Y + (((int64_t)gz * H + gy) * W + gx) * 16 + (c & 1) * 8) = *(const uint4 *)(so + c * 8);
         }
     }
 }
@@ -374,12 +437,17 @@ k_conv3_first(int D, int H, int W, const double *__restrict__ r, const double *_
 // channels are the next plane.  A tap only moves the start address (by
 // 16 dx + 160 dy + one z slab dz), so one copy of the halo serves all 27.
 //
-// A single thread issues one M = 128 MMA every ~150 cycles whatever N is;
-// at N = 16 that is a quarter of what the tensor pipe takes, so four warps
-// issue.  Warp roles, coupled only by mbarriers:
+// The tensor pipe takes an M = 128, K = 16 MMA about every 42 cycles per SM
+// for N up to 32, so N = 16 caps the rate at a quarter of the dense peak.
+// The N dimension therefore stacks the brick's two z-planes: a halo plane hz
+// at tap (dy, dx) meets the weights of tap dz = hz - z for output plane z, so
+// one MMA with B = [W(hz) | W(hz - 1)] (zero blocks where dz is out of
+// range) serves both planes: 36 MMAs with N = 32 per brick and 16-channel
+// chunk instead of 54 with N = 16.  A single thread issues one MMA every
+// ~150 cycles, so four warps issue.  Warp roles, coupled only by mbarriers:
 //   warps 0-3   MMA issue (lane 0).  Warp w owns accumulator w of each TMEM
-//               set: a z-plane and half of the taps (16 input channels), or a
-//               quarter of the taps (32); the partial sums meet in the epilogue.
+//               set: halo plane w, both output planes; the four partial sums
+//               meet in the epilogue.
 //   warps 4-11  epilogue: tcgen05.ld of the partials, bias, ReLU, bf16 stores;
 //               a warp reads TMEM lanes 32 (warp mod 4) + 0..31.
 //   warp 12     producer (lane 0): TMA box loads into an NBUF-slot ring.
@@ -389,19 +457,21 @@ k_conv3_first(int D, int H, int W, const double *__restrict__ r, const double *_
 // ---------------------------------------------------------------------------
 template <int CIN>
 struct TcCfg {
-    static constexpr int BX = 8, BY = 16, BZ = CIN == 16 ? 2 : 1;
+    static constexpr int BX = 8, BY = 16, BZ = 2;
     static constexpr int HXb = BX + 2, HYb = BY + 2, HZb = BZ + 2;
     static constexpr int RS = HXb * 16;                      // bytes of one halo row (10 x, 8 channels)
     static constexpr int BOX = HZb * HYb * RS;               // bytes of one plane's TMA box
     static constexpr int PB = (BOX + 127) / 128 * 128;      // plane stride in shared memory
     static constexpr int NP = CIN / 8, KC = CIN / 16;
     static constexpr int SLOT = NP * PB;
-    static constexpr int NBUF = CIN == 16 ? 6 : 5;
-    static constexpr int WB = 27 * KC * 512;                // weights [t][kc][k half][co][8]
+    static constexpr int NBUF = CIN == 16 ? 6 : 3;
+    // weights: [hz][dy dx][kc][k half][n = 16 z + co][8 channels], 1 KB a block
+    static constexpr int WB = 4 * 9 * KC * 1024;
     static constexpr int SMEM = NBUF * SLOT + WB;
-    static constexpr int NGR = CIN == 16 ? 2 : 4;           // tap groups per z-plane (one issuer each)
-    static constexpr int TPG = (27 + NGR - 1) / NGR;        // taps per group
-    static constexpr int NSET = 4, SET_COLS = 64, TMEM_COLS = 256;
+    static constexpr int ACC_COLS = 32;                     // one issuer's accumulator (N = 32)
+    static constexpr int NSET = 4, SET_COLS = 4 * ACC_COLS, TMEM_COLS = NSET * SET_COLS;
+    static_assert(TMEM_COLS <= 512, "one CTA per SM holds all of TMEM at most");
+    static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
     static constexpr int THREADS = 13 * 32;
 };
 
@@ -413,8 +483,8 @@ __device__ __forceinline__ uint64_t tc_desc(unsigned addr, unsigned lbo, unsigne
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = 16, M = 128
-#define TC_IDESC ((1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24))
+// instruction descriptor: F32 accumulate, BF16 A and B, both K-major, M = 128
+#define TC_IDESC(N) ((1u << 4) | (1u << 7) | (1u << 10) | (((unsigned)(N) >> 3) << 17) | ((128u >> 4) << 24))
 
 // TMA: one box of a 4-D tensor map (coordinates innermost first) into shared memory
 __device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
@@ -426,32 +496,31 @@ __device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *map, int
                  : "memory");
 }
 
+template <int N>
 __device__ __forceinline__ void tc_mma(uint32_t tacc, uint64_t da, uint64_t db, unsigned accumulate)
 {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tacc),
-                 "l"(da), "l"(db), "r"(TC_IDESC), "r"(accumulate)
+                 "l"(da), "l"(db), "r"(TC_IDESC(N)), "r"(accumulate)
                  : "memory");
 }
 
-// the MMAs of issuer WI for one brick: z-plane WI / NGR, taps of group WI % NGR;
-// fully unrolled, so each descriptor is the slot's base plus a constant
+// the MMAs of issuer WI for one brick: halo plane WI at the nine (dy, dx) and
+// each 16-channel chunk, N = 32 (both output planes).  With one chunk the
+// loop is unrolled (each descriptor is the slot's base plus a constant);
+// with two it is not, which keeps the descriptors out of registers.
 template <int CIN, int WI>
 __device__ __forceinline__ void tc_issue(uint32_t tacc, uint64_t dA0, uint64_t dB0)
 {
     typedef TcCfg<CIN> C;
-    constexpr int z = WI / C::NGR, g = WI % C::NGR;
+#pragma unroll(C::KC == 1 ? 9 : 1)
+    for (int j = 0; j < 9; ++j) {
+        const int dy = j / 3, dx = j % 3;
 #pragma unroll
-    for (int i = 0; i < C::TPG; ++i) {
-        const int t = g * C::TPG + i;
-        if (t < 27) {
-            const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-#pragma unroll
-            for (int kc = 0; kc < C::KC; ++kc) {
-                const uint64_t da = dA0 + (uint64_t)((2 * kc * C::PB + ((z + dz) * C::HYb + dy) * C::RS + dx * 16) >> 4);
-                const uint64_t db = dB0 + (uint64_t)(((t * C::KC + kc) * 512) >> 4);
-                tc_mma(tacc, da, db, (i | kc) ? 1u : 0u);
-            }
+        for (int kc = 0; kc < C::KC; ++kc) {
+            const uint64_t da = dA0 + (uint64_t)((2 * kc * C::PB + (WI * C::HYb + dy) * C::RS + dx * 16) >> 4);
+            const uint64_t db = dB0 + (uint64_t)((((WI * 9 + j) * C::KC + kc) * 1024) >> 4);
+            tc_mma<32>(tacc, da, db, (j | kc) ? 1u : 0u);
         }
     }
 }
@@ -460,7 +529,8 @@ template <int CIN>
 __global__ void __launch_bounds__(TcCfg<CIN>::THREADS, 1)
 k_conv3_tc(int D, int H, int W, const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap umap,
            const bf16 *__restrict__ Wp, const float *__restrict__ bias, bf16 *__restrict__ Y, int *err,
-           long long limit, const int *skip)
+           long long limit, const int *skip, const float *__restrict__ wh, const double *__restrict__ scal,
+           float out_scale, double *__restrict__ out, int *flag)
 {
     typedef TcCfg<CIN> C;
     if (skipped(skip)) return;
@@ -469,18 +539,28 @@ k_conv3_tc(int D, int H, int W, const __grid_constant__ CUtensorMap xmap, const 
     unsigned char *wts = tc_smem + C::NBUF * C::SLOT;      // WB
     __shared__ uint32_t tmem_base;
     __shared__ __align__(8) unsigned long long full[C::NBUF], empty[C::NBUF], tfull[C::NSET], tempty[C::NSET];
-    __shared__ float sbias[16];
+    __shared__ float sbias[16], swh[17];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // with wh (16 input channels only) the output head is applied in the
+    // epilogue and out written instead of Y: out[v] = (sum_c wh[c] y[v][c] +
+    // wh[16]) rms s, summed in channel order, non-finite values flagged
+    const bool head = CIN == 16 && wh != nullptr;
     const int nbx = (W + C::BX - 1) / C::BX, nby = (H + C::BY - 1) / C::BY, nbz = (D + C::BZ - 1) / C::BZ;
     const int nbricks = nbx * nby * nbz;
     const int nmine = blockIdx.x < nbricks ? (nbricks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-    for (int i = tid; i < 27 * 16 * C::NP; i += blockDim.x) {
-        const int t = i / (16 * C::NP), co = (i / C::NP) % 16, pl = i % C::NP;
-        const uint4 v = *(const uint4 *)(Wp + ((size_t)t * 16 + co) * CIN + pl * 8);
-        *(uint4 *)(wts + (t * C::KC + (pl >> 1)) * 512 + (pl & 1) * 256 + (co >> 3) * 128 + (co & 7) * 16) = v;
+    // block (hz, dy dx, kc), column n = 16 z + co: W[dz = hz - z][dy][dx][co], zero for dz outside 0..2
+    for (int i = tid; i < 36 * C::KC * 32 * 2; i += blockDim.x) {
+        const int blk = i / 64, n = (i / 2) % 32, kh = i % 2;
+        const int kc = blk % C::KC, hz = blk / (9 * C::KC), j = (blk / C::KC) % 9, z = n >> 4, co = n & 15,
+                  dz = hz - z;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (dz >= 0 && dz <= 2)
+            v = *(const uint4 *)(Wp + ((size_t)(dz * 9 + j) * 16 + co) * CIN + kc * 16 + kh * 8);
+        *(uint4 *)(wts + blk * 1024 + kh * 512 + (n >> 3) * 128 + (n & 7) * 16) = v;
     }
     if (tid < 16) sbias[tid] = bias[tid];
+    if (head && tid < 17) swh[tid] = wh[tid];
     if (tid == 0) {
         for (int k = 0; k < C::NBUF; ++k) {
             mbar_init(&full[k], 1);
@@ -526,13 +606,14 @@ k_conv3_tc(int D, int H, int W, const __grid_constant__ CUtensorMap xmap, const 
     } else if (warp < 4) {
         // MMA issue
         if (lane == 0) {
-            const uint64_t dB0 = tc_desc(smem_u32(wts), 256, 128);
+            // B: the k halves of a block are 512 bytes apart, 8-column groups 128
+            const uint64_t dB0 = tc_desc(smem_u32(wts), 512, 128);
             for (int k = 0; k < nmine; ++k) {
                 const int slot = k % C::NBUF, set = k % C::NSET;
                 mbar_wait(&full[slot], (unsigned)((k / C::NBUF) & 1), limit, err);
                 if (k >= C::NSET) mbar_wait(&tempty[set], (unsigned)((k / C::NSET - 1) & 1), limit, err);
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t tacc = tmem_base + set * C::SET_COLS + warp * 16;
+                const uint32_t tacc = tmem_base + set * C::SET_COLS + warp * C::ACC_COLS;
                 const uint64_t dA0 = tc_desc(smem_u32(bufs + slot * C::SLOT), C::PB, C::RS);
                 switch (warp) {
                 case 0: tc_issue<CIN, 0>(tacc, dA0, dB0); break;
@@ -568,9 +649,10 @@ k_conv3_tc(int D, int H, int W, const __grid_constant__ CUtensorMap xmap, const 
 #pragma unroll
             for (int j = 0; j < NCOL; ++j) f[j] = sbias[c0 + j];
 #pragma unroll
-            for (int g = 0; g < C::NGR; ++g) {
-                const uint32_t ta =
-                    tmem_base + ((uint32_t)(q * 32) << 16) + set * C::SET_COLS + (z * C::NGR + g) * 16 + c0;
+            for (int g = 0; g < 4; ++g) {
+                // issuer g's partial: plane z of its N = 32 accumulator, or its 16 columns
+                const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + set * C::SET_COLS +
+                                    g * C::ACC_COLS + z * 16;
                 uint32_t v[16];
                 if constexpr (NCOL == 16) {
                     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -599,6 +681,21 @@ k_conv3_tc(int D, int H, int W, const __grid_constant__ CUtensorMap xmap, const 
                 for (int j = 0; j < NCOL / 2; ++j) {
                     __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(f[2 * j], 0.f), fmaxf(f[2 * j + 1], 0.f));
                     packed[j] = *(unsigned *)&h;
+                }
+                if constexpr (NCOL == 16) {
+                    if (head) {
+                        float hs = swh[16];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const __nv_bfloat162 h = *(const __nv_bfloat162 *)&packed[j];
+                            hs = fmaf(swh[2 * j], __low2float(h), hs);
+                            hs = fmaf(swh[2 * j + 1], __high2float(h), hs);
+                        }
+                        const double o = (double)hs * (scal[0] * (double)out_scale);
+                        out[vi] = o;
+                        if (!isfinite(o)) atomicOr(flag, 1);
+                        continue;
+                    }
                 }
                 uint4 *dst = (uint4 *)(Y + vi * 16 + c0);
                 dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
@@ -738,23 +835,38 @@ __global__ void k_dw_reduce(int nblocks, int cin, int cinp, const float *__restr
 // ---------------------------------------------------------------------------
 // element-wise kernels
 // ---------------------------------------------------------------------------
-// 2x2x2 average pooling of a 16-channel tensor
+// 2x2x2 average pooling of a 16-channel tensor: a thread per coarse voxel and
+// 8-channel half, 16-byte loads; per channel the eight inputs are summed in
+// FP32 in (dz, dy, dx) order
 __global__ void k_avgpool(int Dc, int Hc, int Wc, const bf16 *__restrict__ X, bf16 *__restrict__ Y, const int *skip)
 {
     if (skipped(skip)) return;
-    const int64_t n = (int64_t)Dc * Hc * Wc * 16;
+    const int64_t n = (int64_t)Dc * Hc * Wc * 2;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % 16);
-        const int64_t vc = i / 16;
+        const int h = (int)(i & 1);
+        const int64_t vc = i >> 1;
         const int x = (int)(vc % Wc), y = (int)((vc / Wc) % Hc), z = (int)(vc / ((int64_t)Wc * Hc));
         const int W = Wc * 2, H = Hc * 2;
-        float s = 0.f;
+        uint4 in[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int64_t vf = ((int64_t)(2 * z + (k >> 2)) * H + (2 * y + ((k >> 1) & 1))) * W + 2 * x + (k & 1);
-            s += __bfloat162float(X[vf * 16 + c]);
+            in[k] = *(const uint4 *)(X + vf * 16 + h * 8);
         }
-        Y[i] = __float2bfloat16_rn(s * 0.125f);
+        unsigned outw[4];
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const bf16 *e = (const bf16 *)&in[k];
+                s0 += __bfloat162float(e[c]);
+                s1 += __bfloat162float(e[c + 1]);
+            }
+            __nv_bfloat162 pr = __floats2bfloat162_rn(s0 * 0.125f, s1 * 0.125f);
+            outw[c >> 1] = *(unsigned *)&pr;
+        }
+        *(uint4 *)(Y + vc * 16 + h * 8) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
     }
 }
 
@@ -809,8 +921,25 @@ k_rms(int64_t n, const double *__restrict__ r, double *red, unsigned *ticket, do
     __shared__ double sm[8];
     __shared__ bool last;
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s = fma(r[i], r[i], s);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (((uintptr_t)r & 15) == 0) {
+        // four 16-byte loads in flight per thread (n is even: the grid's
+        // sides are multiples of 8)
+        const int64_t n2 = n / 2;
+        const double2 *r2 = (const double2 *)r;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += 4 * stride) {
+            double2 a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = i + u * stride < n2 ? r2[i + u * stride] : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s = fma(a[u].x, a[u].x, s);
+                s = fma(a[u].y, a[u].y, s);
+            }
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) s = fma(r[i], r[i], s);
+    }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -822,12 +951,16 @@ k_rms(int64_t n, const double *__restrict__ r, double *red, unsigned *ticket, do
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x >= 32) return;
+    if (!last) return;
     __threadfence();
     double t = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += __ldcg(red + b);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(red + b);
     t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sm[w];
         double rms = sqrt(t / (double)n);
         if (!(rms > 0.0) || !isfinite(rms)) rms = 1.0;
         scal[0] = rms;
@@ -1048,22 +1181,26 @@ static int make_tmap(CUtensorMap *m, const bf16 *base, int C, int W, int H, int 
     return r == CUDA_SUCCESS ? RS_OK : RS_ERR_CUDA;
 }
 
-// the tensor map of a finest-level buffer, encoded on first use (the buffers
+// the tensor map of a workspace buffer, encoded on first use (the buffers
 // live as long as the workspace, which clears the cache)
 static int cached_tmap(rs_net *net, const CUtensorMap **out, const bf16 *base, int W, int H, int D, int bx, int by,
                        int bz)
 {
     for (int k = 0; k < net->ntmaps; ++k) {
         const rs_net::TmapEntry &e = net->tmaps[k];
-        if (e.base == base && e.box[0] == bx && e.box[1] == by && e.box[2] == bz) {
+        if (e.base == base && e.dims[0] == W && e.dims[1] == H && e.dims[2] == D && e.box[0] == bx &&
+            e.box[1] == by && e.box[2] == bz) {
             *out = &e.m;
             return RS_OK;
         }
     }
-    if (net->ntmaps == 8) net->ntmaps = 0;       // more maps than expected: start over
+    if (net->ntmaps == 16) net->ntmaps = 0;      // more maps than expected: start over
     rs_net::TmapEntry &e = net->tmaps[net->ntmaps];
     RS_TRY(make_tmap(&e.m, base, 16, W, H, D, bx, by, bz));
     e.base = base;
+    e.dims[0] = W;
+    e.dims[1] = H;
+    e.dims[2] = D;
     e.box[0] = bx;
     e.box[1] = by;
     e.box[2] = bz;
@@ -1148,14 +1285,27 @@ static int pack_all(rs_net *net)
 }
 
 // launches one forward convolution of layer l
+// The finest level's forward convolutions run on tcgen05, and so do a
+// coarser level's when it has at least two of the kernel's bricks (8 x 16 x 2
+// voxels) per SM: with fewer, the persistent pipeline's prologue (weights,
+// TMEM allocation, first copies) is not amortised and mma.sync is as fast.
+static bool use_tc(const rs_net *net, int level)
+{
+    const Level &L = net->lv[level];
+    const int64_t bricks = (int64_t)((L.nx + 7) / 8) * ((L.ny + 15) / 16) * ((L.nz + 1) / 2);
+    return level == 0 || bricks >= 2 * (int64_t)net->ctx->num_sms;
+}
+
+// hout: the last layer applies the output head in its epilogue and writes
+// the network output there instead of Y (finest level, tcgen05 kernel only)
 static int conv_forward(rs_net *net, int l, const bf16 *X, const bf16 *U, const double *r, const double *logk,
-                        bf16 *Y, const int *skip)
+                        bf16 *Y, const int *skip, double *hout = nullptr)
 {
     rs_ctx *c = net->ctx;
     const Level &L = net->lv[kLayers[l].level];
     const int grid = (int)nbricks(L);
     const float *bias = net->p + net->boff[l];
-    if (kLayers[l].level == 0 && kLayers[l].mode != IN_FIRST) {
+    if (use_tc(net, kLayers[l].level) && kLayers[l].mode != IN_FIRST) {
         const CUtensorMap *xmap, *umap;
         if (kLayers[l].mode == IN_CATUP) {
             // the coarse input, upsampled to this level, is the first half of the concatenation
@@ -1166,20 +1316,23 @@ static int conv_forward(rs_net *net, int l, const bf16 *X, const bf16 *U, const 
             RS_TRY(rs_check_launch(c));
             const int nb = ((L.nx + TC::BX - 1) / TC::BX) * ((L.ny + TC::BY - 1) / TC::BY) * ((L.nz + TC::BZ - 1) / TC::BZ);
             k_conv3_tc<32><<<std::min(nb, c->num_sms), TC::THREADS, TC::SMEM, c->stream>>>(
-                L.nz, L.ny, L.nx, *xmap, *umap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip);
+                L.nz, L.ny, L.nx, *xmap, *umap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip, nullptr,
+                nullptr, 0.f, nullptr, nullptr);
         } else {
             typedef TcCfg<16> TC;
             RS_TRY(cached_tmap(net, &xmap, X, L.nx, L.ny, L.nz, TC::HXb, TC::HYb, TC::HZb));
             const int nb = ((L.nx + TC::BX - 1) / TC::BX) * ((L.ny + TC::BY - 1) / TC::BY) * ((L.nz + TC::BZ - 1) / TC::BZ);
             k_conv3_tc<16><<<std::min(nb, c->num_sms), TC::THREADS, TC::SMEM, c->stream>>>(
-                L.nz, L.ny, L.nx, *xmap, *xmap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip);
+                L.nz, L.ny, L.nx, *xmap, *xmap, net->wf[l], bias, Y, c->d_err, c->spin_limit, skip,
+                hout ? net->p + net->hoff : nullptr, net->scal, net->out_scale, hout, net->flag);
         }
         return rs_check_launch(c);
     }
+    if (hout) return RS_ERR_INVALID_ARG;        // the head is fused on the tcgen05 path only
     switch (kLayers[l].mode) {
     case IN_FIRST:
-        k_conv3_first<<<grid, CONV_THREADS, 0, c->stream>>>(L.nz, L.ny, L.nx, r, logk, net->scal + 1, net->wf[l],
-                                                            bias, Y, skip);
+        k_conv3_first<<<std::min(grid, c->num_sms * 4), CONV_THREADS, 0, c->stream>>>(
+            L.nz, L.ny, L.nx, r, logk, net->scal + 1, net->wf[l], bias, Y, skip);
         break;
     case IN_CATUP:
         k_conv3<32, 16, IN_CATUP><<<grid, CONV_THREADS, conv_smem(32, 16), c->stream>>>(
@@ -1196,12 +1349,15 @@ static int pool_forward(rs_net *net, int lvl, const bf16 *X, bf16 *Y, const int 
 {
     rs_ctx *c = net->ctx;
     const Level &L = net->lv[lvl];
-    k_avgpool<<<ew_grid(c, L.nvox * 16), 256, 0, c->stream>>>(L.nz, L.ny, L.nx, X, Y, skip);
+    k_avgpool<<<ew_grid(c, L.nvox * 2), 256, 0, c->stream>>>(L.nz, L.ny, L.nx, X, Y, skip);
     return rs_check_launch(c);
 }
 
-// forward pass; out (FP64, nvox) = network(r, logk) * rms * out_scale
-static int net_forward(rs_net *net, const double *r, const double *logk, double *out, const int *skip)
+// forward pass; out (FP64, nvox) = network(r, logk) * rms * out_scale.
+// keep: the last layer's activations are kept for a backward pass; else the
+// output head runs in the last convolution's epilogue
+static int net_forward(rs_net *net, const double *r, const double *logk, double *out, const int *skip,
+                       bool keep = false)
 {
     rs_ctx *c = net->ctx;
     const int64_t n0 = net->lv[0].nvox;
@@ -1227,6 +1383,7 @@ static int net_forward(rs_net *net, const double *r, const double *logk, double 
     RS_TRY(conv_forward(net, D1A, A[E1B], A[D2B], nullptr, nullptr, A[D1A], skip));
     RS_TRY(conv_forward(net, D1B, A[D1A], nullptr, nullptr, nullptr, A[D1B], skip));
     RS_TRY(conv_forward(net, D0A, A[E0B], A[D1B], nullptr, nullptr, A[D0A], skip));
+    if (!keep) return conv_forward(net, D0B, A[D0A], nullptr, nullptr, nullptr, A[D0B], skip, out);
     RS_TRY(conv_forward(net, D0B, A[D0A], nullptr, nullptr, nullptr, A[D0B], skip));
     k_head<<<ew_grid(c, n0), 256, 0, c->stream>>>(n0, A[D0B], net->p + net->hoff, net->scal, net->out_scale, out,
                                                  net->flag, skip);
@@ -1476,7 +1633,7 @@ extern "C" int rs_net_accumulate(rs_net *net, int32_t nx, int32_t ny, int32_t nz
     RS_TRY(ensure_workspace(net, nx, ny, nz));
     rs_ctx *c = net->ctx;
     const int64_t n0 = net->lv[0].nvox;
-    RS_TRY(net_forward(net, r, logk, net->outb, nullptr));
+    RS_TRY(net_forward(net, r, logk, net->outb, nullptr, true));
     k_loss_sums<<<c->red_blocks, 256, 0, c->stream>>>(n0, net->outb, e, net->red, net->ticket, net->scal);
     k_loss_grad<<<ew_grid(c, n0), 256, 0, c->stream>>>(n0, net->outb, e, net->scal, weight, net->gout);
     c->launches++;

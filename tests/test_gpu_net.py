@@ -67,6 +67,23 @@ def test_forward_matches_oracle(rs, ctx, shape):
     assert rel(got, ref64) <= 5e-2
 
 
+def test_forward_matches_oracle_with_tcgen05_on_two_levels(rs, ctx):
+    """128 x 64 x 80: the second level (64 x 32 x 40) has 320 bricks of the
+    tcgen05 kernel, two per SM and more, so its convolutions (e1a, e1b, and
+    the decoder d1a with its upsampled input, d1b) run there too."""
+    import torch
+    from oracle import convnet as cn
+    shape = (128, 64, 80)
+    p = _params(3)
+    r, logk, _ = _fields(shape, 4)
+    net = rs.Net(ctx, p, out_scale=5.0)
+    out = torch.zeros(r.size, dtype=torch.float64, device="cuda")
+    net.forward(shape, _dev(r), _dev(logk), out)
+    got = out.cpu().numpy().reshape(r.shape)
+    ref, _ = cn.forward(p, r, logk, out_scale=5.0, bf16=True)
+    assert rel(got, ref) <= 2e-2, rel(got, ref)
+
+
 def test_gradients_match_oracle(rs, ctx):
     from oracle import convnet as cn
     shape = (16, 16, 8)
