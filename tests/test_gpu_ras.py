@@ -245,6 +245,9 @@ def test_cpr_ras_f_stage_on_a_scalar_matrix(rs, ctx, orc):
     ((20, 16, 12), (2, 2, 2), 1, (-1, 1e-3)),
     ((24, 20, 17), (3, 2, 1), 2, (3, 1e-2)),
     ((16, 16, 16), (1, 1, 1), 0, (-1, 1e-4)),
+    # nothing dropped: complete fill, several times the first output region,
+    # so the factorisation is repeated with doubled regions
+    ((10, 9, 8), (2, 1, 1), 1, (1000, 1e-300)),
 ])
 def test_ras_ilut_parity(rs, ctx, orc, shape, parts, overlap, ilut):
     g = synth.Grid(*shape)
