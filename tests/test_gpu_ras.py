@@ -277,6 +277,18 @@ def test_ras_ilut_parity(rs, ctx, orc, shape, parts, overlap, ilut):
     assert abs(info["iters"] - io["iters"]) <= 2, (info, io)
 
 
+def test_ras_ilut_zero_pivot_reports_the_global_row(rs, ctx, orc):
+    """Subdomain 1 holds rows 1 and 2 without overlap; its local row 1 has the
+    pivot 1 - 1 * 1 = 0, so ILUT stops there and reports global row 2."""
+    d = dict(n=3, rowptr=np.array([0, 2, 5, 7], np.int32), col=np.array([0, 1, 0, 1, 2, 1, 2], np.int32),
+             val=np.array([1.0, 2.0, 0.5, 1.0, 1.0, 1.0, 1.0]))
+    part = np.array([0, 1, 1], np.int32)
+    R = orc.Ras(orc.Mat.csr(d), 2, part=part, overlap=0, ilut=(-1, 1e-3))
+    assert R.status != 0
+    M = rs.Precond(ctx, rs.Mat.csr(ctx, d), "ras", nparts=2, part=part, overlap=0, ilut=(-1, 1e-3))
+    assert M.status == rs.ERR_ZERO_PIVOT and M.bad_row == 2
+
+
 def test_ras_ilut_rejected_on_blocks(rs, ctx):
     m = synth.black_oil_bsr3(synth.Grid(6, 5, 4), 65)
     with pytest.raises(rs.RsError) as e:
