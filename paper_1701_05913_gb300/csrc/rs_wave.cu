@@ -78,8 +78,15 @@ struct WaveCfg {
     template <bool LOWER>
     static constexpr int slot_bytes() { return G * 32 * ((LOWER ? RL : RU) + BS) * (int)sizeof(T); }
     static constexpr int ring_bytes() { return HR * 2 * 32 * BS * (int)sizeof(T); }
+    // FP64 block records: the components of a step are computed by BS warps,
+    // one component each (a warp's FP64 multiply-adds share one FP64 unit, so
+    // one warp doing all BS^2 per block is bound by that unit), exchanged
+    // through shared memory; one warp otherwise
+    static constexpr int NCW = (BS > 1 && sizeof(T) == 8) ? BS : 1;
+    static constexpr int THREADS = 32 * (NCW + 1);                   // + the producer warp
+    static constexpr int xbuf_bytes() { return NCW > 1 ? 2 * NCW * 32 * (int)sizeof(T) : 0; }
     template <bool LOWER>
-    static constexpr int smem_bytes() { return HDR_BYTES + R * slot_bytes<LOWER>() + ring_bytes(); }
+    static constexpr int smem_bytes() { return HDR_BYTES + R * slot_bytes<LOWER>() + ring_bytes() + xbuf_bytes(); }
 };
 
 // the block's shared header
@@ -239,7 +246,7 @@ __device__ __forceinline__ float lds_ho(const float *p)
 // after four limits plus RS_WAVE_DRAIN cycles; a poll of another unit's
 // value records it after the limit and carries the sentinel on from then.
 template <int BS, typename T, bool LOWER>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(WaveCfg<BS, T>::THREADS)
 k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T *xv)
 {
     using C = WaveCfg<BS, T>;
@@ -256,11 +263,14 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
     constexpr bits_t SENT = Sentinel<T>::bits;
     extern __shared__ __align__(128) unsigned char wave_smem[];
     if (g.skip && *(volatile const int *)g.skip) return;
+    constexpr int NCW = C::NCW;
     const int lane = threadIdx.x & 31;
-    const bool producer = threadIdx.x >= 32;
+    const int cw = threadIdx.x >> 5;          // compute warp (its component when NCW > 1)
+    const bool producer = cw == NCW;
     WaveHdr *hd = (WaveHdr *)wave_smem;
     unsigned char *slots = wave_smem + C::HDR_BYTES;
     T *ring = (T *)(slots + R * SLOT);       // [HR steps][z, y][32 lanes][BS]
+    T *xbuf = ring + (size_t)HR * 2 * 32 * BS;   // NCW > 1: [2 parities][NCW components][32 lanes]
     if (producer && lane == 0) {
         for (int q = 0; q < R; ++q) mbar_init(&hd->bar[q], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -473,6 +483,7 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
         T vprev[BS];
 #pragma unroll
         for (int k = 0; k < BS; ++k) vprev[k] = T(0);
+        if constexpr (NCW == 1) {
         for (int s0 = 0; s0 < g.npad; s0 += G) {
             wait(s0 / G);
             const unsigned char *sp = slots + (size_t)((s0 / G) % R) * SLOT;
@@ -550,6 +561,83 @@ k_wave_sweep(WaveArgs g, const T *__restrict__ rec, const T *__restrict__ rhs, T
                 for (int i = 0; i < BS; ++i) {
                     vprev[i] = acc[i];
                     st_poll(xout + (int64_t)32 * BS * t + i, acc[i]);
+                }
+            }
+        }
+        } else {
+            // NCW = BS warps: warp cw computes component cw of every cell of
+            // the step, in the single warp's order (so the values are the
+            // same), then the components meet in xbuf; one barrier per step
+            // (double-buffered by the step's parity)
+            const int ci = cw;
+            for (int s0 = 0; s0 < g.npad; s0 += G) {
+                wait(s0 / G);
+                const unsigned char *sp = slots + (size_t)((s0 / G) % R) * SLOT;
+                const T *hring = ring + ((size_t)((s0 & (HR - 1)) * 2) * 32 + lane) * BS;
+#pragma unroll
+                for (int kk = 0; kk < G; ++kk) {
+                    const int s = s0 + kk;
+                    const int t = LOWER ? s : g.npad - 1 - s;
+                    const int pos = LOWER ? kk : G - 1 - kk;
+                    // row ci of each of the record's blocks, and the right-hand side
+                    constexpr int NB = LOWER ? 3 : 4;
+                    T rv[NB * BS], bv[BS], bci;
+                    {
+                        const T *rp0 = (const T *)sp + (pos * 32 + lane) * RB + ci * BS;
+#pragma unroll
+                        for (int q = 0; q < NB; ++q)
+#pragma unroll
+                            for (int j = 0; j < BS; ++j) rv[q * BS + j] = rp0[q * B2 + j];
+                        const T *rp = (const T *)(sp + G * 32 * RB * sizeof(T)) + (pos * 32 + lane) * BS;
+#pragma unroll
+                        for (int k2 = 0; k2 < BS; ++k2) bv[k2] = rp[k2];
+                        bci = rp[ci];
+                    }
+                    T sy[BS], sz[BS];
+#pragma unroll
+                    for (int k2 = 0; k2 < BS; ++k2) {
+                        sy[k2] = LOWER ? __shfl_up_sync(FULL, vprev[k2], 1) : __shfl_down_sync(FULL, vprev[k2], 1);
+                        sz[k2] = LOWER ? __shfl_up_sync(FULL, vprev[k2], a) : __shfl_down_sync(FULL, vprev[k2], a);
+                    }
+                    // steps before s are done with by every compute warp (the
+                    // barrier of step s - 1 is behind all of them)
+                    if (cw == 0) st_cons(&hd->cons, (unsigned)s);
+                    if (avail <= (unsigned)s) avail = wait_prod(s);
+                    T vz[BS], vy[BS];
+#pragma unroll
+                    for (int k2 = 0; k2 < BS; ++k2) {
+                        const T *hp = hring + (size_t)kk * 2 * 32 * BS;
+                        const T hz = lds_ho(hp + k2), hy = lds_ho(hp + 32 * BS + k2);
+                        vy[k2] = yin ? sy[k2] : hy;
+                        vz[k2] = zin ? sz[k2] : hz;
+                    }
+                    T acc;
+                    if (LOWER) {
+                        acc = bci;
+#pragma unroll
+                        for (int j = 0; j < BS; ++j) acc = msub(acc, rv[j], vz[j]);
+#pragma unroll
+                        for (int j = 0; j < BS; ++j) acc = msub(acc, rv[BS + j], vy[j]);
+#pragma unroll
+                        for (int j = 0; j < BS; ++j) acc = msub(acc, rv[2 * BS + j], vprev[j]);
+                    } else {
+                        T sum = T(0);
+#pragma unroll
+                        for (int j = 0; j < BS; ++j) sum = mad(rv[3 * BS + j], bv[j], sum);
+                        acc = sum;
+#pragma unroll
+                        for (int j = 0; j < BS; ++j) acc = msub(acc, rv[j], vz[j]);
+#pragma unroll
+                        for (int j = 0; j < BS; ++j) acc = msub(acc, rv[BS + j], vprev[j]);
+#pragma unroll
+                        for (int j = 0; j < BS; ++j) acc = msub(acc, rv[2 * BS + j], vy[j]);
+                    }
+                    st_poll(xout + (int64_t)32 * BS * t + ci, acc);
+                    T *xb = xbuf + (size_t)(s & 1) * NCW * 32;
+                    xb[ci * 32 + lane] = acc;
+                    asm volatile("bar.sync 1, %0;" ::"r"(NCW * 32) : "memory");
+#pragma unroll
+                    for (int j = 0; j < BS; ++j) vprev[j] = xb[j * 32 + lane];
                 }
             }
         }
@@ -741,13 +829,13 @@ int wave_apply_t(IluFactor *f, const double *r, double *z, const double *scale, 
     {
         RsProfScope prof(ctx, BS == 1 ? RS_PROF_LSWEEP : RS_PROF_BLSWEEP);
         k_wave_in<BS, T><<<gp, WAVE_PERM_THREADS, 0, ctx->stream>>>(g, r, scale, (T *)W.rw, (T *)W.zw);
-        k_wave_sweep<BS, T, true><<<gw, 64, sl, ctx->stream>>>(g, (const T *)W.lrec, (const T *)W.rw,
+        k_wave_sweep<BS, T, true><<<gw, C::THREADS, sl, ctx->stream>>>(g, (const T *)W.lrec, (const T *)W.rw,
                                                                        (T *)W.yw);
     }
     RS_TRY(rs_check_launch(ctx));
     {
         RsProfScope prof(ctx, BS == 1 ? RS_PROF_USWEEP : RS_PROF_BUSWEEP);
-        k_wave_sweep<BS, T, false><<<gw, 64, su, ctx->stream>>>(g, (const T *)W.urec, (const T *)W.yw,
+        k_wave_sweep<BS, T, false><<<gw, C::THREADS, su, ctx->stream>>>(g, (const T *)W.urec, (const T *)W.yw,
                                                                         (T *)W.zw);
         k_wave_out<BS, T><<<gp, WAVE_PERM_THREADS, 0, ctx->stream>>>(g, (const T *)W.zw, (T *)W.yw, z);
     }
