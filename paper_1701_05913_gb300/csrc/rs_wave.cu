@@ -60,8 +60,9 @@ struct WaveCfg {
     static constexpr int VQ = 16 / (int)sizeof(T);                 // T per 16 bytes
     static constexpr int RL = (3 * B2 + VQ - 1) / VQ * VQ;           // L record: L_z, L_y, L_x
     static constexpr int RU = (4 * B2 + VQ - 1) / VQ * VQ;           // U record: U'_z, U'_x, U'_y, D
-    // steps per bulk-copy slot: about 10 KB per U slot
-    static constexpr int G0 = 10240 / (32 * (RU + BS) * (int)sizeof(T));
+    // steps per bulk-copy slot: about 10 KB per U slot (20 KB for FP64
+    // blocks, so that a slot holds two steps)
+    static constexpr int G0 = ((BS > 1 && sizeof(T) == 8) ? 20480 : 10240) / (32 * (RU + BS) * (int)sizeof(T));
     static constexpr int G = G0 >= 16 ? 16 : G0 >= 8 ? 8 : G0 >= 4 ? 4 : G0 >= 2 ? 2 : 1;
     static constexpr int R = 4;                                      // bulk-copy slots (WaveHdr::bar)
     // steps of hand-off values the producer polls at once: enough to keep
@@ -820,8 +821,12 @@ int wave_apply_t(IluFactor *f, const double *r, double *z, const double *scale, 
     const WaveLayout &W = f->W;
     const WaveArgs g = wave_args(ctx, W, f->state, skip);
     const int gp = W.nunits * ((W.npad + 31) / 32);
-    // one unit per block at a time; as many blocks as fit (about four per SM)
-    const int per_sm = std::max(1, std::min(8, (200 * 1024) / C::template smem_bytes<false>()));
+    // one unit per block at a time; up to about 200 KB of blocks per SM (at
+    // 128^3 the FP32 block sweeps were 2 % slower with four blocks per SM than
+    // with three), and as many of the large FP64-block blocks as fit in the
+    // SM's 228 KB (1 KB of it reserved per block)
+    const int per_sm = std::max(1, std::min(8, C::NCW > 1 ? (228 * 1024) / (C::template smem_bytes<false>() + 1024)
+                                                          : (200 * 1024) / C::template smem_bytes<false>()));
     const int gw = std::max(1, std::min(W.nunits, per_sm * ctx->num_sms));
     constexpr int sl = C::template smem_bytes<true>(), su = C::template smem_bytes<false>();
     RS_TRY((raise_sweep_smem<BS, T, true>(ctx)));
