@@ -164,6 +164,40 @@ def test_wave_block_ilu0_matches_oracle(rs, ctx, orc, shape):
         assert rel(z.numpy(), zs.numpy()) <= 2 * tol
 
 
+def _blocks_of_size(m3, bs):
+    """The black-oil 3x3 blocks cut to their leading 2x2 (bs 2), or padded to
+    4x4 with a fourth unknown coupled only to itself (bs 4, diagonal 2)."""
+    b3 = m3["bval"].reshape(-1, 3, 3)
+    if bs == 2:
+        bv = b3[:, :2, :2]
+    else:
+        bv = np.zeros((b3.shape[0], 4, 4))
+        bv[:, :3, :3] = b3
+        row = np.repeat(np.arange(m3["nb"]), np.diff(m3["browptr"]))
+        bv[row == m3["bcol"], 3, 3] = 2.0
+    return dict(nb=m3["nb"], bs=bs, browptr=m3["browptr"], bcol=m3["bcol"], bval=np.ascontiguousarray(bv).reshape(-1))
+
+
+@pytest.mark.parametrize("bs", [2, 4])
+def test_wave_block_ilu0_other_block_sizes(rs, ctx, orc, bs):
+    """2x2 and 4x4 blocks: in FP64 every block size runs its components on
+    separate compute warps (2 and 4 of them), in FP32 on one."""
+    shape = (13, 11, 7)
+    m = _blocks_of_size(synth.black_oil_bsr3(synth.Grid(*shape), 18), bs)
+    A = rs.Mat.bsr(ctx, m)
+    Ao = orc.Mat.bsr(m)
+    st, _, lu_ref, dinv_ref = orc.bilu0(Ao)
+    assert st == 0
+    r = np.random.default_rng(19).standard_normal(A.n)
+    for prec in ("fp64", "mixed"):
+        M = rs.Precond(ctx, A, "bilu0", prec=prec, sweep="wavefront")
+        assert M.sweep_kind() == ("wavefront", shape)
+        z = rs.Vec.zeros(ctx, A.n)
+        M.apply(rs.Vec(ctx, r), z)
+        ref = orc.bilu0_solve(Ao, lu_ref, dinv_ref, r, fp32=(prec == "mixed"))
+        assert rel(z.numpy(), ref) <= (1e-12 if prec == "fp64" else 1e-5)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_wave_cpr_apply_and_fgmres(rs, ctx, orc, prec):
     """CPR on the block system: both of its ILU factors (the decoupled
